@@ -1,0 +1,424 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, exact rational integration, invariants, library routines, a dense
+direct solve and an analytic PDE solution.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_2005_03606_gb300 import inputs
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+# ---------------------------------------------------------------- closed forms
+def kref_closed(dim):
+    """eps = 1 element matrix on the unit cell: 2D 2/3, -1/6 (edge), -1/3
+    (diagonal); 3D 1/3, 0 (edge), -1/12 (face diagonal), -1/12 (body diagonal)."""
+    nv = 1 << dim
+    K = np.zeros((nv, nv))
+    for i in range(nv):
+        for j in range(nv):
+            ham = bin(i ^ j).count("1")
+            if dim == 2:
+                K[i, j] = {0: 2 / 3, 1: -1 / 6, 2: -1 / 3}[ham]
+            else:
+                K[i, j] = {0: 1 / 3, 1: 0.0, 2: -1 / 12, 3: -1 / 12}[ham]
+    return K
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 8])
+def test_constant_eps_gives_exact_stencil(dim, s):
+    # Section "Numerical computation of stencils": constant eps => eps * K_ref at every s.
+    n = 9
+    h = 1.0 / n
+    f = oracle.Field(inputs.const_field(dim, 3.5))
+    for cell in [(0,) * dim, (4,) * dim, (8, 2, 5)[:dim]]:
+        A = oracle.element_matrix(f, n, cell, s)
+        np.testing.assert_allclose(A, 3.5 * kref_closed(dim) * h ** (dim - 2), rtol=0, atol=1e-14)
+
+
+def test_assembled_stencils_match_9_and_27_point():
+    # Section "A matrix-free additive multigrid solver": 9- / 27-point stencils.
+    for dim, centre, nbr in [(2, 8 / 3, {1: -1 / 3, 2: -1 / 3}), (3, 8 / 3, {1: 0.0, 2: -1 / 6, 3: -1 / 12})]:
+        n = 3
+        h = 1.0 / n
+        A = oracle.assemble(oracle.Field(inputs.const_field(dim, 1.0)), n, 1)
+        M = dense.global_matrix(dim, n, A)
+        v = dense.vertex_index(dim, n, [1] * dim)
+        scale = h ** (dim - 2)
+        assert abs(M[v, v] - centre * scale) < 1e-14
+        for off in itertools.product([-1, 0, 1], repeat=dim):
+            k = sum(abs(o) for o in off)
+            if k == 0:
+                continue
+            w = dense.vertex_index(dim, n, [1 + o for o in off])
+            assert abs(M[v, w] - nbr[k] * scale) < 1e-14
+
+
+# ---------------------------------------------------------- exact integration
+def _exact_element_matrix(dim, n, cell, s, eps_of_sub):
+    """Exact rational integral of eps_pc grad phi_i . grad phi_j over the cell,
+    with eps constant on each of the s^d sub-boxes (Section "Numerical
+    computation of stencils"); 1D integrals of the shape-function products
+    done in closed form with Fractions."""
+    nv = 1 << dim
+
+    def i_pp(bi, bj, a, b):  # int_a^b psi_bi psi_bj dt, psi_0 = 1-t, psi_1 = t
+        def F(t):
+            if bi == 0 and bj == 0:
+                return -((1 - t) ** 3) / 3
+            if bi == 1 and bj == 1:
+                return t ** 3 / 3
+            return t ** 2 / 2 - t ** 3 / 3
+        return F(b) - F(a)
+
+    A = [[Fraction(0)] * nv for _ in range(nv)]
+    for j in itertools.product(range(s), repeat=dim):
+        e = eps_of_sub(j)
+        lo = [Fraction(j[a], s) for a in range(dim)]
+        hi = [Fraction(j[a] + 1, s) for a in range(dim)]
+        for p in range(nv):
+            for q in range(nv):
+                tot = Fraction(0)
+                for k in range(dim):
+                    sp = 1 if (p >> k) & 1 else -1
+                    sq = 1 if (q >> k) & 1 else -1
+                    term = Fraction(sp * sq) * (hi[k] - lo[k])
+                    for m in range(dim):
+                        if m != k:
+                            term *= i_pp((p >> m) & 1, (q >> m) & 1, lo[m], hi[m])
+                    tot += term
+                A[p][q] += e * tot
+    hfac = Fraction(1, n) ** (dim - 2)
+    return np.array([[float(A[p][q] * hfac) for q in range(nv)] for p in range(nv)])
+
+
+@pytest.mark.parametrize("dim,s", [(2, 2), (2, 3), (3, 2)])
+def test_element_matrix_matches_exact_rational_integration(dim, s):
+    fld = inputs.boxes_field(dim, seed=11, n_boxes=6, contrast=7.0, side=(0.1, 0.4))
+    f = oracle.Field(fld)
+    n = 3
+    for cell in itertools.product(range(n), repeat=dim):
+        def eps_of_sub(j):
+            x = [Fraction(2 * (cell[a] * s + j[a]) + 1, 2 * n * s) for a in range(dim)]
+            inside = any(all(Fraction(fld.box_lo[b, a]) <= x[a] < Fraction(fld.box_hi[b, a])
+                             for a in range(dim)) for b in range(fld.n_boxes))
+            return Fraction(fld.v_in) if inside else Fraction(fld.v_out)
+        ex = _exact_element_matrix(dim, n, cell, s, eps_of_sub)
+        A = oracle.element_matrix(f, n, cell, s)
+        np.testing.assert_allclose(A, ex, rtol=0, atol=1e-13 * np.abs(ex).max())
+
+
+def test_s1_is_cell_centre_sample():
+    # Section "Numerical computation of stencils": n = 1 samples eps once at the cell centre.
+    for fld in [inputs.fourier_field(3, 5), inputs.boxes_field(3, 6), inputs.disc_field(3)]:
+        f = oracle.Field(fld)
+        n = 9
+        K = kref_closed(3) / n
+        for cell in [(0, 0, 0), (4, 4, 4), (8, 1, 3)]:
+            xc = [(c + 0.5) / n for c in cell]
+            ref = oracle.eps_at(f, xc) * K
+            np.testing.assert_allclose(oracle.element_matrix(f, n, cell, 1), ref,
+                                       rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
+def test_sample_coordinates_are_sub_box_centres():
+    for n, s, i, j in [(81, 8, 0, 0), (81, 8, 80, 7), (243, 16, 100, 5), (3, 1, 1, 0)]:
+        assert oracle.sample_coord(n, s, i, j) == (2 * (i * s + j) + 1) / (2 * n * s)
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("fld", [inputs.fourier_field(3, 7, sigma=1.5), inputs.boxes_field(3, 8),
+                                 inputs.theta_field(2, 16.0), inputs.disc_field(2)])
+def test_symmetry_zero_rowsum_psd(fld):
+    f = oracle.Field(fld)
+    n = 9
+    A = oracle.assemble(f, n, 4)
+    scale = np.abs(A).max(axis=(1, 2))
+    assert np.abs(A - A.transpose(0, 2, 1)).max(axis=(1, 2)).max() <= 1e-15 * scale.max()
+    assert (np.abs(A.sum(axis=2)).max(axis=1) <= 1e-14 * scale).all()
+    w = np.linalg.eigvalsh(A)
+    assert (w[:, 0] >= -1e-13 * scale).all()
+    # null space = constants: exactly one zero eigenvalue
+    assert (w[:, 1] > 1e-6 * scale).all()
+
+
+def test_eps_fields_basic_values():
+    # theta setup (Eq. "theta-setup"): eps(0) = 1 + 0.3/d
+    f = oracle.Field(inputs.theta_field(2, 4.0))
+    assert abs(oracle.eps_at(f, [0.0, 0.0]) - 1.15) < 1e-15
+    x = [0.3, 0.7]
+    ref = 1 + 0.15 * math.exp(-4 * 0.3) * math.cos(math.pi * 4 * 0.3) * math.exp(-4 * 0.7) * math.cos(math.pi * 4 * 0.7)
+    assert abs(oracle.eps_at(f, x) - ref) < 1e-15
+    fd = oracle.Field(inputs.disc_field(2))
+    assert oracle.eps_at(fd, [0.5, 0.5]) == 10.0 and oracle.eps_at(fd, [0.1, 0.1]) == 1.0
+    ff = inputs.fourier_field(3, 99, sigma=1.0, n_modes=4)
+    x = np.array([0.2, 0.4, 0.9])
+    g = sum(math.cos(2 * math.pi * float(ff.k[m] @ x) + ff.phase[m]) for m in range(4))
+    assert abs(oracle.eps_at(oracle.Field(ff), x) - math.exp(math.sqrt(2 / 4) * g)) < 1e-13
+    fj = inputs.fourier_field(3, 99, sigma=1.0, n_modes=4, jump_x=0.37, jump_factor=1e4)
+    x1 = np.array([0.37, 0.4, 0.9])
+    assert abs(oracle.eps_at(oracle.Field(fj), x1) / oracle.eps_at(oracle.Field(ff), x1) - 1e4) < 1e-9
+    x2 = np.array([0.36, 0.4, 0.9])
+    assert oracle.eps_at(oracle.Field(fj), x2) == oracle.eps_at(oracle.Field(ff), x2)
+
+
+# ---------------------------------------------------------------- convergence
+def test_quadrature_converges_second_order_for_smooth_eps():
+    # eps smooth => piecewise-constant midpoint sampling converges as O(1/s^2)
+    from scipy import integrate
+    fld = inputs.theta_field(2, 1.0)
+    f = oracle.Field(fld)
+    n, cell = 3, (1, 2)
+    h = 1.0 / n
+
+    def eps(x, y):
+        return oracle.eps_at(f, [(cell[0] + x) * h, (cell[1] + y) * h])
+
+    def integrand(y, x, p, q):
+        gp = [(1 if (p & 1) else -1) * ((y if (p >> 1) & 1 else 1 - y)),
+              (1 if (p >> 1) & 1 else -1) * ((x if p & 1 else 1 - x))]
+        gq = [(1 if (q & 1) else -1) * ((y if (q >> 1) & 1 else 1 - y)),
+              (1 if (q >> 1) & 1 else -1) * ((x if q & 1 else 1 - x))]
+        return eps(x, y) * (gp[0] * gq[0] + gp[1] * gq[1])
+
+    ex = np.array([[integrate.dblquad(integrand, 0, 1, 0, 1, args=(p, q), epsabs=1e-13, epsrel=1e-13)[0]
+                    for q in range(4)] for p in range(4)])
+    errs = [np.abs(oracle.element_matrix(f, n, cell, s) - ex).max() for s in (2, 4, 8, 16)]
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.6 < r < 4.4 for r in ratios), ratios
+
+
+def test_jump_error_envelope():
+    # Discontinuous eps: not monotone in s, but bounded by an O(1/s) envelope.
+    fld = inputs.fourier_field(2, 3, sigma=0.0, jump_x=0.37, jump_factor=100.0)
+    f = oracle.Field(fld)
+    n, cell = 3, (1, 1)
+    ref = oracle.element_matrix(f, n, cell, 600)
+    nrm = np.abs(ref).max()
+    for s in (1, 2, 4, 8, 16, 32):
+        err = np.abs(oracle.element_matrix(f, n, cell, s) - ref).max() / nrm
+        assert err <= 1.0 / s, (s, err)
+
+
+# ---------------------------------------------------------------- Galerkin
+@pytest.mark.parametrize("dim", [2, 3])
+def test_galerkin_equals_rediscretisation_at_3s(dim):
+    # Nested d-linear spaces: P^T A_h(s) P = A_3h(3s) for piecewise constant eps sampled
+    # on the same sub-boxes (Section "Rediscretisation ... vs Ritz-Galerkin").
+    for fld in [inputs.boxes_field(dim, 21), inputs.fourier_field(dim, 22, sigma=1.0)]:
+        f = oracle.Field(fld)
+        nf, s = 9, 2
+        Af = oracle.assemble(f, nf, s)
+        Ac = oracle.galerkin(dim, nf // 3, Af)
+        Ad = oracle.assemble(f, nf // 3, 3 * s)
+        np.testing.assert_allclose(Ac, Ad, rtol=0, atol=1e-13 * np.abs(Ad).max())
+
+
+def test_galerkin_constant_eps():
+    for dim in (2, 3):
+        f = oracle.Field(inputs.const_field(dim, 2.0))
+        Ac = oracle.galerkin(dim, 3, oracle.assemble(f, 9, 1))
+        for C in range(Ac.shape[0]):
+            np.testing.assert_allclose(Ac[C], 2.0 * kref_closed(dim) * (1 / 3) ** (dim - 2), atol=1e-14)
+
+
+# ---------------------------------------------------------------- transfers
+@pytest.mark.parametrize("dim", [2, 3])
+def test_prolongation_exact_for_linear_functions(dim):
+    nc = 3
+    nf = 9
+
+    def grid(n):
+        pts = np.indices((n + 1,) * dim).reshape(dim, -1)[::-1] / n
+        return pts
+
+    def lin(p):
+        return 0.3 + 1.7 * p[0] - 0.6 * p[1] + (0.9 * p[2] if dim == 3 else 0)
+
+    ec = lin(grid(nc)) * dense.interior_mask(dim, nc)
+    ef = oracle.prolong_add(dim, nc, ec, np.zeros((nf + 1) ** dim))
+    # interior fine vertices whose coarse cell has no boundary vertex see the exact linear function
+    pf = grid(nf)
+    far = np.ones(pf.shape[1], bool)
+    for a in range(dim):
+        far &= (pf[a] >= 1 / 3) & (pf[a] <= 2 / 3)
+    np.testing.assert_allclose(ef[far], lin(pf)[far], atol=1e-14)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_restriction_is_transpose(dim):
+    rng = np.random.default_rng(1)
+    nc, nf = 3, 9
+    r = rng.standard_normal((nf + 1) ** dim) * dense.interior_mask(dim, nf)
+    e = rng.standard_normal((nc + 1) ** dim) * dense.interior_mask(dim, nc)
+    lhs = oracle.restrict(dim, nc, r) @ e
+    rhs = r @ oracle.prolong_add(dim, nc, e, np.zeros_like(r))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+# ---------------------------------------------------------------- smoother and solver
+def test_jacobi_matches_dense_formula():
+    dim, n = 2, 9
+    f = oracle.Field(inputs.disc_field(2))
+    A = oracle.assemble(f, n, 4)
+    M = dense.global_matrix(dim, n, A)
+    m = dense.interior_mask(dim, n)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(M.shape[0]) * m
+    b = rng.standard_normal(M.shape[0]) * m
+    ref = u.copy()
+    Mi = M[np.ix_(m, m)]
+    ref[m] = u[m] + 0.6 * (b[m] - Mi @ u[m]) / np.diag(Mi)
+    np.testing.assert_allclose(oracle.jacobi(dim, n, A, b, u, 0.6), ref, atol=1e-13)
+    np.testing.assert_allclose(oracle.apply(dim, n, A, u)[m], Mi @ u[m], atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,n,fld", [(2, 9, inputs.disc_field(2)), (2, 27, inputs.boxes_field(2, 5)),
+                                       (3, 9, inputs.fourier_field(3, 6, sigma=1.0)),
+                                       (2, 3, inputs.disc_field(2))])
+def test_multigrid_matches_dense_solve(dim, n, fld):
+    f = oracle.Field(fld)
+    A = oracle.assemble(f, n, 4)
+    rhs = oracle.load_vector(dim, n, 1.0)
+    u_ref = dense.dense_solve(dim, n, A, rhs)
+    u, hist, k = oracle.solve(dim, n, A, rtol=1e-12, max_cycles=300)
+    assert hist[-1] <= 1e-12
+    assert np.abs(u - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
+
+
+def test_vcycle_reduces_error():
+    dim, n = 2, 27
+    A = oracle.assemble(oracle.Field(inputs.disc_field(2)), n, 2)
+    u, hist, k = oracle.solve(dim, n, A, rtol=1e-8, max_cycles=100, outer=oracle.OUTER_RICHARDSON)
+    assert k < 40
+    assert all(hist[i + 1] < hist[i] for i in range(len(hist) - 1))
+    # both outer loops reach the same solution
+    u2, hist2, k2 = oracle.solve(dim, n, A, rtol=1e-8, max_cycles=100, outer=oracle.OUTER_FCG)
+    assert k2 <= k
+    assert np.abs(u - u2).max() <= 1e-6 * np.abs(u).max()
+
+
+def test_fcg_handles_high_contrast():
+    # the stationary V(2,2) iteration stagnates for contrast 1e3; FCG with the
+    # same V-cycle as preconditioner does not
+    A = oracle.assemble(oracle.Field(inputs.boxes_field(2, 5, contrast=1e3)), 27, 4)
+    _, hist, k = oracle.solve(2, 27, A, rtol=1e-8, max_cycles=60, outer=oracle.OUTER_RICHARDSON)
+    assert hist[-1] > 1e-6
+    _, hist, k = oracle.solve(2, 27, A, rtol=1e-8, max_cycles=60, outer=oracle.OUTER_FCG)
+    assert hist[-1] <= 1e-8
+
+
+def test_theta_setup_f0_converges_to_zero():
+    # Eq. "theta-setup": with f = 0 the solution is u = 0; start from noise in [0, 4/3].
+    dim, n = 2, 27
+    fld = inputs.theta_field(2, 8.0)
+    A = oracle.assemble(oracle.Field(fld), n, 4)
+    u0 = inputs.noise_vector(dim, n, 7)
+    u, hist, k = oracle.solve(dim, n, A, f_const=0.0, u0=u0, rtol=1e-10, max_cycles=200)
+    assert hist[-1] <= 1e-10
+    assert np.abs(u).max() <= 1e-8 * np.abs(u0).max()
+
+
+def _poisson_centre_series(dim):
+    """u(1/2,...) for -Laplace u = 1 on the unit square/cube with u = 0 on the
+    boundary, from the double/triple sine series."""
+    tot = 0.0
+    M = 401 if dim == 2 else 81
+    odd = np.arange(1, M, 2)
+    if dim == 2:
+        m, nn = np.meshgrid(odd, odd, indexing="ij")
+        sgn = (-1.0) ** ((m - 1) // 2 + (nn - 1) // 2)
+        tot = np.sum(16 / (math.pi ** 4 * m * nn * (m * m + nn * nn)) * sgn)
+    else:
+        l, m, nn = np.meshgrid(odd, odd, odd, indexing="ij")
+        sgn = (-1.0) ** ((l - 1) // 2 + (m - 1) // 2 + (nn - 1) // 2)
+        tot = np.sum(64 / (math.pi ** 5 * l * m * nn * (l * l + m * m + nn * nn)) * sgn)
+    return float(tot)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 81), (3, 27)])
+def test_poisson_centre_value(dim, n):
+    A = oracle.assemble(oracle.Field(inputs.const_field(dim, 1.0)), n, 1)
+    u, hist, k = oracle.solve(dim, n, A, rtol=1e-10, max_cycles=100)
+    U = u.reshape((n + 1,) * dim)
+    c = n // 2
+    centre = U[(slice(c, c + 2),) * dim].mean()   # d-linear value at the centre cell's midpoint
+    exact = _poisson_centre_series(dim)
+    assert abs(centre - exact) <= 3.0 * (1.0 / n) ** 2 * exact, (centre, exact)
+
+
+# ---------------------------------------------------------------- storage formats
+def test_e4m3_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    vals = np.concatenate([rng.uniform(-448, 448, 3000), rng.uniform(-1, 1, 2000),
+                           rng.uniform(-0.02, 0.02, 2000),
+                           np.array([0.0, 448.0, -448.0, 2.0 ** -9, 2.0 ** -10, 3 * 2.0 ** -10,
+                                     1.0625, 1.1875, 17.0, 19.0, 240.0, 272.0])]).astype(np.float32)
+    ref = torch.from_numpy(vals).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = np.array([oracle.round_e4m3(float(v)) for v in vals])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_f16_rounding_matches_numpy():
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([rng.uniform(-65504, 65504, 3000), rng.uniform(-1, 1, 3000),
+                           rng.uniform(-1e-5, 1e-5, 2000),
+                           np.array([0.0, 65504.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -25, 1 + 2.0 ** -11,
+                                     1 + 3 * 2.0 ** -11])])
+    ref = vals.astype(np.float16).astype(np.float64)
+    got = np.array([oracle.round_f16(float(v)) for v in vals])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_compression_rules_and_error_bound():
+    dim, n, s, tau = 3, 9, 4, 1e-6
+    for fld in [inputs.fourier_field(3, 31, sigma=0.02), inputs.fourier_field(3, 31, sigma=1e-5),
+                inputs.boxes_field(3, 32), inputs.fourier_field(3, 33, sigma=1e-7)]:
+        f = oracle.Field(fld)
+        A = oracle.assemble(f, n, s)
+        At, cls, sc = oracle.compress(f, n, A, tau)
+        K = kref_closed(3) / n
+        for c in range(A.shape[0]):
+            cc = np.unravel_index(c, (n,) * 3, order="F")
+            ec = float(np.float32(oracle.eps_at(f, [oracle.sample_coord(n, 1, int(i), 0) for i in cc])))
+            D = A[c] - ec * K
+            Dm = max(abs(D[i, j]) for i in range(8) for j in range(i + 1, 8))
+            An = np.abs(A[c]).max()
+            err = np.abs(At[c] - A[c]).max()
+            if cls[c] == 0:
+                assert 7 * Dm <= tau * An and err <= tau * An * (1 + 1e-12)
+            elif cls[c] in (1, 2):
+                assert 7 * Dm > tau * An
+                assert err <= tau * An * (1 + 1e-9) + 1e-15 * An
+            else:
+                assert err <= 7 * 2.0 ** -24 * Dm + 1e-15 * An
+            # symmetric, zero row sums by construction
+            assert np.abs(At[c] - At[c].T).max() == 0.0
+            assert np.abs(At[c].sum(axis=1)).max() <= 1e-14 * An
+    # constant eps: every cell stores no payload (the paper's p3 = 0)
+    f = oracle.Field(inputs.const_field(3, 1.0))
+    _, cls, _ = oracle.compress(f, n, oracle.assemble(f, n, 4), tau)
+    assert (cls == 0).all()
+
+
+def test_compression_class_mix():
+    # fields of decreasing smoothness reach every storage class
+    f = oracle.Field(inputs.fourier_field(3, 41, sigma=1.0))
+    A = oracle.assemble(f, 9, 4)
+    _, cls, _ = oracle.compress(f, 9, A, 1e-6)
+    assert (cls == 3).mean() > 0.9
+    f = oracle.Field(inputs.fourier_field(3, 41, sigma=2e-5))
+    A = oracle.assemble(f, 9, 4)
+    _, cls, _ = oracle.compress(f, 9, A, 1e-6)
+    assert set(np.unique(cls)) >= {1, 2}
