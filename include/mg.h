@@ -1,0 +1,263 @@
+/*
+ * mg.h - C ABI of the GB300 delayed-assembly multigrid library (libmg.so).
+ *
+ * Solves -div(eps grad u) = f on the unit square / cube with u = 0 on the
+ * boundary, using d-linear Ritz-Galerkin finite elements on a regular grid of
+ * N^d cells, N = 3^L (Murray & Weinzierl, "Delayed approximate matrix
+ * assembly in multigrid with dynamic precisions", Section "A matrix-free
+ * additive multigrid solver on spacetrees": nodal d-linear elements giving
+ * 9-/27-point stencils; 3:1 refinement of the spacetree).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an mg_status; no exception crosses the ABI.  On an
+ *     error, mg_last_error() returns a thread-local message.
+ *   - Descriptors passed in are caller-owned and copied; the library owns all
+ *     device memory it allocates.  Host buffers passed to mg_get_* are
+ *     caller-owned and written synchronously.
+ *   - Vertex arrays are the full (N+1)^d grid, lexicographic with x fastest,
+ *     boundary entries included (they are zero).  Cells are numbered the same
+ *     way on the N^d grid.  The 2^d local vertices of a cell are numbered by
+ *     the bits (b_x, b_y[, b_z]) of the local index.
+ *   - Work is issued on the problem's CUDA stream (given at creation or owned
+ *     by the problem); calls that return host data synchronise that stream.
+ *   - One problem must not be used from two threads at once; distinct
+ *     problems may be used concurrently.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,        /* bad argument: size not 3^L, bad dim, null pointer, ... */
+  MG_ERR_OOM = 2,            /* device or host allocation failed, or above the HBM budget */
+  MG_ERR_CUDA = 3,           /* a CUDA call failed (message in mg_last_error) */
+  MG_ERR_TIMEOUT = 4,        /* a bounded wait ran out */
+  MG_ERR_DIVERGED = 5,       /* ||r|| grew above 1e2 ||r_0|| */
+  MG_ERR_NOT_CONVERGED = 6,  /* max_cycles reached before rtol */
+  MG_ERR_PENDING = 7,        /* request not finished yet (mg_poll) */
+  MG_ERR_CANCELLED = 8,      /* request cancelled or server shut down */
+  MG_ERR_INJECTED = 9        /* failure injected on the host for tests */
+} mg_status;
+
+/* Material field families (eps > 0).  The field is evaluated at sub-box
+ * centres x = (2(i s + j) + 1) / (2 N s) per axis, i the cell and j the
+ * sub-box index (Section "Numerical computation of stencils": eps is taken
+ * constant on each of the s^d sub-boxes of a cell). */
+typedef enum {
+  MG_EPS_CONST = 0,    /* eps = v_out */
+  MG_EPS_DISC = 1,     /* eps = v_in if |x - center|^2 < radius^2 else v_out */
+  MG_EPS_FOURIER = 2,  /* eps = v_out exp(sigma sqrt(2/M) sum_m cos(2 pi k_m.x + phase_m)) */
+  MG_EPS_BOXES = 3,    /* eps = v_in inside the union of [lo, hi) boxes, else v_out */
+  MG_EPS_THETA = 4     /* eps = 1 + (0.3/d) prod_i exp(-theta x_i) cos(pi theta x_i)
+                          (the paper's Eq. "theta-setup") */
+} mg_eps_kind;
+
+#define MG_MAX_MODES 32
+#define MG_MAX_BOXES 64
+
+typedef struct {
+  int32_t kind;          /* mg_eps_kind */
+  int32_t n_modes;       /* FOURIER: M, 1..MG_MAX_MODES */
+  int32_t n_boxes;       /* BOXES: 1..MG_MAX_BOXES */
+  int32_t pad0;
+  double v_out;          /* constant value / background / Fourier base factor */
+  double v_in;           /* DISC and BOXES inside value */
+  double center[3];      /* DISC */
+  double radius;         /* DISC */
+  double sigma;          /* FOURIER amplitude */
+  double theta;          /* THETA */
+  double jump_x;         /* all kinds: eps *= jump_factor where x_0 >= jump_x */
+  double jump_factor;    /* 1 = no jump */
+  int32_t k[MG_MAX_MODES][3];  /* FOURIER integer wavenumbers */
+  double phase[MG_MAX_MODES];  /* FOURIER phases */
+  double box_lo[MG_MAX_BOXES][3];
+  double box_hi[MG_MAX_BOXES][3];
+} mg_eps_desc;
+
+/* Operator storage and arithmetic of a solve. */
+typedef enum {
+  /* element matrices at s_schedule[n_s-1] in FP64, assembled before the first
+   * cycle (the paper's a priori assembly, p = (T, _, 8)); FP64 everywhere */
+  MG_PATH_FP64_PLAIN = 0,
+  /* FP64 storage and arithmetic; cycling starts on the geometric stencils
+   * (s = 1) while s_schedule[1..] are assembled on a side stream and
+   * published at cycle boundaries (Section "Asynchronous and anarchic
+   * stencil integration") */
+  MG_PATH_FP64_DELAYED = 1,
+  /* as FP64_DELAYED, but the fine element matrices are stored as FP32 cell
+   * centre eps plus a lossy hierarchical surplus (FP8-e4m3 / FP16 / FP32 with
+   * an FP32 per-cell scale; Section "Precision toggling and information
+   * density"), V-cycles run in FP32 and the outer residual, norms and the
+   * coarsest solve in FP64 */
+  MG_PATH_MIXED_DELAYED = 2,
+  /* mixed storage/arithmetic, final accuracy assembled before cycling */
+  MG_PATH_MIXED_PLAIN = 3
+} mg_path;
+
+typedef enum {
+  MG_OUTER_FCG = 0,        /* flexible CG (Notay FCG(1)) preconditioned by the V-cycle */
+  MG_OUTER_RICHARDSON = 1  /* residual correction u += V(f - A u) */
+} mg_outer;
+
+typedef struct {
+  int32_t dim;             /* 2 or 3 */
+  int32_t n_cells;         /* cells per axis, 3^L with L >= 1 */
+  mg_eps_desc eps;
+  double f_const;          /* right-hand side f (constant) */
+  int32_t path;            /* mg_path */
+  int32_t outer;           /* mg_outer */
+  int32_t s_schedule[8];   /* accuracies (sub-boxes per axis), increasing; the
+                              last one is final.  Delayed paths start at s = 1. */
+  int32_t n_s;             /* 1..8 */
+  double compress_tau;     /* mixed paths: per-cell entry error bound relative
+                              to max|A_c| (0 => 1e-6) */
+  double omega;            /* Jacobi damping (0 => 0.6) */
+  int32_t nu_pre, nu_post; /* smoothing steps (0,0 => 2,2) */
+  double rtol;             /* stop at ||f - A u||_2 <= rtol ||f||_2 (0 => 1e-8) */
+  int32_t max_cycles;      /* (0 => 500) */
+  int32_t chunks;          /* delayed assembly chunks along the last axis (0 => auto) */
+  const double* u0;        /* optional host initial guess, (N+1)^d values; NULL => 0.
+                              Read during mg_create_problem only. */
+} mg_problem_desc;
+
+typedef struct {
+  int32_t status;          /* mg_status of the solve */
+  int32_t cycles;          /* V-cycles (outer iterations) run */
+  int32_t publishes;       /* chunk publications applied during the solve */
+  int32_t final_s;         /* accuracy of the operator at the end */
+  double rel_residual;     /* ||f - A u||_2 / ||f||_2, FP64, stored operator */
+  double time_ms;          /* wall time of mg_solve */
+  double assembly_ms;      /* wall time spent blocked on assembly (plain paths) */
+  int64_t cells_by_class[4];   /* mixed paths: cells per storage class 0..3 */
+  int64_t payload_bytes;   /* fine-level operator bytes (payload + per-cell data) */
+} mg_solve_info;
+
+typedef struct mg_problem mg_problem;
+
+/* Creates a problem: allocates the level hierarchy, computes the geometric
+ * (s = 1, cell-centre eps) stencils and their Galerkin coarse operators.
+ * cuda_stream: a cudaStream_t to issue work on, or NULL for an own stream.
+ * Errors: MG_ERR_INVALID (dim, n_cells, eps, schedule), MG_ERR_OOM, MG_ERR_CUDA. */
+mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_problem** out);
+
+/* Frees every device and host resource of the problem (waits for its work). */
+mg_status mg_destroy_problem(mg_problem* p);
+
+/* Assembles the finest-level element matrices at accuracy s (s^d sub-boxes
+ * per cell; Section "Numerical computation of stencils", A^(geo)(n)), stores
+ * them in the problem's format and recomputes the coarse Galerkin operators.
+ * async = 0: in stream order, published at once.  async = 1: on the side
+ * stream chunk by chunk; each chunk is published at the next cycle boundary
+ * after it completes (Section "Asynchronous and anarchic stencil
+ * integration").  Errors: MG_ERR_INVALID (s < 1 or s > 64), MG_ERR_OOM, MG_ERR_CUDA. */
+mg_status mg_assemble_level(mg_problem* p, int s, int async);
+
+/* Runs n outer iterations (each one V-cycle) from the current solution,
+ * publishing completed asynchronous chunks at cycle boundaries, and returns
+ * the FP64 relative residual ||f - A u||_2 / ||f||_2 of the stored operator.
+ * rel_residual may be NULL.  Errors: MG_ERR_INVALID, MG_ERR_CUDA. */
+mg_status mg_vcycle(mg_problem* p, int n, double* rel_residual);
+
+/* Full solve according to desc->path: for plain paths assembles
+ * s_schedule[n_s-1] first; for delayed paths starts the schedule on the side
+ * stream and cycles meanwhile.  Stops when rel_residual <= rtol AND every
+ * chunk holds its final accuracy (never earlier: Section "Consistency with
+ * dynamic termination criteria and starvation effects").  info may be NULL.
+ * Errors: MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, MG_ERR_CUDA. */
+mg_status mg_solve(mg_problem* p, mg_solve_info* info);
+
+/* Copies u ((N+1)^d FP64 values) to host_dst; n must be (N+1)^d. */
+mg_status mg_get_solution(const mg_problem* p, double* host_dst, size_t n);
+
+/* Copies the stored (decoded) element matrices of level `level` (0 = finest,
+ * 1 = the next coarser, ...) as FP64, 2^d x 2^d row-major per cell, cells in
+ * index order; n must be n_cells(level)^d * 4^d. */
+mg_status mg_get_element_matrices(const mg_problem* p, int level, double* host_dst, size_t n);
+
+/* Decoded element matrices of selected cells of `level` (flat cell indices,
+ * host array of ncells entries); host_dst receives ncells * 4^d FP64 values,
+ * 2^d x 2^d row-major per cell, in the order of `cells`.  Used for sampled
+ * checks of large grids.  Errors: MG_ERR_INVALID (index out of range). */
+mg_status mg_get_cell_matrices(const mg_problem* p, int level, const int64_t* cells, size_t ncells,
+                               double* host_dst);
+
+/* Per-cell storage class (0..3) and cell-centre eps of the finest level; the
+ * arrays hold n_cells^d entries; either pointer may be NULL. */
+mg_status mg_get_cell_data(const mg_problem* p, uint8_t* cls, double* eps_c, size_t n);
+
+/* Test hooks on the stored operator of `level` (0 = finest), vectors on the
+ * host, (N_level+1)^d FP64 values each, boundary entries ignored/zero:
+ *   op = 0: y = A x (Dirichlet rows zero)
+ *   op = 1: y = x + omega diag(A)^-1 (b - A x)   (one damped Jacobi sweep)
+ *   op = 2: y = b - A x
+ * The arithmetic is the level's own (FP32 V-cycle arithmetic for mixed paths
+ * on level 0 when `inner` = 1; the FP64 outer arithmetic when inner = 0). */
+mg_status mg_apply_level(mg_problem* p, int level, int op, int inner, const double* x,
+                         const double* b, double* y);
+
+/* Runs one V-cycle e = V(b) on the finest level from e = 0 with the
+ * problem's operators; b and e are host (N+1)^d FP64 vectors. */
+mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
+
+/* ---------------- serving ---------------- */
+
+typedef struct {
+  int32_t max_active;       /* concurrent solves on the GPU (0 => 8) */
+  int32_t use_graphs;       /* capture each problem's cycle in a CUDA graph */
+  double hbm_budget_bytes;  /* admission budget (0 => free HBM at creation minus 4 GiB) */
+  int32_t inject_fail_every;/* tests: fail every k-th admission on the host (0 = off) */
+  int32_t pad0;
+} mg_server_desc;
+
+typedef struct {
+  int32_t status;           /* MG_OK when solved; error status otherwise */
+  int32_t cycles;
+  int32_t publishes;
+  int32_t pad0;
+  double rel_residual;
+  double queue_ms;          /* submit -> admission */
+  double solve_ms;          /* admission -> done */
+  double total_ms;          /* submit -> done (time to solution) */
+} mg_result;
+
+typedef struct mg_server mg_server;
+
+/* Starts a server thread that admits submitted problems while the HBM
+ * budget and max_active allow, runs their delayed-assembly solves
+ * concurrently on separate streams and records per-request results. */
+mg_status mg_server_create(const mg_server_desc* desc, mg_server** out);
+
+/* Queues a problem.  solution_dst (optional, (N+1)^d doubles, caller-owned)
+ * receives u when the request finishes; it must stay valid until mg_poll
+ * returns a final status.  ticket receives the request id. */
+mg_status mg_submit(mg_server* s, const mg_problem_desc* desc, double* solution_dst,
+                    uint64_t* ticket);
+
+/* MG_ERR_PENDING until the request finishes, then its final status; result
+ * (optional) is filled once finished. */
+mg_status mg_poll(mg_server* s, uint64_t ticket, mg_result* result);
+
+/* Blocks until every submitted request has finished or timeout_ms elapsed
+ * (MG_ERR_TIMEOUT). */
+mg_status mg_server_drain(mg_server* s, double timeout_ms);
+
+/* Cancels queued requests, waits for running ones, frees everything. */
+mg_status mg_server_destroy(mg_server* s);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* mg_last_error(void);
+
+/* Library version string. */
+const char* mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -1,0 +1,549 @@
+// Element-matrix integration at accuracy s (the paper's A^(geo)(n), Section
+// "Numerical computation of stencils"), the hierarchical surplus against the
+// geometric stencil and its lossy per-cell storage (Section "Precision
+// toggling and information density"), and the packing of the stored records.
+//
+// Integration.  eps is constant on each of the s^d sub-boxes of a cell and
+// taken at the sub-box centre x = (2(i s + j) + 1) / (2 N s).  In reference
+// coordinates xi in [0,1]^d the element matrix is
+//   A_pq = h^(d-2) sum_k sigma_k(p) sigma_k(q) int eps prod_{m != k} psi_{p_m} psi_{q_m}(xi_m) dxi,
+// psi_0 = 1 - t, psi_1 = t, sigma = -1 / +1.  Per sub-box the integral
+// factorises into 1D integrals of 1, (1-t)^2, t(1-t), t^2 over the sub-interval,
+// so a cell needs, per derivative direction k, the 3^(d-1) sums
+//   W_k[types of the other axes] = sum_sub eps' I_0(j_k) prod_{m != k} J_type(j_m)
+// with J_00 = int (1-t)^2, J_01 = int t(1-t), J_11 = int t^2.  The kernel
+// accumulates them row by row (a row = all sub-boxes with the same
+// (j_y[, j_z])), first the x-sums S_0, S_1, S_2 = sum eps' {1, t1, t2}(j_x),
+// then the row's 27 (3D) / 6 (2D) products.  eps' = eps - eps_c, so the result
+// is directly the surplus A(s) - A(1) and A(1) = eps_c K_ref h^(d-2).
+//
+// Work split: one warp handles a batch of cells; the G lanes of a group share
+// one cell (rows strided over the lanes) and reduce their partial sums with
+// warp shuffles; 32/G cells are in flight per warp.
+#include "mg_internal.cuh"
+#include <cstdio>
+
+namespace mg {
+
+namespace {
+
+constexpr int kAsmThreads = 256;
+constexpr int kMaxS = 64;
+
+template <typename T> __device__ __forceinline__ T t_exp(T x);
+template <> __device__ __forceinline__ float t_exp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double t_exp<double>(double x) { return exp(x); }
+template <typename T> __device__ __forceinline__ void t_sincospi(T x, T* s, T* c);
+template <> __device__ __forceinline__ void t_sincospi<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+template <> __device__ __forceinline__ void t_sincospi<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+template <typename T> __device__ __forceinline__ T t_cospi(T x);
+template <> __device__ __forceinline__ float t_cospi<float>(float x) { return cospif(x); }
+template <> __device__ __forceinline__ double t_cospi<double>(double x) { return cospi(x); }
+
+// sample coordinate (FP64, one IEEE division, as on the host)
+__device__ __forceinline__ double sample_x(int N, int s, int i, int j) {
+  return __ddiv_rn((double)(2 * (i * s + j) + 1), (double)(2 * N * s));
+}
+
+// fraction n/(N s) in [0,2) of the phase 2 pi k.x, from the exact integer
+// k.(2 m + 1) mod 2 N s, m the global sub-index along each axis
+__device__ __forceinline__ int phase_num(const EpsDev& F, int m, int D, const int* gm, int twoNs) {
+  int acc = 0;
+  for (int a = 0; a < D; ++a) {
+    int t = (F.k[m][a] * (2 * gm[a] + 1)) % twoNs;
+    acc += t;
+  }
+  acc %= twoNs;
+  if (acc < 0) acc += twoNs;
+  return acc;
+}
+
+// smooth part of theta field along one axis: exp(-theta x) cos(pi theta x)
+template <typename T>
+__device__ __forceinline__ T theta_factor(const EpsDev& F, double x) {
+  return (T)(t_exp<T>((T)(-F.theta * x)) * t_cospi<T>((T)(F.theta * x)));
+}
+
+// eps at the centre of every cell (s = 1), FP64 or FP32
+template <int D, typename T>
+__global__ void eps_centre_kernel(const EpsDev F, int N, T* __restrict__ out) {
+  long long ncell = 1;
+  for (int a = 0; a < D; ++a) ncell *= N;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    int ci[3] = {0, 0, 0};
+    long long t = c;
+    for (int a = 0; a < D; ++a) {
+      ci[a] = (int)(t % N);
+      t /= N;
+    }
+    double x[3];
+    for (int a = 0; a < D; ++a) x[a] = sample_x(N, 1, ci[a], 0);
+    T e = (T)F.v_out;
+    if (F.kind == EPS_DISC) {
+      double r2 = 0.0;
+      for (int a = 0; a < D; ++a) {
+        double d = __dsub_rn(x[a], F.center[a]);
+        r2 = __dadd_rn(r2, __dmul_rn(d, d));
+      }
+      e = (T)(r2 < F.r2lim ? F.v_in : F.v_out);
+    } else if (F.kind == EPS_BOXES) {
+      bool in = false;
+      for (int b = 0; b < F.n_boxes && !in; ++b) {
+        bool ib = true;
+        for (int a = 0; a < D; ++a) ib = ib && (F.box_lo[b][a] <= x[a]) && (x[a] < F.box_hi[b][a]);
+        in = ib;
+      }
+      e = (T)(in ? F.v_in : F.v_out);
+    } else if (F.kind == EPS_THETA) {
+      T p = (T)1;
+      for (int a = 0; a < D; ++a) p *= theta_factor<T>(F, x[a]);
+      e = (T)1 + (T)(0.3 / D) * p;
+    } else if (F.kind == EPS_FOURIER) {
+      int gm[3] = {ci[0], ci[1], ci[2]};
+      const int twoN = 2 * N;
+      T g = 0;
+      for (int m = 0; m < F.n_modes; ++m) {
+        int n = phase_num(F, m, D, gm, twoN);
+        T arg = (T)n / (T)N + (T)F.phi_over_pi[m];
+        g += t_cospi<T>(arg);
+      }
+      e = (T)F.v_out * t_exp<T>((T)F.amp * g);
+    }
+    if (F.jump_factor != 1.0 && x[0] >= F.jump_x) e *= (T)F.jump_factor;
+    out[c] = e;
+  }
+}
+
+struct XEntry {
+  unsigned long long bits;  // BOXES: mask of boxes whose x-interval holds the sample; DISC: dx^2 (FP64 bits)
+  double jmul;              // planar jump multiplier
+  double th;                // THETA: x-factor
+};
+
+template <int D, typename T, int KIND>
+__global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, const AsmLaunch A) {
+  constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
+  constexpr int NW = D == 3 ? 27 : 6;
+  const int N = A.N, s = A.s;
+  __shared__ T s_t1[kMaxS], s_t2[kMaxS];
+  __shared__ T s_rot_c[kMaxModes], s_rot_s[kMaxModes];
+  __shared__ XEntry s_x[kAsmThreads / 32][64];
+  for (int j = threadIdx.x; j < s; j += blockDim.x) {
+    s_t1[j] = (T)(2 * j + 1) / (T)(2 * s);
+    s_t2[j] = (T)(3 * j * j + 3 * j + 1) / (T)(3 * s * s);
+  }
+  if (KIND == EPS_FOURIER) {
+    for (int m = threadIdx.x; m < F.n_modes; m += blockDim.x) {
+      T sn, cs;
+      t_sincospi<T>((T)(2.0 * F.k[m][0] / ((double)N * s)), &sn, &cs);
+      s_rot_c[m] = cs;
+      s_rot_s[m] = sn;
+    }
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int R = 1;
+  for (int a = 1; a < D; ++a) R *= s;
+  int G = 1;
+  while (G * 2 <= R && G < 32) G *= 2;
+  const int CPW = 32 / G;
+  const int grp = lane / G, lig = lane % G;
+  XEntry* xt = &s_x[warp][0];
+  const int xt_stride = s;  // entries per group (CPW * s <= 64 by construction)
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  const T* eps_c = reinterpret_cast<const T*>(A.eps_c);
+  const T invs = (T)1 / (T)s;
+
+  for (long long base = gwarp * CPW; base < A.ncell; base += nwarps * CPW) {
+    const long long lc = base + grp;
+    const bool valid = lc < A.ncell;
+    const long long c = A.cell0 + (valid ? lc : 0);
+    int ci[3] = {0, 0, 0};
+    {
+      long long t = c;
+      for (int a = 0; a < D; ++a) {
+        ci[a] = (int)(t % N);
+        t /= N;
+      }
+    }
+    const T eref = eps_c[c];
+    // x-axis table of the group's cell
+    for (int jx = lig; jx < s; jx += G) {
+      double x = sample_x(N, s, ci[0], jx);
+      XEntry e;
+      e.bits = 0;
+      e.th = 0;
+      e.jmul = (F.jump_factor != 1.0 && x >= F.jump_x) ? F.jump_factor : 1.0;
+      if (KIND == EPS_BOXES) {
+        unsigned long long m = 0;
+        for (int b = 0; b < F.n_boxes; ++b)
+          if (F.box_lo[b][0] <= x && x < F.box_hi[b][0]) m |= 1ull << b;
+        e.bits = m;
+      } else if (KIND == EPS_DISC) {
+        double d = __dsub_rn(x, F.center[0]);
+        e.bits = (unsigned long long)__double_as_longlong(__dmul_rn(d, d));
+      } else if (KIND == EPS_THETA) {
+        e.th = (double)theta_factor<T>(F, x);
+      }
+      xt[grp * xt_stride + jx] = e;
+    }
+    __syncwarp();
+    unsigned long long cand = 0;
+    if (KIND == EPS_BOXES)
+      for (int jx = 0; jx < s; ++jx) cand |= xt[grp * xt_stride + jx].bits;
+
+    T W[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) W[q] = 0;
+
+    for (int r = lig; r < R && valid; r += G) {
+      const int jy = r % s, jz = (D == 3) ? r / s : 0;
+      // per-row set-up
+      unsigned long long rowbits = ~0ull;
+      double rowd = 0.0;
+      T rowth = (T)1;
+      T P_re[KIND == EPS_FOURIER ? kMaxModes : 1], P_im[KIND == EPS_FOURIER ? kMaxModes : 1];
+      const double y = sample_x(N, s, ci[1], jy);
+      const double z = D == 3 ? sample_x(N, s, ci[2], jz) : 0.0;
+      if (KIND == EPS_BOXES) {
+        unsigned long long m = 0, cb = cand;
+        while (cb) {
+          int b = __ffsll((long long)cb) - 1;
+          cb &= cb - 1;
+          bool ok = F.box_lo[b][1] <= y && y < F.box_hi[b][1];
+          if (D == 3) ok = ok && F.box_lo[b][2] <= z && z < F.box_hi[b][2];
+          if (ok) m |= 1ull << b;
+        }
+        rowbits = m;
+      } else if (KIND == EPS_DISC) {
+        double dy = __dsub_rn(y, F.center[1]);
+        rowd = __dmul_rn(dy, dy);
+      } else if (KIND == EPS_THETA) {
+        rowth = theta_factor<T>(F, y);
+        if (D == 3) rowth = rowth * theta_factor<T>(F, z);
+      } else if (KIND == EPS_FOURIER) {
+        int gm[3] = {ci[0] * s, ci[1] * s + jy, D == 3 ? ci[2] * s + jz : 0};
+        const int twoNs = 2 * N * s;
+        for (int m = 0; m < F.n_modes; ++m) {
+          int n = phase_num(F, m, D, gm, twoNs);
+          T sn, cs;
+          t_sincospi<T>((T)n / (T)(N * s) + (T)F.phi_over_pi[m], &sn, &cs);
+          P_re[m] = cs;
+          P_im[m] = sn;
+        }
+      }
+      double dz2 = 0.0;
+      if (KIND == EPS_DISC && D == 3) {
+        double dz = __dsub_rn(z, F.center[2]);
+        dz2 = __dmul_rn(dz, dz);
+      }
+      T S0 = 0, S1 = 0, S2 = 0;
+      for (int jx = 0; jx < s; ++jx) {
+        const XEntry& xe = xt[grp * xt_stride + jx];
+        T e;
+        if (KIND == EPS_CONST) {
+          e = (T)F.v_out;
+        } else if (KIND == EPS_BOXES) {
+          e = (T)((xe.bits & rowbits) ? F.v_in : F.v_out);
+        } else if (KIND == EPS_DISC) {
+          double r2 = __dadd_rn(__longlong_as_double((long long)xe.bits), rowd);
+          if (D == 3) r2 = __dadd_rn(r2, dz2);
+          e = (T)(r2 < F.r2lim ? F.v_in : F.v_out);
+        } else if (KIND == EPS_THETA) {
+          e = (T)1 + (T)(0.3 / D) * ((T)xe.th * rowth);
+        } else {
+          T g = 0;
+          for (int m = 0; m < F.n_modes; ++m) {
+            g += P_re[m];
+            T nr = P_re[m] * s_rot_c[m] - P_im[m] * s_rot_s[m];
+            T ni = P_re[m] * s_rot_s[m] + P_im[m] * s_rot_c[m];
+            P_re[m] = nr;
+            P_im[m] = ni;
+          }
+          e = (T)F.v_out * t_exp<T>((T)F.amp * g);
+        }
+        if (xe.jmul != 1.0) e *= (T)xe.jmul;
+        const T ep = e - eref;
+        S0 += ep;
+        S1 += ep * s_t1[jx];
+        S2 += ep * s_t2[jx];
+      }
+      // J-type sums along x: (1-t)^2 = 1 - 2t + t^2, t(1-t) = t - t^2, t^2
+      const T RJ[3] = {S0 - (T)2 * S1 + S2, S1 - S2, S2};
+      const T t1y = s_t1[jy], t2y = s_t2[jy];
+      const T jyv[3] = {(T)1 - (T)2 * t1y + t2y, t1y - t2y, t2y};
+      if (D == 2) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          W[t] += S0 * jyv[t];      // d/dx term: other axis y
+          W[3 + t] += RJ[t];        // d/dy term: other axis x
+        }
+      } else {
+        const T t1z = s_t1[jz], t2z = s_t2[jz];
+        const T jzv[3] = {(T)1 - (T)2 * t1z + t2z, t1z - t2z, t2z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            W[a * 3 + b] += S0 * jyv[a] * jzv[b];      // d/dx: (y, z)
+            W[9 + a * 3 + b] += RJ[a] * jzv[b];        // d/dy: (x, z)
+            W[18 + a * 3 + b] += RJ[a] * jyv[b];       // d/dz: (x, y)
+          }
+      }
+    }
+    // reduce over the group's lanes
+    for (int off = G / 2; off >= 1; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < NW; ++q) W[q] += __shfl_xor_sync(0xffffffffu, W[q], off);
+    }
+    if (lig == 0 && valid) {
+      T scale = (T)A.hfac;
+      for (int a = 0; a < D; ++a) scale *= invs;
+      T dl[NP];
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = a + 1; b < NV; ++b) {
+          T v = 0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const T sg = (((a >> k) & 1) == ((b >> k) & 1)) ? (T)1 : (T)-1;
+            int idx = 0;
+#pragma unroll
+            for (int m = 0; m < D; ++m)
+              if (m != k) idx = idx * 3 + (((a >> m) & 1) + ((b >> m) & 1));
+            v += sg * W[k * (NW / D) + idx];
+          }
+          dl[pair_index(NV, a, b)] = v * scale;
+        }
+      if (A.prec64) {
+        double* out = reinterpret_cast<double*>(A.out_full);
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+          for (int b = a + 1; b < NV; ++b) {
+            const int p = pair_index(NV, a, b);
+            out[(long long)p * A.ncell + lc] =
+                (double)eref * kref_off<D>(popc_small(a ^ b)) * A.hfac + (double)dl[p];
+          }
+      } else {
+        // storage class from the surplus size (rule also used by the oracle, in FP32 here)
+        float Dm = 0.f, An = 0.f;
+        float rs[NV];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) rs[a] = 0.f;
+        const float ge = (float)eref * (float)A.hfac;
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+          for (int b = a + 1; b < NV; ++b) {
+            const int p = pair_index(NV, a, b);
+            const float d = (float)dl[p];
+            Dm = fmaxf(Dm, fabsf(d));
+            An = fmaxf(An, fabsf(ge * (float)kref_off<D>(popc_small(a ^ b)) + d));
+            rs[a] += d;
+            rs[b] += d;
+          }
+#pragma unroll
+        for (int a = 0; a < NV; ++a) An = fmaxf(An, fabsf(ge * (float)kref_diag<D>() - rs[a]));
+        const float Fm = (float)Dim<D>::F, tau = (float)A.tau;
+        int cls;
+        if (Fm * Dm <= tau * An) cls = 0;
+        else if (Fm * Dm * (16.f / 448.f) <= tau * An) cls = 1;
+        else if (Fm * Dm * (16.f / 65504.f) <= tau * An) cls = 2;
+        else cls = 3;
+        uint8_t* rec = A.out_rec + (size_t)lc * Dim<D>::REC_MAX;
+        if (cls == 1) {
+          const float sc = Dm / 448.f;
+          *reinterpret_cast<float*>(rec) = sc;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            __nv_fp8_e4m3 q((float)dl[p] / sc);
+            rec[4 + p] = q.__x;
+          }
+        } else if (cls == 2) {
+          const float sc = Dm / 65504.f;
+          *reinterpret_cast<float*>(rec) = sc;
+#pragma unroll
+          for (int p = 0; p < NP; ++p)
+            *reinterpret_cast<__half*>(rec + 4 + 2 * p) = __float2half_rn((float)dl[p] / sc);
+        } else if (cls == 3) {
+#pragma unroll
+          for (int p = 0; p < NP; ++p) *reinterpret_cast<float*>(rec + 4 * p) = (float)dl[p];
+        }
+        const long long row = lc / N;
+        const int x = (int)(lc - row * N);
+        A.out_cls[(row * A.nseg_x + (x >> 5)) * kSegCells + (x & 31)] = (uint8_t)cls;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// FP64 full store of the geometric stencils eps_c K_ref h^(d-2) (s = 1)
+template <int D>
+__global__ void geometric_full_kernel(double hfac, const double* __restrict__ eps_c, long long cell0,
+                                      long long ncell, double* __restrict__ out) {
+  constexpr int NV = Dim<D>::NV;
+  for (long long lc = blockIdx.x * (long long)blockDim.x + threadIdx.x; lc < ncell;
+       lc += (long long)gridDim.x * blockDim.x) {
+    const double e = eps_c[cell0 + lc] * hfac;
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int b = a + 1; b < NV; ++b)
+        out[(long long)pair_index(NV, a, b) * ncell + lc] = e * kref_off<D>(popc_small(a ^ b));
+  }
+}
+
+// per-segment class counts (one warp per segment)
+__global__ void pack_count_kernel(long long nseg, const uint8_t* __restrict__ cls,
+                                  uint32_t* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  for (long long seg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; seg < nseg;
+       seg += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int c = cls[seg * kSegCells + lane];
+    for (int k = 1; k <= 3; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, c == k);
+      if (lane == 0) counts[(k - 1) * nseg + seg] = __popc(m);
+    }
+  }
+}
+
+// exclusive scan of counts[k][0..nseg) in place, one block per class; totals[k]
+__global__ void scan_kernel(long long nseg, uint32_t* __restrict__ counts, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t part[1024];
+  uint32_t* c = counts + blockIdx.x * nseg;
+  const long long per = (nseg + blockDim.x - 1) / blockDim.x;
+  const long long b0 = threadIdx.x * per;
+  const long long b1 = b0 + per < nseg ? b0 + per : nseg;
+  uint32_t sum = 0;
+  for (long long i = b0; i < b1; ++i) sum += c[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (long long i = b0; i < b1; ++i) {
+    uint32_t v = c[i];
+    c[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == blockDim.x - 1) totals[blockIdx.x] = part[threadIdx.x];
+}
+
+template <int D>
+__global__ void pack_copy_kernel(long long nseg, const uint8_t* __restrict__ cls,
+                                 const uint32_t* __restrict__ seg_base, int N, int nseg_x,
+                                 const uint8_t* __restrict__ rec, uint8_t* __restrict__ p1,
+                                 uint8_t* __restrict__ p2, uint8_t* __restrict__ p3) {
+  const int lane = threadIdx.x & 31;
+  for (long long seg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; seg < nseg;
+       seg += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int c = cls[seg * kSegCells + lane];
+    const long long row = seg / nseg_x;
+    const int x = (int)(seg - row * nseg_x) * kSegCells + lane;
+    for (int k = 1; k <= 3; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, c == k);
+      if (c == k && x < N) {
+        const unsigned r = __popc(m & ((1u << lane) - 1u));
+        const int rb = k == 1 ? Dim<D>::REC1 : (k == 2 ? Dim<D>::REC2 : Dim<D>::REC3);
+        uint8_t* dst = (k == 1 ? p1 : (k == 2 ? p2 : p3)) + (size_t)(seg_base[(k - 1) * nseg + seg] + r) * rb;
+        const uint4* src = reinterpret_cast<const uint4*>(rec + (size_t)(row * N + x) * Dim<D>::REC_MAX);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        for (int q = 0; q < rb / 16; ++q) d4[q] = src[q];
+      }
+    }
+  }
+}
+
+int grid_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b > 152LL * 64) b = 152LL * 64;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <int D, typename T>
+cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
+  int R = 1;
+  for (int d = 1; d < D; ++d) R *= a.s;
+  int G = 1;
+  while (G * 2 <= R && G < 32) G *= 2;
+  const long long warps = (a.ncell * G + 31) / 32;
+  long long blocks = (warps + kAsmThreads / 32 - 1) / (kAsmThreads / 32);
+  const long long cap = 152LL * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  const EpsDev& F = *a.eps_host;
+  switch (F.kind) {
+    case EPS_CONST: assemble_kernel<D, T, EPS_CONST><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
+    case EPS_DISC: assemble_kernel<D, T, EPS_DISC><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
+    case EPS_FOURIER: assemble_kernel<D, T, EPS_FOURIER><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
+    case EPS_BOXES: assemble_kernel<D, T, EPS_BOXES><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
+    case EPS_THETA: assemble_kernel<D, T, EPS_THETA><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st) {
+  long long ncell = (long long)N * N * (dim == 3 ? N : 1);
+  int g = grid_for(ncell, 256);
+  if (dim == 2) {
+    if (prec64) eps_centre_kernel<2, double><<<g, 256, 0, st>>>(*eps, N, (double*)eps_c);
+    else eps_centre_kernel<2, float><<<g, 256, 0, st>>>(*eps, N, (float*)eps_c);
+  } else {
+    if (prec64) eps_centre_kernel<3, double><<<g, 256, 0, st>>>(*eps, N, (double*)eps_c);
+    else eps_centre_kernel<3, float><<<g, 256, 0, st>>>(*eps, N, (float*)eps_c);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const AsmLaunch& a, cudaStream_t st) {
+  if (a.s < 1 || a.s > kMaxS) return cudaErrorInvalidValue;
+  if (a.dim == 2) return a.prec64 ? launch_assemble_t<2, double>(a, st) : launch_assemble_t<2, float>(a, st);
+  return a.prec64 ? launch_assemble_t<3, double>(a, st) : launch_assemble_t<3, float>(a, st);
+}
+
+cudaError_t launch_geometric_full(int dim, int N, double hfac, const double* eps_c, long long cell0,
+                                  long long ncell, double* out, cudaStream_t st) {
+  (void)N;
+  int g = grid_for(ncell, 256);
+  if (dim == 2) geometric_full_kernel<2><<<g, 256, 0, st>>>(hfac, eps_c, cell0, ncell, out);
+  else geometric_full_kernel<3><<<g, 256, 0, st>>>(hfac, eps_c, cell0, ncell, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_count(int dim, int N, long long nrows, int nseg_x, const uint8_t* cls,
+                              uint32_t* seg_base, uint32_t* totals, cudaStream_t st) {
+  (void)dim;
+  (void)N;
+  const long long nseg = nrows * nseg_x;
+  pack_count_kernel<<<grid_for(nseg * 32, 256), 256, 0, st>>>(nseg, cls, seg_base);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scan_kernel<<<3, 1024, 0, st>>>(nseg, seg_base, totals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const uint8_t* cls,
+                             const uint32_t* seg_base, const uint8_t* rec, uint8_t* p1, uint8_t* p2,
+                             uint8_t* p3, cudaStream_t st) {
+  const long long nseg = nrows * nseg_x;
+  const int g = grid_for(nseg * 32, 256);
+  if (dim == 2) pack_copy_kernel<2><<<g, 256, 0, st>>>(nseg, cls, seg_base, N, nseg_x, rec, p1, p2, p3);
+  else pack_copy_kernel<3><<<g, 256, 0, st>>>(nseg, cls, seg_base, N, nseg_x, rec, p1, p2, p3);
+  return cudaGetLastError();
+}
+
+}  // namespace mg

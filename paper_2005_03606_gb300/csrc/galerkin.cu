@@ -1,0 +1,376 @@
+// Ritz-Galerkin coarse operators A_{l-1} = R A_l P with d-linear 3:1
+// transfers (Section "Rediscretisation and geometric projections between
+// levels vs. Ritz-Galerkin plus algebraic operators"), computed element by
+// element: for coarse cell C,
+//   A_C = sum over its 3^d children f of P_f^T A_f P_f,
+// P_f the d-linear interpolation from C's vertices to f's vertices.  With
+// A_f = -sum_{a<b} A_ab (e_a - e_b)(e_a - e_b)^T (symmetric, zero row sums),
+//   (A_C)_IJ = -sum_f sum_{a<b} A_f,ab (P_aI - P_bI)(P_aJ - P_bJ),
+// which keeps zero row sums by construction.  Children stored as
+// eps_c K_ref + surplus contribute eps_c * G_f (G_f = P_f^T K_ref P_f, a
+// constant table) plus the surplus term, so children of storage class 0 cost
+// one multiply per coarse entry.
+//
+// The coarsest level (3 cells per axis, 2^d interior unknowns) is solved by
+// an FP64 Cholesky factorisation formed once per operator update.
+#include "mg_internal.cuh"
+
+#include <mutex>
+
+namespace mg {
+
+namespace {
+
+__constant__ double c_G2[9][6];
+__constant__ double c_G3[27][28];
+bool g_tables_ready = false;
+
+template <int D>
+__host__ __device__ inline double pweight(int o, int bit_fine, int bit_coarse) {
+  const double t = (o + bit_fine) / 3.0;
+  return bit_coarse ? t : 1.0 - t;
+}
+
+template <int D>
+__host__ __device__ inline void child_P(int ch, double P[Dim<D>::NV][Dim<D>::NV]) {
+  constexpr int NV = Dim<D>::NV;
+  int o[3] = {ch % 3, (ch / 3) % 3, ch / 9};
+  for (int a = 0; a < NV; ++a)
+    for (int I = 0; I < NV; ++I) {
+      double w = 1.0;
+      for (int m = 0; m < D; ++m) w *= pweight<D>(o[m], (a >> m) & 1, (I >> m) & 1);
+      P[a][I] = w;
+    }
+}
+
+template <int D>
+void host_G(double* G) {  // [nchild][NP]
+  constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
+  const int nch = D == 3 ? 27 : 9;
+  for (int ch = 0; ch < nch; ++ch) {
+    double P[NV][NV];
+    child_P<D>(ch, P);
+    for (int I = 0; I < NV; ++I)
+      for (int J = I + 1; J < NV; ++J) {
+        double acc = 0.0;
+        for (int a = 0; a < NV; ++a)
+          for (int b = a + 1; b < NV; ++b) {
+            const double k = kref_off<D>(popc_small(a ^ b));
+            acc -= k * (P[a][I] - P[b][I]) * (P[a][J] - P[b][J]);
+          }
+        G[ch * NP + pair_index(NV, I, J)] = acc;
+      }
+  }
+}
+
+std::mutex g_tables_mu;
+
+cudaError_t ensure_tables() {
+  std::lock_guard<std::mutex> lk(g_tables_mu);
+  if (g_tables_ready) return cudaSuccess;
+  double g2[9 * 6], g3[27 * 28];
+  host_G<2>(g2);
+  host_G<3>(g3);
+  cudaError_t e = cudaMemcpyToSymbol(c_G2, g2, sizeof(g2));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_G3, g3, sizeof(g3));
+  if (e == cudaSuccess) g_tables_ready = true;
+  return e;
+}
+
+// off-diagonals of the fine cell (i,j,k) (full storage) into A[NP]
+template <int D, typename TA, typename TS>
+__device__ __forceinline__ void load_full(const LevelOp& op, int ci, int cj, int ck, TA* A) {
+  constexpr int NP = Dim<D>::NP;
+  const int N = op.N;
+  const long long c = D == 2 ? (long long)cj * N + ci : ((long long)ck * N + cj) * N + ci;
+  int ch = (D == 2 ? cj : ck) / op.layers;
+  if (ch >= op.nchunk) ch = op.nchunk - 1;
+  const long long lc = c - (long long)ch * op.chunk_cells;
+  const TS* a = reinterpret_cast<const TS*>(op.full[ch].a);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) A[p] = (TA)a[(long long)p * op.chunk_cells + lc];
+}
+
+template <int D, typename TA, typename TS, typename TC, bool CMP>
+__global__ void galerkin_kernel(const LevelOp fine, int last0, int last1, TC* __restrict__ out) {
+  constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
+  const int Nc = fine.N / 3;
+  const long long per_layer = D == 2 ? (long long)Nc : (long long)Nc * Nc;
+  const long long ncc_total = per_layer * Nc;
+  const long long c_begin = (long long)last0 * per_layer, c_end = (long long)last1 * per_layer;
+  for (long long C = c_begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; C < c_end;
+       C += (long long)gridDim.x * blockDim.x) {
+    const int I0 = (int)(C % Nc);
+    const int J0 = (int)((C / Nc) % Nc);
+    const int K0 = D == 3 ? (int)(C / ((long long)Nc * Nc)) : 0;
+    TA acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = 0;
+    const int nch = D == 3 ? 27 : 9;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int ox = ch % 3, oy = (ch / 3) % 3, oz = ch / 9;
+      const int fi = 3 * I0 + ox, fj = 3 * J0 + oy, fk = D == 3 ? 3 * K0 + oz : 0;
+      TA A[NP];
+      bool have_full = true;
+      if (CMP) {
+        const long long c = D == 2 ? (long long)fj * fine.N + fi : ((long long)fk * fine.N + fj) * fine.N + fi;
+        const TA ge = (TA)fine.eps_c[c] * (TA)fine.hfac;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) acc[p] += ge * (TA)(D == 3 ? c_G3[ch][p] : c_G2[ch][p]);
+        int chn = (D == 2 ? fj : fk) / fine.layers;
+        if (chn >= fine.nchunk) chn = fine.nchunk - 1;
+        const long long lc = c - (long long)chn * fine.chunk_cells;
+        const CmpChunk& ck = fine.cmp[chn];
+        const int cls = cell_class(ck, fine.N, fine.nseg_x, lc);
+        if (cls == 0) {
+          have_full = false;
+        } else {
+          const uint8_t* rec = cell_record<D>(ck, fine.N, fine.nseg_x, lc, cls);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) A[p] = (TA)decode_entry<D>(rec, cls, p);
+        }
+      } else {
+        load_full<D, TA, TS>(fine, fi, fj, fk, A);
+      }
+      if (!have_full) continue;
+      // interpolation weights of this child: P[a][I] = prod_m w(o_m, a_m, I_m)
+      TA P[NV][NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int I = 0; I < NV; ++I) {
+          TA w = 1;
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            const int o = m == 0 ? ox : (m == 1 ? oy : oz);
+            const TA t = (TA)(o + ((a >> m) & 1)) / (TA)3;
+            w *= ((I >> m) & 1) ? t : (TA)1 - t;
+          }
+          P[a][I] = w;
+        }
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = a + 1; b < NV; ++b) {
+          const TA v = A[pair_index(NV, a, b)];
+          TA q[NV];
+#pragma unroll
+          for (int I = 0; I < NV; ++I) q[I] = P[a][I] - P[b][I];
+#pragma unroll
+          for (int I = 0; I < NV; ++I)
+#pragma unroll
+            for (int J = I + 1; J < NV; ++J) acc[pair_index(NV, I, J)] -= v * q[I] * q[J];
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[(long long)p * ncc_total + C] = (TC)acc[p];
+  }
+}
+
+// dense interior system of the coarsest level (N = 3) and its Cholesky factor
+template <int D, typename TS>
+__global__ void coarse_factor_kernel(const LevelOp op, double* L) {
+  constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n = NV;  // 2^d interior vertices (1..2 per axis)
+  double M[NV][NV];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) M[i][j] = 0.0;
+  const TS* a = reinterpret_cast<const TS*>(op.full[0].a);
+  const long long ncell = op.chunk_cells;
+  const int ncell_i = D == 3 ? 27 : 9;
+  for (int c = 0; c < ncell_i; ++c) {
+    const int ci = c % 3, cj = (c / 3) % 3, ck = c / 9;
+    int gidx[NV];
+    for (int b = 0; b < NV; ++b) {
+      const int vx = ci + (b & 1), vy = cj + ((b >> 1) & 1), vz = D == 3 ? ck + ((b >> 2) & 1) : 1;
+      const bool in = vx >= 1 && vx <= 2 && vy >= 1 && vy <= 2 && vz >= 1 && vz <= 2;
+      gidx[b] = in ? (vx - 1) + 2 * (vy - 1) + (D == 3 ? 4 * (vz - 1) : 0) : -1;
+    }
+    double A[NV][NV];
+    for (int x = 0; x < NV; ++x) A[x][x] = 0.0;
+    for (int x = 0; x < NV; ++x)
+      for (int y = x + 1; y < NV; ++y) {
+        const double v = (double)a[(long long)pair_index(NV, x, y) * ncell + c];
+        A[x][y] = v;
+        A[y][x] = v;
+        A[x][x] -= v;
+        A[y][y] -= v;
+      }
+    for (int x = 0; x < NV; ++x)
+      for (int y = 0; y < NV; ++y)
+        if (gidx[x] >= 0 && gidx[y] >= 0) M[gidx[x]][gidx[y]] += A[x][y];
+  }
+  (void)NP;
+  for (int j = 0; j < n; ++j) {
+    double s = M[j][j];
+    for (int k = 0; k < j; ++k) s -= M[j][k] * M[j][k];
+    M[j][j] = sqrt(s);
+    for (int i = j + 1; i < n; ++i) {
+      double t = M[i][j];
+      for (int k = 0; k < j; ++k) t -= M[i][k] * M[j][k];
+      M[i][j] = t / M[j][j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) L[i * n + j] = j <= i ? M[i][j] : 0.0;
+}
+
+template <int D, typename TV>
+__global__ void coarse_solve_kernel(const double* __restrict__ L, const TV* __restrict__ b, TV* __restrict__ e) {
+  constexpr int n = Dim<D>::NV;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double z[n];
+  long long vid[n];
+  for (int t = 0; t < n; ++t) {
+    const int vx = 1 + (t & 1), vy = 1 + ((t >> 1) & 1), vz = D == 3 ? 1 + ((t >> 2) & 1) : 0;
+    vid[t] = D == 3 ? ((long long)vz * 4 + vy) * 4 + vx : (long long)vy * 4 + vx;
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = (double)b[vid[i]];
+    for (int k = 0; k < i; ++k) t -= L[i * n + k] * z[k];
+    z[i] = t / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = z[i];
+    for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * z[k];
+    z[i] = t / L[i * n + i];
+  }
+  for (int i = 0; i < n; ++i) e[vid[i]] = (TV)z[i];
+}
+
+template <int D, typename TS, bool CMP>
+__global__ void decode_kernel(const LevelOp op, const long long* __restrict__ cells, long long nout,
+                              double* __restrict__ out) {
+  constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
+  const int N = op.N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nout;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = cells ? cells[t] : t;
+    const int ci = (int)(c % N), cj = (int)((c / N) % N), ck = D == 3 ? (int)(c / ((long long)N * N)) : 0;
+    double A[NP];
+    if (CMP) {
+      const double ge = (double)op.eps_c[c] * op.hfac;
+      int ch = (D == 2 ? cj : ck) / op.layers;
+      if (ch >= op.nchunk) ch = op.nchunk - 1;
+      const long long lc = c - (long long)ch * op.chunk_cells;
+      const CmpChunk& chk = op.cmp[ch];
+      const int cls = cell_class(chk, N, op.nseg_x, lc);
+      const uint8_t* rec = cls ? cell_record<D>(chk, N, op.nseg_x, lc, cls) : nullptr;
+      for (int a = 0; a < NV; ++a)
+        for (int b = a + 1; b < NV; ++b) {
+          const int p = pair_index(NV, a, b);
+          double v = ge * kref_off<D>(popc_small(a ^ b));
+          if (cls) v += (double)decode_entry<D>(rec, cls, p);
+          A[p] = v;
+        }
+    } else {
+      load_full<D, double, TS>(op, ci, cj, ck, A);
+    }
+    double* M = out + t * NV * NV;
+    for (int a = 0; a < NV; ++a) M[a * NV + a] = 0.0;
+    for (int a = 0; a < NV; ++a)
+      for (int b = a + 1; b < NV; ++b) {
+        const double v = A[pair_index(NV, a, b)];
+        M[a * NV + b] = v;
+        M[b * NV + a] = v;
+        M[a * NV + a] -= v;
+        M[b * NV + b] -= v;
+      }
+  }
+}
+
+int ggrid(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+// Galerkin over the coarse cell layers [last0, last1) along the last axis.
+cudaError_t launch_galerkin_range(const LevelOp& fine, int out64, void* coarse_full, int last0, int last1,
+                                  cudaStream_t st) {
+  cudaError_t e = ensure_tables();
+  if (e != cudaSuccess) return e;
+  const int Nc = fine.N / 3;
+  const long long per_layer = fine.dim == 2 ? (long long)Nc : (long long)Nc * Nc;
+  const long long n = per_layer * (last1 - last0);
+  if (n <= 0) return cudaSuccess;
+  const int T = 128;
+  const int g = ggrid(n, T);
+#define MG_GAL(D, TA, TS, TC, CMP) \
+  galerkin_kernel<D, TA, TS, TC, CMP><<<g, T, 0, st>>>(fine, last0, last1, (TC*)coarse_full)
+  if (fine.dim == 2) {
+    if (fine.compressed) {
+      if (out64) MG_GAL(2, double, float, double, true);
+      else MG_GAL(2, float, float, float, true);
+    } else if (fine.elem64) {
+      if (out64) MG_GAL(2, double, double, double, false);
+      else MG_GAL(2, double, double, float, false);
+    } else {
+      if (out64) MG_GAL(2, double, float, double, false);
+      else MG_GAL(2, float, float, float, false);
+    }
+  } else {
+    if (fine.compressed) {
+      if (out64) MG_GAL(3, double, float, double, true);
+      else MG_GAL(3, float, float, float, true);
+    } else if (fine.elem64) {
+      if (out64) MG_GAL(3, double, double, double, false);
+      else MG_GAL(3, double, double, float, false);
+    } else {
+      if (out64) MG_GAL(3, double, float, double, false);
+      else MG_GAL(3, float, float, float, false);
+    }
+  }
+#undef MG_GAL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin(const LevelOp& fine, int out64, void* coarse_full, cudaStream_t st) {
+  return launch_galerkin_range(fine, out64, coarse_full, 0, fine.N / 3, st);
+}
+
+cudaError_t launch_coarse_factor(const LevelOp& coarsest, double* L, cudaStream_t st) {
+  if (coarsest.N != 3 || coarsest.compressed) return cudaErrorInvalidValue;
+  if (coarsest.dim == 2) {
+    if (coarsest.elem64) coarse_factor_kernel<2, double><<<1, 32, 0, st>>>(coarsest, L);
+    else coarse_factor_kernel<2, float><<<1, 32, 0, st>>>(coarsest, L);
+  } else {
+    if (coarsest.elem64) coarse_factor_kernel<3, double><<<1, 32, 0, st>>>(coarsest, L);
+    else coarse_factor_kernel<3, float><<<1, 32, 0, st>>>(coarsest, L);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void* b, void* e, cudaStream_t st) {
+  if (dim == 2) {
+    if (vec64) coarse_solve_kernel<2, double><<<1, 32, 0, st>>>(L, (const double*)b, (double*)e);
+    else coarse_solve_kernel<2, float><<<1, 32, 0, st>>>(L, (const float*)b, (float*)e);
+  } else {
+    if (vec64) coarse_solve_kernel<3, double><<<1, 32, 0, st>>>(L, (const double*)b, (double*)e);
+    else coarse_solve_kernel<3, float><<<1, 32, 0, st>>>(L, (const float*)b, (float*)e);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_matrices(const LevelOp& op, const long long* cells, long long ncells, double* out,
+                                   cudaStream_t st) {
+  const long long ncell = cells ? ncells : (long long)op.N * op.N * (op.dim == 3 ? op.N : 1);
+  const int g = ggrid(ncell, 128);
+  if (op.dim == 2) {
+    if (op.compressed) decode_kernel<2, float, true><<<g, 128, 0, st>>>(op, cells, ncell, out);
+    else if (op.elem64) decode_kernel<2, double, false><<<g, 128, 0, st>>>(op, cells, ncell, out);
+    else decode_kernel<2, float, false><<<g, 128, 0, st>>>(op, cells, ncell, out);
+  } else {
+    if (op.compressed) decode_kernel<3, float, true><<<g, 128, 0, st>>>(op, cells, ncell, out);
+    else if (op.elem64) decode_kernel<3, double, false><<<g, 128, 0, st>>>(op, cells, ncell, out);
+    else decode_kernel<3, float, false><<<g, 128, 0, st>>>(op, cells, ncell, out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,235 @@
+// Internal definitions shared by the CUDA translation units of libmg.so.
+//
+// Element matrices (Eq. "weak-form-of-assembly", one 2^d x 2^d matrix per
+// cell) are symmetric with zero row sums, so only the NP = 2^d (2^d - 1) / 2
+// off-diagonal entries a < b are stored; the diagonal is minus the row sum.
+// Pair p(a, b), a < b, is numbered lexicographically.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace mg {
+
+constexpr int kMaxLevels = 12;
+constexpr int kMaxModes = 32;
+constexpr int kMaxBoxes = 64;
+constexpr int kSegCells = 32;  // cells per storage segment along x
+
+template <int D>
+struct Dim {
+  static constexpr int NV = 1 << D;                 // vertices per cell
+  static constexpr int NP = NV * (NV - 1) / 2;      // stored off-diagonal pairs
+  static constexpr int F = NV - 1;                  // entries per row besides the diagonal
+  // record bytes of storage classes 1 (FP8 + scale), 2 (FP16 + scale), 3 (FP32)
+  static constexpr int REC1 = D == 3 ? 32 : 16;
+  static constexpr int REC2 = D == 3 ? 64 : 16;
+  static constexpr int REC3 = D == 3 ? 112 : 32;
+  static constexpr int REC_MAX = REC3;
+};
+
+__host__ __device__ constexpr inline int pair_index(int nv, int a, int b) {
+  // a < b
+  return a * (2 * nv - a - 1) / 2 + (b - a - 1);
+}
+__host__ __device__ constexpr inline int pair_of(int nv, int a, int b) {
+  return a < b ? pair_index(nv, a, b) : pair_index(nv, b, a);
+}
+__host__ __device__ constexpr inline int popc_small(int x) {
+  return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1);
+}
+
+// eps = 1 element matrix on the unit reference cell (constant-eps precompute
+// of Section "Numerical computation of stencils"): off-diagonal value by the
+// Hamming distance of the two local vertices; physical matrix = h^(d-2) times it.
+template <int D>
+__host__ __device__ constexpr inline double kref_off(int ham) {
+  return D == 2 ? (ham == 1 ? -1.0 / 6.0 : -1.0 / 3.0) : (ham == 1 ? 0.0 : -1.0 / 12.0);
+}
+template <int D>
+__host__ __device__ constexpr inline double kref_diag() {
+  return D == 2 ? 2.0 / 3.0 : 1.0 / 3.0;
+}
+
+// ------------------------------------------------------------ material field
+enum EpsKind { EPS_CONST = 0, EPS_DISC = 1, EPS_FOURIER = 2, EPS_BOXES = 3, EPS_THETA = 4 };
+
+struct EpsDev {
+  int kind, dim, n_modes, n_boxes;
+  double v_out, v_in;
+  double center[3];
+  double r2lim;        // radius * radius (IEEE product)
+  double amp;          // sigma * sqrt(2 / M)
+  double theta;
+  double jump_x, jump_factor;
+  int k[kMaxModes][3];
+  double phi_over_pi[kMaxModes];   // phase / pi
+  double box_lo[kMaxBoxes][3];
+  double box_hi[kMaxBoxes][3];
+};
+
+// ------------------------------------------------------------ operator storage
+// Compressed finest level (mixed paths), one chunk = a slab of whole cell
+// layers along the last axis.  cls holds one byte per cell, padded to
+// kSegCells per x-row segment: cls[(row * nseg_x + sx) * 32 + lane].  Records
+// of class k (1..3) are stored in pool[k-1] ordered by segment then x;
+// seg_base[(k-1) * nseg + seg] is the number of class-k cells before segment seg.
+struct CmpChunk {
+  const uint8_t* cls;
+  const uint32_t* seg_base;
+  const uint8_t* pool[3];
+  long long nseg;
+};
+
+// Full storage: SoA off-diagonals a[p * chunk_cells + local_cell].
+struct FullChunk {
+  const void* a;
+};
+
+struct LevelOp {
+  int N;                  // cells per axis
+  int dim;
+  int layers;             // cell layers (last axis) per chunk
+  int nchunk;
+  long long chunk_cells;  // cells per chunk (layers * N^(d-1))
+  int nseg_x;             // segments per x-row
+  int compressed;         // 1: CmpChunk + eps_c; 0: FullChunk
+  int elem64;             // full storage element type: 1 double, 0 float
+  const float* eps_c;     // compressed: cell-centre eps (FP32) of all cells
+  const CmpChunk* cmp;    // device array [nchunk]
+  const FullChunk* full;  // device array [nchunk]
+  double hfac;            // h^(d-2)
+};
+
+// ------------------------------------------------------------ helpers
+__device__ __forceinline__ long long cell_index(int D, int N, int i, int j, int k) {
+  return D == 2 ? (long long)j * N + i : ((long long)k * N + j) * N + i;
+}
+
+// rank of `lane` among the cells of class k in a 32-byte class segment
+__device__ __forceinline__ unsigned rank_in_segment(const uint8_t* seg, int lane, int k) {
+  const uint4* q = reinterpret_cast<const uint4*>(seg);
+  uint4 w0 = __ldg(q), w1 = __ldg(q + 1);
+  unsigned words[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+  unsigned kk = 0x01010101u * (unsigned)k;
+  unsigned cnt = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    unsigned eq = __vcmpeq4(words[w], kk);          // 0xff per equal byte
+    int lo = w * 4;
+    unsigned keep;
+    if (lane >= lo + 4) keep = 0xffffffffu;
+    else if (lane <= lo) keep = 0u;
+    else keep = 0xffffffffu >> (8 * (4 - (lane - lo)));
+    cnt += __popc(eq & keep);
+  }
+  return cnt >> 3;
+}
+
+// Decoded surplus entry p of a record of class cls (1..3).
+template <int D>
+__device__ __forceinline__ float decode_entry(const uint8_t* rec, int cls, int p) {
+  if (cls == 1) {
+    float scale = *reinterpret_cast<const float*>(rec);
+    __nv_fp8_e4m3 v;
+    v.__x = rec[4 + p];
+    return float(v) * scale;
+  } else if (cls == 2) {
+    float scale = *reinterpret_cast<const float*>(rec);
+    __half v = *reinterpret_cast<const __half*>(rec + 4 + 2 * p);
+    return __half2float(v) * scale;
+  } else {
+    return *reinterpret_cast<const float*>(rec + 4 * p);
+  }
+}
+
+// Pointer to the record of a cell with class cls > 0 in a compressed chunk.
+template <int D>
+__device__ __forceinline__ const uint8_t* cell_record(const CmpChunk& ck, int N, int nseg_x,
+                                                      long long local_cell, int cls) {
+  long long row = local_cell / N;
+  int x = (int)(local_cell - row * N);
+  long long seg = row * nseg_x + (x >> 5);
+  const uint8_t* sg = ck.cls + seg * kSegCells;
+  unsigned r = rank_in_segment(sg, x & 31, cls);
+  unsigned base = ck.seg_base[(cls - 1) * ck.nseg + seg];
+  int recb = cls == 1 ? Dim<D>::REC1 : (cls == 2 ? Dim<D>::REC2 : Dim<D>::REC3);
+  return ck.pool[cls - 1] + (size_t)(base + r) * recb;
+}
+
+__device__ __forceinline__ uint8_t cell_class(const CmpChunk& ck, int N, int nseg_x, long long local_cell) {
+  long long row = local_cell / N;
+  int x = (int)(local_cell - row * N);
+  return ck.cls[(row * nseg_x + (x >> 5)) * kSegCells + (x & 31)];
+}
+
+// ------------------------------------------------------------ host API (internal)
+struct DevScalars {     // per-problem scalars written by reductions
+  double rr, pq, pr, zq, alpha, beta, ff, r0;
+};
+
+void set_error(const char* fmt, ...);
+bool cuda_ok(cudaError_t e, const char* what);
+
+// assemble.cu
+struct AsmLaunch {
+  int dim, N, s, kind;
+  int prec64;            // 1: FP64 arithmetic, FP64 full store; 0: FP32, compressed records
+  long long cell0, ncell;   // chunk cell range (whole layers)
+  const EpsDev* eps_host;   // field (copied into kernel parameters)
+  double hfac;
+  const void* eps_c;     // cell-centre eps of all cells (double for prec64, float otherwise)
+  void* out_full;        // prec64: SoA double [NP][ncell]
+  uint8_t* out_rec;      // !prec64: scratch records [ncell][REC_MAX]
+  uint8_t* out_cls;      // !prec64: padded class bytes of the chunk
+  int nseg_x;
+  double tau;
+};
+cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st);
+cudaError_t launch_assemble(const AsmLaunch& a, cudaStream_t st);
+cudaError_t launch_geometric_full(int dim, int N, double hfac, const double* eps_c, long long cell0,
+                                  long long ncell, double* out, cudaStream_t st);
+cudaError_t launch_pack_count(int dim, int N, long long nrows, int nseg_x, const uint8_t* cls,
+                              uint32_t* seg_base, uint32_t* totals, cudaStream_t st);
+cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const uint8_t* cls,
+                             const uint32_t* seg_base, const uint8_t* rec, uint8_t* p1, uint8_t* p2,
+                             uint8_t* p3, cudaStream_t st);
+
+// sweep.cu
+enum SweepMode { SW_JACOBI = 0, SW_RESID = 1, SW_MATVEC = 2 };
+cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, const void* b,
+                         void* y, double omega, double* partials, int* nblocks, cudaStream_t st);
+cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
+cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+// vector ops for the outer loop (FP64 vectors; n = vertices)
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks,
+                       cudaStream_t st);
+cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double* partials, int* nblocks,
+                           cudaStream_t st);
+cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out,
+                                 cudaStream_t st);
+enum ScalarOp { SC_SET_BETA = 0, SC_SET_ALPHA = 1 };
+cudaError_t launch_scalar_op(DevScalars* sc, int op, cudaStream_t st);
+cudaError_t launch_fcg_direction(long long n, int first, int z64, const void* z, double* p,
+                                 const DevScalars* sc, cudaStream_t st);
+cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p, const double* q,
+                              const DevScalars* sc, int r32_out, void* rin, double* partials,
+                              int* nblocks, cudaStream_t st);
+cudaError_t launch_richardson_update(long long n, double* u, int z64, const void* z, cudaStream_t st);
+cudaError_t launch_convert(long long n, int to64, const void* src, void* dst, cudaStream_t st);
+cudaError_t launch_load_vector(int dim, int N, double val, double* f, cudaStream_t st);
+
+// galerkin.cu
+cudaError_t launch_galerkin(const LevelOp& fine, int out64, void* coarse_full, cudaStream_t st);
+cudaError_t launch_galerkin_range(const LevelOp& fine, int out64, void* coarse_full, int last0, int last1,
+                                  cudaStream_t st);
+cudaError_t launch_coarse_factor(const LevelOp& coarsest, double* L, cudaStream_t st);
+cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void* b, void* e,
+                                cudaStream_t st);
+cudaError_t launch_decode_matrices(const LevelOp& op, const long long* cells, long long ncells, double* out,
+                                   cudaStream_t st);
+
+}  // namespace mg

@@ -1,0 +1,1194 @@
+// Problem lifecycle, V-cycle and outer-loop orchestration, delayed assembly
+// and the C ABI entry points for single problems (declared in include/mg.h).
+//
+// Level l = 0 is the finest grid (N cells per axis), level L-1 the coarsest
+// (3 cells per axis).  The finest operator is split into chunks of whole cell
+// layers along the last axis; each chunk holds the stencils of one accuracy s
+// and is replaced as a unit when a better one has been assembled (the
+// marker p1 of Section "Stencil assembly variants" per chunk; the in-flight
+// marker p2 is the chunk's pending job).  Coarse levels hold element matrices
+// produced by the Galerkin kernel.
+#include "mg_internal.cuh"
+#include "mg.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace mg {
+
+static thread_local std::string t_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+}
+
+bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return false;
+}
+
+const char* last_error() { return t_err.c_str(); }
+
+}  // namespace mg
+
+using namespace mg;
+
+#define MG_CHECK(call)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) {                        \
+      set_error("%s: %s", #call, cudaGetErrorString(e_)); \
+      return MG_ERR_CUDA;                           \
+    }                                               \
+  } while (0)
+
+namespace {
+
+struct ChunkStore {
+  int s = 0;
+  void* a64 = nullptr;            // FP64 full storage [NP][chunk_cells]
+  uint8_t* cls = nullptr;         // compressed: padded classes
+  uint32_t* seg_base = nullptr;   // compressed: [3][nseg]
+  uint8_t* pool[3] = {nullptr, nullptr, nullptr};
+  uint32_t totals[3] = {0, 0, 0};
+  size_t bytes = 0;
+};
+
+struct Level {
+  int N = 0;
+  long long ncell = 0, nvert = 0;
+  LevelOp op{};
+  FullChunk* d_full = nullptr;
+  CmpChunk* d_cmp = nullptr;
+  void* full_store = nullptr;     // coarse levels: single chunk
+  void* b = nullptr;              // V-cycle right-hand side (TV)
+  void* x0 = nullptr;             // V-cycle iterates (TV)
+  void* x1 = nullptr;
+};
+
+struct Job {
+  int s = 0, chunk = 0;
+  cudaEvent_t ev = nullptr;
+  ChunkStore store;
+  int status = MG_OK;
+};
+
+}  // namespace
+
+struct mg_problem {
+  mg_problem_desc desc{};
+  EpsDev eps{};
+  int dim = 0, N = 0, L = 0;
+  bool mixed = false, delayed = false;
+  cudaStream_t st = nullptr, side = nullptr;
+  bool own_stream = false;
+  size_t tv = 8;                  // V-cycle vector element size
+  std::vector<Level> lev;
+  // finest-level chunking
+  int nchunk = 1, layers = 1, nseg_x = 1;
+  long long chunk_cells = 0, chunk_rows = 0, chunk_nseg = 0;
+  std::vector<ChunkStore> cur;
+  std::vector<FullChunk> h_full;
+  std::vector<CmpChunk> h_cmp;
+  void* eps_c = nullptr;          // float (mixed) or double per cell
+  // outer FP64 vectors
+  double *u = nullptr, *f = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+  double* partials = nullptr;
+  long long npartials = 0;
+  DevScalars* sc = nullptr;
+  DevScalars* h_sc = nullptr;     // pinned
+  double* Lc = nullptr;           // coarse Cholesky factor
+  uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
+  uint32_t* d_totals = nullptr;   // per stream: [0..2] main, [4..6] side
+  uint32_t* h_totals = nullptr;   // pinned, same layout
+  std::vector<void*> allocs;      // long-lived device allocations
+  // outer-loop state
+  bool first = true, need_restart = true;
+  double ff = 0.0, rr = 0.0, rr_first = 0.0;
+  int cycles = 0, publishes = 0;
+  cudaGraphExec_t g_iter[2] = {nullptr, nullptr};
+  bool use_graphs = true;
+  // delayed assembly
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Job> todo, ready;
+  int in_flight = 0;
+  bool stop = false;
+  int inject_fail = 0;
+};
+
+namespace {
+
+int ipow3(int L) {
+  int r = 1;
+  while (L-- > 0) r *= 3;
+  return r;
+}
+
+template <typename T>
+cudaError_t dalloc(mg_problem* P, T** ptr, size_t bytes, bool track = true) {
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, P->st);
+  if (e != cudaSuccess) return e;
+  *ptr = (T*)p;
+  if (track) P->allocs.push_back(p);
+  return cudaSuccess;
+}
+
+mg_status oom_or_cuda(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+}
+
+void fill_eps(const mg_eps_desc& d, int dim, EpsDev* e) {
+  memset(e, 0, sizeof(*e));
+  e->kind = d.kind;
+  e->dim = dim;
+  e->n_modes = d.n_modes;
+  e->n_boxes = d.n_boxes;
+  e->v_out = d.v_out;
+  e->v_in = d.v_in;
+  for (int a = 0; a < 3; ++a) e->center[a] = d.center[a];
+  e->r2lim = d.radius * d.radius;
+  e->amp = d.n_modes > 0 ? d.sigma * std::sqrt(2.0 / d.n_modes) : 0.0;
+  e->theta = d.theta;
+  e->jump_x = d.jump_x;
+  e->jump_factor = d.jump_factor;
+  for (int m = 0; m < MG_MAX_MODES; ++m) {
+    for (int a = 0; a < 3; ++a) e->k[m][a] = d.k[m][a];
+    e->phi_over_pi[m] = d.phase[m] / 3.14159265358979323846;
+  }
+  for (int b = 0; b < MG_MAX_BOXES; ++b)
+    for (int a = 0; a < 3; ++a) {
+      e->box_lo[b][a] = d.box_lo[b][a];
+      e->box_hi[b][a] = d.box_hi[b][a];
+    }
+}
+
+mg_status validate(const mg_problem_desc* d) {
+  if (!d) {
+    set_error("null descriptor");
+    return MG_ERR_INVALID;
+  }
+  if (d->dim != 2 && d->dim != 3) {
+    set_error("dim must be 2 or 3 (got %d)", d->dim);
+    return MG_ERR_INVALID;
+  }
+  int n = d->n_cells;
+  if (n < 9) {
+    set_error("n_cells must be 3^L with L >= 2 (got %d)", n);
+    return MG_ERR_INVALID;
+  }
+  while (n % 3 == 0 && n > 1) n /= 3;
+  if (n != 1) {
+    set_error("n_cells must be a power of 3 (got %d)", d->n_cells);
+    return MG_ERR_INVALID;
+  }
+  if (d->dim == 3 && d->n_cells > 729) {
+    set_error("3D n_cells above 729 not supported");
+    return MG_ERR_INVALID;
+  }
+  if (d->dim == 2 && d->n_cells > 19683) {
+    set_error("2D n_cells above 19683 not supported");
+    return MG_ERR_INVALID;
+  }
+  const mg_eps_desc& e = d->eps;
+  if (e.kind < 0 || e.kind > 4) {
+    set_error("unknown eps kind %d", e.kind);
+    return MG_ERR_INVALID;
+  }
+  if (e.kind == MG_EPS_FOURIER && (e.n_modes < 1 || e.n_modes > MG_MAX_MODES)) {
+    set_error("n_modes out of range");
+    return MG_ERR_INVALID;
+  }
+  if (e.kind == MG_EPS_FOURIER)
+    for (int m = 0; m < e.n_modes; ++m)
+      for (int a = 0; a < 3; ++a)
+        if (std::abs(e.k[m][a]) > 64) {
+          set_error("wavenumber component above 64");
+          return MG_ERR_INVALID;
+        }
+  if (e.kind == MG_EPS_BOXES && (e.n_boxes < 1 || e.n_boxes > MG_MAX_BOXES)) {
+    set_error("n_boxes out of range");
+    return MG_ERR_INVALID;
+  }
+  if (!(e.jump_factor > 0.0) || !(e.v_out > 0.0)) {
+    set_error("eps must be positive");
+    return MG_ERR_INVALID;
+  }
+  if ((e.kind == MG_EPS_DISC || e.kind == MG_EPS_BOXES) && !(e.v_in > 0.0)) {
+    set_error("eps must be positive");
+    return MG_ERR_INVALID;
+  }
+  if (d->n_s < 1 || d->n_s > 8) {
+    set_error("n_s must be 1..8");
+    return MG_ERR_INVALID;
+  }
+  for (int i = 0; i < d->n_s; ++i) {
+    if (d->s_schedule[i] < 1 || d->s_schedule[i] > 64 || (i && d->s_schedule[i] <= d->s_schedule[i - 1])) {
+      set_error("s_schedule must increase within 1..64");
+      return MG_ERR_INVALID;
+    }
+  }
+  if (d->path < 0 || d->path > 3) {
+    set_error("unknown path %d", d->path);
+    return MG_ERR_INVALID;
+  }
+  return MG_OK;
+}
+
+LevelOp& fine_op(mg_problem* P) { return P->lev[0].op; }
+
+// ------------------------------------------------------------ assembly of one chunk
+mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, ChunkStore* out, int tot_slot) {
+  const int D = P->dim;
+  const int NP = D == 3 ? 28 : 6;
+  const long long cell0 = (long long)chunk * P->chunk_cells;
+  ChunkStore cs;
+  cs.s = s;
+  if (!P->mixed) {
+    cudaError_t e = cudaMallocAsync(&cs.a64, sizeof(double) * NP * P->chunk_cells, st);
+    if (e != cudaSuccess) return oom_or_cuda(e, "chunk storage");
+    cs.bytes = sizeof(double) * NP * P->chunk_cells;
+    if (s == 1) {
+      MG_CHECK(launch_geometric_full(D, P->N, fine_op(P).hfac, (const double*)P->eps_c, cell0, P->chunk_cells,
+                                     (double*)cs.a64, st));
+    } else {
+      AsmLaunch a{};
+      a.dim = D;
+      a.N = P->N;
+      a.s = s;
+      a.kind = P->eps.kind;
+      a.prec64 = 1;
+      a.cell0 = cell0;
+      a.ncell = P->chunk_cells;
+      a.eps_host = &P->eps;
+      a.hfac = fine_op(P).hfac;
+      a.eps_c = P->eps_c;
+      a.out_full = cs.a64;
+      a.nseg_x = P->nseg_x;
+      a.tau = 0;
+      MG_CHECK(launch_assemble(a, st));
+    }
+    *out = cs;
+    return MG_OK;
+  }
+  const size_t cls_bytes = (size_t)P->chunk_nseg * kSegCells;
+  cudaError_t e = cudaMallocAsync(&cs.cls, cls_bytes, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&cs.seg_base, sizeof(uint32_t) * 3 * P->chunk_nseg, st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "chunk classes");
+  MG_CHECK(cudaMemsetAsync(cs.cls, 0, cls_bytes, st));
+  cs.bytes = cls_bytes + sizeof(uint32_t) * 3 * P->chunk_nseg;
+  if (s == 1) {
+    MG_CHECK(cudaMemsetAsync(cs.seg_base, 0, sizeof(uint32_t) * 3 * P->chunk_nseg, st));
+    *out = cs;
+    return MG_OK;
+  }
+  AsmLaunch a{};
+  a.dim = D;
+  a.N = P->N;
+  a.s = s;
+  a.kind = P->eps.kind;
+  a.prec64 = 0;
+  a.cell0 = cell0;
+  a.ncell = P->chunk_cells;
+  a.eps_host = &P->eps;
+  a.hfac = fine_op(P).hfac;
+  a.eps_c = P->eps_c;
+  a.out_rec = P->scratch;
+  a.out_cls = cs.cls;
+  a.nseg_x = P->nseg_x;
+  a.tau = P->desc.compress_tau;
+  MG_CHECK(launch_assemble(a, st));
+  uint32_t* dt = P->d_totals + tot_slot;
+  uint32_t* ht = P->h_totals + tot_slot;
+  MG_CHECK(launch_pack_count(D, P->N, P->chunk_rows, P->nseg_x, cs.cls, cs.seg_base, dt, st));
+  MG_CHECK(cudaMemcpyAsync(ht, dt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, st));
+  MG_CHECK(cudaStreamSynchronize(st));
+  const int rb[3] = {D == 3 ? 32 : 16, D == 3 ? 64 : 16, D == 3 ? 112 : 32};
+  for (int k = 0; k < 3; ++k) {
+    cs.totals[k] = ht[k];
+    if (ht[k]) {
+      e = cudaMallocAsync(&cs.pool[k], (size_t)ht[k] * rb[k], st);
+      if (e != cudaSuccess) return oom_or_cuda(e, "payload pool");
+      cs.bytes += (size_t)ht[k] * rb[k];
+    }
+  }
+  MG_CHECK(launch_pack_copy(D, P->N, P->chunk_rows, P->nseg_x, cs.cls, cs.seg_base, P->scratch, cs.pool[0],
+                            cs.pool[1], cs.pool[2], st));
+  *out = cs;
+  return MG_OK;
+}
+
+void free_store(ChunkStore& cs, cudaStream_t st) {
+  if (cs.a64) cudaFreeAsync(cs.a64, st);
+  if (cs.cls) cudaFreeAsync(cs.cls, st);
+  if (cs.seg_base) cudaFreeAsync(cs.seg_base, st);
+  for (int k = 0; k < 3; ++k)
+    if (cs.pool[k]) cudaFreeAsync(cs.pool[k], st);
+  cs = ChunkStore();
+}
+
+// install a store as the published operator of a chunk (host mirror only)
+void install(mg_problem* P, int chunk, const ChunkStore& cs) {
+  free_store(P->cur[chunk], P->st);   // stream-ordered: kernels already queued keep the old store
+  P->cur[chunk] = cs;
+  if (P->mixed) {
+    CmpChunk c{};
+    c.cls = cs.cls;
+    c.seg_base = cs.seg_base;
+    for (int k = 0; k < 3; ++k) c.pool[k] = cs.pool[k];
+    c.nseg = P->chunk_nseg;
+    P->h_cmp[chunk] = c;
+  } else {
+    P->h_full[chunk].a = cs.a64;
+  }
+}
+
+mg_status upload_tables(mg_problem* P) {
+  Level& l0 = P->lev[0];
+  if (P->mixed)
+    MG_CHECK(cudaMemcpyAsync(l0.d_cmp, P->h_cmp.data(), sizeof(CmpChunk) * P->nchunk, cudaMemcpyHostToDevice, P->st));
+  else
+    MG_CHECK(cudaMemcpyAsync(l0.d_full, P->h_full.data(), sizeof(FullChunk) * P->nchunk, cudaMemcpyHostToDevice,
+                             P->st));
+  // pageable source: the copy is staged before return, the host mirror may change afterwards
+  return MG_OK;
+}
+
+mg_status rebuild_coarse(mg_problem* P) {
+  for (int l = 0; l + 1 < P->L; ++l)
+    MG_CHECK(launch_galerkin(P->lev[l].op, P->mixed ? 0 : 1, P->lev[l + 1].full_store, P->st));
+  MG_CHECK(launch_coarse_factor(P->lev[P->L - 1].op, P->Lc, P->st));
+  return MG_OK;
+}
+
+// ------------------------------------------------------------ V-cycle
+void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
+  Level& lv = P->lev[l];
+  const int vec64 = P->mixed ? 0 : 1;
+  cudaStream_t st = P->st;
+  cudaError_t e;
+  if (l == P->L - 1) {
+    e = launch_coarse_solve(P->dim, P->Lc, vec64, lv.b, lv.x0, st);
+    if (e != cudaSuccess) *stt = oom_or_cuda(e, "coarse solve");
+    return lv.x0;
+  }
+  const size_t vb = P->tv * lv.nvert;
+  const double om = P->desc.omega;
+  void* cur = lv.x0;
+  void* oth = lv.x1;
+  if ((e = cudaMemsetAsync(cur, 0, vb, st)) != cudaSuccess) *stt = oom_or_cuda(e, "zero");
+  for (int k = 0; k < P->desc.nu_pre; ++k) {
+    if ((e = launch_sweep(lv.op, SW_JACOBI, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
+      *stt = oom_or_cuda(e, "pre-smooth");
+    std::swap(cur, oth);
+  }
+  if ((e = launch_sweep(lv.op, SW_RESID, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
+    *stt = oom_or_cuda(e, "residual");
+  Level& lc = P->lev[l + 1];
+  if ((e = launch_restrict(P->dim, lc.N, vec64, oth, lc.b, st)) != cudaSuccess) *stt = oom_or_cuda(e, "restrict");
+  void* ec = vcycle_enqueue(P, l + 1, stt);
+  if ((e = launch_prolong_add(P->dim, lc.N, vec64, ec, cur, st)) != cudaSuccess) *stt = oom_or_cuda(e, "prolong");
+  for (int k = 0; k < P->desc.nu_post; ++k) {
+    if ((e = launch_sweep(lv.op, SW_JACOBI, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
+      *stt = oom_or_cuda(e, "post-smooth");
+    std::swap(cur, oth);
+  }
+  return cur;
+}
+
+// ------------------------------------------------------------ outer loop
+// r = f - A u (FP64), rr = r.r, V-cycle input from r; resets the Krylov direction
+mg_status outer_restart(mg_problem* P) {
+  cudaStream_t st = P->st;
+  Level& l0 = P->lev[0];
+  int nb = 0;
+  MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->r, 0.0, nullptr, nullptr, st));
+  MG_CHECK(launch_dot(P->r, P->r, l0.nvert, P->partials, &nb, st));
+  MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
+  if (P->mixed) MG_CHECK(launch_convert(l0.nvert, 0, P->r, l0.b, st));
+  P->first = true;
+  P->need_restart = false;
+  return MG_OK;
+}
+
+// one outer iteration, enqueue only
+mg_status outer_iteration_enqueue(mg_problem* P, int first) {
+  cudaStream_t st = P->st;
+  Level& l0 = P->lev[0];
+  const long long n = l0.nvert;
+  const int z64 = P->mixed ? 0 : 1;
+  mg_status stt = MG_OK;
+  void* z = vcycle_enqueue(P, 0, &stt);
+  if (stt != MG_OK) return stt;
+  int nb = 0;
+  if (P->desc.outer == MG_OUTER_RICHARDSON) {
+    MG_CHECK(launch_richardson_update(n, P->u, z64, z, st));
+    MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->r, 0.0, nullptr, nullptr, st));
+    MG_CHECK(launch_dot(P->r, P->r, n, P->partials, &nb, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
+    if (P->mixed) MG_CHECK(launch_convert(n, 0, P->r, l0.b, st));
+    return MG_OK;
+  }
+  if (!first) {
+    if (z64) MG_CHECK(launch_dot((const double*)z, P->q, n, P->partials, &nb, st));
+    else MG_CHECK(launch_dot_f32((const float*)z, P->q, n, P->partials, &nb, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st));
+    MG_CHECK(launch_scalar_op(P->sc, SC_SET_BETA, st));
+  }
+  MG_CHECK(launch_fcg_direction(n, first, z64, z, P->p, P->sc, st));
+  MG_CHECK(launch_sweep(l0.op, SW_MATVEC, 1, P->p, P->r, P->q, 0.0, P->partials, &nb, st));
+  MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st));
+  MG_CHECK(launch_scalar_op(P->sc, SC_SET_ALPHA, st));
+  MG_CHECK(launch_fcg_update(n, P->u, P->r, P->p, P->q, P->sc, P->mixed ? 1 : 0, P->mixed ? l0.b : nullptr,
+                             P->partials, &nb, st));
+  MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
+  return MG_OK;
+}
+
+mg_status outer_iteration(mg_problem* P) {
+  const int first = P->first ? 1 : 0;
+  if (P->use_graphs) {
+    if (!P->g_iter[first]) {
+      cudaGraph_t g;
+      MG_CHECK(cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal));
+      mg_status s = outer_iteration_enqueue(P, first);
+      cudaError_t e = cudaStreamEndCapture(P->st, &g);
+      if (s != MG_OK) return s;
+      if (e != cudaSuccess) return oom_or_cuda(e, "end capture");
+      e = cudaGraphInstantiate(&P->g_iter[first], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return oom_or_cuda(e, "graph instantiate");
+    }
+    MG_CHECK(cudaGraphLaunch(P->g_iter[first], P->st));
+  } else {
+    mg_status s = outer_iteration_enqueue(P, first);
+    if (s != MG_OK) return s;
+  }
+  P->first = false;
+  P->cycles++;
+  return MG_OK;
+}
+
+mg_status read_scalars(mg_problem* P) {
+  MG_CHECK(cudaMemcpyAsync(P->h_sc, P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->st));
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  P->rr = P->h_sc->rr;
+  return MG_OK;
+}
+
+// ------------------------------------------------------------ delayed assembly
+void worker_main(mg_problem* P) {
+  for (;;) {
+    Job job;
+    {
+      std::unique_lock<std::mutex> lk(P->mu);
+      P->cv.wait(lk, [&] { return P->stop || !P->todo.empty(); });
+      if (P->stop) return;
+      job = P->todo.front();
+      P->todo.pop_front();
+    }
+    if (P->inject_fail && job.s == P->inject_fail) {
+      job.status = MG_ERR_INJECTED;
+    } else {
+      job.status = assemble_chunk(P, job.s, job.chunk, P->side, &job.store, 4);
+      if (job.status == MG_OK && cudaEventRecord(job.ev, P->side) != cudaSuccess) job.status = MG_ERR_CUDA;
+    }
+    {
+      std::lock_guard<std::mutex> lk(P->mu);
+      P->ready.push_back(job);
+    }
+    P->cv.notify_all();
+  }
+}
+
+void start_worker(mg_problem* P) {
+  if (!P->worker.joinable()) P->worker = std::thread(worker_main, P);
+}
+
+mg_status enqueue_async(mg_problem* P, int s) {
+  std::lock_guard<std::mutex> lk(P->mu);
+  for (int c = 0; c < P->nchunk; ++c) {
+    Job j;
+    j.s = s;
+    j.chunk = c;
+    if (cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("event create failed");
+      return MG_ERR_CUDA;
+    }
+    P->todo.push_back(j);
+    P->in_flight++;
+  }
+  P->cv.notify_all();
+  return MG_OK;
+}
+
+// Publishes every completed job (at a cycle boundary).  wait = 1 blocks for
+// at least one job when any is in flight.  Returns the number published.
+mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
+  *npub = 0;
+  std::vector<Job> done;
+  {
+    std::unique_lock<std::mutex> lk(P->mu);
+    if (wait && P->in_flight > 0 && P->ready.empty())
+      P->cv.wait(lk, [&] { return !P->ready.empty() || P->stop; });
+    for (auto it = P->ready.begin(); it != P->ready.end();) {
+      bool complete = it->status != MG_OK;
+      if (!complete) {
+        cudaError_t q = wait && done.empty() ? cudaEventSynchronize(it->ev) : cudaEventQuery(it->ev);
+        complete = q == cudaSuccess;
+        if (q != cudaSuccess && q != cudaErrorNotReady) {
+          it->status = MG_ERR_CUDA;
+          complete = true;
+        }
+      }
+      if (complete) {
+        done.push_back(*it);
+        it = P->ready.erase(it);
+        P->in_flight--;
+      } else {
+        ++it;
+      }
+    }
+  }
+  mg_status bad = MG_OK;
+  for (Job& j : done) {
+    if (j.ev) cudaEventDestroy(j.ev);
+    if (j.status != MG_OK) {
+      bad = (mg_status)j.status;
+      set_error(j.status == MG_ERR_INJECTED ? "injected assembly failure" : "assembly job failed");
+      free_store(j.store, P->st);
+      continue;
+    }
+    if (j.store.s > P->cur[j.chunk].s) {
+      install(P, j.chunk, j.store);
+      (*npub)++;
+    } else {
+      free_store(j.store, P->st);
+    }
+  }
+  if (*npub) {
+    mg_status s = upload_tables(P);
+    if (s != MG_OK) return s;
+    s = rebuild_coarse(P);
+    if (s != MG_OK) return s;
+    P->publishes += *npub;
+    P->need_restart = true;
+  }
+  return bad;
+}
+
+void stop_worker(mg_problem* P) {
+  {
+    std::lock_guard<std::mutex> lk(P->mu);
+    P->stop = true;
+  }
+  P->cv.notify_all();
+  if (P->worker.joinable()) P->worker.join();
+  cudaStreamSynchronize(P->side);
+  for (Job& j : P->ready) {
+    if (j.ev) cudaEventDestroy(j.ev);
+    free_store(j.store, P->side);
+  }
+  for (Job& j : P->todo)
+    if (j.ev) cudaEventDestroy(j.ev);
+  P->ready.clear();
+  P->todo.clear();
+  P->in_flight = 0;
+}
+
+int final_s(const mg_problem* P) { return P->desc.s_schedule[P->desc.n_s - 1]; }
+
+bool all_final(const mg_problem* P) {
+  for (const ChunkStore& c : P->cur)
+    if (c.s < final_s(P)) return false;
+  return true;
+}
+
+int min_s(const mg_problem* P) {
+  int m = 1 << 30;
+  for (const ChunkStore& c : P->cur) m = std::min(m, c.s);
+  return m;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* mg_last_error(void) { return mg::last_error(); }
+const char* mg_version(void) { return "mg-gb300 1.0"; }
+
+mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_problem** out) {
+  if (!out) {
+    set_error("null output pointer");
+    return MG_ERR_INVALID;
+  }
+  *out = nullptr;
+  mg_status v = validate(desc);
+  if (v != MG_OK) return v;
+  mg_problem* P = new mg_problem();
+  P->desc = *desc;
+  mg_problem_desc& d = P->desc;
+  if (d.compress_tau <= 0) d.compress_tau = 1e-6;
+  if (d.omega <= 0) d.omega = 0.6;
+  if (d.nu_pre <= 0 && d.nu_post <= 0) d.nu_pre = d.nu_post = 2;
+  if (d.rtol <= 0) d.rtol = 1e-8;
+  if (d.max_cycles <= 0) d.max_cycles = 500;
+  P->dim = d.dim;
+  P->N = d.n_cells;
+  P->mixed = d.path == MG_PATH_MIXED_DELAYED || d.path == MG_PATH_MIXED_PLAIN;
+  P->delayed = d.path == MG_PATH_FP64_DELAYED || d.path == MG_PATH_MIXED_DELAYED;
+  P->tv = P->mixed ? 4 : 8;
+  fill_eps(d.eps, d.dim, &P->eps);
+  auto fail = [&](mg_status s) {
+    mg_destroy_problem(P);
+    return s;
+  };
+  if (cuda_stream) {
+    P->st = (cudaStream_t)cuda_stream;
+  } else {
+    if (!cuda_ok(cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking), "stream")) return fail(MG_ERR_CUDA);
+    P->own_stream = true;
+  }
+  if (!cuda_ok(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking), "side stream")) return fail(MG_ERR_CUDA);
+  // levels
+  int L = 0;
+  for (int n = P->N; n >= 3; n /= 3) ++L;
+  P->L = L;
+  P->lev.resize(L);
+  const int D = P->dim;
+  const int NP = D == 3 ? 28 : 6;
+  for (int l = 0; l < L; ++l) {
+    Level& lv = P->lev[l];
+    lv.N = P->N / ipow3(l);
+    lv.ncell = (long long)lv.N * lv.N * (D == 3 ? lv.N : 1);
+    lv.nvert = (long long)(lv.N + 1) * (lv.N + 1) * (D == 3 ? (lv.N + 1) : 1);
+    double h = 1.0 / lv.N;
+    LevelOp& op = lv.op;
+    op.N = lv.N;
+    op.dim = D;
+    op.hfac = D == 3 ? h : 1.0;
+    op.nseg_x = (lv.N + kSegCells - 1) / kSegCells;
+    cudaError_t e;
+    if (l > 0) {
+      op.layers = lv.N;
+      op.nchunk = 1;
+      op.chunk_cells = lv.ncell;
+      op.compressed = 0;
+      op.elem64 = P->mixed ? 0 : 1;
+      if ((e = dalloc(P, &lv.full_store, (size_t)NP * lv.ncell * (P->mixed ? 4 : 8))) != cudaSuccess)
+        return fail(oom_or_cuda(e, "coarse storage"));
+      if ((e = dalloc(P, &lv.d_full, sizeof(FullChunk))) != cudaSuccess) return fail(oom_or_cuda(e, "table"));
+      FullChunk fc{lv.full_store};
+      if (!cuda_ok(cudaMemcpyAsync(lv.d_full, &fc, sizeof(fc), cudaMemcpyHostToDevice, P->st), "table upload"))
+        return fail(MG_ERR_CUDA);
+      op.full = lv.d_full;
+    }
+    const size_t vb = P->tv * lv.nvert;
+    if ((e = dalloc(P, &lv.b, vb)) != cudaSuccess || (e = dalloc(P, &lv.x0, vb)) != cudaSuccess ||
+        (e = dalloc(P, &lv.x1, vb)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "level vectors"));
+    cudaMemsetAsync(lv.b, 0, vb, P->st);
+    cudaMemsetAsync(lv.x0, 0, vb, P->st);
+    cudaMemsetAsync(lv.x1, 0, vb, P->st);
+  }
+  // finest level chunking: slabs of whole cell layers along the last axis
+  Level& l0 = P->lev[0];
+  int nch = d.chunks > 0 ? d.chunks : (P->N >= 27 ? 9 : 1);
+  if (nch > P->N) nch = P->N;
+  P->layers = (P->N + nch - 1) / nch;
+  P->nchunk = (P->N + P->layers - 1) / P->layers;
+  if (P->N % P->layers != 0) {  // keep equal chunk sizes: fall back to one chunk
+    P->layers = P->N;
+    P->nchunk = 1;
+  }
+  P->nseg_x = l0.op.nseg_x;
+  P->chunk_cells = l0.ncell / P->nchunk;
+  P->chunk_rows = P->chunk_cells / P->N;
+  P->chunk_nseg = P->chunk_rows * P->nseg_x;
+  l0.op.layers = P->layers;
+  l0.op.nchunk = P->nchunk;
+  l0.op.chunk_cells = P->chunk_cells;
+  l0.op.compressed = P->mixed ? 1 : 0;
+  l0.op.elem64 = P->mixed ? 0 : 1;
+  P->cur.resize(P->nchunk);
+  P->h_full.resize(P->nchunk);
+  P->h_cmp.resize(P->nchunk);
+  cudaError_t e;
+  if (P->mixed) {
+    if ((e = dalloc(P, &l0.d_cmp, sizeof(CmpChunk) * P->nchunk)) != cudaSuccess) return fail(oom_or_cuda(e, "table"));
+    l0.op.cmp = l0.d_cmp;
+    if ((e = dalloc(P, &P->scratch, (size_t)P->chunk_cells * (D == 3 ? 112 : 32))) != cudaSuccess)
+      return fail(oom_or_cuda(e, "scratch"));
+  } else {
+    if ((e = dalloc(P, &l0.d_full, sizeof(FullChunk) * P->nchunk)) != cudaSuccess) return fail(oom_or_cuda(e, "table"));
+    l0.op.full = l0.d_full;
+  }
+  if ((e = dalloc(P, &P->eps_c, (size_t)l0.ncell * (P->mixed ? 4 : 8))) != cudaSuccess)
+    return fail(oom_or_cuda(e, "eps_c"));
+  if (P->mixed) l0.op.eps_c = (const float*)P->eps_c;
+  // outer vectors
+  const size_t v8 = sizeof(double) * l0.nvert;
+  if ((e = dalloc(P, &P->u, v8)) != cudaSuccess || (e = dalloc(P, &P->f, v8)) != cudaSuccess ||
+      (e = dalloc(P, &P->r, v8)) != cudaSuccess || (e = dalloc(P, &P->p, v8)) != cudaSuccess ||
+      (e = dalloc(P, &P->q, v8)) != cudaSuccess)
+    return fail(oom_or_cuda(e, "outer vectors"));
+  cudaMemsetAsync(P->u, 0, v8, P->st);
+  cudaMemsetAsync(P->r, 0, v8, P->st);
+  cudaMemsetAsync(P->p, 0, v8, P->st);
+  cudaMemsetAsync(P->q, 0, v8, P->st);
+  if (!P->mixed) {
+    // FP64 V-cycle reads its right-hand side straight from r
+    P->allocs.erase(std::find(P->allocs.begin(), P->allocs.end(), l0.b));
+    cudaFreeAsync(l0.b, P->st);
+    l0.b = P->r;
+  }
+  {
+    const long long ni = P->N - 1;
+    long long sweep_blocks = ((ni + 31) / 32) * ((ni + 7) / 8) * (D == 3 ? ni : 1);
+    P->npartials = 2 * std::max<long long>(sweep_blocks, 152 * 4) + 64;
+  }
+  if ((e = dalloc(P, &P->partials, sizeof(double) * P->npartials)) != cudaSuccess ||
+      (e = dalloc(P, &P->sc, sizeof(DevScalars))) != cudaSuccess ||
+      (e = dalloc(P, &P->Lc, sizeof(double) * 64)) != cudaSuccess ||
+      (e = dalloc(P, &P->d_totals, sizeof(uint32_t) * 8)) != cudaSuccess)
+    return fail(oom_or_cuda(e, "scalars"));
+  cudaMemsetAsync(P->sc, 0, sizeof(DevScalars), P->st);
+  if (!cuda_ok(cudaMallocHost(&P->h_sc, sizeof(DevScalars)), "pinned") ||
+      !cuda_ok(cudaMallocHost(&P->h_totals, sizeof(uint32_t) * 8), "pinned"))
+    return fail(MG_ERR_CUDA);
+  // load vector f_v = f_const h^d, initial guess
+  double hd = 1.0;
+  for (int a = 0; a < D; ++a) hd /= P->N;
+  if (!cuda_ok(launch_load_vector(D, P->N, d.f_const * hd, P->f, P->st), "load vector")) return fail(MG_ERR_CUDA);
+  if (d.u0) {
+    if (!cuda_ok(cudaMemcpyAsync(P->u, d.u0, v8, cudaMemcpyHostToDevice, P->st), "u0 upload") ||
+        !cuda_ok(cudaStreamSynchronize(P->st), "u0 sync"))
+      return fail(MG_ERR_CUDA);
+    // boundary values are forced to zero by the operator (Dirichlet rows are never written)
+  }
+  P->desc.u0 = nullptr;
+  {
+    // ||f||^2 (or later ||r_0||^2 when f = 0)
+    int nb = 0;
+    if (!cuda_ok(launch_dot(P->f, P->f, l0.nvert, P->partials, &nb, P->st), "dot") ||
+        !cuda_ok(launch_reduce_finish(P->partials, nb, 1, &P->sc->ff, P->st), "reduce"))
+      return fail(MG_ERR_CUDA);
+  }
+  // cell-centre eps and the geometric (s = 1) operator
+  if (!cuda_ok(launch_eps_centre(D, P->N, &P->eps, P->mixed ? 0 : 1, P->eps_c, P->st), "eps centre"))
+    return fail(MG_ERR_CUDA);
+  for (int c = 0; c < P->nchunk; ++c) {
+    ChunkStore cs;
+    mg_status s = assemble_chunk(P, 1, c, P->st, &cs, 0);
+    if (s != MG_OK) return fail(s);
+    install(P, c, cs);
+  }
+  mg_status s = upload_tables(P);
+  if (s == MG_OK) s = rebuild_coarse(P);
+  if (s != MG_OK) return fail(s);
+  if (!cuda_ok(read_scalars(P) == MG_OK ? cudaSuccess : cudaErrorUnknown, "create sync")) return fail(MG_ERR_CUDA);
+  P->ff = P->h_sc->ff;
+  P->need_restart = true;
+  *out = P;
+  return MG_OK;
+}
+
+mg_status mg_destroy_problem(mg_problem* P) {
+  if (!P) return MG_OK;
+  stop_worker(P);
+  if (P->st) cudaStreamSynchronize(P->st);
+  for (int g = 0; g < 2; ++g)
+    if (P->g_iter[g]) cudaGraphExecDestroy(P->g_iter[g]);
+  cudaStream_t st = P->st;
+  if (st) {
+    for (ChunkStore& c : P->cur) free_store(c, st);
+    for (void* a : P->allocs) cudaFreeAsync(a, st);
+    cudaStreamSynchronize(st);
+  }
+  if (P->h_sc) cudaFreeHost(P->h_sc);
+  if (P->h_totals) cudaFreeHost(P->h_totals);
+  if (P->side) cudaStreamDestroy(P->side);
+  if (P->own_stream && P->st) cudaStreamDestroy(P->st);
+  delete P;
+  return MG_OK;
+}
+
+mg_status mg_assemble_level(mg_problem* P, int s, int async) {
+  if (!P || s < 1 || s > 64) {
+    set_error("bad problem or accuracy");
+    return MG_ERR_INVALID;
+  }
+  if (async) {
+    start_worker(P);
+    return enqueue_async(P, s);
+  }
+  // synchronous: wait for in-flight jobs first (the scratch buffer is shared)
+  for (;;) {
+    int npub = 0;
+    {
+      std::lock_guard<std::mutex> lk(P->mu);
+      if (P->in_flight == 0) break;
+    }
+    mg_status st = publish_ready(P, true, &npub);
+    if (st != MG_OK) return st;
+  }
+  for (int c = 0; c < P->nchunk; ++c) {
+    ChunkStore cs;
+    mg_status st = assemble_chunk(P, s, c, P->st, &cs, 0);
+    if (st != MG_OK) return st;
+    install(P, c, cs);
+  }
+  mg_status st = upload_tables(P);
+  if (st == MG_OK) st = rebuild_coarse(P);
+  P->need_restart = true;
+  return st;
+}
+
+mg_status mg_vcycle(mg_problem* P, int n, double* rel_residual) {
+  if (!P || n < 0) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  for (int it = 0; it < n; ++it) {
+    int npub = 0;
+    mg_status s = publish_ready(P, false, &npub);
+    if (s != MG_OK) return s;
+    if (P->need_restart) {
+      s = outer_restart(P);
+      if (s != MG_OK) return s;
+    }
+    s = outer_iteration(P);
+    if (s != MG_OK) return s;
+  }
+  // true residual of the current iterate
+  Level& l0 = P->lev[0];
+  int nb = 0;
+  MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->p, 0.0, nullptr, nullptr, P->st));
+  MG_CHECK(launch_dot(P->p, P->p, l0.nvert, P->partials, &nb, P->st));
+  MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->r0, P->st));
+  mg_status s = read_scalars(P);
+  if (s != MG_OK) return s;
+  P->need_restart = true;  // p was used as scratch
+  const double ref = P->ff > 0 ? P->ff : 1.0;
+  if (rel_residual) *rel_residual = std::sqrt(P->h_sc->r0 / ref);
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
+  if (!P) {
+    set_error("null problem");
+    return MG_ERR_INVALID;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  double asm_ms = 0.0;
+  const mg_problem_desc& d = P->desc;
+  P->cycles = 0;
+  P->publishes = 0;
+  if (!P->delayed) {
+    auto ta = std::chrono::steady_clock::now();
+    if (min_s(P) < final_s(P)) {
+      mg_status s = mg_assemble_level(P, final_s(P), 0);
+      if (s != MG_OK) return s;
+    }
+    MG_CHECK(cudaStreamSynchronize(P->st));
+    asm_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
+  } else {
+    start_worker(P);
+    for (int i = 0; i < d.n_s; ++i)
+      if (d.s_schedule[i] > min_s(P)) {
+        mg_status s = enqueue_async(P, d.s_schedule[i]);
+        if (s != MG_OK) return s;
+      }
+  }
+  const double ref = P->ff > 0 ? P->ff : 1.0;
+  const double tol2 = d.rtol * d.rtol;
+  mg_status result = MG_ERR_NOT_CONVERGED;
+  bool have_first = false;
+  while (P->cycles < d.max_cycles) {
+    int npub = 0;
+    mg_status s = publish_ready(P, false, &npub);
+    if (s != MG_OK) {
+      result = s;
+      break;
+    }
+    if (P->need_restart) {
+      s = outer_restart(P);
+      if (s != MG_OK) return s;
+      s = read_scalars(P);
+      if (s != MG_OK) return s;
+      if (!have_first) {
+        P->rr_first = P->rr;
+        have_first = true;
+      }
+      if (P->ff <= 0) P->ff = P->rr > 0 ? P->rr : 1.0;
+    }
+    const double refn = P->ff > 0 ? P->ff : ref;
+    if (P->rr <= tol2 * refn) {
+      bool pending;
+      {
+        std::lock_guard<std::mutex> lk(P->mu);
+        pending = P->in_flight > 0;
+      }
+      if (all_final(P) && !pending) {
+        result = MG_OK;
+        break;
+      }
+      if (pending) {  // converged on stale stencils: wait for the next publication
+        s = publish_ready(P, true, &npub);
+        if (s != MG_OK) {
+          result = s;
+          break;
+        }
+        continue;
+      }
+      // not final and nothing pending: the schedule was cut short
+      result = MG_OK;
+      break;
+    }
+    s = outer_iteration(P);
+    if (s != MG_OK) return s;
+    s = read_scalars(P);
+    if (s != MG_OK) return s;
+    if (!(P->rr == P->rr) || (P->cycles > 5 && P->rr > 1e4 * std::max(P->rr_first, 1e-300))) {
+      result = MG_ERR_DIVERGED;
+      set_error("residual diverged");
+      break;
+    }
+  }
+  // verify with the true residual
+  double rel = 0.0;
+  {
+    Level& l0 = P->lev[0];
+    int nb = 0;
+    MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->p, 0.0, nullptr, nullptr, P->st));
+    MG_CHECK(launch_dot(P->p, P->p, l0.nvert, P->partials, &nb, P->st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->r0, P->st));
+    mg_status s = read_scalars(P);
+    if (s != MG_OK) return s;
+    rel = std::sqrt(P->h_sc->r0 / (P->ff > 0 ? P->ff : 1.0));
+    P->need_restart = true;
+  }
+  if (result == MG_OK && rel > 2.0 * d.rtol) result = MG_ERR_NOT_CONVERGED;
+  if (result == MG_ERR_NOT_CONVERGED) set_error("not converged: rel residual %.3e after %d cycles", rel, P->cycles);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = result;
+    info->cycles = P->cycles;
+    info->publishes = P->publishes;
+    info->final_s = min_s(P);
+    info->rel_residual = rel;
+    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->assembly_ms = asm_ms;
+    long long n0 = 0;
+    int64_t bytes = 0;
+    for (const ChunkStore& c : P->cur) {
+      for (int k = 0; k < 3; ++k) info->cells_by_class[k + 1] += c.totals[k];
+      n0 += P->chunk_cells - (c.totals[0] + c.totals[1] + c.totals[2]);
+      bytes += (int64_t)c.bytes;
+    }
+    info->cells_by_class[0] = P->mixed ? n0 : 0;
+    bytes += (int64_t)P->lev[0].ncell * (P->mixed ? 4 : 0);
+    info->payload_bytes = bytes;
+  }
+  return result;
+}
+
+mg_status mg_get_solution(const mg_problem* P, double* host_dst, size_t n) {
+  if (!P || !host_dst || n != (size_t)P->lev[0].nvert) {
+    set_error("bad arguments (n must be (N+1)^d)");
+    return MG_ERR_INVALID;
+  }
+  MG_CHECK(cudaMemcpyAsync(host_dst, P->u, sizeof(double) * n, cudaMemcpyDeviceToHost, P->st));
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
+mg_status mg_get_element_matrices(const mg_problem* Pc, int level, double* host_dst, size_t n) {
+  mg_problem* P = const_cast<mg_problem*>(Pc);
+  if (!P || !host_dst || level < 0 || level >= P->L) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  const Level& lv = P->lev[level];
+  const int nv = 1 << P->dim;
+  if (n != (size_t)lv.ncell * nv * nv) {
+    set_error("n must be cells * 4^d");
+    return MG_ERR_INVALID;
+  }
+  double* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * n, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "decode buffer");
+  MG_CHECK(launch_decode_matrices(lv.op, nullptr, 0, tmp, P->st));
+  MG_CHECK(cudaMemcpyAsync(host_dst, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, P->st));
+  cudaFreeAsync(tmp, P->st);
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
+mg_status mg_get_cell_matrices(const mg_problem* Pc, int level, const int64_t* cells, size_t ncells,
+                               double* host_dst) {
+  mg_problem* P = const_cast<mg_problem*>(Pc);
+  if (!P || !cells || !host_dst || level < 0 || level >= P->L) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  const Level& lv = P->lev[level];
+  for (size_t i = 0; i < ncells; ++i)
+    if (cells[i] < 0 || cells[i] >= lv.ncell) {
+      set_error("cell index %lld out of range", (long long)cells[i]);
+      return MG_ERR_INVALID;
+    }
+  if (ncells == 0) return MG_OK;
+  const int nv = 1 << P->dim;
+  long long* dc = nullptr;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&dc, sizeof(long long) * ncells, P->st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, sizeof(double) * ncells * nv * nv, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "gather buffers");
+  MG_CHECK(cudaMemcpyAsync(dc, cells, sizeof(long long) * ncells, cudaMemcpyHostToDevice, P->st));
+  MG_CHECK(launch_decode_matrices(lv.op, dc, (long long)ncells, tmp, P->st));
+  MG_CHECK(cudaMemcpyAsync(host_dst, tmp, sizeof(double) * ncells * nv * nv, cudaMemcpyDeviceToHost, P->st));
+  cudaFreeAsync(dc, P->st);
+  cudaFreeAsync(tmp, P->st);
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
+mg_status mg_get_cell_data(const mg_problem* Pc, uint8_t* cls, double* eps_c, size_t n) {
+  mg_problem* P = const_cast<mg_problem*>(Pc);
+  if (!P || n != (size_t)P->lev[0].ncell) {
+    set_error("bad arguments (n must be cells)");
+    return MG_ERR_INVALID;
+  }
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  if (cls) {
+    std::vector<uint8_t> pad((size_t)P->chunk_nseg * kSegCells);
+    for (int c = 0; c < P->nchunk; ++c) {
+      if (!P->mixed) {
+        memset(cls + (size_t)c * P->chunk_cells, 0, P->chunk_cells);
+        continue;
+      }
+      MG_CHECK(cudaMemcpy(pad.data(), P->cur[c].cls, pad.size(), cudaMemcpyDeviceToHost));
+      for (long long row = 0; row < P->chunk_rows; ++row)
+        for (int x = 0; x < P->N; ++x)
+          cls[(size_t)c * P->chunk_cells + row * P->N + x] =
+              pad[(size_t)(row * P->nseg_x + x / kSegCells) * kSegCells + (x % kSegCells)];
+    }
+  }
+  if (eps_c) {
+    if (P->mixed) {
+      std::vector<float> t(n);
+      MG_CHECK(cudaMemcpy(t.data(), P->eps_c, sizeof(float) * n, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) eps_c[i] = t[i];
+    } else {
+      MG_CHECK(cudaMemcpy(eps_c, P->eps_c, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    }
+  }
+  return MG_OK;
+}
+
+mg_status mg_apply_level(mg_problem* P, int level, int op, int inner, const double* x, const double* b, double* y) {
+  if (!P || level < 0 || level >= P->L || op < 0 || op > 2 || !x || !y || (op != 0 && !b)) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  Level& lv = P->lev[level];
+  const int vec64 = (inner && P->mixed) ? 0 : 1;
+  const size_t n = lv.nvert;
+  const size_t eb = vec64 ? 8 : 4;
+  void *dx = nullptr, *db = nullptr, *dy = nullptr;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&dx, eb * n, P->st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&db, eb * n, P->st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dy, eb * n, P->st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, 8 * n, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "buffers");
+  std::vector<double> zeros;
+  const double* bsrc = b;
+  if (!b) {
+    zeros.assign(n, 0.0);
+    bsrc = zeros.data();
+  }
+  MG_CHECK(cudaMemsetAsync(dy, 0, eb * n, P->st));
+  if (vec64) {
+    MG_CHECK(cudaMemcpyAsync(dx, x, 8 * n, cudaMemcpyHostToDevice, P->st));
+    MG_CHECK(cudaMemcpyAsync(db, bsrc, 8 * n, cudaMemcpyHostToDevice, P->st));
+  } else {
+    MG_CHECK(cudaMemcpyAsync(tmp, x, 8 * n, cudaMemcpyHostToDevice, P->st));
+    MG_CHECK(launch_convert(n, 0, tmp, dx, P->st));
+    MG_CHECK(cudaStreamSynchronize(P->st));
+    MG_CHECK(cudaMemcpyAsync(tmp, bsrc, 8 * n, cudaMemcpyHostToDevice, P->st));
+    MG_CHECK(launch_convert(n, 0, tmp, db, P->st));
+  }
+  const int mode = op == 0 ? SW_MATVEC : (op == 1 ? SW_JACOBI : SW_RESID);
+  int nb = 0;
+  MG_CHECK(launch_sweep(lv.op, mode, vec64, dx, db, dy, P->desc.omega, P->partials, &nb, P->st));
+  if (vec64) {
+    MG_CHECK(cudaMemcpyAsync(y, dy, 8 * n, cudaMemcpyDeviceToHost, P->st));
+  } else {
+    MG_CHECK(launch_convert(n, 1, dy, tmp, P->st));
+    MG_CHECK(cudaMemcpyAsync(y, tmp, 8 * n, cudaMemcpyDeviceToHost, P->st));
+  }
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  cudaFreeAsync(dx, P->st);
+  cudaFreeAsync(db, P->st);
+  cudaFreeAsync(dy, P->st);
+  cudaFreeAsync(tmp, P->st);
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
+mg_status mg_vcycle_apply(mg_problem* P, const double* b, double* e_out) {
+  if (!P || !b || !e_out) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  Level& l0 = P->lev[0];
+  const size_t n = l0.nvert;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&tmp, 8 * n, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "buffer");
+  // the V-cycle reads lev[0].b (aliases r on FP64 paths): stage b there
+  if (P->mixed) {
+    MG_CHECK(cudaMemcpyAsync(tmp, b, 8 * n, cudaMemcpyHostToDevice, P->st));
+    MG_CHECK(launch_convert(n, 0, tmp, l0.b, P->st));
+  } else {
+    MG_CHECK(cudaMemcpyAsync(l0.b, b, 8 * n, cudaMemcpyHostToDevice, P->st));
+  }
+  mg_status stt = MG_OK;
+  void* z = vcycle_enqueue(P, 0, &stt);
+  if (stt != MG_OK) return stt;
+  if (P->mixed) {
+    MG_CHECK(launch_convert(n, 1, z, tmp, P->st));
+    MG_CHECK(cudaMemcpyAsync(e_out, tmp, 8 * n, cudaMemcpyDeviceToHost, P->st));
+  } else {
+    MG_CHECK(cudaMemcpyAsync(e_out, z, 8 * n, cudaMemcpyDeviceToHost, P->st));
+  }
+  cudaFreeAsync(tmp, P->st);
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  P->need_restart = true;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,452 @@
+// Matrix-free operator application on one level: residual, damped Jacobi
+// sweep and FP64 matvec (Section "Numerical computation of stencils in a task
+// language": the element matrices of the 2^d cells around a vertex feed its
+// residual, then the point smoother S = omega diag^-1(A) of Section
+// "adaFAC-x" acts on it), the 3:1 d-linear transfers P and R = P^T, and the
+// vector kernels of the outer FP64 loop.
+//
+// Element matrices have zero row sums, so the row of vertex v (local index a
+// in cell c) contributes sum_{b != a} A_ab (u_b - u_a) and the diagonal is
+// -sum_{b != a} A_ab.  On the compressed finest level A = eps_c K_ref h^(d-2)
+// + decode(surplus), the geometric part from constants and the cell-centre
+// eps, the surplus only for cells of storage class > 0.
+#include "mg_internal.cuh"
+
+namespace mg {
+
+namespace {
+
+constexpr int kBX = 32, kBY = 8;
+
+template <int D>
+__device__ __forceinline__ void locate(const LevelOp& op, long long c, int clast, int* chunk, long long* lc) {
+  int ch = clast / op.layers;
+  if (ch >= op.nchunk) ch = op.nchunk - 1;
+  *chunk = ch;
+  *lc = c - (long long)ch * op.chunk_cells;
+}
+
+// (A u)_v and diag_v at interior vertex (i, j, k) from the 3^d neighbourhood u.
+template <int D, typename TA, bool CMP, typename TS>
+__device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, int k, const TA* u,
+                                             TA* Au, TA* dg) {
+  constexpr int NV = Dim<D>::NV;
+  const int N = op.N;
+  TA acc = 0, dgs = 0;
+#pragma unroll
+  for (int o = 0; o < NV; ++o) {
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = D == 3 ? (o >> 2) & 1 : 0;
+    const int cx = i - 1 + ox, cy = j - 1 + oy, cz = D == 3 ? k - 1 + oz : 0;
+    const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
+    const long long c = D == 2 ? (long long)cy * N + cx : ((long long)cz * N + cy) * N + cx;
+    int ch;
+    long long lc;
+    locate<D>(op, c, D == 2 ? cy : cz, &ch, &lc);
+    // neighbourhood index of local vertex b of this cell: offset (o - 1 + bits(b))
+    const int ua = (ox + ((a) & 1)) + 3 * (oy + ((a >> 1) & 1)) + (D == 3 ? 9 * (oz + ((a >> 2) & 1)) : 0);
+    const TA u_a = u[ua];
+    if (CMP) {
+      const TA ge = (TA)__ldg(op.eps_c + c) * (TA)op.hfac;
+#pragma unroll
+      for (int b = 0; b < NV; ++b) {
+        if (b == a) continue;
+        const double kv = kref_off<D>(popc_small(a ^ b));
+        if (kv == 0.0) continue;
+        const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+        acc += ge * (TA)kv * (u[ub] - u_a);
+      }
+      dgs += ge * (TA)kref_diag<D>();
+      const CmpChunk& ck = op.cmp[ch];
+      const int cls = cell_class(ck, N, op.nseg_x, lc);
+      if (cls) {
+        const uint8_t* rec = cell_record<D>(ck, N, op.nseg_x, lc, cls);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+          if (b == a) continue;
+          const TA dv = (TA)decode_entry<D>(rec, cls, pair_of(NV, a, b));
+          const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+          acc += dv * (u[ub] - u_a);
+          dgs -= dv;
+        }
+      }
+    } else {
+      const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
+      const long long cc = op.chunk_cells;
+#pragma unroll
+      for (int b = 0; b < NV; ++b) {
+        if (b == a) continue;
+        const TA av = (TA)__ldg(A + (long long)pair_of(NV, a, b) * cc + lc);
+        const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+        acc += av * (u[ub] - u_a);
+        dgs -= av;
+      }
+    }
+  }
+  *Au = acc;
+  *dg = dgs;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+  __syncthreads();
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  T r = 0;
+  if (tid == 0)
+    for (int w = 0; w < nw; ++w) r += sh[w];
+  return r;
+}
+
+// One sweep over the interior vertices of one level.
+//  SW_JACOBI: y = x + omega (b - A x) / diag
+//  SW_RESID : y = b - A x
+//  SW_MATVEC: y = A x; partials += (x.y, x.b) per block
+template <int D, typename TV, typename TA, typename TS, int MODE, bool CMP>
+__global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, const TV* __restrict__ x,
+                                                          const TV* __restrict__ b, TV* __restrict__ y,
+                                                          TA omega, double* __restrict__ partials) {
+  __shared__ double sh[2][kBX * kBY / 32];
+  const int N = op.N, n1 = N + 1;
+  const int i = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int j = 1 + blockIdx.y * kBY + threadIdx.y;
+  const int k = D == 3 ? 1 + blockIdx.z : 0;
+  const bool valid = i < N && j < N;
+  double d1 = 0.0, d2 = 0.0;
+  if (valid) {
+    TA u[D == 3 ? 27 : 9];
+    const long long v = D == 2 ? (long long)j * n1 + i : ((long long)k * n1 + j) * n1 + i;
+#pragma unroll
+    for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const long long w = v + (dx - 1) + (long long)(dy - 1) * n1 + (D == 3 ? (long long)(dz - 1) * n1 * n1 : 0);
+          u[dx + 3 * dy + 9 * dz] = (TA)__ldg(x + w);
+        }
+    TA Au, dg;
+    vertex_apply<D, TA, CMP, TS>(op, i, j, k, u, &Au, &dg);
+    const TA uv = u[D == 3 ? 13 : 4];
+    if (MODE == SW_JACOBI) {
+      y[v] = (TV)(uv + omega * ((TA)b[v] - Au) / dg);
+    } else if (MODE == SW_RESID) {
+      y[v] = (TV)((TA)b[v] - Au);
+    } else {
+      y[v] = (TV)Au;
+      d1 = (double)uv * (double)Au;
+      d2 = (double)uv * (double)b[v];
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      partials[2 * blk] = s1;
+      partials[2 * blk + 1] = s2;
+    }
+  }
+}
+
+template <int D, typename TV, typename TA, typename TS, bool CMP>
+cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const void* b, void* y, double omega,
+                           double* partials, int* nblocks, cudaStream_t st) {
+  const int ni = op.N - 1;
+  dim3 blk(kBX, kBY, 1);
+  dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
+  if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+  const TV* xv = (const TV*)x;
+  const TV* bv = (const TV*)b;
+  TV* yv = (TV*)y;
+  if (mode == SW_JACOBI)
+    sweep_kernel<D, TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+  else if (mode == SW_RESID)
+    sweep_kernel<D, TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+  else
+    sweep_kernel<D, TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- transfers
+// b_c(I) = sum_{|delta| <= 2} prod_a (1 - |delta_a| / 3) r_f(3 I + delta)   (R = P^T)
+template <int D, typename TV>
+__global__ void restrict_kernel(int Nc, const TV* __restrict__ rf, TV* __restrict__ bc) {
+  const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
+  long long ni = 1;
+  for (int a = 0; a < D; ++a) ni *= (Nc - 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ni;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = 1 + (int)(t % (Nc - 1));
+    const int J = 1 + (int)((t / (Nc - 1)) % (Nc - 1));
+    const int K = D == 3 ? 1 + (int)(t / ((long long)(Nc - 1) * (Nc - 1))) : 0;
+    double acc = 0.0;
+    const double w1[5] = {1.0 / 3.0, 2.0 / 3.0, 1.0, 2.0 / 3.0, 1.0 / 3.0};
+    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz)
+      for (int dy = -2; dy <= 2; ++dy) {
+        const long long rowbase = D == 3 ? ((long long)(3 * K + dz) * nf1 + (3 * J + dy)) * nf1
+                                         : (long long)(3 * J + dy) * nf1;
+        const double wyz = w1[dy + 2] * (D == 3 ? w1[dz + 2] : 1.0);
+        double racc = 0.0;
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) racc += w1[dx + 2] * (double)rf[rowbase + 3 * I + dx];
+        acc += wyz * racc;
+      }
+    const long long vc = D == 3 ? ((long long)K * nc1 + J) * nc1 + I : (long long)J * nc1 + I;
+    bc[vc] = (TV)acc;
+  }
+}
+
+// e_f += P e_c (d-linear interpolation on the 3:1 refined grid)
+template <int D, typename TV>
+__global__ void prolong_kernel(int Nc, const TV* __restrict__ ec, TV* __restrict__ ef) {
+  const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
+  long long ni = 1;
+  for (int a = 0; a < D; ++a) ni *= (Nf - 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ni;
+       t += (long long)gridDim.x * blockDim.x) {
+    int f[3];
+    f[0] = 1 + (int)(t % (Nf - 1));
+    f[1] = 1 + (int)((t / (Nf - 1)) % (Nf - 1));
+    f[2] = D == 3 ? 1 + (int)(t / ((long long)(Nf - 1) * (Nf - 1))) : 0;
+    int c0[3], rr[3];
+    for (int a = 0; a < D; ++a) {
+      c0[a] = f[a] / 3;
+      rr[a] = f[a] - 3 * c0[a];
+    }
+    double acc = 0.0;
+    for (int corner = 0; corner < (1 << D); ++corner) {
+      double w = 1.0;
+      int cv[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        const int up = (corner >> a) & 1;
+        const double tt = rr[a] / 3.0;
+        w *= up ? tt : 1.0 - tt;
+        cv[a] = c0[a] + up;
+      }
+      if (w != 0.0) {
+        const long long vc = D == 3 ? ((long long)cv[2] * nc1 + cv[1]) * nc1 + cv[0] : (long long)cv[1] * nc1 + cv[0];
+        acc += w * (double)ec[vc];
+      }
+    }
+    const long long vf = D == 3 ? ((long long)f[2] * nf1 + f[1]) * nf1 + f[0] : (long long)f[1] * nf1 + f[0];
+    ef[vf] = (TV)((double)ef[vf] + acc);
+  }
+}
+
+int vgrid(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------- vector kernels
+constexpr int kRedBlocks = 152 * 4;
+
+template <typename TA, typename TB>
+__global__ void dot_kernel(const TA* __restrict__ a, const TB* __restrict__ b, long long n, double* partials) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    acc += (double)a[t] * (double)b[t];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void reduce_finish_kernel(const double* __restrict__ partials, int nblocks, int ncomp, double* out) {
+  __shared__ double sh[32];
+  for (int c = 0; c < ncomp; ++c) {
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < nblocks; t += blockDim.x) acc += partials[(long long)t * ncomp + c];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[c] = s;
+    __syncthreads();
+  }
+}
+
+__global__ void scalar_kernel(DevScalars* sc, int op) {
+  if (op == SC_SET_BETA) sc->beta = sc->pq != 0.0 ? -sc->zq / sc->pq : 0.0;
+  else sc->alpha = sc->pq != 0.0 ? sc->pr / sc->pq : 0.0;
+}
+
+template <typename TZ>
+__global__ void fcg_direction_kernel(long long n, int first, const TZ* __restrict__ z, double* __restrict__ p,
+                                     const DevScalars* __restrict__ sc) {
+  const double beta = first ? 0.0 : sc->beta;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    p[t] = (double)z[t] + (first ? 0.0 : beta * p[t]);
+}
+
+template <typename TR>
+__global__ void fcg_update_kernel(long long n, double* __restrict__ u, double* __restrict__ r,
+                                  const double* __restrict__ p, const double* __restrict__ q,
+                                  const DevScalars* __restrict__ sc, TR* __restrict__ rin, double* partials) {
+  __shared__ double sh[8];
+  const double alpha = sc->alpha;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    u[t] += alpha * p[t];
+    const double rv = r[t] - alpha * q[t];
+    r[t] = rv;
+    if (rin) rin[t] = (TR)rv;
+    acc += rv * rv;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename TZ>
+__global__ void richardson_kernel(long long n, double* __restrict__ u, const TZ* __restrict__ z) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    u[t] += (double)z[t];
+}
+
+template <typename TS, typename TD>
+__global__ void convert_kernel(long long n, const TS* __restrict__ s, TD* __restrict__ d) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    d[t] = (TD)s[t];
+}
+
+template <int D>
+__global__ void load_vector_kernel(int N, double val, double* f) {
+  const int n1 = N + 1;
+  long long nv = 1;
+  for (int a = 0; a < D; ++a) nv *= n1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nv; t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    bool inside = true;
+    for (int a = 0; a < D; ++a) {
+      const int c = (int)(r % n1);
+      r /= n1;
+      inside = inside && c > 0 && c < N;
+    }
+    f[t] = inside ? val : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, const void* b, void* y,
+                         double omega, double* partials, int* nblocks, cudaStream_t st) {
+  if (op.N < 2) return cudaErrorInvalidValue;
+  // arithmetic: FP64 when the vectors are FP64, FP32 otherwise
+#define MG_SW(D, TV, TA, TS, CMP) \
+  return sweep_dispatch<D, TV, TA, TS, CMP>(op, mode, x, b, y, omega, partials, nblocks, st)
+  if (op.dim == 2) {
+    if (op.compressed) {
+      if (vec64) MG_SW(2, double, double, float, true);
+      MG_SW(2, float, float, float, true);
+    }
+    if (vec64) {
+      if (op.elem64) MG_SW(2, double, double, double, false);
+      MG_SW(2, double, double, float, false);
+    }
+    if (op.elem64) MG_SW(2, float, float, double, false);
+    MG_SW(2, float, float, float, false);
+  }
+  if (op.compressed) {
+    if (vec64) MG_SW(3, double, double, float, true);
+    MG_SW(3, float, float, float, true);
+  }
+  if (vec64) {
+    if (op.elem64) MG_SW(3, double, double, double, false);
+    MG_SW(3, double, double, float, false);
+  }
+  if (op.elem64) MG_SW(3, float, float, double, false);
+  MG_SW(3, float, float, float, false);
+#undef MG_SW
+}
+
+cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st) {
+  long long ni = 1;
+  for (int a = 0; a < dim; ++a) ni *= (Nc - 1);
+  const int g = vgrid(ni);
+  if (dim == 2) {
+    if (vec64) restrict_kernel<2, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
+    else restrict_kernel<2, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+  } else {
+    if (vec64) restrict_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
+    else restrict_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st) {
+  long long ni = 1;
+  for (int a = 0; a < dim; ++a) ni *= (3 * Nc - 1);
+  const int g = vgrid(ni);
+  if (dim == 2) {
+    if (vec64) prolong_kernel<2, double><<<g, 256, 0, st>>>(Nc, (const double*)ec, (double*)ef);
+    else prolong_kernel<2, float><<<g, 256, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+  } else {
+    if (vec64) prolong_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)ec, (double*)ef);
+    else prolong_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
+
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks, cudaStream_t st) {
+  *nblocks = kRedBlocks;
+  dot_kernel<double, double><<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double* partials, int* nblocks,
+                           cudaStream_t st) {
+  *nblocks = kRedBlocks;
+  dot_kernel<float, double><<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st) {
+  reduce_finish_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncomp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_op(DevScalars* sc, int op, cudaStream_t st) {
+  scalar_kernel<<<1, 1, 0, st>>>(sc, op);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcg_direction(long long n, int first, int z64, const void* z, double* p, const DevScalars* sc,
+                                 cudaStream_t st) {
+  if (z64) fcg_direction_kernel<double><<<vgrid(n), 256, 0, st>>>(n, first, (const double*)z, p, sc);
+  else fcg_direction_kernel<float><<<vgrid(n), 256, 0, st>>>(n, first, (const float*)z, p, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p, const double* q,
+                              const DevScalars* sc, int r32_out, void* rin, double* partials, int* nblocks,
+                              cudaStream_t st) {
+  *nblocks = kRedBlocks;
+  if (r32_out) fcg_update_kernel<float><<<kRedBlocks, 256, 0, st>>>(n, u, r, p, q, sc, (float*)rin, partials);
+  else fcg_update_kernel<double><<<kRedBlocks, 256, 0, st>>>(n, u, r, p, q, sc, (double*)rin, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_richardson_update(long long n, double* u, int z64, const void* z, cudaStream_t st) {
+  if (z64) richardson_kernel<double><<<vgrid(n), 256, 0, st>>>(n, u, (const double*)z);
+  else richardson_kernel<float><<<vgrid(n), 256, 0, st>>>(n, u, (const float*)z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(long long n, int to64, const void* src, void* dst, cudaStream_t st) {
+  if (to64) convert_kernel<float, double><<<vgrid(n), 256, 0, st>>>(n, (const float*)src, (double*)dst);
+  else convert_kernel<double, float><<<vgrid(n), 256, 0, st>>>(n, (const double*)src, (float*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_vector(int dim, int N, double val, double* f, cudaStream_t st) {
+  long long nv = 1;
+  for (int a = 0; a < dim; ++a) nv *= (N + 1);
+  if (dim == 2) load_vector_kernel<2><<<vgrid(nv), 256, 0, st>>>(N, val, f);
+  else load_vector_kernel<3><<<vgrid(nv), 256, 0, st>>>(N, val, f);
+  return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libmg.so (C ABI in include/mg.h).
+
+Argument marshalling only: every step of assembly, compression and solving
+runs in the CUDA library.  Loading fails loudly if the library is missing;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmg.so")
+
+MG_OK, MG_ERR_INVALID, MG_ERR_OOM, MG_ERR_CUDA, MG_ERR_TIMEOUT = 0, 1, 2, 3, 4
+MG_ERR_DIVERGED, MG_ERR_NOT_CONVERGED, MG_ERR_PENDING, MG_ERR_CANCELLED, MG_ERR_INJECTED = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "DIVERGED",
+                6: "NOT_CONVERGED", 7: "PENDING", 8: "CANCELLED", 9: "INJECTED"}
+
+PATH_FP64_PLAIN, PATH_FP64_DELAYED, PATH_MIXED_DELAYED, PATH_MIXED_PLAIN = 0, 1, 2, 3
+OUTER_FCG, OUTER_RICHARDSON = 0, 1
+MAX_MODES, MAX_BOXES = 32, 64
+
+
+class mg_eps_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_modes", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
+                ("pad0", ctypes.c_int32), ("v_out", ctypes.c_double), ("v_in", ctypes.c_double),
+                ("center", ctypes.c_double * 3), ("radius", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("theta", ctypes.c_double), ("jump_x", ctypes.c_double), ("jump_factor", ctypes.c_double),
+                ("k", (ctypes.c_int32 * 3) * MAX_MODES), ("phase", ctypes.c_double * MAX_MODES),
+                ("box_lo", (ctypes.c_double * 3) * MAX_BOXES), ("box_hi", (ctypes.c_double * 3) * MAX_BOXES)]
+
+
+class mg_problem_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_cells", ctypes.c_int32), ("eps", mg_eps_desc),
+                ("f_const", ctypes.c_double), ("path", ctypes.c_int32), ("outer", ctypes.c_int32),
+                ("s_schedule", ctypes.c_int32 * 8), ("n_s", ctypes.c_int32), ("compress_tau", ctypes.c_double),
+                ("omega", ctypes.c_double), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
+                ("rtol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("chunks", ctypes.c_int32),
+                ("u0", ctypes.POINTER(ctypes.c_double))]
+
+
+class mg_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("publishes", ctypes.c_int32),
+                ("final_s", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("assembly_ms", ctypes.c_double), ("cells_by_class", ctypes.c_int64 * 4),
+                ("payload_bytes", ctypes.c_int64)]
+
+
+class mg_server_desc(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_double), ("inject_fail_every", ctypes.c_int32),
+                ("pad0", ctypes.c_int32)]
+
+
+class mg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cycles", ctypes.c_int32), ("publishes", ctypes.c_int32),
+                ("pad0", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmg.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        st = ctypes.c_int
+        sig = {
+            "mg_create_problem": (st, [ctypes.POINTER(mg_problem_desc), _VP, ctypes.POINTER(_VP)]),
+            "mg_destroy_problem": (st, [_VP]),
+            "mg_assemble_level": (st, [_VP, ctypes.c_int, ctypes.c_int]),
+            "mg_vcycle": (st, [_VP, ctypes.c_int, _D]),
+            "mg_solve": (st, [_VP, ctypes.POINTER(mg_solve_info)]),
+            "mg_get_solution": (st, [_VP, _D, ctypes.c_size_t]),
+            "mg_get_element_matrices": (st, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
+            "mg_get_cell_data": (st, [_VP, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t]),
+            "mg_get_cell_matrices": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t, _D]),
+            "mg_apply_level": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
+            "mg_vcycle_apply": (st, [_VP, _D, _D]),
+            "mg_server_create": (st, [ctypes.POINTER(mg_server_desc), ctypes.POINTER(_VP)]),
+            "mg_submit": (st, [_VP, ctypes.POINTER(mg_problem_desc), _D, ctypes.POINTER(ctypes.c_uint64)]),
+            "mg_poll": (st, [_VP, ctypes.c_uint64, ctypes.POINTER(mg_result)]),
+            "mg_server_drain": (st, [_VP, ctypes.c_double]),
+            "mg_server_destroy": (st, [_VP]),
+            "mg_last_error": (ctypes.c_char_p, []),
+            "mg_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int) -> int:
+    if status != MG_OK:
+        raise MGError(status, load().mg_last_error().decode())
+    return status
+
+
+def last_error() -> str:
+    return load().mg_last_error().decode()
+
+
+def eps_desc(field: "_inputs.EpsField") -> mg_eps_desc:
+    e = mg_eps_desc()
+    e.kind = int(field.kind)
+    e.n_modes = int(field.n_modes)
+    e.n_boxes = int(field.n_boxes)
+    e.v_out, e.v_in = float(field.v_out), float(field.v_in)
+    for a in range(3):
+        e.center[a] = float(field.center[a]) if a < len(field.center) else 0.0
+    e.radius, e.sigma, e.theta = float(field.radius), float(field.sigma), float(field.theta)
+    e.jump_x, e.jump_factor = float(field.jump_x), float(field.jump_factor)
+    for m in range(field.n_modes):
+        for a in range(3):
+            e.k[m][a] = int(field.k[m, a])
+        e.phase[m] = float(field.phase[m])
+    for b in range(field.n_boxes):
+        for a in range(3):
+            e.box_lo[b][a] = float(field.box_lo[b, a])
+            e.box_hi[b][a] = float(field.box_hi[b, a])
+    return e
+
+
+def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_schedule=(8,),
+                 f_const: float = 1.0, outer: int = OUTER_FCG, tau: float = 1e-6, omega: float = 0.6,
+                 nu_pre: int = 2, nu_post: int = 2, rtol: float = 1e-8, max_cycles: int = 500,
+                 chunks: int = 0, u0: Optional[np.ndarray] = None) -> mg_problem_desc:
+    d = mg_problem_desc()
+    d.dim, d.n_cells = dim, n_cells
+    d.eps = eps_desc(field)
+    d.f_const = f_const
+    d.path, d.outer = path, outer
+    for i, s in enumerate(s_schedule):
+        d.s_schedule[i] = int(s)
+    d.n_s = len(s_schedule)
+    d.compress_tau, d.omega = tau, omega
+    d.nu_pre, d.nu_post = nu_pre, nu_post
+    d.rtol, d.max_cycles, d.chunks = rtol, max_cycles, chunks
+    if u0 is not None:
+        u0 = np.ascontiguousarray(u0, np.float64)
+        d.u0 = u0.ctypes.data_as(_D)
+        d._u0_keep = u0
+    return d
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+class Problem:
+    """One solve: owns an mg_problem handle."""
+
+    def __init__(self, desc: mg_problem_desc, stream: Optional[int] = None):
+        self.desc = desc
+        self.dim, self.n = desc.dim, desc.n_cells
+        h = _VP()
+        _check(load().mg_create_problem(ctypes.byref(desc), stream, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().mg_destroy_problem(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def nvert(self) -> int:
+        return (self.n + 1) ** self.dim
+
+    def level_cells(self, level: int) -> int:
+        return (self.n // 3 ** level) ** self.dim
+
+    def assemble(self, s: int, async_: bool = False):
+        _check(load().mg_assemble_level(self.h, int(s), 1 if async_ else 0))
+
+    def vcycle(self, n: int) -> float:
+        rel = ctypes.c_double()
+        _check(load().mg_vcycle(self.h, int(n), ctypes.byref(rel)))
+        return rel.value
+
+    def solve(self, check: bool = True) -> mg_solve_info:
+        info = mg_solve_info()
+        st = load().mg_solve(self.h, ctypes.byref(info))
+        if check:
+            _check(st)
+        return info
+
+    def solution(self) -> np.ndarray:
+        u = np.zeros(self.nvert)
+        _check(load().mg_get_solution(self.h, _p(u), u.size))
+        return u
+
+    def element_matrices(self, level: int = 0) -> np.ndarray:
+        nv = 1 << self.dim
+        A = np.zeros((self.level_cells(level), nv, nv))
+        _check(load().mg_get_element_matrices(self.h, level, _p(A), A.size))
+        return A
+
+    def cell_matrices(self, cells, level: int = 0) -> np.ndarray:
+        nv = 1 << self.dim
+        cells = np.ascontiguousarray(np.asarray(cells, np.int64))
+        A = np.zeros((cells.shape[0], nv, nv))
+        _check(load().mg_get_cell_matrices(self.h, level, cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           cells.shape[0], _p(A)))
+        return A
+
+    def cell_data(self):
+        n = self.level_cells(0)
+        cls = np.zeros(n, np.uint8)
+        ec = np.zeros(n)
+        _check(load().mg_get_cell_data(self.h, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _p(ec), n))
+        return cls, ec
+
+    def apply(self, level: int, op: int, x: np.ndarray, b: Optional[np.ndarray] = None, inner: bool = False):
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.zeros_like(x)
+        bp = _p(np.ascontiguousarray(b, np.float64)) if b is not None else None
+        _check(load().mg_apply_level(self.h, level, op, 1 if inner else 0, _p(x), bp, _p(y)))
+        return y
+
+    def vcycle_apply(self, b: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(b, np.float64)
+        e = np.zeros_like(b)
+        _check(load().mg_vcycle_apply(self.h, _p(b), _p(e)))
+        return e
+
+
+class Server:
+    def __init__(self, max_active: int = 8, budget_bytes: float = 0.0, inject_fail_every: int = 0,
+                 use_graphs: bool = True):
+        d = mg_server_desc()
+        d.max_active, d.hbm_budget_bytes = max_active, budget_bytes
+        d.inject_fail_every, d.use_graphs = inject_fail_every, 1 if use_graphs else 0
+        h = _VP()
+        _check(load().mg_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, desc: mg_problem_desc, want_solution: bool = False) -> int:
+        t = ctypes.c_uint64()
+        dst = None
+        if want_solution:
+            dst = np.zeros((desc.n_cells + 1) ** desc.dim)
+        _check(load().mg_submit(self.h, ctypes.byref(desc), _p(dst) if dst is not None else None, ctypes.byref(t)))
+        self._keep[t.value] = (desc, dst)
+        return t.value
+
+    def poll(self, ticket: int):
+        r = mg_result()
+        st = load().mg_poll(self.h, ticket, ctypes.byref(r))
+        return st, r
+
+    def solution(self, ticket: int) -> Optional[np.ndarray]:
+        return self._keep[ticket][1]
+
+    def drain(self, timeout_ms: float = 0.0) -> int:
+        return load().mg_server_drain(self.h, float(timeout_ms))
+
+    def close(self):
+        if self.h:
+            load().mg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load, export every function declared in include/*.h, agree
+with the binding on struct layouts, and reject bad input before touching the
+device.  Serving admission and host-injected failures run here too.
+"""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+import time
+
+import numpy as np
+import pytest
+
+from paper_2005_03606_gb300 import build as mgbuild
+from paper_2005_03606_gb300 import inputs, mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mgbuild.build()
+    return mg.load()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:mg_status|const char\*)\s+(mg_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", mg.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mg_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "mg.h"\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
+                   "sizeof(mg_eps_desc), sizeof(mg_problem_desc), sizeof(mg_solve_info), sizeof(mg_server_desc),"
+                   "sizeof(mg_result), offsetof(mg_problem_desc, u0), offsetof(mg_eps_desc, box_hi));return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(mg.mg_eps_desc), ctypes.sizeof(mg.mg_problem_desc), ctypes.sizeof(mg.mg_solve_info),
+            ctypes.sizeof(mg.mg_server_desc), ctypes.sizeof(mg.mg_result), mg.mg_problem_desc.u0.offset,
+            mg.mg_eps_desc.box_hi.offset]
+    assert got == want
+
+
+def test_version(lib):
+    assert lib.mg_version().decode().startswith("mg-gb300")
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dim=4), "dim"), (dict(n_cells=10), "power of 3"), (dict(n_cells=3), "L >= 2"),
+    (dict(s_schedule=(4, 2)), "s_schedule"), (dict(s_schedule=(128,)), "s_schedule"),
+])
+def test_invalid_descriptors_rejected_on_host(lib, kw, msg):
+    dim = kw.pop("dim", 2)
+    n = kw.pop("n_cells", 9)
+    d = mg.problem_desc(dim, n, inputs.disc_field(2), **kw)
+    with pytest.raises(mg.MGError) as ei:
+        mg.Problem(d)
+    assert ei.value.status == mg.MG_ERR_INVALID
+    assert msg in str(ei.value)
+
+
+def test_invalid_field_rejected(lib):
+    fld = inputs.fourier_field(3, 1)
+    fld.k[0, 0] = 100
+    with pytest.raises(mg.MGError) as ei:
+        mg.Problem(mg.problem_desc(3, 9, fld))
+    assert ei.value.status == mg.MG_ERR_INVALID
+    neg = inputs.const_field(2, -1.0)
+    with pytest.raises(mg.MGError):
+        mg.Problem(mg.problem_desc(2, 9, neg))
+
+
+def test_server_admission_and_injected_failures(lib):
+    # budget too small for the request: rejected at submit, nothing reaches the device
+    s = mg.Server(max_active=2, budget_bytes=1e6)
+    with pytest.raises(mg.MGError) as ei:
+        s.submit(mg.problem_desc(3, 81, inputs.disc_field(3)))
+    assert ei.value.status == mg.MG_ERR_OOM
+    s.close()
+    # every admission fails on the host: each request ends with MG_ERR_INJECTED
+    s = mg.Server(max_active=3, budget_bytes=64e9, inject_fail_every=1)
+    tickets = [s.submit(mg.problem_desc(2, 27, inputs.disc_field(2))) for _ in range(7)]
+    assert s.drain(20000) == mg.MG_OK
+    for t in tickets:
+        st, r = s.poll(t)
+        assert st == mg.MG_ERR_INJECTED and r.status == mg.MG_ERR_INJECTED
+        assert r.total_ms >= r.queue_ms >= 0
+    st, _ = s.poll(12345)
+    assert st == mg.MG_ERR_INVALID
+    s.close()
+
+
+def test_server_fifo_admission_respects_budget(lib):
+    # one slot's worth of budget: requests are admitted one at a time, in order
+    s = mg.Server(max_active=4, budget_bytes=2.0e9, inject_fail_every=1)
+    d = mg.problem_desc(3, 81, inputs.disc_field(3))
+    ts = [s.submit(d) for _ in range(5)]
+    assert s.drain(20000) == mg.MG_OK
+    res = [s.poll(t)[1] for t in ts]
+    assert all(r.status == mg.MG_ERR_INJECTED for r in res)
+    s.close()
+
+
+def test_inputs_are_seeded_and_deterministic():
+    a = inputs.fourier_field(3, 2002)
+    b = inputs.fourier_field(3, 2002)
+    c = inputs.fourier_field(3, 2003)
+    assert np.array_equal(a.k, b.k) and np.array_equal(a.phase, b.phase)
+    assert not np.array_equal(a.phase, c.phase)
+    assert a.n_modes == 16 and np.abs(a.k).max() <= 8 and (np.abs(a.k).max(axis=1) >= 1).all()
+    bx = inputs.boxes_field(3, 2003)
+    assert bx.n_boxes == 64
+    w = bx.box_hi - bx.box_lo
+    assert (w >= 0.02).all() and (w <= 0.15).all() and (bx.box_hi <= 1.0).all()
+    r1 = inputs.serving_requests(20, seed=2004)
+    r2 = inputs.serving_requests(20, seed=2004)
+    assert [x["n_cells"] for x in r1] == [x["n_cells"] for x in r2]
+    assert all(0.5 <= x["sigma"] <= 2.0 for x in r1)
+    # known first splitmix64 output for seed 0 (published reference value)
+    assert inputs.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF

@@ -1,0 +1,346 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances:
+  * FP64 assembly: per cell max|A_gpu - A_oracle| <= 1e-12 max|A_oracle|.
+  * FP32 (mixed) assembly incl. lossy storage: <= 1e-5 max|A_oracle| per cell
+    (compression bound tau = 1e-6 plus FP32 integration error).
+  * Operators, transfers, V-cycle in FP64: 1e-11 relative; in FP32: 1e-5.
+  * Solutions: both sides converge to rtol; the difference is bounded by the
+    conditioning times the residual gap and checked at the stated factors.
+Storage classes are integers decided in FP32 on the GPU and FP64 in the
+oracle: they must agree except for cells whose oracle size ratio lies within
+1% of a class threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_2005_03606_gb300 import inputs, mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2005_03606_gb300 import build
+    build.build()
+    return mg.load()
+
+
+def cellwise_err(A, B):
+    den = np.abs(B).max(axis=(1, 2))
+    return (np.abs(A - B).max(axis=(1, 2)) / den).max()
+
+
+ASM_CASES = [
+    (2, 27, inputs.disc_field(2), 8),
+    (2, 81, inputs.theta_field(2, 16.0), 5),
+    (2, 729, inputs.fourier_field(2, 12, sigma=1.0), 2),
+    (3, 9, inputs.fourier_field(3, 13, sigma=1.0), 4),
+    (3, 27, inputs.boxes_field(3, 14), 4),
+    (3, 9, inputs.disc_field(3), 3),
+    (3, 27, inputs.fourier_field(3, 15, sigma=2.0, jump_x=0.37, jump_factor=1e4), 6),
+    (3, 9, inputs.const_field(3, 2.5), 16),
+    (3, 81, inputs.theta_field(3, 4.0), 2),
+]
+
+
+@pytest.mark.parametrize("dim,n,fld,s", ASM_CASES)
+def test_fp64_assembly_matches_oracle(dim, n, fld, s):
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=mg.PATH_FP64_PLAIN, s_schedule=(s,))) as P:
+        P.assemble(s)
+        if n ** dim <= 30000:
+            A = P.element_matrices(0)
+            ref = oracle.assemble(oracle.Field(fld), n, s)
+        else:
+            cells = np.random.default_rng(0).choice(n ** dim, 3000, replace=False)
+            cells = np.concatenate([cells, [0, n ** dim - 1, n - 1]])
+            A = P.cell_matrices(cells)
+            ref = oracle.assemble_cells(oracle.Field(fld), n, s, cells)
+    assert cellwise_err(A, ref) <= 1e-12
+
+
+def test_fp64_geometric_stencil_is_cell_centre_sample():
+    fld = inputs.fourier_field(3, 16)
+    with mg.Problem(mg.problem_desc(3, 27, fld, path=mg.PATH_FP64_DELAYED, s_schedule=(1, 2))) as P:
+        A = P.element_matrices(0)
+    ref = oracle.assemble(oracle.Field(fld), 27, 1)
+    assert cellwise_err(A, ref) <= 1e-12
+
+
+def _class_ratio_near_threshold(A_ref, eps_c32, K, tau, dim):
+    """True where the oracle's class decision lies within 1% of a threshold."""
+    nv = 1 << dim
+    iu = np.triu_indices(nv, 1)
+    D = A_ref - eps_c32[:, None, None] * K[None]
+    Dm = np.abs(D[:, iu[0], iu[1]]).max(axis=1)
+    An = np.abs(A_ref).max(axis=(1, 2))
+    F = nv - 1
+    x = F * Dm / np.maximum(tau * An, 1e-300)
+    # FP32 evaluation of eps and of the surplus sums carries an absolute noise of
+    # about 2e-7 max|A| per entry; decisions within that band (plus 1%) may differ
+    band = F * 2e-7 / tau
+    near = np.zeros(len(x), bool)
+    for thr in (1.0, 448.0 / 16.0, 65504.0 / 16.0):
+        near |= np.abs(x - thr) < 0.01 * thr + band
+    return near
+
+
+MIXED_CASES = [
+    (3, 27, inputs.boxes_field(3, 21), 4),
+    (3, 27, inputs.fourier_field(3, 22, sigma=1.0), 4),
+    (3, 27, inputs.fourier_field(3, 23, sigma=2e-5), 4),
+    (3, 9, inputs.fourier_field(3, 24, sigma=2.0, jump_x=0.37, jump_factor=1e4), 8),
+    (2, 81, inputs.disc_field(2), 8),
+    (2, 243, inputs.fourier_field(2, 25, sigma=1e-4), 3),
+]
+
+
+@pytest.mark.parametrize("dim,n,fld,s", MIXED_CASES)
+def test_mixed_assembly_and_storage_match_oracle(dim, n, fld, s):
+    tau = 1e-6
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(s,), tau=tau)) as P:
+        P.assemble(s)
+        A = P.element_matrices(0)
+        cls, ec = P.cell_data()
+    f = oracle.Field(fld)
+    ref = oracle.assemble(f, n, s)
+    At_ref, cls_ref, _ = oracle.compress(f, n, ref, tau)
+    # assembly error of the stored FP32 operator against the exact FP64 one
+    assert cellwise_err(A, ref) <= 1e-5
+    # stored operator symmetric with zero row sums
+    assert np.abs(A - A.transpose(0, 2, 1)).max() == 0.0
+    assert (np.abs(A.sum(axis=2)).max(axis=1) <= 1e-6 * np.abs(A).max(axis=(1, 2))).all()
+    # storage classes: equal except near a threshold
+    K = oracle.kref(dim, n)
+    near = _class_ratio_near_threshold(ref, ec.astype(np.float32).astype(np.float64), K, tau, dim)
+    mism = (cls != cls_ref) & ~near
+    assert mism.sum() == 0, (np.unique(cls, return_counts=True), np.unique(cls_ref, return_counts=True))
+    # class-0 cells store exactly the geometric stencil
+    z = cls == 0
+    if z.any():
+        np.testing.assert_allclose(A[z], ec[z, None, None] * K[None], rtol=0, atol=1e-7 * np.abs(ref).max())
+    # where classes agree, the decoded surplus agrees within the storage bound
+    same = cls == cls_ref
+    err = np.abs(A[same] - At_ref[same]).max(axis=(1, 2)) / np.abs(ref[same]).max(axis=(1, 2))
+    assert (err <= 2.5e-6 + 1e-5).all()
+
+
+def test_mixed_storage_classes_cover_all_formats():
+    fld = inputs.fourier_field(3, 41, sigma=2e-5)
+    with mg.Problem(mg.problem_desc(3, 27, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(4,))) as P:
+        P.assemble(4)
+        cls, _ = P.cell_data()
+    assert set(np.unique(cls)) >= {1, 2}
+
+
+def _stored_operator(path, fld, n, s):
+    """The oracle's stored operator of a path: A(s) in FP64, or the decoded
+    lossy surplus storage for the mixed paths."""
+    f = oracle.Field(fld)
+    A = oracle.assemble(f, n, s)
+    if path in (mg.PATH_MIXED_PLAIN, mg.PATH_MIXED_DELAYED):
+        A, _, _ = oracle.compress(f, n, A, 1e-6)
+    return A
+
+
+@pytest.mark.parametrize("path,s,opdiff", [(mg.PATH_FP64_PLAIN, 4, 0.0), (mg.PATH_MIXED_PLAIN, 1, 0.0),
+                                           (mg.PATH_MIXED_PLAIN, 4, 1e-5)])
+@pytest.mark.parametrize("dim,n,fld", [(2, 81, inputs.disc_field(2)), (3, 27, inputs.boxes_field(3, 31)),
+                                       (3, 81, inputs.disc_field(3, v_in=100.0))])
+def test_operator_apply_and_jacobi_match_oracle(path, s, opdiff, dim, n, fld):
+    # opdiff bounds max|A_gpu - A_oracle| / max|A| per cell (0: both sides store the
+    # same numbers, e.g. the geometric stencils of a piecewise-constant field)
+    stored = _stored_operator(path, fld, n, s)
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(s,))) as P:
+        if s > 1:
+            P.assemble(s)
+        rng = np.random.default_rng(5)
+        m = dense.interior_mask(dim, n)
+        x = rng.standard_normal((n + 1) ** dim) * m
+        b = rng.standard_normal((n + 1) ** dim) * m
+        y_ref = oracle.apply(dim, n, stored, x)
+        j_ref = oracle.jacobi(dim, n, stored, b, x, 0.6)
+        r_ref = oracle.residual(dim, n, stored, b, x)
+        # the 2^d cells around a vertex each contribute up to 7 |A| |x| terms
+        scale = np.abs(stored).max() * np.abs(x).max() * (1 << dim) * 8
+        tol = 1e-13 * scale + opdiff * scale
+        y = P.apply(0, 0, x, b)
+        assert np.abs(y - y_ref).max() <= tol
+        assert np.abs(P.apply(0, 2, x, b) - r_ref).max() <= tol
+        dmin = np.abs(oracle.diag(dim, n, stored)[m]).min()
+        assert np.abs(P.apply(0, 1, x, b) - j_ref).max() <= 0.6 * (tol / dmin) * 4 + 1e-12 * np.abs(j_ref).max()
+        if path == mg.PATH_MIXED_PLAIN:
+            # FP32 inner arithmetic of the V-cycle
+            tol32 = 1e-6 * scale + opdiff * scale
+            assert np.abs(P.apply(0, 0, x, b, inner=True) - y_ref).max() <= tol32
+            assert np.abs(P.apply(0, 1, x, b, inner=True) - j_ref).max() <= 0.6 * (tol32 / dmin) * 4 + 1e-6 * np.abs(j_ref).max()
+
+
+@pytest.mark.parametrize("path", [mg.PATH_FP64_PLAIN, mg.PATH_MIXED_PLAIN])
+@pytest.mark.parametrize("dim,n,fld,s", [(2, 243, inputs.disc_field(2), 2), (3, 81, inputs.boxes_field(3, 33), 2),
+                                         (3, 27, inputs.fourier_field(3, 34, sigma=1.0), 4)])
+def test_galerkin_levels_match_oracle(path, dim, n, fld, s):
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(s,))) as P:
+        P.assemble(s)
+        levels = [P.element_matrices(l) for l in range(1, 3)]
+    Af = _stored_operator(path, fld, n, s)
+    tol = 1e-12 if path == mg.PATH_FP64_PLAIN else 2e-5
+    nc = n // 3
+    for Ac in levels:
+        ref = oracle.galerkin(dim, nc, Af)
+        assert cellwise_err(Ac, ref) <= tol
+        Af = ref
+        nc //= 3
+
+
+@pytest.mark.parametrize("path", [mg.PATH_FP64_PLAIN, mg.PATH_MIXED_PLAIN])
+@pytest.mark.parametrize("dim,n,fld", [(2, 81, inputs.disc_field(2)), (3, 27, inputs.fourier_field(3, 35, sigma=1.0))])
+def test_vcycle_matches_oracle(path, dim, n, fld):
+    A = _stored_operator(path, fld, n, 4)
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(4,))) as P:
+        P.assemble(4)
+        rng = np.random.default_rng(6)
+        b = rng.standard_normal((n + 1) ** dim) * dense.interior_mask(dim, n)
+        e = P.vcycle_apply(b)
+    e_ref = oracle.vcycle_once(dim, n, A, b)
+    tol = 1e-11 if path == mg.PATH_FP64_PLAIN else 1e-4
+    assert np.abs(e - e_ref).max() <= tol * np.abs(e_ref).max()
+
+
+@pytest.mark.parametrize("outer", [mg.OUTER_FCG, mg.OUTER_RICHARDSON])
+def test_fp64_plain_solve_matches_oracle_2d_disc(outer):
+    # 2D 81^2, eps = 10 in the disc r = 0.3, s = 8, V(2,2), omega = 0.6
+    w = inputs.workload("disc2d")
+    d = mg.problem_desc(2, 81, w.eps, path=mg.PATH_FP64_PLAIN, s_schedule=(8,), rtol=1e-10, outer=outer)
+    with mg.Problem(d) as P:
+        info = P.solve()
+        u = P.solution()
+    A = oracle.assemble(oracle.Field(w.eps), 81, 8)
+    u_ref, hist, k = oracle.solve(2, 81, A, rtol=1e-10, outer=outer)
+    assert info.rel_residual <= 2e-10
+    assert np.abs(u - u_ref).max() <= 1e-8 * np.abs(u_ref).max()
+    assert abs(info.cycles - k) <= 2
+    # residual of the GPU solution under the oracle's operator, in FP64 on the host
+    r = oracle.residual(2, 81, A, oracle.load_vector(2, 81), u)
+    assert np.linalg.norm(r) <= 3e-10 * np.linalg.norm(oracle.load_vector(2, 81))
+
+
+def test_mixed_solve_matches_oracle_compressed_operator():
+    fld = inputs.boxes_field(3, 2003)
+    n, s = 27, 4
+    d = mg.problem_desc(3, n, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(s,), rtol=1e-9)
+    with mg.Problem(d) as P:
+        info = P.solve()
+        u = P.solution()
+    f = oracle.Field(fld)
+    A = oracle.assemble(f, n, s)
+    At, _, _ = oracle.compress(f, n, A, 1e-6)
+    u_ref, _, _ = oracle.solve(3, n, At, rtol=1e-9)
+    u_exact_op, _, _ = oracle.solve(3, n, A, rtol=1e-9)
+    assert info.rel_residual <= 2e-9
+    assert np.abs(u - u_ref).max() <= 1e-5 * np.abs(u_ref).max()
+    # error against the FP64 oracle operator (reported, bounded)
+    assert np.abs(u - u_exact_op).max() <= 1e-4 * np.abs(u_exact_op).max()
+
+
+@pytest.mark.parametrize("path", [mg.PATH_FP64_DELAYED, mg.PATH_MIXED_DELAYED])
+def test_delayed_path_reaches_plain_solution(path):
+    fld = inputs.fourier_field(3, 2002, sigma=1.0)
+    n = 27
+    plain = mg.PATH_FP64_PLAIN if path == mg.PATH_FP64_DELAYED else mg.PATH_MIXED_PLAIN
+    with mg.Problem(mg.problem_desc(3, n, fld, path=plain, s_schedule=(8,), rtol=1e-9)) as P:
+        P.solve()
+        u_plain = P.solution()
+    with mg.Problem(mg.problem_desc(3, n, fld, path=path, s_schedule=(1, 2, 4, 8), rtol=1e-9)) as P:
+        info = P.solve()
+        u_del = P.solution()
+        A_del = P.element_matrices(0)
+    assert info.final_s == 8 and info.publishes >= 9
+    assert info.rel_residual <= 2e-9
+    assert np.abs(u_del - u_plain).max() <= 1e-6 * np.abs(u_plain).max()
+    ref = oracle.assemble(oracle.Field(fld), n, 8)
+    assert cellwise_err(A_del, ref) <= (1e-12 if path == mg.PATH_FP64_DELAYED else 1e-5)
+
+
+def test_async_assembly_published_at_cycle_boundaries():
+    fld = inputs.boxes_field(3, 2003)
+    with mg.Problem(mg.problem_desc(3, 81, fld, path=mg.PATH_MIXED_DELAYED, s_schedule=(1, 8))) as P:
+        r0 = P.vcycle(1)
+        P.assemble(8, async_=True)
+        rels = [P.vcycle(2) for _ in range(40)]
+        info = P.solve()
+        A = P.cell_matrices(np.arange(0, 81 ** 3, 997))
+    ref = oracle.assemble_cells(oracle.Field(fld), 81, 8, np.arange(0, 81 ** 3, 997))
+    assert cellwise_err(A, ref) <= 1e-5
+    assert info.status == mg.MG_OK and info.rel_residual <= 2e-8
+    assert r0 > rels[-1]
+
+
+def test_theta_setup_with_zero_rhs_converges_to_zero():
+    # Eq. "theta-setup": f = 0 has the solution u = 0; start from noise in [0, 4/3]
+    fld = inputs.theta_field(2, 8.0)
+    n = 81
+    u0 = inputs.noise_vector(2, n, 11)
+    d = mg.problem_desc(2, n, fld, path=mg.PATH_MIXED_DELAYED, s_schedule=(1, 2, 4), f_const=0.0, rtol=1e-10, u0=u0)
+    with mg.Problem(d) as P:
+        info = P.solve()
+        u = P.solution()
+    assert info.status == mg.MG_OK
+    assert np.abs(u).max() <= 1e-7
+
+
+def test_full_size_mixed_assembly_sampled():
+    # 243^3 cells, 64 boxes of contrast 1e3, s = 8, at the benchmark's size and chunking
+    w = inputs.workload("boxes3d")
+    n = w.n_cells
+    with mg.Problem(mg.problem_desc(3, n, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,))) as P:
+        P.assemble(8)
+        rng = np.random.default_rng(7)
+        cls_all, _ = P.cell_data()
+        nz = np.flatnonzero(cls_all)
+        cells = np.concatenate([rng.choice(n ** 3, 400, replace=False), rng.choice(nz, 400, replace=False),
+                                [0, n - 1, n ** 3 - 1, n ** 3 - n]])
+        A = P.cell_matrices(cells)
+    ref = oracle.assemble_cells(oracle.Field(w.eps), n, 8, cells)
+    assert cellwise_err(A, ref) <= 1e-5
+    assert 0.0 < (cls_all > 0).mean() < 0.5
+
+
+def test_serving_results_alone_and_in_mix_agree():
+    reqs = [(3, 27, inputs.fourier_field(3, 101, sigma=0.7)), (2, 243, inputs.fourier_field(2, 102, sigma=1.5)),
+            (3, 81, inputs.fourier_field(3, 103, sigma=1.0)), (2, 81, inputs.fourier_field(2, 104, sigma=2.0)),
+            (3, 27, inputs.fourier_field(3, 105, sigma=2.0))]
+    descs = [mg.problem_desc(d, n, f, path=mg.PATH_MIXED_DELAYED, s_schedule=(1, 2, 4, 8), rtol=1e-8)
+             for d, n, f in reqs]
+    alone = []
+    for d in descs:
+        with mg.Problem(d) as P:
+            P.solve()
+            alone.append(P.solution())
+    S = mg.Server(max_active=4)
+    ts = [S.submit(d, want_solution=True) for d in descs for _ in range(2)]
+    assert S.drain(120000) == mg.MG_OK
+    for i, t in enumerate(ts):
+        st, r = S.poll(t)
+        assert st == mg.MG_OK, mg.STATUS_NAMES[st]
+        assert r.rel_residual <= 2e-8
+        u = S.solution(t)
+        ua = alone[i // 2]
+        assert np.abs(u - ua).max() <= 1e-6 * np.abs(ua).max()
+    S.close()
+
+
+def test_edge_cases_smallest_grid_and_errors():
+    fld = inputs.disc_field(3)
+    with mg.Problem(mg.problem_desc(3, 9, fld, path=mg.PATH_FP64_PLAIN, s_schedule=(2,), rtol=1e-12)) as P:
+        info = P.solve()
+        u = P.solution()
+        with pytest.raises(mg.MGError):
+            P.element_matrices(5)
+        with pytest.raises(mg.MGError):
+            P.cell_matrices([9 ** 3])
+    A = oracle.assemble(oracle.Field(fld), 9, 2)
+    u_ref = dense.dense_solve(3, 9, A, oracle.load_vector(3, 9))
+    assert np.abs(u - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
