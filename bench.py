@@ -1,0 +1,335 @@
+"""Benchmark: time-to-1e-8 solves of the delayed-assembly mixed-precision path.
+
+One step = one complete solve of the workload (default: 3D, 243^3 cells,
+64 seeded box inclusions of contrast 1e3, accuracies s = 1 -> 2 -> 4 -> 8
+assembled on a side stream while FP32 V(2,2) cycles run under an FP64
+flexible-CG outer loop, stopping at ||f - A u|| <= 1e-8 ||f|| with every
+chunk at s = 8).  Problems are created before the timed region (their
+grids, geometric stencils and vectors resident in HBM); the timed region
+covers K mg_solve calls.  The working set of one solve (several GB) is far
+larger than L2, so no flush is needed between steps.
+
+Printed (one JSON line on rank 0): solves/s, p50/p99 time-to-solution, the
+FP64 plain assemble-then-solve path on the same workload, the roofline of
+the dominant kernel, the end-to-end figure through the C ABI with host
+buffers, clocks sampled during the timed region and the CPU oracle baseline.
+
+--impl reference times the CPU oracle (the reference arm of this build) on
+a bounded sample per step, scaled to the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2005_03606_gb300 import inputs  # noqa: E402
+
+METRIC = "solves/s & p50/p99 time-to-1e-8 residual, mixed vs FP64 plain; stencil GB/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_desc(mg, name, path, n_cells=None):
+    w = inputs.workload(name, n_cells)
+    sched = w.s_schedule if path in (mg.PATH_FP64_DELAYED, mg.PATH_MIXED_DELAYED) else [w.s_final]
+    return w, mg.problem_desc(w.dim, w.n_cells, w.eps, path=path, s_schedule=tuple(sched), rtol=1e-8,
+                              max_cycles=3000)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+def sweep_bytes(dim, n, cells_by_class, mixed, vec_bytes):
+    """Algorithmic DRAM bytes of one finest-level sweep: each vertex value read
+    (x, b) and written (y) once, each cell's stored operator read once."""
+    nvert = (n + 1) ** dim
+    ncell = n ** dim
+    np_ = 28 if dim == 3 else 6
+    b = nvert * 3 * vec_bytes
+    if mixed:
+        rec = (32, 64, 112) if dim == 3 else (16, 16, 32)
+        b += ncell * (4 + 1)                                  # eps_c, class byte
+        b += sum(int(cells_by_class[k + 1]) * rec[k] for k in range(3))
+        b += ncell // 32 * 12                                 # segment bases
+    else:
+        b += ncell * np_ * 8
+    return b
+
+
+# ---------------------------------------------------------------- oracle baseline
+def oracle_sample(name, cycles_full):
+    """Oracle cost of the workload, estimated from a bounded sample:
+    sampled-cell assembly at the final accuracy on the full grid, plus a
+    complete oracle solve of the same field on a 27^3 grid (assembly at s_final
+    and FCG cycles), scaled by cells and by the measured cycle count."""
+    import oracle
+    w = inputs.workload(name)
+    f = oracle.Field(w.eps)
+    n = w.n_cells
+    rng = np.random.default_rng(1)
+    ns = 4000
+    cells = rng.choice(n ** w.dim, ns, replace=False)
+    t0 = time.perf_counter()
+    oracle.assemble_cells(f, n, w.s_final, cells)
+    t_cell = (time.perf_counter() - t0) / ns
+    nsmall = 27
+    t0 = time.perf_counter()
+    A = oracle.assemble(f, nsmall, w.s_final)
+    t_asm_small = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, hist, k = oracle.solve(w.dim, nsmall, A, rtol=1e-8, max_cycles=400)
+    t_solve = time.perf_counter() - t0
+    t_cycle_vert = t_solve / max(k, 1) / (nsmall + 1) ** w.dim
+    est = t_cell * n ** w.dim + t_cycle_vert * (n + 1) ** w.dim * cycles_full
+    sample = (f"oracle FP64: {ns} sampled cells of {n}^{w.dim} at s={w.s_final} "
+              f"({t_cell * 1e3:.3f} ms/cell) + full oracle solve at {nsmall}^{w.dim} "
+              f"({k} FCG cycles, {t_solve:.1f} s; assembly {t_asm_small:.1f} s), scaled to {n}^{w.dim} cells "
+              f"and {cycles_full} cycles")
+    return 1.0 / est, sample, oracle.num_threads(), t_cell * ns + t_asm_small + t_solve
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    cycles_full = args.ref_cycles
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        v, sample, cores, spent = oracle_sample(args.workload, cycles_full)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(spent)
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "path": "oracle", "flush": "n/a (CPU)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2005_03606_gb300 import mg
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    lib = mg.load()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w, desc = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED)
+    mixed_path = mg.PATH_MIXED_DELAYED
+    # warm-up solves (also JIT of graphs, pool growth)
+    for _ in range(args.warmup):
+        with mg.Problem(desc) as P:
+            P.solve()
+    # device-resident timed region: K problems created beforehand
+    probs = [mg.Problem(workload_desc(mg, args.workload, mixed_path)[1]) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    barrier()
+    l0 = lib.mg_launch_count()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    infos, walls = [], []
+    for P in probs:
+        t0 = time.perf_counter()
+        infos.append(P.solve())
+        walls.append((time.perf_counter() - t0) * 1e3)
+    ev1.record()
+    barrier()
+    ck = clocks.stop()
+    launches = lib.mg_launch_count() - l0
+    region_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = world * args.steps / (region_ms / 1e3)
+    info0 = infos[-1]
+    # roofline: the finest-level V-cycle sweep (most launched kernel) and the FP64 matvec
+    P = probs[-1]
+    n, dim = w.n_cells, w.dim
+    ms_sweep = P.profile(0, 20)
+    ms_mv = P.profile(1, 10)
+    ms_gal = P.profile(3, 3)
+    cbc = list(info0.cells_by_class)
+    b_sweep = sweep_bytes(dim, n, cbc, True, 4)
+    b_mv = sweep_bytes(dim, n, cbc, True, 8)
+    peak, peak_kind = peaks()
+    kernels = {
+        "sweep_jacobi_f32": {"ms": ms_sweep, "bytes": b_sweep, "gbs": b_sweep / ms_sweep / 1e6},
+        "matvec_f64": {"ms": ms_mv, "bytes": b_mv, "gbs": b_mv / ms_mv / 1e6},
+        "galerkin_f32": {"ms": ms_gal},
+    }
+    for P in probs:
+        P.close()
+    # FP64 plain assemble-then-solve on the same workload
+    _, d64 = workload_desc(mg, args.workload, mg.PATH_FP64_PLAIN)
+    fp64_ms, fp64_cycles = [], []
+    for _ in range(args.fp64_steps):
+        with mg.Problem(d64) as P:
+            barrier()
+            t0 = time.perf_counter()
+            inf = P.solve()
+            fp64_ms.append((time.perf_counter() - t0) * 1e3)
+            fp64_cycles.append(inf.cycles)
+    # end to end through the C ABI with host buffers: create from the host
+    # descriptor, solve, read u back to the host, destroy
+    e2e_ms = []
+    nvert = (n + 1) ** dim
+    u_host = np.zeros(nvert)
+    for _ in range(max(1, args.e2e_steps)):
+        barrier()
+        t0 = time.perf_counter()
+        with mg.Problem(workload_desc(mg, args.workload, mixed_path)[1]) as P:
+            P.solve()
+            u_host[:] = P.solution()
+        barrier()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = world * len(e2e_ms) / (max_over_ranks(sum(e2e_ms)) / 1e3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, cores, _ = oracle_sample(args.workload, int(info0.cycles))
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank != 0:
+        return
+    walls_sorted = sorted(walls)
+    p50 = float(np.percentile(walls_sorted, 50))
+    p99 = float(np.percentile(walls_sorted, 99))
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": region_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (fp8/fp16/fp32 surplus storage)",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {dim}D {n}^{dim} cells, {w.eps.n_boxes or w.eps.n_modes} "
+                               f"{'boxes' if w.eps.n_boxes else 'modes'}, s={w.s_schedule}",
+                   "path": "mixed delayed (FP32 V(2,2) + FP64 FCG)", "parallelism": f"replicas x{world}",
+                   "flush": "working set > L2 (no flush)"},
+        "p50_ms": p50, "p99_ms": p99,
+        "cycles": int(info0.cycles), "publishes": int(info0.publishes), "rel_residual": info0.rel_residual,
+        "cells_by_class": cbc, "stencil_bytes": int(info0.payload_bytes),
+        "fp64_plain": {"solves_per_s": 1e3 / statistics.median(fp64_ms), "ms": fp64_ms, "cycles": fp64_cycles},
+        "speedup_vs_fp64_plain": statistics.median(fp64_ms) / p50,
+        "roofline": {"bound": "hbm", "kernel": "sweep_jacobi_f32 (finest level, V-cycle smoother)",
+                     "achieved": kernels["sweep_jacobi_f32"]["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": kernels["sweep_jacobi_f32"]["gbs"] / peak, "peak_kind": peak_kind,
+                     "traffic": None},
+        "kernels": kernels,
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(ctypes_sizeof_desc()),
+                "d2h_bytes_per_step": int(nvert * 8)},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ctypes_sizeof_desc():
+    import ctypes
+    from paper_2005_03606_gb300 import mg
+    return ctypes.sizeof(mg.mg_problem_desc)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="boxes3d", choices=["boxes3d", "fourier3d", "jump3d", "disc2d"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-cycles", type=int, default=200,
+                    help="cycle count used to scale the oracle sample in --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,21 @@ mg_status mg_apply_level(mg_problem* p, int level, int op, int inner, const doub
  * problem's operators; b and e are host (N+1)^d FP64 vectors. */
 mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
 
+/* Times `reps` back-to-back launches of one kernel of the solve on the
+ * problem's stream with CUDA events (3 untimed launches first) and returns
+ * the mean milliseconds per launch:
+ *   which = 0: finest-level damped Jacobi sweep in the V-cycle arithmetic
+ *   which = 1: finest-level FP64 matvec of the outer loop (with dot products)
+ *   which = 2: finest-level FP64 residual f - A u
+ *   which = 3: Galerkin product finest -> next coarser level
+ * The problem's iteration vectors are used as scratch (the next cycle
+ * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_CUDA. */
+mg_status mg_profile_kernel(mg_problem* p, int which, int reps, double* ms_per_launch);
+
+/* Number of kernels of this library launched so far in this process
+ * (graph replays count every kernel they contain). */
+uint64_t mg_launch_count(void);
+
 /* ---------------- serving ---------------- */
 
 typedef struct {

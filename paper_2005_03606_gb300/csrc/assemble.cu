@@ -491,7 +491,7 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
     case EPS_THETA: assemble_kernel<D, T, EPS_THETA><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace
@@ -506,7 +506,7 @@ cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, voi
     if (prec64) eps_centre_kernel<3, double><<<g, 256, 0, st>>>(*eps, N, (double*)eps_c);
     else eps_centre_kernel<3, float><<<g, 256, 0, st>>>(*eps, N, (float*)eps_c);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_assemble(const AsmLaunch& a, cudaStream_t st) {
@@ -521,7 +521,7 @@ cudaError_t launch_geometric_full(int dim, int N, double hfac, const double* eps
   int g = grid_for(ncell, 256);
   if (dim == 2) geometric_full_kernel<2><<<g, 256, 0, st>>>(hfac, eps_c, cell0, ncell, out);
   else geometric_full_kernel<3><<<g, 256, 0, st>>>(hfac, eps_c, cell0, ncell, out);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_pack_count(int dim, int N, long long nrows, int nseg_x, const uint8_t* cls,
@@ -530,10 +530,10 @@ cudaError_t launch_pack_count(int dim, int N, long long nrows, int nseg_x, const
   (void)N;
   const long long nseg = nrows * nseg_x;
   pack_count_kernel<<<grid_for(nseg * 32, 256), 256, 0, st>>>(nseg, cls, seg_base);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launched();
   if (e != cudaSuccess) return e;
   scan_kernel<<<3, 1024, 0, st>>>(nseg, seg_base, totals);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const uint8_t* cls,
@@ -543,7 +543,7 @@ cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const 
   const int g = grid_for(nseg * 32, 256);
   if (dim == 2) pack_copy_kernel<2><<<g, 256, 0, st>>>(nseg, cls, seg_base, N, nseg_x, rec, p1, p2, p3);
   else pack_copy_kernel<3><<<g, 256, 0, st>>>(nseg, cls, seg_base, N, nseg_x, rec, p1, p2, p3);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace mg

@@ -327,7 +327,7 @@ cudaError_t launch_galerkin_range(const LevelOp& fine, int out64, void* coarse_f
     }
   }
 #undef MG_GAL
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_galerkin(const LevelOp& fine, int out64, void* coarse_full, cudaStream_t st) {
@@ -343,7 +343,7 @@ cudaError_t launch_coarse_factor(const LevelOp& coarsest, double* L, cudaStream_
     if (coarsest.elem64) coarse_factor_kernel<3, double><<<1, 32, 0, st>>>(coarsest, L);
     else coarse_factor_kernel<3, float><<<1, 32, 0, st>>>(coarsest, L);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void* b, void* e, cudaStream_t st) {
@@ -354,7 +354,7 @@ cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void*
     if (vec64) coarse_solve_kernel<3, double><<<1, 32, 0, st>>>(L, (const double*)b, (double*)e);
     else coarse_solve_kernel<3, float><<<1, 32, 0, st>>>(L, (const float*)b, (float*)e);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_decode_matrices(const LevelOp& op, const long long* cells, long long ncells, double* out,
@@ -370,7 +370,7 @@ cudaError_t launch_decode_matrices(const LevelOp& op, const long long* cells, lo
     else if (op.elem64) decode_kernel<3, double, false><<<g, 128, 0, st>>>(op, cells, ncell, out);
     else decode_kernel<3, float, false><<<g, 128, 0, st>>>(op, cells, ncell, out);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace mg

@@ -172,6 +172,15 @@ struct DevScalars {     // per-problem scalars written by reductions
 void set_error(const char* fmt, ...);
 bool cuda_ok(cudaError_t e, const char* what);
 
+// Counts kernels of this library enqueued on a stream (launch wrappers call
+// it once per kernel); graph replays add their captured kernel count.
+void count_launches(long long n);
+long long launch_count();
+inline cudaError_t launched() {
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // assemble.cu
 struct AsmLaunch {
   int dim, N, s, kind;

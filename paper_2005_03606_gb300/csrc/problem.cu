@@ -46,6 +46,15 @@ bool cuda_ok(cudaError_t e, const char* what) {
 
 const char* last_error() { return t_err.c_str(); }
 
+static std::atomic<long long> g_launches{0};
+static thread_local long long t_launches = 0;
+void count_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
+
 }  // namespace mg
 
 using namespace mg;
@@ -96,6 +105,7 @@ struct mg_problem {
   mg_problem_desc desc{};
   EpsDev eps{};
   int dim = 0, N = 0, L = 0;
+  int device = 0;                 // CUDA device current at creation
   bool mixed = false, delayed = false;
   cudaStream_t st = nullptr, side = nullptr;
   bool own_stream = false;
@@ -124,6 +134,7 @@ struct mg_problem {
   double ff = 0.0, rr = 0.0, rr_first = 0.0;
   int cycles = 0, publishes = 0;
   cudaGraphExec_t g_iter[2] = {nullptr, nullptr};
+  long long g_kernels[2] = {0, 0};   // kernels per graph replay
   bool use_graphs = true;
   // delayed assembly
   std::thread worker;
@@ -471,8 +482,11 @@ mg_status outer_iteration(mg_problem* P) {
     if (!P->g_iter[first]) {
       cudaGraph_t g;
       MG_CHECK(cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal));
+      const long long before = thread_launch_count();
       mg_status s = outer_iteration_enqueue(P, first);
       cudaError_t e = cudaStreamEndCapture(P->st, &g);
+      P->g_kernels[first] = thread_launch_count() - before;
+      count_launches(-P->g_kernels[first]);  // captured, not launched
       if (s != MG_OK) return s;
       if (e != cudaSuccess) return oom_or_cuda(e, "end capture");
       e = cudaGraphInstantiate(&P->g_iter[first], g, 0);
@@ -480,6 +494,7 @@ mg_status outer_iteration(mg_problem* P) {
       if (e != cudaSuccess) return oom_or_cuda(e, "graph instantiate");
     }
     MG_CHECK(cudaGraphLaunch(P->g_iter[first], P->st));
+    count_launches(P->g_kernels[first]);
   } else {
     mg_status s = outer_iteration_enqueue(P, first);
     if (s != MG_OK) return s;
@@ -498,6 +513,7 @@ mg_status read_scalars(mg_problem* P) {
 
 // ------------------------------------------------------------ delayed assembly
 void worker_main(mg_problem* P) {
+  cudaSetDevice(P->device);
   for (;;) {
     Job job;
     {
@@ -660,6 +676,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   P->delayed = d.path == MG_PATH_FP64_DELAYED || d.path == MG_PATH_MIXED_DELAYED;
   P->tv = P->mixed ? 4 : 8;
   fill_eps(d.eps, d.dim, &P->eps);
+  if (cudaGetDevice(&P->device) != cudaSuccess) P->device = 0;
   auto fail = [&](mg_status s) {
     mg_destroy_problem(P);
     return s;
@@ -925,6 +942,8 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   const double tol2 = d.rtol * d.rtol;
   mg_status result = MG_ERR_NOT_CONVERGED;
   bool have_first = false;
+  double seg_rr = 0.0;
+  int seg_cycles = 0;
   while (P->cycles < d.max_cycles) {
     int npub = 0;
     mg_status s = publish_ready(P, false, &npub);
@@ -942,6 +961,10 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
         have_first = true;
       }
       if (P->ff <= 0) P->ff = P->rr > 0 ? P->rr : 1.0;
+      // divergence is judged against the residual of the current operator
+      // at the last restart (a publication changes the operator)
+      seg_rr = P->rr;
+      seg_cycles = 0;
     }
     const double refn = P->ff > 0 ? P->ff : ref;
     if (P->rr <= tol2 * refn) {
@@ -970,9 +993,11 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     if (s != MG_OK) return s;
     s = read_scalars(P);
     if (s != MG_OK) return s;
-    if (!(P->rr == P->rr) || (P->cycles > 5 && P->rr > 1e4 * std::max(P->rr_first, 1e-300))) {
+    ++seg_cycles;
+    if (!std::isfinite(P->rr) || (seg_cycles > 5 && P->rr > 1e4 * std::max(seg_rr, 1e-300))) {
       result = MG_ERR_DIVERGED;
-      set_error("residual diverged");
+      set_error("residual diverged: ||r||^2 = %.3e after %d cycles (%.3e at the last restart)", P->rr,
+                P->cycles, seg_rr);
       break;
     }
   }
@@ -1158,6 +1183,42 @@ mg_status mg_apply_level(mg_problem* P, int level, int op, int inner, const doub
   MG_CHECK(cudaStreamSynchronize(P->st));
   return MG_OK;
 }
+
+mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_launch) {
+  if (!P || reps < 1 || which < 0 || which > 3 || !ms_per_launch) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  Level& l0 = P->lev[0];
+  cudaEvent_t e0, e1;
+  MG_CHECK(cudaEventCreate(&e0));
+  MG_CHECK(cudaEventCreate(&e1));
+  const int vec64 = P->mixed ? 0 : 1;
+  auto launch = [&](int i) -> cudaError_t {
+    void* x = (i & 1) ? l0.x1 : l0.x0;
+    void* y = (i & 1) ? l0.x0 : l0.x1;
+    switch (which) {
+      case 0: return launch_sweep(l0.op, SW_JACOBI, vec64, x, l0.b, y, P->desc.omega, nullptr, nullptr, P->st);
+      case 1: return launch_sweep(l0.op, SW_MATVEC, 1, P->p, P->r, P->q, 0.0, P->partials, nullptr, P->st);
+      case 2: return launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->q, 0.0, nullptr, nullptr, P->st);
+      default: return launch_galerkin(l0.op, P->mixed ? 0 : 1, P->lev[1].full_store, P->st);
+    }
+  };
+  for (int i = 0; i < 3; ++i) MG_CHECK(launch(i));
+  MG_CHECK(cudaEventRecord(e0, P->st));
+  for (int i = 0; i < reps; ++i) MG_CHECK(launch(i));
+  MG_CHECK(cudaEventRecord(e1, P->st));
+  MG_CHECK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  MG_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = ms / reps;
+  P->need_restart = true;
+  return MG_OK;
+}
+
+uint64_t mg_launch_count(void) { return (uint64_t)launch_count(); }
 
 mg_status mg_vcycle_apply(mg_problem* P, const double* b, double* e_out) {
   if (!P || !b || !e_out) {

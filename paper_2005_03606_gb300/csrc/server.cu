@@ -61,6 +61,7 @@ struct mg_server {
   mg_server_desc desc{};
   size_t budget = 0, in_use = 0;
   int active = 0;
+  int device = 0;
   uint64_t next_id = 1;
   uint64_t admissions = 0;
   bool stop = false;
@@ -110,6 +111,7 @@ void run_request(mg_server* S, Request* R) {
 }
 
 void worker_loop(mg_server* S) {
+  cudaSetDevice(S->device);
   for (;;) {
     Request* R = nullptr;
     {
@@ -150,6 +152,7 @@ mg_status mg_server_create(const mg_server_desc* desc, mg_server** out) {
   mg_server* S = new mg_server();
   if (desc) S->desc = *desc;
   if (S->desc.max_active <= 0) S->desc.max_active = 8;
+  if (cudaGetDevice(&S->device) != cudaSuccess) S->device = 0;
   if (S->desc.hbm_budget_bytes > 0) {
     S->budget = (size_t)S->desc.hbm_budget_bytes;
   } else {

@@ -167,7 +167,7 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     sweep_kernel<D, TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
   else
     sweep_kernel<D, TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
-  return cudaGetLastError();
+  return launched();
 }
 
 // ---------------------------------------------------------------- transfers
@@ -371,7 +371,7 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
     if (vec64) restrict_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
     else restrict_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st) {
@@ -385,7 +385,7 @@ cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void*
     if (vec64) prolong_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)ec, (double*)ef);
     else prolong_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)ec, (float*)ef);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
@@ -393,31 +393,31 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMem
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks, cudaStream_t st) {
   *nblocks = kRedBlocks;
   dot_kernel<double, double><<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double* partials, int* nblocks,
                            cudaStream_t st) {
   *nblocks = kRedBlocks;
   dot_kernel<float, double><<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st) {
   reduce_finish_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncomp, out);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_scalar_op(DevScalars* sc, int op, cudaStream_t st) {
   scalar_kernel<<<1, 1, 0, st>>>(sc, op);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_fcg_direction(long long n, int first, int z64, const void* z, double* p, const DevScalars* sc,
                                  cudaStream_t st) {
   if (z64) fcg_direction_kernel<double><<<vgrid(n), 256, 0, st>>>(n, first, (const double*)z, p, sc);
   else fcg_direction_kernel<float><<<vgrid(n), 256, 0, st>>>(n, first, (const float*)z, p, sc);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p, const double* q,
@@ -426,19 +426,19 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
   *nblocks = kRedBlocks;
   if (r32_out) fcg_update_kernel<float><<<kRedBlocks, 256, 0, st>>>(n, u, r, p, q, sc, (float*)rin, partials);
   else fcg_update_kernel<double><<<kRedBlocks, 256, 0, st>>>(n, u, r, p, q, sc, (double*)rin, partials);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_richardson_update(long long n, double* u, int z64, const void* z, cudaStream_t st) {
   if (z64) richardson_kernel<double><<<vgrid(n), 256, 0, st>>>(n, u, (const double*)z);
   else richardson_kernel<float><<<vgrid(n), 256, 0, st>>>(n, u, (const float*)z);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_convert(long long n, int to64, const void* src, void* dst, cudaStream_t st) {
   if (to64) convert_kernel<float, double><<<vgrid(n), 256, 0, st>>>(n, (const float*)src, (double*)dst);
   else convert_kernel<double, float><<<vgrid(n), 256, 0, st>>>(n, (const double*)src, (float*)dst);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_load_vector(int dim, int N, double val, double* f, cudaStream_t st) {
@@ -446,7 +446,7 @@ cudaError_t launch_load_vector(int dim, int N, double val, double* f, cudaStream
   for (int a = 0; a < dim; ++a) nv *= (N + 1);
   if (dim == 2) load_vector_kernel<2><<<vgrid(nv), 256, 0, st>>>(N, val, f);
   else load_vector_kernel<3><<<vgrid(nv), 256, 0, st>>>(N, val, f);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace mg

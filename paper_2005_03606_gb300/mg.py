@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_server_destroy": (st, [_VP]),
             "mg_last_error": (ctypes.c_char_p, []),
             "mg_version": (ctypes.c_char_p, []),
+            "mg_profile_kernel": (st, [_VP, ctypes.c_int, ctypes.c_int, _D]),
+            "mg_launch_count": (ctypes.c_uint64, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -249,6 +251,11 @@ class Problem:
         bp = _p(np.ascontiguousarray(b, np.float64)) if b is not None else None
         _check(load().mg_apply_level(self.h, level, op, 1 if inner else 0, _p(x), bp, _p(y)))
         return y
+
+    def profile(self, which: int, reps: int = 20) -> float:
+        ms = ctypes.c_double()
+        _check(load().mg_profile_kernel(self.h, which, reps, ctypes.byref(ms)))
+        return ms.value
 
     def vcycle_apply(self, b: np.ndarray) -> np.ndarray:
         b = np.ascontiguousarray(b, np.float64)

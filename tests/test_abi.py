@@ -31,7 +31,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:mg_status|const char\*)\s+(mg_\w+)\s*\(", src, flags=re.M)
+        names += re.findall(r"^\s*(?:mg_status|const char\*|uint64_t)\s+(mg_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
