@@ -301,6 +301,23 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_probe(args, local_rank):
+    """Small-case kernel probe for profilers: one problem of the workload at
+    --n cells, assembled to its final accuracy, then `--probe-reps` launches
+    of one kernel through mg_profile_kernel."""
+    import torch
+    from paper_2005_03606_gb300 import mg
+    torch.cuda.set_device(local_rank)
+    which = {"sweep": 0, "matvec": 1, "residual": 2, "galerkin": 3}[args.probe]
+    path = mg.PATH_FP64_PLAIN if args.probe_fp64 else mg.PATH_MIXED_PLAIN
+    w, d = workload_desc(mg, args.workload, path, n_cells=args.n)
+    with mg.Problem(d) as P:
+        P.assemble(w.s_final)
+        ms = P.profile(which, args.probe_reps)
+    print(json.dumps({"probe": args.probe, "workload": args.workload, "n_cells": w.n_cells, "fp64": args.probe_fp64,
+                      "ms_per_launch": ms}), flush=True)
+
+
 def ctypes_sizeof_desc():
     import ctypes
     from paper_2005_03606_gb300 import mg
@@ -319,7 +336,15 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=200,
                     help="cycle count used to scale the oracle sample in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin"],
+                    help="profile one kernel on a small case instead of benchmarking")
+    ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
+    ap.add_argument("--probe-reps", type=int, default=3)
+    ap.add_argument("--n", type=int, default=None, help="cells per axis for --probe")
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))

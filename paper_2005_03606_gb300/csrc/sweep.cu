@@ -18,15 +18,20 @@ namespace {
 
 constexpr int kBX = 32, kBY = 8;
 
+// Record of a cell of storage class cls > 0: the rank of the cell among the
+// class-cls cells of its 32-cell segment (from the segment's class bytes)
+// plus the segment's base offset.  seg = segment index within the chunk.
 template <int D>
-__device__ __forceinline__ void locate(const LevelOp& op, long long c, int clast, int* chunk, long long* lc) {
-  int ch = clast / op.layers;
-  if (ch >= op.nchunk) ch = op.nchunk - 1;
-  *chunk = ch;
-  *lc = c - (long long)ch * op.chunk_cells;
+__device__ __forceinline__ const uint8_t* record_at(const CmpChunk& ck, int seg, int lane, int cls) {
+  const unsigned r = rank_in_segment(ck.cls + (size_t)seg * kSegCells, lane, cls);
+  const unsigned base = __ldg(ck.seg_base + (size_t)(cls - 1) * ck.nseg + seg);
+  const int recb = cls == 1 ? Dim<D>::REC1 : (cls == 2 ? Dim<D>::REC2 : Dim<D>::REC3);
+  return ck.pool[cls - 1] + (size_t)(base + r) * recb;
 }
 
 // (A u)_v and diag_v at interior vertex (i, j, k) from the 3^d neighbourhood u.
+// All index arithmetic is 32-bit and done per cell layer (the layer along the
+// last axis fixes the chunk); 64-bit products appear only in byte offsets.
 template <int D, typename TA, bool CMP, typename TS>
 __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, int k, const TA* u,
                                              TA* Au, TA* dg) {
@@ -34,51 +39,65 @@ __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, in
   const int N = op.N;
   TA acc = 0, dgs = 0;
 #pragma unroll
-  for (int o = 0; o < NV; ++o) {
-    const int ox = o & 1, oy = (o >> 1) & 1, oz = D == 3 ? (o >> 2) & 1 : 0;
-    const int cx = i - 1 + ox, cy = j - 1 + oy, cz = D == 3 ? k - 1 + oz : 0;
-    const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
-    const long long c = D == 2 ? (long long)cy * N + cx : ((long long)cz * N + cy) * N + cx;
-    int ch;
-    long long lc;
-    locate<D>(op, c, D == 2 ? cy : cz, &ch, &lc);
-    // neighbourhood index of local vertex b of this cell: offset (o - 1 + bits(b))
-    const int ua = (ox + ((a) & 1)) + 3 * (oy + ((a >> 1) & 1)) + (D == 3 ? 9 * (oz + ((a >> 2) & 1)) : 0);
-    const TA u_a = u[ua];
-    if (CMP) {
-      const TA ge = (TA)__ldg(op.eps_c + c) * (TA)op.hfac;
+  for (int ol = 0; ol < 2; ++ol) {
+    // cell layer along the last axis and its chunk
+    const int cl = (D == 3 ? k : j) - 1 + ol;
+    int ch = cl / op.layers;
+    ch = ch < op.nchunk ? ch : op.nchunk - 1;
+    const int ll = cl - ch * op.layers;  // layer within the chunk
 #pragma unroll
-      for (int b = 0; b < NV; ++b) {
-        if (b == a) continue;
-        const double kv = kref_off<D>(popc_small(a ^ b));
-        if (kv == 0.0) continue;
-        const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
-        acc += ge * (TA)kv * (u[ub] - u_a);
-      }
-      dgs += ge * (TA)kref_diag<D>();
-      const CmpChunk& ck = op.cmp[ch];
-      const int cls = cell_class(ck, N, op.nseg_x, lc);
-      if (cls) {
-        const uint8_t* rec = cell_record<D>(ck, N, op.nseg_x, lc, cls);
+    for (int om = 0; om < (D == 3 ? 2 : 1); ++om) {
+      // for D = 3: om selects the y row; for D = 2 the row is the layer itself
+      const int cy = D == 3 ? j - 1 + om : cl;
+      const int row = D == 3 ? ll * N + cy : ll;      // x-row within the chunk
+      const int cbase = D == 3 ? (cl * N + cy) * N : cl * N;  // global cell index of x = 0
+      const int segrow = row * op.nseg_x;
 #pragma unroll
-        for (int b = 0; b < NV; ++b) {
-          if (b == a) continue;
-          const TA dv = (TA)decode_entry<D>(rec, cls, pair_of(NV, a, b));
-          const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
-          acc += dv * (u[ub] - u_a);
-          dgs -= dv;
+      for (int ox = 0; ox < 2; ++ox) {
+        const int cx = i - 1 + ox;
+        const int oy = D == 3 ? om : ol, oz = D == 3 ? ol : 0;
+        const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
+        // neighbourhood index of local vertex b of this cell: offset (o - 1 + bits(b))
+        const int ua = 1 + 3 + (D == 3 ? 9 : 0);
+        const TA u_a = u[ua];
+        if (CMP) {
+          const TA ge = (TA)__ldg(op.eps_c + cbase + cx) * (TA)op.hfac;
+#pragma unroll
+          for (int b = 0; b < NV; ++b) {
+            if (b == a) continue;
+            const double kv = kref_off<D>(popc_small(a ^ b));
+            if (kv == 0.0) continue;
+            const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+            acc += ge * (TA)kv * (u[ub] - u_a);
+          }
+          dgs += ge * (TA)kref_diag<D>();
+          const CmpChunk& ck = op.cmp[ch];
+          const int seg = segrow + (cx >> 5);
+          const int cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
+          if (cls) {
+            const uint8_t* rec = record_at<D>(ck, seg, cx & 31, cls);
+#pragma unroll
+            for (int b = 0; b < NV; ++b) {
+              if (b == a) continue;
+              const TA dv = (TA)decode_entry<D>(rec, cls, pair_of(NV, a, b));
+              const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+              acc += dv * (u[ub] - u_a);
+              dgs -= dv;
+            }
+          }
+        } else {
+          const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
+          const size_t cc = (size_t)op.chunk_cells;
+          const int lc = row * N + cx;
+#pragma unroll
+          for (int b = 0; b < NV; ++b) {
+            if (b == a) continue;
+            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, b) * cc + lc);
+            const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+            acc += av * (u[ub] - u_a);
+            dgs -= av;
+          }
         }
-      }
-    } else {
-      const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
-      const long long cc = op.chunk_cells;
-#pragma unroll
-      for (int b = 0; b < NV; ++b) {
-        if (b == a) continue;
-        const TA av = (TA)__ldg(A + (long long)pair_of(NV, a, b) * cc + lc);
-        const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
-        acc += av * (u[ub] - u_a);
-        dgs -= av;
       }
     }
   }
@@ -117,16 +136,16 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
   double d1 = 0.0, d2 = 0.0;
   if (valid) {
     TA u[D == 3 ? 27 : 9];
-    const long long v = D == 2 ? (long long)j * n1 + i : ((long long)k * n1 + j) * n1 + i;
+    const int v = D == 2 ? j * n1 + i : (k * n1 + j) * n1 + i;
+    const int plane = n1 * n1;
 #pragma unroll
     for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < 3; ++dy) {
+        const TV* xr = x + (v + (dy - 1) * n1 + (D == 3 ? (dz - 1) * plane : 0));
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const long long w = v + (dx - 1) + (long long)(dy - 1) * n1 + (D == 3 ? (long long)(dz - 1) * n1 * n1 : 0);
-          u[dx + 3 * dy + 9 * dz] = (TA)__ldg(x + w);
-        }
+        for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy + 9 * dz] = (TA)__ldg(xr + (dx - 1));
+      }
     TA Au, dg;
     vertex_apply<D, TA, CMP, TS>(op, i, j, k, u, &Au, &dg);
     const TA uv = u[D == 3 ? 13 : 4];
