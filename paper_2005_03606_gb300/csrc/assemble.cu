@@ -115,10 +115,13 @@ __global__ void eps_centre_kernel(const EpsDev F, int N, T* __restrict__ out) {
   }
 }
 
-struct XEntry {
+// per-sample x-axis data of a cell, in the arithmetic precision T (the
+// discontinuity decisions behind `bits` and `jmul` are taken in FP64)
+template <typename T>
+struct XEntryT {
   unsigned long long bits;  // BOXES: mask of boxes whose x-interval holds the sample; DISC: dx^2 (FP64 bits)
-  double jmul;              // planar jump multiplier
-  double th;                // THETA: x-factor
+  T jmul;                   // planar jump multiplier
+  T th;                     // THETA: x-factor
 };
 
 template <int D, typename T, int KIND>
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
   const int N = A.N, s = A.s;
   __shared__ T s_t1[kMaxS], s_t2[kMaxS];
   __shared__ T s_rot_c[kMaxModes], s_rot_s[kMaxModes];
-  __shared__ XEntry s_x[kAsmThreads / 32][64];
+  __shared__ XEntryT<T> s_x[kAsmThreads / 32][64];
+  const T vin = (T)F.v_in, vout = (T)F.v_out;
   for (int j = threadIdx.x; j < s; j += blockDim.x) {
     s_t1[j] = (T)(2 * j + 1) / (T)(2 * s);
     s_t2[j] = (T)(3 * j * j + 3 * j + 1) / (T)(3 * s * s);
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
   while (G * 2 <= R && G < 32) G *= 2;
   const int CPW = 32 / G;
   const int grp = lane / G, lig = lane % G;
-  XEntry* xt = &s_x[warp][0];
+  XEntryT<T>* xt = &s_x[warp][0];
   const int xt_stride = s;  // entries per group (CPW * s <= 64 by construction)
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -173,10 +177,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     // x-axis table of the group's cell
     for (int jx = lig; jx < s; jx += G) {
       double x = sample_x(N, s, ci[0], jx);
-      XEntry e;
+      XEntryT<T> e;
       e.bits = 0;
       e.th = 0;
-      e.jmul = (F.jump_factor != 1.0 && x >= F.jump_x) ? F.jump_factor : 1.0;
+      e.jmul = (T)((F.jump_factor != 1.0 && x >= F.jump_x) ? F.jump_factor : 1.0);
       if (KIND == EPS_BOXES) {
         unsigned long long m = 0;
         for (int b = 0; b < F.n_boxes; ++b)
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
         double d = __dsub_rn(x, F.center[0]);
         e.bits = (unsigned long long)__double_as_longlong(__dmul_rn(d, d));
       } else if (KIND == EPS_THETA) {
-        e.th = (double)theta_factor<T>(F, x);
+        e.th = theta_factor<T>(F, x);
       }
       xt[grp * xt_stride + jx] = e;
     }
@@ -194,12 +198,15 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     unsigned long long cand = 0;
     if (KIND == EPS_BOXES)
       for (int jx = 0; jx < s; ++jx) cand |= xt[grp * xt_stride + jx].bits;
+    // no box reaches a sample of this cell and eps is the same everywhere in it:
+    // every sample equals the cell-centre value and the surplus is exactly zero
+    const bool flat = KIND == EPS_BOXES && cand == 0 && F.jump_factor == 1.0 && eref == vout;
 
     T W[NW];
 #pragma unroll
     for (int q = 0; q < NW; ++q) W[q] = 0;
 
-    for (int r = lig; r < R && valid; r += G) {
+    for (int r = lig; r < R && valid && !flat; r += G) {
       const int jy = r % s, jz = (D == 3) ? r / s : 0;
       // per-row set-up
       unsigned long long rowbits = ~0ull;
@@ -242,18 +249,18 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
       }
       T S0 = 0, S1 = 0, S2 = 0;
       for (int jx = 0; jx < s; ++jx) {
-        const XEntry& xe = xt[grp * xt_stride + jx];
+        const XEntryT<T>& xe = xt[grp * xt_stride + jx];
         T e;
         if (KIND == EPS_CONST) {
           e = (T)F.v_out;
         } else if (KIND == EPS_BOXES) {
-          e = (T)((xe.bits & rowbits) ? F.v_in : F.v_out);
+          e = (xe.bits & rowbits) ? vin : vout;
         } else if (KIND == EPS_DISC) {
           double r2 = __dadd_rn(__longlong_as_double((long long)xe.bits), rowd);
           if (D == 3) r2 = __dadd_rn(r2, dz2);
-          e = (T)(r2 < F.r2lim ? F.v_in : F.v_out);
+          e = r2 < F.r2lim ? vin : vout;
         } else if (KIND == EPS_THETA) {
-          e = (T)1 + (T)(0.3 / D) * ((T)xe.th * rowth);
+          e = (T)1 + (T)(0.3 / D) * (xe.th * rowth);
         } else {
           T g = 0;
           for (int m = 0; m < F.n_modes; ++m) {
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           }
           e = (T)F.v_out * t_exp<T>((T)F.amp * g);
         }
-        if (xe.jmul != 1.0) e *= (T)xe.jmul;
+        e *= xe.jmul;
         const T ep = e - eref;
         S0 += ep;
         S1 += ep * s_t1[jx];

@@ -170,10 +170,188 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
   }
 }
 
+// ---------------------------------------------------------------- 3D tiled sweep
+// A CTA owns a 32 x 8 column of vertices and marches along z over kZC vertex
+// planes.  u planes (with a one-vertex halo) and cell layers (cell-centre
+// eps times h, storage class, record pointer) pass through shared-memory
+// rings, so each value is fetched from global memory once per CTA instead of
+// once per vertex that touches it.
+constexpr int kTX = 32, kTY = 8, kZC = 32;
+
+template <typename TV, typename TA, typename TS, int MODE, bool CMP>
+__global__ void __launch_bounds__(kTX * kTY) sweep3_tiled(const LevelOp op, const TV* __restrict__ x,
+                                                          const TV* __restrict__ b, TV* __restrict__ y,
+                                                          TA omega, double* __restrict__ partials) {
+  constexpr int NV = 8;
+  __shared__ TA su[3][kTY + 2][kTX + 2];
+  __shared__ TA sge[2][kTY + 1][kTX + 1];
+  __shared__ const uint8_t* srec[2][kTY + 1][kTX + 1];
+  __shared__ uint8_t scls[2][kTY + 1][kTX + 1];
+  __shared__ const TS* sA[2];
+  __shared__ int srow[2];
+  __shared__ double sh[2][kTX * kTY / 32];
+  const int N = op.N, n1 = N + 1;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;  // vertex x0 + tx + 1 is this thread's column
+  const int i = x0 + tx + 1, j = y0 + ty + 1;
+  const bool col_ok = i < N && j < N;
+  const int k0 = 1 + blockIdx.z * kZC;
+  const int k1 = min(N - 1, k0 + kZC - 1);
+  double d1 = 0.0, d2 = 0.0;
+
+  auto load_plane = [&](int p) {   // u plane p (vertices x0..x0+33, y0..y0+9)
+    TA(*dst)[kTX + 2] = su[p % 3];
+    for (int t = tid; t < (kTY + 2) * (kTX + 2); t += kTX * kTY) {
+      const int dy = t / (kTX + 2), dx = t - dy * (kTX + 2);
+      const int xx = x0 + dx, yy = y0 + dy;
+      TA v = 0;
+      if (xx <= N && yy <= N && p >= 0 && p <= N) v = (TA)__ldg(x + ((size_t)p * n1 + yy) * n1 + xx);
+      dst[dy][dx] = v;
+    }
+  };
+  auto load_layer = [&](int l) {   // cell layer l (cells x0..x0+32, y0..y0+8)
+    const int s = l & 1;
+    int ch = l / op.layers;
+    ch = ch < op.nchunk ? ch : op.nchunk - 1;
+    const int rb = (l - ch * op.layers) * N;   // first x-row of layer l within its chunk
+    if (!CMP) {
+      if (tid == 0) {
+        sA[s] = reinterpret_cast<const TS*>(op.full[ch].a);
+        srow[s] = rb;
+      }
+      return;
+    }
+    const CmpChunk ck = op.cmp[ch];
+    for (int t = tid; t < (kTY + 1) * (kTX + 1); t += kTX * kTY) {
+      const int dy = t / (kTX + 1), dx = t - dy * (kTX + 1);
+      const int cx = x0 + dx, cy = y0 + dy;
+      TA ge = 0;
+      int cls = 0;
+      const uint8_t* rec = nullptr;
+      if (cx < N && cy < N) {
+        ge = (TA)__ldg(op.eps_c + ((size_t)l * N + cy) * N + cx) * (TA)(op.hfac * kref_off<3>(2));
+        const int seg = (rb + cy) * op.nseg_x + (cx >> 5);
+        cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
+        if (cls) rec = record_at<3>(ck, seg, cx & 31, cls);
+      }
+      sge[s][dy][dx] = ge;
+      scls[s][dy][dx] = (uint8_t)cls;
+      srec[s][dy][dx] = rec;
+    }
+  };
+
+  if (k0 <= k1) {
+    load_plane(k0 - 1);
+    load_plane(k0);
+    load_layer(k0 - 1);
+  }
+  for (int k = k0; k <= k1; ++k) {
+    load_plane(k + 1);
+    load_layer(k);
+    __syncthreads();
+    if (col_ok) {
+      TA u[27];
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy + 9 * dz] = su[(k - 1 + dz) % 3][ty + dy][tx + dx];
+      const TA u_a = u[13];
+      TA acc = 0, dgs = 0;
+#pragma unroll
+      for (int o = 0; o < NV; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+        const int s = (k - 1 + oz) & 1;
+        if (CMP) {
+          // geometric part: in 3D every nonzero off-diagonal of K_ref is -1/12
+          // (face and body diagonals), so the row is (-eps_c h / 12) times
+          // (sum of those 4 neighbours - 4 u_a); sge holds -eps_c h / 12
+          const TA gk = sge[s][ty + oy][tx + ox];
+          TA s4 = 0;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb) {
+            if (bb == a || popc_small(a ^ bb) < 2) continue;
+            const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
+            s4 += u[ub];
+          }
+          acc += gk * (s4 - (TA)4 * u_a);
+          dgs -= (TA)4 * gk;
+          const int cls = scls[s][ty + oy][tx + ox];
+          if (cls) {
+            const uint8_t* rec = srec[s][ty + oy][tx + ox];
+#pragma unroll
+            for (int bb = 0; bb < NV; ++bb) {
+              if (bb == a) continue;
+              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
+              const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
+              acc += dv * (u[ub] - u_a);
+              dgs -= dv;
+            }
+          }
+        } else {
+          const TS* A = sA[s];
+          const int cx = i - 1 + ox, cy = j - 1 + oy;
+          const int lc = (srow[s] + cy) * N + cx;
+          const size_t cc = (size_t)op.chunk_cells;
+          // row a: sum_b A_ab u_b - (sum_b A_ab) u_a, the row sum is minus the diagonal
+          TA t = 0, rs = 0;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb) {
+            if (bb == a) continue;
+            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * cc + lc);
+            const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
+            t += av * u[ub];
+            rs += av;
+          }
+          acc += t - rs * u_a;
+          dgs -= rs;
+        }
+      }
+      const size_t v = ((size_t)k * n1 + j) * n1 + i;
+      if (MODE == SW_JACOBI) {
+        y[v] = (TV)(u_a + omega * ((TA)b[v] - acc) / dgs);
+      } else if (MODE == SW_RESID) {
+        y[v] = (TV)((TA)b[v] - acc);
+      } else {
+        y[v] = (TV)acc;
+        d1 += (double)u_a * (double)acc;
+        d2 += (double)u_a * (double)b[v];
+      }
+    }
+    __syncthreads();
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (tid == 0) {
+      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      partials[2 * blk] = s1;
+      partials[2 * blk + 1] = s2;
+    }
+  }
+}
+
 template <int D, typename TV, typename TA, typename TS, bool CMP>
 cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const void* b, void* y, double omega,
                            double* partials, int* nblocks, cudaStream_t st) {
   const int ni = op.N - 1;
+  if (D == 3 && op.N >= 27) {
+    dim3 blk(kTX, kTY, 1);
+    dim3 grd((ni + kTX - 1) / kTX, (ni + kTY - 1) / kTY, (ni + kZC - 1) / kZC);
+    if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+    const TV* xv = (const TV*)x;
+    const TV* bv = (const TV*)b;
+    TV* yv = (TV*)y;
+    if (mode == SW_JACOBI)
+      sweep3_tiled<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else if (mode == SW_RESID)
+      sweep3_tiled<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else
+      sweep3_tiled<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    return launched();
+  }
   dim3 blk(kBX, kBY, 1);
   dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
@@ -201,16 +379,18 @@ __global__ void restrict_kernel(int Nc, const TV* __restrict__ rf, TV* __restric
     const int I = 1 + (int)(t % (Nc - 1));
     const int J = 1 + (int)((t / (Nc - 1)) % (Nc - 1));
     const int K = D == 3 ? 1 + (int)(t / ((long long)(Nc - 1) * (Nc - 1))) : 0;
-    double acc = 0.0;
-    const double w1[5] = {1.0 / 3.0, 2.0 / 3.0, 1.0, 2.0 / 3.0, 1.0 / 3.0};
-    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz)
-      for (int dy = -2; dy <= 2; ++dy) {
-        const long long rowbase = D == 3 ? ((long long)(3 * K + dz) * nf1 + (3 * J + dy)) * nf1
-                                         : (long long)(3 * J + dy) * nf1;
-        const double wyz = w1[dy + 2] * (D == 3 ? w1[dz + 2] : 1.0);
-        double racc = 0.0;
+    // arithmetic in the vectors' own precision (FP32 V-cycles stay off the FP64 pipe)
+    TV acc = 0;
+    const TV w1[5] = {(TV)(1.0 / 3.0), (TV)(2.0 / 3.0), (TV)1, (TV)(2.0 / 3.0), (TV)(1.0 / 3.0)};
 #pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) racc += w1[dx + 2] * (double)rf[rowbase + 3 * I + dx];
+    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz)
+#pragma unroll
+      for (int dy = -2; dy <= 2; ++dy) {
+        const int rowbase = D == 3 ? ((3 * K + dz) * nf1 + (3 * J + dy)) * nf1 : (3 * J + dy) * nf1;
+        const TV wyz = w1[dy + 2] * (D == 3 ? w1[dz + 2] : (TV)1);
+        TV racc = 0;
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) racc += w1[dx + 2] * __ldg(rf + rowbase + 3 * I + dx);
         acc += wyz * racc;
       }
     const long long vc = D == 3 ? ((long long)K * nc1 + J) * nc1 + I : (long long)J * nc1 + I;
@@ -221,38 +401,41 @@ __global__ void restrict_kernel(int Nc, const TV* __restrict__ rf, TV* __restric
 // e_f += P e_c (d-linear interpolation on the 3:1 refined grid)
 template <int D, typename TV>
 __global__ void prolong_kernel(int Nc, const TV* __restrict__ ec, TV* __restrict__ ef) {
+  // one thread per interior fine vertex: x from the block's x range, y from
+  // blockIdx.y/threadIdx.y, z from blockIdx.z (3D)
   const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
-  long long ni = 1;
-  for (int a = 0; a < D; ++a) ni *= (Nf - 1);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ni;
-       t += (long long)gridDim.x * blockDim.x) {
-    int f[3];
-    f[0] = 1 + (int)(t % (Nf - 1));
-    f[1] = 1 + (int)((t / (Nf - 1)) % (Nf - 1));
-    f[2] = D == 3 ? 1 + (int)(t / ((long long)(Nf - 1) * (Nf - 1))) : 0;
-    int c0[3], rr[3];
-    for (int a = 0; a < D; ++a) {
-      c0[a] = f[a] / 3;
-      rr[a] = f[a] - 3 * c0[a];
-    }
-    double acc = 0.0;
-    for (int corner = 0; corner < (1 << D); ++corner) {
-      double w = 1.0;
-      int cv[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) {
-        const int up = (corner >> a) & 1;
-        const double tt = rr[a] / 3.0;
-        w *= up ? tt : 1.0 - tt;
-        cv[a] = c0[a] + up;
-      }
-      if (w != 0.0) {
-        const long long vc = D == 3 ? ((long long)cv[2] * nc1 + cv[1]) * nc1 + cv[0] : (long long)cv[1] * nc1 + cv[0];
-        acc += w * (double)ec[vc];
-      }
-    }
-    const long long vf = D == 3 ? ((long long)f[2] * nf1 + f[1]) * nf1 + f[0] : (long long)f[1] * nf1 + f[0];
-    ef[vf] = (TV)((double)ef[vf] + acc);
+  int f[3];
+  f[0] = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  f[1] = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  f[2] = D == 3 ? 1 + blockIdx.z : 0;
+  if (f[0] >= Nf || f[1] >= Nf) return;
+  int c0[3] = {0, 0, 0};
+  TV w0[3] = {1, 1, 1}, w1[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    c0[a] = f[a] / 3;
+    const int r = f[a] - 3 * c0[a];
+    w1[a] = (TV)r * (TV)(1.0 / 3.0);
+    w0[a] = (TV)1 - w1[a];
   }
+  TV acc = 0;
+#pragma unroll
+  for (int corner = 0; corner < (1 << D); ++corner) {
+    TV w = 1;
+    int cv[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int up = (corner >> a) & 1;
+      w *= up ? w1[a] : w0[a];
+      cv[a] = c0[a] + up;
+    }
+    if (w != (TV)0) {
+      const int vc = D == 3 ? (cv[2] * nc1 + cv[1]) * nc1 + cv[0] : cv[1] * nc1 + cv[0];
+      acc += w * __ldg(ec + vc);
+    }
+  }
+  const size_t vf = D == 3 ? ((size_t)f[2] * nf1 + f[1]) * nf1 + f[0] : (size_t)f[1] * nf1 + f[0];
+  ef[vf] += acc;
 }
 
 int vgrid(long long n) {
@@ -394,15 +577,15 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
 }
 
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st) {
-  long long ni = 1;
-  for (int a = 0; a < dim; ++a) ni *= (3 * Nc - 1);
-  const int g = vgrid(ni);
+  const int nf = 3 * Nc - 1;
+  const dim3 blk(32, 8, 1);
+  const dim3 g((nf + 31) / 32, (nf + 7) / 8, dim == 3 ? nf : 1);
   if (dim == 2) {
-    if (vec64) prolong_kernel<2, double><<<g, 256, 0, st>>>(Nc, (const double*)ec, (double*)ef);
-    else prolong_kernel<2, float><<<g, 256, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+    if (vec64) prolong_kernel<2, double><<<g, blk, 0, st>>>(Nc, (const double*)ec, (double*)ef);
+    else prolong_kernel<2, float><<<g, blk, 0, st>>>(Nc, (const float*)ec, (float*)ef);
   } else {
-    if (vec64) prolong_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)ec, (double*)ef);
-    else prolong_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+    if (vec64) prolong_kernel<3, double><<<g, blk, 0, st>>>(Nc, (const double*)ec, (double*)ef);
+    else prolong_kernel<3, float><<<g, blk, 0, st>>>(Nc, (const float*)ec, (float*)ef);
   }
   return launched();
 }
