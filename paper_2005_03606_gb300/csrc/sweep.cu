@@ -333,6 +333,151 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_tiled(const LevelOp op, cons
   }
 }
 
+// ---------------------------------------------------------------- 3D register z-march
+// One thread per (x, y) vertex column walks kZC vertex planes along z.  The
+// 3 x 3 u neighbourhood of planes k-1 and k and the four cells of layer k-1
+// stay in registers from the previous plane, so each plane step loads only
+// the 9 u values of plane k+1 and the 4 cells of layer k (L1/L2 serve the
+// neighbouring columns).  A cell is kept as (-eps_c h / 12, record pointer
+// with the storage class in its low 2 bits; records are 16-byte aligned).
+template <typename TV, typename TA>
+__device__ __forceinline__ void load_plane9(const TV* __restrict__ x, size_t base, int n1, TA* u) {
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy] = (TA)__ldg(x + base + (size_t)(dy - 1) * n1 + (dx - 1));
+}
+
+template <typename TA>
+__device__ __forceinline__ void load_cells4(const LevelOp& op, int l, int i, int j, TA* g, uintptr_t* rc) {
+  const int N = op.N;
+  int ch = l / op.layers;
+  ch = ch < op.nchunk ? ch : op.nchunk - 1;
+  const int rb = (l - ch * op.layers) * N;
+  const CmpChunk& ck = op.cmp[ch];
+  const TA gscale = (TA)(op.hfac * kref_off<3>(2));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cx = i - 1 + (q & 1), cy = j - 1 + (q >> 1);
+    g[q] = (TA)__ldg(op.eps_c + ((size_t)l * N + cy) * N + cx) * gscale;
+    const int seg = (rb + cy) * op.nseg_x + (cx >> 5);
+    const int cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
+    rc[q] = cls ? (reinterpret_cast<uintptr_t>(record_at<3>(ck, seg, cx & 31, cls)) | (uintptr_t)cls) : 0;
+  }
+}
+
+template <typename TV, typename TA, typename TS, int MODE, bool CMP>
+__global__ void __launch_bounds__(kTX * kTY) sweep3_march(const LevelOp op, const TV* __restrict__ x,
+                                                          const TV* __restrict__ b, TV* __restrict__ y,
+                                                          TA omega, double* __restrict__ partials) {
+  constexpr int NV = 8;
+  __shared__ double sh[2][kTX * kTY / 32];
+  const int N = op.N, n1 = N + 1;
+  const int i = 1 + blockIdx.x * kTX + threadIdx.x;
+  const int j = 1 + blockIdx.y * kTY + threadIdx.y;
+  const int k0 = 1 + blockIdx.z * kZC;
+  const int k1 = min(N - 1, k0 + kZC - 1);
+  double d1 = 0.0, d2 = 0.0;
+  if (i < N && j < N && k0 <= k1) {
+    const size_t plane = (size_t)n1 * n1;
+    const size_t col = (size_t)j * n1 + i;
+    TA um[9], uc[9], up[9];       // planes k-1, k, k+1 around the column
+    TA gm[4], gc[4];              // cells of layers k-1, k
+    uintptr_t rm[4], rcur[4];
+    load_plane9<TV, TA>(x, (size_t)(k0 - 1) * plane + col, n1, um);
+    load_plane9<TV, TA>(x, (size_t)k0 * plane + col, n1, uc);
+    if (CMP) load_cells4<TA>(op, k0 - 1, i, j, gm, rm);
+    for (int k = k0; k <= k1; ++k) {
+      load_plane9<TV, TA>(x, (size_t)(k + 1) * plane + col, n1, up);
+      if (CMP) load_cells4<TA>(op, k, i, j, gc, rcur);
+      const size_t v = (size_t)k * plane + col;
+      const TV bv = MODE == SW_MATVEC ? TV(0) : b[v];
+      const TA u_a = uc[4];
+      TA acc = 0, dgs = 0;
+#pragma unroll
+      for (int o = 0; o < NV; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+        const int q = ox | (oy << 1);
+        // u of local vertex bb of this cell: plane (oz + bz) in {k-1, k, k+1}
+        auto U = [&](int bb) -> TA {
+          const int pz = oz + ((bb >> 2) & 1);
+          const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
+          return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
+        };
+        if (CMP) {
+          const TA gk = oz ? gc[q] : gm[q];
+          TA s4 = 0;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb)
+            if (bb != a && popc_small(a ^ bb) >= 2) s4 += U(bb);
+          acc += gk * (s4 - (TA)4 * u_a);
+          dgs -= (TA)4 * gk;
+          const uintptr_t rr = oz ? rcur[q] : rm[q];
+          if (rr) {
+            const int cls = (int)(rr & 3);
+            const uint8_t* rec = reinterpret_cast<const uint8_t*>(rr & ~(uintptr_t)3);
+#pragma unroll
+            for (int bb = 0; bb < NV; ++bb) {
+              if (bb == a) continue;
+              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
+              acc += dv * (U(bb) - u_a);
+              dgs -= dv;
+            }
+          }
+        } else {
+          const int l = k - 1 + oz;
+          int ch = l / op.layers;
+          ch = ch < op.nchunk ? ch : op.nchunk - 1;
+          const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
+          const int lc = ((l - ch * op.layers) * N + (j - 1 + oy)) * N + (i - 1 + ox);
+          const size_t cc = (size_t)op.chunk_cells;
+          TA t = 0, rs = 0;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb) {
+            if (bb == a) continue;
+            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * cc + lc);
+            t += av * U(bb);
+            rs += av;
+          }
+          acc += t - rs * u_a;
+          dgs -= rs;
+        }
+      }
+      if (MODE == SW_JACOBI) {
+        y[v] = (TV)(u_a + omega * ((TA)bv - acc) / dgs);
+      } else if (MODE == SW_RESID) {
+        y[v] = (TV)((TA)bv - acc);
+      } else {
+        y[v] = (TV)acc;
+        d1 += (double)u_a * (double)acc;
+        d2 += (double)u_a * (double)b[v];
+      }
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        um[t] = uc[t];
+        uc[t] = up[t];
+      }
+      if (CMP) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          gm[t] = gc[t];
+          rm[t] = rcur[t];
+        }
+      }
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      partials[2 * blk] = s1;
+      partials[2 * blk + 1] = s2;
+    }
+  }
+}
+
 template <int D, typename TV, typename TA, typename TS, bool CMP>
 cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const void* b, void* y, double omega,
                            double* partials, int* nblocks, cudaStream_t st) {
@@ -345,11 +490,11 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     const TV* bv = (const TV*)b;
     TV* yv = (TV*)y;
     if (mode == SW_JACOBI)
-      sweep3_tiled<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      sweep3_march<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     else if (mode == SW_RESID)
-      sweep3_tiled<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      sweep3_march<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     else
-      sweep3_tiled<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      sweep3_march<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     return launched();
   }
   dim3 blk(kBX, kBY, 1);
