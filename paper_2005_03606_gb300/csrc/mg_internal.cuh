@@ -100,6 +100,8 @@ struct LevelOp {
   const CmpChunk* cmp;    // device array [nchunk]
   const FullChunk* full;  // device array [nchunk]
   double hfac;            // h^(d-2)
+  float gk32;             // 3D: h * (-1/12), the nonzero off-diagonal of K_ref h^(d-2)
+  double gk64;
 };
 
 // ------------------------------------------------------------ helpers

@@ -705,6 +705,8 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     op.N = lv.N;
     op.dim = D;
     op.hfac = D == 3 ? h : 1.0;
+    op.gk64 = op.hfac * (-1.0 / 12.0);
+    op.gk32 = (float)op.gk64;
     op.nseg_x = (lv.N + kSegCells - 1) / kSegCells;
     cudaError_t e;
     if (l > 0) {

@@ -333,6 +333,234 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_tiled(const LevelOp op, cons
   }
 }
 
+// ---------------------------------------------------------------- 3D pipelined tile sweep
+// A CTA owns a 32 x 8 column of vertices and walks kZC vertex planes along z.
+// u planes (34 x 10 with halo), cell layers (33 x 9 cell-centre eps) and the
+// layers' class bytes are brought into shared-memory rings by asynchronous
+// copies (cp.async) issued two planes ahead, so global latency overlaps the
+// arithmetic of the current plane; one barrier per plane.  Ring depths (5
+// planes, 4 layers) make the slot being filled differ from every slot read in
+// the same or the previous plane (u values of planes k-1 and k and the
+// cells of layer k-1 are carried in registers from the previous plane).
+__device__ __forceinline__ void cp_async_bytes4(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes8(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes16(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* s, const T* g) {
+  if (sizeof(T) == 4) cp_async_bytes4(s, g);
+  else cp_async_bytes8(s, g);
+}
+
+constexpr int kPS = 4, kLS = 3;          // plane / layer ring depths
+constexpr int kUW = kTX + 2, kUH = kTY + 2;  // u tile with halo
+constexpr int kCW = kTX + 1, kCH = kTY + 1;  // cell tile
+
+template <typename TV, typename TA, typename TS, int MODE, bool CMP>
+__global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const TV* __restrict__ x,
+                                                         const TV* __restrict__ b, TV* __restrict__ y,
+                                                         TA omega, double* __restrict__ partials) {
+  constexpr int NV = 8;
+  __shared__ TV su[kPS][kUH][kUW];
+  __shared__ float sge[CMP ? kLS : 1][kCH][kCW];
+  __shared__ __align__(16) uint8_t scls[CMP ? kLS : 1][kCH][48];
+  __shared__ double sh[2][kTX * kTY / 32];
+  const int N = op.N, n1 = N + 1;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int i = x0 + tx + 1, j = y0 + ty + 1;
+  const bool col_ok = i < N && j < N;
+  const int k0 = 1 + blockIdx.z * kZC;
+  const int k1 = min(N - 1, k0 + kZC - 1);
+  const size_t plane = (size_t)n1 * n1;
+  double d1 = 0.0, d2 = 0.0;
+
+  // asynchronous fetch of u plane p into its ring slot
+  auto fetch_plane = [&](int p) {
+    TV(*dst)[kUW] = su[p % kPS];
+    for (int t = tid; t < kUH * kUW; t += kTX * kTY) {
+      const int dy = t / kUW, dx = t - dy * kUW;
+      const int xx = x0 + dx, yy = y0 + dy;
+      if (xx <= N && yy <= N) cp_async_elem<TV>(&dst[dy][dx], x + (size_t)p * plane + (size_t)yy * n1 + xx);
+      else dst[dy][dx] = TV(0);
+    }
+  };
+  // asynchronous fetch of cell layer l (eps_c and class bytes)
+  auto fetch_layer = [&](int l) {
+    if (!CMP) return;
+    const int s = l % kLS;
+    int ch = l / op.layers;
+    ch = ch < op.nchunk ? ch : op.nchunk - 1;
+    const int rb = (l - ch * op.layers) * N;
+    const uint8_t* cls = op.cmp[ch].cls;
+    for (int t = tid; t < kCH * kCW; t += kTX * kTY) {
+      const int dy = t / kCW, dx = t - dy * kCW;
+      const int cx = x0 + dx, cy = y0 + dy;
+      if (cx < N && cy < N) cp_async_bytes4(&sge[s][dy][dx], op.eps_c + ((size_t)l * N + cy) * N + cx);
+      else sge[s][dy][dx] = 0.f;
+    }
+    // class bytes: the 32-byte segment x0/32 of each row plus the first 16 bytes of the next one
+    if (tid < kCH * 3) {
+      const int dy = tid / 3, part = tid - dy * 3;
+      const int cy = y0 + dy;
+      const int sx = (x0 >> 5) + (part == 2 ? 1 : 0);
+      if (cy < N && sx < op.nseg_x)
+        cp_async_bytes16(&scls[s][dy][16 * part], cls + ((size_t)(rb + cy) * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0));
+      else
+        *reinterpret_cast<uint4*>(&scls[s][dy][16 * part]) = make_uint4(0, 0, 0, 0);
+    }
+  };
+
+  if (k0 <= k1) {
+    fetch_plane(k0 - 1);
+    fetch_plane(k0);
+    fetch_layer(k0 - 1);
+    cp_async_commit();
+    fetch_plane(k0 + 1);
+    fetch_layer(k0);
+    cp_async_commit();
+  }
+  TA um[9], uc[9], up[9];
+  float gm[4] = {0, 0, 0, 0};
+  int cm = 0;   // class bytes of the 4 cells of layer k-1 (packed)
+  bool first = true;
+  for (int k = k0; k <= k1; ++k) {
+    if (k + 2 <= N) fetch_plane(k + 2);
+    if (k + 1 <= N - 1) fetch_layer(k + 1);
+    cp_async_commit();
+    cp_async_wait1();   // everything but the group just issued has landed
+    __syncthreads();
+    if (col_ok) {
+      if (first) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          um[t] = (TA)su[(k - 1) % kPS][ty + t / 3][tx + t % 3];
+          uc[t] = (TA)su[k % kPS][ty + t / 3][tx + t % 3];
+        }
+        if (CMP) {
+          const int s = (k - 1) % kLS;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            gm[q] = sge[s][ty + (q >> 1)][tx + (q & 1)];
+            cm |= (int)scls[s][ty + (q >> 1)][tx + (q & 1)] << (8 * q);
+          }
+        }
+        first = false;
+      }
+#pragma unroll
+      for (int t = 0; t < 9; ++t) up[t] = (TA)su[(k + 1) % kPS][ty + t / 3][tx + t % 3];
+      float gc[4] = {0, 0, 0, 0};
+      int cc = 0;
+      if (CMP) {
+        const int s = k % kLS;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          gc[q] = sge[s][ty + (q >> 1)][tx + (q & 1)];
+          cc |= (int)scls[s][ty + (q >> 1)][tx + (q & 1)] << (8 * q);
+        }
+      }
+      const size_t v = (size_t)k * plane + (size_t)j * n1 + i;
+      const TA u_a = uc[4];
+      TA acc = 0, dgs = 0;
+      const TA gscale = (TA)(sizeof(TA) == 4 ? op.gk32 : op.gk64);
+#pragma unroll
+      for (int o = 0; o < NV; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+        const int q = ox | (oy << 1);
+        auto U = [&](int bb) -> TA {
+          const int pz = oz + ((bb >> 2) & 1);
+          const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
+          return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
+        };
+        if (CMP) {
+          const TA gk = (TA)(oz ? gc[q] : gm[q]) * gscale;
+          TA s4 = 0;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb)
+            if (bb != a && popc_small(a ^ bb) >= 2) s4 += U(bb);
+          acc += gk * (s4 - (TA)4 * u_a);
+          dgs -= (TA)4 * gk;
+          const int cls = ((oz ? cc : cm) >> (8 * q)) & 0xff;
+          if (cls) {
+            // record of this cell: rank among same-class cells of its segment
+            const int l = k - 1 + oz;
+            int ch = l / op.layers;
+            ch = ch < op.nchunk ? ch : op.nchunk - 1;
+            const CmpChunk& ck = op.cmp[ch];
+            const int cx = i - 1 + ox, cy = j - 1 + oy;
+            const int seg = ((l - ch * op.layers) * N + cy) * op.nseg_x + (cx >> 5);
+            const uint8_t* rec = record_at<3>(ck, seg, cx & 31, cls);
+#pragma unroll
+            for (int bb = 0; bb < NV; ++bb) {
+              if (bb == a) continue;
+              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
+              acc += dv * (U(bb) - u_a);
+              dgs -= dv;
+            }
+          }
+        } else {
+          const int l = k - 1 + oz;
+          int ch = l / op.layers;
+          ch = ch < op.nchunk ? ch : op.nchunk - 1;
+          const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
+          const int lc = ((l - ch * op.layers) * N + (j - 1 + oy)) * N + (i - 1 + ox);
+          const size_t ccs = (size_t)op.chunk_cells;
+          TA t = 0, rs = 0;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb) {
+            if (bb == a) continue;
+            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * ccs + lc);
+            t += av * U(bb);
+            rs += av;
+          }
+          acc += t - rs * u_a;
+          dgs -= rs;
+        }
+      }
+      if (MODE == SW_JACOBI) {
+        y[v] = (TV)(u_a + omega * ((TA)b[v] - acc) / dgs);
+      } else if (MODE == SW_RESID) {
+        y[v] = (TV)((TA)b[v] - acc);
+      } else {
+        y[v] = (TV)acc;
+        d1 += (double)u_a * (double)acc;
+        d2 += (double)u_a * (double)b[v];
+      }
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        um[t] = uc[t];
+        uc[t] = up[t];
+      }
+      if (CMP) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gm[q] = gc[q];
+        cm = cc;
+      }
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (tid == 0) {
+      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      partials[2 * blk] = s1;
+      partials[2 * blk + 1] = s2;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- 3D register z-march
 // One thread per (x, y) vertex column walks kZC vertex planes along z.  The
 // 3 x 3 u neighbourhood of planes k-1 and k and the four cells of layer k-1
@@ -490,11 +718,11 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     const TV* bv = (const TV*)b;
     TV* yv = (TV*)y;
     if (mode == SW_JACOBI)
-      sweep3_march<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      sweep3_pipe<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     else if (mode == SW_RESID)
-      sweep3_march<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      sweep3_pipe<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     else
-      sweep3_march<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      sweep3_pipe<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     return launched();
   }
   dim3 blk(kBX, kBY, 1);
