@@ -677,6 +677,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   P->tv = P->mixed ? 4 : 8;
   fill_eps(d.eps, d.dim, &P->eps);
   if (cudaGetDevice(&P->device) != cudaSuccess) P->device = 0;
+  if (const char* ng = getenv("MG_NO_GRAPHS")) P->use_graphs = ng[0] == '0';
   auto fail = [&](mg_status s) {
     mg_destroy_problem(P);
     return s;

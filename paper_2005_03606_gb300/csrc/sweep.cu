@@ -363,7 +363,12 @@ __device__ __forceinline__ void cp_async_elem(T* s, const T* g) {
   else cp_async_bytes8(s, g);
 }
 
-constexpr int kPS = 4, kLS = 3;          // plane / layer ring depths
+// Ring depths: plane p is filled at step p-2 and read at step p-1 (and, at the
+// first step k0, planes k0-1..k0+1 and layers k0-1..k0 are read).  The slot
+// filled at step k must not be read at step k-1 (no barrier separates them):
+// with 5 plane slots and 4 layer slots the first step's slots are refilled
+// only after the barrier of step k0+1.
+constexpr int kPS = 5, kLS = 4;
 constexpr int kUW = kTX + 2, kUH = kTY + 2;  // u tile with halo
 constexpr int kCW = kTX + 1, kCH = kTY + 1;  // cell tile
 
