@@ -12,6 +12,8 @@
 // eps, the surplus only for cells of storage class > 0.
 #include "mg_internal.cuh"
 
+#include <mutex>
+
 namespace mg {
 
 namespace {
@@ -29,9 +31,10 @@ __device__ __forceinline__ const uint8_t* record_at(const CmpChunk& ck, int seg,
   return ck.pool[cls - 1] + (size_t)(base + r) * recb;
 }
 
-// (A u)_v and diag_v at interior vertex (i, j, k) from the 3^d neighbourhood u.
-// All index arithmetic is 32-bit and done per cell layer (the layer along the
-// last axis fixes the chunk); 64-bit products appear only in byte offsets.
+// (A u)_v and diag_v at interior vertex (i, j, k) from the 3^d neighbourhood u
+// (vertex-per-thread form, used for 2D and for small 3D levels).  All index
+// arithmetic is 32-bit and done per cell layer (the layer along the last axis
+// fixes the chunk).
 template <int D, typename TA, bool CMP, typename TS>
 __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, int k, const TA* u,
                                              TA* Au, TA* dg) {
@@ -40,16 +43,14 @@ __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, in
   TA acc = 0, dgs = 0;
 #pragma unroll
   for (int ol = 0; ol < 2; ++ol) {
-    // cell layer along the last axis and its chunk
     const int cl = (D == 3 ? k : j) - 1 + ol;
     int ch = cl / op.layers;
     ch = ch < op.nchunk ? ch : op.nchunk - 1;
     const int ll = cl - ch * op.layers;  // layer within the chunk
 #pragma unroll
     for (int om = 0; om < (D == 3 ? 2 : 1); ++om) {
-      // for D = 3: om selects the y row; for D = 2 the row is the layer itself
       const int cy = D == 3 ? j - 1 + om : cl;
-      const int row = D == 3 ? ll * N + cy : ll;      // x-row within the chunk
+      const int row = D == 3 ? ll * N + cy : ll;              // x-row within the chunk
       const int cbase = D == 3 ? (cl * N + cy) * N : cl * N;  // global cell index of x = 0
       const int segrow = row * op.nseg_x;
 #pragma unroll
@@ -57,11 +58,9 @@ __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, in
         const int cx = i - 1 + ox;
         const int oy = D == 3 ? om : ol, oz = D == 3 ? ol : 0;
         const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
-        // neighbourhood index of local vertex b of this cell: offset (o - 1 + bits(b))
-        const int ua = 1 + 3 + (D == 3 ? 9 : 0);
-        const TA u_a = u[ua];
+        const TA u_a = u[D == 3 ? 13 : 4];
         if (CMP) {
-          const TA ge = (TA)__ldg(op.eps_c + cbase + cx) * (TA)op.hfac;
+          const TA ge = (TA)__ldg(op.eps_c + cbase + cx) * (TA)(sizeof(TA) == 4 ? (double)(float)op.hfac : op.hfac);
 #pragma unroll
           for (int b = 0; b < NV; ++b) {
             if (b == a) continue;
@@ -89,14 +88,17 @@ __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, in
           const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
           const size_t cc = (size_t)op.chunk_cells;
           const int lc = row * N + cx;
+          TA t = 0, rs = 0;
 #pragma unroll
           for (int b = 0; b < NV; ++b) {
             if (b == a) continue;
             const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, b) * cc + lc);
             const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
-            acc += av * (u[ub] - u_a);
-            dgs -= av;
+            t += av * u[ub];
+            rs += av;
           }
+          acc += t - rs * u_a;
+          dgs -= rs;
         }
       }
     }
@@ -119,7 +121,7 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;
 }
 
-// One sweep over the interior vertices of one level.
+// One sweep over the interior vertices of one level, one vertex per thread.
 //  SW_JACOBI: y = x + omega (b - A x) / diag
 //  SW_RESID : y = b - A x
 //  SW_MATVEC: y = A x; partials += (x.y, x.b) per block
@@ -170,187 +172,25 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
   }
 }
 
-// ---------------------------------------------------------------- 3D tiled sweep
-// A CTA owns a 32 x 8 column of vertices and marches along z over kZC vertex
-// planes.  u planes (with a one-vertex halo) and cell layers (cell-centre
-// eps times h, storage class, record pointer) pass through shared-memory
-// rings, so each value is fetched from global memory once per CTA instead of
-// once per vertex that touches it.
-constexpr int kTX = 32, kTY = 8, kZC = 32;
-
-template <typename TV, typename TA, typename TS, int MODE, bool CMP>
-__global__ void __launch_bounds__(kTX * kTY) sweep3_tiled(const LevelOp op, const TV* __restrict__ x,
-                                                          const TV* __restrict__ b, TV* __restrict__ y,
-                                                          TA omega, double* __restrict__ partials) {
-  constexpr int NV = 8;
-  __shared__ TA su[3][kTY + 2][kTX + 2];
-  __shared__ TA sge[2][kTY + 1][kTX + 1];
-  __shared__ const uint8_t* srec[2][kTY + 1][kTX + 1];
-  __shared__ uint8_t scls[2][kTY + 1][kTX + 1];
-  __shared__ const TS* sA[2];
-  __shared__ int srow[2];
-  __shared__ double sh[2][kTX * kTY / 32];
-  const int N = op.N, n1 = N + 1;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;  // vertex x0 + tx + 1 is this thread's column
-  const int i = x0 + tx + 1, j = y0 + ty + 1;
-  const bool col_ok = i < N && j < N;
-  const int k0 = 1 + blockIdx.z * kZC;
-  const int k1 = min(N - 1, k0 + kZC - 1);
-  double d1 = 0.0, d2 = 0.0;
-
-  auto load_plane = [&](int p) {   // u plane p (vertices x0..x0+33, y0..y0+9)
-    TA(*dst)[kTX + 2] = su[p % 3];
-    for (int t = tid; t < (kTY + 2) * (kTX + 2); t += kTX * kTY) {
-      const int dy = t / (kTX + 2), dx = t - dy * (kTX + 2);
-      const int xx = x0 + dx, yy = y0 + dy;
-      TA v = 0;
-      if (xx <= N && yy <= N && p >= 0 && p <= N) v = (TA)__ldg(x + ((size_t)p * n1 + yy) * n1 + xx);
-      dst[dy][dx] = v;
-    }
-  };
-  auto load_layer = [&](int l) {   // cell layer l (cells x0..x0+32, y0..y0+8)
-    const int s = l & 1;
-    int ch = l / op.layers;
-    ch = ch < op.nchunk ? ch : op.nchunk - 1;
-    const int rb = (l - ch * op.layers) * N;   // first x-row of layer l within its chunk
-    if (!CMP) {
-      if (tid == 0) {
-        sA[s] = reinterpret_cast<const TS*>(op.full[ch].a);
-        srow[s] = rb;
-      }
-      return;
-    }
-    const CmpChunk ck = op.cmp[ch];
-    for (int t = tid; t < (kTY + 1) * (kTX + 1); t += kTX * kTY) {
-      const int dy = t / (kTX + 1), dx = t - dy * (kTX + 1);
-      const int cx = x0 + dx, cy = y0 + dy;
-      TA ge = 0;
-      int cls = 0;
-      const uint8_t* rec = nullptr;
-      if (cx < N && cy < N) {
-        ge = (TA)__ldg(op.eps_c + ((size_t)l * N + cy) * N + cx) * (TA)(op.hfac * kref_off<3>(2));
-        const int seg = (rb + cy) * op.nseg_x + (cx >> 5);
-        cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
-        if (cls) rec = record_at<3>(ck, seg, cx & 31, cls);
-      }
-      sge[s][dy][dx] = ge;
-      scls[s][dy][dx] = (uint8_t)cls;
-      srec[s][dy][dx] = rec;
-    }
-  };
-
-  if (k0 <= k1) {
-    load_plane(k0 - 1);
-    load_plane(k0);
-    load_layer(k0 - 1);
-  }
-  for (int k = k0; k <= k1; ++k) {
-    load_plane(k + 1);
-    load_layer(k);
-    __syncthreads();
-    if (col_ok) {
-      TA u[27];
-#pragma unroll
-      for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy + 9 * dz] = su[(k - 1 + dz) % 3][ty + dy][tx + dx];
-      const TA u_a = u[13];
-      TA acc = 0, dgs = 0;
-#pragma unroll
-      for (int o = 0; o < NV; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-        const int s = (k - 1 + oz) & 1;
-        if (CMP) {
-          // geometric part: in 3D every nonzero off-diagonal of K_ref is -1/12
-          // (face and body diagonals), so the row is (-eps_c h / 12) times
-          // (sum of those 4 neighbours - 4 u_a); sge holds -eps_c h / 12
-          const TA gk = sge[s][ty + oy][tx + ox];
-          TA s4 = 0;
-#pragma unroll
-          for (int bb = 0; bb < NV; ++bb) {
-            if (bb == a || popc_small(a ^ bb) < 2) continue;
-            const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
-            s4 += u[ub];
-          }
-          acc += gk * (s4 - (TA)4 * u_a);
-          dgs -= (TA)4 * gk;
-          const int cls = scls[s][ty + oy][tx + ox];
-          if (cls) {
-            const uint8_t* rec = srec[s][ty + oy][tx + ox];
-#pragma unroll
-            for (int bb = 0; bb < NV; ++bb) {
-              if (bb == a) continue;
-              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
-              const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
-              acc += dv * (u[ub] - u_a);
-              dgs -= dv;
-            }
-          }
-        } else {
-          const TS* A = sA[s];
-          const int cx = i - 1 + ox, cy = j - 1 + oy;
-          const int lc = (srow[s] + cy) * N + cx;
-          const size_t cc = (size_t)op.chunk_cells;
-          // row a: sum_b A_ab u_b - (sum_b A_ab) u_a, the row sum is minus the diagonal
-          TA t = 0, rs = 0;
-#pragma unroll
-          for (int bb = 0; bb < NV; ++bb) {
-            if (bb == a) continue;
-            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * cc + lc);
-            const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
-            t += av * u[ub];
-            rs += av;
-          }
-          acc += t - rs * u_a;
-          dgs -= rs;
-        }
-      }
-      const size_t v = ((size_t)k * n1 + j) * n1 + i;
-      if (MODE == SW_JACOBI) {
-        y[v] = (TV)(u_a + omega * ((TA)b[v] - acc) / dgs);
-      } else if (MODE == SW_RESID) {
-        y[v] = (TV)((TA)b[v] - acc);
-      } else {
-        y[v] = (TV)acc;
-        d1 += (double)u_a * (double)acc;
-        d2 += (double)u_a * (double)b[v];
-      }
-    }
-    __syncthreads();
-  }
-  if (MODE == SW_MATVEC) {
-    const double s1 = block_sum(d1, sh[0]);
-    const double s2 = block_sum(d2, sh[1]);
-    if (tid == 0) {
-      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-      partials[2 * blk] = s1;
-      partials[2 * blk + 1] = s2;
-    }
-  }
-}
-
 // ---------------------------------------------------------------- 3D pipelined tile sweep
 // A CTA owns a 32 x 8 column of vertices and walks kZC vertex planes along z.
 // u planes (34 x 10 with halo), cell layers (33 x 9 cell-centre eps) and the
 // layers' class bytes are brought into shared-memory rings by asynchronous
 // copies (cp.async) issued two planes ahead, so global latency overlaps the
-// arithmetic of the current plane; one barrier per plane.  Ring depths (5
-// planes, 4 layers) make the slot being filled differ from every slot read in
-// the same or the previous plane (u values of planes k-1 and k and the
-// cells of layer k-1 are carried in registers from the previous plane).
-__device__ __forceinline__ void cp_async_bytes4(void* s, const void* g) {
+// arithmetic of the current plane.  The surplus records of the cells of a
+// layer with storage class > 0 are located once per CTA (rank from the class
+// bytes already in shared memory) and decoded into a shared-memory ring, so
+// a vertex reads its 7 row entries from shared memory.  u of planes k-1 and k
+// are carried in registers from the previous plane.
+__device__ __forceinline__ void cp_async4(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
 }
-__device__ __forceinline__ void cp_async_bytes8(void* s, const void* g) {
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
 }
-__device__ __forceinline__ void cp_async_bytes16(void* s, const void* g) {
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
 }
@@ -359,18 +199,39 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* s, const T* g) {
-  if (sizeof(T) == 4) cp_async_bytes4(s, g);
-  else cp_async_bytes8(s, g);
+  if (sizeof(T) == 4) cp_async4(s, g);
+  else cp_async8(s, g);
 }
 
-// Ring depths: plane p is filled at step p-2 and read at step p-1 (and, at the
-// first step k0, planes k0-1..k0+1 and layers k0-1..k0 are read).  The slot
-// filled at step k must not be read at step k-1 (no barrier separates them):
-// with 5 plane slots and 4 layer slots the first step's slots are refilled
-// only after the barrier of step k0+1.
-constexpr int kPS = 5, kLS = 4;
-constexpr int kUW = kTX + 2, kUH = kTY + 2;  // u tile with halo
-constexpr int kCW = kTX + 1, kCH = kTY + 1;  // cell tile
+constexpr int kTX = 32, kTY = 8, kZC = 32;
+constexpr int kUW = kTX + 2, kUH = kTY + 2;   // u tile with halo
+constexpr int kCW = kTX + 1, kCH = kTY + 1;   // cell tile
+constexpr int kCells = kCW * kCH;
+constexpr int kDelPitch = 29;                 // floats per decoded cell (28 + 1: odd stride)
+// Ring depths.  Plane p is filled at step p-2 and read at step p-1; layer l is
+// filled at step l-1 and read at steps l and l+1; decoded layer l is written
+// at step l and read at steps l, l+1; the first step k0 also reads planes
+// k0-1..k0+1 and layers k0-1..k0.  The slot filled at step k is never one
+// read at step k-1 (no barrier separates the two).
+constexpr int kPS = 5, kLS = 4, kDS = 2;
+constexpr size_t kDelBytes = sizeof(float) * kDS * kCells * kDelPitch;
+
+// rank of byte `lane` among the bytes equal to k in a 16-byte-aligned row of 32 bytes (shared memory)
+__device__ __forceinline__ int rank_in_row(const uint8_t* row, int lane, int k) {
+  const unsigned kk = 0x01010101u * (unsigned)k;
+  const unsigned* w = reinterpret_cast<const unsigned*>(row);
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int lo = 4 * q;
+    if (lo >= lane) break;
+    unsigned eq = __vcmpeq4(w[q], kk);
+    const int nb = lane - lo;   // bytes of this word before `lane`
+    if (nb < 4) eq &= 0xffffffffu >> (8 * (4 - nb));
+    cnt += __popc(eq);
+  }
+  return cnt >> 3;
+}
 
 template <typename TV, typename TA, typename TS, int MODE, bool CMP>
 __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const TV* __restrict__ x,
@@ -381,6 +242,7 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
   __shared__ float sge[CMP ? kLS : 1][kCH][kCW];
   __shared__ __align__(16) uint8_t scls[CMP ? kLS : 1][kCH][48];
   __shared__ double sh[2][kTX * kTY / 32];
+  extern __shared__ float sdel[];   // [kDS][kCells][kDelPitch] (CMP only)
   const int N = op.N, n1 = N + 1;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -401,7 +263,8 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
       else dst[dy][dx] = TV(0);
     }
   };
-  // asynchronous fetch of cell layer l (eps_c and class bytes)
+  // asynchronous fetch of cell layer l: eps_c and the class bytes (the 32-byte
+  // segment x0/32 of each row plus the first 16 bytes of the next segment)
   auto fetch_layer = [&](int l) {
     if (!CMP) return;
     const int s = l % kLS;
@@ -409,21 +272,57 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
     ch = ch < op.nchunk ? ch : op.nchunk - 1;
     const int rb = (l - ch * op.layers) * N;
     const uint8_t* cls = op.cmp[ch].cls;
-    for (int t = tid; t < kCH * kCW; t += kTX * kTY) {
+    for (int t = tid; t < kCells; t += kTX * kTY) {
       const int dy = t / kCW, dx = t - dy * kCW;
       const int cx = x0 + dx, cy = y0 + dy;
-      if (cx < N && cy < N) cp_async_bytes4(&sge[s][dy][dx], op.eps_c + ((size_t)l * N + cy) * N + cx);
+      if (cx < N && cy < N) cp_async4(&sge[s][dy][dx], op.eps_c + ((size_t)l * N + cy) * N + cx);
       else sge[s][dy][dx] = 0.f;
     }
-    // class bytes: the 32-byte segment x0/32 of each row plus the first 16 bytes of the next one
     if (tid < kCH * 3) {
       const int dy = tid / 3, part = tid - dy * 3;
       const int cy = y0 + dy;
       const int sx = (x0 >> 5) + (part == 2 ? 1 : 0);
       if (cy < N && sx < op.nseg_x)
-        cp_async_bytes16(&scls[s][dy][16 * part], cls + ((size_t)(rb + cy) * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0));
+        cp_async16(&scls[s][dy][16 * part],
+                   cls + ((size_t)(rb + cy) * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0));
       else
-        *reinterpret_cast<uint4*>(&scls[s][dy][16 * part]) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(&scls[s][dy][16 * part]) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  // decode the surplus records of layer l (classes already in shared memory)
+  auto decode_layer = [&](int l) {
+    if (!CMP) return;
+    const int s = l % kLS;
+    float* dl = sdel + (size_t)(l % kDS) * kCells * kDelPitch;
+    int ch = l / op.layers;
+    ch = ch < op.nchunk ? ch : op.nchunk - 1;
+    const int rb = (l - ch * op.layers) * N;
+    const CmpChunk& ck = op.cmp[ch];
+    for (int t = tid; t < kCells; t += kTX * kTY) {
+      const int dy = t / kCW, dx = t - dy * kCW;
+      const int cls = scls[s][dy][dx];
+      if (!cls) continue;
+      const int cx = x0 + dx, cy = y0 + dy;
+      const int seg = (rb + cy) * op.nseg_x + (cx >> 5);
+      const int r = dx < kTX ? rank_in_row(&scls[s][dy][0], dx, cls) : 0;
+      const unsigned base = __ldg(ck.seg_base + (size_t)(cls - 1) * ck.nseg + seg);
+      const int recb = cls == 1 ? Dim<3>::REC1 : (cls == 2 ? Dim<3>::REC2 : Dim<3>::REC3);
+      const uint8_t* rec = ck.pool[cls - 1] + (size_t)(base + r) * recb;
+      float* o = dl + (size_t)t * kDelPitch;
+      if (cls == 3) {
+        const float4* r4 = reinterpret_cast<const float4*>(rec);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+          const float4 v = __ldg(r4 + q);
+          o[4 * q] = v.x;
+          o[4 * q + 1] = v.y;
+          o[4 * q + 2] = v.z;
+          o[4 * q + 3] = v.w;
+        }
+      } else {
+#pragma unroll 4
+        for (int p = 0; p < 28; ++p) o[p] = decode_entry<3>(rec, cls, p);
+      }
     }
   };
 
@@ -437,91 +336,69 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
     cp_async_commit();
   }
   TA um[9], uc[9], up[9];
-  float gm[4] = {0, 0, 0, 0};
-  int cm = 0;   // class bytes of the 4 cells of layer k-1 (packed)
-  bool first = true;
+  const TA gscale = (TA)(sizeof(TA) == 4 ? (double)op.gk32 : op.gk64);
   for (int k = k0; k <= k1; ++k) {
     if (k + 2 <= N) fetch_plane(k + 2);
     if (k + 1 <= N - 1) fetch_layer(k + 1);
     cp_async_commit();
-    cp_async_wait1();   // everything but the group just issued has landed
+    cp_async_wait1();   // all groups but the one just issued have landed
     __syncthreads();
+    if (CMP) {
+      if (k == k0) decode_layer(k0 - 1);
+      decode_layer(k);
+      __syncthreads();
+    }
     if (col_ok) {
-      if (first) {
+      if (k == k0) {
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
           um[t] = (TA)su[(k - 1) % kPS][ty + t / 3][tx + t % 3];
           uc[t] = (TA)su[k % kPS][ty + t / 3][tx + t % 3];
         }
-        if (CMP) {
-          const int s = (k - 1) % kLS;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            gm[q] = sge[s][ty + (q >> 1)][tx + (q & 1)];
-            cm |= (int)scls[s][ty + (q >> 1)][tx + (q & 1)] << (8 * q);
-          }
-        }
-        first = false;
       }
 #pragma unroll
       for (int t = 0; t < 9; ++t) up[t] = (TA)su[(k + 1) % kPS][ty + t / 3][tx + t % 3];
-      float gc[4] = {0, 0, 0, 0};
-      int cc = 0;
-      if (CMP) {
-        const int s = k % kLS;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          gc[q] = sge[s][ty + (q >> 1)][tx + (q & 1)];
-          cc |= (int)scls[s][ty + (q >> 1)][tx + (q & 1)] << (8 * q);
-        }
-      }
       const size_t v = (size_t)k * plane + (size_t)j * n1 + i;
       const TA u_a = uc[4];
       TA acc = 0, dgs = 0;
-      const TA gscale = (TA)(sizeof(TA) == 4 ? op.gk32 : op.gk64);
 #pragma unroll
       for (int o = 0; o < NV; ++o) {
         const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
         const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-        const int q = ox | (oy << 1);
         auto U = [&](int bb) -> TA {
           const int pz = oz + ((bb >> 2) & 1);
           const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
           return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
         };
+        const int l = k - 1 + oz;
         if (CMP) {
-          const TA gk = (TA)(oz ? gc[q] : gm[q]) * gscale;
+          // geometric part: in 3D every nonzero off-diagonal of K_ref is -1/12
+          // (face and body diagonals): the row is (-eps_c h / 12) times
+          // (sum of those 4 neighbours - 4 u_a)
+          const TA gk = (TA)sge[l % kLS][ty + oy][tx + ox] * gscale;
           TA s4 = 0;
 #pragma unroll
           for (int bb = 0; bb < NV; ++bb)
             if (bb != a && popc_small(a ^ bb) >= 2) s4 += U(bb);
           acc += gk * (s4 - (TA)4 * u_a);
           dgs -= (TA)4 * gk;
-          const int cls = ((oz ? cc : cm) >> (8 * q)) & 0xff;
-          if (cls) {
-            // record of this cell: rank among same-class cells of its segment
-            const int l = k - 1 + oz;
-            int ch = l / op.layers;
-            ch = ch < op.nchunk ? ch : op.nchunk - 1;
-            const CmpChunk& ck = op.cmp[ch];
-            const int cx = i - 1 + ox, cy = j - 1 + oy;
-            const int seg = ((l - ch * op.layers) * N + cy) * op.nseg_x + (cx >> 5);
-            const uint8_t* rec = record_at<3>(ck, seg, cx & 31, cls);
+          if (scls[l % kLS][ty + oy][tx + ox]) {
+            const float* dp = sdel + ((size_t)(l % kDS) * kCells + (ty + oy) * kCW + tx + ox) * kDelPitch;
 #pragma unroll
             for (int bb = 0; bb < NV; ++bb) {
               if (bb == a) continue;
-              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
+              const TA dv = (TA)dp[pair_of(NV, a, bb)];
               acc += dv * (U(bb) - u_a);
               dgs -= dv;
             }
           }
         } else {
-          const int l = k - 1 + oz;
           int ch = l / op.layers;
           ch = ch < op.nchunk ? ch : op.nchunk - 1;
           const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
           const int lc = ((l - ch * op.layers) * N + (j - 1 + oy)) * N + (i - 1 + ox);
           const size_t ccs = (size_t)op.chunk_cells;
+          // row a: sum_b A_ab u_b - (sum_b A_ab) u_a, the row sum is minus the diagonal
           TA t = 0, rs = 0;
 #pragma unroll
           for (int bb = 0; bb < NV; ++bb) {
@@ -548,11 +425,6 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
         um[t] = uc[t];
         uc[t] = up[t];
       }
-      if (CMP) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gm[q] = gc[q];
-        cm = cc;
-      }
     }
   }
   if (MODE == SW_MATVEC) {
@@ -566,176 +438,39 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
   }
 }
 
-// ---------------------------------------------------------------- 3D register z-march
-// One thread per (x, y) vertex column walks kZC vertex planes along z.  The
-// 3 x 3 u neighbourhood of planes k-1 and k and the four cells of layer k-1
-// stay in registers from the previous plane, so each plane step loads only
-// the 9 u values of plane k+1 and the 4 cells of layer k (L1/L2 serve the
-// neighbouring columns).  A cell is kept as (-eps_c h / 12, record pointer
-// with the storage class in its low 2 bits; records are 16-byte aligned).
-template <typename TV, typename TA>
-__device__ __forceinline__ void load_plane9(const TV* __restrict__ x, size_t base, int n1, TA* u) {
-#pragma unroll
-  for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy] = (TA)__ldg(x + base + (size_t)(dy - 1) * n1 + (dx - 1));
-}
-
-template <typename TA>
-__device__ __forceinline__ void load_cells4(const LevelOp& op, int l, int i, int j, TA* g, uintptr_t* rc) {
-  const int N = op.N;
-  int ch = l / op.layers;
-  ch = ch < op.nchunk ? ch : op.nchunk - 1;
-  const int rb = (l - ch * op.layers) * N;
-  const CmpChunk& ck = op.cmp[ch];
-  const TA gscale = (TA)(op.hfac * kref_off<3>(2));
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int cx = i - 1 + (q & 1), cy = j - 1 + (q >> 1);
-    g[q] = (TA)__ldg(op.eps_c + ((size_t)l * N + cy) * N + cx) * gscale;
-    const int seg = (rb + cy) * op.nseg_x + (cx >> 5);
-    const int cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
-    rc[q] = cls ? (reinterpret_cast<uintptr_t>(record_at<3>(ck, seg, cx & 31, cls)) | (uintptr_t)cls) : 0;
-  }
-}
-
 template <typename TV, typename TA, typename TS, int MODE, bool CMP>
-__global__ void __launch_bounds__(kTX * kTY) sweep3_march(const LevelOp op, const TV* __restrict__ x,
-                                                          const TV* __restrict__ b, TV* __restrict__ y,
-                                                          TA omega, double* __restrict__ partials) {
-  constexpr int NV = 8;
-  __shared__ double sh[2][kTX * kTY / 32];
-  const int N = op.N, n1 = N + 1;
-  const int i = 1 + blockIdx.x * kTX + threadIdx.x;
-  const int j = 1 + blockIdx.y * kTY + threadIdx.y;
-  const int k0 = 1 + blockIdx.z * kZC;
-  const int k1 = min(N - 1, k0 + kZC - 1);
-  double d1 = 0.0, d2 = 0.0;
-  if (i < N && j < N && k0 <= k1) {
-    const size_t plane = (size_t)n1 * n1;
-    const size_t col = (size_t)j * n1 + i;
-    TA um[9], uc[9], up[9];       // planes k-1, k, k+1 around the column
-    TA gm[4], gc[4];              // cells of layers k-1, k
-    uintptr_t rm[4], rcur[4];
-    load_plane9<TV, TA>(x, (size_t)(k0 - 1) * plane + col, n1, um);
-    load_plane9<TV, TA>(x, (size_t)k0 * plane + col, n1, uc);
-    if (CMP) load_cells4<TA>(op, k0 - 1, i, j, gm, rm);
-    for (int k = k0; k <= k1; ++k) {
-      load_plane9<TV, TA>(x, (size_t)(k + 1) * plane + col, n1, up);
-      if (CMP) load_cells4<TA>(op, k, i, j, gc, rcur);
-      const size_t v = (size_t)k * plane + col;
-      const TV bv = MODE == SW_MATVEC ? TV(0) : b[v];
-      const TA u_a = uc[4];
-      TA acc = 0, dgs = 0;
-#pragma unroll
-      for (int o = 0; o < NV; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-        const int q = ox | (oy << 1);
-        // u of local vertex bb of this cell: plane (oz + bz) in {k-1, k, k+1}
-        auto U = [&](int bb) -> TA {
-          const int pz = oz + ((bb >> 2) & 1);
-          const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
-          return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
-        };
-        if (CMP) {
-          const TA gk = oz ? gc[q] : gm[q];
-          TA s4 = 0;
-#pragma unroll
-          for (int bb = 0; bb < NV; ++bb)
-            if (bb != a && popc_small(a ^ bb) >= 2) s4 += U(bb);
-          acc += gk * (s4 - (TA)4 * u_a);
-          dgs -= (TA)4 * gk;
-          const uintptr_t rr = oz ? rcur[q] : rm[q];
-          if (rr) {
-            const int cls = (int)(rr & 3);
-            const uint8_t* rec = reinterpret_cast<const uint8_t*>(rr & ~(uintptr_t)3);
-#pragma unroll
-            for (int bb = 0; bb < NV; ++bb) {
-              if (bb == a) continue;
-              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
-              acc += dv * (U(bb) - u_a);
-              dgs -= dv;
-            }
-          }
-        } else {
-          const int l = k - 1 + oz;
-          int ch = l / op.layers;
-          ch = ch < op.nchunk ? ch : op.nchunk - 1;
-          const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
-          const int lc = ((l - ch * op.layers) * N + (j - 1 + oy)) * N + (i - 1 + ox);
-          const size_t cc = (size_t)op.chunk_cells;
-          TA t = 0, rs = 0;
-#pragma unroll
-          for (int bb = 0; bb < NV; ++bb) {
-            if (bb == a) continue;
-            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * cc + lc);
-            t += av * U(bb);
-            rs += av;
-          }
-          acc += t - rs * u_a;
-          dgs -= rs;
-        }
-      }
-      if (MODE == SW_JACOBI) {
-        y[v] = (TV)(u_a + omega * ((TA)bv - acc) / dgs);
-      } else if (MODE == SW_RESID) {
-        y[v] = (TV)((TA)bv - acc);
-      } else {
-        y[v] = (TV)acc;
-        d1 += (double)u_a * (double)acc;
-        d2 += (double)u_a * (double)b[v];
-      }
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        um[t] = uc[t];
-        uc[t] = up[t];
-      }
-      if (CMP) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          gm[t] = gc[t];
-          rm[t] = rcur[t];
-        }
-      }
-    }
-  }
-  if (MODE == SW_MATVEC) {
-    const double s1 = block_sum(d1, sh[0]);
-    const double s2 = block_sum(d2, sh[1]);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-      partials[2 * blk] = s1;
-      partials[2 * blk + 1] = s2;
-    }
-  }
+cudaError_t launch_pipe(const LevelOp& op, dim3 grd, dim3 blk, const TV* x, const TV* b, TV* y, TA omega,
+                        double* partials, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  const size_t dyn = CMP ? kDelBytes : 0;
+  std::call_once(once, [&] {
+    if (dyn) attr = cudaFuncSetAttribute(sweep3_pipe<TV, TA, TS, MODE, CMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  });
+  if (attr != cudaSuccess) return attr;
+  sweep3_pipe<TV, TA, TS, MODE, CMP><<<grd, blk, dyn, st>>>(op, x, b, y, omega, partials);
+  return launched();
 }
 
 template <int D, typename TV, typename TA, typename TS, bool CMP>
 cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const void* b, void* y, double omega,
                            double* partials, int* nblocks, cudaStream_t st) {
   const int ni = op.N - 1;
+  const TV* xv = (const TV*)x;
+  const TV* bv = (const TV*)b;
+  TV* yv = (TV*)y;
   if (D == 3 && op.N >= 27) {
     dim3 blk(kTX, kTY, 1);
     dim3 grd((ni + kTX - 1) / kTX, (ni + kTY - 1) / kTY, (ni + kZC - 1) / kZC);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-    const TV* xv = (const TV*)x;
-    const TV* bv = (const TV*)b;
-    TV* yv = (TV*)y;
-    if (mode == SW_JACOBI)
-      sweep3_pipe<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
-    else if (mode == SW_RESID)
-      sweep3_pipe<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
-    else
-      sweep3_pipe<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
-    return launched();
+    if (mode == SW_JACOBI) return launch_pipe<TV, TA, TS, SW_JACOBI, CMP>(op, grd, blk, xv, bv, yv, (TA)omega, partials, st);
+    if (mode == SW_RESID) return launch_pipe<TV, TA, TS, SW_RESID, CMP>(op, grd, blk, xv, bv, yv, (TA)omega, partials, st);
+    return launch_pipe<TV, TA, TS, SW_MATVEC, CMP>(op, grd, blk, xv, bv, yv, (TA)omega, partials, st);
   }
   dim3 blk(kBX, kBY, 1);
   dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-  const TV* xv = (const TV*)x;
-  const TV* bv = (const TV*)b;
-  TV* yv = (TV*)y;
   if (mode == SW_JACOBI)
     sweep_kernel<D, TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
   else if (mode == SW_RESID)
