@@ -169,6 +169,8 @@ __device__ __forceinline__ uint8_t cell_class(const CmpChunk& ck, int N, int nse
 // ------------------------------------------------------------ host API (internal)
 struct DevScalars {     // per-problem scalars written by reductions
   double rr, pq, pr, zq, alpha, beta, ff, r0;
+  double rr_in;   // mixed path: inner (FP32) residual norm^2 of the unit-scaled residual equation
+  double s;       // mixed path: scale of the current outer residual (its 2-norm)
 };
 
 void set_error(const char* fmt, ...);
@@ -230,6 +232,15 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
                               const DevScalars* sc, int r32_out, void* rin, double* partials,
                               int* nblocks, cudaStream_t st);
 cudaError_t launch_richardson_update(long long n, double* u, int z64, const void* z, cudaStream_t st);
+// FP32 inner solve of the mixed path
+cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, const DevScalars* sc,
+                                   cudaStream_t st);
+cudaError_t launch_fcg32_update(long long n, float* e, float* r, const float* p, const float* q,
+                                const DevScalars* sc, double* partials, int* nblocks, cudaStream_t st);
+cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st);
+cudaError_t launch_apply_correction(long long n, double* u, const float* e, const DevScalars* sc, cudaStream_t st);
+cudaError_t launch_dot_f32f32(const float* a, const float* b, long long n, double* partials, int* nblocks,
+                              cudaStream_t st);
 cudaError_t launch_convert(long long n, int to64, const void* src, void* dst, cudaStream_t st);
 cudaError_t launch_load_vector(int dim, int N, double val, double* f, cudaStream_t st);
 

@@ -128,6 +128,11 @@ struct mg_problem {
   uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
   uint32_t* d_totals = nullptr;   // per stream: [0..2] main, [4..6] side
   uint32_t* h_totals = nullptr;   // pinned, same layout
+  // mixed paths: FP32 inner solve (iterative refinement)
+  float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+  int inner_its = 0;
+  bool have_correction = false;
+  double eta2 = 1e-10;            // inner tolerance (squared, relative to the unit-scaled residual)
   std::vector<void*> allocs;      // long-lived device allocations
   // outer-loop state
   bool first = true, need_restart = true;
@@ -428,7 +433,9 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
 }
 
 // ------------------------------------------------------------ outer loop
-// r = f - A u (FP64), rr = r.r, V-cycle input from r; resets the Krylov direction
+// r = f - A u (FP64) and rr = r.r.  FP64 paths: the V-cycle reads r and the
+// Krylov direction is reset.  Mixed paths (iterative refinement): the FP32
+// inner solve starts on the unit-scaled residual r_in = r / ||r|| with e = 0.
 mg_status outer_restart(mg_problem* P) {
   cudaStream_t st = P->st;
   Level& l0 = P->lev[0];
@@ -436,13 +443,27 @@ mg_status outer_restart(mg_problem* P) {
   MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->r, 0.0, nullptr, nullptr, st));
   MG_CHECK(launch_dot(P->r, P->r, l0.nvert, P->partials, &nb, st));
   MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
-  if (P->mixed) MG_CHECK(launch_convert(l0.nvert, 0, P->r, l0.b, st));
+  if (P->mixed) {
+    MG_CHECK(launch_scale_residual(l0.nvert, P->r, (float*)l0.b, P->sc, st));
+    MG_CHECK(cudaMemsetAsync(P->e32, 0, sizeof(float) * l0.nvert, st));
+    P->inner_its = 0;
+    P->have_correction = false;
+  }
   P->first = true;
   P->need_restart = false;
   return MG_OK;
 }
 
-// one outer iteration, enqueue only
+// u += s e (mixed paths): the FP32 correction of the inner solve in FP64
+mg_status apply_inner_correction(mg_problem* P) {
+  if (!P->mixed || !P->have_correction) return MG_OK;
+  MG_CHECK(launch_apply_correction(P->lev[0].nvert, P->u, P->e32, P->sc, P->st));
+  P->have_correction = false;
+  P->need_restart = true;
+  return MG_OK;
+}
+
+// one iteration, enqueue only
 mg_status outer_iteration_enqueue(mg_problem* P, int first) {
   cudaStream_t st = P->st;
   Level& l0 = P->lev[0];
@@ -452,6 +473,27 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
   void* z = vcycle_enqueue(P, 0, &stt);
   if (stt != MG_OK) return stt;
   int nb = 0;
+  if (P->mixed) {
+    const float* zf = (const float*)z;
+    float* rin = (float*)l0.b;
+    if (P->desc.outer == MG_OUTER_RICHARDSON) {   // e = V(r_in), applied after this iteration
+      MG_CHECK(cudaMemcpyAsync(P->e32, zf, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+      return MG_OK;
+    }
+    // FP32 flexible CG on A e = r_in, preconditioned by the FP32 V-cycle
+    if (!first) {
+      MG_CHECK(launch_dot_f32f32(zf, P->q32, n, P->partials, &nb, st));
+      MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st));
+      MG_CHECK(launch_scalar_op(P->sc, SC_SET_BETA, st));
+    }
+    MG_CHECK(launch_fcg32_direction(n, first, zf, P->p32, P->sc, st));
+    MG_CHECK(launch_sweep(l0.op, SW_MATVEC, 0, P->p32, rin, P->q32, 0.0, P->partials, &nb, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st));
+    MG_CHECK(launch_scalar_op(P->sc, SC_SET_ALPHA, st));
+    MG_CHECK(launch_fcg32_update(n, P->e32, rin, P->p32, P->q32, P->sc, P->partials, &nb, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr_in, st));
+    return MG_OK;
+  }
   if (P->desc.outer == MG_OUTER_RICHARDSON) {
     MG_CHECK(launch_richardson_update(n, P->u, z64, z, st));
     MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->r, 0.0, nullptr, nullptr, st));
@@ -508,6 +550,31 @@ mg_status read_scalars(mg_problem* P) {
   MG_CHECK(cudaMemcpyAsync(P->h_sc, P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->st));
   MG_CHECK(cudaStreamSynchronize(P->st));
   P->rr = P->h_sc->rr;
+  return MG_OK;
+}
+
+// Inner tolerance of the mixed path after an outer residual: reduce the
+// unit-scaled residual to 0.3 rtol ||f|| / ||r|| (enough to finish), but at
+// least to 1e-5 (about what FP32 arithmetic resolves) and at most to 0.1.
+constexpr int kMaxInner = 400;
+
+void set_inner_tolerance(mg_problem* P) {
+  const double rel = std::sqrt(P->rr / (P->ff > 0 ? P->ff : 1.0));
+  double eta = 0.3 * P->desc.rtol / std::max(rel, 1e-300);
+  eta = std::min(std::max(eta, 1e-5), 0.1);
+  P->eta2 = eta * eta;
+}
+
+// After one inner iteration of the mixed path: apply the correction and ask
+// for a new outer residual once the inner residual met its tolerance.
+mg_status mixed_after_iteration(mg_problem* P, bool* diverged) {
+  P->inner_its++;
+  P->have_correction = true;
+  const double rin = P->h_sc->rr_in;
+  *diverged = !std::isfinite(rin) || rin > 1e8;
+  if (*diverged) return MG_OK;
+  if (P->desc.outer == MG_OUTER_RICHARDSON || rin <= P->eta2 || P->inner_its >= kMaxInner)
+    return apply_inner_correction(P);
   return MG_OK;
 }
 
@@ -782,6 +849,14 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     P->allocs.erase(std::find(P->allocs.begin(), P->allocs.end(), l0.b));
     cudaFreeAsync(l0.b, P->st);
     l0.b = P->r;
+  } else {
+    const size_t v4 = sizeof(float) * l0.nvert;
+    if ((e = dalloc(P, &P->p32, v4)) != cudaSuccess || (e = dalloc(P, &P->q32, v4)) != cudaSuccess ||
+        (e = dalloc(P, &P->e32, v4)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "inner vectors"));
+    cudaMemsetAsync(P->p32, 0, v4, P->st);
+    cudaMemsetAsync(P->q32, 0, v4, P->st);
+    cudaMemsetAsync(P->e32, 0, v4, P->st);
   }
   {
     const long long ni = P->N - 1;
@@ -894,13 +969,29 @@ mg_status mg_vcycle(mg_problem* P, int n, double* rel_residual) {
     int npub = 0;
     mg_status s = publish_ready(P, false, &npub);
     if (s != MG_OK) return s;
+    if (npub) {
+      s = apply_inner_correction(P);
+      if (s != MG_OK) return s;
+    }
     if (P->need_restart) {
       s = outer_restart(P);
+      if (s == MG_OK && P->mixed) {
+        s = read_scalars(P);
+        set_inner_tolerance(P);
+      }
       if (s != MG_OK) return s;
     }
     s = outer_iteration(P);
     if (s != MG_OK) return s;
+    if (P->mixed) {
+      s = read_scalars(P);
+      bool diverged = false;
+      if (s == MG_OK) s = mixed_after_iteration(P, &diverged);
+      if (s != MG_OK) return s;
+    }
   }
+  mg_status sc_ = apply_inner_correction(P);
+  if (sc_ != MG_OK) return sc_;
   // true residual of the current iterate
   Level& l0 = P->lev[0];
   int nb = 0;
@@ -954,6 +1045,10 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       result = s;
       break;
     }
+    if (npub) {   // the correction computed so far belongs to the old operator: apply it
+      s = apply_inner_correction(P);
+      if (s != MG_OK) return s;
+    }
     if (P->need_restart) {
       s = outer_restart(P);
       if (s != MG_OK) return s;
@@ -964,6 +1059,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
         have_first = true;
       }
       if (P->ff <= 0) P->ff = P->rr > 0 ? P->rr : 1.0;
+      if (P->mixed) set_inner_tolerance(P);
       // divergence is judged against the residual of the current operator
       // at the last restart (a publication changes the operator)
       seg_rr = P->rr;
@@ -997,6 +1093,17 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     s = read_scalars(P);
     if (s != MG_OK) return s;
     ++seg_cycles;
+    if (P->mixed) {
+      bool diverged = false;
+      s = mixed_after_iteration(P, &diverged);
+      if (s != MG_OK) return s;
+      if (diverged) {
+        result = MG_ERR_DIVERGED;
+        set_error("inner residual diverged after %d cycles", P->cycles);
+        break;
+      }
+      continue;
+    }
     if (!std::isfinite(P->rr) || (seg_cycles > 5 && P->rr > 1e4 * std::max(seg_rr, 1e-300))) {
       result = MG_ERR_DIVERGED;
       set_error("residual diverged: ||r||^2 = %.3e after %d cycles (%.3e at the last restart)", P->rr,
@@ -1007,6 +1114,8 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   // verify with the true residual
   double rel = 0.0;
   {
+    mg_status s = apply_inner_correction(P);
+    if (s != MG_OK) return s;
     Level& l0 = P->lev[0];
     int nb = 0;
     MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->p, 0.0, nullptr, nullptr, P->st));

@@ -233,16 +233,29 @@ __device__ __forceinline__ int rank_in_row(const uint8_t* row, int lane, int k) 
   return cnt >> 3;
 }
 
+template <typename TA>
+__device__ __forceinline__ TA jacobi_div(TA num, TA den) {
+  return num / den;
+}
+template <>
+__device__ __forceinline__ float jacobi_div<float>(float num, float den) {
+  return __fdividef(num, den);   // smoother arithmetic of the FP32 V-cycle
+}
+
+__device__ __forceinline__ int ring_next(int s, int n) { return s + 1 == n ? 0 : s + 1; }
+
 template <typename TV, typename TA, typename TS, int MODE, bool CMP>
 __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const TV* __restrict__ x,
                                                          const TV* __restrict__ b, TV* __restrict__ y,
                                                          TA omega, double* __restrict__ partials) {
   constexpr int NV = 8;
-  __shared__ TV su[kPS][kUH][kUW];
-  __shared__ float sge[CMP ? kLS : 1][kCH][kCW];
+  constexpr int NT = kTX * kTY;
+  __shared__ TV su[kPS][kUH * kUW];
+  __shared__ float sge[CMP ? kLS : 1][kCells];         // eps_c, negated for cells with a surplus record
   __shared__ __align__(16) uint8_t scls[CMP ? kLS : 1][kCH][48];
-  __shared__ double sh[2][kTX * kTY / 32];
-  extern __shared__ float sdel[];   // [kDS][kCells][kDelPitch] (CMP only)
+  __shared__ int s_ch[kLS], s_rb[kLS];                 // chunk and chunk-row base of each layer slot
+  __shared__ double sh[2][NT / 32];
+  extern __shared__ float sdel[];                      // [kDS][kCells][kDelPitch] (CMP only)
   const int N = op.N, n1 = N + 1;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -251,54 +264,85 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
   const int k0 = 1 + blockIdx.z * kZC;
   const int k1 = min(N - 1, k0 + kZC - 1);
   const size_t plane = (size_t)n1 * n1;
+  const size_t cplane = (size_t)N * N;
   double d1 = 0.0, d2 = 0.0;
 
-  // asynchronous fetch of u plane p into its ring slot
-  auto fetch_plane = [&](int p) {
-    TV(*dst)[kUW] = su[p % kPS];
-    for (int t = tid; t < kUH * kUW; t += kTX * kTY) {
-      const int dy = t / kUW, dx = t - dy * kUW;
-      const int xx = x0 + dx, yy = y0 + dy;
-      if (xx <= N && yy <= N) cp_async_elem<TV>(&dst[dy][dx], x + (size_t)p * plane + (size_t)yy * n1 + xx);
-      else dst[dy][dx] = TV(0);
+  // per-thread fetch descriptors (the tile geometry is the same for every plane)
+  int u_g[2], u_s[2];          // global offset within a plane (-1: outside, zero fill), smem offset
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int t = tid + e * NT;
+    u_s[e] = t < kUH * kUW ? t : -1;
+    const int dy = t / kUW, dx = t - dy * kUW;
+    const int xx = x0 + dx, yy = y0 + dy;
+    u_g[e] = (u_s[e] >= 0 && xx <= N && yy <= N) ? yy * n1 + xx : -1;
+  }
+  int c_g[2], c_s[2];          // cell offsets within a layer
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int t = tid + e * NT;
+    c_s[e] = t < kCells ? t : -1;
+    const int dy = t / kCW, dx = t - dy * kCW;
+    const int cx = x0 + dx, cy = y0 + dy;
+    c_g[e] = (c_s[e] >= 0 && cx < N && cy < N) ? cy * N + cx : -1;
+  }
+  // class bytes: thread tid < 27 copies 16 bytes of row tid/3
+  int cl_row = -1, cl_part = 0, cl_off = 0;
+  if (CMP && tid < kCH * 3) {
+    const int dy = tid / 3, part = tid - dy * 3;
+    const int cy = y0 + dy, sx = (x0 >> 5) + (part == 2 ? 1 : 0);
+    cl_part = part;
+    if (cy < N && sx < op.nseg_x) {
+      cl_row = dy;
+      cl_off = (cy * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0);
+    } else {
+      cl_row = -2 - dy;   // zero fill row dy
+    }
+  }
+
+  auto fetch_plane = [&](int p, int slot) {
+    TV* dst = su[slot];
+    const TV* src = x + (size_t)p * plane;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (u_s[e] < 0) continue;
+      if (u_g[e] >= 0) cp_async_elem<TV>(dst + u_s[e], src + u_g[e]);
+      else dst[u_s[e]] = TV(0);
     }
   };
-  // asynchronous fetch of cell layer l: eps_c and the class bytes (the 32-byte
-  // segment x0/32 of each row plus the first 16 bytes of the next segment)
-  auto fetch_layer = [&](int l) {
+  // layer l into slot s; ch/ll: its chunk and layer within the chunk
+  auto fetch_layer = [&](int l, int s, int ch, int ll) {
     if (!CMP) return;
-    const int s = l % kLS;
-    int ch = l / op.layers;
-    ch = ch < op.nchunk ? ch : op.nchunk - 1;
-    const int rb = (l - ch * op.layers) * N;
-    const uint8_t* cls = op.cmp[ch].cls;
-    for (int t = tid; t < kCells; t += kTX * kTY) {
-      const int dy = t / kCW, dx = t - dy * kCW;
-      const int cx = x0 + dx, cy = y0 + dy;
-      if (cx < N && cy < N) cp_async4(&sge[s][dy][dx], op.eps_c + ((size_t)l * N + cy) * N + cx);
-      else sge[s][dy][dx] = 0.f;
+    const float* src = op.eps_c + (size_t)l * cplane;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (c_s[e] < 0) continue;
+      if (c_g[e] >= 0) cp_async4(&sge[s][c_s[e]], src + c_g[e]);
+      else sge[s][c_s[e]] = 0.f;
     }
-    if (tid < kCH * 3) {
-      const int dy = tid / 3, part = tid - dy * 3;
-      const int cy = y0 + dy;
-      const int sx = (x0 >> 5) + (part == 2 ? 1 : 0);
-      if (cy < N && sx < op.nseg_x)
-        cp_async16(&scls[s][dy][16 * part],
-                   cls + ((size_t)(rb + cy) * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0));
-      else
-        *reinterpret_cast<uint4*>(&scls[s][dy][16 * part]) = make_uint4(0u, 0u, 0u, 0u);
+    const int rb = ll * N;
+    if (cl_row >= 0) {
+      cp_async16(&scls[s][cl_row][16 * cl_part],
+                 op.cmp[ch].cls + (size_t)rb * op.nseg_x * kSegCells + cl_off);
+    } else if (cl_row <= -2) {
+      *reinterpret_cast<uint4*>(&scls[s][-2 - cl_row][16 * cl_part]) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+      s_ch[s] = ch;
+      s_rb[s] = rb;
     }
   };
-  // decode the surplus records of layer l (classes already in shared memory)
-  auto decode_layer = [&](int l) {
+  // decode the surplus records of the layer in slot s into decode slot ds and
+  // mark those cells by a negative eps_c in shared memory
+  auto decode_layer = [&](int s, int ds) {
     if (!CMP) return;
-    const int s = l % kLS;
-    float* dl = sdel + (size_t)(l % kDS) * kCells * kDelPitch;
-    int ch = l / op.layers;
-    ch = ch < op.nchunk ? ch : op.nchunk - 1;
-    const int rb = (l - ch * op.layers) * N;
-    const CmpChunk& ck = op.cmp[ch];
-    for (int t = tid; t < kCells; t += kTX * kTY) {
+    const CmpChunk& ck = op.cmp[s_ch[s]];
+    const int rb = s_rb[s];
+    float* dl = sdel + (size_t)ds * kCells * kDelPitch;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int t = c_s[e];
+      if (t < 0) continue;
       const int dy = t / kCW, dx = t - dy * kCW;
       const int cls = scls[s][dy][dx];
       if (!cls) continue;
@@ -323,67 +367,115 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
 #pragma unroll 4
         for (int p = 0; p < 28; ++p) o[p] = decode_entry<3>(rec, cls, p);
       }
+      sge[s][t] = -sge[s][t];
     }
   };
 
+  // ring bookkeeping (slot of the next plane / layer to fetch, and the chunk walk)
+  int ps_fetch = 0, ls_fetch = 0;
+  int f_ch = 0, f_ll = 0;   // chunk / layer-in-chunk of the next layer to fetch
+  auto advance_layer = [&]() {
+    if (++f_ll == op.layers && f_ch + 1 < op.nchunk) {
+      ++f_ch;
+      f_ll = 0;
+    }
+  };
+  int ps_read, ls_m, ls_c, ds_m, ds_c;   // slots of plane k+1, layers k-1 and k, decoded layers k-1 and k
   if (k0 <= k1) {
-    fetch_plane(k0 - 1);
-    fetch_plane(k0);
-    fetch_layer(k0 - 1);
+    // first fetched layer k0 - 1
+    f_ch = (k0 - 1) / op.layers;
+    f_ch = f_ch < op.nchunk ? f_ch : op.nchunk - 1;
+    f_ll = (k0 - 1) - f_ch * op.layers;
+    fetch_plane(k0 - 1, 0);
+    fetch_plane(k0, 1);
+    fetch_layer(k0 - 1, 0, f_ch, f_ll);
+    advance_layer();
     cp_async_commit();
-    fetch_plane(k0 + 1);
-    fetch_layer(k0);
+    fetch_plane(k0 + 1, 2);
+    fetch_layer(k0, 1, f_ch, f_ll);
+    advance_layer();
     cp_async_commit();
+    ps_fetch = 3;
+    ls_fetch = 2;
   }
+  ps_read = 2;        // plane k0 + 1
+  ls_m = 0;           // layer k0 - 1
+  ls_c = 1;           // layer k0
+  ds_m = 0;
+  ds_c = 1;
   TA um[9], uc[9], up[9];
   const TA gscale = (TA)(sizeof(TA) == 4 ? (double)op.gk32 : op.gk64);
   for (int k = k0; k <= k1; ++k) {
-    if (k + 2 <= N) fetch_plane(k + 2);
-    if (k + 1 <= N - 1) fetch_layer(k + 1);
+    if (k + 2 <= N) fetch_plane(k + 2, ps_fetch);
+    if (k + 1 <= N - 1) {
+      fetch_layer(k + 1, ls_fetch, f_ch, f_ll);
+      advance_layer();
+    }
     cp_async_commit();
     cp_async_wait1();   // all groups but the one just issued have landed
     __syncthreads();
     if (CMP) {
-      if (k == k0) decode_layer(k0 - 1);
-      decode_layer(k);
+      if (k == k0) decode_layer(ls_m, ds_m);
+      decode_layer(ls_c, ds_c);
       __syncthreads();
     }
     if (col_ok) {
       if (k == k0) {
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-          um[t] = (TA)su[(k - 1) % kPS][ty + t / 3][tx + t % 3];
-          uc[t] = (TA)su[k % kPS][ty + t / 3][tx + t % 3];
+          um[t] = (TA)su[0][(ty + t / 3) * kUW + tx + t % 3];
+          uc[t] = (TA)su[1][(ty + t / 3) * kUW + tx + t % 3];
         }
       }
 #pragma unroll
-      for (int t = 0; t < 9; ++t) up[t] = (TA)su[(k + 1) % kPS][ty + t / 3][tx + t % 3];
+      for (int t = 0; t < 9; ++t) up[t] = (TA)su[ps_read][(ty + t / 3) * kUW + tx + t % 3];
       const size_t v = (size_t)k * plane + (size_t)j * n1 + i;
       const TA u_a = uc[4];
       TA acc = 0, dgs = 0;
+      if (CMP) {
+        // geometric part: every nonzero off-diagonal of the 3D K_ref is -1/12, so
+        // cell c adds (-eps_c h / 12) (sum of its 4 face/body-diagonal
+        // neighbours of v - 4 u_v); one multiply by -h/12 at the end
+        float g[NV];
+        float gmin = 1.f;
 #pragma unroll
-      for (int o = 0; o < NV; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-        auto U = [&](int bb) -> TA {
-          const int pz = oz + ((bb >> 2) & 1);
-          const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
-          return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
-        };
-        const int l = k - 1 + oz;
-        if (CMP) {
-          // geometric part: in 3D every nonzero off-diagonal of K_ref is -1/12
-          // (face and body diagonals): the row is (-eps_c h / 12) times
-          // (sum of those 4 neighbours - 4 u_a)
-          const TA gk = (TA)sge[l % kLS][ty + oy][tx + ox] * gscale;
+        for (int o = 0; o < NV; ++o) {
+          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+          g[o] = sge[oz ? ls_c : ls_m][(ty + oy) * kCW + tx + ox];
+          gmin = fminf(gmin, g[o]);
+        }
+        TA ag = 0, gs = 0;
+#pragma unroll
+        for (int o = 0; o < NV; ++o) {
+          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+          auto U = [&](int bb) -> TA {
+            const int pz = oz + ((bb >> 2) & 1);
+            const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
+            return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
+          };
           TA s4 = 0;
 #pragma unroll
           for (int bb = 0; bb < NV; ++bb)
             if (bb != a && popc_small(a ^ bb) >= 2) s4 += U(bb);
-          acc += gk * (s4 - (TA)4 * u_a);
-          dgs -= (TA)4 * gk;
-          if (scls[l % kLS][ty + oy][tx + ox]) {
-            const float* dp = sdel + ((size_t)(l % kDS) * kCells + (ty + oy) * kCW + tx + ox) * kDelPitch;
+          const TA gv = (TA)fabsf(g[o]);
+          ag += gv * (s4 - (TA)4 * u_a);
+          gs += gv;
+        }
+        acc = ag * gscale;
+        dgs = (TA)-4 * gscale * gs;
+        if (gmin < 0.f) {   // some cell of this vertex carries a surplus
+#pragma unroll
+          for (int o = 0; o < NV; ++o) {
+            if (g[o] >= 0.f) continue;
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+            auto U = [&](int bb) -> TA {
+              const int pz = oz + ((bb >> 2) & 1);
+              const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
+              return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
+            };
+            const float* dp = sdel + ((size_t)(oz ? ds_c : ds_m) * kCells + (ty + oy) * kCW + tx + ox) * kDelPitch;
 #pragma unroll
             for (int bb = 0; bb < NV; ++bb) {
               if (bb == a) continue;
@@ -392,7 +484,18 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
               dgs -= dv;
             }
           }
-        } else {
+        }
+      } else {
+#pragma unroll
+        for (int o = 0; o < NV; ++o) {
+          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+          auto U = [&](int bb) -> TA {
+            const int pz = oz + ((bb >> 2) & 1);
+            const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
+            return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
+          };
+          const int l = k - 1 + oz;
           int ch = l / op.layers;
           ch = ch < op.nchunk ? ch : op.nchunk - 1;
           const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
@@ -412,7 +515,7 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
         }
       }
       if (MODE == SW_JACOBI) {
-        y[v] = (TV)(u_a + omega * ((TA)b[v] - acc) / dgs);
+        y[v] = (TV)(u_a + omega * jacobi_div<TA>((TA)b[v] - acc, dgs));
       } else if (MODE == SW_RESID) {
         y[v] = (TV)((TA)b[v] - acc);
       } else {
@@ -426,6 +529,13 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
         uc[t] = up[t];
       }
     }
+    ps_fetch = ring_next(ps_fetch, kPS);
+    ps_read = ring_next(ps_read, kPS);
+    ls_fetch = ring_next(ls_fetch, kLS);
+    ls_m = ls_c;
+    ls_c = ring_next(ls_c, kLS);
+    ds_m = ds_c;
+    ds_c = ring_next(ds_c, kDS);
   }
   if (MODE == SW_MATVEC) {
     const double s1 = block_sum(d1, sh[0]);
@@ -711,6 +821,13 @@ cudaError_t launch_dot(const double* a, const double* b, long long n, double* pa
   return launched();
 }
 
+cudaError_t launch_dot_f32f32(const float* a, const float* b, long long n, double* partials, int* nblocks,
+                              cudaStream_t st) {
+  *nblocks = kRedBlocks;
+  dot_kernel<float, float><<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
+  return launched();
+}
+
 cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double* partials, int* nblocks,
                            cudaStream_t st) {
   *nblocks = kRedBlocks;
@@ -741,6 +858,71 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
   *nblocks = kRedBlocks;
   if (r32_out) fcg_update_kernel<float><<<kRedBlocks, 256, 0, st>>>(n, u, r, p, q, sc, (float*)rin, partials);
   else fcg_update_kernel<double><<<kRedBlocks, 256, 0, st>>>(n, u, r, p, q, sc, (double*)rin, partials);
+  return launched();
+}
+
+// ---- FP32 inner flexible CG of the mixed path (vectors FP32, dot products FP64)
+__global__ void fcg32_direction_kernel(long long n, int first, const float* __restrict__ z, float* __restrict__ p,
+                                       const DevScalars* __restrict__ sc) {
+  const float beta = first ? 0.f : (float)sc->beta;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    p[t] = first ? z[t] : z[t] + beta * p[t];
+}
+
+__global__ void fcg32_update_kernel(long long n, float* __restrict__ e, float* __restrict__ r,
+                                    const float* __restrict__ p, const float* __restrict__ q,
+                                    const DevScalars* __restrict__ sc, double* partials) {
+  __shared__ double sh[8];
+  const float alpha = (float)sc->alpha;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    e[t] += alpha * p[t];
+    const float rv = r[t] - alpha * q[t];
+    r[t] = rv;
+    acc += (double)rv * (double)rv;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// r_in = r / s with s = sqrt(rr) (the residual scaled to unit norm, FP32)
+__global__ void scale_residual_kernel(long long n, const double* __restrict__ r, float* __restrict__ rin,
+                                      DevScalars* __restrict__ sc) {
+  const double s = sc->rr > 0.0 ? sqrt(sc->rr) : 1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->s = s;
+  const double inv = 1.0 / s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    rin[t] = (float)(r[t] * inv);
+}
+
+// u += s e (the scaled FP32 correction applied in FP64)
+__global__ void apply_correction_kernel(long long n, double* __restrict__ u, const float* __restrict__ e,
+                                        const DevScalars* __restrict__ sc) {
+  const double s = sc->s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    u[t] += s * (double)e[t];
+}
+
+cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, const DevScalars* sc,
+                                   cudaStream_t st) {
+  fcg32_direction_kernel<<<vgrid(n), 256, 0, st>>>(n, first, z, p, sc);
+  return launched();
+}
+
+cudaError_t launch_fcg32_update(long long n, float* e, float* r, const float* p, const float* q,
+                                const DevScalars* sc, double* partials, int* nblocks, cudaStream_t st) {
+  *nblocks = kRedBlocks;
+  fcg32_update_kernel<<<kRedBlocks, 256, 0, st>>>(n, e, r, p, q, sc, partials);
+  return launched();
+}
+
+cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st) {
+  scale_residual_kernel<<<vgrid(n), 256, 0, st>>>(n, r, rin, sc);
+  return launched();
+}
+
+cudaError_t launch_apply_correction(long long n, double* u, const float* e, const DevScalars* sc, cudaStream_t st) {
+  apply_correction_kernel<<<vgrid(n), 256, 0, st>>>(n, u, e, sc);
   return launched();
 }
 
