@@ -1121,7 +1121,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->p, 0.0, nullptr, nullptr, P->st));
     MG_CHECK(launch_dot(P->p, P->p, l0.nvert, P->partials, &nb, P->st));
     MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->r0, P->st));
-    mg_status s = read_scalars(P);
+    s = read_scalars(P);
     if (s != MG_OK) return s;
     rel = std::sqrt(P->h_sc->r0 / (P->ff > 0 ? P->ff : 1.0));
     P->need_restart = true;
