@@ -172,16 +172,16 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
   }
 }
 
-// ---------------------------------------------------------------- 3D pipelined tile sweep
-// A CTA owns a 32 x 8 column of vertices and walks kZC vertex planes along z.
-// u planes (34 x 10 with halo), cell layers (33 x 9 cell-centre eps) and the
-// layers' class bytes are brought into shared-memory rings by asynchronous
-// copies (cp.async) issued two planes ahead, so global latency overlaps the
-// arithmetic of the current plane.  The surplus records of the cells of a
-// layer with storage class > 0 are located once per CTA (rank from the class
-// bytes already in shared memory) and decoded into a shared-memory ring, so
-// a vertex reads its 7 row entries from shared memory.  u of planes k-1 and k
-// are carried in registers from the previous plane.
+// ---------------------------------------------------------------- 3D streaming tile sweep
+// A CTA owns a 32 x 8 column of vertices and walks kZC vertex planes along z,
+// one vertex per thread and plane.  u planes (34 x 10 with halo), b planes,
+// cell layers (33 x 9 cell-centre eps) and the layers' storage-class bytes
+// stream into shared-memory rings through asynchronous copies (cp.async)
+// issued kPF planes ahead, so a CTA keeps about kPF planes of traffic in
+// flight; one barrier per plane.  Cells with a surplus record (class > 0)
+// are resolved per vertex: the rank inside the cell's 32-cell segment comes
+// from the class bytes already in shared memory, the record from global
+// memory (L1/L2 serve the 8 vertices of the cell).
 __device__ __forceinline__ void cp_async4(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
@@ -195,7 +195,8 @@ __device__ __forceinline__ void cp_async16(void* s, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* s, const T* g) {
@@ -207,14 +208,13 @@ constexpr int kTX = 32, kTY = 8, kZC = 32;
 constexpr int kUW = kTX + 2, kUH = kTY + 2;   // u tile with halo
 constexpr int kCW = kTX + 1, kCH = kTY + 1;   // cell tile
 constexpr int kCells = kCW * kCH;
-constexpr int kDelPitch = 29;                 // floats per decoded cell (28 + 1: odd stride)
-// Ring depths.  Plane p is filled at step p-2 and read at step p-1; layer l is
-// filled at step l-1 and read at steps l and l+1; decoded layer l is written
-// at step l and read at steps l, l+1; the first step k0 also reads planes
-// k0-1..k0+1 and layers k0-1..k0.  The slot filled at step k is never one
-// read at step k-1 (no barrier separates the two).
-constexpr int kPS = 5, kLS = 4, kDS = 2;
-constexpr size_t kDelBytes = sizeof(float) * kDS * kCells * kDelPitch;
+constexpr int kPF = 4;                        // planes fetched ahead
+// Ring depths.  At step k (vertex plane k) the copies for plane k+kPF, b plane
+// k+kPF and cell layer k+kPF-1 are issued, and planes k-1..k+1, b plane k,
+// layers k-1..k are read.  A slot filled at step k must not be read at step
+// k-1 (no barrier between the two): rings of kPF+3 planes / kPF+2 layers
+// (and kPF+2 b planes) guarantee that.
+constexpr int kPS = kPF + 3, kLS = kPF + 2, kBS = kPF + 2;
 
 // rank of byte `lane` among the bytes equal to k in a 16-byte-aligned row of 32 bytes (shared memory)
 __device__ __forceinline__ int rank_in_row(const uint8_t* row, int lane, int k) {
@@ -243,19 +243,20 @@ __device__ __forceinline__ float jacobi_div<float>(float num, float den) {
 }
 
 __device__ __forceinline__ int ring_next(int s, int n) { return s + 1 == n ? 0 : s + 1; }
+__device__ __forceinline__ int ring_add(int s, int d, int n) { return s + d >= n ? s + d - n : s + d; }
 
 template <typename TV, typename TA, typename TS, int MODE, bool CMP>
-__global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const TV* __restrict__ x,
-                                                         const TV* __restrict__ b, TV* __restrict__ y,
-                                                         TA omega, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kTX * kTY, 3) sweep3_stream(const LevelOp op, const TV* __restrict__ x,
+                                                              const TV* __restrict__ b, TV* __restrict__ y,
+                                                              TA omega, double* __restrict__ partials) {
   constexpr int NV = 8;
   constexpr int NT = kTX * kTY;
   __shared__ TV su[kPS][kUH * kUW];
-  __shared__ float sge[CMP ? kLS : 1][kCells];         // eps_c, negated for cells with a surplus record
+  __shared__ TV sb[kBS][NT];
+  __shared__ float sge[CMP ? kLS : 1][kCells];
   __shared__ __align__(16) uint8_t scls[CMP ? kLS : 1][kCH][48];
-  __shared__ int s_ch[kLS], s_rb[kLS];                 // chunk and chunk-row base of each layer slot
+  __shared__ int s_ch[CMP ? kLS : 1];
   __shared__ double sh[2][NT / 32];
-  extern __shared__ float sdel[];                      // [kDS][kCells][kDelPitch] (CMP only)
   const int N = op.N, n1 = N + 1;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -264,223 +265,163 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
   const int k0 = 1 + blockIdx.z * kZC;
   const int k1 = min(N - 1, k0 + kZC - 1);
   const size_t plane = (size_t)n1 * n1;
-  const size_t cplane = (size_t)N * N;
   double d1 = 0.0, d2 = 0.0;
 
-  // per-thread fetch descriptors (the tile geometry is the same for every plane)
-  int u_g[2], u_s[2];          // global offset within a plane (-1: outside, zero fill), smem offset
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int t = tid + e * NT;
-    u_s[e] = t < kUH * kUW ? t : -1;
-    const int dy = t / kUW, dx = t - dy * kUW;
-    const int xx = x0 + dx, yy = y0 + dy;
-    u_g[e] = (u_s[e] >= 0 && xx <= N && yy <= N) ? yy * n1 + xx : -1;
-  }
-  int c_g[2], c_s[2];          // cell offsets within a layer
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int t = tid + e * NT;
-    c_s[e] = t < kCells ? t : -1;
-    const int dy = t / kCW, dx = t - dy * kCW;
-    const int cx = x0 + dx, cy = y0 + dy;
-    c_g[e] = (c_s[e] >= 0 && cx < N && cy < N) ? cy * N + cx : -1;
-  }
-  // class bytes: thread tid < 27 copies 16 bytes of row tid/3
-  int cl_row = -1, cl_part = 0, cl_off = 0;
+  // per-thread copy descriptors (the tile geometry is the same for every plane)
+  const int u_g0 = [&] {
+    const int dy = tid / kUW, dx = tid - dy * kUW;
+    return (x0 + dx <= N && y0 + dy <= N) ? (y0 + dy) * n1 + x0 + dx : -1;
+  }();
+  const int t1 = tid + NT;   // second u element of this thread (84 of them exist)
+  const int u_g1 = [&] {
+    if (t1 >= kUH * kUW) return -2;
+    const int dy = t1 / kUW, dx = t1 - dy * kUW;
+    return (x0 + dx <= N && y0 + dy <= N) ? (y0 + dy) * n1 + x0 + dx : -1;
+  }();
+  const int b_g = col_ok ? j * n1 + i : -1;
+  const int c_g0 = [&] {
+    const int dy = tid / kCW, dx = tid - dy * kCW;
+    return (x0 + dx < N && y0 + dy < N) ? (y0 + dy) * N + x0 + dx : -1;
+  }();
+  const int c_g1 = [&] {
+    if (t1 >= kCells) return -2;
+    const int dy = t1 / kCW, dx = t1 - dy * kCW;
+    return (x0 + dx < N && y0 + dy < N) ? (y0 + dy) * N + x0 + dx : -1;
+  }();
+  // class bytes: thread tid < 27 copies 16 bytes of row tid/3 (segment x0/32
+  // of the row, then the first 16 bytes of the next segment)
+  int cl_off = -1;
   if (CMP && tid < kCH * 3) {
     const int dy = tid / 3, part = tid - dy * 3;
     const int cy = y0 + dy, sx = (x0 >> 5) + (part == 2 ? 1 : 0);
-    cl_part = part;
-    if (cy < N && sx < op.nseg_x) {
-      cl_row = dy;
-      cl_off = (cy * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0);
-    } else {
-      cl_row = -2 - dy;   // zero fill row dy
-    }
+    if (cy < N && sx < op.nseg_x) cl_off = (cy * op.nseg_x + sx) * kSegCells + (part == 1 ? 16 : 0);
   }
 
-  auto fetch_plane = [&](int p, int slot) {
-    TV* dst = su[slot];
+  auto fetch_plane = [&](int p, int s) {
+    TV* dst = su[s];
     const TV* src = x + (size_t)p * plane;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      if (u_s[e] < 0) continue;
-      if (u_g[e] >= 0) cp_async_elem<TV>(dst + u_s[e], src + u_g[e]);
-      else dst[u_s[e]] = TV(0);
-    }
+    if (u_g0 >= 0) cp_async_elem<TV>(dst + tid, src + u_g0);
+    else dst[tid] = TV(0);
+    if (u_g1 >= 0) cp_async_elem<TV>(dst + t1, src + u_g1);
+    else if (u_g1 == -1) dst[t1] = TV(0);
   };
-  // layer l into slot s; ch/ll: its chunk and layer within the chunk
-  auto fetch_layer = [&](int l, int s, int ch, int ll) {
-    if (!CMP) return;
-    const float* src = op.eps_c + (size_t)l * cplane;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      if (c_s[e] < 0) continue;
-      if (c_g[e] >= 0) cp_async4(&sge[s][c_s[e]], src + c_g[e]);
-      else sge[s][c_s[e]] = 0.f;
-    }
-    const int rb = ll * N;
-    if (cl_row >= 0) {
-      cp_async16(&scls[s][cl_row][16 * cl_part],
-                 op.cmp[ch].cls + (size_t)rb * op.nseg_x * kSegCells + cl_off);
-    } else if (cl_row <= -2) {
-      *reinterpret_cast<uint4*>(&scls[s][-2 - cl_row][16 * cl_part]) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    if (tid == 0) {
-      s_ch[s] = ch;
-      s_rb[s] = rb;
-    }
+  auto fetch_b = [&](int p, int s) {
+    if (b_g >= 0) cp_async_elem<TV>(&sb[s][tid], b + (size_t)p * plane + b_g);
   };
-  // decode the surplus records of the layer in slot s into decode slot ds and
-  // mark those cells by a negative eps_c in shared memory
-  auto decode_layer = [&](int s, int ds) {
+  // cell layer l (eps_c and class bytes) into slot s
+  auto fetch_layer = [&](int l, int s) {
     if (!CMP) return;
-    const CmpChunk& ck = op.cmp[s_ch[s]];
-    const int rb = s_rb[s];
-    float* dl = sdel + (size_t)ds * kCells * kDelPitch;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int t = c_s[e];
-      if (t < 0) continue;
-      const int dy = t / kCW, dx = t - dy * kCW;
-      const int cls = scls[s][dy][dx];
-      if (!cls) continue;
-      const int cx = x0 + dx, cy = y0 + dy;
-      const int seg = (rb + cy) * op.nseg_x + (cx >> 5);
-      const int r = dx < kTX ? rank_in_row(&scls[s][dy][0], dx, cls) : 0;
-      const unsigned base = __ldg(ck.seg_base + (size_t)(cls - 1) * ck.nseg + seg);
-      const int recb = cls == 1 ? Dim<3>::REC1 : (cls == 2 ? Dim<3>::REC2 : Dim<3>::REC3);
-      const uint8_t* rec = ck.pool[cls - 1] + (size_t)(base + r) * recb;
-      float* o = dl + (size_t)t * kDelPitch;
-      if (cls == 3) {
-        const float4* r4 = reinterpret_cast<const float4*>(rec);
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-          const float4 v = __ldg(r4 + q);
-          o[4 * q] = v.x;
-          o[4 * q + 1] = v.y;
-          o[4 * q + 2] = v.z;
-          o[4 * q + 3] = v.w;
-        }
-      } else {
-#pragma unroll 4
-        for (int p = 0; p < 28; ++p) o[p] = decode_entry<3>(rec, cls, p);
-      }
-      sge[s][t] = -sge[s][t];
+    const float* src = op.eps_c + (size_t)l * N * N;
+    if (c_g0 >= 0) cp_async4(&sge[s][tid], src + c_g0);
+    else sge[s][tid] = 0.f;
+    if (c_g1 >= 0) cp_async4(&sge[s][t1], src + c_g1);
+    else if (c_g1 == -1) sge[s][t1] = 0.f;
+    if (tid < kCH * 3) {
+      int ch = l / op.layers;
+      ch = ch < op.nchunk ? ch : op.nchunk - 1;
+      uint8_t* dst = &scls[s][tid / 3][16 * (tid % 3)];
+      if (cl_off >= 0)
+        cp_async16(dst, op.cmp[ch].cls + (size_t)(l - ch * op.layers) * N * op.nseg_x * kSegCells + cl_off);
+      else
+        *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+      if (tid == 0) s_ch[s] = ch;
     }
   };
 
-  // ring bookkeeping (slot of the next plane / layer to fetch, and the chunk walk)
-  int ps_fetch = 0, ls_fetch = 0;
-  int f_ch = 0, f_ll = 0;   // chunk / layer-in-chunk of the next layer to fetch
-  auto advance_layer = [&]() {
-    if (++f_ll == op.layers && f_ch + 1 < op.nchunk) {
-      ++f_ch;
-      f_ll = 0;
-    }
-  };
-  int ps_read, ls_m, ls_c, ds_m, ds_c;   // slots of plane k+1, layers k-1 and k, decoded layers k-1 and k
-  if (k0 <= k1) {
-    // first fetched layer k0 - 1
-    f_ch = (k0 - 1) / op.layers;
-    f_ch = f_ch < op.nchunk ? f_ch : op.nchunk - 1;
-    f_ll = (k0 - 1) - f_ch * op.layers;
-    fetch_plane(k0 - 1, 0);
-    fetch_plane(k0, 1);
-    fetch_layer(k0 - 1, 0, f_ch, f_ll);
-    advance_layer();
-    cp_async_commit();
-    fetch_plane(k0 + 1, 2);
-    fetch_layer(k0, 1, f_ch, f_ll);
-    advance_layer();
-    cp_async_commit();
-    ps_fetch = 3;
-    ls_fetch = 2;
-  }
-  ps_read = 2;        // plane k0 + 1
-  ls_m = 0;           // layer k0 - 1
-  ls_c = 1;           // layer k0
-  ds_m = 0;
-  ds_c = 1;
-  TA um[9], uc[9], up[9];
   const TA gscale = (TA)(sizeof(TA) == 4 ? (double)op.gk32 : op.gk64);
+  // prologue: planes k0-1 .. k0+kPF-1, b planes and layers k0-1 .. k0+kPF-2
+  int sp = 0, sbq = 0, sl = 0;   // next slot to fill in each ring
+  if (k0 <= k1) {
+    for (int p = k0 - 1; p <= k0 + kPF - 1; ++p) {
+      if (p <= N) fetch_plane(p, sp);
+      if (p >= k0 && p <= k1) fetch_b(p, sbq);
+      if (p - 1 >= k0 - 1 && p - 1 <= N - 1) fetch_layer(p - 1, sl);
+      cp_async_commit();
+      sp = ring_next(sp, kPS);
+      if (p >= k0) sbq = ring_next(sbq, kBS);
+      if (p - 1 >= k0 - 1) sl = ring_next(sl, kLS);
+    }
+  }
+  // slots read at step k: planes k-1, k, k+1 start at ring slot 0; layers k-1, k at 0; b plane k at 0
+  int rp = 0, rl = 0, rb = 0;
   for (int k = k0; k <= k1; ++k) {
-    if (k + 2 <= N) fetch_plane(k + 2, ps_fetch);
-    if (k + 1 <= N - 1) {
-      fetch_layer(k + 1, ls_fetch, f_ch, f_ll);
-      advance_layer();
+    // issue step k + kPF: plane k+kPF, b plane k+kPF, layer k+kPF-1
+    {
+      const int p = k + kPF;
+      if (p <= N) fetch_plane(p, sp);
+      if (p <= k1) fetch_b(p, sbq);
+      if (p - 1 <= N - 1) fetch_layer(p - 1, sl);
+      cp_async_commit();
+      sp = ring_next(sp, kPS);
+      sbq = ring_next(sbq, kBS);
+      sl = ring_next(sl, kLS);
     }
-    cp_async_commit();
-    cp_async_wait1();   // all groups but the one just issued have landed
+    cp_async_wait<kPF - 1>();   // groups up to plane k+1 / layer k / b plane k have landed
     __syncthreads();
-    if (CMP) {
-      if (k == k0) decode_layer(ls_m, ds_m);
-      decode_layer(ls_c, ds_c);
-      __syncthreads();
-    }
     if (col_ok) {
-      if (k == k0) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          um[t] = (TA)su[0][(ty + t / 3) * kUW + tx + t % 3];
-          uc[t] = (TA)su[1][(ty + t / 3) * kUW + tx + t % 3];
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 9; ++t) up[t] = (TA)su[ps_read][(ty + t / 3) * kUW + tx + t % 3];
-      const size_t v = (size_t)k * plane + (size_t)j * n1 + i;
-      const TA u_a = uc[4];
+      const TV* um = su[rp];
+      const TV* uc = su[ring_add(rp, 1, kPS)];
+      const TV* up = su[ring_add(rp, 2, kPS)];
+      const int base = ty * kUW + tx;
+      auto U = [&](int pz, int idx) -> TA {
+        const int off = base + (idx / 3) * kUW + (idx % 3);
+        return (TA)(pz == 0 ? um[off] : (pz == 1 ? uc[off] : up[off]));
+      };
+      const TA u_a = U(1, 4);
       TA acc = 0, dgs = 0;
+      const int lm = rl, lc = ring_next(rl, kLS);
       if (CMP) {
         // geometric part: every nonzero off-diagonal of the 3D K_ref is -1/12, so
         // cell c adds (-eps_c h / 12) (sum of its 4 face/body-diagonal
-        // neighbours of v - 4 u_v); one multiply by -h/12 at the end
-        float g[NV];
-        float gmin = 1.f;
-#pragma unroll
-        for (int o = 0; o < NV; ++o) {
-          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-          g[o] = sge[oz ? ls_c : ls_m][(ty + oy) * kCW + tx + ox];
-          gmin = fminf(gmin, g[o]);
-        }
+        // neighbours of v - 4 u_v)
         TA ag = 0, gs = 0;
 #pragma unroll
         for (int o = 0; o < NV; ++o) {
           const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
           const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-          auto U = [&](int bb) -> TA {
-            const int pz = oz + ((bb >> 2) & 1);
-            const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
-            return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
-          };
+          const TA gv = (TA)sge[oz ? lc : lm][(ty + oy) * kCW + tx + ox];
           TA s4 = 0;
 #pragma unroll
           for (int bb = 0; bb < NV; ++bb)
-            if (bb != a && popc_small(a ^ bb) >= 2) s4 += U(bb);
-          const TA gv = (TA)fabsf(g[o]);
+            if (bb != a && popc_small(a ^ bb) >= 2)
+              s4 += U(oz + ((bb >> 2) & 1), (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)));
           ag += gv * (s4 - (TA)4 * u_a);
           gs += gv;
         }
         acc = ag * gscale;
         dgs = (TA)-4 * gscale * gs;
-        if (gmin < 0.f) {   // some cell of this vertex carries a surplus
+        // surplus of cells with a record
+        unsigned any = 0;
 #pragma unroll
+        for (int o = 0; o < NV; ++o) {
+          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+          any |= scls[oz ? lc : lm][ty + oy][tx + ox];
+        }
+        if (any) {
+#pragma unroll 1
           for (int o = 0; o < NV; ++o) {
-            if (g[o] >= 0.f) continue;
             const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            const int ls = oz ? lc : lm;
+            const int cls = scls[ls][ty + oy][tx + ox];
+            if (!cls) continue;
             const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-            auto U = [&](int bb) -> TA {
-              const int pz = oz + ((bb >> 2) & 1);
-              const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
-              return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
-            };
-            const float* dp = sdel + ((size_t)(oz ? ds_c : ds_m) * kCells + (ty + oy) * kCW + tx + ox) * kDelPitch;
+            const int l = k - 1 + oz;
+            const int ch = s_ch[ls];
+            const CmpChunk& ck = op.cmp[ch];
+            const int cx = i - 1 + ox, cy = j - 1 + oy;
+            const int seg = ((l - ch * op.layers) * N + cy) * op.nseg_x + (cx >> 5);
+            const int dx = tx + ox;
+            const int r = dx < kTX ? rank_in_row(&scls[ls][ty + oy][0], dx, cls) : 0;
+            const unsigned base_r = __ldg(ck.seg_base + (size_t)(cls - 1) * ck.nseg + seg);
+            const int recb = cls == 1 ? Dim<3>::REC1 : (cls == 2 ? Dim<3>::REC2 : Dim<3>::REC3);
+            const uint8_t* rec = ck.pool[cls - 1] + (size_t)(base_r + r) * recb;
 #pragma unroll
             for (int bb = 0; bb < NV; ++bb) {
               if (bb == a) continue;
-              const TA dv = (TA)dp[pair_of(NV, a, bb)];
-              acc += dv * (U(bb) - u_a);
+              const TA dv = (TA)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
+              const int pz = oz + ((bb >> 2) & 1);
+              const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
+              acc += dv * (U(pz, idx) - u_a);
               dgs -= dv;
             }
           }
@@ -490,52 +431,40 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
         for (int o = 0; o < NV; ++o) {
           const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
           const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-          auto U = [&](int bb) -> TA {
-            const int pz = oz + ((bb >> 2) & 1);
-            const int idx = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1));
-            return pz == 0 ? um[idx] : (pz == 1 ? uc[idx] : up[idx]);
-          };
           const int l = k - 1 + oz;
           int ch = l / op.layers;
           ch = ch < op.nchunk ? ch : op.nchunk - 1;
           const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
-          const int lc = ((l - ch * op.layers) * N + (j - 1 + oy)) * N + (i - 1 + ox);
+          const int lcell = ((l - ch * op.layers) * N + (j - 1 + oy)) * N + (i - 1 + ox);
           const size_t ccs = (size_t)op.chunk_cells;
           // row a: sum_b A_ab u_b - (sum_b A_ab) u_a, the row sum is minus the diagonal
           TA t = 0, rs = 0;
 #pragma unroll
           for (int bb = 0; bb < NV; ++bb) {
             if (bb == a) continue;
-            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * ccs + lc);
-            t += av * U(bb);
+            const TA av = (TA)__ldg(A + (size_t)pair_of(NV, a, bb) * ccs + lcell);
+            t += av * U(oz + ((bb >> 2) & 1), (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)));
             rs += av;
           }
           acc += t - rs * u_a;
           dgs -= rs;
         }
       }
+      const size_t v = (size_t)k * plane + (size_t)j * n1 + i;
+      const TA bv = (TA)sb[rb][tid];
       if (MODE == SW_JACOBI) {
-        y[v] = (TV)(u_a + omega * jacobi_div<TA>((TA)b[v] - acc, dgs));
+        y[v] = (TV)(u_a + omega * jacobi_div<TA>(bv - acc, dgs));
       } else if (MODE == SW_RESID) {
-        y[v] = (TV)((TA)b[v] - acc);
+        y[v] = (TV)(bv - acc);
       } else {
         y[v] = (TV)acc;
         d1 += (double)u_a * (double)acc;
-        d2 += (double)u_a * (double)b[v];
-      }
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        um[t] = uc[t];
-        uc[t] = up[t];
+        d2 += (double)u_a * (double)bv;
       }
     }
-    ps_fetch = ring_next(ps_fetch, kPS);
-    ps_read = ring_next(ps_read, kPS);
-    ls_fetch = ring_next(ls_fetch, kLS);
-    ls_m = ls_c;
-    ls_c = ring_next(ls_c, kLS);
-    ds_m = ds_c;
-    ds_c = ring_next(ds_c, kDS);
+    rp = ring_next(rp, kPS);
+    rl = ring_next(rl, kLS);
+    rb = ring_next(rb, kBS);
   }
   if (MODE == SW_MATVEC) {
     const double s1 = block_sum(d1, sh[0]);
@@ -546,21 +475,6 @@ __global__ void __launch_bounds__(kTX * kTY) sweep3_pipe(const LevelOp op, const
       partials[2 * blk + 1] = s2;
     }
   }
-}
-
-template <typename TV, typename TA, typename TS, int MODE, bool CMP>
-cudaError_t launch_pipe(const LevelOp& op, dim3 grd, dim3 blk, const TV* x, const TV* b, TV* y, TA omega,
-                        double* partials, cudaStream_t st) {
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  const size_t dyn = CMP ? kDelBytes : 0;
-  std::call_once(once, [&] {
-    if (dyn) attr = cudaFuncSetAttribute(sweep3_pipe<TV, TA, TS, MODE, CMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  });
-  if (attr != cudaSuccess) return attr;
-  sweep3_pipe<TV, TA, TS, MODE, CMP><<<grd, blk, dyn, st>>>(op, x, b, y, omega, partials);
-  return launched();
 }
 
 template <int D, typename TV, typename TA, typename TS, bool CMP>
@@ -574,9 +488,13 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     dim3 blk(kTX, kTY, 1);
     dim3 grd((ni + kTX - 1) / kTX, (ni + kTY - 1) / kTY, (ni + kZC - 1) / kZC);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-    if (mode == SW_JACOBI) return launch_pipe<TV, TA, TS, SW_JACOBI, CMP>(op, grd, blk, xv, bv, yv, (TA)omega, partials, st);
-    if (mode == SW_RESID) return launch_pipe<TV, TA, TS, SW_RESID, CMP>(op, grd, blk, xv, bv, yv, (TA)omega, partials, st);
-    return launch_pipe<TV, TA, TS, SW_MATVEC, CMP>(op, grd, blk, xv, bv, yv, (TA)omega, partials, st);
+    if (mode == SW_JACOBI)
+      sweep3_stream<TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else if (mode == SW_RESID)
+      sweep3_stream<TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else
+      sweep3_stream<TV, TA, TS, SW_MATVEC, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    return launched();
   }
   dim3 blk(kBX, kBY, 1);
   dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
