@@ -102,6 +102,9 @@ struct LevelOp {
   double hfac;            // h^(d-2)
   float gk32;             // 3D: h * (-1/12), the nonzero off-diagonal of K_ref h^(d-2)
   double gk64;
+  // compressed 3D finest level: vertices with an adjacent cell of class > 0
+  const int* touched;     // vertex indices (nullptr: no split sweep)
+  const int* ntouched;    // device count
 };
 
 // ------------------------------------------------------------ helpers
@@ -216,6 +219,8 @@ cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, 
 cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
+                                 cudaStream_t st);
 
 // vector ops for the outer loop (FP64 vectors; n = vertices)
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks,

@@ -128,6 +128,11 @@ struct mg_problem {
   uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
   uint32_t* d_totals = nullptr;   // per stream: [0..2] main, [4..6] side
   uint32_t* h_totals = nullptr;   // pinned, same layout
+  // mixed 3D finest level: vertices touched by cells with a surplus record
+  int* touched = nullptr;
+  int* ntouched = nullptr;
+  uint8_t* tflags = nullptr;
+  uint32_t* tcounts = nullptr;
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   int inner_its = 0;
@@ -387,6 +392,9 @@ mg_status upload_tables(mg_problem* P) {
     MG_CHECK(cudaMemcpyAsync(l0.d_full, P->h_full.data(), sizeof(FullChunk) * P->nchunk, cudaMemcpyHostToDevice,
                              P->st));
   // pageable source: the copy is staged before return, the host mirror may change afterwards
+  if (P->touched) {
+    MG_CHECK(launch_build_touched(l0.op, P->tflags, P->tcounts, P->touched, P->ntouched, P->st));
+  }
   return MG_OK;
 }
 
@@ -834,6 +842,18 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   if ((e = dalloc(P, &P->eps_c, (size_t)l0.ncell * (P->mixed ? 4 : 8))) != cudaSuccess)
     return fail(oom_or_cuda(e, "eps_c"));
   if (P->mixed) l0.op.eps_c = (const float*)P->eps_c;
+  if (P->mixed && D == 3 && P->N >= 27 && (P->N + 1) % 4 == 0 && !getenv("MG_NO_SPLIT_SWEEP")) {
+    // split sweep (geometric bulk pass + fix-up of vertices next to surplus cells)
+    const long long ng = (l0.nvert + 31) / 32;
+    if ((e = dalloc(P, &P->touched, sizeof(int) * l0.nvert)) != cudaSuccess ||
+        (e = dalloc(P, &P->ntouched, sizeof(int))) != cudaSuccess ||
+        (e = dalloc(P, &P->tflags, (size_t)l0.nvert)) != cudaSuccess ||
+        (e = dalloc(P, &P->tcounts, sizeof(uint32_t) * ng)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "touched list"));
+    cudaMemsetAsync(P->ntouched, 0, sizeof(int), P->st);
+    l0.op.touched = P->touched;
+    l0.op.ntouched = P->ntouched;
+  }
   // outer vectors
   const size_t v8 = sizeof(double) * l0.nvert;
   if ((e = dalloc(P, &P->u, v8)) != cudaSuccess || (e = dalloc(P, &P->f, v8)) != cudaSuccess ||

@@ -477,6 +477,293 @@ __global__ void __launch_bounds__(kTX * kTY, 3) sweep3_stream(const LevelOp op, 
   }
 }
 
+// ---------------------------------------------------------------- 3D FP32 geometric bulk sweep
+// The finest compressed level in FP32 splits each sweep in two kernels:
+//  (1) a class-blind bulk pass that applies only the geometric part
+//      eps_c K_ref h to every interior vertex, and
+//  (2) a fix-up pass over the list of vertices touched by a cell with a
+//      surplus record, which recomputes those vertices with every term.
+// The bulk pass is bound by load instructions rather than DRAM bytes, so it
+// is shaped to issue few of them: a thread owns 4 consecutive vertices in x
+// (rows of (N+1) floats with (N+1) % 4 == 0 keep float4 loads aligned) and
+// walks kGZ vertex planes along z with the u rows of planes k-1..k+1 and the
+// eps of cell layers k-1, k held in registers; plane k+2 and layer k+1 are
+// loaded one plane ahead.  Per 4 vertices and plane: 3 float4 + 6 scalar u
+// loads, 10 eps loads, one float4 b load and one float4 y store.
+constexpr int kGZ = 16;
+
+struct Rows6 {   // x[q-1], x[q..q+3], x[q+4] of three rows j-1, j, j+1
+  float v[3][6];
+};
+
+__device__ __forceinline__ void load_rows6(const float* __restrict__ x, size_t rowbase, int n1, int q,
+                                           bool has_left, bool has_right, Rows6& r) {
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) {
+    const float* p = x + rowbase + (size_t)(dy - 1) * n1 + q;
+    const float4 c = __ldg(reinterpret_cast<const float4*>(p));
+    r.v[dy][0] = has_left ? __ldg(p - 1) : 0.f;
+    r.v[dy][1] = c.x;
+    r.v[dy][2] = c.y;
+    r.v[dy][3] = c.z;
+    r.v[dy][4] = c.w;
+    r.v[dy][5] = has_right ? __ldg(p + 4) : 0.f;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
+                                                      const float* __restrict__ b, float* __restrict__ y,
+                                                      float omega, double* __restrict__ partials) {
+  __shared__ double sh[2][8];
+  const int N = op.N, n1 = N + 1;
+  const int qx = blockIdx.x * blockDim.x + threadIdx.x;   // quad: vertices 4 qx .. 4 qx + 3
+  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = 1 + blockIdx.z * kGZ;
+  const int k1 = min(N - 1, k0 + kGZ - 1);
+  const int q = 4 * qx;
+  const bool active = q < n1 && j < N && k0 <= k1;
+  double d1 = 0.0, d2 = 0.0;
+  if (active) {
+    const size_t plane = (size_t)n1 * n1;
+    const bool has_left = q > 0, has_right = q + 4 <= N;
+    const float gscale = op.gk32;
+    // eps of the 5 cells x = q-1 .. q+3 of rows j-1, j of layer l
+    auto load_eps = [&](int l, float (&g)[2][5]) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float* e = op.eps_c + ((size_t)l * N + (j - 1 + r)) * N;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const int cx = q - 1 + c;
+          g[r][c] = (cx >= 0 && cx < N) ? __ldg(e + cx) : 0.f;
+        }
+      }
+    };
+    Rows6 um, uc, up;
+    float gm[2][5], gc[2][5];
+    const size_t row0 = (size_t)j * n1;
+    load_rows6(x, (size_t)(k0 - 1) * plane + row0, n1, q, has_left, has_right, um);
+    load_rows6(x, (size_t)k0 * plane + row0, n1, q, has_left, has_right, uc);
+    load_rows6(x, (size_t)(k0 + 1) * plane + row0, n1, q, has_left, has_right, up);
+    load_eps(k0 - 1, gm);
+    load_eps(k0, gc);
+    float4 bcur = __ldg(reinterpret_cast<const float4*>(b + (size_t)k0 * plane + row0 + q));
+    for (int k = k0; k <= k1; ++k) {
+      // one plane ahead
+      Rows6 un;
+      float gn[2][5];
+      float4 bn = make_float4(0, 0, 0, 0);
+      const bool more = k + 1 <= k1;
+      if (more) {
+        load_rows6(x, (size_t)(k + 2) * plane + row0, n1, q, has_left, has_right, un);
+        load_eps(k + 1, gn);
+        bn = __ldg(reinterpret_cast<const float4*>(b + (size_t)(k + 1) * plane + row0 + q));
+      }
+      float out[4];
+      const float bb4[4] = {bcur.x, bcur.y, bcur.z, bcur.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        // vertex i = q + e: u column offset e + 1 in the rows, cells c = e (x = i-1) and e + 1 (x = i)
+        const float ua = uc.v[1][e + 1];
+        float ag = 0.f, gs = 0.f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+          const float gv = oz ? gc[oy][e + ox] : gm[oy][e + ox];
+          float s4 = 0.f;
+#pragma unroll
+          for (int bb = 0; bb < 8; ++bb)
+            if (bb != a && popc_small(a ^ bb) >= 2) {
+              const int pz = oz + ((bb >> 2) & 1);
+              const int ry = oy + ((bb >> 1) & 1);
+              const int cx = e + ox + (bb & 1);   // column in the 6-wide rows
+              s4 += pz == 0 ? um.v[ry][cx] : (pz == 1 ? uc.v[ry][cx] : up.v[ry][cx]);
+            }
+          ag += gv * (s4 - 4.f * ua);
+          gs += gv;
+        }
+        const float acc = ag * gscale;
+        const float dg = -4.f * gscale * gs;
+        const int i = q + e;
+        const bool valid = i >= 1 && i <= N - 1;
+        float r;
+        if (MODE == SW_JACOBI) r = ua + omega * __fdividef(bb4[e] - acc, dg);
+        else if (MODE == SW_RESID) r = bb4[e] - acc;
+        else {
+          r = acc;
+          if (valid) {
+            d1 += (double)ua * (double)acc;
+            d2 += (double)ua * (double)bb4[e];
+          }
+        }
+        out[e] = valid ? r : 0.f;   // boundary vertices stay zero
+      }
+      *reinterpret_cast<float4*>(y + (size_t)k * plane + row0 + q) = make_float4(out[0], out[1], out[2], out[3]);
+      um = uc;
+      uc = up;
+      up = un;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          gm[r][c] = gc[r][c];
+          gc[r][c] = gn[r][c];
+        }
+      bcur = bn;
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      partials[2 * blk] = s1;
+      partials[2 * blk + 1] = s2;
+    }
+  }
+}
+
+// Fix-up pass: vertices in op.touched (count *op.ntouched) recomputed with the
+// full operator (geometric part and decoded surplus).  For SW_MATVEC the
+// difference to the value the bulk pass wrote is added to the dot products.
+template <int MODE>
+__global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const float* __restrict__ x,
+                                                    const float* __restrict__ b, float* __restrict__ y,
+                                                    float omega, double* __restrict__ partials) {
+  __shared__ double sh[2][8];
+  const int N = op.N, n1 = N + 1;
+  const int nt = *op.ntouched;
+  double d1 = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int v = op.touched[t];
+    const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
+    float u[27];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+          u[dx + 3 * dy + 9 * dz] = __ldg(x + (size_t)v + (dx - 1) + (dy - 1) * n1 + (size_t)(dz - 1) * n1 * n1);
+    float Au, dg;
+    vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
+    const float uv = u[13];
+    if (MODE == SW_JACOBI) {
+      y[v] = uv + omega * (b[v] - Au) / dg;
+    } else if (MODE == SW_RESID) {
+      y[v] = b[v] - Au;
+    } else {
+      const float qg = y[v];
+      y[v] = Au;
+      d1 += (double)uv * ((double)Au - (double)qg);
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    if (threadIdx.x == 0) {
+      partials[2 * blockIdx.x] = s1;
+      partials[2 * blockIdx.x + 1] = 0.0;
+    }
+  }
+}
+
+constexpr int kFixBlocks = 152 * 2;
+
+// ---- list of vertices touched by a cell with a surplus record (finest compressed level)
+__global__ void touched_mark_kernel(const LevelOp op, uint8_t* __restrict__ flags) {
+  const int N = op.N, n1 = N + 1;
+  const long long ncell = (long long)N * N * N;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int cx = (int)(c % N), cy = (int)((c / N) % N), cz = (int)(c / ((long long)N * N));
+    int ch = cz / op.layers;
+    ch = ch < op.nchunk ? ch : op.nchunk - 1;
+    const int row = (cz - ch * op.layers) * N + cy;
+    const int cls = op.cmp[ch].cls[((size_t)row * op.nseg_x + (cx >> 5)) * kSegCells + (cx & 31)];
+    if (!cls) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int vx = cx + (a & 1), vy = cy + ((a >> 1) & 1), vz = cz + (a >> 2);
+      if (vx > 0 && vx < N && vy > 0 && vy < N && vz > 0 && vz < N) flags[((size_t)vz * n1 + vy) * n1 + vx] = 1;
+    }
+  }
+}
+
+__global__ void touched_count_kernel(long long nv, const uint8_t* __restrict__ flags, uint32_t* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const long long ng = (nv + 31) / 32;
+  for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < ng;
+       g += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long v = g * 32 + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, v < nv && flags[v]);
+    if (lane == 0) counts[g] = __popc(m);
+  }
+}
+
+// exclusive scan of counts[0..n) in place (one block), total to *total
+__global__ void scan1_kernel(long long n, uint32_t* __restrict__ c, int* __restrict__ total) {
+  __shared__ uint32_t part[1024];
+  const long long per = (n + blockDim.x - 1) / blockDim.x;
+  const long long b0 = threadIdx.x * per;
+  const long long b1 = b0 + per < n ? b0 + per : n;
+  uint32_t sum = 0;
+  for (long long i = b0; i < b1; ++i) sum += c[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (long long i = b0; i < b1; ++i) {
+    const uint32_t v = c[i];
+    c[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == blockDim.x - 1) *total = (int)part[threadIdx.x];
+}
+
+__global__ void touched_write_kernel(long long nv, const uint8_t* __restrict__ flags,
+                                     const uint32_t* __restrict__ base, int* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  const long long ng = (nv + 31) / 32;
+  for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < ng;
+       g += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long v = g * 32 + lane;
+    const bool f = v < nv && flags[v];
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (f) list[base[g] + __popc(m & ((1u << lane) - 1u))] = (int)v;
+  }
+}
+
+cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
+                        double* partials, int* nblocks, cudaStream_t st) {
+  const int nq = (op.N + 1) / 4;
+  dim3 blk(32, 8, 1);
+  dim3 grd((nq + 31) / 32, (op.N - 1 + 7) / 8, (op.N - 1 + kGZ - 1) / kGZ);
+  const int nb_bulk = (int)(grd.x * grd.y * grd.z);
+  double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
+  if (mode == SW_JACOBI) {
+    sweep3_geo4<SW_JACOBI><<<grd, blk, 0, st>>>(op, x, b, y, omega, partials);
+    count_launches(1);
+    sweep3_fixup<SW_JACOBI><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+  } else if (mode == SW_RESID) {
+    sweep3_geo4<SW_RESID><<<grd, blk, 0, st>>>(op, x, b, y, omega, partials);
+    count_launches(1);
+    sweep3_fixup<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+  } else {
+    sweep3_geo4<SW_MATVEC><<<grd, blk, 0, st>>>(op, x, b, y, omega, partials);
+    count_launches(1);
+    sweep3_fixup<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+  }
+  if (nblocks) *nblocks = nb_bulk + kFixBlocks;
+  return launched();
+}
+
 template <int D, typename TV, typename TA, typename TS, bool CMP>
 cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const void* b, void* y, double omega,
                            double* partials, int* nblocks, cudaStream_t st) {
@@ -484,6 +771,8 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   const TV* xv = (const TV*)x;
   const TV* bv = (const TV*)b;
   TV* yv = (TV*)y;
+  if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
+    return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
   if (D == 3 && op.N >= 27) {
     dim3 blk(kTX, kTY, 1);
     dim3 grd((ni + kTX - 1) / kTX, (ni + kTY - 1) / kTY, (ni + kZC - 1) / kZC);
@@ -732,6 +1021,22 @@ cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void*
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
+
+cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
+                                 cudaStream_t st) {
+  const long long nv = (long long)(op.N + 1) * (op.N + 1) * (op.N + 1);
+  const long long ng = (nv + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nv, st);
+  if (e != cudaSuccess) return e;
+  touched_mark_kernel<<<152 * 16, 256, 0, st>>>(op, flags);
+  count_launches(1);
+  touched_count_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts);
+  count_launches(1);
+  scan1_kernel<<<1, 1024, 0, st>>>(ng, counts, ntouched);
+  count_launches(1);
+  touched_write_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts, list);
+  return launched();
+}
 
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks, cudaStream_t st) {
   *nblocks = kRedBlocks;
