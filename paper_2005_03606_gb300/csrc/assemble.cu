@@ -196,11 +196,34 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     }
     __syncwarp();
     unsigned long long cand = 0;
-    if (KIND == EPS_BOXES)
-      for (int jx = 0; jx < s; ++jx) cand |= xt[grp * xt_stride + jx].bits;
-    // no box reaches a sample of this cell and eps is the same everywhere in it:
-    // every sample equals the cell-centre value and the surplus is exactly zero
-    const bool flat = KIND == EPS_BOXES && cand == 0 && F.jump_factor == 1.0 && eref == vout;
+    bool inside_all = false;
+    if (KIND == EPS_BOXES) {
+      // boxes whose x-interval holds some x-sample, kept only if their y (and z)
+      // interval can hold a sample of the cell too (a superset of the boxes that
+      // contain a sample); inside_all: one box holds every sample of the cell
+      unsigned long long xany = 0;
+      for (int jx = 0; jx < s; ++jx) xany |= xt[grp * xt_stride + jx].bits;
+      const double y0 = sample_x(N, s, ci[1], 0), y1 = sample_x(N, s, ci[1], s - 1);
+      const double z0 = D == 3 ? sample_x(N, s, ci[2], 0) : 0.0, z1 = D == 3 ? sample_x(N, s, ci[2], s - 1) : 0.0;
+      const double x0s = sample_x(N, s, ci[0], 0), x1s = sample_x(N, s, ci[0], s - 1);
+      unsigned long long m = xany;
+      while (m) {
+        const int bx = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        bool reach = F.box_lo[bx][1] <= y1 && y0 < F.box_hi[bx][1];
+        bool all = F.box_lo[bx][1] <= y0 && y1 < F.box_hi[bx][1] && F.box_lo[bx][0] <= x0s && x1s < F.box_hi[bx][0];
+        if (D == 3) {
+          reach = reach && F.box_lo[bx][2] <= z1 && z0 < F.box_hi[bx][2];
+          all = all && F.box_lo[bx][2] <= z0 && z1 < F.box_hi[bx][2];
+        }
+        if (reach) cand |= 1ull << bx;
+        inside_all = inside_all || all;
+      }
+    }
+    // eps is the same at every sample of this cell (outside all boxes, or inside
+    // one box): every sample equals the cell-centre value, the surplus is zero
+    const bool flat = KIND == EPS_BOXES && F.jump_factor == 1.0 &&
+                      ((cand == 0 && eref == vout) || (inside_all && eref == vin));
 
     T W[NW];
 #pragma unroll

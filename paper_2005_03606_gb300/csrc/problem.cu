@@ -848,7 +848,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     if ((e = dalloc(P, &P->touched, sizeof(int) * l0.nvert)) != cudaSuccess ||
         (e = dalloc(P, &P->ntouched, sizeof(int))) != cudaSuccess ||
         (e = dalloc(P, &P->tflags, (size_t)l0.nvert)) != cudaSuccess ||
-        (e = dalloc(P, &P->tcounts, sizeof(uint32_t) * ng)) != cudaSuccess)
+        (e = dalloc(P, &P->tcounts, sizeof(uint32_t) * (ng + (ng + 2047) / 2048 + 1))) != cudaSuccess)
       return fail(oom_or_cuda(e, "touched list"));
     cudaMemsetAsync(P->ntouched, 0, sizeof(int), P->st);
     l0.op.touched = P->touched;

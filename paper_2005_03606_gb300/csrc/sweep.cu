@@ -13,6 +13,7 @@
 #include "mg_internal.cuh"
 
 #include <mutex>
+#include <type_traits>
 
 namespace mg {
 
@@ -523,7 +524,9 @@ __global__ void __launch_bounds__(256, 2) sweep3_geo4(const LevelOp op, const fl
   const int k1 = min(N - 1, k0 + kGZ - 1);
   const int q = 4 * qx;
   const bool active = q < n1 && j < N && k0 <= k1;
-  double d1 = 0.0, d2 = 0.0;
+  // per-thread partial dot products in FP32 (a few dozen terms; they only set
+  // the Krylov step lengths), summed over the block in FP64
+  float d1 = 0.f, d2 = 0.f;
   if (active) {
     const size_t plane = (size_t)n1 * n1;
     const bool has_left = q > 0, has_right = q + 4 <= N;
@@ -594,8 +597,8 @@ __global__ void __launch_bounds__(256, 2) sweep3_geo4(const LevelOp op, const fl
         else {
           r = acc;
           if (valid) {
-            d1 += (double)ua * (double)acc;
-            d2 += (double)ua * (double)bb4[e];
+            d1 += ua * acc;
+            d2 += ua * bb4[e];
           }
         }
         out[e] = valid ? r : 0.f;   // boundary vertices stay zero
@@ -615,8 +618,8 @@ __global__ void __launch_bounds__(256, 2) sweep3_geo4(const LevelOp op, const fl
     }
   }
   if (MODE == SW_MATVEC) {
-    const double s1 = block_sum(d1, sh[0]);
-    const double s2 = block_sum(d2, sh[1]);
+    const double s1 = block_sum((double)d1, sh[0]);
+    const double s2 = block_sum((double)d2, sh[1]);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
       partials[2 * blk] = s1;
@@ -727,6 +730,38 @@ __global__ void scan1_kernel(long long n, uint32_t* __restrict__ c, int* __restr
   if (threadIdx.x == blockDim.x - 1) *total = (int)part[threadIdx.x];
 }
 
+// tile-local exclusive scan of c (2048 entries per block of 1024 threads); tile totals to tot
+__global__ void scan_tiles_kernel(long long n, uint32_t* __restrict__ c, uint32_t* __restrict__ tot) {
+  __shared__ uint32_t s[2048];
+  const long long base = (long long)blockIdx.x * 2048;
+  for (int t = threadIdx.x; t < 2048; t += blockDim.x) s[t] = base + t < n ? c[base + t] : 0u;
+  __syncthreads();
+  // Hillis-Steele over pairs: thread t owns s[2t], s[2t+1]
+  const int t = threadIdx.x;
+  uint32_t a0 = s[2 * t], a1 = s[2 * t + 1];
+  uint32_t own = a0 + a1;
+  __shared__ uint32_t ps[1024];
+  ps[t] = own;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const uint32_t v = t >= off ? ps[t - off] : 0u;
+    __syncthreads();
+    ps[t] += v;
+    __syncthreads();
+  }
+  const uint32_t excl = ps[t] - own;
+  if (base + 2 * t < n) c[base + 2 * t] = excl;
+  if (base + 2 * t + 1 < n) c[base + 2 * t + 1] = excl + a0;
+  if (t == 1023) tot[blockIdx.x] = ps[t];
+}
+
+__global__ void scan_add_kernel(long long n, uint32_t* __restrict__ c, const uint32_t* __restrict__ tot) {
+  const long long base = (long long)blockIdx.x * 2048;
+  const uint32_t add = tot[blockIdx.x];
+  for (int t = threadIdx.x; t < 2048; t += blockDim.x)
+    if (base + t < n) c[base + t] += add;
+}
+
 __global__ void touched_write_kernel(long long nv, const uint8_t* __restrict__ flags,
                                      const uint32_t* __restrict__ base, int* __restrict__ list) {
   const int lane = threadIdx.x & 31;
@@ -773,7 +808,9 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   TV* yv = (TV*)y;
   if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
     return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
-  if (D == 3 && op.N >= 27) {
+  // the plane-streaming kernel needs enough (x, y, z-run) tiles to fill the GPU;
+  // smaller grids run one vertex per thread
+  if (D == 3 && op.N >= 243) {
     dim3 blk(kTX, kTY, 1);
     dim3 grd((ni + kTX - 1) / kTX, (ni + kTY - 1) / kTY, (ni + kZC - 1) / kZC);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
@@ -880,11 +917,13 @@ constexpr int kRedBlocks = 152 * 4;
 
 template <typename TA, typename TB>
 __global__ void dot_kernel(const TA* __restrict__ a, const TB* __restrict__ b, long long n, double* partials) {
+  // FP32 operands accumulate per thread in FP32 (about a hundred terms), FP64 otherwise
+  typedef typename std::conditional<sizeof(TA) == 4 && sizeof(TB) == 4, float, double>::type Acc;
   __shared__ double sh[8];
-  double acc = 0.0;
+  Acc acc = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    acc += (double)a[t] * (double)b[t];
-  const double s = block_sum(acc, sh);
+    acc += (Acc)a[t] * (Acc)b[t];
+  const double s = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -1032,7 +1071,14 @@ cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* co
   count_launches(1);
   touched_count_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts);
   count_launches(1);
-  scan1_kernel<<<1, 1024, 0, st>>>(ng, counts, ntouched);
+  // exclusive scan of the group counts in 2048-entry tiles, then of the tile totals
+  const long long ntiles = (ng + 2047) / 2048;
+  uint32_t* tile_tot = counts + ng;   // the counts buffer holds ng + ntiles entries
+  scan_tiles_kernel<<<(unsigned)ntiles, 1024, 0, st>>>(ng, counts, tile_tot);
+  count_launches(1);
+  scan1_kernel<<<1, 1024, 0, st>>>(ntiles, tile_tot, ntouched);
+  count_launches(1);
+  scan_add_kernel<<<(unsigned)ntiles, 1024, 0, st>>>(ng, counts, tile_tot);
   count_launches(1);
   touched_write_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts, list);
   return launched();
@@ -1097,14 +1143,14 @@ __global__ void fcg32_update_kernel(long long n, float* __restrict__ e, float* _
                                     const DevScalars* __restrict__ sc, double* partials) {
   __shared__ double sh[8];
   const float alpha = (float)sc->alpha;
-  double acc = 0.0;
+  float acc = 0.f;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     e[t] += alpha * p[t];
     const float rv = r[t] - alpha * q[t];
     r[t] = rv;
-    acc += (double)rv * (double)rv;
+    acc += rv * rv;
   }
-  const double s = block_sum(acc, sh);
+  const double s = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
