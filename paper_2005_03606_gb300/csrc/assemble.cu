@@ -22,6 +22,8 @@
 // warp shuffles; 32/G cells are in flight per warp.
 #include "mg_internal.cuh"
 #include <cstdio>
+#include <climits>
+#include <cmath>
 
 namespace mg {
 
@@ -64,11 +66,41 @@ __device__ __forceinline__ T theta_factor(const EpsDev& F, double x) {
   return (T)(t_exp<T>((T)(-F.theta * x)) * t_cospi<T>((T)(F.theta * x)));
 }
 
+// field constants in the arithmetic precision T
+template <typename T>
+struct FieldT {
+  T amp, v_out, v_in, jump_factor;
+  __device__ __forceinline__ explicit FieldT(const EpsDev& F) {
+    if (sizeof(T) == 4) {
+      amp = (T)F.amp_f;
+      v_out = (T)F.v_out_f;
+      v_in = (T)F.v_in_f;
+      jump_factor = (T)F.jump_factor_f;
+    } else {
+      amp = (T)F.amp;
+      v_out = (T)F.v_out;
+      v_in = (T)F.v_in;
+      jump_factor = (T)F.jump_factor;
+    }
+  }
+  __device__ __forceinline__ static T phi(const EpsDev& F, int m) {
+    return sizeof(T) == 4 ? (T)F.phi_over_pi_f[m] : (T)F.phi_over_pi[m];
+  }
+};
+
+// box membership of sample indices (m_x, m_y, m_z) through the integer thresholds
+__device__ __forceinline__ bool in_box(const SampleThresholds& TH, int b, int D, const int* m) {
+  bool in = true;
+  for (int a = 0; a < D; ++a) in = in && TH.mlo[b][a] <= m[a] && m[a] < TH.mhi[b][a];
+  return in;
+}
+
 // eps at the centre of every cell (s = 1), FP64 or FP32
 template <int D, typename T>
-__global__ void eps_centre_kernel(const EpsDev F, int N, T* __restrict__ out) {
+__global__ void eps_centre_kernel(const EpsDev F, const SampleThresholds TH, int N, T* __restrict__ out) {
   long long ncell = 1;
   for (int a = 0; a < D; ++a) ncell *= N;
+  const FieldT<T> FT(F);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     int ci[3] = {0, 0, 0};
@@ -77,27 +109,21 @@ __global__ void eps_centre_kernel(const EpsDev F, int N, T* __restrict__ out) {
       ci[a] = (int)(t % N);
       t /= N;
     }
-    double x[3];
-    for (int a = 0; a < D; ++a) x[a] = sample_x(N, 1, ci[a], 0);
-    T e = (T)F.v_out;
+    T e = FT.v_out;
     if (F.kind == EPS_DISC) {
       double r2 = 0.0;
       for (int a = 0; a < D; ++a) {
-        double d = __dsub_rn(x[a], F.center[a]);
+        double d = __dsub_rn(sample_x(N, 1, ci[a], 0), F.center[a]);
         r2 = __dadd_rn(r2, __dmul_rn(d, d));
       }
-      e = (T)(r2 < F.r2lim ? F.v_in : F.v_out);
+      e = r2 < F.r2lim ? FT.v_in : FT.v_out;
     } else if (F.kind == EPS_BOXES) {
       bool in = false;
-      for (int b = 0; b < F.n_boxes && !in; ++b) {
-        bool ib = true;
-        for (int a = 0; a < D; ++a) ib = ib && (F.box_lo[b][a] <= x[a]) && (x[a] < F.box_hi[b][a]);
-        in = ib;
-      }
-      e = (T)(in ? F.v_in : F.v_out);
+      for (int b = 0; b < F.n_boxes && !in; ++b) in = in_box(TH, b, D, ci);
+      e = in ? FT.v_in : FT.v_out;
     } else if (F.kind == EPS_THETA) {
       T p = (T)1;
-      for (int a = 0; a < D; ++a) p *= theta_factor<T>(F, x[a]);
+      for (int a = 0; a < D; ++a) p *= theta_factor<T>(F, sample_x(N, 1, ci[a], 0));
       e = (T)1 + (T)(0.3 / D) * p;
     } else if (F.kind == EPS_FOURIER) {
       int gm[3] = {ci[0], ci[1], ci[2]};
@@ -105,12 +131,12 @@ __global__ void eps_centre_kernel(const EpsDev F, int N, T* __restrict__ out) {
       T g = 0;
       for (int m = 0; m < F.n_modes; ++m) {
         int n = phase_num(F, m, D, gm, twoN);
-        T arg = (T)n / (T)N + (T)F.phi_over_pi[m];
+        T arg = (T)n / (T)N + FieldT<T>::phi(F, m);
         g += t_cospi<T>(arg);
       }
-      e = (T)F.v_out * t_exp<T>((T)F.amp * g);
+      e = FT.v_out * t_exp<T>(FT.amp * g);
     }
-    if (F.jump_factor != 1.0 && x[0] >= F.jump_x) e *= (T)F.jump_factor;
+    if (ci[0] >= TH.mjump) e *= FT.jump_factor;
     out[c] = e;
   }
 }
@@ -125,14 +151,16 @@ struct XEntryT {
 };
 
 template <int D, typename T, int KIND>
-__global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, const AsmLaunch A) {
+__global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, const SampleThresholds TH,
+                                                               const AsmLaunch A) {
   constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
   constexpr int NW = D == 3 ? 27 : 6;
   const int N = A.N, s = A.s;
   __shared__ T s_t1[kMaxS], s_t2[kMaxS];
   __shared__ T s_rot_c[kMaxModes], s_rot_s[kMaxModes];
   __shared__ XEntryT<T> s_x[kAsmThreads / 32][64];
-  const T vin = (T)F.v_in, vout = (T)F.v_out;
+  const FieldT<T> FT(F);
+  const T vin = FT.v_in, vout = FT.v_out;
   for (int j = threadIdx.x; j < s; j += blockDim.x) {
     s_t1[j] = (T)(2 * j + 1) / (T)(2 * s);
     s_t2[j] = (T)(3 * j * j + 3 * j + 1) / (T)(3 * s * s);
@@ -174,23 +202,25 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
       }
     }
     const T eref = eps_c[c];
+    // global sample indices of the cell's first sub-box along each axis
+    const int m0[3] = {ci[0] * s, ci[1] * s, D == 3 ? ci[2] * s : 0};
     // x-axis table of the group's cell
     for (int jx = lig; jx < s; jx += G) {
-      double x = sample_x(N, s, ci[0], jx);
+      const int mx = m0[0] + jx;
       XEntryT<T> e;
       e.bits = 0;
       e.th = 0;
-      e.jmul = (T)((F.jump_factor != 1.0 && x >= F.jump_x) ? F.jump_factor : 1.0);
+      e.jmul = mx >= TH.mjump ? FT.jump_factor : (T)1;
       if (KIND == EPS_BOXES) {
         unsigned long long m = 0;
         for (int b = 0; b < F.n_boxes; ++b)
-          if (F.box_lo[b][0] <= x && x < F.box_hi[b][0]) m |= 1ull << b;
+          if (TH.mlo[b][0] <= mx && mx < TH.mhi[b][0]) m |= 1ull << b;
         e.bits = m;
       } else if (KIND == EPS_DISC) {
-        double d = __dsub_rn(x, F.center[0]);
+        double d = __dsub_rn(sample_x(N, s, ci[0], jx), F.center[0]);
         e.bits = (unsigned long long)__double_as_longlong(__dmul_rn(d, d));
       } else if (KIND == EPS_THETA) {
-        e.th = theta_factor<T>(F, x);
+        e.th = theta_factor<T>(F, sample_x(N, s, ci[0], jx));
       }
       xt[grp * xt_stride + jx] = e;
     }
@@ -198,23 +228,20 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     unsigned long long cand = 0;
     bool inside_all = false;
     if (KIND == EPS_BOXES) {
-      // boxes whose x-interval holds some x-sample, kept only if their y (and z)
-      // interval can hold a sample of the cell too (a superset of the boxes that
-      // contain a sample); inside_all: one box holds every sample of the cell
+      // boxes holding some x-sample, kept only if their y (and z) range can hold
+      // a sample of the cell too (a superset of the boxes that contain a
+      // sample); inside_all: one box holds every sample of the cell
       unsigned long long xany = 0;
       for (int jx = 0; jx < s; ++jx) xany |= xt[grp * xt_stride + jx].bits;
-      const double y0 = sample_x(N, s, ci[1], 0), y1 = sample_x(N, s, ci[1], s - 1);
-      const double z0 = D == 3 ? sample_x(N, s, ci[2], 0) : 0.0, z1 = D == 3 ? sample_x(N, s, ci[2], s - 1) : 0.0;
-      const double x0s = sample_x(N, s, ci[0], 0), x1s = sample_x(N, s, ci[0], s - 1);
       unsigned long long m = xany;
       while (m) {
         const int bx = __ffsll((long long)m) - 1;
         m &= m - 1;
-        bool reach = F.box_lo[bx][1] <= y1 && y0 < F.box_hi[bx][1];
-        bool all = F.box_lo[bx][1] <= y0 && y1 < F.box_hi[bx][1] && F.box_lo[bx][0] <= x0s && x1s < F.box_hi[bx][0];
-        if (D == 3) {
-          reach = reach && F.box_lo[bx][2] <= z1 && z0 < F.box_hi[bx][2];
-          all = all && F.box_lo[bx][2] <= z0 && z1 < F.box_hi[bx][2];
+        bool reach = true, all = true;
+        for (int a = 0; a < D; ++a) {
+          const int lo = TH.mlo[bx][a], hi = TH.mhi[bx][a];
+          if (a > 0) reach = reach && lo <= m0[a] + s - 1 && m0[a] < hi;
+          all = all && lo <= m0[a] && m0[a] + s - 1 < hi;
         }
         if (reach) cand |= 1ull << bx;
         inside_all = inside_all || all;
@@ -222,7 +249,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     }
     // eps is the same at every sample of this cell (outside all boxes, or inside
     // one box): every sample equals the cell-centre value, the surplus is zero
-    const bool flat = KIND == EPS_BOXES && F.jump_factor == 1.0 &&
+    const bool flat = KIND == EPS_BOXES && TH.mjump == INT_MAX &&
                       ((cand == 0 && eref == vout) || (inside_all && eref == vin));
 
     T W[NW];
@@ -236,38 +263,37 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
       double rowd = 0.0;
       T rowth = (T)1;
       T P_re[KIND == EPS_FOURIER ? kMaxModes : 1], P_im[KIND == EPS_FOURIER ? kMaxModes : 1];
-      const double y = sample_x(N, s, ci[1], jy);
-      const double z = D == 3 ? sample_x(N, s, ci[2], jz) : 0.0;
+      const int my = m0[1] + jy, mz = m0[2] + jz;
       if (KIND == EPS_BOXES) {
         unsigned long long m = 0, cb = cand;
         while (cb) {
           int b = __ffsll((long long)cb) - 1;
           cb &= cb - 1;
-          bool ok = F.box_lo[b][1] <= y && y < F.box_hi[b][1];
-          if (D == 3) ok = ok && F.box_lo[b][2] <= z && z < F.box_hi[b][2];
+          bool ok = TH.mlo[b][1] <= my && my < TH.mhi[b][1];
+          if (D == 3) ok = ok && TH.mlo[b][2] <= mz && mz < TH.mhi[b][2];
           if (ok) m |= 1ull << b;
         }
         rowbits = m;
       } else if (KIND == EPS_DISC) {
-        double dy = __dsub_rn(y, F.center[1]);
+        double dy = __dsub_rn(sample_x(N, s, ci[1], jy), F.center[1]);
         rowd = __dmul_rn(dy, dy);
       } else if (KIND == EPS_THETA) {
-        rowth = theta_factor<T>(F, y);
-        if (D == 3) rowth = rowth * theta_factor<T>(F, z);
+        rowth = theta_factor<T>(F, sample_x(N, s, ci[1], jy));
+        if (D == 3) rowth = rowth * theta_factor<T>(F, sample_x(N, s, ci[2], jz));
       } else if (KIND == EPS_FOURIER) {
-        int gm[3] = {ci[0] * s, ci[1] * s + jy, D == 3 ? ci[2] * s + jz : 0};
+        int gm[3] = {m0[0], my, mz};
         const int twoNs = 2 * N * s;
         for (int m = 0; m < F.n_modes; ++m) {
           int n = phase_num(F, m, D, gm, twoNs);
           T sn, cs;
-          t_sincospi<T>((T)n / (T)(N * s) + (T)F.phi_over_pi[m], &sn, &cs);
+          t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
           P_re[m] = cs;
           P_im[m] = sn;
         }
       }
       double dz2 = 0.0;
       if (KIND == EPS_DISC && D == 3) {
-        double dz = __dsub_rn(z, F.center[2]);
+        double dz = __dsub_rn(sample_x(N, s, ci[2], jz), F.center[2]);
         dz2 = __dmul_rn(dz, dz);
       }
       T S0 = 0, S1 = 0, S2 = 0;
@@ -275,7 +301,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
         const XEntryT<T>& xe = xt[grp * xt_stride + jx];
         T e;
         if (KIND == EPS_CONST) {
-          e = (T)F.v_out;
+          e = vout;
         } else if (KIND == EPS_BOXES) {
           e = (xe.bits & rowbits) ? vin : vout;
         } else if (KIND == EPS_DISC) {
@@ -293,7 +319,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
             P_re[m] = nr;
             P_im[m] = ni;
           }
-          e = (T)F.v_out * t_exp<T>((T)F.amp * g);
+          e = vout * t_exp<T>(FT.amp * g);
         }
         e *= xe.jmul;
         const T ep = e - eref;
@@ -494,6 +520,29 @@ __global__ void pack_copy_kernel(long long nseg, const uint8_t* __restrict__ cls
   }
 }
 
+// x(m) = (2m + 1) / (2 N s), evaluated exactly as the FP64 sample position
+double sample_x_host(int N, int s, long long m) { return (double)(2 * m + 1) / (double)(2 * (long long)N * s); }
+
+// smallest m in [0, N s] with x(m) >= v (N s when there is none)
+int first_at_or_above(double v, int N, int s) {
+  const long long M = (long long)N * s;
+  double t = std::floor((v * 2.0 * (double)M - 1.0) / 2.0) - 2.0;
+  long long m = t < 0.0 ? 0 : (t > (double)M ? M : (long long)t);
+  while (m < M && sample_x_host(N, s, m) < v) ++m;
+  while (m > 0 && sample_x_host(N, s, m - 1) >= v) --m;
+  return (int)m;
+}
+
+void make_thresholds(const EpsDev& F, int N, int s, SampleThresholds* TH) {
+  for (int b = 0; b < kMaxBoxes; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const bool used = F.kind == EPS_BOXES && b < F.n_boxes && a < F.dim;
+      TH->mlo[b][a] = used ? first_at_or_above(F.box_lo[b][a], N, s) : 0;
+      TH->mhi[b][a] = used ? first_at_or_above(F.box_hi[b][a], N, s) : 0;
+    }
+  TH->mjump = F.jump_factor != 1.0 ? first_at_or_above(F.jump_x, N, s) : INT_MAX;
+}
+
 int grid_for(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
   if (b > 152LL * 64) b = 152LL * 64;
@@ -513,12 +562,14 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   const EpsDev& F = *a.eps_host;
+  SampleThresholds TH;
+  make_thresholds(F, a.N, a.s, &TH);
   switch (F.kind) {
-    case EPS_CONST: assemble_kernel<D, T, EPS_CONST><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
-    case EPS_DISC: assemble_kernel<D, T, EPS_DISC><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
-    case EPS_FOURIER: assemble_kernel<D, T, EPS_FOURIER><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
-    case EPS_BOXES: assemble_kernel<D, T, EPS_BOXES><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
-    case EPS_THETA: assemble_kernel<D, T, EPS_THETA><<<(int)blocks, kAsmThreads, 0, st>>>(F, a); break;
+    case EPS_CONST: assemble_kernel<D, T, EPS_CONST><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_DISC: assemble_kernel<D, T, EPS_DISC><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_FOURIER: assemble_kernel<D, T, EPS_FOURIER><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_BOXES: assemble_kernel<D, T, EPS_BOXES><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_THETA: assemble_kernel<D, T, EPS_THETA><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();
@@ -527,14 +578,16 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st) {
+  SampleThresholds TH;
+  make_thresholds(*eps, N, 1, &TH);
   long long ncell = (long long)N * N * (dim == 3 ? N : 1);
   int g = grid_for(ncell, 256);
   if (dim == 2) {
-    if (prec64) eps_centre_kernel<2, double><<<g, 256, 0, st>>>(*eps, N, (double*)eps_c);
-    else eps_centre_kernel<2, float><<<g, 256, 0, st>>>(*eps, N, (float*)eps_c);
+    if (prec64) eps_centre_kernel<2, double><<<g, 256, 0, st>>>(*eps, TH, N, (double*)eps_c);
+    else eps_centre_kernel<2, float><<<g, 256, 0, st>>>(*eps, TH, N, (float*)eps_c);
   } else {
-    if (prec64) eps_centre_kernel<3, double><<<g, 256, 0, st>>>(*eps, N, (double*)eps_c);
-    else eps_centre_kernel<3, float><<<g, 256, 0, st>>>(*eps, N, (float*)eps_c);
+    if (prec64) eps_centre_kernel<3, double><<<g, 256, 0, st>>>(*eps, TH, N, (double*)eps_c);
+    else eps_centre_kernel<3, float><<<g, 256, 0, st>>>(*eps, TH, N, (float*)eps_c);
   }
   return launched();
 }

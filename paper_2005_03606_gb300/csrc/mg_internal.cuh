@@ -67,6 +67,18 @@ struct EpsDev {
   double phi_over_pi[kMaxModes];   // phase / pi
   double box_lo[kMaxBoxes][3];
   double box_hi[kMaxBoxes][3];
+  // FP32 copies for the FP32 arithmetic path
+  float amp_f, v_out_f, v_in_f, jump_factor_f;
+  float phi_over_pi_f[kMaxModes];
+};
+
+// Sample positions x(m) = (2m + 1) / (2 N s), m = i s + j the global sub-box
+// index along an axis, are monotone in m, so the FP64 decisions lo <= x(m),
+// x(m) < hi and x(m) >= jump_x reduce to integer thresholds computed once on
+// the host with the same FP64 expression: lo <= x(m) < hi  <=>  mlo <= m < mhi.
+struct SampleThresholds {
+  int mlo[kMaxBoxes][3], mhi[kMaxBoxes][3];
+  int mjump;   // x(m) >= jump_x  <=>  m >= mjump (INT_MAX when there is no jump)
 };
 
 // ------------------------------------------------------------ operator storage

@@ -202,6 +202,11 @@ void fill_eps(const mg_eps_desc& d, int dim, EpsDev* e) {
       e->box_lo[b][a] = d.box_lo[b][a];
       e->box_hi[b][a] = d.box_hi[b][a];
     }
+  e->amp_f = (float)e->amp;
+  e->v_out_f = (float)e->v_out;
+  e->v_in_f = (float)e->v_in;
+  e->jump_factor_f = (float)e->jump_factor;
+  for (int m = 0; m < MG_MAX_MODES; ++m) e->phi_over_pi_f[m] = (float)e->phi_over_pi[m];
 }
 
 mg_status validate(const mg_problem_desc* d) {
