@@ -221,6 +221,34 @@ mg_status mg_profile_kernel(mg_problem* p, int which, int reps, double* ms_per_l
  * (graph replays count every kernel they contain). */
 uint64_t mg_launch_count(void);
 
+/* Allocation-free variant of the mixed-precision assembly (the paper has no
+ * counterpart: it is an interface for callers that cannot allocate device
+ * memory while they run, e.g. a process that plans its whole device
+ * footprint up front or an application whose own allocator owns the device,
+ * and for which a cudaMalloc would break that plan or synchronise the device).
+ * For the cells [cell0, cell0 + ncell) of an n_cells^dim grid (whole x-rows:
+ * cell0 and ncell multiples of n_cells) it computes, at accuracy s with the
+ * storage rule of tolerance tau (0 => 1e-6), exactly what the mixed paths
+ * store: the FP32 cell-centre eps, the storage class (0..3) and the decoded
+ * surplus entries (FP32, NP = 6 (2D) / 28 (3D) per cell, pair order a < b;
+ * zeros for class 0).  All pointers are caller-owned DEVICE buffers:
+ * eps_c_out holds n_cells^dim floats (the whole grid is written), cls_out
+ * ncell bytes, surplus_out ncell * NP floats.  Work is issued on cuda_stream
+ * (NULL = legacy default stream); the call returns without synchronising.
+ * Scratch: a fixed 64 MiB device array inside the library, which bounds one
+ * call to about 460k cells in 3D (ncell * 144 bytes in 3D, ncell * 64 in 2D,
+ * plus padding); larger ranges return MG_ERR_INVALID with the limit in
+ * mg_last_error().  The array is shared by every call on a device and keeps
+ * the last call's contents, so calls that overlap on the GPU (different
+ * streams, or host threads) race and must be serialised by the caller.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  Allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  Errors: MG_ERR_INVALID, MG_ERR_CUDA. */
+mg_status mg_assemble_surplus_noalloc(const mg_eps_desc* eps, int dim, int n_cells, int s, double tau,
+                                      int64_t cell0, int64_t ncell, float* eps_c_out, uint8_t* cls_out,
+                                      float* surplus_out, void* cuda_stream);
+
 /* ---------------- serving ---------------- */
 
 typedef struct {

@@ -728,6 +728,11 @@ int min_s(const mg_problem* P) {
 
 }  // namespace
 
+namespace mg {
+// field descriptor of the C ABI to the device layout (used by other translation units)
+void eps_desc_to_dev(const mg_eps_desc& d, int dim, EpsDev* e) { fill_eps(d, dim, e); }
+}  // namespace mg
+
 // ====================================================================== C ABI
 extern "C" {
 

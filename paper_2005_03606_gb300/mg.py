@@ -98,6 +98,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_version": (ctypes.c_char_p, []),
             "mg_profile_kernel": (st, [_VP, ctypes.c_int, ctypes.c_int, _D]),
             "mg_launch_count": (ctypes.c_uint64, []),
+            "mg_assemble_surplus_noalloc": (st, [ctypes.POINTER(mg_eps_desc), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP,
+                                                 _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -262,6 +265,16 @@ class Problem:
         e = np.zeros_like(b)
         _check(load().mg_vcycle_apply(self.h, _p(b), _p(e)))
         return e
+
+
+def assemble_surplus_noalloc(field, dim: int, n_cells: int, s: int, cell0: int, ncell: int, eps_c_ptr: int,
+                             cls_ptr: int, surplus_ptr: int, tau: float = 1e-6, stream: Optional[int] = None) -> None:
+    """Allocation-free assembly of the stored mixed-precision cell data into
+    caller-owned device buffers (raw device pointers, e.g. torch tensors'
+    data_ptr()); see mg_assemble_surplus_noalloc in include/mg.h."""
+    e = eps_desc(field)
+    _check(load().mg_assemble_surplus_noalloc(ctypes.byref(e), dim, n_cells, s, float(tau), int(cell0), int(ncell),
+                                              eps_c_ptr, cls_ptr, surplus_ptr, stream))
 
 
 class Server:
