@@ -308,6 +308,17 @@ def run_probe(args, local_rank):
     import torch
     from paper_2005_03606_gb300 import mg
     torch.cuda.set_device(local_rank)
+    if args.probe == "solve":   # whole mixed delayed solves, for launch lists
+        w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED, n_cells=args.n)
+        ms = []
+        for _ in range(args.probe_reps):
+            with mg.Problem(d) as P:
+                t0 = time.perf_counter()
+                info = P.solve()
+                ms.append((time.perf_counter() - t0) * 1e3)
+        print(json.dumps({"probe": "solve", "workload": args.workload, "n_cells": w.n_cells, "ms": ms,
+                          "cycles": int(info.cycles), "publishes": int(info.publishes)}), flush=True)
+        return
     which = {"sweep": 0, "matvec": 1, "residual": 2, "galerkin": 3}[args.probe]
     path = mg.PATH_FP64_PLAIN if args.probe_fp64 else mg.PATH_MIXED_PLAIN
     w, d = workload_desc(mg, args.workload, path, n_cells=args.n)
@@ -336,7 +347,7 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=200,
                     help="cycle count used to scale the oracle sample in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin"],
+    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)
