@@ -104,6 +104,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- algorithmic bytes
+def sweep_traffic(workload):
+    """DRAM bytes per launch of the finest-level sweep from the committed ncu
+    summary, or None when that summary was taken on other source code or
+    another workload."""
+    import hashlib
+    import re
+    summ = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "sweep_geo4_fixup_boxes3d_243.md")
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2005_03606_gb300", "csrc", "sweep.cu")
+    if workload != "boxes3d" or not os.path.exists(summ):
+        return None
+    text = open(summ).read()
+    mt = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    mh = re.search(r"source-sha256\(paper_2005_03606_gb300/csrc/sweep.cu\):\s*([0-9a-f]{64})", text)
+    if not mt or not mh:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != mh.group(1):
+        return None
+    return int(mt.group(1))
+
+
 def sweep_bytes(dim, n, cells_by_class, mixed, vec_bytes):
     """Algorithmic DRAM bytes of one finest-level sweep: each vertex value read
     (x, b) and written (y) once, each cell's stored operator read once."""
@@ -290,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "sweep_jacobi_f32 (finest level, V-cycle smoother)",
                      "achieved": kernels["sweep_jacobi_f32"]["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": kernels["sweep_jacobi_f32"]["gbs"] / peak, "peak_kind": peak_kind,
-                     "traffic": None},
+                     "traffic": sweep_traffic(args.workload) if n == 243 else None},
         "kernels": kernels,
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(ctypes_sizeof_desc()),
                 "d2h_bytes_per_step": int(nvert * 8)},
