@@ -117,6 +117,11 @@ struct LevelOp {
   // compressed 3D finest level: vertices with an adjacent cell of class > 0
   const int* touched;     // vertex indices (nullptr: no split sweep)
   const int* ntouched;    // device count
+  // 27-point stencils of the first tcap touched vertices, SoA [27][tcap]:
+  // entry 13 is the diagonal, the others the off-diagonal couplings (the
+  // operator is applied in difference form, sum_k c_k (u_k - u_v))
+  float* tcoef;
+  int tcap;
 };
 
 // ------------------------------------------------------------ helpers

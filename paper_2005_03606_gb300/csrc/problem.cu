@@ -133,6 +133,7 @@ struct mg_problem {
   int* ntouched = nullptr;
   uint8_t* tflags = nullptr;
   uint32_t* tcounts = nullptr;
+  float* tcoef = nullptr;
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   int inner_its = 0;
@@ -860,9 +861,22 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
         (e = dalloc(P, &P->tflags, (size_t)l0.nvert)) != cudaSuccess ||
         (e = dalloc(P, &P->tcounts, sizeof(uint32_t) * (ng + (ng + 2047) / 2048 + 1))) != cudaSuccess)
       return fail(oom_or_cuda(e, "touched list"));
+    // stencil table for up to a quarter of the vertices (more touched vertices
+    // are recomputed from their cell records in the fix-up pass)
+    const long long ni = (long long)(P->N - 1) * (P->N - 1) * (P->N - 1);
+    long long cap = l0.nvert / 4 > 65536 ? l0.nvert / 4 : 65536;
+    cap = cap < ni ? cap : ni;
+    if (const char* ev = getenv("MG_STENCIL_CAP")) {   // smaller table (tests of the record path)
+      const long long c2 = atoll(ev);
+      if (c2 >= 1 && c2 < cap) cap = c2;
+    }
+    if ((e = dalloc(P, &P->tcoef, sizeof(float) * 27 * (size_t)cap)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "stencil table"));
     cudaMemsetAsync(P->ntouched, 0, sizeof(int), P->st);
     l0.op.touched = P->touched;
     l0.op.ntouched = P->ntouched;
+    l0.op.tcoef = P->tcoef;
+    l0.op.tcap = (int)cap;
   }
   // outer vectors
   const size_t v8 = sizeof(double) * l0.nvert;

@@ -108,6 +108,63 @@ __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, in
   *dg = dgs;
 }
 
+// The 27-point stencil of interior vertex (i, j, k) of a compressed 3D level
+// in FP32: c[ub] for the 26 neighbours ub = dx + 3 dy + 9 dz (the sum over the
+// cells that hold both vertices of eps_c K_ref h plus the decoded surplus) and
+// the diagonal in c[13].  Same terms as vertex_apply, gathered by neighbour.
+__device__ __forceinline__ void vertex_coeffs3(const LevelOp& op, int i, int j, int k, float (&c)[27]) {
+  constexpr int NV = 8;
+  const int N = op.N;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) c[q] = 0.f;
+  float dgs = 0.f;
+  const float hf = (float)op.hfac;
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz) {
+    const int cl = k - 1 + oz;
+    int ch = cl / op.layers;
+    ch = ch < op.nchunk ? ch : op.nchunk - 1;
+    const int ll = cl - ch * op.layers;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const int cy = j - 1 + oy;
+      const int row = ll * N + cy;
+      const int cbase = (cl * N + cy) * N;
+      const int segrow = row * op.nseg_x;
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox) {
+        const int cx = i - 1 + ox;
+        const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+        const float ge = __ldg(op.eps_c + cbase + cx) * hf;
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+          if (b == a) continue;
+          const double kv = kref_off<3>(popc_small(a ^ b));
+          if (kv == 0.0) continue;
+          const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + 9 * (oz + ((b >> 2) & 1));
+          c[ub] += ge * (float)kv;
+        }
+        dgs += ge * (float)kref_diag<3>();
+        const CmpChunk& ck = op.cmp[ch];
+        const int seg = segrow + (cx >> 5);
+        const int cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
+        if (cls) {
+          const uint8_t* rec = record_at<3>(ck, seg, cx & 31, cls);
+#pragma unroll
+          for (int b = 0; b < NV; ++b) {
+            if (b == a) continue;
+            const float dv = decode_entry<3>(rec, cls, pair_of(NV, a, b));
+            const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + 9 * (oz + ((b >> 2) & 1));
+            c[ub] += dv;
+            dgs -= dv;
+          }
+        }
+      }
+    }
+  }
+  c[13] = dgs;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
   for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -629,8 +686,10 @@ __global__ void __launch_bounds__(256, 2) sweep3_geo4(const LevelOp op, const fl
 }
 
 // Fix-up pass: vertices in op.touched (count *op.ntouched) recomputed with the
-// full operator (geometric part and decoded surplus).  For SW_MATVEC the
-// difference to the value the bulk pass wrote is added to the dot products.
+// full operator (geometric part and decoded surplus): from the precomputed
+// 27-point stencil for the first op.tcap of them, else from the cell records.
+// For SW_MATVEC the difference to the value the bulk pass wrote is added to
+// the dot products.
 template <int MODE>
 __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const float* __restrict__ x,
                                                     const float* __restrict__ b, float* __restrict__ y,
@@ -638,10 +697,10 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
   __shared__ double sh[2][8];
   const int N = op.N, n1 = N + 1;
   const int nt = *op.ntouched;
-  double d1 = 0.0;
+  const int cap = op.tcap;
+  float d1 = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     const int v = op.touched[t];
-    const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
     float u[27];
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
@@ -651,8 +710,19 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
         for (int dx = 0; dx < 3; ++dx)
           u[dx + 3 * dy + 9 * dz] = __ldg(x + (size_t)v + (dx - 1) + (dy - 1) * n1 + (size_t)(dz - 1) * n1 * n1);
     float Au, dg;
-    vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
     const float uv = u[13];
+    if (t < cap) {
+      const float* cf = op.tcoef + t;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 27; ++q)
+        if (q != 13) acc += __ldg(cf + (size_t)q * cap) * (u[q] - uv);
+      Au = acc;
+      dg = __ldg(cf + (size_t)13 * cap);
+    } else {
+      const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
+      vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
+    }
     if (MODE == SW_JACOBI) {
       y[v] = uv + omega * (b[v] - Au) / dg;
     } else if (MODE == SW_RESID) {
@@ -660,15 +730,29 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
     } else {
       const float qg = y[v];
       y[v] = Au;
-      d1 += (double)uv * ((double)Au - (double)qg);
+      d1 += uv * (Au - qg);
     }
   }
   if (MODE == SW_MATVEC) {
-    const double s1 = block_sum(d1, sh[0]);
+    const double s1 = block_sum((double)d1, sh[0]);
     if (threadIdx.x == 0) {
       partials[2 * blockIdx.x] = s1;
       partials[2 * blockIdx.x + 1] = 0.0;
     }
+  }
+}
+
+// stencils of the first min(*ntouched, tcap) touched vertices
+__global__ void touched_stencil_kernel(const LevelOp op) {
+  const int n1 = op.N + 1;
+  const int nt = min(*op.ntouched, op.tcap);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int v = op.touched[t];
+    const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
+    float c[27];
+    vertex_coeffs3(op, i, j, k, c);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) op.tcoef[(size_t)q * op.tcap + t] = c[q];
   }
 }
 
@@ -1081,6 +1165,10 @@ cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* co
   scan_add_kernel<<<(unsigned)ntiles, 1024, 0, st>>>(ng, counts, tile_tot);
   count_launches(1);
   touched_write_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts, list);
+  if (op.tcoef && op.tcap > 0) {
+    count_launches(1);
+    touched_stencil_kernel<<<152 * 8, 256, 0, st>>>(op);
+  }
   return launched();
 }
 

@@ -309,6 +309,105 @@ def test_full_size_mixed_assembly_sampled():
     assert 0.0 < (cls_all > 0).mean() < 0.5
 
 
+def _oracle_vertex_rows(fld, n, s, verts, x):
+    """(A x)_v and diag_v of the oracle's stored mixed operator at vertices
+    `verts` (flat indices), from the 2^3 cells around each vertex only."""
+    f = oracle.Field(fld)
+    n1 = n + 1
+    K = oracle.kref(3, n)
+    vi, vj, vk = verts % n1, (verts // n1) % n1, verts // (n1 * n1)
+    cells, where = [], []
+    for ox in range(2):
+        for oy in range(2):
+            for oz in range(2):
+                cx, cy, cz = vi - 1 + ox, vj - 1 + oy, vk - 1 + oz
+                cells.append((cz * n + cy) * n + cx)
+                where.append((ox, oy, oz))
+    uniq, inv = np.unique(np.concatenate(cells), return_inverse=True)
+    A = oracle.assemble_cells(f, n, s, uniq)
+    At = np.empty_like(A)
+    for t, c in enumerate(uniq):
+        cc = (c % n, (c // n) % n, c // (n * n))
+        ec = oracle.eps_at(f, [oracle.sample_coord(n, 1, cc[a], 0) for a in range(3)])
+        _, At[t], _ = oracle.compress_cell(3, A[t], ec, K, 1e-6)
+    inv = inv.reshape(8, -1)
+    Ax = np.zeros(len(verts))
+    dg = np.zeros(len(verts))
+    scale = np.zeros(len(verts))
+    for w, (ox, oy, oz) in enumerate(where):
+        a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2)
+        cx, cy, cz = vi - 1 + ox, vj - 1 + oy, vk - 1 + oz
+        M = At[inv[w]]
+        for bb in range(8):
+            xb = x[((cz + (bb >> 2)) * n1 + cy + ((bb >> 1) & 1)) * n1 + cx + (bb & 1)]
+            Ax += M[:, a, bb] * xb
+            scale += np.abs(M[:, a, bb] * xb)
+        dg += M[:, a, a]
+    return Ax, dg, scale
+
+
+def test_full_size_split_sweep_sampled():
+    # 243^3 boxes at s = 8: the FP32 geometric bulk pass + fix-up pass against
+    # the oracle's stored operator at sampled vertices (random ones and ones
+    # at a corner of a cell with a surplus record)
+    w = inputs.workload("boxes3d")
+    n = w.n_cells
+    n1 = n + 1
+    line = np.zeros(n1, bool)
+    line[1:n] = True
+    mask = (line[:, None, None] & line[None, :, None] & line[None, None, :]).reshape(-1)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(n1 ** 3) * mask
+    b = rng.standard_normal(n1 ** 3) * mask
+    with mg.Problem(mg.problem_desc(3, n, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,))) as P:
+        P.assemble(8)
+        y = P.apply(0, 0, x, b, inner=True)
+        jac = P.apply(0, 1, x, b, inner=True)
+        res = P.apply(0, 2, x, b, inner=True)
+        cls_all, _ = P.cell_data()
+    nz = np.flatnonzero(cls_all)
+    cz = rng.choice(nz, 150, replace=False)
+    near = ((cz // (n * n) + 1) * n1 + (cz // n) % n + 1) * n1 + cz % n + 1   # upper corner of the cell
+    verts = np.concatenate([rng.choice(np.flatnonzero(mask), 150, replace=False), near])
+    verts = verts[mask[verts]]
+    Ax, dg, scale = _oracle_vertex_rows(w.eps, n, 8, verts, x)
+    tol = 2e-5 * scale + 1e-7 * np.abs(Ax).max()
+    assert np.all(np.abs(y[verts] - Ax) <= tol)
+    assert np.all(np.abs(res[verts] - (b[verts] - Ax)) <= tol + 1e-6 * np.abs(b[verts]))
+    j_ref = x[verts] + 0.6 * (b[verts] - Ax) / dg
+    assert np.all(np.abs(jac[verts] - j_ref) <= 0.6 * (tol + 1e-6 * np.abs(b[verts])) / dg * 2 + 1e-6 * np.abs(j_ref))
+
+
+def test_split_sweep_record_path_matches_oracle(monkeypatch):
+    # a stencil table smaller than the touched list: the fix-up pass rebuilds
+    # the vertices beyond it from their cell records
+    dim, n, fld, s = 3, 27, inputs.boxes_field(3, 31), 4
+    stored = _stored_operator(mg.PATH_MIXED_PLAIN, fld, n, s)
+    rng = np.random.default_rng(5)
+    m = dense.interior_mask(dim, n)
+    x = rng.standard_normal((n + 1) ** dim) * m
+    b = rng.standard_normal((n + 1) ** dim) * m
+    y_ref = oracle.apply(dim, n, stored, x)
+    j_ref = oracle.jacobi(dim, n, stored, b, x, 0.6)
+    scale = np.abs(stored).max() * np.abs(x).max() * (1 << dim) * 8
+    tol32 = 1e-6 * scale + 1e-5 * scale
+    dmin = np.abs(oracle.diag(dim, n, stored)[m]).min()
+    outs = []
+    for cap in ("64", None):
+        if cap:
+            monkeypatch.setenv("MG_STENCIL_CAP", cap)
+        else:
+            monkeypatch.delenv("MG_STENCIL_CAP", raising=False)
+        with mg.Problem(mg.problem_desc(dim, n, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(s,))) as P:
+            P.assemble(s)
+            y = P.apply(0, 0, x, b, inner=True)
+            jac = P.apply(0, 1, x, b, inner=True)
+        assert np.abs(y - y_ref).max() <= tol32
+        assert np.abs(jac - j_ref).max() <= 0.6 * (tol32 / dmin) * 4 + 1e-6 * np.abs(j_ref).max()
+        outs.append(y)
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * scale
+
+
 def test_serving_results_alone_and_in_mix_agree():
     reqs = [(3, 27, inputs.fourier_field(3, 101, sigma=0.7)), (2, 243, inputs.fourier_field(2, 102, sigma=1.5)),
             (3, 81, inputs.fourier_field(3, 103, sigma=1.0)), (2, 81, inputs.fourier_field(2, 104, sigma=2.0)),
