@@ -541,14 +541,22 @@ __global__ void __launch_bounds__(kTX * kTY, 3) sweep3_stream(const LevelOp op, 
 //      eps_c K_ref h to every interior vertex, and
 //  (2) a fix-up pass over the list of vertices touched by a cell with a
 //      surplus record, which recomputes those vertices with every term.
-// The bulk pass is bound by load instructions rather than DRAM bytes, so it
-// is shaped to issue few of them: a thread owns 4 consecutive vertices in x
-// (rows of (N+1) floats with (N+1) % 4 == 0 keep float4 loads aligned) and
-// walks kGZ vertex planes along z with the u rows of planes k-1..k+1 and the
-// eps of cell layers k-1, k held in registers; plane k+2 and layer k+1 are
-// loaded one plane ahead.  Per 4 vertices and plane: 3 float4 + 6 scalar u
-// loads, 10 eps loads, one float4 b load and one float4 y store.
+//
+// Bulk pass arithmetic.  The trilinear reference matrix satisfies
+// 12 K_ref = 5 I + E - J (E: adjacency along cell edges, J: all ones), so
+//   (A u)_v = h/12 [ 5 u_v G_v + sum_{6 axis neighbours w} W_vw u_w - sum_c eps_c T_c ]
+// with G_v the sum of eps over the 8 cells at v, W_vw the sum of eps over the
+// 4 cells that share the edge vw, and T_c the sum of u over the 8 vertices of
+// cell c.  Cell sums are built separably (pairs along x, then y, then z) and
+// shared by the 4 vertices of a thread and by consecutive planes of its z
+// march, so a vertex costs about a third of the per-cell form's arithmetic.
+//
+// Layout: a thread owns 4 consecutive vertices in x (rows of (N+1) floats with
+// (N+1) % 4 == 0 keep float4 loads aligned) of row j and walks kGZ planes in
+// z, loading the next plane's three u rows, eps rows and b one plane ahead.
+// Blocks loop over (x, y, z-run) tiles (persistent grid, no wave tail).
 constexpr int kGZ = 16;
+constexpr int kGeoBX = 32, kGeoBY = 8;
 
 struct Rows6 {   // x[q-1], x[q..q+3], x[q+4] of three rows j-1, j, j+1
   float v[3][6];
@@ -569,118 +577,157 @@ __device__ __forceinline__ void load_rows6(const float* __restrict__ x, size_t r
   }
 }
 
+// eps of the 5 cells x = q-1 .. q+3 of cell rows j-1 (r = 0) and j (r = 1) of
+// layer l; cells outside the grid read 0 (they only reach boundary vertices)
+__device__ __forceinline__ void load_eps10(const float* __restrict__ eps, int N, int l, int j, int q,
+                                           bool has_left, bool has_right, float (&g)[2][5]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float* e = eps + ((size_t)l * N + (j - 1 + r)) * N + q;
+    g[r][0] = has_left ? __ldg(e - 1) : 0.f;
+    g[r][1] = __ldg(e);
+    g[r][2] = __ldg(e + 1);
+    g[r][3] = __ldg(e + 2);
+    g[r][4] = has_right ? __ldg(e + 3) : 0.f;
+  }
+}
+
+// Py[r][c] = sum of u over the 4 vertices (x, x+1) x (row r, row r+1) of plane rows
+__device__ __forceinline__ void pair_sums(const Rows6& u, float (&py)[2][5]) {
+  float px[3][5];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) px[r][c] = u.v[r][c] + u.v[r][c + 1];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) py[r][c] = px[r][c] + px[r + 1][c];
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
-                                                      const float* __restrict__ b, float* __restrict__ y,
-                                                      float omega, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
+                                                                  const float* __restrict__ b,
+                                                                  float* __restrict__ y, float omega,
+                                                                  double* __restrict__ partials, int ntx, int nty,
+                                                                  int ntiles) {
   __shared__ double sh[2][8];
   const int N = op.N, n1 = N + 1;
-  const int qx = blockIdx.x * blockDim.x + threadIdx.x;   // quad: vertices 4 qx .. 4 qx + 3
-  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-  const int k0 = 1 + blockIdx.z * kGZ;
-  const int k1 = min(N - 1, k0 + kGZ - 1);
-  const int q = 4 * qx;
-  const bool active = q < n1 && j < N && k0 <= k1;
-  // per-thread partial dot products in FP32 (a few dozen terms; they only set
-  // the Krylov step lengths), summed over the block in FP64
+  const size_t plane = (size_t)n1 * n1;
+  const float h12 = -op.gk32;   // h / 12
+  const float h3 = 4.f * h12;   // h / 3
+  // per-thread partial dot products in FP32 (a few hundred terms; they only
+  // set the Krylov step lengths), summed over the block in FP64
   float d1 = 0.f, d2 = 0.f;
-  if (active) {
-    const size_t plane = (size_t)n1 * n1;
-    const bool has_left = q > 0, has_right = q + 4 <= N;
-    const float gscale = op.gk32;
-    // eps of the 5 cells x = q-1 .. q+3 of rows j-1, j of layer l
-    auto load_eps = [&](int l, float (&g)[2][5]) {
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const float* e = op.eps_c + ((size_t)l * N + (j - 1 + r)) * N;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          const int cx = q - 1 + c;
-          g[r][c] = (cx >= 0 && cx < N) ? __ldg(e + cx) : 0.f;
-        }
-      }
-    };
-    Rows6 um, uc, up;
-    float gm[2][5], gc[2][5];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int q = 4 * (tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
+    const int j = 1 + ty * kGeoBY + threadIdx.y;
+    const int k0 = 1 + tz * kGZ;
+    const int k1 = min(N - 1, k0 + kGZ - 1);
+    if (q >= n1 || j >= N || k0 > k1) continue;
+    const bool hl = q > 0, hr = q + 4 <= N;
     const size_t row0 = (size_t)j * n1;
-    load_rows6(x, (size_t)(k0 - 1) * plane + row0, n1, q, has_left, has_right, um);
-    load_rows6(x, (size_t)k0 * plane + row0, n1, q, has_left, has_right, uc);
-    load_rows6(x, (size_t)(k0 + 1) * plane + row0, n1, q, has_left, has_right, up);
-    load_eps(k0 - 1, gm);
-    load_eps(k0, gc);
-    float4 bcur = __ldg(reinterpret_cast<const float4*>(b + (size_t)k0 * plane + row0 + q));
+    // prologue: planes k0-1, k0 (sums), k0+1 (rows); eps layers k0-1, k0
+    Rows6 uc, un;
+    float pyc[2][5], gm[2][5], gc[2][5], yTm[5];
+    {
+      Rows6 um;
+      float pym[2][5];
+      load_rows6(x, (size_t)(k0 - 1) * plane + row0, n1, q, hl, hr, um);
+      load_rows6(x, (size_t)k0 * plane + row0, n1, q, hl, hr, uc);
+      load_eps10(op.eps_c, N, k0 - 1, j, q, hl, hr, gm);
+      pair_sums(um, pym);
+      pair_sums(uc, pyc);
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        yTm[c] = gm[0][c] * (pym[0][c] + pyc[0][c]) + gm[1][c] * (pym[1][c] + pyc[1][c]);
+    }
+    load_rows6(x, (size_t)(k0 + 1) * plane + row0, n1, q, hl, hr, un);
+    load_eps10(op.eps_c, N, k0, j, q, hl, hr, gc);
+    float4 bc = __ldg(reinterpret_cast<const float4*>(b + (size_t)k0 * plane + row0 + q));
+#pragma unroll 1
     for (int k = k0; k <= k1; ++k) {
-      // one plane ahead
-      Rows6 un;
+      // one plane ahead: u rows of plane k+2, eps of layer k+1, b of plane k+1
+      Rows6 unn;
       float gn[2][5];
-      float4 bn = make_float4(0, 0, 0, 0);
-      const bool more = k + 1 <= k1;
-      if (more) {
-        load_rows6(x, (size_t)(k + 2) * plane + row0, n1, q, has_left, has_right, un);
-        load_eps(k + 1, gn);
+      float4 bn = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k + 1 <= k1) {
+        load_rows6(x, (size_t)(k + 2) * plane + row0, n1, q, hl, hr, unn);
+        load_eps10(op.eps_c, N, k + 1, j, q, hl, hr, gn);
         bn = __ldg(reinterpret_cast<const float4*>(b + (size_t)(k + 1) * plane + row0 + q));
       }
+      // layer k: cell sums T = Py(k) + Py(k+1), weighted by eps and summed over the two cell rows
+      float pyn[2][5], yTc[5];
+      pair_sums(un, pyn);
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        yTc[c] = gc[0][c] * (pyc[0][c] + pyn[0][c]) + gc[1][c] * (pyc[1][c] + pyn[1][c]);
+      // eps sums: per cell row over layers k-1, k (ez), per column (ey), per layer over rows (el)
+      float ez[2][5], ey[5], elm[5], elc[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        ez[0][c] = gm[0][c] + gc[0][c];
+        ez[1][c] = gm[1][c] + gc[1][c];
+        ey[c] = ez[0][c] + ez[1][c];
+        elm[c] = gm[0][c] + gm[1][c];
+        elc[c] = gc[0][c] + gc[1][c];
+      }
+      const float bb4[4] = {bc.x, bc.y, bc.z, bc.w};
+      // plane k-1, row j (read two planes ago: an L1/L2 hit)
+      const float4 m4 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(k - 1) * plane + row0 + q));
+      const float um1[4] = {m4.x, m4.y, m4.z, m4.w};
       float out[4];
-      const float bb4[4] = {bcur.x, bcur.y, bcur.z, bcur.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        // vertex i = q + e: u column offset e + 1 in the rows, cells c = e (x = i-1) and e + 1 (x = i)
-        const float ua = uc.v[1][e + 1];
-        float ag = 0.f, gs = 0.f;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-          const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
-          const float gv = oz ? gc[oy][e + ox] : gm[oy][e + ox];
-          float s4 = 0.f;
-#pragma unroll
-          for (int bb = 0; bb < 8; ++bb)
-            if (bb != a && popc_small(a ^ bb) >= 2) {
-              const int pz = oz + ((bb >> 2) & 1);
-              const int ry = oy + ((bb >> 1) & 1);
-              const int cx = e + ox + (bb & 1);   // column in the 6-wide rows
-              s4 += pz == 0 ? um.v[ry][cx] : (pz == 1 ? uc.v[ry][cx] : up.v[ry][cx]);
-            }
-          ag += gv * (s4 - 4.f * ua);
-          gs += gv;
-        }
-        const float acc = ag * gscale;
-        const float dg = -4.f * gscale * gs;
+        const float uv = uc.v[1][e + 1];
+        const float G = ey[e] + ey[e + 1];
+        const float ST = (yTm[e] + yTm[e + 1]) + (yTc[e] + yTc[e + 1]);
+        float w = 5.f * uv * G - ST;
+        w = fmaf(ey[e], uc.v[1][e], w);                                      // x - 1
+        w = fmaf(ey[e + 1], uc.v[1][e + 2], w);                              // x + 1
+        w = fmaf(ez[0][e] + ez[0][e + 1], uc.v[0][e + 1], w);                // y - 1
+        w = fmaf(ez[1][e] + ez[1][e + 1], uc.v[2][e + 1], w);                // y + 1
+        w = fmaf(elm[e] + elm[e + 1], um1[e], w);                            // z - 1
+        w = fmaf(elc[e] + elc[e + 1], un.v[1][e + 1], w);                    // z + 1
+        const float acc = h12 * w;
         const int i = q + e;
         const bool valid = i >= 1 && i <= N - 1;
         float r;
-        if (MODE == SW_JACOBI) r = ua + omega * __fdividef(bb4[e] - acc, dg);
+        if (MODE == SW_JACOBI) r = uv + omega * __fdividef(bb4[e] - acc, h3 * G);
         else if (MODE == SW_RESID) r = bb4[e] - acc;
         else {
           r = acc;
           if (valid) {
-            d1 += ua * acc;
-            d2 += ua * bb4[e];
+            d1 += uv * acc;
+            d2 += uv * bb4[e];
           }
         }
         out[e] = valid ? r : 0.f;   // boundary vertices stay zero
       }
       *reinterpret_cast<float4*>(y + (size_t)k * plane + row0 + q) = make_float4(out[0], out[1], out[2], out[3]);
-      um = uc;
-      uc = up;
-      up = un;
+      // advance one plane
+      uc = un;
+      un = unn;
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          gm[r][c] = gc[r][c];
-          gc[r][c] = gn[r][c];
-        }
-      bcur = bn;
+      for (int c = 0; c < 5; ++c) {
+        pyc[0][c] = pyn[0][c];
+        pyc[1][c] = pyn[1][c];
+        yTm[c] = yTc[c];
+        gm[0][c] = gc[0][c];
+        gm[1][c] = gc[1][c];
+        gc[0][c] = gn[0][c];
+        gc[1][c] = gn[1][c];
+      }
+      bc = bn;
     }
   }
   if (MODE == SW_MATVEC) {
     const double s1 = block_sum((double)d1, sh[0]);
     const double s2 = block_sum((double)d2, sh[1]);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-      partials[2 * blk] = s1;
-      partials[2 * blk + 1] = s2;
+      partials[2 * blockIdx.x] = s1;
+      partials[2 * blockIdx.x + 1] = s2;
     }
   }
 }
@@ -862,20 +909,30 @@ __global__ void touched_write_kernel(long long nv, const uint8_t* __restrict__ f
 cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
                         double* partials, int* nblocks, cudaStream_t st) {
   const int nq = (op.N + 1) / 4;
-  dim3 blk(32, 8, 1);
-  dim3 grd((nq + 31) / 32, (op.N - 1 + 7) / 8, (op.N - 1 + kGZ - 1) / kGZ);
-  const int nb_bulk = (int)(grd.x * grd.y * grd.z);
+  const int ntx = (nq + kGeoBX - 1) / kGeoBX, nty = (op.N - 1 + kGeoBY - 1) / kGeoBY;
+  const int ntz = (op.N - 1 + kGZ - 1) / kGZ;
+  const int ntiles = ntx * nty * ntz;
+  // persistent grid: the resident blocks of all SMs (two per SM by the launch bounds)
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  const int nb_bulk = ntiles < 2 * nsm ? ntiles : 2 * nsm;
+  const dim3 blk(kGeoBX, kGeoBY, 1);
   double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
   if (mode == SW_JACOBI) {
-    sweep3_geo4<SW_JACOBI><<<grd, blk, 0, st>>>(op, x, b, y, omega, partials);
+    sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_JACOBI><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else if (mode == SW_RESID) {
-    sweep3_geo4<SW_RESID><<<grd, blk, 0, st>>>(op, x, b, y, omega, partials);
+    sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else {
-    sweep3_geo4<SW_MATVEC><<<grd, blk, 0, st>>>(op, x, b, y, omega, partials);
+    sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   }
