@@ -605,6 +605,79 @@ __device__ __forceinline__ void pair_sums(const Rows6& u, float (&py)[2][5]) {
     for (int c = 0; c < 5; ++c) py[r][c] = px[r][c] + px[r + 1][c];
 }
 
+struct GeoCtx {
+  const float* x;
+  const float* b;
+  float* y;
+  const float* eps;
+  int N, n1, q, j;
+  size_t plane, row0;
+  bool hl, hr;
+  float h12, h3, omega;
+};
+
+// One plane k of the bulk pass.  In: u rows of plane k (uc), their pair sums
+// (pyc), eps of cell layer k-1 (gm) and its eps-weighted cell sums (yTm).
+// Out: the same quantities one plane up (un, pyn, gc, yTc), loaded or formed
+// here, so that a two-step unrolled loop swaps roles instead of copying.
+template <int MODE>
+__device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc, Rows6& un,
+                                         const float (&pyc)[2][5], float (&pyn)[2][5], const float (&gm)[2][5],
+                                         float (&gc)[2][5], const float (&yTm)[5], float (&yTc)[5], float& d1,
+                                         float& d2) {
+  load_rows6(c.x, (size_t)(k + 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, un);
+  load_eps10(c.eps, c.N, k, c.j, c.q, c.hl, c.hr, gc);
+  const float4 b4 = __ldg(reinterpret_cast<const float4*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
+  // plane k-1, row j (read two planes ago: an L1/L2 hit)
+  const float4 m4 = __ldg(reinterpret_cast<const float4*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
+  // layer k: cell sums T = Py(k) + Py(k+1), weighted by eps and summed over the two cell rows
+  pair_sums(un, pyn);
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    yTc[i] = gc[0][i] * (pyc[0][i] + pyn[0][i]) + gc[1][i] * (pyc[1][i] + pyn[1][i]);
+  // eps sums: per cell row over layers k-1, k (ez), per column (ey), per layer over rows (el)
+  float ez[2][5], ey[5], elm[5], elc[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    ez[0][i] = gm[0][i] + gc[0][i];
+    ez[1][i] = gm[1][i] + gc[1][i];
+    ey[i] = ez[0][i] + ez[1][i];
+    elm[i] = gm[0][i] + gm[1][i];
+    elc[i] = gc[0][i] + gc[1][i];
+  }
+  const float bb4[4] = {b4.x, b4.y, b4.z, b4.w};
+  const float um1[4] = {m4.x, m4.y, m4.z, m4.w};
+  float out[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float uv = uc.v[1][e + 1];
+    const float G = ey[e] + ey[e + 1];
+    const float ST = (yTm[e] + yTm[e + 1]) + (yTc[e] + yTc[e + 1]);
+    float w = 5.f * uv * G - ST;
+    w = fmaf(ey[e], uc.v[1][e], w);                         // x - 1
+    w = fmaf(ey[e + 1], uc.v[1][e + 2], w);                 // x + 1
+    w = fmaf(ez[0][e] + ez[0][e + 1], uc.v[0][e + 1], w);   // y - 1
+    w = fmaf(ez[1][e] + ez[1][e + 1], uc.v[2][e + 1], w);   // y + 1
+    w = fmaf(elm[e] + elm[e + 1], um1[e], w);               // z - 1
+    w = fmaf(elc[e] + elc[e + 1], un.v[1][e + 1], w);       // z + 1
+    const float acc = c.h12 * w;
+    const int i = c.q + e;
+    const bool valid = i >= 1 && i <= c.N - 1;
+    float r;
+    if (MODE == SW_JACOBI) r = uv + c.omega * __fdividef(bb4[e] - acc, c.h3 * G);
+    else if (MODE == SW_RESID) r = bb4[e] - acc;
+    else {
+      r = acc;
+      if (valid) {
+        d1 += uv * acc;
+        d2 += uv * bb4[e];
+      }
+    }
+    out[e] = valid ? r : 0.f;   // boundary vertices stay zero
+  }
+  *reinterpret_cast<float4*>(c.y + (size_t)k * c.plane + c.row0 + c.q) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
                                                                   const float* __restrict__ b,
@@ -612,114 +685,44 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
                                                                   double* __restrict__ partials, int ntx, int nty,
                                                                   int ntiles) {
   __shared__ double sh[2][8];
-  const int N = op.N, n1 = N + 1;
-  const size_t plane = (size_t)n1 * n1;
-  const float h12 = -op.gk32;   // h / 12
-  const float h3 = 4.f * h12;   // h / 3
+  GeoCtx c;
+  c.x = x;
+  c.b = b;
+  c.y = y;
+  c.eps = op.eps_c;
+  c.N = op.N;
+  c.n1 = op.N + 1;
+  c.plane = (size_t)c.n1 * c.n1;
+  c.h12 = -op.gk32;   // h / 12
+  c.h3 = 4.f * c.h12;   // h / 3
+  c.omega = omega;
   // per-thread partial dot products in FP32 (a few hundred terms; they only
   // set the Krylov step lengths), summed over the block in FP64
   float d1 = 0.f, d2 = 0.f;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    const int q = 4 * (tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
-    const int j = 1 + ty * kGeoBY + threadIdx.y;
+    c.q = 4 * (tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
+    c.j = 1 + ty * kGeoBY + threadIdx.y;
     const int k0 = 1 + tz * kGZ;
-    const int k1 = min(N - 1, k0 + kGZ - 1);
-    if (q >= n1 || j >= N || k0 > k1) continue;
-    const bool hl = q > 0, hr = q + 4 <= N;
-    const size_t row0 = (size_t)j * n1;
-    // prologue: planes k0-1, k0 (sums), k0+1 (rows); eps layers k0-1, k0
-    Rows6 uc, un;
-    float pyc[2][5], gm[2][5], gc[2][5], yTm[5];
-    {
-      Rows6 um;
-      float pym[2][5];
-      load_rows6(x, (size_t)(k0 - 1) * plane + row0, n1, q, hl, hr, um);
-      load_rows6(x, (size_t)k0 * plane + row0, n1, q, hl, hr, uc);
-      load_eps10(op.eps_c, N, k0 - 1, j, q, hl, hr, gm);
-      pair_sums(um, pym);
-      pair_sums(uc, pyc);
+    const int k1 = min(c.N - 1, k0 + kGZ - 1);
+    if (c.q >= c.n1 || c.j >= c.N || k0 > k1) continue;
+    c.hl = c.q > 0;
+    c.hr = c.q + 4 <= c.N;
+    c.row0 = (size_t)c.j * c.n1;
+    // prologue: rows and pair sums of plane k0, eps and weighted cell sums of layer k0-1
+    Rows6 ua, ub;
+    float pa[2][5], pb[2][5], ga[2][5], gb[2][5], ta[5], tb[5];
+    load_rows6(x, (size_t)(k0 - 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, ub);
+    load_rows6(x, (size_t)k0 * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, ua);
+    load_eps10(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr, ga);
+    pair_sums(ub, pb);
+    pair_sums(ua, pa);
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
-        yTm[c] = gm[0][c] * (pym[0][c] + pyc[0][c]) + gm[1][c] * (pym[1][c] + pyc[1][c]);
-    }
-    load_rows6(x, (size_t)(k0 + 1) * plane + row0, n1, q, hl, hr, un);
-    load_eps10(op.eps_c, N, k0, j, q, hl, hr, gc);
-    float4 bc = __ldg(reinterpret_cast<const float4*>(b + (size_t)k0 * plane + row0 + q));
-#pragma unroll 1
-    for (int k = k0; k <= k1; ++k) {
-      // one plane ahead: u rows of plane k+2, eps of layer k+1, b of plane k+1
-      Rows6 unn;
-      float gn[2][5];
-      float4 bn = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k + 1 <= k1) {
-        load_rows6(x, (size_t)(k + 2) * plane + row0, n1, q, hl, hr, unn);
-        load_eps10(op.eps_c, N, k + 1, j, q, hl, hr, gn);
-        bn = __ldg(reinterpret_cast<const float4*>(b + (size_t)(k + 1) * plane + row0 + q));
-      }
-      // layer k: cell sums T = Py(k) + Py(k+1), weighted by eps and summed over the two cell rows
-      float pyn[2][5], yTc[5];
-      pair_sums(un, pyn);
-#pragma unroll
-      for (int c = 0; c < 5; ++c)
-        yTc[c] = gc[0][c] * (pyc[0][c] + pyn[0][c]) + gc[1][c] * (pyc[1][c] + pyn[1][c]);
-      // eps sums: per cell row over layers k-1, k (ez), per column (ey), per layer over rows (el)
-      float ez[2][5], ey[5], elm[5], elc[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        ez[0][c] = gm[0][c] + gc[0][c];
-        ez[1][c] = gm[1][c] + gc[1][c];
-        ey[c] = ez[0][c] + ez[1][c];
-        elm[c] = gm[0][c] + gm[1][c];
-        elc[c] = gc[0][c] + gc[1][c];
-      }
-      const float bb4[4] = {bc.x, bc.y, bc.z, bc.w};
-      // plane k-1, row j (read two planes ago: an L1/L2 hit)
-      const float4 m4 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(k - 1) * plane + row0 + q));
-      const float um1[4] = {m4.x, m4.y, m4.z, m4.w};
-      float out[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float uv = uc.v[1][e + 1];
-        const float G = ey[e] + ey[e + 1];
-        const float ST = (yTm[e] + yTm[e + 1]) + (yTc[e] + yTc[e + 1]);
-        float w = 5.f * uv * G - ST;
-        w = fmaf(ey[e], uc.v[1][e], w);                                      // x - 1
-        w = fmaf(ey[e + 1], uc.v[1][e + 2], w);                              // x + 1
-        w = fmaf(ez[0][e] + ez[0][e + 1], uc.v[0][e + 1], w);                // y - 1
-        w = fmaf(ez[1][e] + ez[1][e + 1], uc.v[2][e + 1], w);                // y + 1
-        w = fmaf(elm[e] + elm[e + 1], um1[e], w);                            // z - 1
-        w = fmaf(elc[e] + elc[e + 1], un.v[1][e + 1], w);                    // z + 1
-        const float acc = h12 * w;
-        const int i = q + e;
-        const bool valid = i >= 1 && i <= N - 1;
-        float r;
-        if (MODE == SW_JACOBI) r = uv + omega * __fdividef(bb4[e] - acc, h3 * G);
-        else if (MODE == SW_RESID) r = bb4[e] - acc;
-        else {
-          r = acc;
-          if (valid) {
-            d1 += uv * acc;
-            d2 += uv * bb4[e];
-          }
-        }
-        out[e] = valid ? r : 0.f;   // boundary vertices stay zero
-      }
-      *reinterpret_cast<float4*>(y + (size_t)k * plane + row0 + q) = make_float4(out[0], out[1], out[2], out[3]);
-      // advance one plane
-      uc = un;
-      un = unn;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        pyc[0][c] = pyn[0][c];
-        pyc[1][c] = pyn[1][c];
-        yTm[c] = yTc[c];
-        gm[0][c] = gc[0][c];
-        gm[1][c] = gc[1][c];
-        gc[0][c] = gn[0][c];
-        gc[1][c] = gn[1][c];
-      }
-      bc = bn;
+    for (int i = 0; i < 5; ++i) ta[i] = ga[0][i] * (pb[0][i] + pa[0][i]) + ga[1][i] * (pb[1][i] + pa[1][i]);
+    for (int k = k0; k <= k1; k += 2) {
+      geo_step<MODE>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
+      if (k + 1 > k1) break;
+      geo_step<MODE>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
     }
   }
   if (MODE == SW_MATVEC) {
