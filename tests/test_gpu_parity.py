@@ -378,9 +378,11 @@ def test_full_size_split_sweep_sampled():
     assert np.all(np.abs(jac[verts] - j_ref) <= 0.6 * (tol + 1e-6 * np.abs(b[verts])) / dg * 2 + 1e-6 * np.abs(j_ref))
 
 
-def test_split_sweep_record_path_matches_oracle(monkeypatch):
-    # a stencil table smaller than the touched list: the fix-up pass rebuilds
-    # the vertices beyond it from their cell records
+@pytest.mark.parametrize("env", [{"MG_STENCIL_CAP": "64"}, {"MG_NO_TMA": "1"}, {}])
+def test_split_sweep_variants_match_oracle(monkeypatch, env):
+    # the split FP32 sweep with a stencil table smaller than the touched list
+    # (the fix-up pass rebuilds the vertices beyond it from their cell records),
+    # with the register-only bulk pass instead of the TMA-staged one, and as built
     dim, n, fld, s = 3, 27, inputs.boxes_field(3, 31), 4
     stored = _stored_operator(mg.PATH_MIXED_PLAIN, fld, n, s)
     rng = np.random.default_rng(5)
@@ -389,23 +391,22 @@ def test_split_sweep_record_path_matches_oracle(monkeypatch):
     b = rng.standard_normal((n + 1) ** dim) * m
     y_ref = oracle.apply(dim, n, stored, x)
     j_ref = oracle.jacobi(dim, n, stored, b, x, 0.6)
+    r_ref = oracle.residual(dim, n, stored, b, x)
     scale = np.abs(stored).max() * np.abs(x).max() * (1 << dim) * 8
     tol32 = 1e-6 * scale + 1e-5 * scale
     dmin = np.abs(oracle.diag(dim, n, stored)[m]).min()
-    outs = []
-    for cap in ("64", None):
-        if cap:
-            monkeypatch.setenv("MG_STENCIL_CAP", cap)
-        else:
-            monkeypatch.delenv("MG_STENCIL_CAP", raising=False)
-        with mg.Problem(mg.problem_desc(dim, n, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(s,))) as P:
-            P.assemble(s)
-            y = P.apply(0, 0, x, b, inner=True)
-            jac = P.apply(0, 1, x, b, inner=True)
-        assert np.abs(y - y_ref).max() <= tol32
-        assert np.abs(jac - j_ref).max() <= 0.6 * (tol32 / dmin) * 4 + 1e-6 * np.abs(j_ref).max()
-        outs.append(y)
-    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * scale
+    for k in ("MG_STENCIL_CAP", "MG_NO_TMA"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(s,))) as P:
+        P.assemble(s)
+        y = P.apply(0, 0, x, b, inner=True)
+        jac = P.apply(0, 1, x, b, inner=True)
+        res = P.apply(0, 2, x, b, inner=True)
+    assert np.abs(y - y_ref).max() <= tol32
+    assert np.abs(res - r_ref).max() <= tol32 + 1e-6 * np.abs(b).max()
+    assert np.abs(jac - j_ref).max() <= 0.6 * (tol32 / dmin) * 4 + 1e-6 * np.abs(j_ref).max()
 
 
 def test_serving_results_alone_and_in_mix_agree():
