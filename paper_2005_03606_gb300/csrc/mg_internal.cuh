@@ -122,10 +122,6 @@ struct LevelOp {
   // operator is applied in difference form, sum_k c_k (u_k - u_v))
   float* tcoef;
   int tcap;
-  // TMA-staged bulk pass: eps_c with rows padded to N+1 floats (zero pad), and
-  // a device error word set when a pipeline wait times out (nullptr: unused)
-  const float* eps_pad;
-  int* err;
 };
 
 // ------------------------------------------------------------ helpers
@@ -240,11 +236,6 @@ cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, 
 cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
-// bulk_tma.cu
-bool geo_bulk_tma_usable(const LevelOp& op, const void* x, const void* b);
-cudaError_t launch_geo_bulk_tma(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
-                                double* partials, int* nblocks, cudaStream_t st);
-cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream_t st);
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
                                  cudaStream_t st);
 

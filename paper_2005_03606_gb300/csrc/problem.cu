@@ -134,8 +134,6 @@ struct mg_problem {
   uint8_t* tflags = nullptr;
   uint32_t* tcounts = nullptr;
   float* tcoef = nullptr;
-  float* eps_pad = nullptr;
-  int* dev_err = nullptr;
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   int inner_its = 0;
@@ -879,15 +877,6 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     l0.op.ntouched = P->ntouched;
     l0.op.tcoef = P->tcoef;
     l0.op.tcap = (int)cap;
-    // TMA-staged bulk pass: padded copy of eps_c and the pipeline error word
-    if (!getenv("MG_NO_TMA")) {
-      if ((e = dalloc(P, &P->eps_pad, sizeof(float) * (size_t)P->N * P->N * (P->N + 1))) != cudaSuccess ||
-          (e = dalloc(P, &P->dev_err, sizeof(int))) != cudaSuccess)
-        return fail(oom_or_cuda(e, "padded eps"));
-      cudaMemsetAsync(P->dev_err, 0, sizeof(int), P->st);
-      l0.op.eps_pad = P->eps_pad;
-      l0.op.err = P->dev_err;
-    }
   }
   // outer vectors
   const size_t v8 = sizeof(double) * l0.nvert;
@@ -947,8 +936,6 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   }
   // cell-centre eps and the geometric (s = 1) operator
   if (!cuda_ok(launch_eps_centre(D, P->N, &P->eps, P->mixed ? 0 : 1, P->eps_c, P->st), "eps centre"))
-    return fail(MG_ERR_CUDA);
-  if (P->eps_pad && !cuda_ok(launch_pad_eps(P->N, (const float*)P->eps_c, P->eps_pad, P->st), "padded eps"))
     return fail(MG_ERR_CUDA);
   for (int c = 0; c < P->nchunk; ++c) {
     ChunkStore cs;
@@ -1185,16 +1172,6 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   }
   if (result == MG_OK && rel > 2.0 * d.rtol) result = MG_ERR_NOT_CONVERGED;
   if (result == MG_ERR_NOT_CONVERGED) set_error("not converged: rel residual %.3e after %d cycles", rel, P->cycles);
-  if (P->dev_err) {   // a pipelined sweep gave up waiting for its data: the iterates are not trustworthy
-    int h_err = 0;
-    MG_CHECK(cudaMemcpyAsync(&h_err, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
-    MG_CHECK(cudaStreamSynchronize(P->st));
-    if (h_err) {
-      result = MG_ERR_TIMEOUT;
-      set_error("a pipelined sweep timed out waiting for its staged data");
-      MG_CHECK(cudaMemsetAsync(P->dev_err, 0, sizeof(int), P->st));
-    }
-  }
   if (info) {
     memset(info, 0, sizeof(*info));
     info->status = result;

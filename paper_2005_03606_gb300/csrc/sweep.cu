@@ -925,28 +925,21 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   }
   const int nb_bulk = ntiles < 2 * nsm ? ntiles : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
-  int nb = nb_bulk;
-  cudaError_t e = cudaSuccess;
-  const bool tma = geo_bulk_tma_usable(op, x, b);
-  if (tma) {
-    e = launch_geo_bulk_tma(op, mode, x, b, y, omega, partials, &nb, st);
-    if (e != cudaSuccess) return e;
-  }
-  double* pfix = partials ? partials + 2 * (size_t)nb : nullptr;
+  double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
   if (mode == SW_JACOBI) {
-    if (!tma) sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
+    sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_JACOBI><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else if (mode == SW_RESID) {
-    if (!tma) sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
+    sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else {
-    if (!tma) sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
+    sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   }
-  if (nblocks) *nblocks = nb + kFixBlocks;
+  if (nblocks) *nblocks = nb_bulk + kFixBlocks;
   return launched();
 }
 

@@ -378,11 +378,11 @@ def test_full_size_split_sweep_sampled():
     assert np.all(np.abs(jac[verts] - j_ref) <= 0.6 * (tol + 1e-6 * np.abs(b[verts])) / dg * 2 + 1e-6 * np.abs(j_ref))
 
 
-@pytest.mark.parametrize("env", [{"MG_STENCIL_CAP": "64"}, {"MG_NO_TMA": "1"}, {}])
+@pytest.mark.parametrize("env", [{"MG_STENCIL_CAP": "64"}, {"MG_NO_SPLIT_SWEEP": "1"}, {}])
 def test_split_sweep_variants_match_oracle(monkeypatch, env):
     # the split FP32 sweep with a stencil table smaller than the touched list
     # (the fix-up pass rebuilds the vertices beyond it from their cell records),
-    # with the register-only bulk pass instead of the TMA-staged one, and as built
+    # without the split (one pass over the cell records), and as built
     dim, n, fld, s = 3, 27, inputs.boxes_field(3, 31), 4
     stored = _stored_operator(mg.PATH_MIXED_PLAIN, fld, n, s)
     rng = np.random.default_rng(5)
@@ -395,7 +395,7 @@ def test_split_sweep_variants_match_oracle(monkeypatch, env):
     scale = np.abs(stored).max() * np.abs(x).max() * (1 << dim) * 8
     tol32 = 1e-6 * scale + 1e-5 * scale
     dmin = np.abs(oracle.diag(dim, n, stored)[m]).min()
-    for k in ("MG_STENCIL_CAP", "MG_NO_TMA"):
+    for k in ("MG_STENCIL_CAP", "MG_NO_SPLIT_SWEEP"):
         monkeypatch.delenv(k, raising=False)
     for k, v in env.items():
         monkeypatch.setenv(k, v)
