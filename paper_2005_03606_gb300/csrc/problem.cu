@@ -87,6 +87,7 @@ struct Level {
   FullChunk* d_full = nullptr;
   CmpChunk* d_cmp = nullptr;
   void* full_store = nullptr;     // coarse levels: single chunk
+  void* stencil = nullptr;        // assembled vertex stencils (levels with full storage)
   void* b = nullptr;              // V-cycle right-hand side (TV)
   void* x0 = nullptr;             // V-cycle iterates (TV)
   void* x1 = nullptr;
@@ -401,12 +402,15 @@ mg_status upload_tables(mg_problem* P) {
   if (P->touched) {
     MG_CHECK(launch_build_touched(l0.op, P->tflags, P->tcounts, P->touched, P->ntouched, P->st));
   }
+  if (l0.stencil) MG_CHECK(launch_build_stencil(l0.op, l0.stencil, P->st));
   return MG_OK;
 }
 
 mg_status rebuild_coarse(mg_problem* P) {
-  for (int l = 0; l + 1 < P->L; ++l)
+  for (int l = 0; l + 1 < P->L; ++l) {
     MG_CHECK(launch_galerkin(P->lev[l].op, P->mixed ? 0 : 1, P->lev[l + 1].full_store, P->st));
+    if (P->lev[l + 1].stencil) MG_CHECK(launch_build_stencil(P->lev[l + 1].op, P->lev[l + 1].stencil, P->st));
+  }
   MG_CHECK(launch_coarse_factor(P->lev[P->L - 1].op, P->Lc, P->st));
   return MG_OK;
 }
@@ -810,6 +814,14 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
         return fail(MG_ERR_CUDA);
       op.full = lv.d_full;
     }
+    // assembled vertex stencils for the levels swept with full storage (not the
+    // coarsest, which is solved directly, nor the compressed finest level)
+    if (l < L - 1 && (l > 0 || !P->mixed)) {
+      const size_t sb = (size_t)(D == 3 ? 27 : 9) * lv.nvert * (P->mixed ? 4 : 8);
+      if ((e = dalloc(P, &lv.stencil, sb)) != cudaSuccess) return fail(oom_or_cuda(e, "stencils"));
+      cudaMemsetAsync(lv.stencil, 0, sb, P->st);
+      op.stencil = lv.stencil;
+    }
     const size_t vb = P->tv * lv.nvert;
     if ((e = dalloc(P, &lv.b, vb)) != cudaSuccess || (e = dalloc(P, &lv.x0, vb)) != cudaSuccess ||
         (e = dalloc(P, &lv.x1, vb)) != cudaSuccess)
@@ -905,7 +917,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   {
     const long long ni = P->N - 1;
     long long sweep_blocks = ((ni + 31) / 32) * ((ni + 7) / 8) * (D == 3 ? ni : 1);
-    P->npartials = 2 * std::max<long long>(sweep_blocks, 152 * 4) + 64;
+    P->npartials = 2 * std::max<long long>(sweep_blocks, 152 * 8) + 64;
   }
   if ((e = dalloc(P, &P->partials, sizeof(double) * P->npartials)) != cudaSuccess ||
       (e = dalloc(P, &P->sc, sizeof(DevScalars))) != cudaSuccess ||

@@ -230,6 +230,119 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
   }
 }
 
+// ---------------------------------------------------------------- assembled vertex stencils
+// Levels stored as full cell matrices (Galerkin coarse levels; the finest
+// level of the FP64 paths) also keep the assembled 3^d-point stencil of every
+// vertex, gathered once per rebuild of the cell matrices.  A sweep then costs
+// 3^d coefficient loads and multiply-adds per vertex instead of decoding the
+// 2^d cells around it.
+template <int D, typename TS>
+__global__ void build_stencil_kernel(const LevelOp op, TS* __restrict__ out) {
+  constexpr int NV = Dim<D>::NV, NS = D == 3 ? 27 : 9, C = D == 3 ? 13 : 4;
+  const int N = op.N, n1 = N + 1, ni = N - 1;
+  const long long nv = D == 3 ? (long long)n1 * n1 * n1 : (long long)n1 * n1;
+  const long long nint = D == 3 ? (long long)ni * ni * ni : (long long)ni * ni;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = 1 + (int)(t % ni);
+    const int j = 1 + (int)((t / ni) % ni);
+    const int k = D == 3 ? 1 + (int)(t / ((long long)ni * ni)) : 0;
+    const long long v = D == 3 ? ((long long)k * n1 + j) * n1 + i : (long long)j * n1 + i;
+    TS c[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) c[q] = 0;
+    TS dg = 0;
+#pragma unroll
+    for (int ol = 0; ol < 2; ++ol) {
+      const int cl = (D == 3 ? k : j) - 1 + ol;
+      int ch = cl / op.layers;
+      ch = ch < op.nchunk ? ch : op.nchunk - 1;
+      const int ll = cl - ch * op.layers;
+      const TS* A = reinterpret_cast<const TS*>(op.full[ch].a);
+      const size_t cc = (size_t)op.chunk_cells;
+#pragma unroll
+      for (int om = 0; om < (D == 3 ? 2 : 1); ++om) {
+        const int cy = D == 3 ? j - 1 + om : cl;
+        const int row = D == 3 ? ll * N + cy : ll;
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          const int cx = i - 1 + ox;
+          const int oy = D == 3 ? om : ol, oz = D == 3 ? ol : 0;
+          const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
+          const int lc = row * N + cx;
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb) {
+            if (bb == a) continue;
+            const TS av = __ldg(A + (size_t)pair_of(NV, a, bb) * cc + lc);
+            const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + (D == 3 ? 9 * (oz + ((bb >> 2) & 1)) : 0);
+            c[ub] += av;
+            dg -= av;
+          }
+        }
+      }
+    }
+    c[C] = dg;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) out[(size_t)q * nv + v] = c[q];
+  }
+}
+
+template <int D, typename TV, typename TA, typename TS, int MODE>
+__global__ void __launch_bounds__(kBX * kBY) stencil_sweep_kernel(const LevelOp op, const TV* __restrict__ x,
+                                                                  const TV* __restrict__ b, TV* __restrict__ y,
+                                                                  TA omega, double* __restrict__ partials) {
+  constexpr int C = D == 3 ? 13 : 4;   // centre of the 3^d stencil
+  __shared__ double sh[2][kBX * kBY / 32];
+  const int N = op.N, n1 = N + 1;
+  const int i = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int j = 1 + blockIdx.y * kBY + threadIdx.y;
+  const int k = D == 3 ? 1 + blockIdx.z : 0;
+  const bool valid = i < N && j < N;
+  const size_t nv = D == 3 ? (size_t)n1 * n1 * n1 : (size_t)n1 * n1;
+  double d1 = 0.0, d2 = 0.0;
+  if (valid) {
+    const int v = D == 2 ? j * n1 + i : (k * n1 + j) * n1 + i;
+    const int plane = n1 * n1;
+    const TS* S = reinterpret_cast<const TS*>(op.stencil) + v;
+    const TA uv = (TA)__ldg(x + v);
+    const TA dg = (TA)__ldg(S + (size_t)C * nv);
+    // FP32: difference form sum_q c_q (u_q - u_v) (exact for constants); FP64:
+    // plain sum_q c_q u_q, half the FP64 operations, rounding far below need
+    constexpr bool kDiff = sizeof(TA) == 4;
+    TA acc = kDiff ? (TA)0 : dg * uv;
+#pragma unroll
+    for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int q = dx + 3 * dy + 9 * dz;
+          if (q == C) continue;
+          const TA uq = (TA)__ldg(x + (v + (dx - 1) + (dy - 1) * n1 + (D == 3 ? (dz - 1) * plane : 0)));
+          acc += (TA)__ldg(S + (size_t)q * nv) * (kDiff ? uq - uv : uq);
+        }
+    const TA Au = acc;
+    if (MODE == SW_JACOBI) {
+      y[v] = (TV)(uv + omega * ((TA)b[v] - Au) / dg);
+    } else if (MODE == SW_RESID) {
+      y[v] = (TV)((TA)b[v] - Au);
+    } else {
+      y[v] = (TV)Au;
+      d1 = (double)uv * (double)Au;
+      d2 = (double)uv * (double)b[v];
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      partials[2 * blk] = s1;
+      partials[2 * blk + 1] = s2;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- 3D streaming tile sweep
 // A CTA owns a 32 x 8 column of vertices and walks kZC vertex planes along z,
 // one vertex per thread and plane.  u planes (34 x 10 with halo), b planes,
@@ -952,6 +1065,18 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   TV* yv = (TV*)y;
   if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
     return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
+  if (!CMP && op.stencil) {
+    dim3 blk(kBX, kBY, 1);
+    dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
+    if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+    if (mode == SW_JACOBI)
+      stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else if (mode == SW_RESID)
+      stencil_sweep_kernel<D, TV, TA, TS, SW_RESID><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else
+      stencil_sweep_kernel<D, TV, TA, TS, SW_MATVEC><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    return launched();
+  }
   // the plane-streaming kernel needs enough (x, y, z-run) tiles to fill the GPU;
   // smaller grids run one vertex per thread
   if (D == 3 && op.N >= 243) {
@@ -1057,7 +1182,31 @@ int vgrid(long long n) {
 }
 
 // ---------------------------------------------------------------- vector kernels
-constexpr int kRedBlocks = 152 * 4;
+constexpr int kRedBlocks = 152 * 8;
+
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// FP32 dot product: float4 body when both operands are 16-byte aligned, scalar tail
+__global__ void dot4_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                            double* partials) {
+  __shared__ double sh[8];
+  float acc = 0.f;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n4 = 0;
+  if (aligned16(a) && aligned16(b)) {
+    n4 = n / 4;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    for (long long t = t0; t < n4; t += stride) {
+      const float4 x = __ldg(a4 + t), y = __ldg(b4 + t);
+      acc += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+    }
+  }
+  for (long long t = 4 * n4 + t0; t < n; t += stride) acc += a[t] * b[t];
+  const double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
 
 template <typename TA, typename TB>
 __global__ void dot_kernel(const TA* __restrict__ a, const TB* __restrict__ b, long long n, double* partials) {
@@ -1205,6 +1354,20 @@ cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void*
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
 
+cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st) {
+  if (op.compressed || !out) return cudaErrorInvalidValue;
+  const long long ni = op.N - 1;
+  const int g = vgrid(op.dim == 3 ? ni * ni * ni : ni * ni);
+  if (op.dim == 2) {
+    if (op.elem64) build_stencil_kernel<2, double><<<g, 256, 0, st>>>(op, (double*)out);
+    else build_stencil_kernel<2, float><<<g, 256, 0, st>>>(op, (float*)out);
+  } else {
+    if (op.elem64) build_stencil_kernel<3, double><<<g, 256, 0, st>>>(op, (double*)out);
+    else build_stencil_kernel<3, float><<<g, 256, 0, st>>>(op, (float*)out);
+  }
+  return launched();
+}
+
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
                                  cudaStream_t st) {
   const long long nv = (long long)(op.N + 1) * (op.N + 1) * (op.N + 1);
@@ -1241,7 +1404,7 @@ cudaError_t launch_dot(const double* a, const double* b, long long n, double* pa
 cudaError_t launch_dot_f32f32(const float* a, const float* b, long long n, double* partials, int* nblocks,
                               cudaStream_t st) {
   *nblocks = kRedBlocks;
-  dot_kernel<float, float><<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
+  dot4_kernel<<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
   return launched();
 }
 
@@ -1282,8 +1445,24 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
 __global__ void fcg32_direction_kernel(long long n, int first, const float* __restrict__ z, float* __restrict__ p,
                                        const DevScalars* __restrict__ sc) {
   const float beta = first ? 0.f : (float)sc->beta;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    p[t] = first ? z[t] : z[t] + beta * p[t];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n4 = 0;
+  if (aligned16(z) && aligned16(p)) {
+    n4 = n / 4;
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    float4* p4 = reinterpret_cast<float4*>(p);
+    for (long long t = t0; t < n4; t += stride) {
+      const float4 a = __ldg(z4 + t);
+      if (first) {
+        p4[t] = a;
+      } else {
+        const float4 o = p4[t];
+        p4[t] = make_float4(fmaf(beta, o.x, a.x), fmaf(beta, o.y, a.y), fmaf(beta, o.z, a.z), fmaf(beta, o.w, a.w));
+      }
+    }
+  }
+  for (long long t = 4 * n4 + t0; t < n; t += stride) p[t] = first ? z[t] : z[t] + beta * p[t];
 }
 
 __global__ void fcg32_update_kernel(long long n, float* __restrict__ e, float* __restrict__ r,
@@ -1292,7 +1471,32 @@ __global__ void fcg32_update_kernel(long long n, float* __restrict__ e, float* _
   __shared__ double sh[8];
   const float alpha = (float)sc->alpha;
   float acc = 0.f;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n4 = 0;
+  if (aligned16(e) && aligned16(r) && aligned16(p) && aligned16(q)) {
+    n4 = n / 4;
+    float4* e4 = reinterpret_cast<float4*>(e);
+    float4* r4 = reinterpret_cast<float4*>(r);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    for (long long t = t0; t < n4; t += stride) {
+      const float4 pv = __ldg(p4 + t), qv = __ldg(q4 + t);
+      float4 ev = e4[t], rv = r4[t];
+      ev.x = fmaf(alpha, pv.x, ev.x);
+      ev.y = fmaf(alpha, pv.y, ev.y);
+      ev.z = fmaf(alpha, pv.z, ev.z);
+      ev.w = fmaf(alpha, pv.w, ev.w);
+      rv.x = fmaf(-alpha, qv.x, rv.x);
+      rv.y = fmaf(-alpha, qv.y, rv.y);
+      rv.z = fmaf(-alpha, qv.z, rv.z);
+      rv.w = fmaf(-alpha, qv.w, rv.w);
+      e4[t] = ev;
+      r4[t] = rv;
+      acc += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    }
+  }
+  for (long long t = 4 * n4 + t0; t < n; t += stride) {
     e[t] += alpha * p[t];
     const float rv = r[t] - alpha * q[t];
     r[t] = rv;
@@ -1322,7 +1526,7 @@ __global__ void apply_correction_kernel(long long n, double* __restrict__ u, con
 
 cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, const DevScalars* sc,
                                    cudaStream_t st) {
-  fcg32_direction_kernel<<<vgrid(n), 256, 0, st>>>(n, first, z, p, sc);
+  fcg32_direction_kernel<<<vgrid((n + 3) / 4), 256, 0, st>>>(n, first, z, p, sc);
   return launched();
 }
 
