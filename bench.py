@@ -195,27 +195,51 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+class Replicas:
+    """Replica bookkeeping of a run on N ranks (one process per GPU): a
+    barrier around the timed region and the max over ranks of its duration.
+    The solves on different ranks are independent; there is no collective
+    on the data path (gloo carries only the barrier and the max)."""
+
+    def __init__(self, world: int):
+        self.world = world
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group("gloo")
+            self.dist = dist
+
+    def barrier(self, device_sync=None):
+        if device_sync is not None:
+            device_sync()
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.dist:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def aggregate(self, steps: int, region_ms: float) -> float:
+        """Whole-job throughput: the steps of all ranks over the slowest rank's time."""
+        return self.world * steps / (region_ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2005_03606_gb300 import mg
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
+    rep = Replicas(world)
     lib = mg.load()
 
     def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        rep.barrier(torch.cuda.synchronize)
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = rep.max
 
     w, desc = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED)
     mixed_path = mg.PATH_MIXED_DELAYED
@@ -241,7 +265,7 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     launches = lib.mg_launch_count() - l0
     region_ms = max_over_ranks(ev0.elapsed_time(ev1))
-    value = world * args.steps / (region_ms / 1e3)
+    value = rep.aggregate(args.steps, region_ms)
     info0 = infos[-1]
     # roofline: the finest-level V-cycle sweep (most launched kernel) and the FP64 matvec
     P = probs[-1]
@@ -283,7 +307,7 @@ def run_ours(args, rank, world, local_rank):
             u_host[:] = P.solution()
         barrier()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = world * len(e2e_ms) / (max_over_ranks(sum(e2e_ms)) / 1e3)
+    e2e_val = rep.aggregate(len(e2e_ms), max_over_ranks(sum(e2e_ms)))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores, _ = oracle_sample(args.workload, int(info0.cycles))
