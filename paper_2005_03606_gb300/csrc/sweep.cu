@@ -921,6 +921,266 @@ __global__ void touched_stencil_kernel(const LevelOp op) {
 
 constexpr int kFixBlocks = 152 * 2;
 
+// ---------------------------------------------------------------- 3D FP64 split residual / matvec
+// The outer FP64 iteration of the mixed paths needs r = f - A u and A p on the
+// compressed finest level in FP64, where the FP64 pipe (1/64 of FP32 on this
+// part) is the bound.  The same split as the FP32 sweep: a class-blind bulk
+// pass applies the geometric part in the factored form (fewest FP64 operations
+// per vertex, about 40), then a fix-up pass adds the decoded surplus of the
+// cells with records at the touched vertices (exact FP32 entries, FP64 sums).
+// Bulk: 2 vertices per thread (double2 rows), z march as in the FP32 pass.
+struct Rows4d {   // x[q-1], x[q], x[q+1], x[q+2] of three rows j-1, j, j+1
+  double v[3][4];
+};
+
+__device__ __forceinline__ void load_rows4d(const double* __restrict__ p, int n1, bool has_left, bool has_right,
+                                            Rows4d& r) {
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) {
+    const double* q = p + (dy - 1) * n1;
+    const double2 c = __ldg(reinterpret_cast<const double2*>(q));
+    r.v[dy][0] = has_left ? __ldg(q - 1) : 0.0;
+    r.v[dy][1] = c.x;
+    r.v[dy][2] = c.y;
+    r.v[dy][3] = has_right ? __ldg(q + 2) : 0.0;
+  }
+}
+
+// eps of cells x = q-1, q, q+1 of cell rows j-1 (r = 0) and j (r = 1) of layer l
+__device__ __forceinline__ void load_eps6d(const float* __restrict__ eps, int N, int l, int j, int q,
+                                           bool has_left, bool has_right, double (&g)[2][3]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float* e = eps + ((size_t)l * N + (j - 1 + r)) * N + q;
+    g[r][0] = has_left ? (double)__ldg(e - 1) : 0.0;
+    g[r][1] = (double)__ldg(e);
+    g[r][2] = has_right ? (double)__ldg(e + 1) : 0.0;
+  }
+}
+
+__device__ __forceinline__ void pair_sums4d(const Rows4d& u, double (&py)[2][3]) {
+  double px[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) px[r][c] = u.v[r][c] + u.v[r][c + 1];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) py[r][c] = px[r][c] + px[r + 1][c];
+}
+
+struct Geo64Ctx {
+  const double* x;
+  const double* b;
+  double* y;
+  const float* eps;
+  int N, n1, q, j;
+  size_t plane, row0;
+  bool hl, hr, hr2;
+  double h12;
+};
+
+template <int MODE>
+__device__ __forceinline__ void geo64_step(const Geo64Ctx& c, int k, const Rows4d& uc, Rows4d& un,
+                                           const double (&pyc)[2][3], double (&pyn)[2][3],
+                                           const double (&gm)[2][3], double (&gc)[2][3], const double (&yTm)[3],
+                                           double (&yTc)[3], double& d1, double& d2) {
+  load_rows4d(c.x + (size_t)(k + 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, un);
+  load_eps6d(c.eps, c.N, k, c.j, c.q, c.hl, c.hr2, gc);
+  const double2 b2 = __ldg(reinterpret_cast<const double2*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
+  const double2 m2 = __ldg(reinterpret_cast<const double2*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
+  pair_sums4d(un, pyn);
+  double yZ[3], ez[2][3], ey[3], elm[3], elc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    yTc[i] = gc[0][i] * (pyc[0][i] + pyn[0][i]) + gc[1][i] * (pyc[1][i] + pyn[1][i]);
+    yZ[i] = yTm[i] + yTc[i];
+    ez[0][i] = gm[0][i] + gc[0][i];
+    ez[1][i] = gm[1][i] + gc[1][i];
+    ey[i] = ez[0][i] + ez[1][i];
+    elm[i] = gm[0][i] + gm[1][i];
+    elc[i] = gc[0][i] + gc[1][i];
+  }
+  const double bb[2] = {b2.x, b2.y};
+  const double um1[2] = {m2.x, m2.y};
+  double out[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const double uv = uc.v[1][e + 1];
+    const double G = ey[e] + ey[e + 1];
+    double w = fma(5.0 * uv, G, -(yZ[e] + yZ[e + 1]));
+    w = fma(ey[e], uc.v[1][e], w);                         // x - 1
+    w = fma(ey[e + 1], uc.v[1][e + 2], w);                 // x + 1
+    w = fma(ez[0][e] + ez[0][e + 1], uc.v[0][e + 1], w);   // y - 1
+    w = fma(ez[1][e] + ez[1][e + 1], uc.v[2][e + 1], w);   // y + 1
+    w = fma(elm[e] + elm[e + 1], um1[e], w);               // z - 1
+    w = fma(elc[e] + elc[e + 1], un.v[1][e + 1], w);       // z + 1
+    const double acc = c.h12 * w;
+    const int i = c.q + e;
+    const bool valid = i >= 1 && i <= c.N - 1;
+    double r;
+    if (MODE == SW_RESID) r = bb[e] - acc;
+    else {
+      r = acc;
+      if (valid) {
+        d1 += uv * acc;
+        d2 += uv * bb[e];
+      }
+    }
+    out[e] = valid ? r : 0.0;
+  }
+  *reinterpret_cast<double2*>(c.y + (size_t)k * c.plane + c.row0 + c.q) = make_double2(out[0], out[1]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo64(const LevelOp op, const double* __restrict__ x,
+                                                                   const double* __restrict__ b,
+                                                                   double* __restrict__ y,
+                                                                   double* __restrict__ partials, int ntx, int nty,
+                                                                   int ntiles) {
+  __shared__ double sh[2][8];
+  Geo64Ctx c;
+  c.x = x;
+  c.b = b;
+  c.y = y;
+  c.eps = op.eps_c;
+  c.N = op.N;
+  c.n1 = op.N + 1;
+  c.plane = (size_t)c.n1 * c.n1;
+  c.h12 = -op.gk64;   // h / 12
+  double d1 = 0.0, d2 = 0.0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    c.q = 2 * (tx * kGeoBX + threadIdx.x);   // vertices q, q+1
+    c.j = 1 + ty * kGeoBY + threadIdx.y;
+    const int k0 = 1 + tz * kGZ;
+    const int k1 = min(c.N - 1, k0 + kGZ - 1);
+    if (c.q >= c.n1 || c.j >= c.N || k0 > k1) continue;
+    c.hl = c.q > 0;
+    c.hr = c.q + 2 <= c.N;      // vertex q+2 exists
+    c.hr2 = c.q + 1 <= c.N - 1; // cell q+1 exists
+    c.row0 = (size_t)c.j * c.n1;
+    Rows4d ua, ub;
+    double pa[2][3], pb[2][3], ga[2][3], gb[2][3], ta[3], tb[3];
+    load_rows4d(x + (size_t)(k0 - 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ub);
+    load_rows4d(x + (size_t)k0 * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ua);
+    load_eps6d(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr2, ga);
+    pair_sums4d(ub, pb);
+    pair_sums4d(ua, pa);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ta[i] = ga[0][i] * (pb[0][i] + pa[0][i]) + ga[1][i] * (pb[1][i] + pa[1][i]);
+    for (int k = k0; k <= k1; k += 2) {
+      geo64_step<MODE>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
+      if (k + 1 > k1) break;
+      geo64_step<MODE>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      partials[2 * blockIdx.x] = s1;
+      partials[2 * blockIdx.x + 1] = s2;
+    }
+  }
+}
+
+// surplus part sum_c Delta_c u at the touched vertices, added in FP64 (RESID:
+// y -= it; MATVEC: y += it and its contribution to u . A u)
+template <int MODE>
+__global__ void __launch_bounds__(256) sweep3_fixup64(const LevelOp op, const double* __restrict__ x,
+                                                      double* __restrict__ y, double* __restrict__ partials) {
+  constexpr int NV = 8;
+  __shared__ double sh[2][8];
+  const int N = op.N, n1 = N + 1;
+  const int nt = *op.ntouched;
+  double d1 = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int v = op.touched[t];
+    const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
+    double u[27];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+          u[dx + 3 * dy + 9 * dz] = __ldg(x + (size_t)v + (dx - 1) + (dy - 1) * n1 + (size_t)(dz - 1) * n1 * n1);
+    double acc = 0.0;
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz) {
+      const int cl = k - 1 + oz;
+      int ch = cl / op.layers;
+      ch = ch < op.nchunk ? ch : op.nchunk - 1;
+      const int ll = cl - ch * op.layers;
+      const CmpChunk& ck = op.cmp[ch];
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy) {
+        const int segrow = (ll * N + (j - 1 + oy)) * op.nseg_x;
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          const int cx = i - 1 + ox;
+          const int seg = segrow + (cx >> 5);
+          const int cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
+          if (!cls) continue;
+          const uint8_t* rec = record_at<3>(ck, seg, cx & 31, cls);
+          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+#pragma unroll
+          for (int bb = 0; bb < NV; ++bb) {
+            if (bb == a) continue;
+            const double dv = (double)decode_entry<3>(rec, cls, pair_of(NV, a, bb));
+            const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
+            acc += dv * (u[ub] - u[13]);
+          }
+        }
+      }
+    }
+    if (MODE == SW_RESID) {
+      y[v] -= acc;
+    } else {
+      y[v] += acc;
+      d1 += u[13] * acc;
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    if (threadIdx.x == 0) {
+      partials[2 * blockIdx.x] = s1;
+      partials[2 * blockIdx.x + 1] = 0.0;
+    }
+  }
+}
+
+cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const double* b, double* y,
+                         double* partials, int* nblocks, cudaStream_t st) {
+  const int np = (op.N + 1) / 2;
+  const int ntx = (np + kGeoBX - 1) / kGeoBX, nty = (op.N - 1 + kGeoBY - 1) / kGeoBY;
+  const int ntz = (op.N - 1 + kGZ - 1) / kGZ;
+  const int ntiles = ntx * nty * ntz;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  const int nb = ntiles < 2 * nsm ? ntiles : 2 * nsm;
+  const dim3 blk(kGeoBX, kGeoBY, 1);
+  double* pfix = partials ? partials + 2 * (size_t)nb : nullptr;
+  if (mode == SW_RESID) {
+    sweep3_geo64<SW_RESID><<<nb, blk, 0, st>>>(op, x, b, y, partials, ntx, nty, ntiles);
+    count_launches(1);
+    sweep3_fixup64<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
+  } else {
+    sweep3_geo64<SW_MATVEC><<<nb, blk, 0, st>>>(op, x, b, y, partials, ntx, nty, ntiles);
+    count_launches(1);
+    sweep3_fixup64<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
+  }
+  if (nblocks) *nblocks = nb + kFixBlocks;
+  return launched();
+}
+
 // ---- list of vertices touched by a cell with a surplus record (finest compressed level)
 __global__ void touched_mark_kernel(const LevelOp op, uint8_t* __restrict__ flags) {
   const int N = op.N, n1 = N + 1;
@@ -1065,6 +1325,8 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   TV* yv = (TV*)y;
   if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
     return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
+  if (D == 3 && CMP && sizeof(TV) == 8 && mode != SW_JACOBI && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
+    return launch_geo64(op, mode, (const double*)x, (const double*)b, (double*)y, partials, nblocks, st);
   if (!CMP && op.stencil) {
     dim3 blk(kBX, kBY, 1);
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);

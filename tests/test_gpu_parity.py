@@ -364,6 +364,8 @@ def test_full_size_split_sweep_sampled():
         y = P.apply(0, 0, x, b, inner=True)
         jac = P.apply(0, 1, x, b, inner=True)
         res = P.apply(0, 2, x, b, inner=True)
+        y64 = P.apply(0, 0, x, b)          # FP64 outer operator (split bulk + surplus fix-up)
+        res64 = P.apply(0, 2, x, b)
         cls_all, _ = P.cell_data()
     nz = np.flatnonzero(cls_all)
     cz = rng.choice(nz, 150, replace=False)
@@ -374,6 +376,8 @@ def test_full_size_split_sweep_sampled():
     tol = 2e-5 * scale + 1e-7 * np.abs(Ax).max()
     assert np.all(np.abs(y[verts] - Ax) <= tol)
     assert np.all(np.abs(res[verts] - (b[verts] - Ax)) <= tol + 1e-6 * np.abs(b[verts]))
+    assert np.all(np.abs(y64[verts] - Ax) <= tol)
+    assert np.all(np.abs(res64[verts] - (b[verts] - Ax)) <= tol)
     j_ref = x[verts] + 0.6 * (b[verts] - Ax) / dg
     assert np.all(np.abs(jac[verts] - j_ref) <= 0.6 * (tol + 1e-6 * np.abs(b[verts])) / dg * 2 + 1e-6 * np.abs(j_ref))
 
