@@ -874,26 +874,31 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
           u[dx + 3 * dy + 9 * dz] = __ldg(x + (size_t)v + (dx - 1) + (dy - 1) * n1 + (size_t)(dz - 1) * n1 * n1);
     float Au, dg;
     const float uv = u[13];
+    // right-hand side (the bulk pass's value for the matvec) fetched up front
+    const float bv = MODE == SW_MATVEC ? y[v] : __ldg(b + v);
     if (t < cap) {
+      // all 27 coefficient loads issued before the first use (independent of u)
       const float* cf = op.tcoef + t;
+      float c[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q) c[q] = __ldg(cf + (size_t)q * cap);
       float acc = 0.f;
 #pragma unroll
       for (int q = 0; q < 27; ++q)
-        if (q != 13) acc += __ldg(cf + (size_t)q * cap) * (u[q] - uv);
+        if (q != 13) acc = fmaf(c[q], u[q] - uv, acc);
       Au = acc;
-      dg = __ldg(cf + (size_t)13 * cap);
+      dg = c[13];
     } else {
       const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
       vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
     }
     if (MODE == SW_JACOBI) {
-      y[v] = uv + omega * (b[v] - Au) / dg;
+      y[v] = uv + omega * (bv - Au) / dg;
     } else if (MODE == SW_RESID) {
-      y[v] = b[v] - Au;
+      y[v] = bv - Au;
     } else {
-      const float qg = y[v];
       y[v] = Au;
-      d1 += uv * (Au - qg);
+      d1 += uv * (Au - bv);   // bv: the bulk pass's value at v
     }
   }
   if (MODE == SW_MATVEC) {
@@ -1298,6 +1303,7 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   }
   const int nb_bulk = ntiles < 2 * nsm ? ntiles : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
+
   double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
   if (mode == SW_JACOBI) {
     sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
