@@ -122,6 +122,8 @@ struct LevelOp {
   // operator is applied in difference form, sum_k c_k (u_k - u_v))
   float* tcoef;
   int tcap;
+  // split sweep: eps_c with rows padded to N+1 floats (zero pad), for float4 loads
+  const float* eps_pad;
   // levels with full storage: assembled 3^d-point vertex stencils, SoA
   // [3^d][(N+1)^d] of the storage type (centre entry: the diagonal; the
   // operator is applied in difference form), rebuilt with the cell matrices
@@ -241,6 +243,7 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st);
+cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream_t st);
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
                                  cudaStream_t st);
 

@@ -135,6 +135,7 @@ struct mg_problem {
   uint8_t* tflags = nullptr;
   uint32_t* tcounts = nullptr;
   float* tcoef = nullptr;
+  float* eps_pad = nullptr;
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   int inner_its = 0;
@@ -889,6 +890,10 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     l0.op.ntouched = P->ntouched;
     l0.op.tcoef = P->tcoef;
     l0.op.tcap = (int)cap;
+    // eps_c with padded rows for the bulk pass
+    if ((e = dalloc(P, &P->eps_pad, sizeof(float) * (size_t)P->N * P->N * (P->N + 1))) != cudaSuccess)
+      return fail(oom_or_cuda(e, "padded eps"));
+    l0.op.eps_pad = P->eps_pad;
   }
   // outer vectors
   const size_t v8 = sizeof(double) * l0.nvert;
@@ -948,6 +953,8 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   }
   // cell-centre eps and the geometric (s = 1) operator
   if (!cuda_ok(launch_eps_centre(D, P->N, &P->eps, P->mixed ? 0 : 1, P->eps_c, P->st), "eps centre"))
+    return fail(MG_ERR_CUDA);
+  if (P->eps_pad && !cuda_ok(launch_pad_eps(P->N, (const float*)P->eps_c, P->eps_pad, P->st), "padded eps"))
     return fail(MG_ERR_CUDA);
   for (int c = 0; c < P->nchunk; ++c) {
     ChunkStore cs;

@@ -691,17 +691,20 @@ __device__ __forceinline__ void load_rows6(const float* __restrict__ x, size_t r
 }
 
 // eps of the 5 cells x = q-1 .. q+3 of cell rows j-1 (r = 0) and j (r = 1) of
-// layer l; cells outside the grid read 0 (they only reach boundary vertices)
-__device__ __forceinline__ void load_eps10(const float* __restrict__ eps, int N, int l, int j, int q,
-                                           bool has_left, bool has_right, float (&g)[2][5]) {
+// layer l, from the copy of eps_c whose rows are padded to N+1 floats (one
+// float4 per row plus the left neighbour; cell x = N reads the zero pad, and
+// cells outside the grid only reach boundary vertices)
+__device__ __forceinline__ void load_eps10(const float* __restrict__ eps_pad, int N, int l, int j, int q,
+                                           bool has_left, bool /*has_right*/, float (&g)[2][5]) {
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const float* e = eps + ((size_t)l * N + (j - 1 + r)) * N + q;
+    const float* e = eps_pad + ((size_t)l * N + (j - 1 + r)) * (N + 1) + q;
+    const float4 c = __ldg(reinterpret_cast<const float4*>(e));
     g[r][0] = has_left ? __ldg(e - 1) : 0.f;
-    g[r][1] = __ldg(e);
-    g[r][2] = __ldg(e + 1);
-    g[r][3] = __ldg(e + 2);
-    g[r][4] = has_right ? __ldg(e + 3) : 0.f;
+    g[r][1] = c.x;
+    g[r][2] = c.y;
+    g[r][3] = c.z;
+    g[r][4] = c.w;
   }
 }
 
@@ -739,7 +742,7 @@ __device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc
                                          float (&gc)[2][5], const float (&yTm)[5], float (&yTc)[5], float& d1,
                                          float& d2) {
   load_rows6(c.x, (size_t)(k + 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, un);
-  load_eps10(c.eps, c.N, k, c.j, c.q, c.hl, c.hr, gc);
+  load_eps10(c.eps, c.N, k, c.j, c.q, c.hl, c.hr, gc);   // c.eps: padded rows
   const float4 b4 = __ldg(reinterpret_cast<const float4*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
   // plane k-1, row j (read two planes ago: an L1/L2 hit)
   const float4 m4 = __ldg(reinterpret_cast<const float4*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
@@ -802,7 +805,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
   c.x = x;
   c.b = b;
   c.y = y;
-  c.eps = op.eps_c;
+  c.eps = op.eps_pad;
   c.N = op.N;
   c.n1 = op.N + 1;
   c.plane = (size_t)c.n1 * c.n1;
@@ -827,7 +830,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
     float pa[2][5], pb[2][5], ga[2][5], gb[2][5], ta[5], tb[5];
     load_rows6(x, (size_t)(k0 - 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, ub);
     load_rows6(x, (size_t)k0 * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, ua);
-    load_eps10(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr, ga);
+    load_eps10(op.eps_pad, c.N, k0 - 1, c.j, c.q, c.hl, c.hr, ga);
     pair_sums(ub, pb);
     pair_sums(ua, pa);
 #pragma unroll
@@ -1329,7 +1332,7 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   const TV* xv = (const TV*)x;
   const TV* bv = (const TV*)b;
   TV* yv = (TV*)y;
-  if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
+  if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched && op.eps_pad)
     return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
   if (D == 3 && CMP && sizeof(TV) == 8 && mode != SW_JACOBI && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
     return launch_geo64(op, mode, (const double*)x, (const double*)b, (double*)y, partials, nblocks, st);
@@ -1621,6 +1624,23 @@ cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void*
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
+
+// eps_c with rows padded to N+1 floats (zero pad)
+__global__ void pad_eps_kernel(int N, const float* __restrict__ src, float* __restrict__ dst) {
+  const int n1 = N + 1;
+  const long long total = (long long)N * N * n1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int xx = (int)(t % n1);
+    const long long r = t / n1;
+    dst[t] = xx < N ? src[r * N + xx] : 0.f;
+  }
+}
+
+cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream_t st) {
+  pad_eps_kernel<<<152 * 8, 256, 0, st>>>(N, eps_c, eps_pad);
+  return launched();
+}
 
 cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st) {
   if (op.compressed || !out) return cudaErrorInvalidValue;
