@@ -189,10 +189,12 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
   const T* eps_c = reinterpret_cast<const T*>(A.eps_c);
   const T invs = (T)1 / (T)s;
 
-  for (long long base = gwarp * CPW; base < A.ncell; base += nwarps * CPW) {
-    const long long lc = base + grp;
-    const bool valid = lc < A.ncell;
-    const long long c = A.cell0 + (valid ? lc : 0);
+  const long long count = A.list ? A.nlist : A.ncell;
+  for (long long base = gwarp * CPW; base < count; base += nwarps * CPW) {
+    const long long idx = base + grp;
+    const bool valid = idx < count;
+    const long long lc = !valid ? 0 : (A.list ? (long long)__ldg(A.list + idx) : idx);
+    const long long c = A.cell0 + lc;
     int ci[3] = {0, 0, 0};
     {
       long long t = c;
@@ -556,7 +558,7 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   for (int d = 1; d < D; ++d) R *= a.s;
   int G = 1;
   while (G * 2 <= R && G < 32) G *= 2;
-  const long long warps = (a.ncell * G + 31) / 32;
+  const long long warps = ((a.list ? a.nlist : a.ncell) * G + 31) / 32;
   long long blocks = (warps + kAsmThreads / 32 - 1) / (kAsmThreads / 32);
   const long long cap = 152LL * 16;
   if (blocks > cap) blocks = cap;
@@ -575,7 +577,67 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   return launched();
 }
 
+// one thread per cell: does a discontinuity cross the open cell?  (Cells
+// touched only on their boundary are flat: sample points lie strictly inside.)
+// The decisions carry a relative margin, so rounding can only add cells.
+template <int D>
+__global__ void interface_cells_kernel(const EpsDev F, int N, long long chunk_cells, int* __restrict__ lists,
+                                       int* __restrict__ counts) {
+  long long ncell = 1;
+  for (int a = 0; a < D; ++a) ncell *= N;
+  const double h = 1.0 / N, tol = 1e-9 * h;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double lo[3], hi[3];
+    long long t = c;
+    for (int a = 0; a < D; ++a) {
+      const int ci = (int)(t % N);
+      t /= N;
+      lo[a] = ci * h;
+      hi[a] = (ci + 1) * h;
+    }
+    bool cut = false;
+    if (F.kind == EPS_BOXES) {
+      for (int b = 0; b < F.n_boxes && !cut; ++b) {
+        bool overlap = true, face = false;
+        for (int a = 0; a < D; ++a) {
+          const double bl = F.box_lo[b][a], bh = F.box_hi[b][a];
+          overlap = overlap && bl <= hi[a] + tol && bh >= lo[a] - tol;
+          face = face || (bl > lo[a] - tol && bl < hi[a] + tol) || (bh > lo[a] - tol && bh < hi[a] + tol);
+        }
+        cut = overlap && face;
+      }
+    } else if (F.kind == EPS_DISC) {
+      double dmin = 0.0, dmax = 0.0;
+      for (int a = 0; a < D; ++a) {
+        const double x = F.center[a];
+        const double near = x < lo[a] ? lo[a] - x : (x > hi[a] ? x - hi[a] : 0.0);
+        const double far = fmax(fabs(x - lo[a]), fabs(x - hi[a]));
+        dmin += near * near;
+        dmax += far * far;
+      }
+      cut = dmin <= F.r2lim * (1.0 + 1e-9) && dmax >= F.r2lim * (1.0 - 1e-9);
+    }
+    if (F.jump_factor != 1.0) cut = cut || (F.jump_x > lo[0] - tol && F.jump_x < hi[0] + tol);
+    if (cut) {
+      const int ch = (int)(c / chunk_cells);
+      const int pos = atomicAdd(&counts[ch], 1);
+      lists[(long long)ch * chunk_cells + pos] = (int)(c - (long long)ch * chunk_cells);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long chunk_cells, int* lists,
+                                   int* counts, cudaStream_t st) {
+  if (eps->kind != EPS_BOXES && eps->kind != EPS_DISC && eps->kind != EPS_CONST) return cudaErrorNotSupported;
+  const long long ncell = (long long)N * N * (dim == 3 ? N : 1);
+  const int g = grid_for(ncell, 256);
+  if (dim == 2) interface_cells_kernel<2><<<g, 256, 0, st>>>(*eps, N, chunk_cells, lists, counts);
+  else interface_cells_kernel<3><<<g, 256, 0, st>>>(*eps, N, chunk_cells, lists, counts);
+  return launched();
+}
 
 cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st) {
   SampleThresholds TH;

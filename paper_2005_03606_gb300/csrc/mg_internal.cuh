@@ -224,8 +224,20 @@ struct AsmLaunch {
   uint8_t* out_cls;      // !prec64: padded class bytes of the chunk
   int nseg_x;
   double tau;
+  // optional list of the chunk's cells to integrate (local indices, nlist of
+  // them); the others are left alone (nullptr: every cell of the chunk)
+  const int* list;
+  long long nlist;
 };
 cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st);
+// interface cells: cells that a discontinuity of eps (box face, disc boundary,
+// planar jump) crosses; every other cell sees one eps value at all its sample
+// points, so its element matrix is the geometric one at every accuracy s.
+// Appends the local index of each such cell to lists[chunk * chunk_cells + ...]
+// and counts them in counts[chunk].  Returns cudaErrorNotSupported for fields
+// without a flat-cell notion (every cell must be integrated).
+cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long chunk_cells, int* lists,
+                                   int* counts, cudaStream_t st);
 cudaError_t launch_assemble(const AsmLaunch& a, cudaStream_t st);
 cudaError_t launch_geometric_full(int dim, int N, double hfac, const double* eps_c, long long cell0,
                                   long long ncell, double* out, cudaStream_t st);

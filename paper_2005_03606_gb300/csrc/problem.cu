@@ -127,6 +127,10 @@ struct mg_problem {
   DevScalars* h_sc = nullptr;     // pinned
   double* Lc = nullptr;           // coarse Cholesky factor
   uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
+  // interface cells per chunk (fields with piecewise-constant eps): only these
+  // are integrated at s > 1, every other cell keeps its geometric stencil
+  int* ilist = nullptr;           // [nchunk][chunk_cells] local cell indices
+  std::vector<int> ilist_n;       // count per chunk (host)
   uint32_t* d_totals = nullptr;   // per stream: [0..2] main, [4..6] side
   uint32_t* h_totals = nullptr;   // pinned, same layout
   // mixed 3D finest level: vertices touched by cells with a surplus record
@@ -297,10 +301,11 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
     cudaError_t e = cudaMallocAsync(&cs.a64, sizeof(double) * NP * P->chunk_cells, st);
     if (e != cudaSuccess) return oom_or_cuda(e, "chunk storage");
     cs.bytes = sizeof(double) * NP * P->chunk_cells;
-    if (s == 1) {
+    if (s == 1 || P->ilist) {
       MG_CHECK(launch_geometric_full(D, P->N, fine_op(P).hfac, (const double*)P->eps_c, cell0, P->chunk_cells,
                                      (double*)cs.a64, st));
-    } else {
+    }
+    if (s > 1 && (!P->ilist || P->ilist_n[chunk] > 0)) {
       AsmLaunch a{};
       a.dim = D;
       a.N = P->N;
@@ -315,6 +320,10 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
       a.out_full = cs.a64;
       a.nseg_x = P->nseg_x;
       a.tau = 0;
+      if (P->ilist) {
+        a.list = P->ilist + (size_t)chunk * P->chunk_cells;
+        a.nlist = P->ilist_n[chunk];
+      }
       MG_CHECK(launch_assemble(a, st));
     }
     *out = cs;
@@ -346,7 +355,11 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
   a.out_cls = cs.cls;
   a.nseg_x = P->nseg_x;
   a.tau = P->desc.compress_tau;
-  MG_CHECK(launch_assemble(a, st));
+  if (P->ilist) {   // only the interface cells can carry a surplus (the class bytes start at 0)
+    a.list = P->ilist + (size_t)chunk * P->chunk_cells;
+    a.nlist = P->ilist_n[chunk];
+  }
+  if (!P->ilist || a.nlist > 0) MG_CHECK(launch_assemble(a, st));
   uint32_t* dt = P->d_totals + tot_slot;
   uint32_t* ht = P->h_totals + tot_slot;
   MG_CHECK(launch_pack_count(D, P->N, P->chunk_rows, P->nseg_x, cs.cls, cs.seg_base, dt, st));
@@ -956,6 +969,22 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     return fail(MG_ERR_CUDA);
   if (P->eps_pad && !cuda_ok(launch_pad_eps(P->N, (const float*)P->eps_c, P->eps_pad, P->st), "padded eps"))
     return fail(MG_ERR_CUDA);
+  // interface cells of piecewise-constant fields (the only cells with a surplus)
+  if (!getenv("MG_NO_INTERFACE_LIST") &&
+      (P->eps.kind == EPS_BOXES || P->eps.kind == EPS_DISC || P->eps.kind == EPS_CONST)) {
+    int* counts = nullptr;
+    if ((e = dalloc(P, &P->ilist, sizeof(int) * (size_t)P->chunk_cells * P->nchunk)) != cudaSuccess ||
+        (e = cudaMallocAsync(&counts, sizeof(int) * P->nchunk, P->st)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "interface cells"));
+    P->ilist_n.assign(P->nchunk, 0);
+    if (!cuda_ok(cudaMemsetAsync(counts, 0, sizeof(int) * P->nchunk, P->st), "memset") ||
+        !cuda_ok(launch_interface_cells(D, P->N, &P->eps, P->chunk_cells, P->ilist, counts, P->st), "interface") ||
+        !cuda_ok(cudaMemcpyAsync(P->ilist_n.data(), counts, sizeof(int) * P->nchunk, cudaMemcpyDeviceToHost, P->st),
+                 "counts") ||
+        !cuda_ok(cudaStreamSynchronize(P->st), "interface sync"))
+      return fail(MG_ERR_CUDA);
+    cudaFreeAsync(counts, P->st);
+  }
   for (int c = 0; c < P->nchunk; ++c) {
     ChunkStore cs;
     mg_status s = assemble_chunk(P, 1, c, P->st, &cs, 0);

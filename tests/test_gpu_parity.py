@@ -449,3 +449,30 @@ def test_edge_cases_smallest_grid_and_errors():
     A = oracle.assemble(oracle.Field(fld), 9, 2)
     u_ref = dense.dense_solve(3, 9, A, oracle.load_vector(3, 9))
     assert np.abs(u - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
+
+
+@pytest.mark.parametrize("dim,n,fld,s,path", [
+    (3, 27, inputs.boxes_field(3, 2003), 8, mg.PATH_MIXED_PLAIN),
+    (3, 27, inputs.boxes_field(3, 14), 4, mg.PATH_FP64_PLAIN),
+    (2, 81, inputs.disc_field(2), 8, mg.PATH_FP64_PLAIN),
+    (3, 9, inputs.disc_field(3), 4, mg.PATH_MIXED_PLAIN),
+])
+def test_interface_cell_list_matches_full_assembly(monkeypatch, dim, n, fld, s, path):
+    # piecewise-constant fields integrate only the cells a discontinuity
+    # crosses; every other cell must come out exactly as the full pass has it
+    out = []
+    for env in ({"MG_NO_INTERFACE_LIST": "1"}, {}):
+        monkeypatch.delenv("MG_NO_INTERFACE_LIST", raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(s,))) as P:
+            P.assemble(s)
+            A = P.element_matrices(0)
+            cls, _ = P.cell_data()
+        out.append((A, cls))
+    (A0, c0), (A1, c1) = out
+    assert np.array_equal(c0, c1)
+    assert cellwise_err(A1, A0) <= 1e-14
+    ref = oracle.assemble(oracle.Field(fld), n, s)
+    tol = 1e-12 if path == mg.PATH_FP64_PLAIN else 1e-5
+    assert cellwise_err(A1, ref) <= tol
