@@ -830,7 +830,11 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     }
     // assembled vertex stencils for the levels swept with full storage (not the
     // coarsest, which is solved directly, nor the compressed finest level)
-    if (l < L - 1 && (l > 0 || !P->mixed)) {
+    // (mixed 3D fields without flat cells, e.g. lognormal: every cell carries a
+    // surplus, so the finest level is also swept from assembled FP32 stencils)
+    const bool dense0 = l == 0 && P->mixed && D == 3 && L > 1 && P->eps.kind != EPS_BOXES &&
+                        P->eps.kind != EPS_DISC && P->eps.kind != EPS_CONST && !getenv("MG_NO_DENSE_STENCIL");
+    if (l < L - 1 && (l > 0 || !P->mixed || dense0)) {
       const size_t sb = (size_t)(D == 3 ? 27 : 9) * lv.nvert * (P->mixed ? 4 : 8);
       if ((e = dalloc(P, &lv.stencil, sb)) != cudaSuccess) return fail(oom_or_cuda(e, "stencils"));
       cudaMemsetAsync(lv.stencil, 0, sb, P->st);
@@ -892,11 +896,12 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     const long long ni = (long long)(P->N - 1) * (P->N - 1) * (P->N - 1);
     long long cap = l0.nvert / 4 > 65536 ? l0.nvert / 4 : 65536;
     cap = cap < ni ? cap : ni;
+    if (l0.stencil) cap = 0;   // swept from full stencils: the table is not used
     if (const char* ev = getenv("MG_STENCIL_CAP")) {   // smaller table (tests of the record path)
       const long long c2 = atoll(ev);
       if (c2 >= 1 && c2 < cap) cap = c2;
     }
-    if ((e = dalloc(P, &P->tcoef, sizeof(float) * 27 * (size_t)cap)) != cudaSuccess)
+    if (cap > 0 && (e = dalloc(P, &P->tcoef, sizeof(float) * 27 * (size_t)cap)) != cudaSuccess)
       return fail(oom_or_cuda(e, "stencil table"));
     cudaMemsetAsync(P->ntouched, 0, sizeof(int), P->st);
     l0.op.touched = P->touched;

@@ -1332,6 +1332,24 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   const TV* xv = (const TV*)x;
   const TV* bv = (const TV*)b;
   TV* yv = (TV*)y;
+  if (D == 3 && CMP && sizeof(TV) == 4 && op.stencil) {   // dense surplus: assembled FP32 stencils
+    dim3 blk(kBX, kBY, 1);
+    dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, ni);
+    if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+    if (mode == SW_JACOBI)
+      stencil_sweep_kernel<3, float, float, float, SW_JACOBI><<<grd, blk, 0, st>>>(op, (const float*)x,
+                                                                                 (const float*)b, (float*)y,
+                                                                                 (float)omega, partials);
+    else if (mode == SW_RESID)
+      stencil_sweep_kernel<3, float, float, float, SW_RESID><<<grd, blk, 0, st>>>(op, (const float*)x,
+                                                                                (const float*)b, (float*)y,
+                                                                                (float)omega, partials);
+    else
+      stencil_sweep_kernel<3, float, float, float, SW_MATVEC><<<grd, blk, 0, st>>>(op, (const float*)x,
+                                                                                 (const float*)b, (float*)y,
+                                                                                 (float)omega, partials);
+    return launched();
+  }
   if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched && op.eps_pad)
     return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
   if (D == 3 && CMP && sizeof(TV) == 8 && mode != SW_JACOBI && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
@@ -1642,9 +1660,31 @@ cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream
   return launched();
 }
 
+// full FP32 stencils of a compressed 3D level (fields where every cell carries a surplus)
+__global__ void build_stencil_cmp3_kernel(const LevelOp op, float* __restrict__ out) {
+  const int N = op.N, n1 = N + 1, ni = N - 1;
+  const long long nv = (long long)n1 * n1 * n1;
+  const long long nint = (long long)ni * ni * ni;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = 1 + (int)(t % ni);
+    const int j = 1 + (int)((t / ni) % ni);
+    const int k = 1 + (int)(t / ((long long)ni * ni));
+    const long long v = ((long long)k * n1 + j) * n1 + i;
+    float c[27];
+    vertex_coeffs3(op, i, j, k, c);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) out[(size_t)q * nv + v] = c[q];
+  }
+}
+
 cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st) {
-  if (op.compressed || !out) return cudaErrorInvalidValue;
+  if (!out || (op.compressed && op.dim != 3)) return cudaErrorInvalidValue;
   const long long ni = op.N - 1;
+  if (op.compressed) {
+    build_stencil_cmp3_kernel<<<vgrid(ni * ni * ni), 256, 0, st>>>(op, (float*)out);
+    return launched();
+  }
   const int g = vgrid(op.dim == 3 ? ni * ni * ni : ni * ni);
   if (op.dim == 2) {
     if (op.elem64) build_stencil_kernel<2, double><<<g, 256, 0, st>>>(op, (double*)out);
