@@ -248,7 +248,10 @@ cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const 
                              uint8_t* p3, cudaStream_t st);
 
 // sweep.cu
-enum SweepMode { SW_JACOBI = 0, SW_RESID = 1, SW_MATVEC = 2 };
+// SW_JACOBI0: damped Jacobi from a zero iterate, y = omega D^-1 b (x is not
+// read); launch_sweep returns cudaErrorNotSupported (launching nothing) on the
+// paths without it, where the caller zeroes x and runs SW_JACOBI
+enum SweepMode { SW_JACOBI = 0, SW_RESID = 1, SW_MATVEC = 2, SW_JACOBI0 = 3 };
 cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, const void* b,
                          void* y, double omega, double* partials, int* nblocks, cudaStream_t st);
 cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);

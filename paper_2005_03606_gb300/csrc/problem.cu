@@ -444,8 +444,20 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   const double om = P->desc.omega;
   void* cur = lv.x0;
   void* oth = lv.x1;
-  if ((e = cudaMemsetAsync(cur, 0, vb, st)) != cudaSuccess) *stt = oom_or_cuda(e, "zero");
-  for (int k = 0; k < P->desc.nu_pre; ++k) {
+  // the V-cycle starts from a zero iterate: the first pre-smoothing step is
+  // omega D^-1 b where the sweep supports it (no zeroing, no read of x)
+  int k0 = 0;
+  if (P->desc.nu_pre > 0) {
+    e = launch_sweep(lv.op, SW_JACOBI0, vec64, cur, lv.b, oth, om, nullptr, nullptr, st);
+    if (e == cudaSuccess) {
+      std::swap(cur, oth);
+      k0 = 1;
+    } else if (e != cudaErrorNotSupported) {
+      *stt = oom_or_cuda(e, "pre-smooth");
+    }
+  }
+  if (k0 == 0 && (e = cudaMemsetAsync(cur, 0, vb, st)) != cudaSuccess) *stt = oom_or_cuda(e, "zero");
+  for (int k = k0; k < P->desc.nu_pre; ++k) {
     if ((e = launch_sweep(lv.op, SW_JACOBI, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
       *stt = oom_or_cuda(e, "pre-smooth");
     std::swap(cur, oth);

@@ -204,12 +204,14 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
       for (int dy = 0; dy < 3; ++dy) {
         const TV* xr = x + (v + (dy - 1) * n1 + (D == 3 ? (dz - 1) * plane : 0));
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy + 9 * dz] = (TA)__ldg(xr + (dx - 1));
+        for (int dx = 0; dx < 3; ++dx) u[dx + 3 * dy + 9 * dz] = MODE == SW_JACOBI0 ? (TA)0 : (TA)__ldg(xr + (dx - 1));
       }
     TA Au, dg;
     vertex_apply<D, TA, CMP, TS>(op, i, j, k, u, &Au, &dg);
     const TA uv = u[D == 3 ? 13 : 4];
-    if (MODE == SW_JACOBI) {
+    if (MODE == SW_JACOBI0) {
+      y[v] = (TV)(omega * (TA)b[v] / dg);
+    } else if (MODE == SW_JACOBI) {
       y[v] = (TV)(uv + omega * ((TA)b[v] - Au) / dg);
     } else if (MODE == SW_RESID) {
       y[v] = (TV)((TA)b[v] - Au);
@@ -304,8 +306,12 @@ __global__ void __launch_bounds__(kBX * kBY) stencil_sweep_kernel(const LevelOp 
     const int v = D == 2 ? j * n1 + i : (k * n1 + j) * n1 + i;
     const int plane = n1 * n1;
     const TS* S = reinterpret_cast<const TS*>(op.stencil) + v;
-    const TA uv = (TA)__ldg(x + v);
     const TA dg = (TA)__ldg(S + (size_t)C * nv);
+    if (MODE == SW_JACOBI0) {
+      y[v] = (TV)(omega * (TA)b[v] / dg);
+      return;
+    }
+    const TA uv = (TA)__ldg(x + v);
     // FP32: difference form sum_q c_q (u_q - u_v) (exact for constants); FP64:
     // plain sum_q c_q u_q, half the FP64 operations, rounding far below need
     constexpr bool kDiff = sizeof(TA) == 4;
@@ -867,41 +873,56 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
   float d1 = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     const int v = op.touched[t];
-    float u[27];
+    if constexpr (MODE == SW_JACOBI0) {   // zero iterate: only the diagonal is needed
+      float dg;
+      if (t < cap) {
+        dg = __ldg(op.tcoef + t + (size_t)13 * cap);
+      } else {
+        float u0[27];
 #pragma unroll
-    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx)
-          u[dx + 3 * dy + 9 * dz] = __ldg(x + (size_t)v + (dx - 1) + (dy - 1) * n1 + (size_t)(dz - 1) * n1 * n1);
-    float Au, dg;
-    const float uv = u[13];
-    // right-hand side (the bulk pass's value for the matvec) fetched up front
-    const float bv = MODE == SW_MATVEC ? y[v] : __ldg(b + v);
-    if (t < cap) {
-      // all 27 coefficient loads issued before the first use (independent of u)
-      const float* cf = op.tcoef + t;
-      float c[27];
-#pragma unroll
-      for (int q = 0; q < 27; ++q) c[q] = __ldg(cf + (size_t)q * cap);
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 0; q < 27; ++q)
-        if (q != 13) acc = fmaf(c[q], u[q] - uv, acc);
-      Au = acc;
-      dg = c[13];
+        for (int q = 0; q < 27; ++q) u0[q] = 0.f;
+        float Au0;
+        const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
+        vertex_apply<3, float, true, float>(op, i, j, k, u0, &Au0, &dg);
+      }
+      y[v] = omega * __ldg(b + v) / dg;
     } else {
-      const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
-      vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
-    }
-    if (MODE == SW_JACOBI) {
-      y[v] = uv + omega * (bv - Au) / dg;
-    } else if (MODE == SW_RESID) {
-      y[v] = bv - Au;
-    } else {
-      y[v] = Au;
-      d1 += uv * (Au - bv);   // bv: the bulk pass's value at v
+      float u[27];
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx)
+            u[dx + 3 * dy + 9 * dz] = __ldg(x + (size_t)v + (dx - 1) + (dy - 1) * n1 + (size_t)(dz - 1) * n1 * n1);
+      float Au, dg;
+      const float uv = u[13];
+      // right-hand side (the bulk pass's value for the matvec) fetched up front
+      const float bv = MODE == SW_MATVEC ? y[v] : __ldg(b + v);
+      if (t < cap) {
+        // all 27 coefficient loads issued before the first use (independent of u)
+        const float* cf = op.tcoef + t;
+        float c[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) c[q] = __ldg(cf + (size_t)q * cap);
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 27; ++q)
+          if (q != 13) acc = fmaf(c[q], u[q] - uv, acc);
+        Au = acc;
+        dg = c[13];
+      } else {
+        const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
+        vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
+      }
+      if (MODE == SW_JACOBI) {
+        y[v] = uv + omega * (bv - Au) / dg;
+      } else if (MODE == SW_RESID) {
+        y[v] = bv - Au;
+      } else {
+        y[v] = Au;
+        d1 += uv * (Au - bv);   // bv: the bulk pass's value at v
+      }
     }
   }
   if (MODE == SW_MATVEC) {
@@ -1290,6 +1311,51 @@ __global__ void touched_write_kernel(long long nv, const uint8_t* __restrict__ f
   }
 }
 
+// Zero-iterate damped Jacobi on the finest compressed 3D level, geometric
+// part: y = omega b / (h/3 G) with G the sum of eps over the 8 cells at the
+// vertex (b and the padded eps rows are the only reads; the fix-up pass
+// handles the vertices next to surplus cells).
+__global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp op, const float* __restrict__ b,
+                                                                  float* __restrict__ y, float omega, int ntx,
+                                                                  int nty, int ntiles) {
+  const int N = op.N, n1 = N + 1;
+  const size_t plane = (size_t)n1 * n1;
+  const float c0 = omega / (4.f * -op.gk32);   // omega / (h / 3)
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int q = 4 * (tx * kGeoBX + threadIdx.x);
+    const int j = 1 + ty * kGeoBY + threadIdx.y;
+    const int k0 = 1 + tz * kGZ;
+    const int k1 = min(N - 1, k0 + kGZ - 1);
+    if (q >= n1 || j >= N || k0 > k1) continue;
+    const bool hl = q > 0;
+    unsigned vmask = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (q + e >= 1 && q + e <= N - 1) vmask |= 1u << e;
+    float g[2][5], elm[5];
+    load_eps10(op.eps_pad, N, k0 - 1, j, q, hl, true, g);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) elm[c] = g[0][c] + g[1][c];
+    for (int k = k0; k <= k1; ++k) {
+      load_eps10(op.eps_pad, N, k, j, q, hl, true, g);
+      const float4 b4 = __ldg(reinterpret_cast<const float4*>(b + (size_t)k * plane + (size_t)j * n1 + q));
+      float ey[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float elc = g[0][c] + g[1][c];
+        ey[c] = elm[c] + elc;
+        elm[c] = elc;
+      }
+      const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+      float out[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[e] = (vmask >> e) & 1u ? __fdividef(c0 * bb[e], ey[e] + ey[e + 1]) : 0.f;
+      *reinterpret_cast<float4*>(y + (size_t)k * plane + (size_t)j * n1 + q) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+  }
+}
+
 cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
                         double* partials, int* nblocks, cudaStream_t st) {
   const int nq = (op.N + 1) / 4;
@@ -1308,7 +1374,11 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   const dim3 blk(kGeoBX, kGeoBY, 1);
 
   double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
-  if (mode == SW_JACOBI) {
+  if (mode == SW_JACOBI0) {
+    sweep3_jacobi0<<<nb_bulk, blk, 0, st>>>(op, b, y, omega, ntx, nty, ntiles);
+    count_launches(1);
+    sweep3_fixup<SW_JACOBI0><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+  } else if (mode == SW_JACOBI) {
     sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup<SW_JACOBI><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
@@ -1336,7 +1406,11 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     dim3 blk(kBX, kBY, 1);
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, ni);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-    if (mode == SW_JACOBI)
+    if (mode == SW_JACOBI0)
+      stencil_sweep_kernel<3, float, float, float, SW_JACOBI0><<<grd, blk, 0, st>>>(op, (const float*)x,
+                                                                                  (const float*)b, (float*)y,
+                                                                                  (float)omega, partials);
+    else if (mode == SW_JACOBI)
       stencil_sweep_kernel<3, float, float, float, SW_JACOBI><<<grd, blk, 0, st>>>(op, (const float*)x,
                                                                                  (const float*)b, (float*)y,
                                                                                  (float)omega, partials);
@@ -1352,13 +1426,15 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   }
   if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched && op.eps_pad)
     return launch_geo4(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, nblocks, st);
-  if (D == 3 && CMP && sizeof(TV) == 8 && mode != SW_JACOBI && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
+  if (D == 3 && CMP && sizeof(TV) == 8 && (mode == SW_RESID || mode == SW_MATVEC) && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched)
     return launch_geo64(op, mode, (const double*)x, (const double*)b, (double*)y, partials, nblocks, st);
   if (!CMP && op.stencil) {
     dim3 blk(kBX, kBY, 1);
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-    if (mode == SW_JACOBI)
+    if (mode == SW_JACOBI0)
+      stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI0><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+    else if (mode == SW_JACOBI)
       stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
     else if (mode == SW_RESID)
       stencil_sweep_kernel<D, TV, TA, TS, SW_RESID><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
@@ -1369,6 +1445,7 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   // the plane-streaming kernel needs enough (x, y, z-run) tiles to fill the GPU;
   // smaller grids run one vertex per thread
   if (D == 3 && op.N >= 243) {
+    if (mode == SW_JACOBI0) return cudaErrorNotSupported;
     dim3 blk(kTX, kTY, 1);
     dim3 grd((ni + kTX - 1) / kTX, (ni + kTY - 1) / kTY, (ni + kZC - 1) / kZC);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
@@ -1383,7 +1460,9 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
   dim3 blk(kBX, kBY, 1);
   dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-  if (mode == SW_JACOBI)
+  if (mode == SW_JACOBI0)
+    sweep_kernel<D, TV, TA, TS, SW_JACOBI0, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+  else if (mode == SW_JACOBI)
     sweep_kernel<D, TV, TA, TS, SW_JACOBI, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
   else if (mode == SW_RESID)
     sweep_kernel<D, TV, TA, TS, SW_RESID, CMP><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
