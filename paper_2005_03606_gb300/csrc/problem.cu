@@ -158,6 +158,8 @@ struct mg_problem {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Job> todo, ready;
+  std::vector<Job> held;          // finished jobs not yet published (see publish_ready)
+  int held_since = -1;            // cycle at which the oldest held job was taken
   int in_flight = 0;
   bool stop = false;
   int inject_fail = 0;
@@ -671,6 +673,8 @@ mg_status enqueue_async(mg_problem* P, int s) {
 
 // Publishes every completed job (at a cycle boundary).  wait = 1 blocks for
 // at least one job when any is in flight.  Returns the number published.
+constexpr int kHoldCycles = 8;
+
 mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
   *npub = 0;
   std::vector<Job> done;
@@ -706,6 +710,34 @@ mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
       free_store(j.store, P->st);
       continue;
     }
+    if (P->held.empty()) P->held_since = P->cycles;
+    P->held.push_back(j);
+  }
+  if (P->held.empty()) return bad;
+  // Every publication costs a Galerkin rebuild, a new FP64 residual and a
+  // restart of the Krylov iteration, so finished chunks are held back until a
+  // whole accuracy level is complete, the schedule is done, the solver waits,
+  // or kHoldCycles cycles have passed since the first one finished.
+  bool now = wait || P->cycles - P->held_since >= kHoldCycles;
+  if (!now) {
+    std::lock_guard<std::mutex> lk(P->mu);
+    now = P->todo.empty() && P->in_flight == 0;
+  }
+  if (!now) {
+    std::vector<int> best(P->nchunk, 0);
+    for (int c = 0; c < P->nchunk; ++c) best[c] = P->cur[c].s;
+    for (const Job& j : P->held) best[j.chunk] = std::max(best[j.chunk], j.store.s);
+    for (const Job& j : P->held) {
+      bool level_done = true;
+      for (int c = 0; c < P->nchunk && level_done; ++c) level_done = best[c] >= j.store.s;
+      if (level_done) {
+        now = true;
+        break;
+      }
+    }
+  }
+  if (!now) return bad;
+  for (Job& j : P->held) {
     if (j.store.s > P->cur[j.chunk].s) {
       install(P, j.chunk, j.store);
       (*npub)++;
@@ -713,6 +745,7 @@ mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
       free_store(j.store, P->st);
     }
   }
+  P->held.clear();
   if (*npub) {
     mg_status s = upload_tables(P);
     if (s != MG_OK) return s;
@@ -738,8 +771,10 @@ void stop_worker(mg_problem* P) {
   }
   for (Job& j : P->todo)
     if (j.ev) cudaEventDestroy(j.ev);
+  for (Job& j : P->held) free_store(j.store, P->side);
   P->ready.clear();
   P->todo.clear();
+  P->held.clear();
   P->in_flight = 0;
 }
 
@@ -1052,7 +1087,7 @@ mg_status mg_assemble_level(mg_problem* P, int s, int async) {
     int npub = 0;
     {
       std::lock_guard<std::mutex> lk(P->mu);
-      if (P->in_flight == 0) break;
+      if (P->in_flight == 0 && P->held.empty()) break;
     }
     mg_status st = publish_ready(P, true, &npub);
     if (st != MG_OK) return st;
@@ -1179,7 +1214,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       bool pending;
       {
         std::lock_guard<std::mutex> lk(P->mu);
-        pending = P->in_flight > 0;
+        pending = P->in_flight > 0 || !P->held.empty();
       }
       if (all_final(P) && !pending) {
         result = MG_OK;
