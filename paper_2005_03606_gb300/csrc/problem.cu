@@ -143,7 +143,10 @@ struct mg_problem {
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   int inner_its = 0;
+  int last_inner_its = 0;
   bool have_correction = false;
+  bool trace = false;             // MG_TRACE: outer-loop trace on stderr
+  double eta_min = 1e-3;          // smallest relative reduction asked of one FP32 inner solve
   double eta2 = 1e-10;            // inner tolerance (squared, relative to the unit-scaled residual)
   std::vector<void*> allocs;      // long-lived device allocations
   // outer-loop state
@@ -492,6 +495,7 @@ mg_status outer_restart(mg_problem* P) {
   if (P->mixed) {
     MG_CHECK(launch_scale_residual(l0.nvert, P->r, (float*)l0.b, P->sc, st));
     MG_CHECK(cudaMemsetAsync(P->e32, 0, sizeof(float) * l0.nvert, st));
+    P->last_inner_its = P->inner_its;
     P->inner_its = 0;
     P->have_correction = false;
   }
@@ -607,7 +611,7 @@ constexpr int kMaxInner = 400;
 void set_inner_tolerance(mg_problem* P) {
   const double rel = std::sqrt(P->rr / (P->ff > 0 ? P->ff : 1.0));
   double eta = 0.3 * P->desc.rtol / std::max(rel, 1e-300);
-  eta = std::min(std::max(eta, 1e-5), 0.1);
+  eta = std::min(std::max(eta, P->eta_min), 0.1);
   P->eta2 = eta * eta;
 }
 
@@ -829,6 +833,8 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   fill_eps(d.eps, d.dim, &P->eps);
   if (cudaGetDevice(&P->device) != cudaSuccess) P->device = 0;
   if (const char* ng = getenv("MG_NO_GRAPHS")) P->use_graphs = ng[0] == '0';
+  P->trace = getenv("MG_TRACE") != nullptr;
+  if (const char* em = getenv("MG_INNER_ETA")) P->eta_min = atof(em) > 0 ? atof(em) : P->eta_min;
   auto fail = [&](mg_status s) {
     mg_destroy_problem(P);
     return s;
@@ -1204,6 +1210,9 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       }
       if (P->ff <= 0) P->ff = P->rr > 0 ? P->rr : 1.0;
       if (P->mixed) set_inner_tolerance(P);
+      if (P->trace)   // MG_TRACE=1: one line per outer restart on stderr
+        fprintf(stderr, "mg: restart at cycle %d  rel %.3e  inner its %d  eta %.1e  final %d\n", P->cycles,
+                std::sqrt(P->rr / (P->ff > 0 ? P->ff : 1.0)), P->last_inner_its, std::sqrt(P->eta2), all_final(P) ? 1 : 0);
       // divergence is judged against the residual of the current operator
       // at the last restart (a publication changes the operator)
       seg_rr = P->rr;
