@@ -146,11 +146,12 @@ struct mg_problem {
   int last_inner_its = 0;
   bool have_correction = false;
   bool trace = false;             // MG_TRACE: outer-loop trace on stderr
-  double eta_min = 1e-3;          // smallest relative reduction asked of one FP32 inner solve
+  double eta_min = 1e-2;          // smallest relative reduction asked of one FP32 inner solve
   double eta2 = 1e-10;            // inner tolerance (squared, relative to the unit-scaled residual)
   std::vector<void*> allocs;      // long-lived device allocations
   // outer-loop state
   bool first = true, need_restart = true;
+  bool keep_dir = false;          // next restart is a reliable update (see outer_restart)
   double ff = 0.0, rr = 0.0, rr_first = 0.0;
   int cycles = 0, publishes = 0;
   cudaGraphExec_t g_iter[2] = {nullptr, nullptr};
@@ -499,17 +500,24 @@ mg_status outer_restart(mg_problem* P) {
     P->inner_its = 0;
     P->have_correction = false;
   }
-  P->first = true;
+  // A restart after a reliable update (same operator, the FP32 correction
+  // folded into u) keeps the flexible-CG search direction p and q = A p: only
+  // the residual is replaced by the true one, so the Krylov process goes on
+  // instead of starting over.  After a publication the operator changed and
+  // the iteration starts afresh.
+  P->first = !(P->mixed && P->keep_dir);
+  P->keep_dir = false;
   P->need_restart = false;
   return MG_OK;
 }
 
 // u += s e (mixed paths): the FP32 correction of the inner solve in FP64
-mg_status apply_inner_correction(mg_problem* P) {
+mg_status apply_inner_correction(mg_problem* P, bool reliable = false) {
   if (!P->mixed || !P->have_correction) return MG_OK;
   MG_CHECK(launch_apply_correction(P->lev[0].nvert, P->u, P->e32, P->sc, P->st));
   P->have_correction = false;
   P->need_restart = true;
+  P->keep_dir = reliable && P->desc.outer == MG_OUTER_FCG && !getenv("MG_RESTART_KRYLOV");
   return MG_OK;
 }
 
@@ -624,7 +632,7 @@ mg_status mixed_after_iteration(mg_problem* P, bool* diverged) {
   *diverged = !std::isfinite(rin) || rin > 1e8;
   if (*diverged) return MG_OK;
   if (P->desc.outer == MG_OUTER_RICHARDSON || rin <= P->eta2 || P->inner_its >= kMaxInner)
-    return apply_inner_correction(P);
+    return apply_inner_correction(P, true);
   return MG_OK;
 }
 
@@ -757,6 +765,7 @@ mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
     if (s != MG_OK) return s;
     P->publishes += *npub;
     P->need_restart = true;
+    P->keep_dir = false;
   }
   return bad;
 }
