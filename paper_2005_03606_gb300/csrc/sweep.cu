@@ -1542,6 +1542,47 @@ __global__ void prolong_kernel(int Nc, const TV* __restrict__ ec, TV* __restrict
   ef[vf] += acc;
 }
 
+// 3D FP32 prolongation with 4 consecutive fine x-vertices per thread (rows of
+// (3 Nc + 1) % 4 == 0 floats): the 2 x 2 coarse (y, z) neighbours are first
+// combined for the 3 coarse columns the quad spans, then interpolated along x;
+// one float4 read-modify-write per thread.  Fine boundary vertices in x get
+// P e_c = 0 added (the coarse boundary values are zero).
+__global__ void prolong3_x4_kernel(int Nc, const float* __restrict__ ec, float* __restrict__ ef) {
+  const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
+  const int q = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int fy = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int fz = 1 + blockIdx.z;
+  if (q >= nf1 || fy >= Nf) return;
+  const int cy = fy / 3, cz = fz / 3;
+  const float wy1 = (float)(fy - 3 * cy) * (1.f / 3.f), wz1 = (float)(fz - 3 * cz) * (1.f / 3.f);
+  const float wy0 = 1.f - wy1, wz0 = 1.f - wz1;
+  const int cx0 = q / 3;
+  float V[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int cx = min(cx0 + c, Nc);
+    const float* e = ec + ((size_t)cz * nc1 + cy) * nc1 + cx;
+    const float a00 = __ldg(e), a01 = __ldg(e + nc1), a10 = __ldg(e + (size_t)nc1 * nc1),
+                a11 = __ldg(e + (size_t)nc1 * nc1 + nc1);
+    V[c] = wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
+  }
+  float4* dst = reinterpret_cast<float4*>(ef + ((size_t)fz * nf1 + fy) * nf1 + q);
+  float4 o = *dst;
+  float add[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int x = q + e, cx = x / 3, r = x - 3 * cx;
+    const int jx = cx - cx0;
+    const float w1 = (float)r * (1.f / 3.f);
+    add[e] = (1.f - w1) * (jx == 0 ? V[0] : V[1]) + w1 * (jx == 0 ? V[1] : V[2]);
+  }
+  o.x += add[0];
+  o.y += add[1];
+  o.z += add[2];
+  o.w += add[3];
+  *dst = o;
+}
+
 int vgrid(long long n) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 32) b = 152LL * 32;
@@ -1707,6 +1748,13 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
 }
 
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st) {
+  if (dim == 3 && !vec64 && (3 * Nc + 1) % 4 == 0 && ((uintptr_t)ef & 15) == 0) {
+    const int nq = (3 * Nc + 1) / 4;
+    const dim3 blk(32, 8, 1);
+    const dim3 g((nq + 31) / 32, (3 * Nc - 1 + 7) / 8, 3 * Nc - 1);
+    prolong3_x4_kernel<<<g, blk, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+    return launched();
+  }
   const int nf = 3 * Nc - 1;
   const dim3 blk(32, 8, 1);
   const dim3 g((nf + 31) / 32, (nf + 7) / 8, dim == 3 ? nf : 1);
