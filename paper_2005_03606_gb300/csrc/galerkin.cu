@@ -215,6 +215,23 @@ __global__ void coarse_factor_kernel(const LevelOp op, double* L) {
   }
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) L[i * n + j] = j <= i ? M[i][j] : 0.0;
+  // the inverse, column by column from the factor (L[n*n ..]: row-major, used
+  // by the single-block tail of the FP32 V-cycle)
+  double* Ainv = L + n * n;
+  for (int c = 0; c < n; ++c) {
+    double z[NV];
+    for (int i = 0; i < n; ++i) {
+      double t = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= M[i][k] * z[k];
+      z[i] = t / M[i][i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = z[i];
+      for (int k = i + 1; k < n; ++k) t -= M[k][i] * z[k];
+      z[i] = t / M[i][i];
+    }
+    for (int i = 0; i < n; ++i) Ainv[i * n + c] = z[i];
+  }
 }
 
 template <int D, typename TV>

@@ -258,6 +258,12 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st);
+// the two coarsest levels of an FP32 V-cycle in one block (level N = 9 with
+// full storage and stencils, then the coarsest level solved with the inverse
+// at Lc + n^2); cudaErrorNotSupported (nothing launched) otherwise
+bool vcycle_tail_supported(const LevelOp& op);
+cudaError_t launch_vcycle_tail(const LevelOp& op, const double* Lc, const float* b, float* x, float omega,
+                               int nu_pre, int nu_post, cudaStream_t st);
 cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream_t st);
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
                                  cudaStream_t st);

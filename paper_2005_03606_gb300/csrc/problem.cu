@@ -125,7 +125,7 @@ struct mg_problem {
   long long npartials = 0;
   DevScalars* sc = nullptr;
   DevScalars* h_sc = nullptr;     // pinned
-  double* Lc = nullptr;           // coarse Cholesky factor
+  double* Lc = nullptr;           // coarse Cholesky factor, then the coarse inverse
   uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
   // interface cells per chunk (fields with piecewise-constant eps): only these
   // are integrated at s > 1, every other cell keeps its geometric stencil
@@ -448,6 +448,13 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   }
   const size_t vb = P->tv * lv.nvert;
   const double om = P->desc.omega;
+  if (l == P->L - 2 && !vec64 && vcycle_tail_supported(lv.op) && !getenv("MG_NO_VTAIL")) {
+    // this level and the coarsest in one block
+    e = launch_vcycle_tail(lv.op, P->Lc, (const float*)lv.b, (float*)lv.x0, (float)om, P->desc.nu_pre,
+                           P->desc.nu_post, st);
+    if (e != cudaSuccess) *stt = oom_or_cuda(e, "V-cycle tail");
+    return lv.x0;
+  }
   void* cur = lv.x0;
   void* oth = lv.x1;
   // the V-cycle starts from a zero iterate: the first pre-smoothing step is
@@ -1006,7 +1013,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   }
   if ((e = dalloc(P, &P->partials, sizeof(double) * P->npartials)) != cudaSuccess ||
       (e = dalloc(P, &P->sc, sizeof(DevScalars))) != cudaSuccess ||
-      (e = dalloc(P, &P->Lc, sizeof(double) * 64)) != cudaSuccess ||
+      (e = dalloc(P, &P->Lc, sizeof(double) * 128)) != cudaSuccess ||
       (e = dalloc(P, &P->d_totals, sizeof(uint32_t) * 8)) != cudaSuccess)
     return fail(oom_or_cuda(e, "scalars"));
   cudaMemsetAsync(P->sc, 0, sizeof(DevScalars), P->st);

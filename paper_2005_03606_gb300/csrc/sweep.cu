@@ -1583,6 +1583,152 @@ __global__ void prolong3_x4_kernel(int Nc, const float* __restrict__ ec, float* 
   *dst = o;
 }
 
+// ---------------------------------------------------------------- V-cycle tail in one block
+// The two coarsest levels of an FP32 V-cycle (N = 9 with its assembled
+// stencils, and the 3^d-cell coarsest level solved with its precomputed
+// inverse) in a single block, everything in shared memory: pre-smoothing
+// from the zero iterate, residual, restriction, coarse solve, prolongation
+// and post-smoothing, the same steps and arithmetic as the per-level kernels,
+// without their launch latencies.  One thread per interior vertex.
+constexpr int kTailN = 9;
+constexpr int kTailThreads = 512;
+
+template <int D>
+struct TailDims {
+  static constexpr int n1 = kTailN + 1;
+  static constexpr int nv = D == 3 ? n1 * n1 * n1 : n1 * n1;
+  static constexpr int NS = D == 3 ? 27 : 9;
+  static constexpr int ni = kTailN - 1;
+  static constexpr int nint = D == 3 ? ni * ni * ni : ni * ni;
+  static constexpr int nc = D == 3 ? 8 : 4;    // interior vertices of the coarsest level
+};
+
+template <int D>
+constexpr int tail_smem_bytes() {
+  return (TailDims<D>::NS + 4) * TailDims<D>::nv * (int)sizeof(float);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTailThreads) vcycle_tail_kernel(const float* __restrict__ stencil,
+                                                                   const float* __restrict__ b,
+                                                                   float* __restrict__ xout,
+                                                                   const double* __restrict__ Ainv, float omega,
+                                                                   int nu_pre, int nu_post) {
+  using T = TailDims<D>;
+  constexpr int n1 = T::n1, nv = T::nv, NS = T::NS, C = D == 3 ? 13 : 4;
+  extern __shared__ float tail_smem[];
+  float* S = tail_smem;            // [NS][nv]
+  float* xa = S + NS * nv;
+  float* xb = xa + nv;
+  float* bs = xb + nv;
+  float* rs = bs + nv;
+  __shared__ float bc[T::nc], ec[D == 3 ? 64 : 16];   // coarsest rhs; coarsest iterate on its 4^d grid
+  const int t = threadIdx.x;
+  for (int i = t; i < NS * nv; i += blockDim.x) S[i] = __ldg(stencil + i);
+  for (int i = t; i < nv; i += blockDim.x) {
+    bs[i] = __ldg(b + i);
+    xa[i] = 0.f;
+    xb[i] = 0.f;
+  }
+  for (int i = t; i < (D == 3 ? 64 : 16); i += blockDim.x) ec[i] = 0.f;
+  __syncthreads();
+  // this thread's interior vertex
+  const bool act = t < T::nint;
+  int vi = 1 + t % T::ni, vj = 1 + (t / T::ni) % T::ni, vk = D == 3 ? 1 + t / (T::ni * T::ni) : 0;
+  const int v = act ? (D == 3 ? (vk * n1 + vj) * n1 + vi : vj * n1 + vi) : 0;
+  auto apply = [&](const float* x) -> float {   // sum_q c_q (x_q - x_v)
+    const float xv = x[v];
+    float acc = 0.f;
+#pragma unroll
+    for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int q = dx + 3 * dy + 9 * dz;
+          if (q == C) continue;
+          const int nb = v + (dx - 1) + (dy - 1) * n1 + (D == 3 ? (dz - 1) * n1 * n1 : 0);
+          acc += S[q * nv + v] * (x[nb] - xv);
+        }
+    return acc;
+  };
+  float* cur = xa;
+  float* oth = xb;
+  // pre-smoothing: omega D^-1 b from the zero iterate, then damped Jacobi
+  if (nu_pre > 0) {
+    if (act) cur[v] = omega * bs[v] / S[C * nv + v];
+    __syncthreads();
+  }
+  for (int k = 1; k < nu_pre; ++k) {
+    if (act) oth[v] = cur[v] + omega * (bs[v] - apply(cur)) / S[C * nv + v];
+    __syncthreads();
+    float* tmp = cur;
+    cur = oth;
+    oth = tmp;
+  }
+  // residual, restricted to the coarsest level (R = P^T, 1D weights 1/3, 2/3, 1, 2/3, 1/3)
+  if (act) rs[v] = bs[v] - apply(cur);   // (boundary entries of rs are never read)
+  __syncthreads();
+  if (t < T::nc) {
+    const int I = 1 + (t & 1), J = 1 + ((t >> 1) & 1), K = D == 3 ? 1 + ((t >> 2) & 1) : 0;
+    const float w1[5] = {1.f / 3.f, 2.f / 3.f, 1.f, 2.f / 3.f, 1.f / 3.f};
+    float acc = 0.f;
+    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz)
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          const int fx = 3 * I + dx, fy = 3 * J + dy, fz = 3 * K + dz;
+          const bool inner = fx >= 1 && fx <= kTailN - 1 && fy >= 1 && fy <= kTailN - 1 &&
+                             (D == 2 || (fz >= 1 && fz <= kTailN - 1));
+          const float val = inner ? rs[D == 3 ? (fz * n1 + fy) * n1 + fx : fy * n1 + fx] : 0.f;
+          acc += w1[dx + 2] * w1[dy + 2] * (D == 3 ? w1[dz + 2] : 1.f) * val;
+        }
+    bc[t] = acc;
+  }
+  __syncthreads();
+  // coarsest solve with the precomputed inverse (FP64 accumulation)
+  if (t < T::nc) {
+    double z = 0.0;
+    for (int k = 0; k < T::nc; ++k) z += Ainv[t * T::nc + k] * (double)bc[k];
+    const int I = 1 + (t & 1), J = 1 + ((t >> 1) & 1), K = D == 3 ? 1 + ((t >> 2) & 1) : 0;
+    ec[D == 3 ? (K * 4 + J) * 4 + I : J * 4 + I] = (float)z;
+  }
+  __syncthreads();
+  // prolongation (d-linear, 3:1)
+  if (act) {
+    int f[3] = {vi, vj, vk}, c0[3] = {0, 0, 0};
+    float w0[3] = {1.f, 1.f, 1.f}, w1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      c0[a] = f[a] / 3;
+      w1[a] = (float)(f[a] - 3 * c0[a]) * (1.f / 3.f);
+      w0[a] = 1.f - w1[a];
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int corner = 0; corner < (1 << D); ++corner) {
+      float w = 1.f;
+      int cv[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int up = (corner >> a) & 1;
+        w *= up ? w1[a] : w0[a];
+        cv[a] = c0[a] + up;
+      }
+      acc += w * ec[D == 3 ? (cv[2] * 4 + cv[1]) * 4 + cv[0] : cv[1] * 4 + cv[0]];
+    }
+    cur[v] += acc;
+  }
+  __syncthreads();
+  for (int k = 0; k < nu_post; ++k) {
+    if (act) oth[v] = cur[v] + omega * (bs[v] - apply(cur)) / S[C * nv + v];
+    __syncthreads();
+    float* tmp = cur;
+    cur = oth;
+    oth = tmp;
+  }
+  for (int i = t; i < nv; i += blockDim.x) xout[i] = cur[i];
+}
+
 int vgrid(long long n) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 32) b = 152LL * 32;
@@ -1701,6 +1847,28 @@ __global__ void load_vector_kernel(int N, double val, double* f) {
 }
 
 }  // namespace
+
+bool vcycle_tail_supported(const LevelOp& op) {
+  return op.N == kTailN && !op.compressed && !op.elem64 && op.stencil != nullptr;
+}
+
+cudaError_t launch_vcycle_tail(const LevelOp& op, const double* Lc, const float* b, float* x, float omega,
+                               int nu_pre, int nu_post, cudaStream_t st) {
+  if (!vcycle_tail_supported(op)) return cudaErrorNotSupported;
+  const int n = op.dim == 3 ? 8 : 4;
+  if (op.dim == 3) {
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        vcycle_tail_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tail_smem_bytes<3>());
+    if (attr != cudaSuccess) return attr;
+    vcycle_tail_kernel<3><<<1, kTailThreads, tail_smem_bytes<3>(), st>>>((const float*)op.stencil, b, x, Lc + n * n,
+                                                                          omega, nu_pre, nu_post);
+  } else {
+    vcycle_tail_kernel<2><<<1, kTailThreads, tail_smem_bytes<2>(), st>>>((const float*)op.stencil, b, x, Lc + n * n,
+                                                                          omega, nu_pre, nu_post);
+  }
+  return launched();
+}
+
 
 cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, const void* b, void* y,
                          double omega, double* partials, int* nblocks, cudaStream_t st) {
