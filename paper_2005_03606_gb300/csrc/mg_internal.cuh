@@ -124,9 +124,11 @@ struct LevelOp {
   int tcap;
   // split sweep: eps_c with rows padded to N+1 floats (zero pad), for float4 loads
   const float* eps_pad;
-  // levels with full storage: assembled 3^d-point vertex stencils, SoA
-  // [3^d][(N+1)^d] of the storage type (centre entry: the diagonal; the
-  // operator is applied in difference form), rebuilt with the cell matrices
+  // levels with full storage (and finest levels whose cells all carry a
+  // surplus): assembled 3^d-point vertex stencils, symmetric storage SoA
+  // [(3^d+1)/2][(N+1)^d]: entry 0 the diagonal, entry m > 0 the coupling to
+  // the neighbour at block offset C + m (C the centre of the 3^d block); the
+  // coupling to C - m is the neighbour's entry m.  Rebuilt with the cell matrices.
   const void* stencil;
 };
 

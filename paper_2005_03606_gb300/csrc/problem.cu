@@ -904,7 +904,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     const bool dense0 = l == 0 && P->mixed && D == 3 && L > 1 && P->eps.kind != EPS_BOXES &&
                         P->eps.kind != EPS_DISC && P->eps.kind != EPS_CONST && !getenv("MG_NO_DENSE_STENCIL");
     if (l < L - 1 && (l > 0 || !P->mixed || dense0)) {
-      const size_t sb = (size_t)(D == 3 ? 27 : 9) * lv.nvert * (P->mixed ? 4 : 8);
+      const size_t sb = (size_t)(D == 3 ? 14 : 5) * lv.nvert * (P->mixed ? 4 : 8);   // symmetric storage
       if ((e = dalloc(P, &lv.stencil, sb)) != cudaSuccess) return fail(oom_or_cuda(e, "stencils"));
       cudaMemsetAsync(lv.stencil, 0, sb, P->st);
       op.stencil = lv.stencil;

@@ -51,7 +51,7 @@ size_t estimate_bytes(const mg_problem_desc& d) {
   bytes += nc * per_cell * 2.0;                     // published + one in-flight accuracy
   if (mixed) bytes += nc * (D == 3 ? 112.0 : 32.0) / 9.0 + nc * 1.1;   // scratch (one chunk) + classes
   bytes += nc / (D == 3 ? 27.0 : 9.0) * NP * (mixed ? 4 : 8) * 1.05;   // coarse levels
-  const double ns = D == 3 ? 27.0 : 9.0;                                 // vertex stencils
+  const double ns = D == 3 ? 14.0 : 5.0;                                 // vertex stencils (symmetric)
   bytes += (mixed ? 0.0 : nv * ns * 8) + nv / (D == 3 ? 27.0 : 9.0) * ns * (mixed ? 4 : 8) * 1.05;
   if (mixed && D == 3) bytes += nv * 5 + (nv / 4) * 27 * 4;   // touched list, flags, stencil table
   bytes += 64ull << 20;                             // partials, tables, pool slack

@@ -122,18 +122,21 @@ __device__ __forceinline__ void vertex_coeffs3(const LevelOp& op, int i, int j, 
 #pragma unroll
   for (int oz = 0; oz < 2; ++oz) {
     const int cl = k - 1 + oz;
+    if (cl < 0 || cl >= N) continue;   // cells outside the grid (boundary vertices)
     int ch = cl / op.layers;
     ch = ch < op.nchunk ? ch : op.nchunk - 1;
     const int ll = cl - ch * op.layers;
 #pragma unroll
     for (int oy = 0; oy < 2; ++oy) {
       const int cy = j - 1 + oy;
+      if (cy < 0 || cy >= N) continue;
       const int row = ll * N + cy;
       const int cbase = (cl * N + cy) * N;
       const int segrow = row * op.nseg_x;
 #pragma unroll
       for (int ox = 0; ox < 2; ++ox) {
         const int cx = i - 1 + ox;
+        if (cx < 0 || cx >= N) continue;
         const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
         const float ge = __ldg(op.eps_c + cbase + cx) * hf;
 #pragma unroll
@@ -241,15 +244,15 @@ __global__ void __launch_bounds__(kBX * kBY) sweep_kernel(const LevelOp op, cons
 template <int D, typename TS>
 __global__ void build_stencil_kernel(const LevelOp op, TS* __restrict__ out) {
   constexpr int NV = Dim<D>::NV, NS = D == 3 ? 27 : 9, C = D == 3 ? 13 : 4;
-  const int N = op.N, n1 = N + 1, ni = N - 1;
+  const int N = op.N, n1 = N + 1;
   const long long nv = D == 3 ? (long long)n1 * n1 * n1 : (long long)n1 * n1;
-  const long long nint = D == 3 ? (long long)ni * ni * ni : (long long)ni * ni;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = 1 + (int)(t % ni);
-    const int j = 1 + (int)((t / ni) % ni);
-    const int k = D == 3 ? 1 + (int)(t / ((long long)ni * ni)) : 0;
-    const long long v = D == 3 ? ((long long)k * n1 + j) * n1 + i : (long long)j * n1 + i;
+  // every vertex, boundary ones included: the backward couplings of an
+  // interior vertex to the boundary are read from the boundary vertex's entries
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(v % n1);
+    const int j = (int)((v / n1) % n1);
+    const int k = D == 3 ? (int)(v / ((long long)n1 * n1)) : 0;
     TS c[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) c[q] = 0;
@@ -257,6 +260,7 @@ __global__ void build_stencil_kernel(const LevelOp op, TS* __restrict__ out) {
 #pragma unroll
     for (int ol = 0; ol < 2; ++ol) {
       const int cl = (D == 3 ? k : j) - 1 + ol;
+      if (cl < 0 || cl >= N) continue;   // cells outside the grid
       int ch = cl / op.layers;
       ch = ch < op.nchunk ? ch : op.nchunk - 1;
       const int ll = cl - ch * op.layers;
@@ -265,10 +269,12 @@ __global__ void build_stencil_kernel(const LevelOp op, TS* __restrict__ out) {
 #pragma unroll
       for (int om = 0; om < (D == 3 ? 2 : 1); ++om) {
         const int cy = D == 3 ? j - 1 + om : cl;
+        if (cy < 0 || cy >= N) continue;
         const int row = D == 3 ? ll * N + cy : ll;
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox) {
           const int cx = i - 1 + ox;
+          if (cx < 0 || cx >= N) continue;
           const int oy = D == 3 ? om : ol, oz = D == 3 ? ol : 0;
           const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
           const int lc = row * N + cx;
@@ -284,8 +290,10 @@ __global__ void build_stencil_kernel(const LevelOp op, TS* __restrict__ out) {
       }
     }
     c[C] = dg;
+    // symmetric storage: the diagonal and the couplings to the forward half of
+    // the neighbourhood (q > C); the others are the neighbours' own entries
 #pragma unroll
-    for (int q = 0; q < NS; ++q) out[(size_t)q * nv + v] = c[q];
+    for (int q = C; q < NS; ++q) out[(size_t)(q - C) * nv + v] = c[q];
   }
 }
 
@@ -305,8 +313,9 @@ __global__ void __launch_bounds__(kBX * kBY) stencil_sweep_kernel(const LevelOp 
   if (valid) {
     const int v = D == 2 ? j * n1 + i : (k * n1 + j) * n1 + i;
     const int plane = n1 * n1;
-    const TS* S = reinterpret_cast<const TS*>(op.stencil) + v;
-    const TA dg = (TA)__ldg(S + (size_t)C * nv);
+    const TS* S0 = reinterpret_cast<const TS*>(op.stencil);
+    const TS* S = S0 + v;
+    const TA dg = (TA)__ldg(S);
     if (MODE == SW_JACOBI0) {
       y[v] = (TV)(omega * (TA)b[v] / dg);
       return;
@@ -324,8 +333,11 @@ __global__ void __launch_bounds__(kBX * kBY) stencil_sweep_kernel(const LevelOp 
         for (int dx = 0; dx < 3; ++dx) {
           const int q = dx + 3 * dy + 9 * dz;
           if (q == C) continue;
-          const TA uq = (TA)__ldg(x + (v + (dx - 1) + (dy - 1) * n1 + (D == 3 ? (dz - 1) * plane : 0)));
-          acc += (TA)__ldg(S + (size_t)q * nv) * (kDiff ? uq - uv : uq);
+          const int nb = v + (dx - 1) + (dy - 1) * n1 + (D == 3 ? (dz - 1) * plane : 0);
+          const TA uq = (TA)__ldg(x + nb);
+          // forward couplings are stored at v, backward ones at the neighbour (symmetry)
+          const TA cq = q > C ? (TA)__ldg(S + (size_t)(q - C) * nv) : (TA)__ldg(S0 + (size_t)(C - q) * nv + nb);
+          acc += cq * (kDiff ? uq - uv : uq);
         }
     const TA Au = acc;
     if (MODE == SW_JACOBI) {
@@ -1597,7 +1609,7 @@ template <int D>
 struct TailDims {
   static constexpr int n1 = kTailN + 1;
   static constexpr int nv = D == 3 ? n1 * n1 * n1 : n1 * n1;
-  static constexpr int NS = D == 3 ? 27 : 9;
+  static constexpr int NS = D == 3 ? 14 : 5;   // symmetric storage: diagonal + forward couplings
   static constexpr int ni = kTailN - 1;
   static constexpr int nint = D == 3 ? ni * ni * ni : ni * ni;
   static constexpr int nc = D == 3 ? 8 : 4;    // interior vertices of the coarsest level
@@ -1615,7 +1627,7 @@ __global__ void __launch_bounds__(kTailThreads) vcycle_tail_kernel(const float* 
                                                                    const double* __restrict__ Ainv, float omega,
                                                                    int nu_pre, int nu_post) {
   using T = TailDims<D>;
-  constexpr int n1 = T::n1, nv = T::nv, NS = T::NS, C = D == 3 ? 13 : 4;
+  constexpr int n1 = T::n1, nv = T::nv, NS = T::NS, C = D == 3 ? 13 : 4;   // C: centre of the 3^d block
   extern __shared__ float tail_smem[];
   float* S = tail_smem;            // [NS][nv]
   float* xa = S + NS * nv;
@@ -1648,7 +1660,8 @@ __global__ void __launch_bounds__(kTailThreads) vcycle_tail_kernel(const float* 
           const int q = dx + 3 * dy + 9 * dz;
           if (q == C) continue;
           const int nb = v + (dx - 1) + (dy - 1) * n1 + (D == 3 ? (dz - 1) * n1 * n1 : 0);
-          acc += S[q * nv + v] * (x[nb] - xv);
+          const float cq = q > C ? S[(q - C) * nv + v] : S[(C - q) * nv + nb];
+          acc += cq * (x[nb] - xv);
         }
     return acc;
   };
@@ -1656,11 +1669,11 @@ __global__ void __launch_bounds__(kTailThreads) vcycle_tail_kernel(const float* 
   float* oth = xb;
   // pre-smoothing: omega D^-1 b from the zero iterate, then damped Jacobi
   if (nu_pre > 0) {
-    if (act) cur[v] = omega * bs[v] / S[C * nv + v];
+    if (act) cur[v] = omega * bs[v] / S[v];
     __syncthreads();
   }
   for (int k = 1; k < nu_pre; ++k) {
-    if (act) oth[v] = cur[v] + omega * (bs[v] - apply(cur)) / S[C * nv + v];
+    if (act) oth[v] = cur[v] + omega * (bs[v] - apply(cur)) / S[v];
     __syncthreads();
     float* tmp = cur;
     cur = oth;
@@ -1720,7 +1733,7 @@ __global__ void __launch_bounds__(kTailThreads) vcycle_tail_kernel(const float* 
   }
   __syncthreads();
   for (int k = 0; k < nu_post; ++k) {
-    if (act) oth[v] = cur[v] + omega * (bs[v] - apply(cur)) / S[C * nv + v];
+    if (act) oth[v] = cur[v] + omega * (bs[v] - apply(cur)) / S[v];
     __syncthreads();
     float* tmp = cur;
     cur = oth;
@@ -1957,30 +1970,28 @@ cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream
 
 // full FP32 stencils of a compressed 3D level (fields where every cell carries a surplus)
 __global__ void build_stencil_cmp3_kernel(const LevelOp op, float* __restrict__ out) {
-  const int N = op.N, n1 = N + 1, ni = N - 1;
+  const int N = op.N, n1 = N + 1;
   const long long nv = (long long)n1 * n1 * n1;
-  const long long nint = (long long)ni * ni * ni;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nint;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = 1 + (int)(t % ni);
-    const int j = 1 + (int)((t / ni) % ni);
-    const int k = 1 + (int)(t / ((long long)ni * ni));
-    const long long v = ((long long)k * n1 + j) * n1 + i;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+       v += (long long)gridDim.x * blockDim.x) {   // boundary vertices too (their forward couplings)
+    const int i = (int)(v % n1);
+    const int j = (int)((v / n1) % n1);
+    const int k = (int)(v / ((long long)n1 * n1));
     float c[27];
     vertex_coeffs3(op, i, j, k, c);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) out[(size_t)q * nv + v] = c[q];
+    for (int q = 13; q < 27; ++q) out[(size_t)(q - 13) * nv + v] = c[q];   // symmetric storage
   }
 }
 
 cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st) {
   if (!out || (op.compressed && op.dim != 3)) return cudaErrorInvalidValue;
-  const long long ni = op.N - 1;
+  const long long n1 = op.N + 1;
   if (op.compressed) {
-    build_stencil_cmp3_kernel<<<vgrid(ni * ni * ni), 256, 0, st>>>(op, (float*)out);
+    build_stencil_cmp3_kernel<<<vgrid(n1 * n1 * n1), 256, 0, st>>>(op, (float*)out);
     return launched();
   }
-  const int g = vgrid(op.dim == 3 ? ni * ni * ni : ni * ni);
+  const int g = vgrid(op.dim == 3 ? n1 * n1 * n1 : n1 * n1);
   if (op.dim == 2) {
     if (op.elem64) build_stencil_kernel<2, double><<<g, 256, 0, st>>>(op, (double*)out);
     else build_stencil_kernel<2, float><<<g, 256, 0, st>>>(op, (float*)out);
