@@ -308,6 +308,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = rep.aggregate(len(e2e_ms), max_over_ranks(sum(e2e_ms)))
+    serving = serving_leg(mg, args.serving_requests) if args.serving_requests > 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores, _ = oracle_sample(args.workload, int(info0.cycles))
@@ -341,8 +342,66 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": ck,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
+
+
+def serving_leg(mg, n_requests, seed=2004, load_factor=0.7, max_active=8):
+    """The request loop (configuration 'serving'): seeded requests of mixed
+    sizes, each with its own lognormal eps, mixed delayed path to 1e-8.
+    Closed loop first (all submitted at once: throughput), then open loop
+    with Poisson arrivals at load_factor x that throughput; time-to-solution
+    of a request runs from its submission to its completion (server clock)."""
+    reqs = inputs.serving_requests(n_requests, seed=seed, rate_per_s=1.0)
+
+    def desc(r):
+        return mg.problem_desc(r["dim"], r["n_cells"], r["eps"], path=mg.PATH_MIXED_DELAYED,
+                               s_schedule=(1, 2, 4, 8), rtol=1e-8, max_cycles=3000)
+
+    def wait_all(S, tickets, res):
+        while tickets:
+            for t in list(tickets):
+                st, r = S.poll(t)
+                if st != mg.MG_ERR_PENDING:
+                    res.append((st, r))
+                    tickets.remove(t)
+            time.sleep(0.0005)
+
+    S = mg.Server(max_active=max_active)
+    try:
+        res = []
+        t0 = time.perf_counter()
+        tickets = [S.submit(desc(r)) for r in reqs]
+        wait_all(S, tickets, res)
+        closed_s = time.perf_counter() - t0
+        thr = len(reqs) / closed_s
+        ok_closed = sum(1 for st, _ in res if st == mg.MG_OK)
+        rate = load_factor * thr
+        res2, tickets = [], []
+        t0 = time.perf_counter()
+        for r in reqs:
+            due = t0 + r["arrival_s"] / rate
+            while time.perf_counter() < due:
+                for t in list(tickets):
+                    st, rr = S.poll(t)
+                    if st != mg.MG_ERR_PENDING:
+                        res2.append((st, rr))
+                        tickets.remove(t)
+                time.sleep(0.0002)
+            tickets.append(S.submit(desc(r)))
+        wait_all(S, tickets, res2)
+        open_s = time.perf_counter() - t0
+    finally:
+        S.close()
+    tts = sorted(r.total_ms for st, r in res2 if st == mg.MG_OK)
+    return {"requests": len(reqs), "sizes": "uniform over 27^3, 81^3, 243^3 (3D) and 243^2, 729^2 (2D)",
+            "eps": "lognormal, sigma ~ U[0.5, 2], 16 Fourier modes", "path": "mixed delayed, s = 1 -> 8, rtol 1e-8",
+            "max_active": max_active,
+            "closed_loop": {"solves_per_s": thr, "ok": ok_closed, "seconds": closed_s},
+            "open_loop": {"arrival_rate_per_s": rate, "solves_per_s": len(res2) / open_s,
+                          "ok": len(tts), "p50_ms": float(np.percentile(tts, 50)) if tts else None,
+                          "p99_ms": float(np.percentile(tts, 99)) if tts else None}}
 
 
 def run_probe(args, local_rank):
@@ -352,6 +411,9 @@ def run_probe(args, local_rank):
     import torch
     from paper_2005_03606_gb300 import mg
     torch.cuda.set_device(local_rank)
+    if args.probe == "serving":
+        print(json.dumps({"probe": "serving", **serving_leg(mg, args.probe_reps)}), flush=True)
+        return
     if args.probe == "solve":   # whole mixed delayed solves, for launch lists
         w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED, n_cells=args.n)
         ms = []
@@ -391,7 +453,9 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=200,
                     help="cycle count used to scale the oracle sample in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve"],
+    ap.add_argument("--serving-requests", type=int, default=512,
+                    help="requests of the serving leg (0: skip)")
+    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)
