@@ -21,6 +21,9 @@
 // one cell (rows strided over the lanes) and reduce their partial sums with
 // warp shuffles; 32/G cells are in flight per warp.
 #include "mg_internal.cuh"
+
+#include <algorithm>
+#include <vector>
 #include <cstdio>
 #include <climits>
 #include <cmath>
@@ -577,54 +580,96 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   return launched();
 }
 
-// one thread per cell: does a discontinuity cross the open cell?  (Cells
-// touched only on their boundary are flat: sample points lie strictly inside.)
-// The decisions carry a relative margin, so rounding can only add cells.
+// Interface cells: a discontinuity crosses the open cell.  Cells touched only
+// on their boundary are flat (sample points lie strictly inside); decisions
+// carry a margin of 1e-9 h, so rounding can only add cells.
+//  - boxes and the planar jump: the cells crossed by a face form a box of cell
+//    indices (the face's cell layer times the box's overlap range in the other
+//    axes), found on the host and marked here;
+//  - the disc: one thread per cell.
+struct CellRegion {
+  int lo[3], hi[3];   // inclusive cell index ranges
+};
+
+__global__ void mark_regions_kernel(const CellRegion* __restrict__ regions, const long long* __restrict__ start,
+                                    int nreg, int dim, int N, uint8_t* __restrict__ flags) {
+  const long long total = start[nreg];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int r = 0, rh = nreg - 1;   // the region with start[r] <= t < start[r + 1]
+    while (r < rh) {
+      const int mid = (r + rh + 1) / 2;
+      if (start[mid] <= t) r = mid;
+      else rh = mid - 1;
+    }
+    const CellRegion& g = regions[r];
+    long long u = t - start[r];
+    int ci[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      const int w = g.hi[a] - g.lo[a] + 1;
+      ci[a] = g.lo[a] + (int)(u % w);
+      u /= w;
+    }
+    const long long c = dim == 3 ? ((long long)ci[2] * N + ci[1]) * N + ci[0] : (long long)ci[1] * N + ci[0];
+    flags[c] = 1;
+  }
+}
+
 template <int D>
-__global__ void interface_cells_kernel(const EpsDev F, int N, long long chunk_cells, int* __restrict__ lists,
-                                       int* __restrict__ counts) {
+__global__ void mark_disc_kernel(const EpsDev F, int N, uint8_t* __restrict__ flags) {
   long long ncell = 1;
   for (int a = 0; a < D; ++a) ncell *= N;
-  const double h = 1.0 / N, tol = 1e-9 * h;
+  const double h = 1.0 / N;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
-    double lo[3], hi[3];
     long long t = c;
+    double dmin = 0.0, dmax = 0.0;
     for (int a = 0; a < D; ++a) {
       const int ci = (int)(t % N);
       t /= N;
-      lo[a] = ci * h;
-      hi[a] = (ci + 1) * h;
+      const double lo = ci * h, hi = (ci + 1) * h, x = F.center[a];
+      const double near = x < lo ? lo - x : (x > hi ? x - hi : 0.0);
+      const double far = fmax(fabs(x - lo), fabs(x - hi));
+      dmin += near * near;
+      dmax += far * far;
     }
-    bool cut = false;
-    if (F.kind == EPS_BOXES) {
-      for (int b = 0; b < F.n_boxes && !cut; ++b) {
-        bool overlap = true, face = false;
-        for (int a = 0; a < D; ++a) {
-          const double bl = F.box_lo[b][a], bh = F.box_hi[b][a];
-          overlap = overlap && bl <= hi[a] + tol && bh >= lo[a] - tol;
-          face = face || (bl > lo[a] - tol && bl < hi[a] + tol) || (bh > lo[a] - tol && bh < hi[a] + tol);
-        }
-        cut = overlap && face;
-      }
-    } else if (F.kind == EPS_DISC) {
-      double dmin = 0.0, dmax = 0.0;
-      for (int a = 0; a < D; ++a) {
-        const double x = F.center[a];
-        const double near = x < lo[a] ? lo[a] - x : (x > hi[a] ? x - hi[a] : 0.0);
-        const double far = fmax(fabs(x - lo[a]), fabs(x - hi[a]));
-        dmin += near * near;
-        dmax += far * far;
-      }
-      cut = dmin <= F.r2lim * (1.0 + 1e-9) && dmax >= F.r2lim * (1.0 - 1e-9);
-    }
-    if (F.jump_factor != 1.0) cut = cut || (F.jump_x > lo[0] - tol && F.jump_x < hi[0] + tol);
-    if (cut) {
-      const int ch = (int)(c / chunk_cells);
-      const int pos = atomicAdd(&counts[ch], 1);
-      lists[(long long)ch * chunk_cells + pos] = (int)(c - (long long)ch * chunk_cells);
-    }
+    if (dmin <= F.r2lim * (1.0 + 1e-9) && dmax >= F.r2lim * (1.0 - 1e-9)) flags[c] = 1;
   }
+}
+
+// local index of every flagged cell appended to its chunk's list
+__global__ void flags_to_lists_kernel(long long ncell, long long chunk_cells, const uint8_t* __restrict__ flags,
+                                      int* __restrict__ lists, int* __restrict__ counts) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    if (!flags[c]) continue;
+    const int ch = (int)(c / chunk_cells);
+    const int pos = atomicAdd(&counts[ch], 1);
+    lists[(long long)ch * chunk_cells + pos] = (int)(c - (long long)ch * chunk_cells);
+  }
+}
+
+// cells (inclusive range) whose closed interval meets [a, b] (with margin), and
+// whose open interval contains x (with margin; lo > hi when none)
+void overlap_range(double a, double b, int N, int* lo, int* hi) {
+  const double h = 1.0 / N, tol = 1e-9 * h;
+  *lo = N;
+  *hi = -1;
+  for (int c = 0; c < N; ++c)
+    if (a <= (c + 1) * h + tol && b >= c * h - tol) {
+      *lo = std::min(*lo, c);
+      *hi = std::max(*hi, c);
+    }
+}
+void face_range(double x, int N, int* lo, int* hi) {
+  const double h = 1.0 / N, tol = 1e-9 * h;
+  *lo = N;
+  *hi = -1;
+  for (int c = 0; c < N; ++c)
+    if (x > c * h - tol && x < (c + 1) * h + tol) {
+      *lo = std::min(*lo, c);
+      *hi = std::max(*hi, c);
+    }
 }
 
 }  // namespace
@@ -633,10 +678,81 @@ cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long 
                                    int* counts, cudaStream_t st) {
   if (eps->kind != EPS_BOXES && eps->kind != EPS_DISC && eps->kind != EPS_CONST) return cudaErrorNotSupported;
   const long long ncell = (long long)N * N * (dim == 3 ? N : 1);
-  const int g = grid_for(ncell, 256);
-  if (dim == 2) interface_cells_kernel<2><<<g, 256, 0, st>>>(*eps, N, chunk_cells, lists, counts);
-  else interface_cells_kernel<3><<<g, 256, 0, st>>>(*eps, N, chunk_cells, lists, counts);
-  return launched();
+  uint8_t* flags = nullptr;
+  cudaError_t e = cudaMallocAsync(&flags, (size_t)ncell, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(flags, 0, (size_t)ncell, st);
+  // face regions of the boxes and of the planar jump
+  std::vector<CellRegion> regs;
+  auto add_face = [&](int axis, double x, const int* olo, const int* ohi) {
+    int flo, fhi;
+    face_range(x, N, &flo, &fhi);
+    if (flo > fhi) return;
+    CellRegion g{};
+    for (int a = 0; a < 3; ++a) {
+      g.lo[a] = a < dim ? olo[a] : 0;
+      g.hi[a] = a < dim ? ohi[a] : 0;
+    }
+    g.lo[axis] = flo;
+    g.hi[axis] = fhi;
+    for (int a = 0; a < dim; ++a)
+      if (g.lo[a] > g.hi[a]) return;
+    regs.push_back(g);
+  };
+  if (eps->kind == EPS_BOXES) {
+    for (int b = 0; b < eps->n_boxes; ++b) {
+      int olo[3], ohi[3];
+      bool any = true;
+      for (int a = 0; a < dim; ++a) {
+        overlap_range(eps->box_lo[b][a], eps->box_hi[b][a], N, &olo[a], &ohi[a]);
+        any = any && olo[a] <= ohi[a];
+      }
+      if (!any) continue;
+      for (int a = 0; a < dim; ++a) {
+        add_face(a, eps->box_lo[b][a], olo, ohi);
+        add_face(a, eps->box_hi[b][a], olo, ohi);
+      }
+    }
+  }
+  if (eps->jump_factor != 1.0) {
+    const int olo[3] = {0, 0, 0}, ohi[3] = {N - 1, N - 1, N - 1};
+    add_face(0, eps->jump_x, olo, ohi);
+  }
+  CellRegion* d_regs = nullptr;
+  long long* d_start = nullptr;
+  std::vector<long long> start(regs.size() + 1, 0);
+  for (size_t r = 0; r < regs.size(); ++r) {
+    long long v = 1;
+    for (int a = 0; a < dim; ++a) v *= regs[r].hi[a] - regs[r].lo[a] + 1;
+    start[r + 1] = start[r] + v;
+  }
+  if (e == cudaSuccess && !regs.empty()) {
+    e = cudaMallocAsync(&d_regs, sizeof(CellRegion) * regs.size(), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_start, sizeof(long long) * start.size(), st);
+    // pageable sources: staged before the calls return
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_regs, regs.data(), sizeof(CellRegion) * regs.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_start, start.data(), sizeof(long long) * start.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      mark_regions_kernel<<<grid_for(start.back(), 256), 256, 0, st>>>(d_regs, d_start, (int)regs.size(), dim, N,
+                                                                        flags);
+      e = launched();
+    }
+  }
+  if (e == cudaSuccess && eps->kind == EPS_DISC) {
+    if (dim == 2) mark_disc_kernel<2><<<grid_for(ncell, 256), 256, 0, st>>>(*eps, N, flags);
+    else mark_disc_kernel<3><<<grid_for(ncell, 256), 256, 0, st>>>(*eps, N, flags);
+    e = launched();
+  }
+  if (e == cudaSuccess) {
+    flags_to_lists_kernel<<<grid_for(ncell, 256), 256, 0, st>>>(ncell, chunk_cells, flags, lists, counts);
+    e = launched();
+  }
+  if (d_regs) cudaFreeAsync(d_regs, st);
+  if (d_start) cudaFreeAsync(d_start, st);
+  cudaFreeAsync(flags, st);
+  return e;
 }
 
 cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st) {
