@@ -153,14 +153,23 @@ struct XEntryT {
   T th;                     // THETA: x-factor
 };
 
-template <int D, typename T, int KIND>
+template <typename T>
+struct Cplx {   // (cos, sin) pair
+  T c, s;
+};
+
+// MODES: compile-time bound of the Fourier mode loops (>= F.n_modes), so that
+// the per-row phases stay in registers
+template <int D, typename T, int KIND, int MODES>
 __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, const SampleThresholds TH,
                                                                const AsmLaunch A) {
   constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
   constexpr int NW = D == 3 ? 27 : 6;
   const int N = A.N, s = A.s;
   __shared__ T s_t1[kMaxS], s_t2[kMaxS];
-  __shared__ T s_rot_c[kMaxModes], s_rot_s[kMaxModes];
+  // Fourier fields: e^{i 2 pi k_x x} along a row of samples is the row's start
+  // phase times s_X[m][jx] = e^{i pi 2 k_x jx / (N s)}, the same for every cell
+  __shared__ Cplx<T> s_X[KIND == EPS_FOURIER ? MODES : 1][KIND == EPS_FOURIER ? kMaxS : 1];
   __shared__ XEntryT<T> s_x[kAsmThreads / 32][64];
   const FieldT<T> FT(F);
   const T vin = FT.v_in, vout = FT.v_out;
@@ -169,11 +178,12 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     s_t2[j] = (T)(3 * j * j + 3 * j + 1) / (T)(3 * s * s);
   }
   if (KIND == EPS_FOURIER) {
-    for (int m = threadIdx.x; m < F.n_modes; m += blockDim.x) {
+    for (int idx = threadIdx.x; idx < F.n_modes * s; idx += blockDim.x) {
+      const int m = idx / s, j = idx - m * s;
       T sn, cs;
-      t_sincospi<T>((T)(2.0 * F.k[m][0] / ((double)N * s)), &sn, &cs);
-      s_rot_c[m] = cs;
-      s_rot_s[m] = sn;
+      t_sincospi<T>((T)(2.0 * F.k[m][0] * j / ((double)N * s)), &sn, &cs);
+      s_X[m][j].c = cs;
+      s_X[m][j].s = sn;
     }
   }
   __syncthreads();
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
       unsigned long long rowbits = ~0ull;
       double rowd = 0.0;
       T rowth = (T)1;
-      T P_re[KIND == EPS_FOURIER ? kMaxModes : 1], P_im[KIND == EPS_FOURIER ? kMaxModes : 1];
+      T P_re[KIND == EPS_FOURIER ? MODES : 1], P_im[KIND == EPS_FOURIER ? MODES : 1];
       const int my = m0[1] + jy, mz = m0[2] + jz;
       if (KIND == EPS_BOXES) {
         unsigned long long m = 0, cb = cand;
@@ -288,12 +298,17 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
       } else if (KIND == EPS_FOURIER) {
         int gm[3] = {m0[0], my, mz};
         const int twoNs = 2 * N * s;
-        for (int m = 0; m < F.n_modes; ++m) {
-          int n = phase_num(F, m, D, gm, twoNs);
-          T sn, cs;
-          t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
-          P_re[m] = cs;
-          P_im[m] = sn;
+#pragma unroll
+        for (int m = 0; m < MODES; ++m) {
+          P_re[m] = 0;
+          P_im[m] = 0;
+          if (m < F.n_modes) {
+            int n = phase_num(F, m, D, gm, twoNs);
+            T sn, cs;
+            t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
+            P_re[m] = cs;
+            P_im[m] = sn;
+          }
         }
       }
       double dz2 = 0.0;
@@ -316,13 +331,13 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
         } else if (KIND == EPS_THETA) {
           e = (T)1 + (T)(0.3 / D) * (xe.th * rowth);
         } else {
+          // g = sum_m Re(P_m X_m[jx]) (modes beyond n_modes have P = 0)
           T g = 0;
-          for (int m = 0; m < F.n_modes; ++m) {
-            g += P_re[m];
-            T nr = P_re[m] * s_rot_c[m] - P_im[m] * s_rot_s[m];
-            T ni = P_re[m] * s_rot_s[m] + P_im[m] * s_rot_c[m];
-            P_re[m] = nr;
-            P_im[m] = ni;
+#pragma unroll
+          for (int m = 0; m < MODES; ++m) {
+            const Cplx<T> x = s_X[m][jx];
+            g = fma(P_re[m], x.c, g);
+            g = fma(-P_im[m], x.s, g);
           }
           e = vout * t_exp<T>(FT.amp * g);
         }
@@ -570,11 +585,15 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   SampleThresholds TH;
   make_thresholds(F, a.N, a.s, &TH);
   switch (F.kind) {
-    case EPS_CONST: assemble_kernel<D, T, EPS_CONST><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
-    case EPS_DISC: assemble_kernel<D, T, EPS_DISC><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
-    case EPS_FOURIER: assemble_kernel<D, T, EPS_FOURIER><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
-    case EPS_BOXES: assemble_kernel<D, T, EPS_BOXES><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
-    case EPS_THETA: assemble_kernel<D, T, EPS_THETA><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_CONST: assemble_kernel<D, T, EPS_CONST, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_DISC: assemble_kernel<D, T, EPS_DISC, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_FOURIER:
+      if (F.n_modes <= 8) assemble_kernel<D, T, EPS_FOURIER, 8><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a);
+      else if (F.n_modes <= 16) assemble_kernel<D, T, EPS_FOURIER, 16><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a);
+      else assemble_kernel<D, T, EPS_FOURIER, kMaxModes><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a);
+      break;
+    case EPS_BOXES: assemble_kernel<D, T, EPS_BOXES, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
+    case EPS_THETA: assemble_kernel<D, T, EPS_THETA, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();
