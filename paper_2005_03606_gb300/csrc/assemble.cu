@@ -698,7 +698,7 @@ cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long 
   if (eps->kind != EPS_BOXES && eps->kind != EPS_DISC && eps->kind != EPS_CONST) return cudaErrorNotSupported;
   const long long ncell = (long long)N * N * (dim == 3 ? N : 1);
   uint8_t* flags = nullptr;
-  cudaError_t e = cudaMallocAsync(&flags, (size_t)ncell, st);
+  cudaError_t e = mg_malloc_async(&flags, (size_t)ncell, st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(flags, 0, (size_t)ncell, st);
   // face regions of the boxes and of the planar jump
@@ -746,8 +746,8 @@ cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long 
     start[r + 1] = start[r] + v;
   }
   if (e == cudaSuccess && !regs.empty()) {
-    e = cudaMallocAsync(&d_regs, sizeof(CellRegion) * regs.size(), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_start, sizeof(long long) * start.size(), st);
+    e = mg_malloc_async(&d_regs, sizeof(CellRegion) * regs.size(), st);
+    if (e == cudaSuccess) e = mg_malloc_async(&d_start, sizeof(long long) * start.size(), st);
     // pageable sources: staged before the calls return
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_regs, regs.data(), sizeof(CellRegion) * regs.size(), cudaMemcpyHostToDevice, st);

@@ -232,6 +232,15 @@ struct AsmLaunch {
   long long nlist;
 };
 cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st);
+// stream-ordered allocation from the library's memory pool on the current
+// device: freed blocks stay in the pool for the next problems (no release
+// back to the driver), so creating and destroying problems does not pay for
+// driver allocations each time
+cudaError_t mg_malloc_async(void** p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t mg_malloc_async(T** p, size_t bytes, cudaStream_t st) {
+  return mg_malloc_async(reinterpret_cast<void**>(p), bytes, st);
+}
 // interface cells: cells that a discontinuity of eps (box face, disc boundary,
 // planar jump) crosses; every other cell sees one eps value at all its sample
 // points, so its element matrix is the geometric one at every accuracy s.

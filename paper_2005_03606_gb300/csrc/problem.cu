@@ -177,10 +177,41 @@ int ipow3(int L) {
   return r;
 }
 
+}  // namespace
+
+cudaError_t mg::mg_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np;
+      e = cudaMemPoolCreate(&np, &props);
+      if (e != cudaSuccess) return cudaMallocAsync(p, bytes, st);
+      unsigned long long keep = ~0ull;
+      cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+      pools[dev] = np;
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+namespace {
+
 template <typename T>
 cudaError_t dalloc(mg_problem* P, T** ptr, size_t bytes, bool track = true) {
   void* p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, P->st);
+  cudaError_t e = mg_malloc_async(&p, bytes ? bytes : 16, P->st);
   if (e != cudaSuccess) return e;
   *ptr = (T*)p;
   if (track) P->allocs.push_back(p);
@@ -304,7 +335,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
   ChunkStore cs;
   cs.s = s;
   if (!P->mixed) {
-    cudaError_t e = cudaMallocAsync(&cs.a64, sizeof(double) * NP * P->chunk_cells, st);
+    cudaError_t e = mg_malloc_async(&cs.a64, sizeof(double) * NP * P->chunk_cells, st);
     if (e != cudaSuccess) return oom_or_cuda(e, "chunk storage");
     cs.bytes = sizeof(double) * NP * P->chunk_cells;
     if (s == 1 || P->ilist) {
@@ -336,8 +367,8 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
     return MG_OK;
   }
   const size_t cls_bytes = (size_t)P->chunk_nseg * kSegCells;
-  cudaError_t e = cudaMallocAsync(&cs.cls, cls_bytes, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&cs.seg_base, sizeof(uint32_t) * 3 * P->chunk_nseg, st);
+  cudaError_t e = mg_malloc_async(&cs.cls, cls_bytes, st);
+  if (e == cudaSuccess) e = mg_malloc_async(&cs.seg_base, sizeof(uint32_t) * 3 * P->chunk_nseg, st);
   if (e != cudaSuccess) return oom_or_cuda(e, "chunk classes");
   MG_CHECK(cudaMemsetAsync(cs.cls, 0, cls_bytes, st));
   cs.bytes = cls_bytes + sizeof(uint32_t) * 3 * P->chunk_nseg;
@@ -375,7 +406,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
   for (int k = 0; k < 3; ++k) {
     cs.totals[k] = ht[k];
     if (ht[k]) {
-      e = cudaMallocAsync(&cs.pool[k], (size_t)ht[k] * rb[k], st);
+      e = mg_malloc_async(&cs.pool[k], (size_t)ht[k] * rb[k], st);
       if (e != cudaSuccess) return oom_or_cuda(e, "payload pool");
       cs.bytes += (size_t)ht[k] * rb[k];
     }
@@ -1048,7 +1079,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
       (P->eps.kind == EPS_BOXES || P->eps.kind == EPS_DISC || P->eps.kind == EPS_CONST)) {
     int* counts = nullptr;
     if ((e = dalloc(P, &P->ilist, sizeof(int) * (size_t)P->chunk_cells * P->nchunk)) != cudaSuccess ||
-        (e = cudaMallocAsync(&counts, sizeof(int) * P->nchunk, P->st)) != cudaSuccess)
+        (e = mg_malloc_async(&counts, sizeof(int) * P->nchunk, P->st)) != cudaSuccess)
       return fail(oom_or_cuda(e, "interface cells"));
     P->ilist_n.assign(P->nchunk, 0);
     if (!cuda_ok(cudaMemsetAsync(counts, 0, sizeof(int) * P->nchunk, P->st), "memset") ||
@@ -1343,7 +1374,7 @@ mg_status mg_get_element_matrices(const mg_problem* Pc, int level, double* host_
     return MG_ERR_INVALID;
   }
   double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * n, P->st);
+  cudaError_t e = mg_malloc_async(&tmp, sizeof(double) * n, P->st);
   if (e != cudaSuccess) return oom_or_cuda(e, "decode buffer");
   MG_CHECK(launch_decode_matrices(lv.op, nullptr, 0, tmp, P->st));
   MG_CHECK(cudaMemcpyAsync(host_dst, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, P->st));
@@ -1369,8 +1400,8 @@ mg_status mg_get_cell_matrices(const mg_problem* Pc, int level, const int64_t* c
   const int nv = 1 << P->dim;
   long long* dc = nullptr;
   double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(&dc, sizeof(long long) * ncells, P->st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, sizeof(double) * ncells * nv * nv, P->st);
+  cudaError_t e = mg_malloc_async(&dc, sizeof(long long) * ncells, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&tmp, sizeof(double) * ncells * nv * nv, P->st);
   if (e != cudaSuccess) return oom_or_cuda(e, "gather buffers");
   MG_CHECK(cudaMemcpyAsync(dc, cells, sizeof(long long) * ncells, cudaMemcpyHostToDevice, P->st));
   MG_CHECK(launch_decode_matrices(lv.op, dc, (long long)ncells, tmp, P->st));
@@ -1425,10 +1456,10 @@ mg_status mg_apply_level(mg_problem* P, int level, int op, int inner, const doub
   const size_t eb = vec64 ? 8 : 4;
   void *dx = nullptr, *db = nullptr, *dy = nullptr;
   double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(&dx, eb * n, P->st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&db, eb * n, P->st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&dy, eb * n, P->st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, 8 * n, P->st);
+  cudaError_t e = mg_malloc_async(&dx, eb * n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&db, eb * n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&dy, eb * n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&tmp, 8 * n, P->st);
   if (e != cudaSuccess) return oom_or_cuda(e, "buffers");
   std::vector<double> zeros;
   const double* bsrc = b;
@@ -1509,7 +1540,7 @@ mg_status mg_vcycle_apply(mg_problem* P, const double* b, double* e_out) {
   Level& l0 = P->lev[0];
   const size_t n = l0.nvert;
   double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(&tmp, 8 * n, P->st);
+  cudaError_t e = mg_malloc_async(&tmp, 8 * n, P->st);
   if (e != cudaSuccess) return oom_or_cuda(e, "buffer");
   // the V-cycle reads lev[0].b (aliases r on FP64 paths): stage b there
   if (P->mixed) {
