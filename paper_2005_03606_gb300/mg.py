@@ -222,8 +222,12 @@ class Problem:
             _check(st)
         return info
 
-    def solution(self) -> np.ndarray:
-        u = np.zeros(self.nvert)
+    def solution(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """u on the (N+1)^d vertex grid (FP64); `out`, if given, is filled
+        instead (e.g. a view of pinned host memory for fast copies)."""
+        u = np.zeros(self.nvert) if out is None else out
+        if u.dtype != np.float64 or u.size != self.nvert or not u.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of (N+1)^d entries")
         _check(load().mg_get_solution(self.h, _p(u), u.size))
         return u
 
