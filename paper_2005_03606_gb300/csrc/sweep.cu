@@ -970,37 +970,53 @@ constexpr int kFixBlocks = 152 * 2;
 // per vertex, about 40), then a fix-up pass adds the decoded surplus of the
 // cells with records at the touched vertices (exact FP32 entries, FP64 sums).
 // Bulk: 2 vertices per thread (double2 rows), z march as in the FP32 pass.
-struct Rows4d {   // x[q-1], x[q], x[q+1], x[q+2] of three rows j-1, j, j+1
-  double v[3][4];
+template <typename T>
+struct Vec2T;
+template <>
+struct Vec2T<float> {
+  using type = float2;
+};
+template <>
+struct Vec2T<double> {
+  using type = double2;
 };
 
-__device__ __forceinline__ void load_rows4d(const double* __restrict__ p, int n1, bool has_left, bool has_right,
-                                            Rows4d& r) {
+template <typename T>
+struct Rows4 {   // x[q-1], x[q], x[q+1], x[q+2] of three rows j-1, j, j+1
+  T v[3][4];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_rows4(const T* __restrict__ p, int n1, bool has_left, bool has_right,
+                                           Rows4<T>& r) {
+  using V2 = typename Vec2T<T>::type;
 #pragma unroll
   for (int dy = 0; dy < 3; ++dy) {
-    const double* q = p + (dy - 1) * n1;
-    const double2 c = __ldg(reinterpret_cast<const double2*>(q));
-    r.v[dy][0] = has_left ? __ldg(q - 1) : 0.0;
+    const T* q = p + (dy - 1) * n1;
+    const V2 c = __ldg(reinterpret_cast<const V2*>(q));
+    r.v[dy][0] = has_left ? __ldg(q - 1) : (T)0;
     r.v[dy][1] = c.x;
     r.v[dy][2] = c.y;
-    r.v[dy][3] = has_right ? __ldg(q + 2) : 0.0;
+    r.v[dy][3] = has_right ? __ldg(q + 2) : (T)0;
   }
 }
 
 // eps of cells x = q-1, q, q+1 of cell rows j-1 (r = 0) and j (r = 1) of layer l
-__device__ __forceinline__ void load_eps6d(const float* __restrict__ eps, int N, int l, int j, int q,
-                                           bool has_left, bool has_right, double (&g)[2][3]) {
+template <typename T>
+__device__ __forceinline__ void load_eps6(const float* __restrict__ eps, int N, int l, int j, int q,
+                                          bool has_left, bool has_right, T (&g)[2][3]) {
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const float* e = eps + ((size_t)l * N + (j - 1 + r)) * N + q;
-    g[r][0] = has_left ? (double)__ldg(e - 1) : 0.0;
-    g[r][1] = (double)__ldg(e);
-    g[r][2] = has_right ? (double)__ldg(e + 1) : 0.0;
+    g[r][0] = has_left ? (T)__ldg(e - 1) : (T)0;
+    g[r][1] = (T)__ldg(e);
+    g[r][2] = has_right ? (T)__ldg(e + 1) : (T)0;
   }
 }
 
-__device__ __forceinline__ void pair_sums4d(const Rows4d& u, double (&py)[2][3]) {
-  double px[3][3];
+template <typename T>
+__device__ __forceinline__ void pair_sums4(const Rows4<T>& u, T (&py)[2][3]) {
+  T px[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -1011,28 +1027,29 @@ __device__ __forceinline__ void pair_sums4d(const Rows4d& u, double (&py)[2][3])
     for (int c = 0; c < 3; ++c) py[r][c] = px[r][c] + px[r + 1][c];
 }
 
-struct Geo64Ctx {
-  const double* x;
-  const double* b;
-  double* y;
+template <typename T>
+struct Geo2Ctx {
+  const T* x;
+  const T* b;
+  T* y;
   const float* eps;
   int N, n1, q, j;
   size_t plane, row0;
   bool hl, hr, hr2;
-  double h12;
+  T h12, h3, omega;
 };
 
-template <int MODE>
-__device__ __forceinline__ void geo64_step(const Geo64Ctx& c, int k, const Rows4d& uc, Rows4d& un,
-                                           const double (&pyc)[2][3], double (&pyn)[2][3],
-                                           const double (&gm)[2][3], double (&gc)[2][3], const double (&yTm)[3],
-                                           double (&yTc)[3], double& d1, double& d2) {
-  load_rows4d(c.x + (size_t)(k + 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, un);
-  load_eps6d(c.eps, c.N, k, c.j, c.q, c.hl, c.hr2, gc);
-  const double2 b2 = __ldg(reinterpret_cast<const double2*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
-  const double2 m2 = __ldg(reinterpret_cast<const double2*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
-  pair_sums4d(un, pyn);
-  double yZ[3], ez[2][3], ey[3], elm[3], elc[3];
+template <typename T, int MODE>
+__device__ __forceinline__ void geo2_step(const Geo2Ctx<T>& c, int k, const Rows4<T>& uc, Rows4<T>& un,
+                                          const T (&pyc)[2][3], T (&pyn)[2][3], const T (&gm)[2][3], T (&gc)[2][3],
+                                          const T (&yTm)[3], T (&yTc)[3], double& d1, double& d2) {
+  using V2 = typename Vec2T<T>::type;
+  load_rows4<T>(c.x + (size_t)(k + 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, un);
+  load_eps6<T>(c.eps, c.N, k, c.j, c.q, c.hl, c.hr2, gc);
+  const V2 b2 = __ldg(reinterpret_cast<const V2*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
+  const V2 m2 = __ldg(reinterpret_cast<const V2*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
+  pair_sums4<T>(un, pyn);
+  T yZ[3], ez[2][3], ey[3], elm[3], elc[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     yTc[i] = gc[0][i] * (pyc[0][i] + pyn[0][i]) + gc[1][i] * (pyc[1][i] + pyn[1][i]);
@@ -1043,45 +1060,54 @@ __device__ __forceinline__ void geo64_step(const Geo64Ctx& c, int k, const Rows4
     elm[i] = gm[0][i] + gm[1][i];
     elc[i] = gc[0][i] + gc[1][i];
   }
-  const double bb[2] = {b2.x, b2.y};
-  const double um1[2] = {m2.x, m2.y};
-  double out[2];
+  const T bb[2] = {b2.x, b2.y};
+  const T um1[2] = {m2.x, m2.y};
+  T out[2];
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    const double uv = uc.v[1][e + 1];
-    const double G = ey[e] + ey[e + 1];
-    double w = fma(5.0 * uv, G, -(yZ[e] + yZ[e + 1]));
+    const T uv = uc.v[1][e + 1];
+    const T G = ey[e] + ey[e + 1];
+    T w = fma((T)5 * uv, G, -(yZ[e] + yZ[e + 1]));
     w = fma(ey[e], uc.v[1][e], w);                         // x - 1
     w = fma(ey[e + 1], uc.v[1][e + 2], w);                 // x + 1
     w = fma(ez[0][e] + ez[0][e + 1], uc.v[0][e + 1], w);   // y - 1
     w = fma(ez[1][e] + ez[1][e + 1], uc.v[2][e + 1], w);   // y + 1
     w = fma(elm[e] + elm[e + 1], um1[e], w);               // z - 1
     w = fma(elc[e] + elc[e + 1], un.v[1][e + 1], w);       // z + 1
-    const double acc = c.h12 * w;
+    const T acc = c.h12 * w;
     const int i = c.q + e;
     const bool valid = i >= 1 && i <= c.N - 1;
-    double r;
-    if (MODE == SW_RESID) r = bb[e] - acc;
-    else {
+    T r;
+    if (MODE == SW_JACOBI) {
+      if (sizeof(T) == 4) r = uv + c.omega * __fdividef((float)(bb[e] - acc), (float)(c.h3 * G));
+      else r = uv + c.omega * (bb[e] - acc) / (c.h3 * G);
+    } else if (MODE == SW_RESID) {
+      r = bb[e] - acc;
+    } else {
       r = acc;
       if (valid) {
-        d1 += uv * acc;
-        d2 += uv * bb[e];
+        d1 += (double)uv * (double)acc;
+        d2 += (double)uv * (double)bb[e];
       }
     }
-    out[e] = valid ? r : 0.0;
+    out[e] = valid ? r : (T)0;
   }
-  *reinterpret_cast<double2*>(c.y + (size_t)k * c.plane + c.row0 + c.q) = make_double2(out[0], out[1]);
+  V2 o;
+  o.x = out[0];
+  o.y = out[1];
+  *reinterpret_cast<V2*>(c.y + (size_t)k * c.plane + c.row0 + c.q) = o;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo64(const LevelOp op, const double* __restrict__ x,
-                                                                   const double* __restrict__ b,
-                                                                   double* __restrict__ y,
-                                                                   double* __restrict__ partials, int ntx, int nty,
-                                                                   int ntiles) {
+// The factored bulk pass with 2 vertices per thread (vec2 rows), used in FP64
+// for the outer residual.  (An FP32 instance with 3 blocks per SM ran no faster
+// than the 4-vertex FP32 pass: both are bound by loads in flight per SM.)
+template <typename T, int MODE, int MINB>
+__global__ void __launch_bounds__(kGeoBX * kGeoBY, MINB) sweep3_geo2(const LevelOp op, const T* __restrict__ x,
+                                                                      const T* __restrict__ b, T* __restrict__ y,
+                                                                      T omega, double* __restrict__ partials,
+                                                                      int ntx, int nty, int ntiles) {
   __shared__ double sh[2][8];
-  Geo64Ctx c;
+  Geo2Ctx<T> c;
   c.x = x;
   c.b = b;
   c.y = y;
@@ -1089,7 +1115,9 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo64(const LevelOp
   c.N = op.N;
   c.n1 = op.N + 1;
   c.plane = (size_t)c.n1 * c.n1;
-  c.h12 = -op.gk64;   // h / 12
+  c.h12 = sizeof(T) == 4 ? (T)-op.gk32 : (T)-op.gk64;   // h / 12
+  c.h3 = (T)4 * c.h12;
+  c.omega = omega;
   double d1 = 0.0, d2 = 0.0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
@@ -1102,19 +1130,19 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo64(const LevelOp
     c.hr = c.q + 2 <= c.N;      // vertex q+2 exists
     c.hr2 = c.q + 1 <= c.N - 1; // cell q+1 exists
     c.row0 = (size_t)c.j * c.n1;
-    Rows4d ua, ub;
-    double pa[2][3], pb[2][3], ga[2][3], gb[2][3], ta[3], tb[3];
-    load_rows4d(x + (size_t)(k0 - 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ub);
-    load_rows4d(x + (size_t)k0 * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ua);
-    load_eps6d(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr2, ga);
-    pair_sums4d(ub, pb);
-    pair_sums4d(ua, pa);
+    Rows4<T> ua, ub;
+    T pa[2][3], pb[2][3], ga[2][3], gb[2][3], ta[3], tb[3];
+    load_rows4<T>(x + (size_t)(k0 - 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ub);
+    load_rows4<T>(x + (size_t)k0 * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ua);
+    load_eps6<T>(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr2, ga);
+    pair_sums4<T>(ub, pb);
+    pair_sums4<T>(ua, pa);
 #pragma unroll
     for (int i = 0; i < 3; ++i) ta[i] = ga[0][i] * (pb[0][i] + pa[0][i]) + ga[1][i] * (pb[1][i] + pa[1][i]);
     for (int k = k0; k <= k1; k += 2) {
-      geo64_step<MODE>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
+      geo2_step<T, MODE>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
       if (k + 1 > k1) break;
-      geo64_step<MODE>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
+      geo2_step<T, MODE>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
     }
   }
   if (MODE == SW_MATVEC) {
@@ -1210,11 +1238,11 @@ cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const dou
   const dim3 blk(kGeoBX, kGeoBY, 1);
   double* pfix = partials ? partials + 2 * (size_t)nb : nullptr;
   if (mode == SW_RESID) {
-    sweep3_geo64<SW_RESID><<<nb, blk, 0, st>>>(op, x, b, y, partials, ntx, nty, ntiles);
+    sweep3_geo2<double, SW_RESID, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup64<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
   } else {
-    sweep3_geo64<SW_MATVEC><<<nb, blk, 0, st>>>(op, x, b, y, partials, ntx, nty, ntiles);
+    sweep3_geo2<double, SW_MATVEC, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty, ntiles);
     count_launches(1);
     sweep3_fixup64<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
   }
@@ -1384,7 +1412,6 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   }
   const int nb_bulk = ntiles < 2 * nsm ? ntiles : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
-
   double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
   if (mode == SW_JACOBI0) {
     sweep3_jacobi0<<<nb_bulk, blk, 0, st>>>(op, b, y, omega, ntx, nty, ntiles);
