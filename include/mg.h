@@ -108,7 +108,7 @@ typedef enum {
 
 typedef struct {
   int32_t dim;             /* 2 or 3 */
-  int32_t n_cells;         /* cells per axis, 3^L with L >= 1 */
+  int32_t n_cells;         /* cells per axis, 3^L with L >= 2 (N >= 9: at least one level above the 3^d coarse solve) */
   mg_eps_desc eps;
   double f_const;          /* right-hand side f (constant) */
   int32_t path;            /* mg_path */

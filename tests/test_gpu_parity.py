@@ -507,3 +507,91 @@ def test_dense_surplus_field_sweeps_match_oracle(monkeypatch, env):
         assert np.abs(P.apply(0, 2, x, b) - (b - y_ref) * m).max() <= tol
         info = P.solve()
         assert info.status == mg.MG_OK
+
+
+# ---------------------------------------------------------------- degenerate and limit cases
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("path", [mg.PATH_FP64_PLAIN, mg.PATH_FP64_DELAYED, mg.PATH_MIXED_DELAYED,
+                                  mg.PATH_MIXED_PLAIN])
+def test_smallest_grids(dim, path):
+    # N = 3 has no coarser level: rejected (L >= 2 is required).  N = 9, the
+    # smallest accepted grid, is one smoothing level over the 3^d coarse solve.
+    fld = inputs.fourier_field(dim, 41, sigma=1.0)
+    s = 4
+    sched = (1, s) if path in (mg.PATH_FP64_DELAYED, mg.PATH_MIXED_DELAYED) else (s,)
+    with pytest.raises(mg.MGError) as ei:
+        mg.Problem(mg.problem_desc(dim, 3, fld, path=path, s_schedule=sched))
+    assert ei.value.status == mg.MG_ERR_INVALID
+    with mg.Problem(mg.problem_desc(dim, 9, fld, path=path, s_schedule=sched, rtol=1e-10)) as P:
+        info = P.solve()
+        u = P.solution()
+    A = _stored_operator(path, fld, 9, s)
+    u_ref = dense.dense_solve(dim, 9, A, oracle.load_vector(dim, 9))
+    assert info.status == mg.MG_OK
+    tol = 1e-8 if path in (mg.PATH_FP64_PLAIN, mg.PATH_FP64_DELAYED) else 1e-4
+    assert np.abs(u - u_ref).max() <= tol * np.abs(u_ref).max()
+
+
+@pytest.mark.parametrize("path", [mg.PATH_MIXED_DELAYED, mg.PATH_FP64_PLAIN])
+def test_zero_right_hand_side_gives_zero(path):
+    fld = inputs.boxes_field(3, 2003)
+    with mg.Problem(mg.problem_desc(3, 27, fld, path=path, s_schedule=(1, 2) if path == mg.PATH_MIXED_DELAYED
+                                    else (2,), f_const=0.0)) as P:
+        info = P.solve()
+        u = P.solution()
+    assert info.status == mg.MG_OK
+    assert np.abs(u).max() == 0.0
+
+
+def test_constant_field_has_no_surplus_and_matches_geometric_solve():
+    # constant eps: A(s) = eps K_ref at every s, so every cell is class 0 and
+    # the mixed solve equals the s = 1 (geometric) FP64 solve
+    fld = inputs.const_field(3, 2.5)
+    with mg.Problem(mg.problem_desc(3, 27, fld, path=mg.PATH_MIXED_DELAYED, s_schedule=(1, 2, 4, 8))) as P:
+        info = P.solve()
+        u = P.solution()
+    assert info.status == mg.MG_OK
+    assert list(info.cells_by_class)[1:] == [0, 0, 0]
+    with mg.Problem(mg.problem_desc(3, 27, fld, path=mg.PATH_FP64_PLAIN, s_schedule=(1,), rtol=1e-12)) as P:
+        P.solve()
+        u64 = P.solution()
+    assert np.abs(u - u64).max() <= 1e-7 * np.abs(u64).max()
+
+
+def test_initial_guess_and_cycle_limit():
+    fld = inputs.disc_field(2)
+    base = mg.problem_desc(2, 81, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,), rtol=1e-9)
+    with mg.Problem(base) as P:
+        P.solve()
+        u_ref = P.solution()
+    u0 = np.ascontiguousarray(inputs.noise_vector(2, 81, 7))
+    with mg.Problem(mg.problem_desc(2, 81, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,), rtol=1e-9,
+                                    u0=u0)) as P:
+        info = P.solve()
+        u = P.solution()
+    assert info.status == mg.MG_OK
+    assert np.abs(u - u_ref).max() <= 1e-6 * np.abs(u_ref).max()
+    with mg.Problem(mg.problem_desc(2, 81, fld, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,), rtol=1e-12,
+                                    max_cycles=2)) as P:
+        info = P.solve(check=False)
+    assert info.status == mg.MG_ERR_NOT_CONVERGED
+    assert info.cycles <= 3
+
+
+def test_largest_2d_grid_residual_checked_on_the_host():
+    # 729^2 cells (the largest 2D serving size), mixed delayed path: the final
+    # residual of the oracle's stored operator, recomputed on the host
+    n = 729
+    fld = inputs.fourier_field(2, 12, sigma=1.5)
+    with mg.Problem(mg.problem_desc(2, n, fld, path=mg.PATH_MIXED_DELAYED, s_schedule=(1, 2, 4, 8),
+                                    rtol=1e-8)) as P:
+        info = P.solve()
+        u = P.solution()
+    assert info.status == mg.MG_OK
+    stored = _stored_operator(mg.PATH_MIXED_PLAIN, fld, n, 8)
+    f = oracle.load_vector(2, n)
+    m = dense.interior_mask(2, n)
+    r = (f - oracle.apply(2, n, stored, u)) * m
+    # the GPU solves its own stored operator (within 1e-5 of the oracle's per cell)
+    assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(f * m)
