@@ -60,6 +60,8 @@ def _load():
         lib.oc_element_matrix.argtypes = [FP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _D]
         lib.oc_assemble.argtypes = [FP, ctypes.c_int, ctypes.c_int, _D]
         lib.oc_assemble_cells.argtypes = [FP, ctypes.c_int, ctypes.c_int, _I64, ctypes.c_int64, _D]
+        lib.oc_assemble_adaptive.argtypes = [FP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                             ctypes.c_double, _D, ctypes.POINTER(ctypes.c_int32)]
         lib.oc_round_format.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         lib.oc_round_format.restype = ctypes.c_double
         lib.oc_round_e4m3.argtypes = [ctypes.c_double]
@@ -157,6 +159,19 @@ def assemble_cells(field: Field, n_cells: int, s: int, cells) -> np.ndarray:
     _load().oc_assemble_cells(ctypes.byref(field.c), n_cells, s,
                               cells.ctypes.data_as(_I64), cells.shape[0], _p(A))
     return A
+
+
+def assemble_adaptive(field: Field, n_cells: int, schedule, C: float):
+    """Adaptive per-cell accuracy (Section "Adaptive stencil integration"):
+    (element matrices of every cell, accuracy s of each stored matrix)."""
+    nv = 1 << field.dim
+    ncell = n_cells ** field.dim
+    A = np.zeros((ncell, nv, nv))
+    sc = np.zeros(ncell, np.int32)
+    sched = np.ascontiguousarray(np.asarray(schedule, np.int32))
+    _load().oc_assemble_adaptive(ctypes.byref(field.c), n_cells, sched.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 len(sched), float(C), _p(A), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return A, sc
 
 
 def kref(dim: int, n_cells: int) -> np.ndarray:

@@ -193,6 +193,39 @@ void oc_assemble_cells(const oc_field* F, int N, int s, const int64_t* cells, in
   }
 }
 
+/* Adaptive per-cell accuracy (Section "Adaptive stencil integration", Eq.
+ * "termination-criterion"): each cell walks the accuracy schedule sched[0],
+ * sched[1], ... and keeps the newest element matrix; it stops at the first
+ * level k >= 1 where the relative change in the element-wise maximum norm,
+ * ||A(sched[k]) - A(sched[k-1])||_max / ||A(sched[k-1])||_max, falls below C.
+ * s_cell receives the accuracy of the stored matrix. */
+void oc_assemble_adaptive(const oc_field* F, int N, const int* sched, int n_s, double C, double* A_all,
+                          int32_t* s_cell) {
+  const int d = F->dim, nv = 1 << d;
+  const int64_t ncell = ipow(N, d);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t c = 0; c < ncell; ++c) {
+    int cc[3] = {0, 0, 0};
+    cell_coords(d, N, c, cc);
+    double* A = A_all + c * nv * nv;
+    double Anew[64];
+    oc_element_matrix(F, N, cc, sched[0], A);
+    int sf = sched[0];
+    for (int k = 1; k < n_s; ++k) {
+      oc_element_matrix(F, N, cc, sched[k], Anew);
+      double num = 0.0, den = 0.0;
+      for (int i = 0; i < nv * nv; ++i) {
+        if (fabs(Anew[i] - A[i]) > num) num = fabs(Anew[i] - A[i]);
+        if (fabs(A[i]) > den) den = fabs(A[i]);
+      }
+      memcpy(A, Anew, sizeof(double) * nv * nv);
+      sf = sched[k];
+      if (num < C * den) break;
+    }
+    s_cell[c] = sf;
+  }
+}
+
 /* ---------------- lossy storage of the hierarchical surplus ---------------- */
 
 /* Round x to the nearest value (ties to even) of a binary floating-point

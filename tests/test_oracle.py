@@ -422,3 +422,56 @@ def test_compression_class_mix():
     A = oracle.assemble(f, 9, 4)
     _, cls, _ = oracle.compress(f, 9, A, 1e-6)
     assert set(np.unique(cls)) >= {1, 2}
+
+
+# ---------------------------------------------------------------- adaptive per-cell accuracy
+
+def test_adaptive_constant_field_stops_at_the_first_comparison():
+    # constant eps: A(s) = eps K_ref at every s, the change is 0 < C
+    f = oracle.Field(inputs.const_field(3, 2.0))
+    A, sc = oracle.assemble_adaptive(f, 9, (1, 2, 4, 8), 1e-2)
+    assert np.all(sc == 2)
+    assert np.allclose(A, oracle.assemble(f, 9, 1), rtol=0, atol=1e-14 * np.abs(A).max())
+
+
+def test_adaptive_rule_matches_a_hand_loop_and_its_limits():
+    fld = inputs.fourier_field(2, 5, sigma=1.0)
+    f = oracle.Field(fld)
+    n, sched, C = 9, (1, 2, 3, 4, 6, 8), 2e-2
+    A, sc = oracle.assemble_adaptive(f, n, sched, C)
+    # hand loop on a few cells, straight from the termination criterion
+    for c in (0, 17, 40, 80):
+        cell = (c % n, c // n)
+        old = oracle.element_matrix(f, n, cell, sched[0])
+        s_fin = sched[0]
+        for s in sched[1:]:
+            new = oracle.element_matrix(f, n, cell, s)
+            change = np.abs(new - old).max() / np.abs(old).max()
+            old, s_fin = new, s
+            if change < C:
+                break
+        assert sc[c] == s_fin
+        assert np.allclose(A[c], old, rtol=0, atol=1e-15 * np.abs(old).max())
+    # a huge C stops everything at the second level; C = 0 runs the whole schedule
+    _, s_hi = oracle.assemble_adaptive(f, n, sched, 1e30)
+    _, s_lo = oracle.assemble_adaptive(f, n, sched, 0.0)
+    assert np.all(s_hi == sched[1]) and np.all(s_lo == sched[-1])
+    # accuracy is monotone in C
+    _, s_mid = oracle.assemble_adaptive(f, n, sched, 1e-3)
+    assert np.all(s_mid >= sc)
+
+
+def test_adaptive_piecewise_constant_cells_away_from_the_interface_stop_early():
+    f = oracle.Field(inputs.disc_field(2))
+    A, sc = oracle.assemble_adaptive(f, 27, (1, 2, 4, 8), 1e-2)
+    cut = sc > 2
+    assert cut.any() and (~cut).any()
+    # the cells that keep refining are the ones the disc boundary crosses
+    h = 1 / 27
+    for c in np.flatnonzero(cut):
+        i, j = c % 27, c // 27
+        xs = np.array([i * h, (i + 1) * h]) - 0.5
+        ys = np.array([j * h, (j + 1) * h]) - 0.5
+        dmax = np.sqrt(np.max(xs ** 2) + np.max(ys ** 2))
+        dmin = np.sqrt((0 if xs[0] * xs[1] <= 0 else np.min(xs ** 2)) + (0 if ys[0] * ys[1] <= 0 else np.min(ys ** 2)))
+        assert dmin <= 0.3 <= dmax
