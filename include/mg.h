@@ -125,6 +125,14 @@ typedef struct {
   int32_t chunks;          /* delayed assembly chunks along the last axis (0 => auto) */
   const double* u0;        /* optional host initial guess, (N+1)^d values; NULL => 0.
                               Read during mg_create_problem only. */
+  double adapt_C;          /* > 0: adaptive per-cell accuracy (Section "Adaptive stencil
+                              integration", Eq. "termination-criterion"): each cell walks
+                              s_schedule and stops refining at the first level whose
+                              element matrix differs from the stored previous one by less
+                              than adapt_C in the relative element-wise maximum norm (the
+                              paper uses 1%); the plain paths then assemble the whole
+                              schedule before solving.  0 => every cell reaches the last
+                              accuracy of the schedule. */
 } mg_problem_desc;
 
 typedef struct {
@@ -191,6 +199,14 @@ mg_status mg_get_cell_matrices(const mg_problem* p, int level, const int64_t* ce
 /* Per-cell storage class (0..3) and cell-centre eps of the finest level; the
  * arrays hold n_cells^d entries; either pointer may be NULL. */
 mg_status mg_get_cell_data(const mg_problem* p, uint8_t* cls, double* eps_c, size_t n);
+
+/* Accuracy s of the stored element matrix of every finest-level cell
+ * (n_cells^d entries, cell index order): with adapt_C > 0 the level at which
+ * the cell became final (or the last one integrated); otherwise the published
+ * accuracy of the cell's chunk.  Call after mg_solve or a synchronous
+ * mg_assemble_level (integrations still in flight are not reflected).
+ * Errors: MG_ERR_INVALID (n). */
+mg_status mg_get_cell_accuracy(const mg_problem* p, int32_t* s_out, size_t n);
 
 /* Test hooks on the stored operator of `level` (0 = finest), vectors on the
  * host, (N_level+1)^d FP64 values each, boundary entries ignored/zero:

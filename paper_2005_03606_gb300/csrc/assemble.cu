@@ -395,6 +395,40 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           }
           dl[pair_index(NV, a, b)] = v * scale;
         }
+      if (A.final_flags) {
+        // adaptive accuracy: relative change against the previously stored
+        // matrix in the element-wise maximum norm (diagonals included)
+        const T ge = eref * (T)A.hfac;
+        const int pcls = A.prec64 ? 0 : cell_class(A.prev_cmp, N, A.nseg_x, lc);
+        const uint8_t* prec = pcls ? cell_record<D>(A.prev_cmp, N, A.nseg_x, lc, pcls) : nullptr;
+        T num = 0, den = 0, rsn[NV], rso[NV];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) rsn[a] = rso[a] = 0;
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+          for (int b = a + 1; b < NV; ++b) {
+            const int p = pair_index(NV, a, b);
+            const T geo = ge * (T)kref_off<D>(popc_small(a ^ b));
+            const T vn = geo + dl[p];
+            T vo;
+            if (A.prec64) vo = (T)A.prev_full[(long long)p * A.ncell + lc];
+            else vo = geo + (pcls ? (T)decode_entry<D>(prec, pcls, p) : (T)0);
+            num = fmax(num, fabs(vn - vo));
+            den = fmax(den, fabs(vo));
+            rsn[a] += vn;
+            rsn[b] += vn;
+            rso[a] += vo;
+            rso[b] += vo;
+          }
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+          num = fmax(num, fabs(rso[a] - rsn[a]));
+          den = fmax(den, fabs(rso[a]));
+        }
+        if (num < (T)A.adapt_C * den) A.final_flags[lc] = 1;
+        A.s_cell[lc] = (uint8_t)s;
+      }
       if (A.prec64) {
         double* out = reinterpret_cast<double*>(A.out_full);
 #pragma unroll
@@ -691,7 +725,91 @@ void face_range(double x, int N, int* lo, int* hi) {
     }
 }
 
+// adaptive accuracy: the final cells' previous matrices into the new store
+template <int D>
+__global__ void carry_final_kernel(long long ncell, int N, int nseg_x, const uint8_t* __restrict__ flags,
+                                   const CmpChunk prev, uint8_t* __restrict__ out_rec, uint8_t* __restrict__ out_cls,
+                                   uint8_t* __restrict__ s_cell, int s, int first) {
+  for (long long lc = blockIdx.x * (long long)blockDim.x + threadIdx.x; lc < ncell;
+       lc += (long long)gridDim.x * blockDim.x) {
+    if (!flags[lc]) continue;
+    if (first) s_cell[lc] = (uint8_t)s;
+    const int cls = cell_class(prev, N, nseg_x, lc);
+    const long long row = lc / N;
+    const int x = (int)(lc - row * N);
+    out_cls[(row * nseg_x + (x >> 5)) * kSegCells + (x & 31)] = (uint8_t)cls;
+    if (cls) {
+      const uint8_t* src = cell_record<D>(prev, N, nseg_x, lc, cls);
+      const int bytes = cls == 1 ? Dim<D>::REC1 : (cls == 2 ? Dim<D>::REC2 : Dim<D>::REC3);
+      uint8_t* dst = out_rec + (size_t)lc * Dim<D>::REC_MAX;
+      for (int i = 0; i < bytes; ++i) dst[i] = src[i];
+    }
+  }
+}
+
+__global__ void carry_final64_kernel(long long ncell, int np, const uint8_t* __restrict__ flags,
+                                     const double* __restrict__ prev, double* __restrict__ out,
+                                     uint8_t* __restrict__ s_cell, int s, int first) {
+  for (long long lc = blockIdx.x * (long long)blockDim.x + threadIdx.x; lc < ncell;
+       lc += (long long)gridDim.x * blockDim.x) {
+    if (!flags[lc]) continue;
+    if (first) s_cell[lc] = (uint8_t)s;
+    for (int p = 0; p < np; ++p) out[(long long)p * ncell + lc] = prev[(long long)p * ncell + lc];
+  }
+}
+
+// work list: the candidate cells (cand, or 0 .. ncand-1) that are not final
+__global__ void adaptive_work_kernel(long long ncand, const int* __restrict__ cand, const uint8_t* __restrict__ flags,
+                                     int* __restrict__ work, int* __restrict__ nwork) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncand;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int lc = cand ? cand[t] : (int)t;
+    if (!flags[lc]) work[atomicAdd(nwork, 1)] = lc;
+  }
+}
+
+__global__ void clear_listed_kernel(long long n, const int* __restrict__ list, uint8_t* __restrict__ flags) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    flags[list[t]] = 0;
+}
+
 }  // namespace
+
+cudaError_t launch_adaptive_prepare(int dim, int N, int nseg_x, long long chunk_cells, int prec64,
+                                    const uint8_t* final_flags, const CmpChunk& prev_cmp, const double* prev_full,
+                                    uint8_t* out_rec, uint8_t* out_cls, double* out_full, const int* cand,
+                                    long long ncand, int* work, int* nwork, uint8_t* s_cell, int s, int first,
+                                    cudaStream_t st) {
+  const int g = grid_for(chunk_cells, 256);
+  if (prec64) {
+    carry_final64_kernel<<<g, 256, 0, st>>>(chunk_cells, dim == 3 ? 28 : 6, final_flags, prev_full, out_full, s_cell,
+                                            s, first);
+  } else if (dim == 3) {
+    carry_final_kernel<3><<<g, 256, 0, st>>>(chunk_cells, N, nseg_x, final_flags, prev_cmp, out_rec, out_cls, s_cell,
+                                             s, first);
+  } else {
+    carry_final_kernel<2><<<g, 256, 0, st>>>(chunk_cells, N, nseg_x, final_flags, prev_cmp, out_rec, out_cls, s_cell,
+                                             s, first);
+  }
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(nwork, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (ncand > 0) adaptive_work_kernel<<<grid_for(ncand, 256), 256, 0, st>>>(ncand, cand, final_flags, work, nwork);
+  return launched();
+}
+
+cudaError_t launch_adaptive_init(long long chunk_cells, int nchunk, const int* lists, const int* counts_host,
+                                 uint8_t* final_flags, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(final_flags, 1, (size_t)chunk_cells * nchunk, st);
+  for (int c = 0; c < nchunk && e == cudaSuccess; ++c) {
+    if (counts_host[c] <= 0) continue;
+    clear_listed_kernel<<<grid_for(counts_host[c], 256), 256, 0, st>>>(counts_host[c], lists + (size_t)c * chunk_cells,
+                                                                     final_flags + (size_t)c * chunk_cells);
+    e = launched();
+  }
+  return e;
+}
 
 cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long chunk_cells, int* lists,
                                    int* counts, cudaStream_t st) {

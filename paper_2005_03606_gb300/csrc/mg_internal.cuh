@@ -230,7 +230,30 @@ struct AsmLaunch {
   // them); the others are left alone (nullptr: every cell of the chunk)
   const int* list;
   long long nlist;
+  // adaptive accuracy (Section "Adaptive stencil integration"): the chunk's
+  // previously stored matrices, its per-cell final flags (set here when the
+  // relative max-norm change falls below adapt_C) and the accuracy of each
+  // stored matrix; final_flags == nullptr: not adaptive
+  CmpChunk prev_cmp;
+  const double* prev_full;
+  uint8_t* final_flags;
+  uint8_t* s_cell;
+  double adapt_C;
 };
+// adaptive accuracy, before the integration of one chunk at a new level: the
+// cells already final keep their previous matrix (copied into the new store:
+// records + class bytes, or the FP64 entries), and the work list receives the
+// candidate cells (the interface list, or every cell) that are not final.
+// first = 1 on the first judged level: the cells final before any judgement
+// (constant eps over the cell) take accuracy s there.
+cudaError_t launch_adaptive_prepare(int dim, int N, int nseg_x, long long chunk_cells, int prec64,
+                                    const uint8_t* final_flags, const CmpChunk& prev_cmp, const double* prev_full,
+                                    uint8_t* out_rec, uint8_t* out_cls, double* out_full, const int* cand,
+                                    long long ncand, int* work, int* nwork, uint8_t* s_cell, int s, int first,
+                                    cudaStream_t st);
+// marks every cell final except the listed candidate cells of each chunk
+cudaError_t launch_adaptive_init(long long chunk_cells, int nchunk, const int* lists, const int* counts_host,
+                                 uint8_t* final_flags, cudaStream_t st);
 cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, void* eps_c, cudaStream_t st);
 // stream-ordered allocation from the library's memory pool on the current
 // device: freed blocks stay in the pool for the next problems (no release

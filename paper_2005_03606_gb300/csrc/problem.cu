@@ -131,6 +131,13 @@ struct mg_problem {
   // are integrated at s > 1, every other cell keeps its geometric stencil
   int* ilist = nullptr;           // [nchunk][chunk_cells] local cell indices
   std::vector<int> ilist_n;       // count per chunk (host)
+  // adaptive accuracy (desc.adapt_C > 0)
+  bool adapt = false;
+  uint8_t* final_flags = nullptr; // [nchunk][chunk_cells]: 1 once the cell stopped refining
+  uint8_t* s_cell = nullptr;      // [nchunk][chunk_cells]: accuracy of the cell's latest matrix
+  int* awork = nullptr;           // work list of one chunk
+  int* anwork = nullptr;          // its length (device)
+  std::vector<ChunkStore> wlast;  // latest store integrated per chunk (published or not)
   uint32_t* d_totals = nullptr;   // per stream: [0..2] main, [4..6] side
   uint32_t* h_totals = nullptr;   // pinned, same layout
   // mixed 3D finest level: vertices touched by cells with a surplus record
@@ -280,6 +287,10 @@ mg_status validate(const mg_problem_desc* d) {
     set_error("2D n_cells above 19683 not supported");
     return MG_ERR_INVALID;
   }
+  if (!(d->adapt_C >= 0.0) || !std::isfinite(d->adapt_C)) {
+    set_error("adapt_C must be a finite value >= 0");
+    return MG_ERR_INVALID;
+  }
   const mg_eps_desc& e = d->eps;
   if (e.kind < 0 || e.kind > 4) {
     set_error("unknown eps kind %d", e.kind);
@@ -328,6 +339,15 @@ mg_status validate(const mg_problem_desc* d) {
 LevelOp& fine_op(mg_problem* P) { return P->lev[0].op; }
 
 // ------------------------------------------------------------ assembly of one chunk
+// Adaptive accuracy (Section "Adaptive stencil integration"): a level s of a
+// chunk is judged against the chunk's previous level once that one is at
+// least the first level of the schedule; the first judged level is the one
+// right after it.
+bool adaptive_judged(const mg_problem* P, int s, int chunk) {
+  return P->adapt && s > 1 && P->wlast[chunk].s >= P->desc.s_schedule[0];
+}
+int adaptive_first(const mg_problem* P, int chunk) { return P->wlast[chunk].s == P->desc.s_schedule[0]; }
+
 mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, ChunkStore* out, int tot_slot) {
   const int D = P->dim;
   const int NP = D == 3 ? 28 : 6;
@@ -342,7 +362,23 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
       MG_CHECK(launch_geometric_full(D, P->N, fine_op(P).hfac, (const double*)P->eps_c, cell0, P->chunk_cells,
                                      (double*)cs.a64, st));
     }
-    if (s > 1 && (!P->ilist || P->ilist_n[chunk] > 0)) {
+    const bool judge = adaptive_judged(P, s, chunk);
+    long long nwork = -1;   // adaptive: cells still refining in this chunk
+    if (judge) {
+      const size_t off = (size_t)chunk * P->chunk_cells;
+      MG_CHECK(launch_adaptive_prepare(D, P->N, P->nseg_x, P->chunk_cells, 1, P->final_flags + off, CmpChunk{},
+                                       (const double*)P->wlast[chunk].a64, nullptr, nullptr, (double*)cs.a64,
+                                       P->ilist ? P->ilist + off : nullptr,
+                                       P->ilist ? P->ilist_n[chunk] : P->chunk_cells, P->awork, P->anwork,
+                                       P->s_cell + off, s, adaptive_first(P, chunk), st));
+      int h = 0;
+      MG_CHECK(cudaMemcpyAsync(&h, P->anwork, sizeof(int), cudaMemcpyDeviceToHost, st));
+      MG_CHECK(cudaStreamSynchronize(st));
+      nwork = h;
+    } else if (P->adapt && s > 1) {
+      MG_CHECK(cudaMemsetAsync(P->s_cell + (size_t)chunk * P->chunk_cells, s, P->chunk_cells, st));
+    }
+    if (s > 1 && (judge ? nwork > 0 : (!P->ilist || P->ilist_n[chunk] > 0))) {
       AsmLaunch a{};
       a.dim = D;
       a.N = P->N;
@@ -357,12 +393,21 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
       a.out_full = cs.a64;
       a.nseg_x = P->nseg_x;
       a.tau = 0;
-      if (P->ilist) {
+      if (judge) {
+        const size_t off = (size_t)chunk * P->chunk_cells;
+        a.list = P->awork;
+        a.nlist = nwork;
+        a.prev_full = (const double*)P->wlast[chunk].a64;
+        a.final_flags = P->final_flags + off;
+        a.s_cell = P->s_cell + off;
+        a.adapt_C = P->desc.adapt_C;
+      } else if (P->ilist) {
         a.list = P->ilist + (size_t)chunk * P->chunk_cells;
         a.nlist = P->ilist_n[chunk];
       }
       MG_CHECK(launch_assemble(a, st));
     }
+    if (P->adapt) P->wlast[chunk] = cs;
     *out = cs;
     return MG_OK;
   }
@@ -392,11 +437,35 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
   a.out_cls = cs.cls;
   a.nseg_x = P->nseg_x;
   a.tau = P->desc.compress_tau;
-  if (P->ilist) {   // only the interface cells can carry a surplus (the class bytes start at 0)
+  const bool judge = adaptive_judged(P, s, chunk);
+  if (P->adapt && !judge) MG_CHECK(cudaMemsetAsync(P->s_cell + (size_t)chunk * P->chunk_cells, s, P->chunk_cells, st));
+  if (judge) {
+    // final cells keep their previous record; the others not final are integrated
+    const ChunkStore& pv = P->wlast[chunk];
+    CmpChunk prev{};
+    prev.cls = pv.cls;
+    prev.seg_base = pv.seg_base;
+    for (int k = 0; k < 3; ++k) prev.pool[k] = pv.pool[k];
+    prev.nseg = P->chunk_nseg;
+    const size_t off = (size_t)chunk * P->chunk_cells;
+    MG_CHECK(launch_adaptive_prepare(D, P->N, P->nseg_x, P->chunk_cells, 0, P->final_flags + off, prev, nullptr,
+                                     P->scratch, cs.cls, nullptr, P->ilist ? P->ilist + off : nullptr,
+                                     P->ilist ? P->ilist_n[chunk] : P->chunk_cells, P->awork, P->anwork,
+                                     P->s_cell + off, s, adaptive_first(P, chunk), st));
+    int h = 0;
+    MG_CHECK(cudaMemcpyAsync(&h, P->anwork, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MG_CHECK(cudaStreamSynchronize(st));
+    a.list = P->awork;
+    a.nlist = h;
+    a.prev_cmp = prev;
+    a.final_flags = P->final_flags + off;
+    a.s_cell = P->s_cell + off;
+    a.adapt_C = P->desc.adapt_C;
+  } else if (P->ilist) {   // only the interface cells can carry a surplus (the class bytes start at 0)
     a.list = P->ilist + (size_t)chunk * P->chunk_cells;
     a.nlist = P->ilist_n[chunk];
   }
-  if (!P->ilist || a.nlist > 0) MG_CHECK(launch_assemble(a, st));
+  if ((!P->ilist && !judge) || a.nlist > 0) MG_CHECK(launch_assemble(a, st));
   uint32_t* dt = P->d_totals + tot_slot;
   uint32_t* ht = P->h_totals + tot_slot;
   MG_CHECK(launch_pack_count(D, P->N, P->chunk_rows, P->nseg_x, cs.cls, cs.seg_base, dt, st));
@@ -413,6 +482,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
   }
   MG_CHECK(launch_pack_copy(D, P->N, P->chunk_rows, P->nseg_x, cs.cls, cs.seg_base, P->scratch, cs.pool[0],
                             cs.pool[1], cs.pool[2], st));
+  if (P->adapt) P->wlast[chunk] = cs;
   *out = cs;
   return MG_OK;
 }
@@ -1090,12 +1160,28 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
       return fail(MG_ERR_CUDA);
     cudaFreeAsync(counts, P->st);
   }
+  if (d.adapt_C > 0.0 && d.n_s >= 2) {
+    P->adapt = true;
+    P->wlast.resize(P->nchunk);
+    const size_t nc = (size_t)P->chunk_cells * P->nchunk;
+    if ((e = dalloc(P, &P->final_flags, nc)) != cudaSuccess || (e = dalloc(P, &P->s_cell, nc)) != cudaSuccess ||
+        (e = dalloc(P, &P->awork, sizeof(int) * (size_t)P->chunk_cells)) != cudaSuccess ||
+        (e = dalloc(P, &P->anwork, sizeof(int))) != cudaSuccess)
+      return fail(oom_or_cuda(e, "adaptive accuracy"));
+    // cells with eps constant over them have the exact matrix at every s:
+    // they are final from the start (all other cells are judged)
+    e = P->ilist ? launch_adaptive_init(P->chunk_cells, P->nchunk, P->ilist, P->ilist_n.data(), P->final_flags, P->st)
+                 : cudaMemsetAsync(P->final_flags, 0, nc, P->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->s_cell, 1, nc, P->st);   // the centre sample
+    if (!cuda_ok(e, "adaptive init")) return fail(MG_ERR_CUDA);
+  }
   for (int c = 0; c < P->nchunk; ++c) {
     ChunkStore cs;
     mg_status s = assemble_chunk(P, 1, c, P->st, &cs, 0);
     if (s != MG_OK) return fail(s);
     install(P, c, cs);
   }
+  if (P->adapt) P->wlast = P->cur;
   mg_status s = upload_tables(P);
   if (s == MG_OK) s = rebuild_coarse(P);
   if (s != MG_OK) return fail(s);
@@ -1215,7 +1301,13 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   P->publishes = 0;
   if (!P->delayed) {
     auto ta = std::chrono::steady_clock::now();
-    if (min_s(P) < final_s(P)) {
+    if (P->adapt) {   // the adaptive rule needs every level of the schedule, in order
+      for (int i = 0; i < d.n_s; ++i)
+        if (d.s_schedule[i] > min_s(P)) {
+          mg_status s = mg_assemble_level(P, d.s_schedule[i], 0);
+          if (s != MG_OK) return s;
+        }
+    } else if (min_s(P) < final_s(P)) {
       mg_status s = mg_assemble_level(P, final_s(P), 0);
       if (s != MG_OK) return s;
     }
@@ -1409,6 +1501,25 @@ mg_status mg_get_cell_matrices(const mg_problem* Pc, int level, const int64_t* c
   cudaFreeAsync(dc, P->st);
   cudaFreeAsync(tmp, P->st);
   MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
+mg_status mg_get_cell_accuracy(const mg_problem* Pc, int32_t* s_out, size_t n) {
+  mg_problem* P = const_cast<mg_problem*>(Pc);
+  if (!P || !s_out || n != (size_t)P->lev[0].ncell) {
+    set_error("bad arguments (n must be cells)");
+    return MG_ERR_INVALID;
+  }
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  if (P->side) MG_CHECK(cudaStreamSynchronize(P->side));
+  if (P->adapt) {
+    std::vector<uint8_t> t(n);
+    MG_CHECK(cudaMemcpy(t.data(), P->s_cell, n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) s_out[i] = t[i];
+  } else {
+    for (int c = 0; c < P->nchunk; ++c)
+      for (long long i = 0; i < P->chunk_cells; ++i) s_out[(size_t)c * P->chunk_cells + i] = P->cur[c].s;
+  }
   return MG_OK;
 }
 

@@ -42,7 +42,7 @@ class mg_problem_desc(ctypes.Structure):
                 ("s_schedule", ctypes.c_int32 * 8), ("n_s", ctypes.c_int32), ("compress_tau", ctypes.c_double),
                 ("omega", ctypes.c_double), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("chunks", ctypes.c_int32),
-                ("u0", ctypes.POINTER(ctypes.c_double))]
+                ("u0", ctypes.POINTER(ctypes.c_double)), ("adapt_C", ctypes.c_double)]
 
 
 class mg_solve_info(ctypes.Structure):
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_get_solution": (st, [_VP, _D, ctypes.c_size_t]),
             "mg_get_element_matrices": (st, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
             "mg_get_cell_data": (st, [_VP, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t]),
+            "mg_get_cell_accuracy": (st, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_size_t]),
             "mg_get_cell_matrices": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t, _D]),
             "mg_apply_level": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
             "mg_vcycle_apply": (st, [_VP, _D, _D]),
@@ -150,7 +151,7 @@ def eps_desc(field: "_inputs.EpsField") -> mg_eps_desc:
 def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_schedule=(8,),
                  f_const: float = 1.0, outer: int = OUTER_FCG, tau: float = 1e-6, omega: float = 0.6,
                  nu_pre: int = 2, nu_post: int = 2, rtol: float = 1e-8, max_cycles: int = 500,
-                 chunks: int = 0, u0: Optional[np.ndarray] = None) -> mg_problem_desc:
+                 chunks: int = 0, u0: Optional[np.ndarray] = None, adapt_C: float = 0.0) -> mg_problem_desc:
     d = mg_problem_desc()
     d.dim, d.n_cells = dim, n_cells
     d.eps = eps_desc(field)
@@ -162,6 +163,7 @@ def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_s
     d.compress_tau, d.omega = tau, omega
     d.nu_pre, d.nu_post = nu_pre, nu_post
     d.rtol, d.max_cycles, d.chunks = rtol, max_cycles, chunks
+    d.adapt_C = adapt_C
     if u0 is not None:
         u0 = np.ascontiguousarray(u0, np.float64)
         d.u0 = u0.ctypes.data_as(_D)
@@ -251,6 +253,12 @@ class Problem:
         ec = np.zeros(n)
         _check(load().mg_get_cell_data(self.h, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _p(ec), n))
         return cls, ec
+
+    def cell_accuracy(self) -> np.ndarray:
+        n = self.level_cells(0)
+        sc = np.zeros(n, np.int32)
+        _check(load().mg_get_cell_accuracy(self.h, sc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n))
+        return sc
 
     def apply(self, level: int, op: int, x: np.ndarray, b: Optional[np.ndarray] = None, inner: bool = False):
         x = np.ascontiguousarray(x, np.float64)
