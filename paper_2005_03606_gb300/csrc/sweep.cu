@@ -683,11 +683,49 @@ __global__ void __launch_bounds__(kTX * kTY, 3) sweep3_stream(const LevelOp op, 
 // march, so a vertex costs about a third of the per-cell form's arithmetic.
 //
 // Layout: a thread owns 4 consecutive vertices in x (rows of (N+1) floats with
-// (N+1) % 4 == 0 keep float4 loads aligned) of row j and walks kGZ planes in
-// z, loading the next plane's three u rows, eps rows and b one plane ahead.
-// Blocks loop over (x, y, z-run) tiles (persistent grid, no wave tail).
-constexpr int kGZ = 16;
+// (N+1) % 4 == 0 keep float4 loads aligned) of row j and marches in z,
+// loading the next plane's three u rows, eps rows and b one plane ahead and
+// prefetching the rows kGeoPF planes further into L2.  Blocks (persistent
+// grid, no wave tail) take equal shares of the z runs of all columns.
 constexpr int kGeoBX = 32, kGeoBY = 8;
+#ifndef MG_GEO_PF
+#define MG_GEO_PF 1
+#endif
+constexpr int kGeoPF = MG_GEO_PF;   // planes of L2 prefetch ahead of the z march
+
+// Balanced static partition of a bulk pass: the (x-tile, y-tile) columns of
+// interior planes 1 .. N-1 are laid end to end (plane fastest) and block b
+// takes the b-th of gridDim.x equal contiguous shares -- one z run, or the
+// end of one column and the start of the next.  Every block then does the
+// same number of plane steps (a tile grid of fixed z runs left whole runs
+// for a fraction of the blocks: up to 1.3x the average at 243^3).
+struct GeoRun {
+  int tx, ty, k0, k1;
+};
+
+__device__ __forceinline__ bool next_geo_run(long long& w, long long w1, int nk, int ntx, GeoRun& r) {
+  if (w >= w1) return false;
+  const long long col = w / nk;
+  const long long wend = min(w1, (col + 1) * (long long)nk);
+  r.tx = (int)(col % ntx);
+  r.ty = (int)(col / ntx);
+  r.k0 = 1 + (int)(w - col * nk);
+  r.k1 = r.k0 + (int)(wend - w) - 1;
+  w = wend;
+  return true;
+}
+
+__device__ __forceinline__ void geo_share(int ntx, int nty, int N, long long& w0, long long& w1) {
+  const long long total = (long long)ntx * nty * (N - 1);
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  w0 = min(total, (long long)blockIdx.x * per);
+  w1 = min(total, w0 + per);
+}
+
+// L2 prefetch of one address (no register, no scoreboard wait)
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 struct Rows6 {   // x[q-1], x[q..q+3], x[q+4] of three rows j-1, j, j+1
   float v[3][6];
@@ -745,10 +783,28 @@ struct GeoCtx {
   float* y;
   const float* eps;
   int N, n1, q, j;
+  int k1;                 // last plane of the current z run
   size_t plane, row0;
   bool hl, hr;
+  bool first_row, last_row;   // edge rows of the block also prefetch the halo rows
   float h12, h3, omega;
 };
+
+// the lines plane k + 1 + kGeoPF (u) and k + kGeoPF (b, eps) of a thread's rows
+__device__ __forceinline__ void geo_prefetch(const GeoCtx& c, int k) {
+  if (kGeoPF == 0 || k + kGeoPF > c.k1) return;
+  const int kp = k + kGeoPF;
+  const float* u = c.x + (size_t)(kp + 1) * c.plane + c.row0 + c.q;
+  prefetch_l2(u);
+  prefetch_l2(c.b + (size_t)kp * c.plane + c.row0 + c.q);
+  const float* e = c.eps + ((size_t)kp * c.N + c.j) * (c.N + 1) + c.q;   // eps row j of layer kp
+  prefetch_l2(e);
+  if (c.first_row) {
+    prefetch_l2(u - c.n1);
+    prefetch_l2(e - (c.N + 1));
+  }
+  if (c.last_row) prefetch_l2(u + c.n1);
+}
 
 // One plane k of the bulk pass.  In: u rows of plane k (uc), their pair sums
 // (pyc), eps of cell layer k-1 (gm) and its eps-weighted cell sums (yTm).
@@ -761,6 +817,7 @@ __device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc
                                          float& d2) {
   load_rows6(c.x, (size_t)(k + 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, un);
   load_eps10(c.eps, c.N, k, c.j, c.q, c.hl, c.hr, gc);   // c.eps: padded rows
+  geo_prefetch(c, k);
   const float4 b4 = __ldg(reinterpret_cast<const float4*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
   // plane k-1, row j (read two planes ago: an L1/L2 hit)
   const float4 m4 = __ldg(reinterpret_cast<const float4*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
@@ -816,8 +873,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
                                                                   const float* __restrict__ b,
                                                                   float* __restrict__ y, float omega,
-                                                                  double* __restrict__ partials, int ntx, int nty,
-                                                                  int ntiles) {
+                                                                  double* __restrict__ partials, int ntx, int nty) {
   __shared__ double sh[2][8];
   GeoCtx c;
   c.x = x;
@@ -833,15 +889,19 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
   // per-thread partial dot products in FP32 (a few hundred terms; they only
   // set the Krylov step lengths), summed over the block in FP64
   float d1 = 0.f, d2 = 0.f;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    c.q = 4 * (tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
-    c.j = 1 + ty * kGeoBY + threadIdx.y;
-    const int k0 = 1 + tz * kGZ;
-    const int k1 = min(c.N - 1, k0 + kGZ - 1);
-    if (c.q >= c.n1 || c.j >= c.N || k0 > k1) continue;
+  long long w, w1;
+  geo_share(ntx, nty, c.N, w, w1);
+  GeoRun run;
+  while (next_geo_run(w, w1, c.N - 1, ntx, run)) {
+    c.q = 4 * (run.tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
+    c.j = 1 + run.ty * kGeoBY + threadIdx.y;
+    const int k0 = run.k0, k1 = run.k1;
+    if (c.q >= c.n1 || c.j >= c.N) continue;
+    c.k1 = k1;
     c.hl = c.q > 0;
     c.hr = c.q + 4 <= c.N;
+    c.first_row = threadIdx.y == 0;
+    c.last_row = threadIdx.y == kGeoBY - 1 || c.j == c.N - 1;
     c.row0 = (size_t)c.j * c.n1;
     // prologue: rows and pair sums of plane k0, eps and weighted cell sums of layer k0-1
     Rows6 ua, ub;
@@ -1105,7 +1165,7 @@ template <typename T, int MODE, int MINB>
 __global__ void __launch_bounds__(kGeoBX * kGeoBY, MINB) sweep3_geo2(const LevelOp op, const T* __restrict__ x,
                                                                       const T* __restrict__ b, T* __restrict__ y,
                                                                       T omega, double* __restrict__ partials,
-                                                                      int ntx, int nty, int ntiles) {
+                                                                      int ntx, int nty) {
   __shared__ double sh[2][8];
   Geo2Ctx<T> c;
   c.x = x;
@@ -1119,13 +1179,14 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, MINB) sweep3_geo2(const Level
   c.h3 = (T)4 * c.h12;
   c.omega = omega;
   double d1 = 0.0, d2 = 0.0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    c.q = 2 * (tx * kGeoBX + threadIdx.x);   // vertices q, q+1
-    c.j = 1 + ty * kGeoBY + threadIdx.y;
-    const int k0 = 1 + tz * kGZ;
-    const int k1 = min(c.N - 1, k0 + kGZ - 1);
-    if (c.q >= c.n1 || c.j >= c.N || k0 > k1) continue;
+  long long w, w1;
+  geo_share(ntx, nty, c.N, w, w1);
+  GeoRun run;
+  while (next_geo_run(w, w1, c.N - 1, ntx, run)) {
+    c.q = 2 * (run.tx * kGeoBX + threadIdx.x);   // vertices q, q+1
+    c.j = 1 + run.ty * kGeoBY + threadIdx.y;
+    const int k0 = run.k0, k1 = run.k1;
+    if (c.q >= c.n1 || c.j >= c.N) continue;
     c.hl = c.q > 0;
     c.hr = c.q + 2 <= c.N;      // vertex q+2 exists
     c.hr2 = c.q + 1 <= c.N - 1; // cell q+1 exists
@@ -1225,8 +1286,7 @@ cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const dou
                          double* partials, int* nblocks, cudaStream_t st) {
   const int np = (op.N + 1) / 2;
   const int ntx = (np + kGeoBX - 1) / kGeoBX, nty = (op.N - 1 + kGeoBY - 1) / kGeoBY;
-  const int ntz = (op.N - 1 + kGZ - 1) / kGZ;
-  const int ntiles = ntx * nty * ntz;
+  const long long ntiles = (long long)ntx * nty * (op.N - 1);
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -1234,15 +1294,15 @@ cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const dou
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 152;
   }
-  const int nb = ntiles < 2 * nsm ? ntiles : 2 * nsm;
+  const int nb = ntiles < 2 * nsm ? (int)ntiles : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
   double* pfix = partials ? partials + 2 * (size_t)nb : nullptr;
   if (mode == SW_RESID) {
-    sweep3_geo2<double, SW_RESID, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty, ntiles);
+    sweep3_geo2<double, SW_RESID, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup64<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
   } else {
-    sweep3_geo2<double, SW_MATVEC, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty, ntiles);
+    sweep3_geo2<double, SW_MATVEC, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup64<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
   }
@@ -1357,17 +1417,18 @@ __global__ void touched_write_kernel(long long nv, const uint8_t* __restrict__ f
 // handles the vertices next to surplus cells).
 __global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp op, const float* __restrict__ b,
                                                                   float* __restrict__ y, float omega, int ntx,
-                                                                  int nty, int ntiles) {
+                                                                  int nty) {
   const int N = op.N, n1 = N + 1;
   const size_t plane = (size_t)n1 * n1;
   const float c0 = omega / (4.f * -op.gk32);   // omega / (h / 3)
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    const int q = 4 * (tx * kGeoBX + threadIdx.x);
-    const int j = 1 + ty * kGeoBY + threadIdx.y;
-    const int k0 = 1 + tz * kGZ;
-    const int k1 = min(N - 1, k0 + kGZ - 1);
-    if (q >= n1 || j >= N || k0 > k1) continue;
+  long long w, w1;
+  geo_share(ntx, nty, N, w, w1);
+  GeoRun run;
+  while (next_geo_run(w, w1, N - 1, ntx, run)) {
+    const int q = 4 * (run.tx * kGeoBX + threadIdx.x);
+    const int j = 1 + run.ty * kGeoBY + threadIdx.y;
+    const int k0 = run.k0, k1 = run.k1;
+    if (q >= n1 || j >= N) continue;
     const bool hl = q > 0;
     unsigned vmask = 0;
 #pragma unroll
@@ -1380,6 +1441,12 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp 
     for (int k = k0; k <= k1; ++k) {
       load_eps10(op.eps_pad, N, k, j, q, hl, true, g);
       const float4 b4 = __ldg(reinterpret_cast<const float4*>(b + (size_t)k * plane + (size_t)j * n1 + q));
+      if (kGeoPF > 0 && k + kGeoPF <= k1) {
+        const float* e = op.eps_pad + ((size_t)(k + kGeoPF) * N + j) * n1 + q;
+        prefetch_l2(b + (size_t)(k + kGeoPF) * plane + (size_t)j * n1 + q);
+        prefetch_l2(e);
+        if (threadIdx.y == 0) prefetch_l2(e - n1);
+      }
       float ey[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -1400,8 +1467,7 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
                         double* partials, int* nblocks, cudaStream_t st) {
   const int nq = (op.N + 1) / 4;
   const int ntx = (nq + kGeoBX - 1) / kGeoBX, nty = (op.N - 1 + kGeoBY - 1) / kGeoBY;
-  const int ntz = (op.N - 1 + kGZ - 1) / kGZ;
-  const int ntiles = ntx * nty * ntz;
+  const long long ntiles = (long long)ntx * nty * (op.N - 1);   // plane steps of 32 x 8 threads
   // persistent grid: the resident blocks of all SMs (two per SM by the launch bounds)
   static int nsm = 0;
   if (!nsm) {
@@ -1410,23 +1476,23 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 152;
   }
-  const int nb_bulk = ntiles < 2 * nsm ? ntiles : 2 * nsm;
+  const int nb_bulk = ntiles < 2 * nsm ? (int)ntiles : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
   double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
   if (mode == SW_JACOBI0) {
-    sweep3_jacobi0<<<nb_bulk, blk, 0, st>>>(op, b, y, omega, ntx, nty, ntiles);
+    sweep3_jacobi0<<<nb_bulk, blk, 0, st>>>(op, b, y, omega, ntx, nty);
     count_launches(1);
     sweep3_fixup<SW_JACOBI0><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else if (mode == SW_JACOBI) {
-    sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
+    sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup<SW_JACOBI><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else if (mode == SW_RESID) {
-    sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
+    sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   } else {
-    sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, ntiles);
+    sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
   }
