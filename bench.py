@@ -426,6 +426,51 @@ def run_probe(args, local_rank):
         print(json.dumps({"probe": "solve", "workload": args.workload, "n_cells": w.n_cells, "ms": ms,
                           "cycles": int(info.cycles), "publishes": int(info.publishes)}), flush=True)
         return
+    if args.probe == "adaptive":   # adaptive per-cell accuracy (C = 1%) against the whole schedule
+        w = inputs.workload(args.workload, args.n)
+        rows = []
+        for path, name in ((mg.PATH_MIXED_DELAYED, "mixed delayed"), (mg.PATH_MIXED_PLAIN, "mixed plain")):
+            for C in (0.0, 0.01):
+                sched = tuple(w.s_schedule) if (C > 0 or path == mg.PATH_MIXED_DELAYED) else (w.s_final,)
+                d = mg.problem_desc(w.dim, w.n_cells, w.eps, path=path, s_schedule=sched, rtol=1e-8,
+                                    max_cycles=3000, adapt_C=C)
+                ms = []
+                for _ in range(args.probe_reps):
+                    with mg.Problem(d) as P:
+                        t0 = time.perf_counter()
+                        info = P.solve()
+                        ms.append((time.perf_counter() - t0) * 1e3)
+                        acc = P.cell_accuracy()
+                # samples integrated per cell: every schedule level up to the cell's own
+                walked = [sum(t ** w.dim for t in sched if 1 < t <= a) for a in (int(v) for v in np.unique(acc))]
+                cnt = {int(v): int((acc == v).sum()) for v in np.unique(acc)}
+                samples = sum(wk * cnt[a] for wk, a in zip(walked, sorted(cnt))) / acc.size
+                rows.append({"path": name, "adapt_C": C, "ms": ms, "cycles": int(info.cycles),
+                             "rel_residual": float(info.rel_residual), "cells_by_s": cnt,
+                             "samples_per_cell": samples})
+        print(json.dumps({"probe": "adaptive", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
+              flush=True)
+        return
+    if args.probe == "starvation":   # per-iteration residual and pending assembly jobs
+        # 2D 243^2 (59,049 unknowns), eps in {1e-5, 1}: disc of radius 0.3
+        fld = inputs.disc_field(2, v_in=1e-5, v_out=1.0)
+        n = args.n or 243
+        out = {}
+        for path, name in ((mg.PATH_FP64_PLAIN, "fp64 precomputed"), (mg.PATH_FP64_DELAYED, "fp64 delayed"),
+                           (mg.PATH_MIXED_DELAYED, "mixed delayed")):
+            sched = (8,) if path == mg.PATH_FP64_PLAIN else (1, 2, 4, 8)
+            d = mg.problem_desc(2, n, fld, path=path, s_schedule=sched, rtol=1e-10, max_cycles=3000)
+            with mg.Problem(d) as P:
+                info = P.solve()
+                tr = P.trace()
+            out[name] = {"cycles": int(info.cycles), "publishes": int(info.publishes),
+                         "rel_residual": float(info.rel_residual),
+                         "trace": [[t["cycle"], round(t["rel_residual_est"], 14), t["pending_jobs"],
+                                    round(t["time_ms"], 3)] for t in tr]}
+        print(json.dumps({"probe": "starvation", "n_cells": n, "eps": "disc r=0.3, 1e-5 inside, 1 outside",
+                          "trace_fields": ["cycle", "rel_residual_est", "pending_jobs", "ms"], "paths": out}),
+              flush=True)
+        return
     which = {"sweep": 0, "matvec": 1, "residual": 2, "galerkin": 3}[args.probe]
     path = mg.PATH_FP64_PLAIN if args.probe_fp64 else mg.PATH_MIXED_PLAIN
     w, d = workload_desc(mg, args.workload, path, n_cells=args.n)
@@ -456,7 +501,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving"],
+    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving", "adaptive",
+                                        "starvation"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)

@@ -196,6 +196,26 @@ mg_status mg_get_element_matrices(const mg_problem* p, int level, double* host_d
 mg_status mg_get_cell_matrices(const mg_problem* p, int level, const int64_t* cells, size_t ncells,
                                double* host_dst);
 
+/* One record per outer iteration of the last mg_solve (Section "Consistency
+ * with dynamic termination criteria and starvation effects": the residual
+ * and the number of pending background integration tasks per iteration).
+ * rel_residual_est: FP64 paths the recurrence residual ||r||/||f||; mixed
+ * paths the outer residual at the last restart times the inner FP32
+ * residual (an estimate of ||f - A(u + e)|| / ||f||).  pending_jobs: chunk
+ * assembly jobs enqueued, running, finished or held and not yet published. */
+typedef struct {
+  int32_t cycle;           /* 1-based outer iteration */
+  int32_t pending_jobs;
+  int32_t publishes;       /* chunk publications so far */
+  int32_t restarted;       /* 1 if an outer restart preceded this iteration */
+  double rel_residual_est;
+  double time_ms;          /* since the start of mg_solve, when the iteration's scalars were read */
+} mg_trace_entry;
+
+/* Copies up to cap records of the last solve to host_out (may be NULL with
+ * cap = 0) and the total count to *n.  Errors: MG_ERR_INVALID (null p or n). */
+mg_status mg_get_trace(const mg_problem* p, mg_trace_entry* host_out, size_t cap, size_t* n);
+
 /* Per-cell storage class (0..3) and cell-centre eps of the finest level; the
  * arrays hold n_cells^d entries; either pointer may be NULL. */
 mg_status mg_get_cell_data(const mg_problem* p, uint8_t* cls, double* eps_c, size_t n);

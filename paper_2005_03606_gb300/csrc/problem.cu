@@ -131,6 +131,7 @@ struct mg_problem {
   // are integrated at s > 1, every other cell keeps its geometric stencil
   int* ilist = nullptr;           // [nchunk][chunk_cells] local cell indices
   std::vector<int> ilist_n;       // count per chunk (host)
+  std::vector<mg_trace_entry> trace_log;   // per outer iteration of the last solve
   // adaptive accuracy (desc.adapt_C > 0)
   bool adapt = false;
   uint8_t* final_flags = nullptr; // [nchunk][chunk_cells]: 1 once the cell stopped refining
@@ -1325,6 +1326,8 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   const double tol2 = d.rtol * d.rtol;
   mg_status result = MG_ERR_NOT_CONVERGED;
   bool have_first = false;
+  bool restarted = false;
+  P->trace_log.clear();
   double seg_rr = 0.0;
   int seg_cycles = 0;
   while (P->cycles < d.max_cycles) {
@@ -1356,6 +1359,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       // at the last restart (a publication changes the operator)
       seg_rr = P->rr;
       seg_cycles = 0;
+      restarted = true;
     }
     const double refn = P->ff > 0 ? P->ff : ref;
     if (P->rr <= tol2 * refn) {
@@ -1385,6 +1389,22 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     s = read_scalars(P);
     if (s != MG_OK) return s;
     ++seg_cycles;
+    {
+      mg_trace_entry t{};
+      t.cycle = P->cycles;
+      {
+        std::lock_guard<std::mutex> lk(P->mu);
+        t.pending_jobs = P->in_flight + (int)P->held.size();
+      }
+      t.publishes = P->publishes;
+      t.restarted = restarted ? 1 : 0;
+      const double ffn = P->ff > 0 ? P->ff : 1.0;
+      t.rel_residual_est = P->mixed ? std::sqrt(P->rr / ffn) * std::sqrt(std::max(P->h_sc->rr_in, 0.0))
+                                    : std::sqrt(P->rr / ffn);
+      t.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      P->trace_log.push_back(t);
+      restarted = false;
+    }
     if (P->mixed) {
       bool diverged = false;
       s = mixed_after_iteration(P, &diverged);
@@ -1501,6 +1521,16 @@ mg_status mg_get_cell_matrices(const mg_problem* Pc, int level, const int64_t* c
   cudaFreeAsync(dc, P->st);
   cudaFreeAsync(tmp, P->st);
   MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
+mg_status mg_get_trace(const mg_problem* P, mg_trace_entry* out, size_t cap, size_t* n) {
+  if (!P || !n || (cap && !out)) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  *n = P->trace_log.size();
+  for (size_t i = 0; i < cap && i < P->trace_log.size(); ++i) out[i] = P->trace_log[i];
   return MG_OK;
 }
 

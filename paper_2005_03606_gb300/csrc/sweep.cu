@@ -722,6 +722,17 @@ __device__ __forceinline__ void geo_share(int ntx, int nty, int N, long long& w0
   w1 = min(total, w0 + per);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream still runs;
+// griddepcontrol.wait blocks the calling thread until the predecessor grid
+// has completed and its memory operations are visible.
+#ifndef MG_FIX_PDL
+#define MG_FIX_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // L2 prefetch of one address (no register, no scoreboard wait)
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -838,12 +849,15 @@ __device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc
   }
   const float bb4[4] = {b4.x, b4.y, b4.z, b4.w};
   const float um1[4] = {m4.x, m4.y, m4.z, m4.w};
+  float yT[5];   // eps-weighted cell sums of both layers, per cell column
+#pragma unroll
+  for (int i = 0; i < 5; ++i) yT[i] = yTm[i] + yTc[i];
   float out[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const float uv = uc.v[1][e + 1];
     const float G = ey[e] + ey[e + 1];
-    const float ST = (yTm[e] + yTm[e + 1]) + (yTc[e] + yTc[e + 1]);
+    const float ST = yT[e] + yT[e + 1];
     float w = 5.f * uv * G - ST;
     w = fmaf(ey[e], uc.v[1][e], w);                         // x - 1
     w = fmaf(ey[e + 1], uc.v[1][e + 2], w);                 // x + 1
@@ -851,13 +865,14 @@ __device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc
     w = fmaf(ez[1][e] + ez[1][e + 1], uc.v[2][e + 1], w);   // y + 1
     w = fmaf(elm[e] + elm[e + 1], um1[e], w);               // z - 1
     w = fmaf(elc[e] + elc[e + 1], un.v[1][e + 1], w);       // z + 1
-    const float acc = c.h12 * w;
     const int i = c.q + e;
     const bool valid = i >= 1 && i <= c.N - 1;
     float r;
-    if (MODE == SW_JACOBI) r = uv + c.omega * __fdividef(bb4[e] - acc, c.h3 * G);
-    else if (MODE == SW_RESID) r = bb4[e] - acc;
+    // Jacobi: u + omega (b - h/12 w) / (h/3 G), with omega / (h/3) folded into c.omega
+    if (MODE == SW_JACOBI) r = fmaf(c.omega, __fdividef(fmaf(-c.h12, w, bb4[e]), G), uv);
+    else if (MODE == SW_RESID) r = fmaf(-c.h12, w, bb4[e]);
     else {
+      const float acc = c.h12 * w;
       r = acc;
       if (valid) {
         d1 += uv * acc;
@@ -885,7 +900,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
   c.plane = (size_t)c.n1 * c.n1;
   c.h12 = -op.gk32;   // h / 12
   c.h3 = 4.f * c.h12;   // h / 3
-  c.omega = omega;
+  c.omega = omega / c.h3;   // the Jacobi step divides by h/3 G
   // per-thread partial dot products in FP32 (a few hundred terms; they only
   // set the Krylov step lengths), summed over the block in FP64
   float d1 = 0.f, d2 = 0.f;
@@ -943,6 +958,13 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
   const int nt = *op.ntouched;
   const int cap = op.tcap;
   float d1 = 0.f;
+  // Launched as a programmatic dependent of the bulk pass: everything up to
+  // the first access of y (written by the bulk pass) overlaps its tail.
+  bool waited = false;
+  auto wait_bulk = [&]() {
+    if (!waited) pdl_wait();
+    waited = true;
+  };
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     const int v = op.touched[t];
     if constexpr (MODE == SW_JACOBI0) {   // zero iterate: only the diagonal is needed
@@ -957,7 +979,9 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
         const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
         vertex_apply<3, float, true, float>(op, i, j, k, u0, &Au0, &dg);
       }
-      y[v] = omega * __ldg(b + v) / dg;
+      const float r = omega * __ldg(b + v) / dg;
+      wait_bulk();
+      y[v] = r;
     } else {
       float u[27];
 #pragma unroll
@@ -970,6 +994,7 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
       float Au, dg;
       const float uv = u[13];
       // right-hand side (the bulk pass's value for the matvec) fetched up front
+      if (MODE == SW_MATVEC) wait_bulk();
       const float bv = MODE == SW_MATVEC ? y[v] : __ldg(b + v);
       if (t < cap) {
         // all 27 coefficient loads issued before the first use (independent of u)
@@ -988,15 +1013,20 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
         vertex_apply<3, float, true, float>(op, i, j, k, u, &Au, &dg);
       }
       if (MODE == SW_JACOBI) {
-        y[v] = uv + omega * (bv - Au) / dg;
+        const float r = uv + omega * (bv - Au) / dg;
+        wait_bulk();
+        y[v] = r;
       } else if (MODE == SW_RESID) {
-        y[v] = bv - Au;
+        const float r = bv - Au;
+        wait_bulk();
+        y[v] = r;
       } else {
         y[v] = Au;
         d1 += uv * (Au - bv);   // bv: the bulk pass's value at v
       }
     }
   }
+  wait_bulk();   // the grid never completes before the bulk pass
   if (MODE == SW_MATVEC) {
     const double s1 = block_sum((double)d1, sh[0]);
     if (threadIdx.x == 0) {
@@ -1463,6 +1493,25 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp 
   }
 }
 
+template <int MODE>
+void launch_fixup(const LevelOp& op, const float* x, const float* b, float* y, float omega, double* pfix,
+                  cudaStream_t st) {
+#if MG_FIX_PDL
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(kFixBlocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, sweep3_fixup<MODE>, op, x, b, y, omega, pfix);
+#else
+  sweep3_fixup<MODE><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+#endif
+}
+
 cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
                         double* partials, int* nblocks, cudaStream_t st) {
   const int nq = (op.N + 1) / 4;
@@ -1482,19 +1531,19 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   if (mode == SW_JACOBI0) {
     sweep3_jacobi0<<<nb_bulk, blk, 0, st>>>(op, b, y, omega, ntx, nty);
     count_launches(1);
-    sweep3_fixup<SW_JACOBI0><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+    launch_fixup<SW_JACOBI0>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_JACOBI) {
     sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
-    sweep3_fixup<SW_JACOBI><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+    launch_fixup<SW_JACOBI>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_RESID) {
     sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
-    sweep3_fixup<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+    launch_fixup<SW_RESID>(op, x, b, y, omega, pfix, st);
   } else {
     sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
-    sweep3_fixup<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+    launch_fixup<SW_MATVEC>(op, x, b, y, omega, pfix, st);
   }
   if (nblocks) *nblocks = nb_bulk + kFixBlocks;
   return launched();

@@ -52,6 +52,11 @@ class mg_solve_info(ctypes.Structure):
                 ("payload_bytes", ctypes.c_int64)]
 
 
+class mg_trace_entry(ctypes.Structure):
+    _fields_ = [("cycle", ctypes.c_int32), ("pending_jobs", ctypes.c_int32), ("publishes", ctypes.c_int32),
+                ("restarted", ctypes.c_int32), ("rel_residual_est", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
 class mg_server_desc(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_double), ("inject_fail_every", ctypes.c_int32),
@@ -87,6 +92,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_get_element_matrices": (st, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
             "mg_get_cell_data": (st, [_VP, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t]),
             "mg_get_cell_accuracy": (st, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_size_t]),
+            "mg_get_trace": (st, [_VP, ctypes.POINTER(mg_trace_entry), ctypes.c_size_t,
+                                  ctypes.POINTER(ctypes.c_size_t)]),
             "mg_get_cell_matrices": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t, _D]),
             "mg_apply_level": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
             "mg_vcycle_apply": (st, [_VP, _D, _D]),
@@ -253,6 +260,14 @@ class Problem:
         ec = np.zeros(n)
         _check(load().mg_get_cell_data(self.h, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _p(ec), n))
         return cls, ec
+
+    def trace(self) -> list:
+        """Per-iteration records of the last solve, as dicts."""
+        n = ctypes.c_size_t(0)
+        _check(load().mg_get_trace(self.h, None, 0, ctypes.byref(n)))
+        buf = (mg_trace_entry * max(n.value, 1))()
+        _check(load().mg_get_trace(self.h, buf, n.value, ctypes.byref(n)))
+        return [{f: getattr(buf[i], f) for f, _ in mg_trace_entry._fields_} for i in range(n.value)]
 
     def cell_accuracy(self) -> np.ndarray:
         n = self.level_cells(0)

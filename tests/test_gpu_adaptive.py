@@ -127,3 +127,28 @@ def test_adaptive_rejects_bad_C():
         with pytest.raises(mg.MGError) as ei:
             mg.Problem(mg.problem_desc(2, 27, fld, s_schedule=(1, 2), adapt_C=bad))
         assert ei.value.status == mg.MG_ERR_INVALID
+
+
+@pytest.mark.parametrize("path", [mg.PATH_FP64_DELAYED, mg.PATH_MIXED_DELAYED, mg.PATH_FP64_PLAIN])
+def test_solve_trace_records_every_iteration(path):
+    """Per-iteration telemetry (residual and pending background jobs, the two
+    quantities of the paper's starvation experiment)."""
+    fld = inputs.disc_field(2, v_in=1e-3, v_out=1.0)
+    sched = (1, 2, 4, 8) if path != mg.PATH_FP64_PLAIN else (8,)
+    with mg.Problem(mg.problem_desc(2, 81, fld, path=path, s_schedule=sched, chunks=3)) as P:
+        info = P.solve()
+        tr = P.trace()
+        # a second solve replaces the record
+        info2 = P.solve()
+        tr2 = P.trace()
+    assert len(tr) == info.cycles and len(tr2) == info2.cycles
+    assert [t["cycle"] for t in tr] == list(range(1, info.cycles + 1))
+    pend = [t["pending_jobs"] for t in tr]
+    assert all(a >= b for a, b in zip(pend, pend[1:]))          # no job is added during a solve
+    assert pend[-1] == 0 and tr[-1]["publishes"] == info.publishes
+    if path == mg.PATH_FP64_PLAIN:
+        assert max(pend) == 0 and info.publishes == 0
+    times = [t["time_ms"] for t in tr]
+    assert all(a <= b for a, b in zip(times, times[1:]))
+    assert tr[0]["restarted"] == 1
+    assert tr[-1]["rel_residual_est"] <= 1e-6
