@@ -451,6 +451,22 @@ def run_probe(args, local_rank):
         print(json.dumps({"probe": "adaptive", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
               flush=True)
         return
+    if args.probe == "paths":   # time-to-solution of the four paths on one workload
+        names = {mg.PATH_MIXED_DELAYED: "mixed delayed", mg.PATH_MIXED_PLAIN: "mixed plain",
+                 mg.PATH_FP64_DELAYED: "fp64 delayed", mg.PATH_FP64_PLAIN: "fp64 plain"}
+        for path, name in names.items():
+            w, d = workload_desc(mg, args.workload, path, n_cells=args.n)
+            runs = []
+            for _ in range(args.probe_reps):
+                with mg.Problem(d) as P:
+                    t0 = time.perf_counter()
+                    info = P.solve()
+                    runs.append({"ms": (time.perf_counter() - t0) * 1e3, "cycles": int(info.cycles),
+                                 "publishes": int(info.publishes), "rel_residual": float(info.rel_residual),
+                                 "assembly_ms": float(info.assembly_ms)})
+            print(json.dumps({"probe": "paths", "workload": args.workload, "n_cells": w.n_cells, "path": name,
+                              "runs": runs}), flush=True)
+        return
     if args.probe == "starvation":   # per-iteration residual and pending assembly jobs
         # 2D 243^2 (59,049 unknowns), eps in {1e-5, 1}: disc of radius 0.3
         fld = inputs.disc_field(2, v_in=1e-5, v_out=1.0)
@@ -502,7 +518,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving", "adaptive",
-                                        "starvation"],
+                                        "starvation", "paths"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)
