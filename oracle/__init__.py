@@ -73,6 +73,12 @@ def _load():
         lib.oc_kref.argtypes = [ctypes.c_int, ctypes.c_int, _D]
         lib.oc_compress.argtypes = [FP, ctypes.c_int, _D, ctypes.c_double, _D,
                                     ctypes.POINTER(ctypes.c_uint8), _D]
+        lib.oc_pf_roundtrip.argtypes = [ctypes.c_double, ctypes.c_int]
+        lib.oc_pf_roundtrip.restype = ctypes.c_double
+        lib.oc_pf_choose.argtypes = [_D, ctypes.c_int, ctypes.c_double]
+        lib.oc_pf_choose.restype = ctypes.c_int
+        lib.oc_paper_format.argtypes = [ctypes.c_int, ctypes.c_int64, _D, _D, _D, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_int32), _D]
         lib.oc_apply.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
         lib.oc_diag.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         lib.oc_residual.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
@@ -212,6 +218,38 @@ def compress(field: Field, n_cells: int, A_all: np.ndarray, tau: float):
     _load().oc_compress(ctypes.byref(field.c), n_cells, _p(A_all), float(tau), _p(At),
                         cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _p(sc))
     return At, cls, sc
+
+
+def pf_roundtrip(x: float, p3: int) -> float:
+    """Value of x after storage in the paper's format with p3 bytes
+    (Section "Precision toggling and information density")."""
+    return _load().oc_pf_roundtrip(float(x), int(p3))
+
+
+def pf_choose(dA, delta: float) -> int:
+    """Bytes per entry of a cell's surplus entries dA at absolute threshold delta."""
+    a = np.ascontiguousarray(np.ravel(dA), np.float64)
+    return _load().oc_pf_choose(_p(a), a.size, float(delta))
+
+
+def paper_format(dim: int, A_all: np.ndarray, eps_c: np.ndarray, K: np.ndarray, delta: float):
+    """(p3 per cell, decoded stored matrices) of the paper's format on the
+    surplus A - eps_c K of every cell."""
+    A_all = np.ascontiguousarray(A_all, np.float64)
+    ncell = A_all.shape[0]
+    p3 = np.zeros(ncell, np.int32)
+    At = np.zeros_like(A_all)
+    _load().oc_paper_format(dim, ncell, _p(A_all), _p(np.ascontiguousarray(eps_c, np.float64)),
+                            _p(np.ascontiguousarray(K, np.float64)), float(delta),
+                            p3.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _p(At))
+    return p3, At
+
+
+def paper_compression(dim: int, p3: np.ndarray) -> float:
+    """Compression factor of the paper's accounting: a full element matrix is
+    4^d doubles; a cell stores one marker byte plus p3 bytes per entry."""
+    ne = 4 ** dim
+    return float(p3.size * ne * 8) / float(np.sum(1 + ne * p3.astype(np.int64)))
 
 
 def apply(dim: int, n_cells: int, A_all: np.ndarray, u: np.ndarray) -> np.ndarray:

@@ -17,6 +17,9 @@
  *   - the hierarchical surplus A(s) - A(1) and its lossy storage
  *     (Section "Precision toggling and information density"), with the
  *     formats FP8-e4m3 / FP16 / FP32 plus a per-cell FP32 scale;
+ *   - the paper's own truncated-float storage of that surplus (sign bit,
+ *     truncated mantissa, signed-char exponent; p3 bytes per entry chosen
+ *     against an absolute error threshold) and its compression factor;
  *   - d-linear 3:1 prolongation P, restriction R = P^T and element-local
  *     Ritz-Galerkin coarse operators R A P (Section "Rediscretisation and
  *     geometric projections"; Eq. for the Galerkin operator);
@@ -336,6 +339,72 @@ void oc_compress(const oc_field* F, int N, const double* A_all, double tau, doub
     double sc;
     cls[c] = (uint8_t)oc_compress_cell(d, A_all + c * nv * nv, ec, K, tau, At_all + c * nv * nv, &sc);
     if (scales) scales[c] = sc;
+  }
+}
+
+/* ---------------- the paper's own storage format ----------------
+ * Section "Precision toggling and information density": with p3 bytes per
+ * entry (2 <= p3 < 8) an entry is a sign bit, m = 8 (p3 - 1) - 1 mantissa bits
+ * and a plain signed-char exponent e^ in [-128, 127] without bias; the
+ * mantissa is truncated, not rounded.  p3 = 8 is plain double precision and
+ * p3 = 0 stores nothing (the entry decodes to zero).  Readings where the text
+ * is silent: e^ = -128 is reserved for non-normalised values
+ * (f / 2^m) 2^-127, which holds zero and anything below 2^-127; values at or
+ * above 2^128 saturate to the largest encoding (2 - 2^-m) 2^127. */
+double oc_pf_roundtrip(double x, int p3) {
+  if (p3 >= 8) return x;
+  if (p3 <= 0 || x == 0.0) return 0.0;
+  const int m = 8 * (p3 - 1) - 1;
+  const double a = fabs(x);
+  int E;
+  frexp(a, &E);            /* a = f 2^E with f in [0.5, 1): a in [2^(E-1), 2^E) */
+  const int e = E - 1;
+  double r;
+  if (e > 127) {
+    r = (2.0 - ldexp(1.0, -m)) * ldexp(1.0, 127);
+  } else if (e >= -127) {
+    const double frac = a / ldexp(1.0, e) - 1.0;               /* in [0, 1) */
+    r = (1.0 + floor(ldexp(frac, m)) / ldexp(1.0, m)) * ldexp(1.0, e);
+  } else {
+    r = floor(ldexp(a, 127 + m)) * ldexp(1.0, -(127 + m));
+  }
+  return x < 0 ? -r : r;
+}
+
+/* Bytes per entry of one cell's hierarchical surplus (n entries): 0 when its
+ * Frobenius norm is below the absolute threshold delta (the format would
+ * store zeros), else the smallest p3 in 2..7 whose truncation error is at
+ * most delta for every entry, else 8. */
+int oc_pf_choose(const double* dA, int n, double delta) {
+  double f2 = 0.0;
+  for (int i = 0; i < n; ++i) f2 += dA[i] * dA[i];
+  if (sqrt(f2) < delta) return 0;
+  for (int p3 = 2; p3 <= 7; ++p3) {
+    double err = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double e = fabs(dA[i] - oc_pf_roundtrip(dA[i], p3));
+      if (e > err) err = e;
+    }
+    if (err <= delta) return p3;
+  }
+  return 8;
+}
+
+/* Every cell: surplus against the one-sample matrix eps_c[c] K (K = K_ref
+ * h^(d-2), eps_c the cell-centre value the path stores), its p3, and the
+ * decoded stored matrix eps_c K + roundtrip(A - eps_c K). */
+void oc_paper_format(int d, int64_t ncell, const double* A_all, const double* eps_c, const double* K,
+                     double delta, int32_t* p3_out, double* At_all) {
+  const int nv = 1 << d, ne = nv * nv;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < ncell; ++c) {
+    double dA[64];
+    const double* A = A_all + c * ne;
+    for (int i = 0; i < ne; ++i) dA[i] = A[i] - eps_c[c] * K[i];
+    const int p3 = oc_pf_choose(dA, ne, delta);
+    p3_out[c] = p3;
+    if (At_all)
+      for (int i = 0; i < ne; ++i) At_all[c * ne + i] = eps_c[c] * K[i] + oc_pf_roundtrip(dA[i], p3);
   }
 }
 

@@ -475,3 +475,94 @@ def test_adaptive_piecewise_constant_cells_away_from_the_interface_stop_early():
         dmax = np.sqrt(np.max(xs ** 2) + np.max(ys ** 2))
         dmin = np.sqrt((0 if xs[0] * xs[1] <= 0 else np.min(xs ** 2)) + (0 if ys[0] * ys[1] <= 0 else np.min(ys ** 2)))
         assert dmin <= 0.3 <= dmax
+
+
+# ---------------------------------------------------------------- the paper's truncated storage format
+
+def _mask_truncate(x, m):
+    """Truncation of a normal double to m mantissa bits by clearing the low
+    52 - m bits of its IEEE encoding (an independent formulation)."""
+    b = np.array([x], np.float64).view(np.uint64)[0]
+    mask = np.uint64(~((1 << (52 - m)) - 1) & 0xFFFFFFFFFFFFFFFF)
+    return float(np.array([b & mask], np.uint64).view(np.float64)[0])
+
+
+def test_paper_format_keeps_representable_values_and_truncates_the_rest():
+    # p3 = 2: 7 mantissa bits
+    assert oracle.pf_roundtrip(1.5, 2) == 1.5
+    assert oracle.pf_roundtrip(1 + 2 ** -7, 2) == 1 + 2 ** -7
+    assert oracle.pf_roundtrip(1 + 2 ** -8, 2) == 1.0          # truncated, not rounded
+    assert oracle.pf_roundtrip(1 + 2 ** -7 + 2 ** -8, 2) == 1 + 2 ** -7
+    assert oracle.pf_roundtrip(-(1 + 2 ** -8), 2) == -1.0      # toward zero for negatives too
+    assert oracle.pf_roundtrip(0.0, 3) == 0.0
+    assert oracle.pf_roundtrip(0.123, 0) == 0.0                # p3 = 0 stores nothing
+    assert oracle.pf_roundtrip(0.1, 8) == 0.1                  # p3 = 8 is plain double
+
+
+def test_paper_format_equals_mantissa_bit_truncation():
+    rng = np.random.default_rng(7)
+    xs = rng.uniform(1, 2, 400) * 2.0 ** rng.integers(-120, 120, 400) * rng.choice([-1, 1], 400)
+    for p3 in range(2, 8):
+        m = 8 * (p3 - 1) - 1
+        for x in xs:
+            r = oracle.pf_roundtrip(x, p3)
+            assert r == _mask_truncate(x, m)
+            e = np.floor(np.log2(abs(x)))
+            assert 0 <= abs(x) - abs(r) < 2.0 ** (e - m)
+
+
+def test_paper_format_exponent_range():
+    m2, m4 = 7, 23
+    # below 2^-127: non-normalised, quantum 2^-(127 + m)
+    assert oracle.pf_roundtrip(2.0 ** -130, 4) == 2.0 ** -130
+    assert oracle.pf_roundtrip(3 * 2.0 ** -140, 2) == 0.0
+    assert oracle.pf_roundtrip(2.0 ** -130 + 2.0 ** -160, 4) == 2.0 ** -130
+    # at or above 2^128: the largest encoding
+    assert oracle.pf_roundtrip(2.0 ** 130, 2) == (2 - 2.0 ** -m2) * 2.0 ** 127
+    assert oracle.pf_roundtrip(-(2.0 ** 128), 4) == -(2 - 2.0 ** -m4) * 2.0 ** 127
+    assert oracle.pf_roundtrip(2.0 ** 127, 2) == 2.0 ** 127
+
+
+def test_paper_format_byte_choice():
+    delta = 1e-8
+    assert oracle.pf_choose(np.zeros(16), delta) == 0
+    assert oracle.pf_choose(np.full(16, 0.99e-8 / 4), delta) == 0   # Frobenius norm just below delta
+    assert oracle.pf_choose(np.full(16, 1.01e-8 / 4), delta) == 2   # 2.5e-9 = 1.01 * 2^-28.6: exact enough
+    x = 2.0 ** -10 * (2 - 2.0 ** -30)        # 30 mantissa bits set: 1.11...1 (binary) 2^-10
+    # truncation error about 2^-10 * 2^-m: m = 7 -> 7.6e-6, m = 15 -> 3.0e-8, m = 23 -> 1.2e-10
+    assert oracle.pf_choose(np.array([x]), delta) == 4
+    assert oracle.pf_choose(np.array([x]), 4e-8) == 3
+    assert oracle.pf_choose(np.array([x]), 1e-5) == 2
+    assert oracle.pf_choose(np.array([x]), 1e-14) == 5      # m = 31 holds all 30 bits: exact
+    assert oracle.pf_roundtrip(x, 5) == x
+    assert oracle.pf_choose(np.array([0.1]), 1e-20) == 8
+    assert oracle.pf_choose(np.array([0.5 + 2 ** -5]), 1e-30) == 2   # exact in 7 bits
+
+
+def test_paper_format_compression_accounting():
+    # a full 2D element matrix is 16 doubles = 128 bytes; a marker byte alone compresses 128-fold
+    assert oracle.paper_compression(2, np.zeros(10, np.int32)) == 128.0
+    assert oracle.paper_compression(3, np.zeros(10, np.int32)) == 512.0
+    assert oracle.paper_compression(2, np.full(4, 2, np.int32)) == 128.0 / 33.0
+    assert oracle.paper_compression(2, np.array([0, 8], np.int32)) == 256.0 / (1 + 129)
+
+
+def test_paper_format_of_assembled_operators():
+    n = 9
+    K = oracle.kref(2, n)
+    # constant eps: no surplus anywhere, so every cell is a marker byte
+    f = oracle.Field(inputs.const_field(2, 2.5))
+    A = oracle.assemble(f, n, 4)
+    p3, At = oracle.paper_format(2, A, np.full(n * n, 2.5), K, 1e-8)
+    assert np.all(p3 == 0) and np.array_equal(At, 2.5 * K[None].repeat(n * n, 0))
+    # a varying field: every stored entry within delta of the assembled one
+    f = oracle.Field(inputs.theta_field(2, 16.0))
+    A = oracle.assemble(f, n, 4)
+    ec = np.array([oracle.eps_at(f, ((i + 0.5) / n, (j + 0.5) / n)) for j in range(n) for i in range(n)])
+    for delta in (1e-4, 1e-8, 1e-12):
+        p3, At = oracle.paper_format(2, A, ec, K, delta)
+        assert np.abs(At - A).max() <= delta
+        assert set(np.unique(p3)) <= {0, 2, 3, 4, 5, 6, 7, 8}
+    p_lo, _ = oracle.paper_format(2, A, ec, K, 1e-4)
+    p_hi, _ = oracle.paper_format(2, A, ec, K, 1e-12)
+    assert np.all(p_hi >= p_lo) and p_hi.sum() > p_lo.sum()
