@@ -451,6 +451,28 @@ def run_probe(args, local_rank):
         print(json.dumps({"probe": "adaptive", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
               flush=True)
         return
+    if args.probe == "paper_format":   # Table "memory-footprint": accuracy and compression per cycle
+        # 2D theta setup at h = 1/27, adaptive accuracy C = 1%, one accuracy level per
+        # cycle, the paper's truncated format at an absolute 1e-8 on the surplus
+        n = args.n or 27
+        out = {}
+        for theta in (1.0, 16.0, 64.0):
+            d = mg.problem_desc(2, n, inputs.theta_field(2, theta), path=mg.PATH_FP64_PLAIN,
+                                s_schedule=tuple(range(1, 9)), adapt_C=0.01)
+            rows = []
+            with mg.Problem(d) as P:
+                for s in range(1, 9):
+                    if s > 1:
+                        P.assemble(s)
+                    acc = P.cell_accuracy()
+                    p3, _, st = P.paper_format(1e-8)
+                    rows.append({"cycle": s, "max_n": int(acc.max()), "avg_n": float(acc.mean()),
+                                 "compression": st["compression"], "cells_by_p3": st["cells_by_p3"],
+                                 "max_abs_error": st["max_abs_error"]})
+            out[str(theta)] = rows
+        print(json.dumps({"probe": "paper_format", "n_cells": n, "delta": 1e-8, "C": 0.01, "theta": out}),
+              flush=True)
+        return
     if args.probe == "paths":   # time-to-solution of the four paths on one workload
         names = {mg.PATH_MIXED_DELAYED: "mixed delayed", mg.PATH_MIXED_PLAIN: "mixed plain",
                  mg.PATH_FP64_DELAYED: "fp64 delayed", mg.PATH_FP64_PLAIN: "fp64 plain"}
@@ -518,7 +540,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving", "adaptive",
-                                        "starvation", "paths"],
+                                        "starvation", "paths", "paper_format"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)

@@ -216,6 +216,31 @@ typedef struct {
  * cap = 0) and the total count to *n.  Errors: MG_ERR_INVALID (null p or n). */
 mg_status mg_get_trace(const mg_problem* p, mg_trace_entry* host_out, size_t cap, size_t* n);
 
+/* The paper's own storage format (Section "Precision toggling and
+ * information density") applied to the finest level's stored operator A:
+ * per cell the hierarchical surplus A - eps_c K_ref h^(d-2) (eps_c the
+ * cell-centre value the path stores), held with p3 bytes per entry: a sign
+ * bit, a truncated mantissa of 8 (p3 - 1) - 1 bits and a signed-char exponent
+ * without bias (p3 = 8: plain FP64).  p3 = 0 (nothing stored) when the
+ * surplus' Frobenius norm is below delta, else the smallest p3 with every
+ * entry's truncation error at most delta.  The values the format cannot
+ * normalise (below 2^-127) are held as multiples of 2^-(127 + m); values at or
+ * above 2^128 saturate.  Outputs (each may be NULL): p3 per cell (host,
+ * n_cells^d bytes), the decoded stored matrices eps_c K + trunc(surplus)
+ * (host, n_cells^d * 4^d FP64, 2^d x 2^d row-major per cell), and the
+ * statistics below; n must be n_cells^d.  The problem is not modified.
+ * Errors: MG_ERR_INVALID (n, delta < 0 or not finite), MG_ERR_OOM, MG_ERR_CUDA. */
+typedef struct {
+  int64_t cells_by_p3[9];   /* cells per p3 = 0 .. 8 (1 never occurs) */
+  double bytes_full;        /* 4^d doubles per cell */
+  double bytes_paper;       /* one marker byte plus 4^d p3 bytes per cell */
+  double compression;       /* bytes_full / bytes_paper */
+  double max_abs_error;     /* max over all entries |stored - A| */
+} mg_paper_format_stats;
+
+mg_status mg_paper_format(const mg_problem* p, double delta, uint8_t* p3_host, double* decoded_host, size_t n,
+                          mg_paper_format_stats* stats);
+
 /* Per-cell storage class (0..3) and cell-centre eps of the finest level; the
  * arrays hold n_cells^d entries; either pointer may be NULL. */
 mg_status mg_get_cell_data(const mg_problem* p, uint8_t* cls, double* eps_c, size_t n);

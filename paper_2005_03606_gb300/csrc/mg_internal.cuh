@@ -339,4 +339,9 @@ cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void*
 cudaError_t launch_decode_matrices(const LevelOp& op, const long long* cells, long long ncells, double* out,
                                    cudaStream_t st);
 
+// paper_format.cu: the paper's truncated storage of a level's surplus
+cudaError_t launch_paper_format(int dim, long long ncell, const double* A, const void* eps_c, int eps64,
+                                double hfac, double delta, uint8_t* p3_out, double* At, unsigned long long* hist,
+                                unsigned long long* maxerr_bits, cudaStream_t st);
+
 }  // namespace mg

@@ -1553,6 +1553,55 @@ mg_status mg_get_cell_accuracy(const mg_problem* Pc, int32_t* s_out, size_t n) {
   return MG_OK;
 }
 
+mg_status mg_paper_format(const mg_problem* Pc, double delta, uint8_t* p3_host, double* decoded_host, size_t n,
+                          mg_paper_format_stats* stats) {
+  mg_problem* P = const_cast<mg_problem*>(Pc);
+  if (!P || n != (size_t)P->lev[0].ncell || !(delta >= 0.0) || !std::isfinite(delta)) {
+    set_error("bad arguments (n must be cells, delta finite and >= 0)");
+    return MG_ERR_INVALID;
+  }
+  const Level& l0 = P->lev[0];
+  const int nv = 1 << P->dim;
+  const size_t ne = (size_t)nv * nv;
+  double* A = nullptr;
+  double* At = nullptr;
+  uint8_t* p3 = nullptr;
+  unsigned long long* cnt = nullptr;   // hist[9], then the max-error bits
+  cudaError_t e = mg_malloc_async(&A, sizeof(double) * n * ne, P->st);
+  if (e == cudaSuccess && decoded_host) e = mg_malloc_async(&At, sizeof(double) * n * ne, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&p3, n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&cnt, sizeof(unsigned long long) * 10, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "paper format buffers");
+  unsigned long long h[10];
+  MG_CHECK(cudaMemsetAsync(cnt, 0, sizeof(h), P->st));
+  MG_CHECK(launch_decode_matrices(l0.op, nullptr, 0, A, P->st));
+  MG_CHECK(launch_paper_format(P->dim, (long long)n, A, P->eps_c, P->mixed ? 0 : 1, l0.op.hfac, delta, p3, At, cnt,
+                               cnt + 9, P->st));
+  MG_CHECK(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, P->st));
+  if (p3_host) MG_CHECK(cudaMemcpyAsync(p3_host, p3, n, cudaMemcpyDeviceToHost, P->st));
+  if (decoded_host) MG_CHECK(cudaMemcpyAsync(decoded_host, At, sizeof(double) * n * ne, cudaMemcpyDeviceToHost, P->st));
+  cudaFreeAsync(A, P->st);
+  if (At) cudaFreeAsync(At, P->st);
+  cudaFreeAsync(p3, P->st);
+  cudaFreeAsync(cnt, P->st);
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    double paper = 0.0;
+    for (int k = 0; k < 9; ++k) {
+      stats->cells_by_p3[k] = (int64_t)h[k];
+      paper += (double)h[k] * (1.0 + (double)ne * k);
+    }
+    stats->bytes_full = (double)n * ne * 8.0;
+    stats->bytes_paper = paper;
+    stats->compression = paper > 0 ? stats->bytes_full / paper : 0.0;
+    double em;
+    memcpy(&em, &h[9], sizeof(em));
+    stats->max_abs_error = em;
+  }
+  return MG_OK;
+}
+
 mg_status mg_get_cell_data(const mg_problem* Pc, uint8_t* cls, double* eps_c, size_t n) {
   mg_problem* P = const_cast<mg_problem*>(Pc);
   if (!P || n != (size_t)P->lev[0].ncell) {

@@ -57,6 +57,11 @@ class mg_trace_entry(ctypes.Structure):
                 ("restarted", ctypes.c_int32), ("rel_residual_est", ctypes.c_double), ("time_ms", ctypes.c_double)]
 
 
+class mg_paper_format_stats(ctypes.Structure):
+    _fields_ = [("cells_by_p3", ctypes.c_int64 * 9), ("bytes_full", ctypes.c_double), ("bytes_paper", ctypes.c_double),
+                ("compression", ctypes.c_double), ("max_abs_error", ctypes.c_double)]
+
+
 class mg_server_desc(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_double), ("inject_fail_every", ctypes.c_int32),
@@ -94,6 +99,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_get_cell_accuracy": (st, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_size_t]),
             "mg_get_trace": (st, [_VP, ctypes.POINTER(mg_trace_entry), ctypes.c_size_t,
                                   ctypes.POINTER(ctypes.c_size_t)]),
+            "mg_paper_format": (st, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t,
+                                     ctypes.POINTER(mg_paper_format_stats)]),
             "mg_get_cell_matrices": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t, _D]),
             "mg_apply_level": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
             "mg_vcycle_apply": (st, [_VP, _D, _D]),
@@ -268,6 +275,20 @@ class Problem:
         buf = (mg_trace_entry * max(n.value, 1))()
         _check(load().mg_get_trace(self.h, buf, n.value, ctypes.byref(n)))
         return [{f: getattr(buf[i], f) for f, _ in mg_trace_entry._fields_} for i in range(n.value)]
+
+    def paper_format(self, delta: float = 1e-8, decoded: bool = False):
+        """The paper's truncated storage of the finest level's surplus:
+        (p3 per cell, decoded matrices or None, statistics as a dict)."""
+        n = self.level_cells(0)
+        nv = 1 << self.dim
+        p3 = np.zeros(n, np.uint8)
+        At = np.zeros((n, nv, nv)) if decoded else None
+        st = mg_paper_format_stats()
+        _check(load().mg_paper_format(self.h, float(delta), p3.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                      _p(At) if decoded else None, n, ctypes.byref(st)))
+        stats = {"cells_by_p3": list(st.cells_by_p3), "bytes_full": st.bytes_full, "bytes_paper": st.bytes_paper,
+                 "compression": st.compression, "max_abs_error": st.max_abs_error}
+        return p3, At, stats
 
     def cell_accuracy(self) -> np.ndarray:
         n = self.level_cells(0)

@@ -48,16 +48,17 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sz.c"
-    src.write_text('#include <stdio.h>\n#include "mg.h"\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+    src.write_text('#include <stdio.h>\n#include "mg.h"\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                    "sizeof(mg_eps_desc), sizeof(mg_problem_desc), sizeof(mg_solve_info), sizeof(mg_server_desc),"
                    "sizeof(mg_result), offsetof(mg_problem_desc, u0), offsetof(mg_eps_desc, box_hi), sizeof(mg_trace_entry),"
-                   "offsetof(mg_problem_desc, adapt_C));return 0;}\n")
+                   "offsetof(mg_problem_desc, adapt_C), sizeof(mg_paper_format_stats));return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(mg.mg_eps_desc), ctypes.sizeof(mg.mg_problem_desc), ctypes.sizeof(mg.mg_solve_info),
             ctypes.sizeof(mg.mg_server_desc), ctypes.sizeof(mg.mg_result), mg.mg_problem_desc.u0.offset,
-            mg.mg_eps_desc.box_hi.offset, ctypes.sizeof(mg.mg_trace_entry), mg.mg_problem_desc.adapt_C.offset]
+            mg.mg_eps_desc.box_hi.offset, ctypes.sizeof(mg.mg_trace_entry), mg.mg_problem_desc.adapt_C.offset,
+            ctypes.sizeof(mg.mg_paper_format_stats)]
     assert got == want
 
 
