@@ -93,6 +93,9 @@ def _load():
         lib.oc_vcycle_once.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_int, _D]
         lib.oc_vcycle_once.restype = ctypes.c_int
+        lib.oc_inject.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.oc_additive_once.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int, _D]
+        lib.oc_additive_once.restype = ctypes.c_int
         lib.oc_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -319,6 +322,25 @@ def vcycle_once(dim, n_cells, A_fine, b, omega=0.6, nu_pre=2, nu_post=2):
                                 _p(np.ascontiguousarray(b, np.float64)), float(omega), nu_pre, nu_post, _p(e))
     if rc < 0:
         raise ValueError("bad grid size")
+    return e
+
+
+def inject(dim, nc, rf):
+    bc = np.zeros((nc + 1) ** dim)
+    _load().oc_inject(dim, nc, _p(np.ascontiguousarray(rf, np.float64)), _p(bc))
+    return bc
+
+
+ADDITIVE, ADAFAC_PI, ADAFAC_JAC = 0, 1, 2
+
+
+def additive_once(dim, n_cells, A_fine, b, omega=0.6, variant=ADAFAC_JAC):
+    """One additive cycle (plain, adaFAC-PI or adaFAC-Jac) for A e = b from e = 0."""
+    e = np.zeros((n_cells + 1) ** dim)
+    rc = _load().oc_additive_once(dim, n_cells, _p(np.ascontiguousarray(A_fine, np.float64)),
+                                  _p(np.ascontiguousarray(b, np.float64)), float(omega), int(variant), _p(e))
+    if rc != 0:
+        raise ValueError("n_cells must be a power of 3")
     return e
 
 

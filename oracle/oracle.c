@@ -23,6 +23,8 @@
  *   - d-linear 3:1 prolongation P, restriction R = P^T and element-local
  *     Ritz-Galerkin coarse operators R A P (Section "Rediscretisation and
  *     geometric projections"; Eq. for the Galerkin operator);
+ *   - the additive cycles of Section "adaFAC-x" (plain additive multigrid,
+ *     adaFAC-PI and adaFAC-Jac) with injection for adaFAC-PI;
  *   - damped Jacobi S = omega diag^-1(A) (Section "adaFAC-x"), the
  *     multiplicative V(nu1,nu2) cycle on the correction equation (Section
  *     "Multiplicative vs. additive schemes"), a dense solve on the coarsest
@@ -850,6 +852,114 @@ int oc_vcycle_once(int d, int N, const double* A_fine, const double* b, double o
   }
   coarse_setup(&mg);
   vcycle(&mg, L - 1, b, e);
+  for (int l = L - 2; l >= 0; --l) free(mg.A[l]);
+  free(mg.dense);
+  free(mg.int_idx);
+  return 0;
+}
+
+/* Injection of fine vertex values to the coinciding coarse vertices (the
+ * restriction of adaFAC-PI's auxiliary equation, Section "adaFAC-x"). */
+void oc_inject(int d, int Nc, const double* rf, double* bc) {
+  const int Nf = 3 * Nc;
+  const int64_t ncv = ipow(Nc + 1, d);
+  for (int64_t v = 0; v < ncv; ++v) {
+    int c[3] = {0, 0, 0};
+    int64_t t = v;
+    for (int a = 0; a < d; ++a) {
+      c[a] = (int)(t % (Nc + 1));
+      t /= Nc + 1;
+    }
+    int f[3] = {3 * c[0], 3 * c[1], 3 * c[2]};
+    bc[v] = on_boundary(d, Nc, v) ? 0.0 : rf[vidx(d, Nf, f)];
+  }
+}
+
+/* One additive cycle for the correction equation A e = b, from e = 0
+ * (Section "adaFAC-x", Eq. "adaFAC-x", in correction form): the fine residual
+ * is restricted to every level; every level but the coarsest takes one
+ * damped Jacobi step on it, c_l = omega D_l^-1 r_l, the coarsest is solved
+ * exactly, and all corrections are prolongated to the finest level and
+ * added.  variant 1 (adaFAC-PI) and 2 (adaFAC-Jac) subtract from each c_l
+ * (l above the coarsest) the projection P s of an auxiliary Jacobi step on
+ * the next coarser level, s = omega D_(l-1)^-1 t, which mimics the
+ * overshoot of the coarse corrections running concurrently: t = I r_l
+ * (injection) for adaFAC-PI, t = R (r_l - A_l c_l) (the residual the level's
+ * own smoothing leaves, restricted) for adaFAC-Jac.  variant 0 is plain
+ * additive multigrid.  Levels of mg: 0 coarsest .. L-1 finest. */
+static void additive_cycle(const oc_mg* mg, const double* b, double* e, int variant) {
+  const int d = mg->d, L = mg->L;
+  double* r[16];
+  double* c[16];
+  for (int l = 0; l < L; ++l) {
+    const int64_t nv = ipow(mg->N[l] + 1, d);
+    r[l] = (double*)calloc(nv, sizeof(double));
+    c[l] = (double*)calloc(nv, sizeof(double));
+  }
+  memcpy(r[L - 1], b, sizeof(double) * ipow(mg->N[L - 1] + 1, d));
+  for (int l = L - 1; l >= 1; --l) oc_restrict(d, mg->N[l - 1], r[l], r[l - 1]);
+  coarse_solve(mg, r[0], c[0]);
+  for (int l = 1; l < L; ++l) {
+    const int N = mg->N[l], Nc = mg->N[l - 1];
+    const int64_t nv = ipow(N + 1, d), ncv = ipow(Nc + 1, d);
+    double* zero = (double*)calloc(nv, sizeof(double));
+    oc_jacobi(d, N, mg->A[l], r[l], zero, mg->omega, c[l]);
+    if (variant == 1 || variant == 2) {
+      double* t = (double*)calloc(ncv, sizeof(double));
+      double* sc = (double*)calloc(ncv, sizeof(double));
+      double* zc = (double*)calloc(ncv, sizeof(double));
+      if (variant == 1) {
+        oc_inject(d, Nc, r[l], t);
+      } else {
+        double* q = (double*)calloc(nv, sizeof(double));
+        oc_residual(d, N, mg->A[l], r[l], c[l], q);
+        oc_restrict(d, Nc, q, t);
+        free(q);
+      }
+      oc_jacobi(d, Nc, mg->A[l - 1], t, zc, mg->omega, sc);
+      for (int64_t v = 0; v < ncv; ++v) sc[v] = -sc[v];
+      oc_prolong_add(d, Nc, sc, c[l]);
+      free(t);
+      free(sc);
+      free(zc);
+    }
+    free(zero);
+  }
+  for (int l = 1; l < L; ++l) oc_prolong_add(d, mg->N[l - 1], c[l - 1], c[l]);
+  memcpy(e, c[L - 1], sizeof(double) * ipow(mg->N[L - 1] + 1, d));
+  for (int l = 0; l < L; ++l) {
+    free(r[l]);
+    free(c[l]);
+  }
+}
+
+int oc_additive_once(int d, int N, const double* A_fine, const double* b, double omega, int variant, double* e) {
+  oc_mg mg;
+  memset(&mg, 0, sizeof(mg));
+  mg.d = d;
+  mg.omega = omega;
+  int L = 0, n = N;
+  while (n >= 3) {
+    L++;
+    if (n == 3) break;
+    if (n % 3) return -1;
+    n /= 3;
+  }
+  if (n != 3) return -1;
+  mg.L = L;
+  const int nv = 1 << d;
+  n = N;
+  for (int l = L - 1; l >= 0; --l) {
+    mg.N[l] = n;
+    n /= 3;
+  }
+  mg.A[L - 1] = (double*)A_fine;
+  for (int l = L - 2; l >= 0; --l) {
+    mg.A[l] = (double*)malloc(sizeof(double) * ipow(mg.N[l], d) * nv * nv);
+    oc_galerkin(d, mg.N[l], mg.A[l + 1], mg.A[l]);
+  }
+  coarse_setup(&mg);
+  additive_cycle(&mg, b, e, variant);
   for (int l = L - 2; l >= 0; --l) free(mg.A[l]);
   free(mg.dense);
   free(mg.int_idx);

@@ -566,3 +566,125 @@ def test_paper_format_of_assembled_operators():
     p_lo, _ = oracle.paper_format(2, A, ec, K, 1e-4)
     p_hi, _ = oracle.paper_format(2, A, ec, K, 1e-12)
     assert np.all(p_hi >= p_lo) and p_hi.sum() > p_lo.sum()
+
+
+# ---------------------------------------------------------------- additive cycles (adaFAC-x)
+
+def _dense_levels(dim, n, A_fine):
+    """Element matrices of every level (finest first) from the oracle's Galerkin."""
+    levels = [(n, A_fine)]
+    while levels[-1][0] > 3:
+        nc = levels[-1][0] // 3
+        levels.append((nc, oracle.galerkin(dim, nc, levels[-1][1])))
+    return levels
+
+
+def _inject_dense(dim, nc, rf):
+    """Coarse vertex (I, J[, K]) takes fine vertex (3I, 3J[, 3K]); boundary zero."""
+    nf = 3 * nc
+    out = np.zeros((nc + 1) ** dim)
+    for idx in itertools.product(range(nc + 1), repeat=dim):
+        ci = idx[::-1]
+        if any(c in (0, nc) for c in ci):
+            continue
+        out[dense.vertex_index(dim, nc, ci)] = rf[dense.vertex_index(dim, nf, [3 * c for c in ci])]
+    return out
+
+
+def _additive_dense(dim, n, A_fine, b, omega, variant):
+    """The additive cycle from dense global matrices: per level the Jacobi step
+    omega D^-1 r on the interior, the coarsest solved with numpy, the
+    auxiliary term of adaFAC-PI / adaFAC-Jac, all corrections prolongated."""
+    levels = _dense_levels(dim, n, A_fine)
+    mats = []
+    for (nl, Al) in levels:
+        M = dense.global_matrix(dim, nl, Al)
+        m = dense.interior_mask(dim, nl)
+        mats.append((nl, M, m))
+
+    def smooth(k, r):          # omega D^-1 r on level k (interior only)
+        nl, M, m = mats[k]
+        out = np.zeros_like(r)
+        out[m] = omega * r[m] / np.diag(M)[m]
+        return out
+
+    L = len(levels)
+    rs = [b.copy()]
+    for k in range(1, L):
+        rs.append(oracle.restrict(dim, levels[k][0], rs[-1]))
+    cs = [None] * L
+    nl, M, m = mats[L - 1]
+    cs[L - 1] = np.zeros_like(rs[L - 1])
+    cs[L - 1][m] = np.linalg.solve(M[np.ix_(m, m)], rs[L - 1][m])
+    for k in range(L - 2, -1, -1):
+        nl, M, m = mats[k]
+        c = smooth(k, rs[k])
+        if variant:
+            if variant == oracle.ADAFAC_PI:
+                t = _inject_dense(dim, levels[k + 1][0], rs[k])
+            else:
+                q = np.zeros_like(rs[k])
+                q[m] = rs[k][m] - M[np.ix_(m, m)] @ c[m]
+                t = oracle.restrict(dim, levels[k + 1][0], q)
+            s = smooth(k + 1, t)
+            c = c - oracle.prolong_add(dim, levels[k + 1][0], s, np.zeros_like(c))
+        cs[k] = c
+    e = cs[L - 1]
+    for k in range(L - 2, -1, -1):
+        e = cs[k] + oracle.prolong_add(dim, levels[k + 1][0], e, np.zeros_like(cs[k]))
+    return e
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (2, 27), (3, 9)])
+@pytest.mark.parametrize("variant", [oracle.ADDITIVE, oracle.ADAFAC_PI, oracle.ADAFAC_JAC])
+def test_additive_cycle_matches_dense_formula(dim, n, variant):
+    f = oracle.Field(inputs.boxes_field(dim, 11) if dim == 2 else inputs.fourier_field(3, 4, sigma=1.0))
+    A = oracle.assemble(f, n, 4)
+    b = np.random.default_rng(3).standard_normal((n + 1) ** dim) * dense.interior_mask(dim, n)
+    e = oracle.additive_once(dim, n, A, b, 0.6, variant)
+    ref = _additive_dense(dim, n, A, b, 0.6, variant)
+    assert np.abs(e - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_injection_picks_coinciding_vertices():
+    dim, nc = 2, 3
+    rf = np.arange(10 * 10, dtype=float)
+    bc = oracle.inject(dim, nc, rf)
+    assert bc[dense.vertex_index(dim, nc, [1, 2])] == rf[dense.vertex_index(dim, 9, [3, 6])]
+    assert np.array_equal(bc, _inject_dense(dim, nc, rf))
+
+
+def test_plain_additive_cycle_is_symmetric():
+    dim, n = 2, 27
+    A = oracle.assemble(oracle.Field(inputs.disc_field(2)), n, 4)
+    rng = np.random.default_rng(4)
+    m = dense.interior_mask(dim, n)
+    b1, b2 = rng.standard_normal((2, (n + 1) ** dim)) * m
+    e1 = oracle.additive_once(dim, n, A, b1, 0.6, oracle.ADDITIVE)
+    e2 = oracle.additive_once(dim, n, A, b2, 0.6, oracle.ADDITIVE)
+    assert abs(b2 @ e1 - b1 @ e2) <= 1e-12 * abs(b2 @ e1)
+
+
+def test_adafac_pi_term_vanishes_off_the_coarse_vertices():
+    # two levels and a fine residual that is zero on every vertex the coarse
+    # level shares: the injected auxiliary right-hand side is zero, so
+    # adaFAC-PI = plain additive (the coarsest level has no auxiliary term)
+    dim, n = 2, 9
+    A = oracle.assemble(oracle.Field(inputs.disc_field(2)), n, 4)
+    b = np.random.default_rng(5).standard_normal((n + 1) ** dim) * dense.interior_mask(dim, n)
+    for idx in itertools.product(range(0, n + 1, 3), repeat=dim):
+        b[dense.vertex_index(dim, n, idx[::-1])] = 0.0
+    e_pi = oracle.additive_once(dim, n, A, b, 0.6, oracle.ADAFAC_PI)
+    e_add = oracle.additive_once(dim, n, A, b, 0.6, oracle.ADDITIVE)
+    e_jac = oracle.additive_once(dim, n, A, b, 0.6, oracle.ADAFAC_JAC)
+    assert np.array_equal(e_pi, e_add)
+    assert np.abs(e_jac - e_add).max() > 1e-6 * np.abs(e_add).max()
+
+
+def test_additive_cycle_on_the_coarsest_grid_is_the_exact_solve():
+    dim, n = 2, 3
+    A = oracle.assemble(oracle.Field(inputs.disc_field(2)), n, 4)
+    b = np.random.default_rng(6).standard_normal(16) * dense.interior_mask(dim, n)
+    ref = dense.dense_solve(dim, n, A, b)
+    for v in (0, 1, 2):
+        np.testing.assert_allclose(oracle.additive_once(dim, n, A, b, 0.6, v), ref, atol=1e-13)
