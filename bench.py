@@ -473,6 +473,25 @@ def run_probe(args, local_rank):
         print(json.dumps({"probe": "paper_format", "n_cells": n, "delta": 1e-8, "C": 0.01, "theta": out}),
               flush=True)
         return
+    if args.probe == "cycles":   # the multiplicative V-cycle against the additive cycles of Section adaFAC-x
+        w = inputs.workload(args.workload, args.n)
+        names = {mg.CYCLE_V: "V(2,2)", mg.CYCLE_ADDITIVE: "additive", mg.CYCLE_ADAFAC_PI: "adaFAC-PI",
+                 mg.CYCLE_ADAFAC_JAC: "adaFAC-Jac"}
+        for path, pname in ((mg.PATH_MIXED_DELAYED, "mixed delayed"), (mg.PATH_FP64_PLAIN, "fp64 plain")):
+            sched = tuple(w.s_schedule) if path == mg.PATH_MIXED_DELAYED else (w.s_final,)
+            for outer, oname in ((mg.OUTER_FCG, "fcg"), (mg.OUTER_RICHARDSON, "richardson")):
+                for cyc, cname in names.items():
+                    d = mg.problem_desc(w.dim, w.n_cells, w.eps, path=path, s_schedule=sched, rtol=1e-8,
+                                        max_cycles=args.max_cycles, outer=outer, cycle=cyc)
+                    with mg.Problem(d) as P:
+                        t0 = time.perf_counter()
+                        info = P.solve(check=False)
+                        ms = (time.perf_counter() - t0) * 1e3
+                    print(json.dumps({"probe": "cycles", "workload": args.workload, "n_cells": w.n_cells,
+                                      "path": pname, "outer": oname, "cycle": cname, "status": int(info.status),
+                                      "cycles": int(info.cycles), "ms": ms,
+                                      "rel_residual": float(info.rel_residual)}), flush=True)
+        return
     if args.probe == "paths":   # time-to-solution of the four paths on one workload
         names = {mg.PATH_MIXED_DELAYED: "mixed delayed", mg.PATH_MIXED_PLAIN: "mixed plain",
                  mg.PATH_FP64_DELAYED: "fp64 delayed", mg.PATH_FP64_PLAIN: "fp64 plain"}
@@ -540,10 +559,11 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving", "adaptive",
-                                        "starvation", "paths", "paper_format"],
+                                        "starvation", "paths", "paper_format", "cycles"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)
+    ap.add_argument("--max-cycles", type=int, default=600, help="cycle limit of --probe cycles")
     ap.add_argument("--n", type=int, default=None, help="cells per axis for --probe")
     args = ap.parse_args()
     if args.probe:

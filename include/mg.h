@@ -106,6 +106,21 @@ typedef enum {
   MG_OUTER_RICHARDSON = 1  /* residual correction u += V(f - A u) */
 } mg_outer;
 
+/* Multigrid cycle of one outer iteration (applied to the outer residual). */
+typedef enum {
+  MG_CYCLE_V = 0,           /* multiplicative V(nu_pre, nu_post), damped Jacobi, exact coarsest solve */
+  MG_CYCLE_ADDITIVE = 1,    /* additive: every level smooths (one damped Jacobi step from zero) its
+                               restriction of the fine residual at once, the coarsest is solved
+                               exactly, all corrections are prolongated and summed (Section
+                               "adaFAC-x", the "standard additive scheme" term of Eq. "adaFAC-x") */
+  MG_CYCLE_ADAFAC_PI = 2,   /* additive plus, on every level above the coarsest, minus P of one
+                               damped Jacobi step on the next coarser level of the injected level
+                               residual (adaFAC-PI: P and injection in the auxiliary equation) */
+  MG_CYCLE_ADAFAC_JAC = 3   /* the same with the auxiliary right-hand side R (r_l - A_l c_l): the
+                               level residual left by the level's own Jacobi step, restricted
+                               (adaFAC-Jac: Jacobi-smoothed restriction) */
+} mg_cycle;
+
 typedef struct {
   int32_t dim;             /* 2 or 3 */
   int32_t n_cells;         /* cells per axis, 3^L with L >= 2 (N >= 9: at least one level above the 3^d coarse solve) */
@@ -133,6 +148,8 @@ typedef struct {
                               paper uses 1%); the plain paths then assemble the whole
                               schedule before solving.  0 => every cell reaches the last
                               accuracy of the schedule. */
+  int32_t cycle;           /* mg_cycle: the multigrid cycle each outer iteration applies */
+  int32_t pad1;
 } mg_problem_desc;
 
 typedef struct {

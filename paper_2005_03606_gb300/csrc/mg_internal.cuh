@@ -290,6 +290,7 @@ cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, 
                          void* y, double omega, double* partials, int* nblocks, cudaStream_t st);
 cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
+cudaError_t launch_inject(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st);
 // the two coarsest levels of an FP32 V-cycle in one block (level N = 9 with

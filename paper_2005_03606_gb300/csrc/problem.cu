@@ -330,6 +330,10 @@ mg_status validate(const mg_problem_desc* d) {
       return MG_ERR_INVALID;
     }
   }
+  if (d->cycle < MG_CYCLE_V || d->cycle > MG_CYCLE_ADAFAC_JAC) {
+    set_error("unknown cycle %d", d->cycle);
+    return MG_ERR_INVALID;
+  }
   if (d->path < 0 || d->path > 3) {
     set_error("unknown path %d", d->path);
     return MG_ERR_INVALID;
@@ -591,6 +595,67 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   return cur;
 }
 
+// Additive cycles (Section "adaFAC-x", Eq. "adaFAC-x", in correction form)
+// for A e = lev[0].b from e = 0; returns the correction (lev[0].x0).  The fine
+// residual is restricted to every level; the coarsest is solved exactly and
+// every other level takes one damped Jacobi step from zero on its residual,
+// c_l = omega D_l^-1 r_l.  adaFAC-PI / adaFAC-Jac subtract from c_l the
+// prolongation of one damped Jacobi step on the next coarser level of the
+// auxiliary right-hand side I r_l (injection) / R (r_l - A_l c_l).  The
+// corrections are summed from the coarsest level up.  Levels are processed
+// coarse to fine, so a level's b and x1 are free for the auxiliary step of
+// the level above it.
+void* additive_enqueue(mg_problem* P, mg_status* stt) {
+  const int vec64 = P->mixed ? 0 : 1;
+  const int L = P->L;
+  const int cyc = P->desc.cycle;
+  cudaStream_t st = P->st;
+  const double om = P->desc.omega;
+  cudaError_t e;
+  for (int l = 0; l + 1 < L; ++l)
+    if ((e = launch_restrict(P->dim, P->lev[l + 1].N, vec64, P->lev[l].b, P->lev[l + 1].b, st)) != cudaSuccess)
+      *stt = oom_or_cuda(e, "restrict");
+  Level& lcst = P->lev[L - 1];
+  if ((e = launch_coarse_solve(P->dim, P->Lc, vec64, lcst.b, lcst.x0, st)) != cudaSuccess)
+    *stt = oom_or_cuda(e, "coarse solve");
+  // y = w D^-1 b on a level (one Jacobi step from zero).  Where the level's
+  // sweep has no zero-iterate form (the finest level of the plane-streaming
+  // sweep), a Jacobi step reads a zeroed scratch vector instead; coarser
+  // levels sweep stencils, which always have it.
+  auto jacobi0 = [&](Level& lv, void* b, void* y, double w, void* zero_scratch) {
+    cudaError_t r = launch_sweep(lv.op, SW_JACOBI0, vec64, y, b, y, w, nullptr, nullptr, st);
+    if (r == cudaErrorNotSupported && zero_scratch) {
+      r = cudaMemsetAsync(zero_scratch, 0, P->tv * lv.nvert, st);
+      if (r == cudaSuccess) r = launch_sweep(lv.op, SW_JACOBI, vec64, zero_scratch, b, y, w, nullptr, nullptr, st);
+    }
+    if (r != cudaSuccess) *stt = oom_or_cuda(r, "additive smoothing");
+  };
+  for (int l = L - 2; l >= 0; --l) {
+    Level& lv = P->lev[l];
+    Level& lc = P->lev[l + 1];
+    jacobi0(lv, lv.b, lv.x0, om, lv.x1);
+    if (cyc == MG_CYCLE_ADAFAC_PI || cyc == MG_CYCLE_ADAFAC_JAC) {
+      if (cyc == MG_CYCLE_ADAFAC_PI) {
+        e = launch_inject(P->dim, lc.N, vec64, lv.b, lc.b, st);
+      } else {
+        e = launch_sweep(lv.op, SW_RESID, vec64, lv.x0, lv.b, lv.x1, om, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = launch_restrict(P->dim, lc.N, vec64, lv.x1, lc.b, st);
+      }
+      if (e != cudaSuccess) *stt = oom_or_cuda(e, "auxiliary residual");
+      jacobi0(lc, lc.b, lc.x1, -om, nullptr);   // minus the auxiliary step ...
+      if ((e = launch_prolong_add(P->dim, lc.N, vec64, lc.x1, lv.x0, st)) != cudaSuccess)   // ... prolongated
+        *stt = oom_or_cuda(e, "auxiliary prolongation");
+    }
+    if ((e = launch_prolong_add(P->dim, lc.N, vec64, lc.x0, lv.x0, st)) != cudaSuccess)
+      *stt = oom_or_cuda(e, "prolong");
+  }
+  return P->lev[0].x0;
+}
+
+void* cycle_enqueue(mg_problem* P, mg_status* stt) {
+  return P->desc.cycle == MG_CYCLE_V ? vcycle_enqueue(P, 0, stt) : additive_enqueue(P, stt);
+}
+
 // ------------------------------------------------------------ outer loop
 // r = f - A u (FP64) and rr = r.r.  FP64 paths: the V-cycle reads r and the
 // Krylov direction is reset.  Mixed paths (iterative refinement): the FP32
@@ -637,7 +702,7 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
   const long long n = l0.nvert;
   const int z64 = P->mixed ? 0 : 1;
   mg_status stt = MG_OK;
-  void* z = vcycle_enqueue(P, 0, &stt);
+  void* z = cycle_enqueue(P, &stt);
   if (stt != MG_OK) return stt;
   int nb = 0;
   if (P->mixed) {
@@ -1740,7 +1805,7 @@ mg_status mg_vcycle_apply(mg_problem* P, const double* b, double* e_out) {
     MG_CHECK(cudaMemcpyAsync(l0.b, b, 8 * n, cudaMemcpyHostToDevice, P->st));
   }
   mg_status stt = MG_OK;
-  void* z = vcycle_enqueue(P, 0, &stt);
+  void* z = cycle_enqueue(P, &stt);
   if (stt != MG_OK) return stt;
   if (P->mixed) {
     MG_CHECK(launch_convert(n, 1, z, tmp, P->st));

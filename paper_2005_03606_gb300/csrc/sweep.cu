@@ -1656,6 +1656,24 @@ __global__ void restrict_kernel(int Nc, const TV* __restrict__ rf, TV* __restric
   }
 }
 
+// b_c = I r_f: interior coarse vertices take the fine value at the coinciding
+// vertex (the restriction of adaFAC-PI's auxiliary equation)
+template <int D, typename TV>
+__global__ void inject_kernel(int Nc, const TV* __restrict__ rf, TV* __restrict__ bc) {
+  const int nc1 = Nc + 1, nf1 = 3 * Nc + 1;
+  long long ni = 1;
+  for (int a = 0; a < D; ++a) ni *= (Nc - 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ni;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = 1 + (int)(t % (Nc - 1));
+    const int J = 1 + (int)((t / (Nc - 1)) % (Nc - 1));
+    const int K = D == 3 ? 1 + (int)(t / ((long long)(Nc - 1) * (Nc - 1))) : 0;
+    const long long vc = D == 3 ? ((long long)K * nc1 + J) * nc1 + I : (long long)J * nc1 + I;
+    const long long vf = D == 3 ? ((long long)(3 * K) * nf1 + 3 * J) * nf1 + 3 * I : (long long)(3 * J) * nf1 + 3 * I;
+    bc[vc] = rf[vf];
+  }
+}
+
 // e_f += P e_c (d-linear interpolation on the 3:1 refined grid)
 template <int D, typename TV>
 __global__ void prolong_kernel(int Nc, const TV* __restrict__ ec, TV* __restrict__ ef) {
@@ -2066,6 +2084,20 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
   } else {
     if (vec64) restrict_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
     else restrict_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+  }
+  return launched();
+}
+
+cudaError_t launch_inject(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st) {
+  long long ni = 1;
+  for (int a = 0; a < dim; ++a) ni *= (Nc - 1);
+  const int g = vgrid(ni);
+  if (dim == 2) {
+    if (vec64) inject_kernel<2, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
+    else inject_kernel<2, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+  } else {
+    if (vec64) inject_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
+    else inject_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
   }
   return launched();
 }

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "DI
 
 PATH_FP64_PLAIN, PATH_FP64_DELAYED, PATH_MIXED_DELAYED, PATH_MIXED_PLAIN = 0, 1, 2, 3
 OUTER_FCG, OUTER_RICHARDSON = 0, 1
+CYCLE_V, CYCLE_ADDITIVE, CYCLE_ADAFAC_PI, CYCLE_ADAFAC_JAC = 0, 1, 2, 3
 MAX_MODES, MAX_BOXES = 32, 64
 
 
@@ -42,7 +43,8 @@ class mg_problem_desc(ctypes.Structure):
                 ("s_schedule", ctypes.c_int32 * 8), ("n_s", ctypes.c_int32), ("compress_tau", ctypes.c_double),
                 ("omega", ctypes.c_double), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("chunks", ctypes.c_int32),
-                ("u0", ctypes.POINTER(ctypes.c_double)), ("adapt_C", ctypes.c_double)]
+                ("u0", ctypes.POINTER(ctypes.c_double)), ("adapt_C", ctypes.c_double), ("cycle", ctypes.c_int32),
+                ("pad1", ctypes.c_int32)]
 
 
 class mg_solve_info(ctypes.Structure):
@@ -165,7 +167,8 @@ def eps_desc(field: "_inputs.EpsField") -> mg_eps_desc:
 def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_schedule=(8,),
                  f_const: float = 1.0, outer: int = OUTER_FCG, tau: float = 1e-6, omega: float = 0.6,
                  nu_pre: int = 2, nu_post: int = 2, rtol: float = 1e-8, max_cycles: int = 500,
-                 chunks: int = 0, u0: Optional[np.ndarray] = None, adapt_C: float = 0.0) -> mg_problem_desc:
+                 chunks: int = 0, u0: Optional[np.ndarray] = None, adapt_C: float = 0.0,
+                 cycle: int = 0) -> mg_problem_desc:
     d = mg_problem_desc()
     d.dim, d.n_cells = dim, n_cells
     d.eps = eps_desc(field)
@@ -178,6 +181,7 @@ def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_s
     d.nu_pre, d.nu_post = nu_pre, nu_post
     d.rtol, d.max_cycles, d.chunks = rtol, max_cycles, chunks
     d.adapt_C = adapt_C
+    d.cycle = cycle
     if u0 is not None:
         u0 = np.ascontiguousarray(u0, np.float64)
         d.u0 = u0.ctypes.data_as(_D)
