@@ -492,6 +492,33 @@ def run_probe(args, local_rank):
                                       "cycles": int(info.cycles), "ms": ms,
                                       "rel_residual": float(info.rel_residual)}), flush=True)
         return
+    if args.probe == "coarse":   # compressed coarse-level operators against full FP32 ones
+        w = inputs.workload(args.workload, args.n)
+        rec = {2: (0, 16, 16, 32), 3: (0, 32, 64, 112)}[w.dim]
+        np_ = 6 if w.dim == 2 else 28
+        for tau in (0.0, 1e-6):
+            d = mg.problem_desc(w.dim, w.n_cells, w.eps, path=mg.PATH_MIXED_DELAYED, s_schedule=tuple(w.s_schedule),
+                                rtol=1e-8, max_cycles=3000, coarse_tau=tau)
+            ms = []
+            for _ in range(args.probe_reps):
+                with mg.Problem(d) as P:
+                    t0 = time.perf_counter()
+                    info = P.solve()
+                    ms.append((time.perf_counter() - t0) * 1e3)
+                    levels = []
+                    if tau > 0:
+                        l, nl = 1, w.n_cells // 3
+                        while nl >= 3:
+                            cls = P.coarse_classes(l)
+                            cnt = [int((cls == k).sum()) for k in range(4)]
+                            levels.append({"level": l, "cells": int(cls.size), "cells_by_class": cnt,
+                                           "bytes_full": int(cls.size) * np_ * 4,
+                                           "bytes_stored": int(sum(c * (5 + rec[k]) for k, c in enumerate(cnt)))})
+                            l, nl = l + 1, nl // 3
+            print(json.dumps({"probe": "coarse", "workload": args.workload, "n_cells": w.n_cells, "coarse_tau": tau,
+                              "ms": ms, "cycles": int(info.cycles), "rel_residual": float(info.rel_residual),
+                              "levels": levels}), flush=True)
+        return
     if args.probe == "paths":   # time-to-solution of the four paths on one workload
         names = {mg.PATH_MIXED_DELAYED: "mixed delayed", mg.PATH_MIXED_PLAIN: "mixed plain",
                  mg.PATH_FP64_DELAYED: "fp64 delayed", mg.PATH_FP64_PLAIN: "fp64 plain"}
@@ -559,7 +586,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving", "adaptive",
-                                        "starvation", "paths", "paper_format", "cycles"],
+                                        "starvation", "paths", "paper_format", "cycles", "coarse"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)

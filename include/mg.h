@@ -150,6 +150,13 @@ typedef struct {
                               accuracy of the schedule. */
   int32_t cycle;           /* mg_cycle: the multigrid cycle each outer iteration applies */
   int32_t pad1;
+  double coarse_tau;       /* mixed paths, > 0: every coarse level stores its Galerkin operator
+                              as the hierarchical surplus over its one-sample rediscretisation
+                              eps(x_C) K_ref h_C^(d-2) (eps at the coarse cell centre), with the
+                              finest level's storage classes under this relative bound (Section
+                              "Precision toggling and information density"); the level's
+                              stencils, the next Galerkin product and the coarsest factor use
+                              the stored operator.  0 => coarse operators in full FP32. */
 } mg_problem_desc;
 
 typedef struct {
@@ -257,6 +264,12 @@ typedef struct {
 
 mg_status mg_paper_format(const mg_problem* p, double delta, uint8_t* p3_host, double* decoded_host, size_t n,
                           mg_paper_format_stats* stats);
+
+/* Storage classes (0..3) of the cells of coarse level `level` (1 = the first
+ * coarse level) after the last Galerkin rebuild, when desc->coarse_tau > 0
+ * (host array of n_cells(level)^d bytes).  Errors: MG_ERR_INVALID (level out
+ * of range, n, or coarse compression off). */
+mg_status mg_get_coarse_classes(const mg_problem* p, int level, uint8_t* cls, size_t n);
 
 /* Per-cell storage class (0..3) and cell-centre eps of the finest level; the
  * arrays hold n_cells^d entries; either pointer may be NULL. */

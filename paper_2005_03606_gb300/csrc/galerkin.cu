@@ -305,6 +305,73 @@ int ggrid(long long n, int threads) {
   return (int)b;
 }
 
+// Compressed coarse-level operators (Section "Precision toggling and
+// information density": store only the hierarchical surplus of an operator
+// over its one-sample rediscretisation, with as few bytes as the error bound
+// allows).  In place, cell by cell of a coarse level's FP32 Galerkin store
+// (SoA [NP][ncell]): the surplus over eps_C K_ref h^(d-2) (eps_C the field at
+// the coarse cell centre, FP32) takes the storage class of the finest level's
+// rule with bound tau, is encoded (FP8 e4m3 or FP16 with an FP32 scale, or
+// FP32) and decoded again, so every later use of the level (its stencils, the
+// next Galerkin product, the coarsest factor) sees the stored operator.
+template <int D>
+__global__ void compress_coarse_kernel(long long ncell, float* __restrict__ a, const float* __restrict__ eps_c,
+                                       float hfac, float tau, uint8_t* __restrict__ cls_out,
+                                       unsigned long long* __restrict__ counts) {
+  constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const float ge = eps_c[c] * hfac;
+    float dl[NP], g[NP];
+    float Dm = 0.f, An = 0.f, rs[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rs[v] = 0.f;
+#pragma unroll
+    for (int x = 0; x < NV; ++x)
+#pragma unroll
+      for (int y = x + 1; y < NV; ++y) {
+        const int p = pair_index(NV, x, y);
+        const float av = a[(long long)p * ncell + c];
+        g[p] = ge * (float)kref_off<D>(popc_small(x ^ y));
+        dl[p] = av - g[p];
+        Dm = fmaxf(Dm, fabsf(dl[p]));
+        An = fmaxf(An, fabsf(av));
+        rs[x] += av;
+        rs[y] += av;
+      }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) An = fmaxf(An, fabsf(rs[v]));   // the diagonal is minus the row sum
+    const float Fm = (float)Dim<D>::F;
+    int cls;
+    if (Fm * Dm <= tau * An) cls = 0;
+    else if (Fm * Dm * (16.f / 448.f) <= tau * An) cls = 1;
+    else if (Fm * Dm * (16.f / 65504.f) <= tau * An) cls = 2;
+    else cls = 3;
+    uint8_t rec[Dim<D>::REC_MAX];
+    if (cls == 1) {
+      const float sc = Dm / 448.f;
+      *reinterpret_cast<float*>(rec) = sc;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        __nv_fp8_e4m3 q(dl[p] / sc);
+        rec[4 + p] = q.__x;
+      }
+    } else if (cls == 2) {
+      const float sc = Dm / 65504.f;
+      *reinterpret_cast<float*>(rec) = sc;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) *reinterpret_cast<__half*>(rec + 4 + 2 * p) = __float2half_rn(dl[p] / sc);
+    } else if (cls == 3) {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) *reinterpret_cast<float*>(rec + 4 * p) = dl[p];
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) a[(long long)p * ncell + c] = g[p] + (cls ? decode_entry<D>(rec, cls, p) : 0.f);
+    cls_out[c] = (uint8_t)cls;
+    if (counts) atomicAdd(counts + cls, 1ull);
+  }
+}
+
 }  // namespace
 
 // Galerkin over the coarse cell layers [last0, last1) along the last axis.
@@ -349,6 +416,17 @@ cudaError_t launch_galerkin_range(const LevelOp& fine, int out64, void* coarse_f
 
 cudaError_t launch_galerkin(const LevelOp& fine, int out64, void* coarse_full, cudaStream_t st) {
   return launch_galerkin_range(fine, out64, coarse_full, 0, fine.N / 3, st);
+}
+
+cudaError_t launch_compress_coarse(int dim, long long ncell, float* a, const float* eps_c, double hfac, double tau,
+                                   uint8_t* cls_out, unsigned long long* counts, cudaStream_t st) {
+  if (ncell <= 0) return cudaSuccess;
+  const int g = ggrid(ncell, 128);
+  if (dim == 3)
+    compress_coarse_kernel<3><<<g, 128, 0, st>>>(ncell, a, eps_c, (float)hfac, (float)tau, cls_out, counts);
+  else
+    compress_coarse_kernel<2><<<g, 128, 0, st>>>(ncell, a, eps_c, (float)hfac, (float)tau, cls_out, counts);
+  return launched();
 }
 
 cudaError_t launch_coarse_factor(const LevelOp& coarsest, double* L, cudaStream_t st) {

@@ -340,6 +340,10 @@ cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void*
 cudaError_t launch_decode_matrices(const LevelOp& op, const long long* cells, long long ncells, double* out,
                                    cudaStream_t st);
 
+// galerkin.cu: lossy surplus storage of a coarse level's FP32 Galerkin store, in place
+cudaError_t launch_compress_coarse(int dim, long long ncell, float* a, const float* eps_c, double hfac, double tau,
+                                   uint8_t* cls_out, unsigned long long* counts, cudaStream_t st);
+
 // paper_format.cu: the paper's truncated storage of a level's surplus
 cudaError_t launch_paper_format(int dim, long long ncell, const double* A, const void* eps_c, int eps64,
                                 double hfac, double delta, uint8_t* p3_out, double* At, unsigned long long* hist,

@@ -91,6 +91,8 @@ struct Level {
   void* b = nullptr;              // V-cycle right-hand side (TV)
   void* x0 = nullptr;             // V-cycle iterates (TV)
   void* x1 = nullptr;
+  float* eps_c = nullptr;         // coarse compression: eps at the cell centres (FP32)
+  uint8_t* cls = nullptr;         // coarse compression: storage class per cell
 };
 
 struct Job {
@@ -330,6 +332,11 @@ mg_status validate(const mg_problem_desc* d) {
       return MG_ERR_INVALID;
     }
   }
+  if (!(d->coarse_tau >= 0.0) || !std::isfinite(d->coarse_tau) ||
+      (d->coarse_tau > 0.0 && d->path != MG_PATH_MIXED_DELAYED && d->path != MG_PATH_MIXED_PLAIN)) {
+    set_error("coarse_tau must be finite, >= 0, and 0 on the FP64 paths");
+    return MG_ERR_INVALID;
+  }
   if (d->cycle < MG_CYCLE_V || d->cycle > MG_CYCLE_ADAFAC_JAC) {
     set_error("unknown cycle %d", d->cycle);
     return MG_ERR_INVALID;
@@ -534,8 +541,12 @@ mg_status upload_tables(mg_problem* P) {
 
 mg_status rebuild_coarse(mg_problem* P) {
   for (int l = 0; l + 1 < P->L; ++l) {
-    MG_CHECK(launch_galerkin(P->lev[l].op, P->mixed ? 0 : 1, P->lev[l + 1].full_store, P->st));
-    if (P->lev[l + 1].stencil) MG_CHECK(launch_build_stencil(P->lev[l + 1].op, P->lev[l + 1].stencil, P->st));
+    Level& lc = P->lev[l + 1];
+    MG_CHECK(launch_galerkin(P->lev[l].op, P->mixed ? 0 : 1, lc.full_store, P->st));
+    if (lc.cls)   // stored as a lossy surplus: every later use sees the decoded operator
+      MG_CHECK(launch_compress_coarse(P->dim, lc.ncell, (float*)lc.full_store, lc.eps_c, lc.op.hfac,
+                                      P->desc.coarse_tau, lc.cls, nullptr, P->st));
+    if (lc.stencil) MG_CHECK(launch_build_stencil(lc.op, lc.stencil, P->st));
   }
   MG_CHECK(launch_coarse_factor(P->lev[P->L - 1].op, P->Lc, P->st));
   return MG_OK;
@@ -1063,6 +1074,13 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
       if (!cuda_ok(cudaMemcpyAsync(lv.d_full, &fc, sizeof(fc), cudaMemcpyHostToDevice, P->st), "table upload"))
         return fail(MG_ERR_CUDA);
       op.full = lv.d_full;
+      if (P->mixed && d.coarse_tau > 0.0) {
+        if ((e = dalloc(P, &lv.eps_c, sizeof(float) * lv.ncell)) != cudaSuccess ||
+            (e = dalloc(P, &lv.cls, lv.ncell)) != cudaSuccess)
+          return fail(oom_or_cuda(e, "coarse compression"));
+        if (!cuda_ok(launch_eps_centre(D, lv.N, &P->eps, 0, lv.eps_c, P->st), "coarse eps"))
+          return fail(MG_ERR_CUDA);
+      }
     }
     // assembled vertex stencils for the levels swept with full storage (not the
     // coarsest, which is solved directly, nor the compressed finest level)
@@ -1664,6 +1682,16 @@ mg_status mg_paper_format(const mg_problem* Pc, double delta, uint8_t* p3_host, 
     memcpy(&em, &h[9], sizeof(em));
     stats->max_abs_error = em;
   }
+  return MG_OK;
+}
+
+mg_status mg_get_coarse_classes(const mg_problem* P, int level, uint8_t* cls, size_t n) {
+  if (!P || !cls || level < 1 || level >= P->L || n != (size_t)P->lev[level].ncell || !P->lev[level].cls) {
+    set_error("bad arguments (level >= 1, n cells of the level, coarse compression on)");
+    return MG_ERR_INVALID;
+  }
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  MG_CHECK(cudaMemcpy(cls, P->lev[level].cls, n, cudaMemcpyDeviceToHost));
   return MG_OK;
 }
 

@@ -44,7 +44,7 @@ class mg_problem_desc(ctypes.Structure):
                 ("omega", ctypes.c_double), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("chunks", ctypes.c_int32),
                 ("u0", ctypes.POINTER(ctypes.c_double)), ("adapt_C", ctypes.c_double), ("cycle", ctypes.c_int32),
-                ("pad1", ctypes.c_int32)]
+                ("pad1", ctypes.c_int32), ("coarse_tau", ctypes.c_double)]
 
 
 class mg_solve_info(ctypes.Structure):
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_get_element_matrices": (st, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
             "mg_get_cell_data": (st, [_VP, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t]),
             "mg_get_cell_accuracy": (st, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_size_t]),
+            "mg_get_coarse_classes": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), ctypes.c_size_t]),
             "mg_get_trace": (st, [_VP, ctypes.POINTER(mg_trace_entry), ctypes.c_size_t,
                                   ctypes.POINTER(ctypes.c_size_t)]),
             "mg_paper_format": (st, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t,
@@ -168,7 +169,7 @@ def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_s
                  f_const: float = 1.0, outer: int = OUTER_FCG, tau: float = 1e-6, omega: float = 0.6,
                  nu_pre: int = 2, nu_post: int = 2, rtol: float = 1e-8, max_cycles: int = 500,
                  chunks: int = 0, u0: Optional[np.ndarray] = None, adapt_C: float = 0.0,
-                 cycle: int = 0) -> mg_problem_desc:
+                 cycle: int = 0, coarse_tau: float = 0.0) -> mg_problem_desc:
     d = mg_problem_desc()
     d.dim, d.n_cells = dim, n_cells
     d.eps = eps_desc(field)
@@ -182,6 +183,7 @@ def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_s
     d.rtol, d.max_cycles, d.chunks = rtol, max_cycles, chunks
     d.adapt_C = adapt_C
     d.cycle = cycle
+    d.coarse_tau = coarse_tau
     if u0 is not None:
         u0 = np.ascontiguousarray(u0, np.float64)
         d.u0 = u0.ctypes.data_as(_D)
@@ -293,6 +295,12 @@ class Problem:
         stats = {"cells_by_p3": list(st.cells_by_p3), "bytes_full": st.bytes_full, "bytes_paper": st.bytes_paper,
                  "compression": st.compression, "max_abs_error": st.max_abs_error}
         return p3, At, stats
+
+    def coarse_classes(self, level: int) -> np.ndarray:
+        n = self.level_cells(level)
+        cls = np.zeros(n, np.uint8)
+        _check(load().mg_get_coarse_classes(self.h, level, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n))
+        return cls
 
     def cell_accuracy(self) -> np.ndarray:
         n = self.level_cells(0)
