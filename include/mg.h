@@ -271,6 +271,25 @@ mg_status mg_paper_format(const mg_problem* p, double delta, uint8_t* p3_host, d
  * of range, n, or coarse compression off). */
 mg_status mg_get_coarse_classes(const mg_problem* p, int level, uint8_t* cls, size_t n);
 
+/* Checkpoint of a problem's state (not in the paper; for resuming a solve in
+ * another process or after a restart).  The state holds the solution u, the
+ * finest level's stored operator chunk by chunk with each chunk's accuracy s
+ * (FP64 matrices, or the class bytes, segment bases and class pools of the
+ * mixed paths, byte for byte) and, with adaptive accuracy, every cell's final
+ * flag and accuracy; coarse operators are rebuilt on import.  A pending FP32
+ * correction of the mixed paths is folded into u first.
+ * mg_export_state: host_buf NULL => *size receives the bytes needed; else
+ *   cap must be at least that and the state is written to host_buf.
+ * mg_import_state: p must come from a descriptor with the same dim, n_cells,
+ *   path and chunking; replaces its stored operator and u (the problem then
+ *   restarts its outer iteration from the imported u).
+ * Both wait for the problem's stream and fail with MG_ERR_PENDING while
+ * delayed assembly jobs are in flight.  Errors: MG_ERR_INVALID (arguments,
+ * cap, a buffer that is not a state of a compatible problem or is truncated),
+ * MG_ERR_PENDING, MG_ERR_OOM, MG_ERR_CUDA. */
+mg_status mg_export_state(mg_problem* p, void* host_buf, size_t cap, size_t* size);
+mg_status mg_import_state(mg_problem* p, const void* host_buf, size_t size);
+
 /* Per-cell storage class (0..3) and cell-centre eps of the finest level; the
  * arrays hold n_cells^d entries; either pointer may be NULL. */
 mg_status mg_get_cell_data(const mg_problem* p, uint8_t* cls, double* eps_c, size_t n);

@@ -1685,6 +1685,207 @@ mg_status mg_paper_format(const mg_problem* Pc, double delta, uint8_t* p3_host, 
   return MG_OK;
 }
 
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t dim, n_cells, mixed, nchunk;
+  int64_t chunk_cells, chunk_nseg, nvert;
+  int32_t adapt, np;
+};
+constexpr char kStateMagic[8] = {'M', 'G', 'S', 'T', 'A', 'T', 'E', '1'};
+
+struct ChunkHeader {
+  int32_t s;
+  uint32_t totals[3];
+};
+
+// record bytes of classes 1..3 in the class pools
+int pool_rec_bytes(int dim, int k) {
+  static const int r3[3] = {32, 64, 112}, r2[3] = {16, 16, 32};
+  return dim == 3 ? r3[k] : r2[k];
+}
+
+size_t chunk_state_bytes(const mg_problem* P, const uint32_t totals[3]) {
+  const int NP = P->dim == 3 ? 28 : 6;
+  if (!P->mixed) return sizeof(double) * NP * (size_t)P->chunk_cells;
+  size_t b = (size_t)P->chunk_nseg * kSegCells + sizeof(uint32_t) * 3 * (size_t)P->chunk_nseg;
+  for (int k = 0; k < 3; ++k) b += (size_t)totals[k] * pool_rec_bytes(P->dim, k);
+  return b;
+}
+
+bool jobs_pending(mg_problem* P) {
+  std::lock_guard<std::mutex> lk(P->mu);
+  return P->in_flight > 0 || !P->held.empty();
+}
+}  // namespace
+
+mg_status mg_export_state(mg_problem* P, void* buf, size_t cap, size_t* size) {
+  if (!P || !size) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  if (jobs_pending(P)) {
+    set_error("delayed assembly jobs are in flight");
+    return MG_ERR_PENDING;
+  }
+  mg_status s = apply_inner_correction(P);
+  if (s != MG_OK) return s;
+  const Level& l0 = P->lev[0];
+  size_t total = sizeof(StateHeader) + sizeof(double) * (size_t)l0.nvert;
+  for (const ChunkStore& c : P->cur) total += sizeof(ChunkHeader) + chunk_state_bytes(P, c.totals);
+  if (P->adapt) total += 2 * (size_t)P->chunk_cells * P->nchunk;
+  *size = total;
+  if (!buf) return MG_OK;
+  if (cap < total) {
+    set_error("buffer of %zu bytes, the state needs %zu", cap, total);
+    return MG_ERR_INVALID;
+  }
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  uint8_t* w = static_cast<uint8_t*>(buf);
+  StateHeader h{};
+  memcpy(h.magic, kStateMagic, 8);
+  h.dim = P->dim;
+  h.n_cells = P->N;
+  h.mixed = P->mixed ? 1 : 0;
+  h.nchunk = P->nchunk;
+  h.chunk_cells = P->chunk_cells;
+  h.chunk_nseg = P->chunk_nseg;
+  h.nvert = l0.nvert;
+  h.adapt = P->adapt ? 1 : 0;
+  h.np = P->dim == 3 ? 28 : 6;
+  memcpy(w, &h, sizeof(h));
+  w += sizeof(h);
+  MG_CHECK(cudaMemcpy(w, P->u, sizeof(double) * (size_t)l0.nvert, cudaMemcpyDeviceToHost));
+  w += sizeof(double) * (size_t)l0.nvert;
+  for (const ChunkStore& c : P->cur) {
+    ChunkHeader ch{};
+    ch.s = c.s;
+    for (int k = 0; k < 3; ++k) ch.totals[k] = c.totals[k];
+    memcpy(w, &ch, sizeof(ch));
+    w += sizeof(ch);
+    if (!P->mixed) {
+      const size_t b = chunk_state_bytes(P, c.totals);
+      MG_CHECK(cudaMemcpy(w, c.a64, b, cudaMemcpyDeviceToHost));
+      w += b;
+      continue;
+    }
+    const size_t cb = (size_t)P->chunk_nseg * kSegCells, sb = sizeof(uint32_t) * 3 * (size_t)P->chunk_nseg;
+    MG_CHECK(cudaMemcpy(w, c.cls, cb, cudaMemcpyDeviceToHost));
+    w += cb;
+    MG_CHECK(cudaMemcpy(w, c.seg_base, sb, cudaMemcpyDeviceToHost));
+    w += sb;
+    for (int k = 0; k < 3; ++k) {
+      const size_t pb = (size_t)c.totals[k] * pool_rec_bytes(P->dim, k);
+      if (pb) MG_CHECK(cudaMemcpy(w, c.pool[k], pb, cudaMemcpyDeviceToHost));
+      w += pb;
+    }
+  }
+  if (P->adapt) {
+    const size_t nc = (size_t)P->chunk_cells * P->nchunk;
+    MG_CHECK(cudaMemcpy(w, P->final_flags, nc, cudaMemcpyDeviceToHost));
+    w += nc;
+    MG_CHECK(cudaMemcpy(w, P->s_cell, nc, cudaMemcpyDeviceToHost));
+  }
+  return MG_OK;
+}
+
+mg_status mg_import_state(mg_problem* P, const void* buf, size_t size) {
+  if (!P || !buf || size < sizeof(StateHeader)) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  if (jobs_pending(P)) {
+    set_error("delayed assembly jobs are in flight");
+    return MG_ERR_PENDING;
+  }
+  const uint8_t* r = static_cast<const uint8_t*>(buf);
+  const uint8_t* end = r + size;
+  StateHeader h;
+  memcpy(&h, r, sizeof(h));
+  r += sizeof(h);
+  const Level& l0 = P->lev[0];
+  if (memcmp(h.magic, kStateMagic, 8) != 0 || h.dim != P->dim || h.n_cells != P->N ||
+      h.mixed != (P->mixed ? 1 : 0) || h.nchunk != P->nchunk || h.chunk_cells != P->chunk_cells ||
+      h.chunk_nseg != P->chunk_nseg || h.nvert != l0.nvert || h.adapt != (P->adapt ? 1 : 0)) {
+    set_error("not a state of a problem with this descriptor");
+    return MG_ERR_INVALID;
+  }
+  // validate the whole layout before changing anything
+  const uint8_t* q = r + sizeof(double) * (size_t)l0.nvert;
+  std::vector<ChunkHeader> chs(P->nchunk);
+  for (int c = 0; c < P->nchunk; ++c) {
+    if (q + sizeof(ChunkHeader) > end) {
+      set_error("truncated state");
+      return MG_ERR_INVALID;
+    }
+    memcpy(&chs[c], q, sizeof(ChunkHeader));
+    if (chs[c].s < 1 || chs[c].s > 64 ||
+        (uint64_t)chs[c].totals[0] + chs[c].totals[1] + chs[c].totals[2] > (uint64_t)P->chunk_cells) {
+      set_error("corrupt chunk header");
+      return MG_ERR_INVALID;
+    }
+    q += sizeof(ChunkHeader) + chunk_state_bytes(P, chs[c].totals);
+  }
+  if (P->adapt) q += 2 * (size_t)P->chunk_cells * P->nchunk;
+  if (q != end) {
+    set_error("state size %zu does not match its contents", size);
+    return MG_ERR_INVALID;
+  }
+  cudaStream_t st = P->st;
+  MG_CHECK(cudaMemcpyAsync(P->u, r, sizeof(double) * (size_t)l0.nvert, cudaMemcpyHostToDevice, st));
+  r += sizeof(double) * (size_t)l0.nvert;
+  for (int c = 0; c < P->nchunk; ++c) {
+    r += sizeof(ChunkHeader);
+    ChunkStore cs;
+    cs.s = chs[c].s;
+    for (int k = 0; k < 3; ++k) cs.totals[k] = chs[c].totals[k];
+    cudaError_t e;
+    if (!P->mixed) {
+      const size_t b = chunk_state_bytes(P, cs.totals);
+      if ((e = mg_malloc_async(&cs.a64, b, st)) != cudaSuccess) return oom_or_cuda(e, "chunk storage");
+      MG_CHECK(cudaMemcpyAsync(cs.a64, r, b, cudaMemcpyHostToDevice, st));
+      cs.bytes = b;
+      r += b;
+    } else {
+      const size_t cb = (size_t)P->chunk_nseg * kSegCells, sb = sizeof(uint32_t) * 3 * (size_t)P->chunk_nseg;
+      e = mg_malloc_async(&cs.cls, cb, st);
+      if (e == cudaSuccess) e = mg_malloc_async(&cs.seg_base, sb, st);
+      if (e != cudaSuccess) return oom_or_cuda(e, "chunk classes");
+      MG_CHECK(cudaMemcpyAsync(cs.cls, r, cb, cudaMemcpyHostToDevice, st));
+      r += cb;
+      MG_CHECK(cudaMemcpyAsync(cs.seg_base, r, sb, cudaMemcpyHostToDevice, st));
+      r += sb;
+      cs.bytes = cb + sb;
+      for (int k = 0; k < 3; ++k) {
+        const size_t pb = (size_t)cs.totals[k] * pool_rec_bytes(P->dim, k);
+        if (pb) {
+          if ((e = mg_malloc_async(&cs.pool[k], pb, st)) != cudaSuccess) return oom_or_cuda(e, "payload pool");
+          MG_CHECK(cudaMemcpyAsync(cs.pool[k], r, pb, cudaMemcpyHostToDevice, st));
+        }
+        cs.bytes += pb;
+        r += pb;
+      }
+    }
+    // the copies read pageable host memory: they are staged before the call returns
+    install(P, c, cs);
+  }
+  if (P->adapt) {
+    const size_t nc = (size_t)P->chunk_cells * P->nchunk;
+    MG_CHECK(cudaMemcpyAsync(P->final_flags, r, nc, cudaMemcpyHostToDevice, st));
+    r += nc;
+    MG_CHECK(cudaMemcpyAsync(P->s_cell, r, nc, cudaMemcpyHostToDevice, st));
+    P->wlast = P->cur;
+  }
+  mg_status s = upload_tables(P);
+  if (s == MG_OK) s = rebuild_coarse(P);
+  if (s != MG_OK) return s;
+  MG_CHECK(cudaStreamSynchronize(st));
+  P->have_correction = false;
+  P->need_restart = true;
+  P->keep_dir = false;
+  return MG_OK;
+}
+
 mg_status mg_get_coarse_classes(const mg_problem* P, int level, uint8_t* cls, size_t n) {
   if (!P || !cls || level < 1 || level >= P->L || n != (size_t)P->lev[level].ncell || !P->lev[level].cls) {
     set_error("bad arguments (level >= 1, n cells of the level, coarse compression on)");

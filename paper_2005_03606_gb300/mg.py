@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_get_element_matrices": (st, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
             "mg_get_cell_data": (st, [_VP, ctypes.POINTER(ctypes.c_uint8), _D, ctypes.c_size_t]),
             "mg_get_cell_accuracy": (st, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_size_t]),
+            "mg_export_state": (st, [_VP, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+            "mg_import_state": (st, [_VP, ctypes.c_void_p, ctypes.c_size_t]),
             "mg_get_coarse_classes": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), ctypes.c_size_t]),
             "mg_get_trace": (st, [_VP, ctypes.POINTER(mg_trace_entry), ctypes.c_size_t,
                                   ctypes.POINTER(ctypes.c_size_t)]),
@@ -295,6 +297,18 @@ class Problem:
         stats = {"cells_by_p3": list(st.cells_by_p3), "bytes_full": st.bytes_full, "bytes_paper": st.bytes_paper,
                  "compression": st.compression, "max_abs_error": st.max_abs_error}
         return p3, At, stats
+
+    def export_state(self) -> bytes:
+        """Checkpoint of the problem's state (solution, stored operator, accuracies)."""
+        n = ctypes.c_size_t(0)
+        _check(load().mg_export_state(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(load().mg_export_state(self.h, buf, n.value, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def import_state(self, state: bytes) -> None:
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check(load().mg_import_state(self.h, buf, len(state)))
 
     def coarse_classes(self, level: int) -> np.ndarray:
         n = self.level_cells(level)
