@@ -1050,7 +1050,15 @@ __global__ void touched_stencil_kernel(const LevelOp op) {
   }
 }
 
-constexpr int kFixBlocks = 152 * 2;
+#ifndef MG_J0_BLOCKS_PER_SM
+#define MG_J0_BLOCKS_PER_SM 5
+#endif
+#ifndef MG_FIX_BLOCKS_PER_SM
+#define MG_FIX_BLOCKS_PER_SM 3
+#endif
+// fix-up grids: the FP32 pass holds three 256-thread blocks per SM at its
+// register count (the FP64 one two; its surplus blocks wait for a slot)
+constexpr int kFixBlocks = 152 * MG_FIX_BLOCKS_PER_SM;
 
 // ---------------------------------------------------------------- 3D FP64 split residual / matvec
 // The outer FP64 iteration of the mixed paths needs r = f - A u and A p on the
@@ -1529,7 +1537,9 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   const dim3 blk(kGeoBX, kGeoBY, 1);
   double* pfix = partials ? partials + 2 * (size_t)nb_bulk : nullptr;
   if (mode == SW_JACOBI0) {
-    sweep3_jacobi0<<<nb_bulk, blk, 0, st>>>(op, b, y, omega, ntx, nty);
+    // a streaming pass at 48 registers: five resident blocks per SM instead of the bulk pass's two
+    const int nb0 = ntiles < MG_J0_BLOCKS_PER_SM * nsm ? (int)ntiles : MG_J0_BLOCKS_PER_SM * nsm;
+    sweep3_jacobi0<<<nb0, blk, 0, st>>>(op, b, y, omega, ntx, nty);
     count_launches(1);
     launch_fixup<SW_JACOBI0>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_JACOBI) {
