@@ -870,7 +870,7 @@ mg_status enqueue_async(mg_problem* P, int s) {
 
 // Publishes every completed job (at a cycle boundary).  wait = 1 blocks for
 // at least one job when any is in flight.  Returns the number published.
-constexpr int kHoldCycles = 8;
+constexpr int kHoldCycles = 16;
 
 mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
   *npub = 0;
@@ -912,26 +912,15 @@ mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
   }
   if (P->held.empty()) return bad;
   // Every publication costs a Galerkin rebuild, a new FP64 residual and a
-  // restart of the Krylov iteration, so finished chunks are held back until a
-  // whole accuracy level is complete, the schedule is done, the solver waits,
-  // or kHoldCycles cycles have passed since the first one finished.
+  // restart of the Krylov iteration, so finished chunks are held back until
+  // the schedule is done, the solver waits, or kHoldCycles cycles have passed
+  // since the first one finished.  (Publishing each accuracy level as soon as
+  // it is complete restarted the iteration once per level when the levels
+  // finish a cycle apart, and made the cycle count depend on that timing.)
   bool now = wait || P->cycles - P->held_since >= kHoldCycles;
   if (!now) {
     std::lock_guard<std::mutex> lk(P->mu);
     now = P->todo.empty() && P->in_flight == 0;
-  }
-  if (!now) {
-    std::vector<int> best(P->nchunk, 0);
-    for (int c = 0; c < P->nchunk; ++c) best[c] = P->cur[c].s;
-    for (const Job& j : P->held) best[j.chunk] = std::max(best[j.chunk], j.store.s);
-    for (const Job& j : P->held) {
-      bool level_done = true;
-      for (int c = 0; c < P->nchunk && level_done; ++c) level_done = best[c] >= j.store.s;
-      if (level_done) {
-        now = true;
-        break;
-      }
-    }
   }
   if (!now) return bad;
   for (Job& j : P->held) {
