@@ -702,7 +702,7 @@ mg_status apply_inner_correction(mg_problem* P, bool reliable = false) {
   MG_CHECK(launch_apply_correction(P->lev[0].nvert, P->u, P->e32, P->sc, P->st));
   P->have_correction = false;
   P->need_restart = true;
-  P->keep_dir = reliable && P->desc.outer == MG_OUTER_FCG && !getenv("MG_RESTART_KRYLOV");
+  P->keep_dir = reliable && P->desc.outer == MG_OUTER_FCG;
   return MG_OK;
 }
 
@@ -1017,7 +1017,6 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   if (cudaGetDevice(&P->device) != cudaSuccess) P->device = 0;
   if (const char* ng = getenv("MG_NO_GRAPHS")) P->use_graphs = ng[0] == '0';
   P->trace = getenv("MG_TRACE") != nullptr;
-  if (const char* em = getenv("MG_INNER_ETA")) P->eta_min = atof(em) > 0 ? atof(em) : P->eta_min;
   auto fail = [&](mg_status s) {
     mg_destroy_problem(P);
     return s;

@@ -595,3 +595,21 @@ def test_largest_2d_grid_residual_checked_on_the_host():
     r = (f - oracle.apply(2, n, stored, u)) * m
     # the GPU solves its own stored operator (within 1e-5 of the oracle's per cell)
     assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(f * m)
+
+
+@pytest.mark.parametrize("switch", ["MG_NO_VTAIL", "MG_NO_GRAPHS"])
+def test_alternative_cycle_implementations_agree(switch, monkeypatch):
+    # the one-block tail of the V-cycle (levels 9 and 3) and the CUDA-graph
+    # replay of an iteration are implementation choices: switching either off
+    # must give the same solve
+    w = inputs.workload("boxes3d", 27)
+    d = mg.problem_desc(3, 27, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,), rtol=1e-8)
+    with mg.Problem(d) as P:
+        i0 = P.solve()
+        u0 = P.solution()
+    monkeypatch.setenv(switch, "1")
+    with mg.Problem(d) as P:
+        i1 = P.solve()
+        u1 = P.solution()
+    assert i1.status == mg.MG_OK and abs(i1.cycles - i0.cycles) <= 1
+    assert np.abs(u1 - u0).max() <= 1e-6 * np.abs(u0).max()
