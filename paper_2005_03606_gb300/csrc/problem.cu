@@ -134,6 +134,7 @@ struct mg_problem {
   int* ilist = nullptr;           // [nchunk][chunk_cells] local cell indices
   std::vector<int> ilist_n;       // count per chunk (host)
   std::vector<mg_trace_entry> trace_log;   // per outer iteration of the last solve
+  bool resid_fresh = false;       // rr is the true FP64 residual of the current u and operator
   // adaptive accuracy (desc.adapt_C > 0)
   bool adapt = false;
   uint8_t* final_flags = nullptr; // [nchunk][chunk_cells]: 1 once the cell stopped refining
@@ -693,6 +694,7 @@ mg_status outer_restart(mg_problem* P) {
   P->first = !(P->mixed && P->keep_dir);
   P->keep_dir = false;
   P->need_restart = false;
+  P->resid_fresh = true;
   return MG_OK;
 }
 
@@ -701,6 +703,7 @@ mg_status apply_inner_correction(mg_problem* P, bool reliable = false) {
   if (!P->mixed || !P->have_correction) return MG_OK;
   MG_CHECK(launch_apply_correction(P->lev[0].nvert, P->u, P->e32, P->sc, P->st));
   P->have_correction = false;
+  P->resid_fresh = false;
   P->need_restart = true;
   P->keep_dir = reliable && P->desc.outer == MG_OUTER_FCG;
   return MG_OK;
@@ -763,6 +766,7 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
 
 mg_status outer_iteration(mg_problem* P) {
   const int first = P->first ? 1 : 0;
+  if (!P->mixed) P->resid_fresh = false;   // the FP64 iteration updates u and a recurrence residual
   if (P->use_graphs) {
     if (!P->g_iter[first]) {
       cudaGraph_t g;
@@ -939,6 +943,7 @@ mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
     if (s != MG_OK) return s;
     P->publishes += *npub;
     P->need_restart = true;
+    P->resid_fresh = false;
     P->keep_dir = false;
   }
   return bad;
@@ -1312,6 +1317,7 @@ mg_status mg_assemble_level(mg_problem* P, int s, int async) {
   mg_status st = upload_tables(P);
   if (st == MG_OK) st = rebuild_coarse(P);
   P->need_restart = true;
+  P->resid_fresh = false;
   return st;
 }
 
@@ -1494,9 +1500,13 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       break;
     }
   }
-  // verify with the true residual
+  // verify with the true residual (already at hand when the last restart
+  // computed it for the current u and operator)
   double rel = 0.0;
-  {
+  if (P->resid_fresh && !P->have_correction) {
+    rel = std::sqrt(P->rr / (P->ff > 0 ? P->ff : 1.0));
+    P->need_restart = true;
+  } else {
     mg_status s = apply_inner_correction(P);
     if (s != MG_OK) return s;
     Level& l0 = P->lev[0];
@@ -1871,6 +1881,7 @@ mg_status mg_import_state(mg_problem* P, const void* buf, size_t size) {
   P->have_correction = false;
   P->need_restart = true;
   P->keep_dir = false;
+  P->resid_fresh = false;
   return MG_OK;
 }
 
