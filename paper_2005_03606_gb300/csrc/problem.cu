@@ -135,6 +135,7 @@ struct mg_problem {
   std::vector<int> ilist_n;       // count per chunk (host)
   std::vector<mg_trace_entry> trace_log;   // per outer iteration of the last solve
   bool resid_fresh = false;       // rr is the true FP64 residual of the current u and operator
+  bool u_zero = true;             // u is still the zero initial guess
   // adaptive accuracy (desc.adapt_C > 0)
   bool adapt = false;
   uint8_t* final_flags = nullptr; // [nchunk][chunk_cells]: 1 once the cell stopped refining
@@ -676,9 +677,14 @@ mg_status outer_restart(mg_problem* P) {
   cudaStream_t st = P->st;
   Level& l0 = P->lev[0];
   int nb = 0;
-  MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->r, 0.0, nullptr, nullptr, st));
-  MG_CHECK(launch_dot(P->r, P->r, l0.nvert, P->partials, &nb, st));
-  MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
+  if (P->u_zero) {   // r = f - A 0 = f, and r.r = f.f (computed at creation)
+    MG_CHECK(cudaMemcpyAsync(P->r, P->f, sizeof(double) * l0.nvert, cudaMemcpyDeviceToDevice, st));
+    MG_CHECK(cudaMemcpyAsync(&P->sc->rr, &P->sc->ff, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    MG_CHECK(launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->r, 0.0, nullptr, nullptr, st));
+    MG_CHECK(launch_dot(P->r, P->r, l0.nvert, P->partials, &nb, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
+  }
   if (P->mixed) {
     MG_CHECK(launch_scale_residual(l0.nvert, P->r, (float*)l0.b, P->sc, st));
     MG_CHECK(cudaMemsetAsync(P->e32, 0, sizeof(float) * l0.nvert, st));
@@ -704,6 +710,7 @@ mg_status apply_inner_correction(mg_problem* P, bool reliable = false) {
   MG_CHECK(launch_apply_correction(P->lev[0].nvert, P->u, P->e32, P->sc, P->st));
   P->have_correction = false;
   P->resid_fresh = false;
+  P->u_zero = false;
   P->need_restart = true;
   P->keep_dir = reliable && P->desc.outer == MG_OUTER_FCG;
   return MG_OK;
@@ -766,7 +773,10 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
 
 mg_status outer_iteration(mg_problem* P) {
   const int first = P->first ? 1 : 0;
-  if (!P->mixed) P->resid_fresh = false;   // the FP64 iteration updates u and a recurrence residual
+  if (!P->mixed) {   // the FP64 iteration updates u and a recurrence residual
+    P->resid_fresh = false;
+    P->u_zero = false;
+  }
   if (P->use_graphs) {
     if (!P->g_iter[first]) {
       cudaGraph_t g;
@@ -1203,6 +1213,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   for (int a = 0; a < D; ++a) hd /= P->N;
   if (!cuda_ok(launch_load_vector(D, P->N, d.f_const * hd, P->f, P->st), "load vector")) return fail(MG_ERR_CUDA);
   if (d.u0) {
+    P->u_zero = false;
     if (!cuda_ok(cudaMemcpyAsync(P->u, d.u0, v8, cudaMemcpyHostToDevice, P->st), "u0 upload") ||
         !cuda_ok(cudaStreamSynchronize(P->st), "u0 sync"))
       return fail(MG_ERR_CUDA);
@@ -1882,6 +1893,7 @@ mg_status mg_import_state(mg_problem* P, const void* buf, size_t size) {
   P->need_restart = true;
   P->keep_dir = false;
   P->resid_fresh = false;
+  P->u_zero = false;
   return MG_OK;
 }
 
