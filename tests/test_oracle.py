@@ -5,6 +5,7 @@ forms, exact rational integration, invariants, library routines, a dense
 direct solve and an analytic PDE solution.
 """
 import itertools
+import os
 import math
 from fractions import Fraction
 
@@ -688,3 +689,44 @@ def test_additive_cycle_on_the_coarsest_grid_is_the_exact_solve():
     ref = dense.dense_solve(dim, n, A, b)
     for v in (0, 1, 2):
         np.testing.assert_allclose(oracle.additive_once(dim, n, A, b, 0.6, v), ref, atol=1e-13)
+
+
+# ---------------------------------------------------------------- golden fixtures
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+@pytest.mark.parametrize("dim,name", [(2, "stencil_2d_const.txt"), (3, "stencil_3d_const.txt")])
+def test_assembled_stencil_matches_golden_classic_stencil(dim, name):
+    vals = [float(Fraction(v)) for row in _golden_rows(name) for v in row]
+    assert len(vals) == 3 ** dim
+    n = 9
+    h = 1.0 / n
+    A = oracle.assemble(oracle.Field(inputs.const_field(dim, 1.0)), n, 3)
+    M = dense.global_matrix(dim, n, A)
+    v = dense.vertex_index(dim, n, [4] * dim)
+    for q, off in enumerate(itertools.product([-1, 0, 1], repeat=dim)):
+        off = off[::-1]   # the fixture runs x fastest
+        w = dense.vertex_index(dim, n, [4 + o for o in off])
+        assert abs(M[v, w] - vals[q] * h ** (dim - 2)) < 1e-14
+
+
+def test_memory_footprint_first_cycle_matches_golden():
+    n = 27
+    K = oracle.kref(2, n)
+    for theta, max_n, avg_n, comp in _golden_rows("memory_footprint_cycle1.txt"):
+        f = oracle.Field(inputs.theta_field(2, float(theta)))
+        A1 = oracle.assemble(f, n, 1)        # every cell at its one-sample matrix
+        ec = np.array([oracle.eps_at(f, ((i + 0.5) / n, (j + 0.5) / n)) for j in range(n) for i in range(n)])
+        p3, _ = oracle.paper_format(2, A1, ec, K, 1e-8)
+        _, s_cell = oracle.assemble_adaptive(f, n, (1,), 0.01)
+        assert s_cell.max() == int(max_n) and round(float(s_cell.mean()), 2) == float(avg_n)
+        assert round(oracle.paper_compression(2, p3), 2) == float(comp)
