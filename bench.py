@@ -309,6 +309,12 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = rep.aggregate(len(e2e_ms), max_over_ranks(sum(e2e_ms)))
+    # the mixed path's solution under the FP64 operator of the final accuracy:
+    # how far the lossy FP32 surplus storage moves the answer
+    with mg.Problem(mg.problem_desc(w.dim, n, w.eps, path=mg.PATH_FP64_PLAIN, s_schedule=(w.s_final,),
+                                    u0=u_host)) as P:
+        P.assemble(w.s_final)
+        rel_fp64_op = P.vcycle(0)
     serving = serving_leg(mg, args.serving_requests) if args.serving_requests > 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -330,6 +336,7 @@ def run_ours(args, rank, world, local_rank):
                    "flush": "working set > L2 (no flush)"},
         "p50_ms": p50, "p99_ms": p99,
         "cycles": int(info0.cycles), "publishes": int(info0.publishes), "rel_residual": info0.rel_residual,
+        "rel_residual_fp64_operator": rel_fp64_op,
         "cells_by_class": cbc, "stencil_bytes": int(info0.payload_bytes),
         "fp64_plain": {"solves_per_s": 1e3 / statistics.median(fp64_ms), "ms": fp64_ms, "cycles": fp64_cycles},
         "speedup_vs_fp64_plain": statistics.median(fp64_ms) / p50,
@@ -348,11 +355,11 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def serving_leg(mg, n_requests, seed=2004, load_factor=0.7, max_active=8):
+def serving_leg(mg, n_requests, seed=2004, load_factors=(0.7,), max_active=8):
     """The request loop (configuration 'serving'): seeded requests of mixed
     sizes, each with its own lognormal eps, mixed delayed path to 1e-8.
     Closed loop first (all submitted at once: throughput), then open loop
-    with Poisson arrivals at load_factor x that throughput; time-to-solution
+    with Poisson arrivals at each load factor x that throughput; time-to-solution
     of a request runs from its submission to its completion (server clock)."""
     reqs = inputs.serving_requests(n_requests, seed=seed, rate_per_s=1.0)
 
@@ -378,31 +385,37 @@ def serving_leg(mg, n_requests, seed=2004, load_factor=0.7, max_active=8):
         closed_s = time.perf_counter() - t0
         thr = len(reqs) / closed_s
         ok_closed = sum(1 for st, _ in res if st == mg.MG_OK)
-        rate = load_factor * thr
-        res2, tickets = [], []
-        t0 = time.perf_counter()
-        for r in reqs:
-            due = t0 + r["arrival_s"] / rate
-            while time.perf_counter() < due:
-                for t in list(tickets):
-                    st, rr = S.poll(t)
-                    if st != mg.MG_ERR_PENDING:
-                        res2.append((st, rr))
-                        tickets.remove(t)
-                time.sleep(0.0002)
-            tickets.append(S.submit(desc(r)))
-        wait_all(S, tickets, res2)
-        open_s = time.perf_counter() - t0
+        open_loops = []
+        for lf in load_factors:
+            rate = lf * thr
+            res2, tickets = [], []
+            t0 = time.perf_counter()
+            for r in reqs:
+                due = t0 + r["arrival_s"] / rate
+                while time.perf_counter() < due:
+                    for t in list(tickets):
+                        st, rr = S.poll(t)
+                        if st != mg.MG_ERR_PENDING:
+                            res2.append((st, rr))
+                            tickets.remove(t)
+                    time.sleep(0.0002)
+                tickets.append(S.submit(desc(r)))
+            wait_all(S, tickets, res2)
+            open_s = time.perf_counter() - t0
+            tts = sorted(r.total_ms for st, r in res2 if st == mg.MG_OK)
+            open_loops.append({"load_factor": lf, "arrival_rate_per_s": rate, "solves_per_s": len(res2) / open_s,
+                               "ok": len(tts), "p50_ms": float(np.percentile(tts, 50)) if tts else None,
+                               "p99_ms": float(np.percentile(tts, 99)) if tts else None})
     finally:
         S.close()
-    tts = sorted(r.total_ms for st, r in res2 if st == mg.MG_OK)
-    return {"requests": len(reqs), "sizes": "uniform over 27^3, 81^3, 243^3 (3D) and 243^2, 729^2 (2D)",
-            "eps": "lognormal, sigma ~ U[0.5, 2], 16 Fourier modes", "path": "mixed delayed, s = 1 -> 8, rtol 1e-8",
-            "max_active": max_active,
-            "closed_loop": {"solves_per_s": thr, "ok": ok_closed, "seconds": closed_s},
-            "open_loop": {"arrival_rate_per_s": rate, "solves_per_s": len(res2) / open_s,
-                          "ok": len(tts), "p50_ms": float(np.percentile(tts, 50)) if tts else None,
-                          "p99_ms": float(np.percentile(tts, 99)) if tts else None}}
+    out = {"requests": len(reqs), "sizes": "uniform over 27^3, 81^3, 243^3 (3D) and 243^2, 729^2 (2D)",
+           "eps": "lognormal, sigma ~ U[0.5, 2], 16 Fourier modes", "path": "mixed delayed, s = 1 -> 8, rtol 1e-8",
+           "max_active": max_active,
+           "closed_loop": {"solves_per_s": thr, "ok": ok_closed, "seconds": closed_s},
+           "open_loop": open_loops[0]}
+    if len(open_loops) > 1:
+        out["open_loop_by_load"] = open_loops
+    return out
 
 
 def run_probe(args, local_rank):
@@ -412,8 +425,9 @@ def run_probe(args, local_rank):
     import torch
     from paper_2005_03606_gb300 import mg
     torch.cuda.set_device(local_rank)
-    if args.probe == "serving":
-        print(json.dumps({"probe": "serving", **serving_leg(mg, args.probe_reps)}), flush=True)
+    if args.probe == "serving":   # --probe-reps requests, open loop at 0.5, 0.7 and 0.9 of the closed-loop rate
+        print(json.dumps({"probe": "serving", **serving_leg(mg, args.probe_reps, load_factors=(0.5, 0.7, 0.9))}),
+              flush=True)
         return
     if args.probe == "solve":   # whole mixed delayed solves, for launch lists
         w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED, n_cells=args.n)
