@@ -788,6 +788,9 @@ __device__ __forceinline__ void pair_sums(const Rows6& u, float (&py)[2][5]) {
     for (int c = 0; c < 5; ++c) py[r][c] = px[r][c] + px[r + 1][c];
 }
 
+// NT > 0: the grid size as a compile-time constant (the strides of every
+// neighbour access fold into address immediates); NT = 0: from the LevelOp
+template <int NT>
 struct GeoCtx {
   const float* x;
   const float* b;
@@ -799,39 +802,43 @@ struct GeoCtx {
   bool hl, hr;
   bool first_row, last_row;   // edge rows of the block also prefetch the halo rows
   float h12, h3, omega;
+  __device__ __forceinline__ int gN() const { return NT ? NT : N; }
+  __device__ __forceinline__ int gn1() const { return NT ? NT + 1 : n1; }
+  __device__ __forceinline__ size_t gplane() const { return NT ? (size_t)(NT + 1) * (NT + 1) : plane; }
 };
 
 // the lines plane k + 1 + kGeoPF (u) and k + kGeoPF (b, eps) of a thread's rows
-__device__ __forceinline__ void geo_prefetch(const GeoCtx& c, int k) {
+template <int NT>
+__device__ __forceinline__ void geo_prefetch(const GeoCtx<NT>& c, int k) {
   if (kGeoPF == 0 || k + kGeoPF > c.k1) return;
   const int kp = k + kGeoPF;
-  const float* u = c.x + (size_t)(kp + 1) * c.plane + c.row0 + c.q;
+  const float* u = c.x + (size_t)(kp + 1) * c.gplane() + c.row0 + c.q;
   prefetch_l2(u);
-  prefetch_l2(c.b + (size_t)kp * c.plane + c.row0 + c.q);
-  const float* e = c.eps + ((size_t)kp * c.N + c.j) * (c.N + 1) + c.q;   // eps row j of layer kp
+  prefetch_l2(c.b + (size_t)kp * c.gplane() + c.row0 + c.q);
+  const float* e = c.eps + ((size_t)kp * c.gN() + c.j) * (c.gN() + 1) + c.q;   // eps row j of layer kp
   prefetch_l2(e);
   if (c.first_row) {
-    prefetch_l2(u - c.n1);
-    prefetch_l2(e - (c.N + 1));
+    prefetch_l2(u - c.gn1());
+    prefetch_l2(e - (c.gN() + 1));
   }
-  if (c.last_row) prefetch_l2(u + c.n1);
+  if (c.last_row) prefetch_l2(u + c.gn1());
 }
 
 // One plane k of the bulk pass.  In: u rows of plane k (uc), their pair sums
 // (pyc), eps of cell layer k-1 (gm) and its eps-weighted cell sums (yTm).
 // Out: the same quantities one plane up (un, pyn, gc, yTc), loaded or formed
 // here, so that a two-step unrolled loop swaps roles instead of copying.
-template <int MODE>
-__device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc, Rows6& un,
+template <int MODE, int NT>
+__device__ __forceinline__ void geo_step(const GeoCtx<NT>& c, int k, const Rows6& uc, Rows6& un,
                                          const float (&pyc)[2][5], float (&pyn)[2][5], const float (&gm)[2][5],
                                          float (&gc)[2][5], const float (&yTm)[5], float (&yTc)[5], float& d1,
                                          float& d2) {
-  load_rows6(c.x, (size_t)(k + 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, un);
-  load_eps10(c.eps, c.N, k, c.j, c.q, c.hl, c.hr, gc);   // c.eps: padded rows
+  load_rows6(c.x, (size_t)(k + 1) * c.gplane() + c.row0, c.gn1(), c.q, c.hl, c.hr, un);
+  load_eps10(c.eps, c.gN(), k, c.j, c.q, c.hl, c.hr, gc);   // c.eps: padded rows
   geo_prefetch(c, k);
-  const float4 b4 = __ldg(reinterpret_cast<const float4*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
+  const float4 b4 = __ldg(reinterpret_cast<const float4*>(c.b + (size_t)k * c.gplane() + c.row0 + c.q));
   // plane k-1, row j (read two planes ago: an L1/L2 hit)
-  const float4 m4 = __ldg(reinterpret_cast<const float4*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
+  const float4 m4 = __ldg(reinterpret_cast<const float4*>(c.x + (size_t)(k - 1) * c.gplane() + c.row0 + c.q));
   // layer k: cell sums T = Py(k) + Py(k+1), weighted by eps and summed over the two cell rows
   pair_sums(un, pyn);
 #pragma unroll
@@ -866,7 +873,7 @@ __device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc
     w = fmaf(elm[e] + elm[e + 1], um1[e], w);               // z - 1
     w = fmaf(elc[e] + elc[e + 1], un.v[1][e + 1], w);       // z + 1
     const int i = c.q + e;
-    const bool valid = i >= 1 && i <= c.N - 1;
+    const bool valid = i >= 1 && i <= c.gN() - 1;
     float r;
     // Jacobi: u + omega (b - h/12 w) / (h/3 G), with omega / (h/3) folded into c.omega
     if (MODE == SW_JACOBI) r = fmaf(c.omega, __fdividef(fmaf(-c.h12, w, bb4[e]), G), uv);
@@ -881,22 +888,23 @@ __device__ __forceinline__ void geo_step(const GeoCtx& c, int k, const Rows6& uc
     }
     out[e] = valid ? r : 0.f;   // boundary vertices stay zero
   }
-  *reinterpret_cast<float4*>(c.y + (size_t)k * c.plane + c.row0 + c.q) = make_float4(out[0], out[1], out[2], out[3]);
+  *reinterpret_cast<float4*>(c.y + (size_t)k * c.gplane() + c.row0 + c.q) =
+      make_float4(out[0], out[1], out[2], out[3]);
 }
 
-template <int MODE>
+template <int MODE, int NT>
 __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
                                                                   const float* __restrict__ b,
                                                                   float* __restrict__ y, float omega,
                                                                   double* __restrict__ partials, int ntx, int nty) {
   __shared__ double sh[2][8];
-  GeoCtx c;
+  GeoCtx<NT> c;
   c.x = x;
   c.b = b;
   c.y = y;
   c.eps = op.eps_pad;
-  c.N = op.N;
-  c.n1 = op.N + 1;
+  c.N = NT ? NT : op.N;
+  c.n1 = c.N + 1;
   c.plane = (size_t)c.n1 * c.n1;
   c.h12 = -op.gk32;   // h / 12
   c.h3 = 4.f * c.h12;   // h / 3
@@ -905,33 +913,33 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
   // set the Krylov step lengths), summed over the block in FP64
   float d1 = 0.f, d2 = 0.f;
   long long w, w1;
-  geo_share(ntx, nty, c.N, w, w1);
+  geo_share(ntx, nty, c.gN(), w, w1);
   GeoRun run;
-  while (next_geo_run(w, w1, c.N - 1, ntx, run)) {
+  while (next_geo_run(w, w1, c.gN() - 1, ntx, run)) {
     c.q = 4 * (run.tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
     c.j = 1 + run.ty * kGeoBY + threadIdx.y;
     const int k0 = run.k0, k1 = run.k1;
-    if (c.q >= c.n1 || c.j >= c.N) continue;
+    if (c.q >= c.gn1() || c.j >= c.gN()) continue;
     c.k1 = k1;
     c.hl = c.q > 0;
-    c.hr = c.q + 4 <= c.N;
+    c.hr = c.q + 4 <= c.gN();
     c.first_row = threadIdx.y == 0;
-    c.last_row = threadIdx.y == kGeoBY - 1 || c.j == c.N - 1;
-    c.row0 = (size_t)c.j * c.n1;
+    c.last_row = threadIdx.y == kGeoBY - 1 || c.j == c.gN() - 1;
+    c.row0 = (size_t)c.j * c.gn1();
     // prologue: rows and pair sums of plane k0, eps and weighted cell sums of layer k0-1
     Rows6 ua, ub;
     float pa[2][5], pb[2][5], ga[2][5], gb[2][5], ta[5], tb[5];
-    load_rows6(x, (size_t)(k0 - 1) * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, ub);
-    load_rows6(x, (size_t)k0 * c.plane + c.row0, c.n1, c.q, c.hl, c.hr, ua);
-    load_eps10(op.eps_pad, c.N, k0 - 1, c.j, c.q, c.hl, c.hr, ga);
+    load_rows6(x, (size_t)(k0 - 1) * c.gplane() + c.row0, c.gn1(), c.q, c.hl, c.hr, ub);
+    load_rows6(x, (size_t)k0 * c.gplane() + c.row0, c.gn1(), c.q, c.hl, c.hr, ua);
+    load_eps10(op.eps_pad, c.gN(), k0 - 1, c.j, c.q, c.hl, c.hr, ga);
     pair_sums(ub, pb);
     pair_sums(ua, pa);
 #pragma unroll
     for (int i = 0; i < 5; ++i) ta[i] = ga[0][i] * (pb[0][i] + pa[0][i]) + ga[1][i] * (pb[1][i] + pa[1][i]);
     for (int k = k0; k <= k1; k += 2) {
-      geo_step<MODE>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
+      geo_step<MODE, NT>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
       if (k + 1 > k1) break;
-      geo_step<MODE>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
+      geo_step<MODE, NT>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
     }
   }
   if (MODE == SW_MATVEC) {
@@ -1543,15 +1551,24 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
     count_launches(1);
     launch_fixup<SW_JACOBI0>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_JACOBI) {
-    sweep3_geo4<SW_JACOBI><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+    if (op.N == 243)
+      sweep3_geo4<SW_JACOBI, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+    else
+      sweep3_geo4<SW_JACOBI, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
     launch_fixup<SW_JACOBI>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_RESID) {
-    sweep3_geo4<SW_RESID><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+    if (op.N == 243)
+      sweep3_geo4<SW_RESID, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+    else
+      sweep3_geo4<SW_RESID, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
     launch_fixup<SW_RESID>(op, x, b, y, omega, pfix, st);
   } else {
-    sweep3_geo4<SW_MATVEC><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+    if (op.N == 243)
+      sweep3_geo4<SW_MATVEC, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+    else
+      sweep3_geo4<SW_MATVEC, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
     count_launches(1);
     launch_fixup<SW_MATVEC>(op, x, b, y, omega, pfix, st);
   }
