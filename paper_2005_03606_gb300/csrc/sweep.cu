@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3) sweep3_stream(const LevelOp op, 
 // grid, no wave tail) take equal shares of the z runs of all columns.
 constexpr int kGeoBX = 32, kGeoBY = 8;
 #ifndef MG_GEO_PF
-#define MG_GEO_PF 1
+#define MG_GEO_PF 2
 #endif
 constexpr int kGeoPF = MG_GEO_PF;   // planes of L2 prefetch ahead of the z march
 
