@@ -89,7 +89,9 @@ typedef enum {
   /* FP64 storage and arithmetic; cycling starts on the geometric stencils
    * (s = 1) while s_schedule[1..] are assembled on a side stream and
    * published at cycle boundaries (Section "Asynchronous and anarchic
-   * stencil integration") */
+   * stencil integration"); finished chunks are held until the schedule is
+   * done, the solver waits for them, or 16 cycles have passed since the first
+   * of them finished, so that one publication restarts the iteration once */
   MG_PATH_FP64_DELAYED = 1,
   /* as FP64_DELAYED, but the fine element matrices are stored as FP32 cell
    * centre eps plus a lossy hierarchical surplus (FP8-e4m3 / FP16 / FP32 with
@@ -186,12 +188,14 @@ mg_status mg_destroy_problem(mg_problem* p);
  * per cell; Section "Numerical computation of stencils", A^(geo)(n)), stores
  * them in the problem's format and recomputes the coarse Galerkin operators.
  * async = 0: in stream order, published at once.  async = 1: on the side
- * stream chunk by chunk; each chunk is published at the next cycle boundary
- * after it completes (Section "Asynchronous and anarchic stencil
- * integration").  Errors: MG_ERR_INVALID (s < 1 or s > 64), MG_ERR_OOM, MG_ERR_CUDA. */
+ * stream chunk by chunk; completed chunks are published at a later cycle
+ * boundary, under the holding rule of MG_PATH_FP64_DELAYED (Section
+ * "Asynchronous and anarchic stencil integration").
+ * Errors: MG_ERR_INVALID (s < 1 or s > 64), MG_ERR_OOM, MG_ERR_CUDA. */
 mg_status mg_assemble_level(mg_problem* p, int s, int async);
 
-/* Runs n outer iterations (each one V-cycle) from the current solution,
+/* Runs n outer iterations (each one multigrid cycle of desc->cycle) from the
+ * current solution (n = 0: only the residual),
  * publishing completed asynchronous chunks at cycle boundaries, and returns
  * the FP64 relative residual ||f - A u||_2 / ||f||_2 of the stored operator.
  * rel_residual may be NULL.  Errors: MG_ERR_INVALID, MG_ERR_CUDA. */
