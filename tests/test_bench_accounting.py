@@ -1,0 +1,36 @@
+"""Host-side accounting of bench.py (no GPU): the algorithmic bytes behind the
+roofline line, and the ncu-summary reader that supplies its DRAM traffic."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import pytest  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def test_sweep_bytes_of_the_benchmark_workload():
+    # boxes3d 243^3 at s = 8: 14,212,390 cells without a surplus, 136,517 with an
+    # FP32 record.  Per vertex u, b, y (4 B each); per cell eps_c 4 B and a class
+    # byte; 112 B per FP32 record; 12 B of segment bases per 32 cells.
+    cbc = [14212390, 0, 0, 136517]
+    n = 243
+    expect = 244 ** 3 * 12 + n ** 3 * 5 + 136517 * 112 + (n ** 3 // 32) * 12
+    assert bench.sweep_bytes(3, n, cbc, True, 4) == expect == 266736683
+
+
+def test_sweep_bytes_full_storage_and_2d():
+    assert bench.sweep_bytes(3, 27, [0, 0, 0, 0], False, 8) == 28 ** 3 * 24 + 27 ** 3 * 28 * 8
+    assert bench.sweep_bytes(2, 81, [6561, 0, 0, 0], True, 4) == 82 ** 2 * 12 + 81 ** 2 * 5 + (81 ** 2 // 32) * 12
+
+
+def test_sweep_traffic_reads_the_committed_summary():
+    assert bench.sweep_traffic("fourier3d") is None      # other workloads: no capture
+    t = bench.sweep_traffic("boxes3d")
+    if t is None:
+        pytest.skip("the sweep source changed since the committed ncu summary was taken")
+    # a positive byte count within 10% of the algorithmic bytes (re-reads would show here)
+    assert abs(t - 266736683) <= 0.1 * 266736683
