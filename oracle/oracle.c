@@ -14,6 +14,10 @@
  *     each sub-box centre (Section "Numerical computation of stencils");
  *     each sub-box integral of grad(phi_i).grad(phi_j) is done with the
  *     2-point Gauss rule per axis, which is exact for that polynomial;
+ *   - adaptive per-cell accuracy: each cell walks the accuracy schedule and
+ *     keeps the first matrix whose relative change in the element-wise
+ *     maximum norm drops below C (Section "Adaptive stencil integration",
+ *     Eq. "termination-criterion");
  *   - the hierarchical surplus A(s) - A(1) and its lossy storage
  *     (Section "Precision toggling and information density"), with the
  *     formats FP8-e4m3 / FP16 / FP32 plus a per-cell FP32 scale;
