@@ -34,3 +34,25 @@ def test_sweep_traffic_reads_the_committed_summary():
         pytest.skip("the sweep source changed since the committed ncu summary was taken")
     # a positive byte count within 10% of the algorithmic bytes (re-reads would show here)
     assert abs(t - 266736683) <= 0.1 * 266736683
+
+
+def test_profile_summaries_name_their_commands_on_committed_files():
+    prof = os.path.join(ROOT, "profiles")
+    names = [f for f in os.listdir(prof) if f.endswith((".md", ".txt"))]
+    assert names
+    for f in names:
+        text = open(os.path.join(prof, f)).read()
+        assert "ncu " in text and "--clock-control none" in text, f
+        assert "_work" not in text, f            # the commands run committed files only
+        assert "python bench.py" in text, f
+
+
+def test_committed_sources_do_not_use_the_working_folder():
+    for top in ("paper_2005_03606_gb300", "oracle", "tests", "include"):
+        for dirpath, _, files in os.walk(os.path.join(ROOT, top)):
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                    text = open(os.path.join(dirpath, f), errors="replace").read()
+                    assert "_work/" not in text.replace('"_work/"', ""), os.path.join(dirpath, f)
+    for f in ("bench.py", "__graft_entry__.py"):
+        assert "_work" not in open(os.path.join(ROOT, f)).read(), f
