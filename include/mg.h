@@ -349,9 +349,13 @@ uint64_t mg_launch_count(void);
  * eps_c_out holds n_cells^dim floats (the whole grid is written), cls_out
  * ncell bytes, surplus_out ncell * NP floats.  Work is issued on cuda_stream
  * (NULL = legacy default stream); the call returns without synchronising.
- * Scratch: a fixed 64 MiB device array inside the library, which bounds one
- * call to about 460k cells in 3D (ncell * 144 bytes in 3D, ncell * 64 in 2D,
- * plus padding); larger ranges return MG_ERR_INVALID with the limit in
+ * Scratch: a fixed 64 MiB (67,108,864-byte) device array inside the library.
+ * One call needs ncell * REC_MAX record bytes (REC_MAX = 112 in 3D, 32 in
+ * 2D) rounded up to a multiple of 256, plus rows * ceil(n_cells/32) * 32
+ * padded class bytes (rows = ncell / n_cells), and the sum must not exceed
+ * 64 MiB: at n_cells = 243 that is at most 2,442 x-rows (593,406 cells) in
+ * 3D.  The eps descriptor is checked as at problem creation.  Larger ranges
+ * and bad descriptors return MG_ERR_INVALID with the reason in
  * mg_last_error().  The array is shared by every call on a device and keeps
  * the last call's contents, so calls that overlap on the GPU (different
  * streams, or host threads) race and must be serialised by the caller.  The

@@ -17,6 +17,7 @@
 
 namespace mg {
 void eps_desc_to_dev(const mg_eps_desc& d, int dim, EpsDev* e);
+mg_status eps_desc_check(const mg_eps_desc& d);
 }
 
 using namespace mg;
@@ -76,6 +77,9 @@ extern "C" mg_status mg_assemble_surplus_noalloc(const mg_eps_desc* eps, int dim
     set_error("mg_assemble_surplus_noalloc: bad arguments");
     return MG_ERR_INVALID;
   }
+  // the same field checks as problem creation: the device tables hold at most
+  // MG_MAX_MODES modes and MG_MAX_BOXES boxes, and eps must be positive
+  if (eps_desc_check(*eps) != MG_OK) return MG_ERR_INVALID;
   const long long N = n_cells;
   const long long total = dim == 3 ? N * N * N : N * N;
   if (cell0 + ncell > total || cell0 % N != 0 || ncell % N != 0) {
@@ -85,23 +89,22 @@ extern "C" mg_status mg_assemble_surplus_noalloc(const mg_eps_desc* eps, int dim
   const int rec_max = dim == 3 ? Dim<3>::REC_MAX : Dim<2>::REC_MAX;
   const int nseg_x = (int)((N + kSegCells - 1) / kSegCells);
   const long long rows = ncell / N;
+  // scratch rule: ncell * REC_MAX record bytes rounded up to 256, then
+  // rows * ceil(N/32) * 32 padded class bytes, at most kNoAllocScratchBytes
   const size_t rec_bytes = (size_t)ncell * rec_max;
+  const size_t rec_span = ((rec_bytes + 255) / 256) * 256;
   const size_t cls_bytes = (size_t)rows * nseg_x * kSegCells;
-  if (rec_bytes + cls_bytes > kNoAllocScratchBytes) {
-    set_error("mg_assemble_surplus_noalloc: %lld cells need %zu scratch bytes, the limit is %zu (at most %lld cells)",
-              (long long)ncell, rec_bytes + cls_bytes, kNoAllocScratchBytes,
-              (long long)(kNoAllocScratchBytes / (rec_max + kSegCells)));
+  if (rec_span + cls_bytes > kNoAllocScratchBytes) {
+    set_error("mg_assemble_surplus_noalloc: %lld cells need %zu scratch bytes (ncell*%d rounded up to 256, plus "
+              "%lld rows * %d padded class bytes); the limit is %zu",
+              (long long)ncell, rec_span + cls_bytes, rec_max, rows, nseg_x * kSegCells, kNoAllocScratchBytes);
     return MG_ERR_INVALID;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   void* base = nullptr;
   if (!cuda_ok(scratch_address(&base), "scratch address")) return MG_ERR_CUDA;
   uint8_t* rec = (uint8_t*)base;
-  uint8_t* cls_pad = rec + ((rec_bytes + 255) / 256) * 256;
-  if ((size_t)(cls_pad - rec) + cls_bytes > kNoAllocScratchBytes) {
-    set_error("mg_assemble_surplus_noalloc: scratch limit exceeded");
-    return MG_ERR_INVALID;
-  }
+  uint8_t* cls_pad = rec + rec_span;
   EpsDev F;
   eps_desc_to_dev(*eps, dim, &F);
   // cell-centre eps of the whole grid (the caller's eps_c_out holds n_cells^dim floats)

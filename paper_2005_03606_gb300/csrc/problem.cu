@@ -265,6 +265,40 @@ void fill_eps(const mg_eps_desc& d, int dim, EpsDev* e) {
   for (int m = 0; m < MG_MAX_MODES; ++m) e->phi_over_pi_f[m] = (float)e->phi_over_pi[m];
 }
 
+// Checks of an eps descriptor shared by problem creation and the
+// allocation-free assembly: kind, mode and box counts within the device
+// tables, wavenumbers, positive values.
+mg_status validate_eps(const mg_eps_desc& e) {
+  if (e.kind < 0 || e.kind > 4) {
+    set_error("unknown eps kind %d", e.kind);
+    return MG_ERR_INVALID;
+  }
+  if (e.kind == MG_EPS_FOURIER && (e.n_modes < 1 || e.n_modes > MG_MAX_MODES)) {
+    set_error("n_modes out of range");
+    return MG_ERR_INVALID;
+  }
+  if (e.kind == MG_EPS_FOURIER)
+    for (int m = 0; m < e.n_modes; ++m)
+      for (int a = 0; a < 3; ++a)
+        if (std::abs(e.k[m][a]) > 64) {
+          set_error("wavenumber component above 64");
+          return MG_ERR_INVALID;
+        }
+  if (e.kind == MG_EPS_BOXES && (e.n_boxes < 1 || e.n_boxes > MG_MAX_BOXES)) {
+    set_error("n_boxes out of range");
+    return MG_ERR_INVALID;
+  }
+  if (!(e.jump_factor > 0.0) || !(e.v_out > 0.0)) {
+    set_error("eps must be positive");
+    return MG_ERR_INVALID;
+  }
+  if ((e.kind == MG_EPS_DISC || e.kind == MG_EPS_BOXES) && !(e.v_in > 0.0)) {
+    set_error("eps must be positive");
+    return MG_ERR_INVALID;
+  }
+  return MG_OK;
+}
+
 mg_status validate(const mg_problem_desc* d) {
   if (!d) {
     set_error("null descriptor");
@@ -296,34 +330,7 @@ mg_status validate(const mg_problem_desc* d) {
     set_error("adapt_C must be a finite value >= 0");
     return MG_ERR_INVALID;
   }
-  const mg_eps_desc& e = d->eps;
-  if (e.kind < 0 || e.kind > 4) {
-    set_error("unknown eps kind %d", e.kind);
-    return MG_ERR_INVALID;
-  }
-  if (e.kind == MG_EPS_FOURIER && (e.n_modes < 1 || e.n_modes > MG_MAX_MODES)) {
-    set_error("n_modes out of range");
-    return MG_ERR_INVALID;
-  }
-  if (e.kind == MG_EPS_FOURIER)
-    for (int m = 0; m < e.n_modes; ++m)
-      for (int a = 0; a < 3; ++a)
-        if (std::abs(e.k[m][a]) > 64) {
-          set_error("wavenumber component above 64");
-          return MG_ERR_INVALID;
-        }
-  if (e.kind == MG_EPS_BOXES && (e.n_boxes < 1 || e.n_boxes > MG_MAX_BOXES)) {
-    set_error("n_boxes out of range");
-    return MG_ERR_INVALID;
-  }
-  if (!(e.jump_factor > 0.0) || !(e.v_out > 0.0)) {
-    set_error("eps must be positive");
-    return MG_ERR_INVALID;
-  }
-  if ((e.kind == MG_EPS_DISC || e.kind == MG_EPS_BOXES) && !(e.v_in > 0.0)) {
-    set_error("eps must be positive");
-    return MG_ERR_INVALID;
-  }
+  if (validate_eps(d->eps) != MG_OK) return MG_ERR_INVALID;
   if (d->n_s < 1 || d->n_s > 8) {
     set_error("n_s must be 1..8");
     return MG_ERR_INVALID;
@@ -999,6 +1006,8 @@ int min_s(const mg_problem* P) {
 namespace mg {
 // field descriptor of the C ABI to the device layout (used by other translation units)
 void eps_desc_to_dev(const mg_eps_desc& d, int dim, EpsDev* e) { fill_eps(d, dim, e); }
+// the descriptor checks of problem creation (MG_OK or MG_ERR_INVALID with the message set)
+mg_status eps_desc_check(const mg_eps_desc& d) { return validate_eps(d); }
 }  // namespace mg
 
 // ====================================================================== C ABI

@@ -91,6 +91,43 @@ def test_invalid_field_rejected(lib):
         mg.Problem(mg.problem_desc(2, 9, neg))
 
 
+def _noalloc_raw(lib, e, dim=3, n=27, s=8, cell0=0, ncell=27):
+    # dummy non-null pointers: every case below is rejected on the host before any device call
+    return lib.mg_assemble_surplus_noalloc(ctypes.byref(e), dim, n, s, 1e-6, cell0, ncell, 16, 16, 16, None)
+
+
+def test_noalloc_rejects_bad_fields_on_host(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("host-rejection checks with dummy pointers run where no device exists")
+    except ImportError:
+        pass
+    good = mg.eps_desc(inputs.boxes_field(3, 2003))
+    bad = []
+    e = mg.eps_desc(inputs.boxes_field(3, 2003)); e.n_boxes = 65; bad.append(e)
+    e = mg.eps_desc(inputs.boxes_field(3, 2003)); e.n_boxes = 0; bad.append(e)
+    e = mg.eps_desc(inputs.fourier_field(3, 2002)); e.n_modes = 0; bad.append(e)
+    e = mg.eps_desc(inputs.fourier_field(3, 2002)); e.n_modes = 33; bad.append(e)
+    e = mg.eps_desc(inputs.fourier_field(3, 2002)); e.k[0][1] = 65; bad.append(e)
+    e = mg.eps_desc(inputs.boxes_field(3, 2003)); e.v_out = 0.0; bad.append(e)
+    e = mg.eps_desc(inputs.boxes_field(3, 2003)); e.v_in = -1.0; bad.append(e)
+    e = mg.eps_desc(inputs.boxes_field(3, 2003)); e.jump_factor = 0.0; bad.append(e)
+    e = mg.eps_desc(inputs.boxes_field(3, 2003)); e.kind = 7; bad.append(e)
+    for e in bad:
+        assert _noalloc_raw(lib, e) == mg.MG_ERR_INVALID
+    # argument and range checks with a valid field
+    assert _noalloc_raw(lib, good, s=65) == mg.MG_ERR_INVALID
+    assert _noalloc_raw(lib, good, s=0) == mg.MG_ERR_INVALID
+    assert _noalloc_raw(lib, good, cell0=5) == mg.MG_ERR_INVALID
+    assert _noalloc_raw(lib, good, cell0=27, ncell=40) == mg.MG_ERR_INVALID
+    assert _noalloc_raw(lib, good, ncell=0) == mg.MG_ERR_INVALID
+    assert _noalloc_raw(lib, good, cell0=27 ** 3 - 27, ncell=54) == mg.MG_ERR_INVALID
+    # the scratch rule: 243^3 cells at 112 record bytes each are far beyond 64 MiB
+    assert _noalloc_raw(lib, good, n=243, ncell=243 ** 3) == mg.MG_ERR_INVALID
+    assert b"scratch" in lib.mg_last_error()
+
+
 def test_server_admission_and_injected_failures(lib):
     # budget too small for the request: rejected at submit, nothing reaches the device
     s = mg.Server(max_active=2, budget_bytes=1e6)

@@ -78,6 +78,8 @@ CASES = [
     (3, 27, inputs.boxes_field(3, 2003), 8, [(0, 27 * 27), (9 * 27 + 5, 300)]),
     (2, 81, inputs.disc_field(2), 8, [(0, 81), (17, 40)]),
     (3, 27, inputs.fourier_field(3, 15, sigma=2.0, jump_x=0.37, jump_factor=1e4), 4, [(27 * 10, 27 * 7), (0, 1)]),
+    # one sample per cell: the surplus is zero by definition (the early-return branch)
+    (3, 27, inputs.boxes_field(3, 2003), 1, [(0, 27 * 27), (5 * 27, 27)]),
 ]
 
 
@@ -102,6 +104,8 @@ def test_noalloc_matches_regular_assembly(dim, n, fld, s, ranges):
         assert err <= TOL, err
         s_np = sur.cpu().numpy()
         assert np.all(s_np[c == 0] == 0.0)
+        if s == 1:
+            assert not c.any() and not s_np.any()
 
 
 def test_noalloc_rejects_ranges_beyond_scratch():
@@ -115,4 +119,10 @@ def test_noalloc_rejects_ranges_beyond_scratch():
     assert "scratch" in str(ei.value)
     with pytest.raises(mg.MGError) as ei:    # not whole x-rows
         mg.assemble_surplus_noalloc(fld, 3, 27, 8, 5, 27, p, p, p)
+    assert ei.value.status == mg.MG_ERR_INVALID
+    with pytest.raises(mg.MGError) as ei:    # row-aligned start, ragged length
+        mg.assemble_surplus_noalloc(fld, 3, 27, 8, 27, 40, p, p, p)
+    assert ei.value.status == mg.MG_ERR_INVALID
+    with pytest.raises(mg.MGError) as ei:    # accuracy beyond 64 samples per axis
+        mg.assemble_surplus_noalloc(fld, 3, 27, 65, 0, 27, p, p, p)
     assert ei.value.status == mg.MG_ERR_INVALID
