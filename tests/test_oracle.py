@@ -730,3 +730,182 @@ def test_memory_footprint_first_cycle_matches_golden():
         _, s_cell = oracle.assemble_adaptive(f, n, (1,), 0.01)
         assert s_cell.max() == int(max_n) and round(float(s_cell.mean()), 2) == float(avg_n)
         assert round(oracle.paper_compression(2, p3), 2) == float(comp)
+
+
+# ---------------------------------------------------------------- V-cycle against sparse global matrices
+# Section "Multiplicative vs. additive schemes" and Section "adaFAC-x" fix the
+# pieces: damped Jacobi S = omega diag(A)^-1, the d-linear 3:1 prolongation P,
+# R = P^T, Galerkin coarse operators P^T A P and an exact coarsest solve.  The
+# reference below builds every one of them from global sparse matrices (no
+# oracle routine besides the element matrices of the finest level), so a
+# swapped nu_pre / nu_post, a dropped smoothing step or a residual of the
+# wrong iterate in the oracle's V-cycle fails it.
+
+def _p1d(nc):
+    """1D 3:1 linear interpolation, coarse vertex I sits on fine vertex 3I."""
+    nf = 3 * nc
+    P = np.zeros((nf + 1, nc + 1))
+    for i in range(nf + 1):
+        for I in range(nc + 1):
+            P[i, I] = max(0.0, 1.0 - abs(i - 3 * I) / 3.0)
+    return P
+
+
+def _prolong_sparse(dim, nc):
+    from scipy import sparse
+    P1 = sparse.csr_matrix(_p1d(nc))
+    P = P1
+    for _ in range(dim - 1):
+        P = sparse.kron(P1, P)          # vertex index has x fastest
+    return P.tocsr()
+
+
+def _global_sparse(dim, n, A_all):
+    """Element sum on all (n+1)^d vertices (boundary rows kept)."""
+    from scipy import sparse
+    nv = 1 << dim
+    n1 = n + 1
+    cells = np.indices((n,) * dim).reshape(dim, -1)[::-1]        # x fastest
+    base = sum(cells[a] * n1 ** a for a in range(dim))
+    off = np.array([sum(((i >> a) & 1) * n1 ** a for a in range(dim)) for i in range(nv)])
+    gv = base[:, None] + off[None, :]                             # [cells, nv]
+    rows = np.repeat(gv, nv, axis=1).ravel()
+    cols = np.tile(gv, (1, nv)).ravel()
+    return sparse.csr_matrix((A_all.reshape(len(base), nv * nv).ravel(), (rows, cols)), shape=(n1 ** dim,) * 2)
+
+
+def _vcycle_sparse(dim, n, A_fine, b, omega, nu_pre, nu_post):
+    from scipy.sparse.linalg import spsolve
+    ns, Ms, Ps = [n], [_global_sparse(dim, n, A_fine)], []
+    while ns[-1] > 3:
+        nc = ns[-1] // 3
+        P = _prolong_sparse(dim, nc)
+        Ms.append((P.T @ Ms[-1] @ P).tocsr())
+        Ps.append(P)
+        ns.append(nc)
+
+    def V(k, rhs):
+        m = dense.interior_mask(dim, ns[k])
+        M = Ms[k]
+        e = np.zeros_like(rhs)
+        if k == len(ns) - 1:
+            e[m] = spsolve(M[m][:, m].tocsc(), rhs[m])
+            return e
+        D = M.diagonal()
+
+        def jac(x):
+            y = x.copy()
+            y[m] = x[m] + omega * (rhs[m] - (M @ x)[m]) / D[m]
+            return y
+
+        for _ in range(nu_pre):
+            e = jac(e)
+        r = np.where(m, rhs - M @ e, 0.0)
+        rc = Ps[k].T @ r
+        rc[~dense.interior_mask(dim, ns[k + 1])] = 0.0
+        e = e + Ps[k] @ V(k + 1, rc)
+        e[~m] = 0.0
+        for _ in range(nu_post):
+            e = jac(e)
+        return e
+
+    return V(0, b)
+
+
+VCYCLE_CASES = [
+    # dim, n (levels: n, n/3, ..., 3), field, nu_pre, nu_post
+    (2, 9, lambda: inputs.disc_field(2), 2, 2),
+    (2, 27, lambda: inputs.boxes_field(2, 11), 1, 3),
+    (2, 81, lambda: inputs.fourier_field(2, 5, sigma=1.0), 3, 1),
+    (3, 9, lambda: inputs.fourier_field(3, 4, sigma=1.0), 2, 2),
+    (3, 27, lambda: inputs.boxes_field(3, 2003), 0, 2),
+    (3, 27, lambda: inputs.fourier_field(3, 6, sigma=1.0), 2, 1),
+]
+
+
+@pytest.mark.parametrize("dim,n,mk,nu_pre,nu_post", VCYCLE_CASES)
+def test_vcycle_matches_sparse_global_formula(dim, n, mk, nu_pre, nu_post):
+    A = oracle.assemble(oracle.Field(mk()), n, 4)
+    b = np.random.default_rng(7).standard_normal((n + 1) ** dim) * dense.interior_mask(dim, n)
+    e = oracle.vcycle_once(dim, n, A, b, 0.6, nu_pre, nu_post)
+    ref = _vcycle_sparse(dim, n, A, b, 0.6, nu_pre, nu_post)
+    assert np.abs(e - ref).max() <= 1e-12 * np.abs(ref).max()
+    if nu_pre != nu_post:      # the case discriminates a swap of the two counts
+        swapped = _vcycle_sparse(dim, n, A, b, 0.6, nu_post, nu_pre)
+        assert np.abs(swapped - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_symmetric_vcycle_is_a_symmetric_operator():
+    # V(nu, nu) with a symmetric smoother and R = P^T is a symmetric map
+    dim, n = 2, 27
+    A = oracle.assemble(oracle.Field(inputs.boxes_field(2, 12)), n, 4)
+    m = dense.interior_mask(dim, n)
+    b1, b2 = np.random.default_rng(8).standard_normal((2, (n + 1) ** dim)) * m
+    for nu in (1, 2):
+        e1 = oracle.vcycle_once(dim, n, A, b1, 0.6, nu, nu)
+        e2 = oracle.vcycle_once(dim, n, A, b2, 0.6, nu, nu)
+        assert abs(b2 @ e1 - b1 @ e2) <= 1e-12 * abs(b2 @ e1)
+    e1 = oracle.vcycle_once(dim, n, A, b1, 0.6, 1, 3)
+    e2 = oracle.vcycle_once(dim, n, A, b2, 0.6, 1, 3)
+    assert abs(b2 @ e1 - b1 @ e2) > 1e-6 * abs(b2 @ e1)
+
+
+# ---------------------------------------------------------------- storage-class boundaries
+# Section "Precision toggling and information density": a cell stores the
+# fewest bytes that keep its matrix within the bound.  With the surplus scaled
+# so that its largest off-diagonal |D|max maps to a format's largest finite
+# value, the worst entry error is the format's largest half-gap between
+# neighbouring values times the scale, and the diagonal (minus the row sum)
+# adds up F = 2^d - 1 such errors.  The half-gaps are found here by
+# enumerating every value of the formats (torch's float8_e4m3fn, numpy's
+# float16), not from the oracle's constants.
+
+def _half_gap_and_max(kind):
+    if kind == "e4m3":
+        torch = pytest.importorskip("torch")
+        bits = torch.arange(256, dtype=torch.int32).to(torch.uint8)
+        v = bits.view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    else:
+        v = np.arange(65536, dtype=np.uint32).astype(np.uint16).view(np.float16).astype(np.float64)
+    v = np.unique(v[np.isfinite(v) & (v >= 0)])
+    return float(np.diff(v).max() / 2), float(v.max())
+
+
+def _cell_with_surplus(dim, t, rng):
+    """A symmetric zero-row-sum matrix eps_c K + t D0 (eps_c = 1, h = 1/9)."""
+    nv = 1 << dim
+    K = kref_closed(dim) * (1.0 / 9 if dim == 3 else 1.0)
+    D0 = np.zeros((nv, nv))
+    for i in range(nv):
+        for j in range(i + 1, nv):
+            D0[i, j] = D0[j, i] = rng.uniform(-0.6, 0.6)
+    D0[0, nv - 1] = D0[nv - 1, 0] = 1.0            # |D|max = t exactly
+    np.fill_diagonal(D0, 0.0)
+    np.fill_diagonal(D0, -D0.sum(axis=1))
+    return K, K + t * D0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_storage_class_boundaries_are_exact(dim):
+    from scipy.optimize import brentq
+    tau, F = 1e-6, (1 << dim) - 1
+    hg8, m8 = _half_gap_and_max("e4m3")
+    hg16, m16 = _half_gap_and_max("f16")
+    assert (hg8, m8, hg16, m16) == (16.0, 448.0, 16.0, 65504.0)
+    rng = np.random.default_rng(21 + dim)
+    seed_state = rng.bit_generator.state
+    # bound factor of each class: storing nothing (error |D|max per entry), FP8, FP16
+    factors = [1.0, hg8 / m8, hg16 / m16]
+    for cls_below, fac in enumerate(factors):
+        def g(t):
+            rng.bit_generator.state = seed_state
+            _, A = _cell_with_surplus(dim, t, rng)
+            return F * t * fac - tau * np.abs(A).max()
+        t_star = brentq(g, 1e-16, 1.0, xtol=1e-30, rtol=1e-15)
+        for t, want in ((t_star * (1 - 1e-9), cls_below), (t_star * (1 + 1e-9), cls_below + 1)):
+            rng.bit_generator.state = seed_state
+            K, A = _cell_with_surplus(dim, t, rng)
+            c, At, _ = oracle.compress_cell(dim, A, 1.0, K, tau)
+            # just below boundary k class k is the cheapest that fits; just above, k + 1
+            assert c == want, (cls_below, t, c)
+            assert np.abs(At - A).max() <= tau * np.abs(A).max() * (1 + 1e-9)
