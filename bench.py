@@ -125,19 +125,33 @@ def sweep_traffic(workload):
 
 
 def sweep_bytes(dim, n, cells_by_class, mixed, vec_bytes):
-    """Algorithmic DRAM bytes of one finest-level sweep: each vertex value read
-    (x, b) and written (y) once, each cell's stored operator read once."""
-    nvert = (n + 1) ** dim
+    """Algorithmic DRAM bytes of one finest-level sweep, counted per cell as
+    the unit: the iterate read and written and the right-hand side read
+    (3 x vec_bytes), plus the cell's stored operator read once.  Mixed paths:
+    FP32 eps_c 4 + class byte 1 + the surplus payload of the cell's class
+    (FP8: NP bytes + 4-byte scale, FP16: 2 NP + 4, FP32: 4 NP + 4, with NP = 28
+    off-diagonals in 3D and 6 in 2D); FP64 paths: NP x 8 bytes.  Layout
+    overheads (the (n+1)^d - n^d extra vertices, per-segment base offsets,
+    record padding) are not algorithmic; `sweep_overhead_bytes` counts them."""
     ncell = n ** dim
     np_ = 28 if dim == 3 else 6
-    b = nvert * 3 * vec_bytes
+    b = ncell * 3 * vec_bytes
     if mixed:
-        rec = (32, 64, 112) if dim == 3 else (16, 16, 32)
-        b += ncell * (4 + 1)                                  # eps_c, class byte
-        b += sum(int(cells_by_class[k + 1]) * rec[k] for k in range(3))
-        b += ncell // 32 * 12                                 # segment bases
+        pay = (np_ + 4, 2 * np_ + 4, 4 * np_ + 4)
+        b += ncell * (4 + 1)
+        b += sum(int(cells_by_class[k + 1]) * pay[k] for k in range(3))
     else:
         b += ncell * np_ * 8
+    return b
+
+
+def sweep_overhead_bytes(dim, n, mixed, vec_bytes):
+    """Bytes the layout adds to one sweep beyond `sweep_bytes`: the boundary
+    ring of the vertex arrays and, on the compressed level, three u32 base
+    offsets per 32-cell segment."""
+    b = ((n + 1) ** dim - n ** dim) * 3 * vec_bytes
+    if mixed:
+        b += n ** (dim - 1) * ((n + 31) // 32) * 12
     return b
 
 
@@ -173,6 +187,36 @@ def oracle_sample(name, cycles_full):
     return 1.0 / est, sample, oracle.num_threads(), t_cell * ns + t_asm_small + t_solve
 
 
+def oracle_full(name):
+    """The oracle run in full on a workload: FP64 assembly at the final
+    accuracy of every cell, then its FCG-preconditioned V(2,2) solve to 1e-8."""
+    import oracle
+    w = inputs.workload(name)
+    f = oracle.Field(w.eps)
+    t0 = time.perf_counter()
+    A = oracle.assemble(f, w.n_cells, w.s_final)
+    ta = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, hist, k = oracle.solve(w.dim, w.n_cells, A, rtol=1e-8, max_cycles=400)
+    ts = time.perf_counter() - t0
+    return {"workload": name, "n_cells": w.n_cells, "dim": w.dim, "s": w.s_final, "threads": oracle.num_threads(),
+            "assembly_s": ta, "solve_s": ts, "cycles": int(k), "rel_residual": float(hist[-1]),
+            "solves_per_s": 1.0 / (ta + ts)}
+
+
+def oracle_probe(names, single_names):
+    """Full oracle timings on the host cores: every workload in `names` with
+    the OpenMP team of all cores, those in `single_names` also on one thread
+    (a child process with OMP_NUM_THREADS=1)."""
+    rows = [oracle_full(nm) for nm in names]
+    for nm in single_names:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", f"import bench, json; print(json.dumps(bench.oracle_full({nm!r})))"],
+                             cwd=ROOT, env=env, capture_output=True, text=True, check=True).stdout
+        rows.append(json.loads(out.strip().splitlines()[-1]))
+    return rows
+
+
 # ---------------------------------------------------------------- arms
 def run_reference(args, rank):
     if rank != 0:
@@ -190,7 +234,9 @@ def run_reference(args, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "path": "oracle", "flush": "n/a (CPU)"},
             "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores,
+                             "kind": "oracle, extrapolated from 4000 sampled cells and a full 27^3 solve",
+                             "sample": sample},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -278,8 +324,10 @@ def run_ours(args, rank, world, local_rank):
     b_mv = sweep_bytes(dim, n, cbc, True, 8)
     peak, peak_kind = peaks()
     kernels = {
-        "sweep_jacobi_f32": {"ms": ms_sweep, "bytes": b_sweep, "gbs": b_sweep / ms_sweep / 1e6},
-        "matvec_f64": {"ms": ms_mv, "bytes": b_mv, "gbs": b_mv / ms_mv / 1e6},
+        "sweep_jacobi_f32": {"ms": ms_sweep, "bytes": b_sweep, "gbs": b_sweep / ms_sweep / 1e6,
+                             "overhead_bytes": sweep_overhead_bytes(dim, n, True, 4)},
+        "matvec_f64": {"ms": ms_mv, "bytes": b_mv, "gbs": b_mv / ms_mv / 1e6,
+                       "overhead_bytes": sweep_overhead_bytes(dim, n, True, 8)},
         "galerkin_f32": {"ms": ms_gal},
     }
     for P in probs:
@@ -294,6 +342,18 @@ def run_ours(args, rank, world, local_rank):
             inf = P.solve()
             fp64_ms.append((time.perf_counter() - t0) * 1e3)
             fp64_cycles.append(inf.cycles)
+    # mixed assemble-then-solve at the same precision: separates the effect of
+    # delayed assembly from that of FP32 smoothing and lossy storage
+    _, dmp = workload_desc(mg, args.workload, mg.PATH_MIXED_PLAIN)
+    mp_ms, mp_cycles, mp_asm = [], [], []
+    for _ in range(args.fp64_steps):
+        with mg.Problem(dmp) as P:
+            barrier()
+            t0 = time.perf_counter()
+            inf = P.solve()
+            mp_ms.append((time.perf_counter() - t0) * 1e3)
+            mp_cycles.append(inf.cycles)
+            mp_asm.append(float(inf.assembly_ms))
     # end to end through the C ABI with host buffers: create from the host
     # descriptor, solve, read u back to the host, destroy
     e2e_ms = []
@@ -319,7 +379,8 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores, _ = oracle_sample(args.workload, int(info0.cycles))
-        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "solves/s", "cores": cores,
+               "kind": "oracle, extrapolated from 4000 sampled cells and a full 27^3 solve", "sample": sample}
     if rank != 0:
         return
     walls_sorted = sorted(walls)
@@ -340,6 +401,10 @@ def run_ours(args, rank, world, local_rank):
         "cells_by_class": cbc, "stencil_bytes": int(info0.payload_bytes),
         "fp64_plain": {"solves_per_s": 1e3 / statistics.median(fp64_ms), "ms": fp64_ms, "cycles": fp64_cycles},
         "speedup_vs_fp64_plain": statistics.median(fp64_ms) / p50,
+        "mixed_plain": {"solves_per_s": 1e3 / statistics.median(mp_ms), "ms": mp_ms, "cycles": mp_cycles,
+                        "assembly_ms": mp_asm},
+        "delayed_vs_mixed_plain": statistics.median(mp_ms) / p50,
+        "cycles_per_solve": [int(i.cycles) for i in infos],
         "roofline": {"bound": "hbm", "kernel": "sweep_jacobi_f32 (finest level, V-cycle smoother)",
                      "achieved": kernels["sweep_jacobi_f32"]["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": kernels["sweep_jacobi_f32"]["gbs"] / peak, "peak_kind": peak_kind,
@@ -427,6 +492,12 @@ def run_probe(args, local_rank):
     torch.cuda.set_device(local_rank)
     if args.probe == "serving":   # --probe-reps requests, open loop at 0.5, 0.7 and 0.9 of the closed-loop rate
         print(json.dumps({"probe": "serving", **serving_leg(mg, args.probe_reps, load_factors=(0.5, 0.7, 0.9))}),
+              flush=True)
+        return
+    if args.probe == "oracle":   # the CPU oracle in full on configurations 1 and 2
+        print(json.dumps({"probe": "oracle", "nproc": os.cpu_count(),
+                          "rows": oracle_probe(["disc2d", "fourier3d"],
+                                              ["disc2d"] + (["fourier3d"] if args.oracle_single_3d else []))}),
               flush=True)
         return
     if args.probe == "solve":   # whole mixed delayed solves, for launch lists
@@ -600,11 +671,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--probe", choices=["sweep", "matvec", "residual", "galerkin", "solve", "serving", "adaptive",
-                                        "starvation", "paths", "paper_format", "cycles", "coarse"],
+    ap.add_argument("--probe", choices=["oracle", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
+                                        "adaptive", "starvation", "paths", "paper_format", "cycles", "coarse"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
     ap.add_argument("--probe-reps", type=int, default=3)
+    ap.add_argument("--oracle-single-3d", action="store_true",
+                    help="--probe oracle: also time the 81^3 workload on one thread (several minutes)")
     ap.add_argument("--max-cycles", type=int, default=600, help="cycle limit of --probe cycles")
     ap.add_argument("--n", type=int, default=None, help="cells per axis for --probe")
     args = ap.parse_args()

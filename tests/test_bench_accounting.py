@@ -14,17 +14,20 @@ import bench  # noqa: E402
 
 def test_sweep_bytes_of_the_benchmark_workload():
     # boxes3d 243^3 at s = 8: 14,212,390 cells without a surplus, 136,517 with an
-    # FP32 record.  Per vertex u, b, y (4 B each); per cell eps_c 4 B and a class
-    # byte; 112 B per FP32 record; 12 B of segment bases per 32 cells.
+    # FP32 record.  Per cell: u read, u written, b read (4 B each), eps_c 4 B and
+    # a class byte (17 B); an FP32 surplus adds 28 x 4 B + a 4-byte scale slot.
     cbc = [14212390, 0, 0, 136517]
     n = 243
-    expect = 244 ** 3 * 12 + n ** 3 * 5 + 136517 * 112 + (n ** 3 // 32) * 12
-    assert bench.sweep_bytes(3, n, cbc, True, 4) == expect == 266736683
+    expect = n ** 3 * 17 + 136517 * 116
+    assert bench.sweep_bytes(3, n, cbc, True, 4) == expect == 259767391
+    # the layout adds the vertex boundary ring and the segment bases
+    assert bench.sweep_overhead_bytes(3, n, True, 4) == (244 ** 3 - n ** 3) * 12 + n * n * 8 * 12
 
 
 def test_sweep_bytes_full_storage_and_2d():
-    assert bench.sweep_bytes(3, 27, [0, 0, 0, 0], False, 8) == 28 ** 3 * 24 + 27 ** 3 * 28 * 8
-    assert bench.sweep_bytes(2, 81, [6561, 0, 0, 0], True, 4) == 82 ** 2 * 12 + 81 ** 2 * 5 + (81 ** 2 // 32) * 12
+    assert bench.sweep_bytes(3, 27, [0, 0, 0, 0], False, 8) == 27 ** 3 * (24 + 28 * 8)
+    assert bench.sweep_bytes(2, 81, [6561, 0, 0, 0], True, 4) == 81 ** 2 * 17
+    assert bench.sweep_bytes(2, 81, [6000, 300, 200, 61], True, 4) == 81 ** 2 * 17 + 300 * 10 + 200 * 16 + 61 * 28
 
 
 def test_sweep_traffic_reads_the_committed_summary():
@@ -32,8 +35,10 @@ def test_sweep_traffic_reads_the_committed_summary():
     t = bench.sweep_traffic("boxes3d")
     if t is None:
         pytest.skip("the sweep source changed since the committed ncu summary was taken")
-    # a positive byte count within 10% of the algorithmic bytes (re-reads would show here)
-    assert abs(t - 266736683) <= 0.1 * 266736683
+    # a positive byte count within 10% of the algorithmic bytes plus the layout
+    # overhead (re-reads would show here)
+    ref = bench.sweep_bytes(3, 243, [14212390, 0, 0, 136517], True, 4) + bench.sweep_overhead_bytes(3, 243, True, 4)
+    assert abs(t - ref) <= 0.1 * ref
 
 
 def test_profile_summaries_name_their_commands_on_committed_files():
