@@ -331,6 +331,16 @@ mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
  * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_CUDA. */
 mg_status mg_profile_kernel(mg_problem* p, int which, int reps, double* ms_per_launch);
 
+/* Test hook for host-side failure injection (the paper has none; Section
+ * "Asynchronous and anarchic stencil integration" runs assembly as
+ * independent background tasks, and this checks that a failed one is
+ * reported): from now on, every side-stream assembly job of accuracy s of
+ * this problem's delayed solves ends with MG_ERR_INJECTED on the host, before
+ * any device work for that chunk; s = 0 turns it off.  mg_solve then returns
+ * MG_ERR_INJECTED at the next cycle boundary and the problem stays valid for
+ * mg_destroy_problem.  Errors: MG_ERR_INVALID (null p or s < 0). */
+mg_status mg_inject_assembly_failure(mg_problem* p, int s);
+
 /* Number of kernels of this library launched so far in this process
  * (graph replays count every kernel they contain). */
 uint64_t mg_launch_count(void);

@@ -847,14 +847,16 @@ void worker_main(mg_problem* P) {
   cudaSetDevice(P->device);
   for (;;) {
     Job job;
+    bool inject = false;
     {
       std::unique_lock<std::mutex> lk(P->mu);
       P->cv.wait(lk, [&] { return P->stop || !P->todo.empty(); });
       if (P->stop) return;
       job = P->todo.front();
       P->todo.pop_front();
+      inject = P->inject_fail != 0 && job.s == P->inject_fail;
     }
-    if (P->inject_fail && job.s == P->inject_fail) {
+    if (inject) {
       job.status = MG_ERR_INJECTED;
     } else {
       job.status = assemble_chunk(P, job.s, job.chunk, P->side, &job.store, 4);
@@ -1051,7 +1053,18 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     if (!cuda_ok(cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking), "stream")) return fail(MG_ERR_CUDA);
     P->own_stream = true;
   }
-  if (!cuda_ok(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking), "side stream")) return fail(MG_ERR_CUDA);
+  // The side stream runs at the greatest priority: its assembly proceeds at
+  // full speed and the solver's kernels fill the device around it.  (The
+  // paper's background tasks use cores the solver leaves idle; on one GPU
+  // both saturate the device, and cycles on stale stencils are the less
+  // valuable work: giving the solver precedence made the delayed solves
+  // slower, with more cycles before the final publication.)
+  {
+    int lo = 0, hi = 0;
+    if (!cuda_ok(cudaDeviceGetStreamPriorityRange(&lo, &hi), "priority range") ||
+        !cuda_ok(cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, hi), "side stream"))
+      return fail(MG_ERR_CUDA);
+  }
   // levels
   int L = 0;
   for (int n = P->N; n >= 3; n /= 3) ++L;
@@ -1427,6 +1440,8 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   P->trace_log.clear();
   double seg_rr = 0.0;
   int seg_cycles = 0;
+  double op_rr = 0.0;   // mixed paths: true residual at the first restart on the current operator
+  int op_cycles = 0;
   while (P->cycles < d.max_cycles) {
     int npub = 0;
     mg_status s = publish_ready(P, false, &npub);
@@ -1434,6 +1449,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       result = s;
       break;
     }
+    if (npub) op_rr = 0.0;
     if (npub) {   // the correction computed so far belongs to the old operator: apply it
       s = apply_inner_correction(P);
       if (s != MG_OK) return s;
@@ -1457,6 +1473,19 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       seg_rr = P->rr;
       seg_cycles = 0;
       restarted = true;
+      // the mixed paths restart at every correction; their divergence is judged
+      // against the first true residual on the current operator
+      if (P->mixed) {
+        if (op_rr == 0.0) {
+          op_rr = P->rr;
+          op_cycles = 0;
+        } else if (!std::isfinite(P->rr) || (op_cycles > 5 && P->rr > 1e4 * std::max(op_rr, 1e-300))) {
+          result = MG_ERR_DIVERGED;
+          set_error("residual diverged: ||r||^2 = %.3e after %d cycles (%.3e on this operator at first)", P->rr,
+                    P->cycles, op_rr);
+          break;
+        }
+      }
     }
     const double refn = P->ff > 0 ? P->ff : ref;
     if (P->rr <= tol2 * refn) {
@@ -1475,6 +1504,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
           result = s;
           break;
         }
+        if (npub) op_rr = 0.0;   // a new operator: its first residual is the new reference
         continue;
       }
       // not final and nothing pending: the schedule was cut short
@@ -1486,6 +1516,7 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     s = read_scalars(P);
     if (s != MG_OK) return s;
     ++seg_cycles;
+    ++op_cycles;
     {
       mg_trace_entry t{};
       t.cycle = P->cycles;
@@ -1562,6 +1593,16 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     info->payload_bytes = bytes;
   }
   return result;
+}
+
+mg_status mg_inject_assembly_failure(mg_problem* P, int s) {
+  if (!P || s < 0) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(P->mu);
+  P->inject_fail = s;
+  return MG_OK;
 }
 
 mg_status mg_get_solution(const mg_problem* P, double* host_dst, size_t n) {

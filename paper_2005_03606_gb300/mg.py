@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_version": (ctypes.c_char_p, []),
             "mg_profile_kernel": (st, [_VP, ctypes.c_int, ctypes.c_int, _D]),
             "mg_launch_count": (ctypes.c_uint64, []),
+            "mg_inject_assembly_failure": (st, [_VP, ctypes.c_int]),
             "mg_assemble_surplus_noalloc": (st, [ctypes.POINTER(mg_eps_desc), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP,
                                                  _VP]),
@@ -245,6 +246,10 @@ class Problem:
         if check:
             _check(st)
         return info
+
+    def inject_assembly_failure(self, s: int) -> None:
+        """Test hook: side-stream assembly jobs of accuracy s fail on the host."""
+        _check(load().mg_inject_assembly_failure(self.h, int(s)))
 
     def solution(self, out: Optional[np.ndarray] = None) -> np.ndarray:
         """u on the (N+1)^d vertex grid (FP64); `out`, if given, is filled

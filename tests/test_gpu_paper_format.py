@@ -105,3 +105,41 @@ def test_paper_format_rejects_bad_threshold():
             with pytest.raises(mg.MGError) as ei:
                 P.paper_format(bad)
             assert ei.value.status == mg.MG_ERR_INVALID
+
+
+E2E_CASES = [
+    (2, 27, inputs.theta_field(2, 16.0), 4, 1e-8),
+    (2, 81, inputs.disc_field(2), 8, 1e-8),
+    (3, 9, inputs.fourier_field(3, 13, sigma=1.0), 4, 1e-8),
+    (2, 27, inputs.theta_field(2, 64.0), 8, 1e-12),
+]
+
+
+@pytest.mark.parametrize("dim,n,fld,s,delta", E2E_CASES)
+def test_paper_format_end_to_end_from_oracle_matrices(dim, n, fld, s, delta):
+    """The whole chain against the oracle alone: the oracle assembles the FP64
+    element matrices, takes eps at the cell centres and encodes them; the GPU
+    assembles, encodes and decodes its own.  The decoded GPU matrices must
+    represent the oracle's exact matrices within delta plus the FP64 assembly
+    tolerance, and the byte choices may differ only in cells whose choice
+    flips within that tolerance (truncation makes it hinge on the last bit):
+    there the GPU's choice must be the oracle's choice for the GPU's own A."""
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=mg.PATH_FP64_PLAIN, s_schedule=(s,))) as P:
+        P.assemble(s)
+        A_gpu = P.element_matrices(0)
+        p3, At, _ = P.paper_format(delta, decoded=True)
+    f = oracle.Field(fld)
+    A_or = oracle.assemble(f, n, s)
+    cc = np.indices((n,) * dim).reshape(dim, -1)[::-1].T          # cell index, x fastest
+    ec = np.array([oracle.eps_at(f, [oracle.sample_coord(n, 1, int(i), 0) for i in c]) for c in cc])
+    K = _kref_closed(dim, n)
+    p_or, At_or = oracle.paper_format(dim, A_or, ec, K, delta)
+    scale = np.abs(A_or).max()
+    assert np.abs(A_gpu - A_or).max() <= 1e-12 * scale
+    assert np.abs(At - A_or).max() <= delta + 2e-12 * scale
+    assert np.abs(At_or - A_or).max() <= delta
+    diff = np.nonzero(p3.astype(np.int32) != p_or)[0]
+    assert diff.size <= max(2, 0.02 * p3.size), diff.size
+    if diff.size:
+        p_own, _ = oracle.paper_format(dim, A_gpu[diff], ec[diff], K, delta)
+        assert np.array_equal(p3[diff].astype(np.int32), p_own)
