@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
         t /= N;
       }
     }
-    const T eref = eps_c[c];
+    // reference of the surplus: the path's cell-centre eps (exact mode: FP64)
+    const T eref = A.eps64 ? (T)A.eps64[c] : eps_c[c];
     // global sample indices of the cell's first sub-box along each axis
     const int m0[3] = {ci[0] * s, ci[1] * s, D == 3 ? ci[2] * s : 0};
     // x-axis table of the group's cell
@@ -270,113 +271,197 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     T W[NW];
 #pragma unroll
     for (int q = 0; q < NW; ++q) W[q] = 0;
-
-    for (int r = lig; r < R && valid && !flat; r += G) {
-      const int jy = r % s, jz = (D == 3) ? r / s : 0;
-      // per-row set-up
-      unsigned long long rowbits = ~0ull;
-      double rowd = 0.0;
-      T rowth = (T)1;
-      T P_re[KIND == EPS_FOURIER ? MODES : 1], P_im[KIND == EPS_FOURIER ? MODES : 1];
-      const int my = m0[1] + jy, mz = m0[2] + jz;
-      if (KIND == EPS_BOXES) {
-        unsigned long long m = 0, cb = cand;
-        while (cb) {
-          int b = __ffsll((long long)cb) - 1;
-          cb &= cb - 1;
-          bool ok = TH.mlo[b][1] <= my && my < TH.mhi[b][1];
-          if (D == 3) ok = ok && TH.mlo[b][2] <= mz && mz < TH.mhi[b][2];
-          if (ok) m |= 1ull << b;
-        }
-        rowbits = m;
-      } else if (KIND == EPS_DISC) {
-        double dy = __dsub_rn(sample_x(N, s, ci[1], jy), F.center[1]);
-        rowd = __dmul_rn(dy, dy);
-      } else if (KIND == EPS_THETA) {
-        rowth = theta_factor<T>(F, sample_x(N, s, ci[1], jy));
-        if (D == 3) rowth = rowth * theta_factor<T>(F, sample_x(N, s, ci[2], jz));
-      } else if (KIND == EPS_FOURIER) {
-        int gm[3] = {m0[0], my, mz};
-        const int twoNs = 2 * N * s;
+    // Exact moments (FP64 exact mode, boxes or disc without a planar jump):
+    // eps - eps_c is (v_in - v_out) times +-1 on the samples on the other side
+    // of the discontinuity from the cell centre, and 0 elsewhere, so the
+    // moment sums are integers: with D = 6 s^2, sum_x {1, t1, t2} over those
+    // samples is {D n0, 3 s n1, 2 n2} / D (n1 = sum (2j + 1), n2 = sum
+    // (3 j^2 + 3 j + 1)), and the J-type factors of the other axes are
+    // integers over D too.  Accumulated in 64-bit integers, scaled once.
+    constexpr bool kIntPath = (KIND == EPS_BOXES || KIND == EPS_DISC) && sizeof(T) == 8;
+    const bool use_int = kIntPath && A.eps64 != nullptr && TH.mjump == INT_MAX;
+    T wscale = (T)1;
+    if (kIntPath && use_int) {
+      long long WI[NW];
 #pragma unroll
-        for (int m = 0; m < MODES; ++m) {
-          P_re[m] = 0;
-          P_im[m] = 0;
-          if (m < F.n_modes) {
-            int n = phase_num(F, m, D, gm, twoNs);
-            T sn, cs;
-            t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
-            P_re[m] = cs;
-            P_im[m] = sn;
+      for (int q = 0; q < NW; ++q) WI[q] = 0;
+      const int Dd = 6 * s * s;
+      const bool cin = eref == vin;   // the cell centre lies inside
+      for (int r = lig; r < R && valid && !flat; r += G) {
+        const int jy = r % s, jz = (D == 3) ? r / s : 0;
+        const int my = m0[1] + jy, mz = m0[2] + jz;
+        unsigned long long rowbits = 0;
+        double rowd = 0.0;
+        if (KIND == EPS_BOXES) {
+          unsigned long long cb = cand;
+          while (cb) {
+            int b = __ffsll((long long)cb) - 1;
+            cb &= cb - 1;
+            bool ok = TH.mlo[b][1] <= my && my < TH.mhi[b][1];
+            if (D == 3) ok = ok && TH.mlo[b][2] <= mz && mz < TH.mhi[b][2];
+            if (ok) rowbits |= 1ull << b;
           }
-        }
-      }
-      double dz2 = 0.0;
-      if (KIND == EPS_DISC && D == 3) {
-        double dz = __dsub_rn(sample_x(N, s, ci[2], jz), F.center[2]);
-        dz2 = __dmul_rn(dz, dz);
-      }
-      T S0 = 0, S1 = 0, S2 = 0;
-      for (int jx = 0; jx < s; ++jx) {
-        const XEntryT<T>& xe = xt[grp * xt_stride + jx];
-        T e;
-        if (KIND == EPS_CONST) {
-          e = vout;
-        } else if (KIND == EPS_BOXES) {
-          e = (xe.bits & rowbits) ? vin : vout;
-        } else if (KIND == EPS_DISC) {
-          double r2 = __dadd_rn(__longlong_as_double((long long)xe.bits), rowd);
-          if (D == 3) r2 = __dadd_rn(r2, dz2);
-          e = r2 < F.r2lim ? vin : vout;
-        } else if (KIND == EPS_THETA) {
-          e = (T)1 + (T)(0.3 / D) * (xe.th * rowth);
         } else {
-          // g = sum_m Re(P_m X_m[jx]) (modes beyond n_modes have P = 0)
-          T g = 0;
+          double dy = __dsub_rn(sample_x(N, s, ci[1], jy), F.center[1]);
+          rowd = __dmul_rn(dy, dy);
+          if (D == 3) {
+            double dz = __dsub_rn(sample_x(N, s, ci[2], jz), F.center[2]);
+            rowd = __dadd_rn(rowd, __dmul_rn(dz, dz));
+          }
+        }
+        int n0 = 0, n1 = 0, n2 = 0;
+        for (int jx = 0; jx < s; ++jx) {
+          const XEntryT<T>& xe = xt[grp * xt_stride + jx];
+          bool inside;
+          if (KIND == EPS_BOXES) inside = (xe.bits & rowbits) != 0;
+          else inside = __dadd_rn(__longlong_as_double((long long)xe.bits), rowd) < F.r2lim;
+          if (inside != cin) {
+            n0 += 1;
+            n1 += 2 * jx + 1;
+            n2 += 3 * jx * jx + 3 * jx + 1;
+          }
+        }
+        const int X0 = Dd * n0, X1 = 3 * s * n1, X2 = 2 * n2;
+        const int RJ[3] = {X0 - 2 * X1 + X2, X1 - X2, X2};
+        const int Y1 = 3 * s * (2 * jy + 1), Y2 = 2 * (3 * jy * jy + 3 * jy + 1);
+        const int Jy[3] = {Dd - 2 * Y1 + Y2, Y1 - Y2, Y2};
+        if (D == 2) {
 #pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            WI[t] += (long long)n0 * Jy[t];
+            WI[3 + t] += RJ[t];
+          }
+        } else {
+          const int Z1 = 3 * s * (2 * jz + 1), Z2 = 2 * (3 * jz * jz + 3 * jz + 1);
+          const int Jz[3] = {Dd - 2 * Z1 + Z2, Z1 - Z2, Z2};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int p0 = n0 * Jy[a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              WI[a * 3 + b] += (long long)p0 * Jz[b];
+              WI[9 + a * 3 + b] += (long long)RJ[a] * Jz[b];
+              WI[18 + a * 3 + b] += (long long)RJ[a] * Jy[b];
+            }
+          }
+        }
+      }
+      for (int off = G / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) WI[q] += __shfl_xor_sync(0xffffffffu, WI[q], off);
+      }
+#pragma unroll
+      for (int q = 0; q < NW; ++q) W[q] = (T)WI[q];
+      const T dv = cin ? vout - vin : vin - vout;
+      wscale = D == 3 ? dv / ((T)Dd * (T)Dd) : dv / (T)Dd;
+    } else {
+      for (int r = lig; r < R && valid && !flat; r += G) {
+        const int jy = r % s, jz = (D == 3) ? r / s : 0;
+        // per-row set-up
+        unsigned long long rowbits = ~0ull;
+        double rowd = 0.0;
+        T rowth = (T)1;
+        T P_re[KIND == EPS_FOURIER ? MODES : 1], P_im[KIND == EPS_FOURIER ? MODES : 1];
+        const int my = m0[1] + jy, mz = m0[2] + jz;
+        if (KIND == EPS_BOXES) {
+          unsigned long long m = 0, cb = cand;
+          while (cb) {
+            int b = __ffsll((long long)cb) - 1;
+            cb &= cb - 1;
+            bool ok = TH.mlo[b][1] <= my && my < TH.mhi[b][1];
+            if (D == 3) ok = ok && TH.mlo[b][2] <= mz && mz < TH.mhi[b][2];
+            if (ok) m |= 1ull << b;
+          }
+          rowbits = m;
+        } else if (KIND == EPS_DISC) {
+          double dy = __dsub_rn(sample_x(N, s, ci[1], jy), F.center[1]);
+          rowd = __dmul_rn(dy, dy);
+        } else if (KIND == EPS_THETA) {
+          rowth = theta_factor<T>(F, sample_x(N, s, ci[1], jy));
+          if (D == 3) rowth = rowth * theta_factor<T>(F, sample_x(N, s, ci[2], jz));
+        } else if (KIND == EPS_FOURIER) {
+          int gm[3] = {m0[0], my, mz};
+          const int twoNs = 2 * N * s;
+  #pragma unroll
           for (int m = 0; m < MODES; ++m) {
-            const Cplx<T> x = s_X[m][jx];
-            g = fma(P_re[m], x.c, g);
-            g = fma(-P_im[m], x.s, g);
+            P_re[m] = 0;
+            P_im[m] = 0;
+            if (m < F.n_modes) {
+              int n = phase_num(F, m, D, gm, twoNs);
+              T sn, cs;
+              t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
+              P_re[m] = cs;
+              P_im[m] = sn;
+            }
           }
-          e = vout * t_exp<T>(FT.amp * g);
         }
-        e *= xe.jmul;
-        const T ep = e - eref;
-        S0 += ep;
-        S1 += ep * s_t1[jx];
-        S2 += ep * s_t2[jx];
-      }
-      // J-type sums along x: (1-t)^2 = 1 - 2t + t^2, t(1-t) = t - t^2, t^2
-      const T RJ[3] = {S0 - (T)2 * S1 + S2, S1 - S2, S2};
-      const T t1y = s_t1[jy], t2y = s_t2[jy];
-      const T jyv[3] = {(T)1 - (T)2 * t1y + t2y, t1y - t2y, t2y};
-      if (D == 2) {
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          W[t] += S0 * jyv[t];      // d/dx term: other axis y
-          W[3 + t] += RJ[t];        // d/dy term: other axis x
+        double dz2 = 0.0;
+        if (KIND == EPS_DISC && D == 3) {
+          double dz = __dsub_rn(sample_x(N, s, ci[2], jz), F.center[2]);
+          dz2 = __dmul_rn(dz, dz);
         }
-      } else {
-        const T t1z = s_t1[jz], t2z = s_t2[jz];
-        const T jzv[3] = {(T)1 - (T)2 * t1z + t2z, t1z - t2z, t2z};
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            W[a * 3 + b] += S0 * jyv[a] * jzv[b];      // d/dx: (y, z)
-            W[9 + a * 3 + b] += RJ[a] * jzv[b];        // d/dy: (x, z)
-            W[18 + a * 3 + b] += RJ[a] * jyv[b];       // d/dz: (x, y)
+        T S0 = 0, S1 = 0, S2 = 0;
+        for (int jx = 0; jx < s; ++jx) {
+          const XEntryT<T>& xe = xt[grp * xt_stride + jx];
+          T e;
+          if (KIND == EPS_CONST) {
+            e = vout;
+          } else if (KIND == EPS_BOXES) {
+            e = (xe.bits & rowbits) ? vin : vout;
+          } else if (KIND == EPS_DISC) {
+            double r2 = __dadd_rn(__longlong_as_double((long long)xe.bits), rowd);
+            if (D == 3) r2 = __dadd_rn(r2, dz2);
+            e = r2 < F.r2lim ? vin : vout;
+          } else if (KIND == EPS_THETA) {
+            e = (T)1 + (T)(0.3 / D) * (xe.th * rowth);
+          } else {
+            // g = sum_m Re(P_m X_m[jx]) (modes beyond n_modes have P = 0)
+            T g = 0;
+  #pragma unroll
+            for (int m = 0; m < MODES; ++m) {
+              const Cplx<T> x = s_X[m][jx];
+              g = fma(P_re[m], x.c, g);
+              g = fma(-P_im[m], x.s, g);
+            }
+            e = vout * t_exp<T>(FT.amp * g);
           }
+          e *= xe.jmul;
+          const T ep = e - eref;
+          S0 += ep;
+          S1 += ep * s_t1[jx];
+          S2 += ep * s_t2[jx];
+        }
+        // J-type sums along x: (1-t)^2 = 1 - 2t + t^2, t(1-t) = t - t^2, t^2
+        const T RJ[3] = {S0 - (T)2 * S1 + S2, S1 - S2, S2};
+        const T t1y = s_t1[jy], t2y = s_t2[jy];
+        const T jyv[3] = {(T)1 - (T)2 * t1y + t2y, t1y - t2y, t2y};
+        if (D == 2) {
+  #pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            W[t] += S0 * jyv[t];      // d/dx term: other axis y
+            W[3 + t] += RJ[t];        // d/dy term: other axis x
+          }
+        } else {
+          const T t1z = s_t1[jz], t2z = s_t2[jz];
+          const T jzv[3] = {(T)1 - (T)2 * t1z + t2z, t1z - t2z, t2z};
+  #pragma unroll
+          for (int a = 0; a < 3; ++a)
+  #pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              W[a * 3 + b] += S0 * jyv[a] * jzv[b];      // d/dx: (y, z)
+              W[9 + a * 3 + b] += RJ[a] * jzv[b];        // d/dy: (x, z)
+              W[18 + a * 3 + b] += RJ[a] * jyv[b];       // d/dz: (x, y)
+            }
+        }
       }
-    }
-    // reduce over the group's lanes
-    for (int off = G / 2; off >= 1; off >>= 1) {
-#pragma unroll
-      for (int q = 0; q < NW; ++q) W[q] += __shfl_xor_sync(0xffffffffu, W[q], off);
+      // reduce over the group's lanes
+      for (int off = G / 2; off >= 1; off >>= 1) {
+  #pragma unroll
+        for (int q = 0; q < NW; ++q) W[q] += __shfl_xor_sync(0xffffffffu, W[q], off);
+      }
     }
     if (lig == 0 && valid) {
-      T scale = (T)A.hfac;
+      T scale = (T)A.hfac * wscale;
       for (int a = 0; a < D; ++a) scale *= invs;
       T dl[NP];
 #pragma unroll
@@ -413,6 +498,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
             const T vn = geo + dl[p];
             T vo;
             if (A.prec64) vo = (T)A.prev_full[(long long)p * A.ncell + lc];
+            else if (A.eps64) vo = geo + (A.prev_x64 ? (T)A.prev_x64[(size_t)A.xpos[c] * NP + p] : (T)0);
             else vo = geo + (pcls ? (T)decode_entry<D>(prec, pcls, p) : (T)0);
             num = fmax(num, fabs(vn - vo));
             den = fmax(den, fabs(vo));
@@ -440,49 +526,61 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
                 (double)eref * kref_off<D>(popc_small(a ^ b)) * A.hfac + (double)dl[p];
           }
       } else {
-        // storage class from the surplus size (rule also used by the oracle, in FP32 here)
-        float Dm = 0.f, An = 0.f;
-        float rs[NV];
+        // storage class from the surplus size (the oracle's rule; in FP32 on
+        // the FP32 assembly, in FP64 in exact mode).  The records hold the
+        // surplus against the FP32 cell-centre stencil: in exact mode the
+        // integration ran against the FP64 one, and d = dl + (e64 - e32) K h.
+        T Dm = 0, An = 0;
+        T rs[NV], d32[NP];
 #pragma unroll
-        for (int a = 0; a < NV; ++a) rs[a] = 0.f;
-        const float ge = (float)eref * (float)A.hfac;
+        for (int a = 0; a < NV; ++a) rs[a] = 0;
+        const T ge = eref * (T)A.hfac;
+        const T ge32 = A.eps64 ? (T)reinterpret_cast<const float*>(A.eps_c)[c] * (T)A.hfac : ge;
 #pragma unroll
         for (int a = 0; a < NV; ++a)
 #pragma unroll
           for (int b = a + 1; b < NV; ++b) {
             const int p = pair_index(NV, a, b);
-            const float d = (float)dl[p];
-            Dm = fmaxf(Dm, fabsf(d));
-            An = fmaxf(An, fabsf(ge * (float)kref_off<D>(popc_small(a ^ b)) + d));
-            rs[a] += d;
-            rs[b] += d;
+            const T kv = (T)kref_off<D>(popc_small(a ^ b));
+            const T full = ge * kv + dl[p];
+            const T d = full - ge32 * kv;
+            d32[p] = A.eps64 ? d : dl[p];
+            Dm = fmax(Dm, fabs(d32[p]));
+            An = fmax(An, fabs(full));
+            rs[a] += dl[p];
+            rs[b] += dl[p];
           }
 #pragma unroll
-        for (int a = 0; a < NV; ++a) An = fmaxf(An, fabsf(ge * (float)kref_diag<D>() - rs[a]));
-        const float Fm = (float)Dim<D>::F, tau = (float)A.tau;
+        for (int a = 0; a < NV; ++a) An = fmax(An, fabs(ge * (T)kref_diag<D>() - rs[a]));
+        if (A.out_x64) {
+          double* o = A.out_x64 + (size_t)A.xpos[c] * NP;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) o[p] = (double)dl[p];
+        }
+        const T Fm = (T)Dim<D>::F, tau = (T)A.tau;
         int cls;
         if (Fm * Dm <= tau * An) cls = 0;
-        else if (Fm * Dm * (16.f / 448.f) <= tau * An) cls = 1;
-        else if (Fm * Dm * (16.f / 65504.f) <= tau * An) cls = 2;
+        else if (Fm * Dm * ((T)16 / (T)448) <= tau * An) cls = 1;
+        else if (Fm * Dm * ((T)16 / (T)65504) <= tau * An) cls = 2;
         else cls = 3;
         uint8_t* rec = A.out_rec + (size_t)lc * Dim<D>::REC_MAX;
         if (cls == 1) {
-          const float sc = Dm / 448.f;
+          const float sc = (float)(Dm / (T)448);
           *reinterpret_cast<float*>(rec) = sc;
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
-            __nv_fp8_e4m3 q((float)dl[p] / sc);
+            __nv_fp8_e4m3 q((float)(d32[p] / (T)sc));
             rec[4 + p] = q.__x;
           }
         } else if (cls == 2) {
-          const float sc = Dm / 65504.f;
+          const float sc = (float)(Dm / (T)65504);
           *reinterpret_cast<float*>(rec) = sc;
 #pragma unroll
           for (int p = 0; p < NP; ++p)
-            *reinterpret_cast<__half*>(rec + 4 + 2 * p) = __float2half_rn((float)dl[p] / sc);
+            *reinterpret_cast<__half*>(rec + 4 + 2 * p) = __float2half_rn((float)(d32[p] / (T)sc));
         } else if (cls == 3) {
 #pragma unroll
-          for (int p = 0; p < NP; ++p) *reinterpret_cast<float*>(rec + 4 * p) = (float)dl[p];
+          for (int p = 0; p < NP; ++p) *reinterpret_cast<float*>(rec + 4 * p) = (float)d32[p];
         }
         const long long row = lc / N;
         const int x = (int)(lc - row * N);
@@ -691,14 +789,65 @@ __global__ void mark_disc_kernel(const EpsDev F, int N, uint8_t* __restrict__ fl
 }
 
 // local index of every flagged cell appended to its chunk's list
-__global__ void flags_to_lists_kernel(long long ncell, long long chunk_cells, const uint8_t* __restrict__ flags,
-                                      int* __restrict__ lists, int* __restrict__ counts) {
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    if (!flags[c]) continue;
-    const int ch = (int)(c / chunk_cells);
-    const int pos = atomicAdd(&counts[ch], 1);
-    lists[(long long)ch * chunk_cells + pos] = (int)(c - (long long)ch * chunk_cells);
+// Ordered compaction of the flagged cells into per-chunk lists (local cell
+// indices, ascending): tiles of kListTile cells per chunk count their flags,
+// one block per chunk scans the tile counts, and each tile writes its cells
+// at its offset in cell order (so that two problems with the same field get
+// the same list, and data kept in list order can move between them).
+constexpr int kListTile = 1024;
+
+__global__ void __launch_bounds__(kListTile) list_tile_count_kernel(long long chunk_cells, int ntpc,
+                                                                    const uint8_t* __restrict__ flags,
+                                                                    int* __restrict__ tcount) {
+  const int ch = blockIdx.x / ntpc, t = blockIdx.x % ntpc;
+  const long long lc = (long long)t * kListTile + threadIdx.x;
+  const int f = lc < chunk_cells && flags[(long long)ch * chunk_cells + lc] ? 1 : 0;
+  const int n = __syncthreads_count(f);
+  if (threadIdx.x == 0) tcount[blockIdx.x] = n;
+}
+
+__global__ void __launch_bounds__(1024) list_tile_scan_kernel(int ntpc, int* __restrict__ tcount,
+                                                              int* __restrict__ counts) {
+  __shared__ int part[1024];
+  int* c = tcount + (long long)blockIdx.x * ntpc;
+  const int per = (ntpc + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = min(b0 + per, ntpc);
+  int sum = 0;
+  for (int i = b0; i < b1; ++i) sum += c[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - sum;
+  for (int i = b0; i < b1; ++i) {
+    const int v = c[i];
+    c[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == blockDim.x - 1) counts[blockIdx.x] = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kListTile) list_tile_write_kernel(long long chunk_cells, int ntpc,
+                                                                    const uint8_t* __restrict__ flags,
+                                                                    const int* __restrict__ toff,
+                                                                    int* __restrict__ lists) {
+  __shared__ int wsum[kListTile / 32];
+  const int ch = blockIdx.x / ntpc, t = blockIdx.x % ntpc;
+  const long long lc = (long long)t * kListTile + threadIdx.x;
+  const bool f = lc < chunk_cells && flags[(long long)ch * chunk_cells + lc];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) wsum[warp] = __popc(m);
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  if (f) {
+    const int pos = toff[blockIdx.x] + before + __popc(m & ((1u << lane) - 1u));
+    lists[(long long)ch * chunk_cells + pos] = (int)lc;
   }
 }
 
@@ -883,8 +1032,23 @@ cudaError_t launch_interface_cells(int dim, int N, const EpsDev* eps, long long 
     e = launched();
   }
   if (e == cudaSuccess) {
-    flags_to_lists_kernel<<<grid_for(ncell, 256), 256, 0, st>>>(ncell, chunk_cells, flags, lists, counts);
-    e = launched();
+    const int nchunk = (int)(ncell / chunk_cells);
+    const int ntpc = (int)((chunk_cells + kListTile - 1) / kListTile);
+    int* tcount = nullptr;
+    e = mg_malloc_async(&tcount, sizeof(int) * (size_t)nchunk * ntpc, st);
+    if (e == cudaSuccess) {
+      list_tile_count_kernel<<<nchunk * ntpc, kListTile, 0, st>>>(chunk_cells, ntpc, flags, tcount);
+      e = launched();
+    }
+    if (e == cudaSuccess) {
+      list_tile_scan_kernel<<<nchunk, 1024, 0, st>>>(ntpc, tcount, counts);
+      e = launched();
+    }
+    if (e == cudaSuccess) {
+      list_tile_write_kernel<<<nchunk * ntpc, kListTile, 0, st>>>(chunk_cells, ntpc, flags, tcount, lists);
+      e = launched();
+    }
+    if (tcount) cudaFreeAsync(tcount, st);
   }
   if (d_regs) cudaFreeAsync(d_regs, st);
   if (d_start) cudaFreeAsync(d_start, st);
@@ -909,8 +1073,9 @@ cudaError_t launch_eps_centre(int dim, int N, const EpsDev* eps, int prec64, voi
 
 cudaError_t launch_assemble(const AsmLaunch& a, cudaStream_t st) {
   if (a.s < 1 || a.s > kMaxS) return cudaErrorInvalidValue;
-  if (a.dim == 2) return a.prec64 ? launch_assemble_t<2, double>(a, st) : launch_assemble_t<2, float>(a, st);
-  return a.prec64 ? launch_assemble_t<3, double>(a, st) : launch_assemble_t<3, float>(a, st);
+  const bool f64 = a.prec64 || a.eps64;   // FP64 arithmetic: FP64 paths and the exact mode
+  if (a.dim == 2) return f64 ? launch_assemble_t<2, double>(a, st) : launch_assemble_t<2, float>(a, st);
+  return f64 ? launch_assemble_t<3, double>(a, st) : launch_assemble_t<3, float>(a, st);
 }
 
 cudaError_t launch_geometric_full(int dim, int N, double hfac, const double* eps_c, long long cell0,

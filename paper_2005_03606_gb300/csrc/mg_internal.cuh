@@ -92,6 +92,9 @@ struct CmpChunk {
   const uint32_t* seg_base;
   const uint8_t* pool[3];
   long long nseg;
+  // exact FP64 surplus of the chunk's interface cells [list position][NP]
+  // (piecewise-constant fields on the mixed paths; nullptr: all zero, s = 1)
+  const double* x64;
 };
 
 // Full storage: SoA off-diagonals a[p * chunk_cells + local_cell].
@@ -130,6 +133,16 @@ struct LevelOp {
   // the neighbour at block offset C + m (C the centre of the 3^d block); the
   // coupling to C - m is the neighbour's entry m.  Rebuilt with the cell matrices.
   const void* stencil;
+  // Exact FP64 operator of the mixed paths on piecewise-constant fields (the
+  // FP64 outer residual and matvec read it; the FP32 sweeps read the lossy
+  // records): FP64 cell-centre eps of every cell, the position of each cell
+  // in its chunk's interface list (-1: no surplus) and the vertices next to
+  // an interface cell.  eps64 == nullptr: the FP64 applications use the
+  // stored (lossy) operator.
+  const double* eps64;
+  const int* xpos;
+  const int* touched64;
+  const int* ntouched64;
 };
 
 // ------------------------------------------------------------ helpers
@@ -239,6 +252,14 @@ struct AsmLaunch {
   uint8_t* final_flags;
   uint8_t* s_cell;
   double adapt_C;
+  // exact surplus of the mixed paths (eps64 != nullptr): FP64 arithmetic with
+  // eps64 as the reference, the lossy records against the FP32 eps_c, and
+  // the FP64 surplus written to out_x64 at the cell's list position xpos;
+  // prev_x64: the previous level's exact surplus for the adaptive test
+  const double* eps64;
+  double* out_x64;
+  const int* xpos;
+  const double* prev_x64;
 };
 // adaptive accuracy, before the integration of one chunk at a new level: the
 // cells already final keep their previous matrix (copied into the new store:
@@ -300,8 +321,13 @@ bool vcycle_tail_supported(const LevelOp& op);
 cudaError_t launch_vcycle_tail(const LevelOp& op, const double* Lc, const float* b, float* x, float omega,
                                int nu_pre, int nu_post, cudaStream_t st);
 cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream_t st);
+// from_xpos = 0: vertices next to a cell with a surplus record (and their
+// stencil table); 1: vertices next to an interface cell (op.xpos >= 0)
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int from_xpos = 0);
+// xpos[chunk * chunk_cells + list[chunk][i]] = i for every interface cell, -1 elsewhere
+cudaError_t launch_xpos(long long chunk_cells, int nchunk, const int* lists, const int* counts_host, int* xpos,
+                        cudaStream_t st);
 
 // vector ops for the outer loop (FP64 vectors; n = vertices)
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks,

@@ -78,6 +78,7 @@ struct ChunkStore {
   uint8_t* pool[3] = {nullptr, nullptr, nullptr};
   uint32_t totals[3] = {0, 0, 0};
   size_t bytes = 0;
+  double* x64 = nullptr;          // exact mode: FP64 surplus [interface list][NP] (nullptr at s = 1)
 };
 
 struct Level {
@@ -131,6 +132,12 @@ struct mg_problem {
   uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
   // interface cells per chunk (fields with piecewise-constant eps): only these
   // are integrated at s > 1, every other cell keeps its geometric stencil
+  // exact FP64 operator of the mixed paths on piecewise-constant fields
+  bool exact = false;
+  double* eps64 = nullptr;        // FP64 cell-centre eps
+  int* xpos = nullptr;            // per cell: position in its chunk's interface list, -1 if none
+  int* touched64 = nullptr;       // 3D split residual: vertices next to an interface cell
+  int* ntouched64 = nullptr;
   int* ilist = nullptr;           // [nchunk][chunk_cells] local cell indices
   std::vector<int> ilist_n;       // count per chunk (host)
   std::vector<mg_trace_entry> trace_log;   // per outer iteration of the last solve
@@ -486,6 +493,21 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
     a.list = P->ilist + (size_t)chunk * P->chunk_cells;
     a.nlist = P->ilist_n[chunk];
   }
+  if (P->exact && P->ilist_n[chunk] > 0) {
+    // FP64 integration of the interface cells; the exact surplus goes to the
+    // store's list-ordered FP64 array (adaptive: final cells keep the
+    // previous level's entries)
+    const size_t xb = sizeof(double) * NP * (size_t)P->ilist_n[chunk];
+    if ((e = mg_malloc_async(&cs.x64, xb, st)) != cudaSuccess) return oom_or_cuda(e, "exact surplus");
+    cs.bytes += xb;
+    const double* px = judge ? P->wlast[chunk].x64 : nullptr;
+    if (px) MG_CHECK(cudaMemcpyAsync(cs.x64, px, xb, cudaMemcpyDeviceToDevice, st));
+    else if (judge) MG_CHECK(cudaMemsetAsync(cs.x64, 0, xb, st));
+    a.eps64 = P->eps64;
+    a.out_x64 = cs.x64;
+    a.xpos = P->xpos;
+    a.prev_x64 = px;
+  }
   if ((!P->ilist && !judge) || a.nlist > 0) MG_CHECK(launch_assemble(a, st));
   uint32_t* dt = P->d_totals + tot_slot;
   uint32_t* ht = P->h_totals + tot_slot;
@@ -514,6 +536,7 @@ void free_store(ChunkStore& cs, cudaStream_t st) {
   if (cs.seg_base) cudaFreeAsync(cs.seg_base, st);
   for (int k = 0; k < 3; ++k)
     if (cs.pool[k]) cudaFreeAsync(cs.pool[k], st);
+  if (cs.x64) cudaFreeAsync(cs.x64, st);
   cs = ChunkStore();
 }
 
@@ -527,6 +550,7 @@ void install(mg_problem* P, int chunk, const ChunkStore& cs) {
     c.seg_base = cs.seg_base;
     for (int k = 0; k < 3; ++k) c.pool[k] = cs.pool[k];
     c.nseg = P->chunk_nseg;
+    c.x64 = cs.x64;
     P->h_cmp[chunk] = c;
   } else {
     P->h_full[chunk].a = cs.a64;
@@ -1270,6 +1294,32 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
       return fail(MG_ERR_CUDA);
     cudaFreeAsync(counts, P->st);
   }
+  // Mixed paths on piecewise-constant fields: the FP64 outer residual and
+  // matvec apply the exact FP64 operator (FP64 cell-centre eps everywhere,
+  // FP64 surplus of the interface cells, which are integrated in FP64), so
+  // that the solution meets the residual target under the operator the FP64
+  // paths assemble; the FP32 V-cycle keeps reading the lossy records.
+  if (P->mixed && P->ilist && !getenv("MG_LOSSY_RESIDUAL")) {
+    P->exact = true;
+    if ((e = dalloc(P, &P->eps64, sizeof(double) * (size_t)l0.ncell)) != cudaSuccess ||
+        (e = dalloc(P, &P->xpos, sizeof(int) * (size_t)l0.ncell)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "exact operator"));
+    if (!cuda_ok(launch_eps_centre(D, P->N, &P->eps, 1, P->eps64, P->st), "eps centre") ||
+        !cuda_ok(launch_xpos(P->chunk_cells, P->nchunk, P->ilist, P->ilist_n.data(), P->xpos, P->st), "positions"))
+      return fail(MG_ERR_CUDA);
+    l0.op.eps64 = P->eps64;
+    l0.op.xpos = P->xpos;
+    if (P->touched) {
+      if ((e = dalloc(P, &P->touched64, sizeof(int) * (size_t)l0.nvert)) != cudaSuccess ||
+          (e = dalloc(P, &P->ntouched64, sizeof(int))) != cudaSuccess)
+        return fail(oom_or_cuda(e, "exact touched list"));
+      if (!cuda_ok(launch_build_touched(l0.op, P->tflags, P->tcounts, P->touched64, P->ntouched64, P->st, 1),
+                   "exact touched list"))
+        return fail(MG_ERR_CUDA);
+      l0.op.touched64 = P->touched64;
+      l0.op.ntouched64 = P->ntouched64;
+    }
+  }
   if (d.adapt_C > 0.0 && d.n_s >= 2) {
     P->adapt = true;
     P->wlast.resize(P->nchunk);
@@ -1750,8 +1800,9 @@ struct StateHeader {
   int32_t dim, n_cells, mixed, nchunk;
   int64_t chunk_cells, chunk_nseg, nvert;
   int32_t adapt, np;
+  int32_t exact, pad0;
 };
-constexpr char kStateMagic[8] = {'M', 'G', 'S', 'T', 'A', 'T', 'E', '1'};
+constexpr char kStateMagic[8] = {'M', 'G', 'S', 'T', 'A', 'T', 'E', '2'};
 
 struct ChunkHeader {
   int32_t s;
@@ -1762,6 +1813,12 @@ struct ChunkHeader {
 int pool_rec_bytes(int dim, int k) {
   static const int r3[3] = {32, 64, 112}, r2[3] = {16, 16, 32};
   return dim == 3 ? r3[k] : r2[k];
+}
+
+// exact mode: the FP64 surplus of a chunk's interface cells (none at s = 1)
+size_t exact_state_bytes(const mg_problem* P, int chunk, int s) {
+  const int NP = P->dim == 3 ? 28 : 6;
+  return P->exact && s > 1 ? sizeof(double) * NP * (size_t)P->ilist_n[chunk] : 0;
 }
 
 size_t chunk_state_bytes(const mg_problem* P, const uint32_t totals[3]) {
@@ -1791,7 +1848,8 @@ mg_status mg_export_state(mg_problem* P, void* buf, size_t cap, size_t* size) {
   if (s != MG_OK) return s;
   const Level& l0 = P->lev[0];
   size_t total = sizeof(StateHeader) + sizeof(double) * (size_t)l0.nvert;
-  for (const ChunkStore& c : P->cur) total += sizeof(ChunkHeader) + chunk_state_bytes(P, c.totals);
+  for (int c = 0; c < P->nchunk; ++c)
+    total += sizeof(ChunkHeader) + chunk_state_bytes(P, P->cur[c].totals) + exact_state_bytes(P, c, P->cur[c].s);
   if (P->adapt) total += 2 * (size_t)P->chunk_cells * P->nchunk;
   *size = total;
   if (!buf) return MG_OK;
@@ -1812,11 +1870,13 @@ mg_status mg_export_state(mg_problem* P, void* buf, size_t cap, size_t* size) {
   h.nvert = l0.nvert;
   h.adapt = P->adapt ? 1 : 0;
   h.np = P->dim == 3 ? 28 : 6;
+  h.exact = P->exact ? 1 : 0;
   memcpy(w, &h, sizeof(h));
   w += sizeof(h);
   MG_CHECK(cudaMemcpy(w, P->u, sizeof(double) * (size_t)l0.nvert, cudaMemcpyDeviceToHost));
   w += sizeof(double) * (size_t)l0.nvert;
-  for (const ChunkStore& c : P->cur) {
+  for (int ci = 0; ci < P->nchunk; ++ci) {
+    const ChunkStore& c = P->cur[ci];
     ChunkHeader ch{};
     ch.s = c.s;
     for (int k = 0; k < 3; ++k) ch.totals[k] = c.totals[k];
@@ -1838,6 +1898,9 @@ mg_status mg_export_state(mg_problem* P, void* buf, size_t cap, size_t* size) {
       if (pb) MG_CHECK(cudaMemcpy(w, c.pool[k], pb, cudaMemcpyDeviceToHost));
       w += pb;
     }
+    const size_t xb = exact_state_bytes(P, ci, c.s);
+    if (xb) MG_CHECK(cudaMemcpy(w, c.x64, xb, cudaMemcpyDeviceToHost));
+    w += xb;
   }
   if (P->adapt) {
     const size_t nc = (size_t)P->chunk_cells * P->nchunk;
@@ -1865,7 +1928,8 @@ mg_status mg_import_state(mg_problem* P, const void* buf, size_t size) {
   const Level& l0 = P->lev[0];
   if (memcmp(h.magic, kStateMagic, 8) != 0 || h.dim != P->dim || h.n_cells != P->N ||
       h.mixed != (P->mixed ? 1 : 0) || h.nchunk != P->nchunk || h.chunk_cells != P->chunk_cells ||
-      h.chunk_nseg != P->chunk_nseg || h.nvert != l0.nvert || h.adapt != (P->adapt ? 1 : 0)) {
+      h.chunk_nseg != P->chunk_nseg || h.nvert != l0.nvert || h.adapt != (P->adapt ? 1 : 0) ||
+      h.exact != (P->exact ? 1 : 0)) {
     set_error("not a state of a problem with this descriptor");
     return MG_ERR_INVALID;
   }
@@ -1883,7 +1947,7 @@ mg_status mg_import_state(mg_problem* P, const void* buf, size_t size) {
       set_error("corrupt chunk header");
       return MG_ERR_INVALID;
     }
-    q += sizeof(ChunkHeader) + chunk_state_bytes(P, chs[c].totals);
+    q += sizeof(ChunkHeader) + chunk_state_bytes(P, chs[c].totals) + exact_state_bytes(P, c, chs[c].s);
   }
   if (P->adapt) q += 2 * (size_t)P->chunk_cells * P->nchunk;
   if (q != end) {
@@ -1923,6 +1987,13 @@ mg_status mg_import_state(mg_problem* P, const void* buf, size_t size) {
         }
         cs.bytes += pb;
         r += pb;
+      }
+      const size_t xb = exact_state_bytes(P, c, cs.s);
+      if (xb) {
+        if ((e = mg_malloc_async(&cs.x64, xb, st)) != cudaSuccess) return oom_or_cuda(e, "exact surplus");
+        MG_CHECK(cudaMemcpyAsync(cs.x64, r, xb, cudaMemcpyHostToDevice, st));
+        cs.bytes += xb;
+        r += xb;
       }
     }
     // the copies read pageable host memory: they are staged before the call returns

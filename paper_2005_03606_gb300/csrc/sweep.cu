@@ -60,7 +60,32 @@ __device__ __forceinline__ void vertex_apply(const LevelOp& op, int i, int j, in
         const int oy = D == 3 ? om : ol, oz = D == 3 ? ol : 0;
         const int a = (1 - ox) | ((1 - oy) << 1) | (D == 3 ? (1 - oz) << 2 : 0);
         const TA u_a = u[D == 3 ? 13 : 4];
-        if (CMP) {
+        if (CMP && sizeof(TA) == 8 && op.eps64) {
+          // exact FP64 operator: FP64 eps_c K_ref h^(d-2) + the exact surplus of interface cells
+          const TA ge = (TA)__ldg(op.eps64 + cbase + cx) * (TA)op.hfac;
+#pragma unroll
+          for (int b = 0; b < NV; ++b) {
+            if (b == a) continue;
+            const double kv = kref_off<D>(popc_small(a ^ b));
+            if (kv == 0.0) continue;
+            const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+            acc += ge * (TA)kv * (u[ub] - u_a);
+          }
+          dgs += ge * (TA)kref_diag<D>();
+          const int ps = __ldg(op.xpos + cbase + cx);
+          const double* xs = op.cmp[ch].x64;
+          if (ps >= 0 && xs) {
+            const double* xr = xs + (size_t)ps * Dim<D>::NP;
+#pragma unroll
+            for (int b = 0; b < NV; ++b) {
+              if (b == a) continue;
+              const TA dv = (TA)__ldg(xr + pair_of(NV, a, b));
+              const int ub = (ox + (b & 1)) + 3 * (oy + ((b >> 1) & 1)) + (D == 3 ? 9 * (oz + ((b >> 2) & 1)) : 0);
+              acc += dv * (u[ub] - u_a);
+              dgs -= dv;
+            }
+          }
+        } else if (CMP) {
           const TA ge = (TA)__ldg(op.eps_c + cbase + cx) * (TA)(sizeof(TA) == 4 ? (double)(float)op.hfac : op.hfac);
 #pragma unroll
           for (int b = 0; b < NV; ++b) {
@@ -1133,12 +1158,26 @@ __device__ __forceinline__ void pair_sums4(const Rows4<T>& u, T (&py)[2][3]) {
     for (int c = 0; c < 3; ++c) py[r][c] = px[r][c] + px[r + 1][c];
 }
 
+// the same from the FP64 cell-centre eps (exact operator of the FP64 residual)
+template <typename T>
+__device__ __forceinline__ void load_eps6(const double* __restrict__ eps, int N, int l, int j, int q,
+                                          bool has_left, bool has_right, T (&g)[2][3]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const double* e = eps + ((size_t)l * N + (j - 1 + r)) * N + q;
+    g[r][0] = has_left ? (T)__ldg(e - 1) : (T)0;
+    g[r][1] = (T)__ldg(e);
+    g[r][2] = has_right ? (T)__ldg(e + 1) : (T)0;
+  }
+}
+
 template <typename T>
 struct Geo2Ctx {
   const T* x;
   const T* b;
   T* y;
   const float* eps;
+  const double* eps64;   // non-null: FP64 cell-centre eps (FP64 instance, exact operator)
   int N, n1, q, j;
   size_t plane, row0;
   bool hl, hr, hr2;
@@ -1151,7 +1190,8 @@ __device__ __forceinline__ void geo2_step(const Geo2Ctx<T>& c, int k, const Rows
                                           const T (&yTm)[3], T (&yTc)[3], double& d1, double& d2) {
   using V2 = typename Vec2T<T>::type;
   load_rows4<T>(c.x + (size_t)(k + 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, un);
-  load_eps6<T>(c.eps, c.N, k, c.j, c.q, c.hl, c.hr2, gc);
+  if (sizeof(T) == 8 && c.eps64) load_eps6<T>(c.eps64, c.N, k, c.j, c.q, c.hl, c.hr2, gc);
+  else load_eps6<T>(c.eps, c.N, k, c.j, c.q, c.hl, c.hr2, gc);
   const V2 b2 = __ldg(reinterpret_cast<const V2*>(c.b + (size_t)k * c.plane + c.row0 + c.q));
   const V2 m2 = __ldg(reinterpret_cast<const V2*>(c.x + (size_t)(k - 1) * c.plane + c.row0 + c.q));
   pair_sums4<T>(un, pyn);
@@ -1218,6 +1258,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, MINB) sweep3_geo2(const Level
   c.b = b;
   c.y = y;
   c.eps = op.eps_c;
+  c.eps64 = sizeof(T) == 8 ? op.eps64 : nullptr;
   c.N = op.N;
   c.n1 = op.N + 1;
   c.plane = (size_t)c.n1 * c.n1;
@@ -1241,7 +1282,8 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, MINB) sweep3_geo2(const Level
     T pa[2][3], pb[2][3], ga[2][3], gb[2][3], ta[3], tb[3];
     load_rows4<T>(x + (size_t)(k0 - 1) * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ub);
     load_rows4<T>(x + (size_t)k0 * c.plane + c.row0 + c.q, c.n1, c.hl, c.hr, ua);
-    load_eps6<T>(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr2, ga);
+    if (c.eps64) load_eps6<T>(c.eps64, c.N, k0 - 1, c.j, c.q, c.hl, c.hr2, ga);
+    else load_eps6<T>(op.eps_c, c.N, k0 - 1, c.j, c.q, c.hl, c.hr2, ga);
     pair_sums4<T>(ub, pb);
     pair_sums4<T>(ua, pa);
 #pragma unroll
@@ -1270,10 +1312,14 @@ __global__ void __launch_bounds__(256) sweep3_fixup64(const LevelOp op, const do
   constexpr int NV = 8;
   __shared__ double sh[2][8];
   const int N = op.N, n1 = N + 1;
-  const int nt = *op.ntouched;
+  // exact operator: every vertex next to an interface cell, the FP64 surplus;
+  // otherwise the vertices next to a cell with a record, the decoded surplus
+  const bool exact = op.eps64 != nullptr;
+  const int* tl = exact ? op.touched64 : op.touched;
+  const int nt = exact ? *op.ntouched64 : *op.ntouched;
   double d1 = 0.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    const int v = op.touched[t];
+    const int v = tl[t];
     const int i = v % n1, j = (v / n1) % n1, k = v / (n1 * n1);
     double u[27];
 #pragma unroll
@@ -1297,11 +1343,24 @@ __global__ void __launch_bounds__(256) sweep3_fixup64(const LevelOp op, const do
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox) {
           const int cx = i - 1 + ox;
+          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
+          if (exact) {
+            const int ps = __ldg(op.xpos + ((size_t)cl * N + (j - 1 + oy)) * N + cx);
+            if (ps < 0 || !ck.x64) continue;
+            const double* xr = ck.x64 + (size_t)ps * 28;
+#pragma unroll
+            for (int bb = 0; bb < NV; ++bb) {
+              if (bb == a) continue;
+              const double dv = __ldg(xr + pair_of(NV, a, bb));
+              const int ub = (ox + (bb & 1)) + 3 * (oy + ((bb >> 1) & 1)) + 9 * (oz + ((bb >> 2) & 1));
+              acc += dv * (u[ub] - u[13]);
+            }
+            continue;
+          }
           const int seg = segrow + (cx >> 5);
           const int cls = __ldg(ck.cls + (size_t)seg * kSegCells + (cx & 31));
           if (!cls) continue;
           const uint8_t* rec = record_at<3>(ck, seg, cx & 31, cls);
-          const int a = (1 - ox) | ((1 - oy) << 1) | ((1 - oz) << 2);
 #pragma unroll
           for (int bb = 0; bb < NV; ++bb) {
             if (bb == a) continue;
@@ -1357,7 +1416,7 @@ cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const dou
 }
 
 // ---- list of vertices touched by a cell with a surplus record (finest compressed level)
-__global__ void touched_mark_kernel(const LevelOp op, uint8_t* __restrict__ flags) {
+__global__ void touched_mark_kernel(const LevelOp op, uint8_t* __restrict__ flags, int from_xpos) {
   const int N = op.N, n1 = N + 1;
   const long long ncell = (long long)N * N * N;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
@@ -1366,7 +1425,8 @@ __global__ void touched_mark_kernel(const LevelOp op, uint8_t* __restrict__ flag
     int ch = cz / op.layers;
     ch = ch < op.nchunk ? ch : op.nchunk - 1;
     const int row = (cz - ch * op.layers) * N + cy;
-    const int cls = op.cmp[ch].cls[((size_t)row * op.nseg_x + (cx >> 5)) * kSegCells + (cx & 31)];
+    const int cls = from_xpos ? (op.xpos[c] >= 0 ? 1 : 0)
+                              : op.cmp[ch].cls[((size_t)row * op.nseg_x + (cx >> 5)) * kSegCells + (cx & 31)];
     if (!cls) continue;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -2204,12 +2264,12 @@ cudaError_t launch_build_stencil(const LevelOp& op, void* out, cudaStream_t st) 
 }
 
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int from_xpos) {
   const long long nv = (long long)(op.N + 1) * (op.N + 1) * (op.N + 1);
   const long long ng = (nv + 31) / 32;
   cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nv, st);
   if (e != cudaSuccess) return e;
-  touched_mark_kernel<<<152 * 16, 256, 0, st>>>(op, flags);
+  touched_mark_kernel<<<152 * 16, 256, 0, st>>>(op, flags, from_xpos);
   count_launches(1);
   touched_count_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts);
   count_launches(1);
@@ -2223,11 +2283,31 @@ cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* co
   scan_add_kernel<<<(unsigned)ntiles, 1024, 0, st>>>(ng, counts, tile_tot);
   count_launches(1);
   touched_write_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts, list);
-  if (op.tcoef && op.tcap > 0) {
+  if (!from_xpos && op.tcoef && op.tcap > 0) {
     count_launches(1);
     touched_stencil_kernel<<<152 * 8, 256, 0, st>>>(op);
   }
   return launched();
+}
+
+__global__ void xpos_kernel(long long chunk_cells, const int* __restrict__ list, int n, int* __restrict__ xpos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) xpos[list[i]] = i;
+}
+
+cudaError_t launch_xpos(long long chunk_cells, int nchunk, const int* lists, const int* counts_host, int* xpos,
+                        cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(xpos, 0xff, sizeof(int) * (size_t)chunk_cells * nchunk, st);
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < nchunk; ++c) {
+    const int n = counts_host[c];
+    if (n <= 0) continue;
+    count_launches(1);
+    const int g = (n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8;
+    xpos_kernel<<<g, 256, 0, st>>>(chunk_cells, lists + (size_t)c * chunk_cells, n,
+                                                  xpos + (size_t)c * chunk_cells);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* partials, int* nblocks, cudaStream_t st) {
