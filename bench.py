@@ -541,12 +541,12 @@ def run_probe(args, local_rank):
         # cycle, the paper's truncated format at an absolute 1e-8 on the surplus
         n = args.n or 27
         out = {}
-        for theta in (1.0, 16.0, 64.0):
+        for theta, keep in ((1.0, 0), (16.0, 0), (64.0, 0), (1.0, 1), (16.0, 1), (64.0, 1)):
             d = mg.problem_desc(2, n, inputs.theta_field(2, theta), path=mg.PATH_FP64_PLAIN,
-                                s_schedule=tuple(range(1, 9)), adapt_C=0.01)
+                                s_schedule=tuple(range(1, 9)), adapt_C=0.01, adapt_keep=keep)
             rows = []
             with mg.Problem(d) as P:
-                for s in range(1, 9):
+                for s in range(1, 11):
                     if s > 1:
                         P.assemble(s)
                     acc = P.cell_accuracy()
@@ -554,7 +554,7 @@ def run_probe(args, local_rank):
                     rows.append({"cycle": s, "max_n": int(acc.max()), "avg_n": float(acc.mean()),
                                  "compression": st["compression"], "cells_by_p3": st["cells_by_p3"],
                                  "max_abs_error": st["max_abs_error"]})
-            out[str(theta)] = rows
+            out[f"theta={theta:g} {'keep-old' if keep else 'keep-new'}"] = rows
         print(json.dumps({"probe": "paper_format", "n_cells": n, "delta": 1e-8, "C": 0.01, "theta": out}),
               flush=True)
         return

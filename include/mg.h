@@ -151,7 +151,12 @@ typedef struct {
                               schedule before solving.  0 => every cell reaches the last
                               accuracy of the schedule. */
   int32_t cycle;           /* mg_cycle: the multigrid cycle each outer iteration applies */
-  int32_t pad1;
+  int32_t adapt_keep;      /* adapt_C > 0: which matrix a cell keeps when its change falls below
+                              adapt_C.  0 => the newer one (the rule as stated in Section
+                              "Adaptive stencil integration"); 1 => the older one it was
+                              tested against, with that older accuracy (the account of Table
+                              "memory-footprint" in the Results: the lowest accuracy that
+                              passes is used all the way through).  Other values: MG_ERR_INVALID. */
   double coarse_tau;       /* mixed paths, > 0: every coarse level stores its Galerkin operator
                               as the hierarchical surplus over its one-sample rediscretisation
                               eps(x_C) K_ref h_C^(d-2) (eps at the coarse cell centre), with the

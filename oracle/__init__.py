@@ -61,7 +61,7 @@ def _load():
         lib.oc_assemble.argtypes = [FP, ctypes.c_int, ctypes.c_int, _D]
         lib.oc_assemble_cells.argtypes = [FP, ctypes.c_int, ctypes.c_int, _I64, ctypes.c_int64, _D]
         lib.oc_assemble_adaptive.argtypes = [FP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
-                                             ctypes.c_double, _D, ctypes.POINTER(ctypes.c_int32)]
+                                             ctypes.c_double, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int32)]
         lib.oc_round_format.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         lib.oc_round_format.restype = ctypes.c_double
         lib.oc_round_e4m3.argtypes = [ctypes.c_double]
@@ -170,16 +170,19 @@ def assemble_cells(field: Field, n_cells: int, s: int, cells) -> np.ndarray:
     return A
 
 
-def assemble_adaptive(field: Field, n_cells: int, schedule, C: float):
+def assemble_adaptive(field: Field, n_cells: int, schedule, C: float, keep_old: bool = False):
     """Adaptive per-cell accuracy (Section "Adaptive stencil integration"):
-    (element matrices of every cell, accuracy s of each stored matrix)."""
+    (element matrices of every cell, accuracy s of each stored matrix).
+    keep_old: a cell that passes the test keeps the older matrix (the
+    reading of Table "memory-footprint") instead of the newer one."""
     nv = 1 << field.dim
     ncell = n_cells ** field.dim
     A = np.zeros((ncell, nv, nv))
     sc = np.zeros(ncell, np.int32)
     sched = np.ascontiguousarray(np.asarray(schedule, np.int32))
     _load().oc_assemble_adaptive(ctypes.byref(field.c), n_cells, sched.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                 len(sched), float(C), _p(A), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+                                 len(sched), float(C), 1 if keep_old else 0, _p(A),
+                                 sc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     return A, sc
 
 

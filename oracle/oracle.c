@@ -204,12 +204,16 @@ void oc_assemble_cells(const oc_field* F, int N, int s, const int64_t* cells, in
 
 /* Adaptive per-cell accuracy (Section "Adaptive stencil integration", Eq.
  * "termination-criterion"): each cell walks the accuracy schedule sched[0],
- * sched[1], ... and keeps the newest element matrix; it stops at the first
- * level k >= 1 where the relative change in the element-wise maximum norm,
+ * sched[1], ... and stops at the first level k >= 1 where the relative change
+ * in the element-wise maximum norm,
  * ||A(sched[k]) - A(sched[k-1])||_max / ||A(sched[k-1])||_max, falls below C.
- * s_cell receives the accuracy of the stored matrix. */
-void oc_assemble_adaptive(const oc_field* F, int N, const int* sched, int n_s, double C, double* A_all,
-                          int32_t* s_cell) {
+ * keep_old = 0: the cell stores A(sched[k]), the newest matrix (the rule's
+ * text); keep_old = 1: it keeps A(sched[k-1]), the matrix that passed the
+ * test (the Results' account of Table "memory-footprint": the lowest
+ * accuracy approximation is used all the way through when the test finds no
+ * difference).  s_cell receives the accuracy of the stored matrix. */
+void oc_assemble_adaptive(const oc_field* F, int N, const int* sched, int n_s, double C, int keep_old,
+                          double* A_all, int32_t* s_cell) {
   const int d = F->dim, nv = 1 << d;
   const int64_t ncell = ipow(N, d);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -227,9 +231,11 @@ void oc_assemble_adaptive(const oc_field* F, int N, const int* sched, int n_s, d
         if (fabs(Anew[i] - A[i]) > num) num = fabs(Anew[i] - A[i]);
         if (fabs(A[i]) > den) den = fabs(A[i]);
       }
+      const int passed = num < C * den;
+      if (passed && keep_old) break;   /* the older, lower-accuracy matrix stays */
       memcpy(A, Anew, sizeof(double) * nv * nv);
       sf = sched[k];
-      if (num < C * den) break;
+      if (passed) break;
     }
     s_cell[c] = sf;
   }
@@ -884,13 +890,19 @@ void oc_inject(int d, int Nc, const double* rf, double* bc) {
  * is restricted to every level; every level but the coarsest takes one
  * damped Jacobi step on it, c_l = omega D_l^-1 r_l, the coarsest is solved
  * exactly, and all corrections are prolongated to the finest level and
- * added.  variant 1 (adaFAC-PI) and 2 (adaFAC-Jac) subtract from each c_l
- * (l above the coarsest) the projection P s of an auxiliary Jacobi step on
- * the next coarser level, s = omega D_(l-1)^-1 t, which mimics the
- * overshoot of the coarse corrections running concurrently: t = I r_l
- * (injection) for adaFAC-PI, t = R (r_l - A_l c_l) (the residual the level's
- * own smoothing leaves, restricted) for adaFAC-Jac.  variant 0 is plain
- * additive multigrid.  Levels of mg: 0 coarsest .. L-1 finest. */
+ * added.  variants 1 (adaFAC-PI) and 2 (adaFAC-Jac) damp each c_l (l above
+ * the coarsest) with an auxiliary Jacobi step on the next coarser level,
+ * s = omega D_(l-1)^-1 t, which mimics the overshoot of the coarse
+ * corrections running concurrently:
+ *   adaFAC-PI:  t = I r_l (injection), c_l = S_l r_l - P s (the BPX-like pair
+ *               P, I);
+ *   adaFAC-Jac: t = R (r_l - A_l S_l r_l), the restriction by the transpose of
+ *               the Jacobi-smoothed prolongation (I - S_l A_l) P, and the
+ *               auxiliary correction is taken out through the level's own
+ *               smoother, c_l = S_l (r_l - A_l P s), the form of the AFACx
+ *               schemes that adaFAC-x derives from (P~ = S_l A_l P).
+ * variant 0 is plain additive multigrid.  Levels of mg: 0 coarsest .. L-1
+ * finest. */
 static void additive_cycle(const oc_mg* mg, const double* b, double* e, int variant) {
   const int d = mg->d, L = mg->L;
   double* r[16];
@@ -921,8 +933,17 @@ static void additive_cycle(const oc_mg* mg, const double* b, double* e, int vari
         free(q);
       }
       oc_jacobi(d, Nc, mg->A[l - 1], t, zc, mg->omega, sc);
-      for (int64_t v = 0; v < ncv; ++v) sc[v] = -sc[v];
-      oc_prolong_add(d, Nc, sc, c[l]);
+      if (variant == 1) {
+        for (int64_t v = 0; v < ncv; ++v) sc[v] = -sc[v];
+        oc_prolong_add(d, Nc, sc, c[l]);
+      } else {
+        /* c_l = S_l (r_l - A_l y), y = P s: one Jacobi step from y, minus y */
+        double* y = (double*)calloc(nv, sizeof(double));
+        oc_prolong_add(d, Nc, sc, y);
+        oc_jacobi(d, N, mg->A[l], r[l], y, mg->omega, c[l]);
+        for (int64_t v = 0; v < nv; ++v) c[l][v] -= y[v];
+        free(y);
+      }
       free(t);
       free(sc);
       free(zc);

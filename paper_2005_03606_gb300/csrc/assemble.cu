@@ -480,12 +480,17 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           }
           dl[pair_index(NV, a, b)] = v * scale;
         }
+      // adaptive accuracy, keep-old reading: a cell that passes the test keeps
+      // its previously stored matrix (and accuracy)
+      bool keep_prev = false;
+      int pcls = 0;
+      const uint8_t* prec = nullptr;
       if (A.final_flags) {
         // adaptive accuracy: relative change against the previously stored
         // matrix in the element-wise maximum norm (diagonals included)
         const T ge = eref * (T)A.hfac;
-        const int pcls = A.prec64 ? 0 : cell_class(A.prev_cmp, N, A.nseg_x, lc);
-        const uint8_t* prec = pcls ? cell_record<D>(A.prev_cmp, N, A.nseg_x, lc, pcls) : nullptr;
+        pcls = A.prec64 ? 0 : cell_class(A.prev_cmp, N, A.nseg_x, lc);
+        prec = pcls ? cell_record<D>(A.prev_cmp, N, A.nseg_x, lc, pcls) : nullptr;
         T num = 0, den = 0, rsn[NV], rso[NV];
 #pragma unroll
         for (int a = 0; a < NV; ++a) rsn[a] = rso[a] = 0;
@@ -512,8 +517,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           num = fmax(num, fabs(rso[a] - rsn[a]));
           den = fmax(den, fabs(rso[a]));
         }
-        if (num < (T)A.adapt_C * den) A.final_flags[lc] = 1;
-        A.s_cell[lc] = (uint8_t)s;
+        const bool passed = num < (T)A.adapt_C * den;
+        if (passed) A.final_flags[lc] = 1;
+        keep_prev = passed && A.adapt_keep;
+        if (!keep_prev) A.s_cell[lc] = (uint8_t)s;
       }
       if (A.prec64) {
         double* out = reinterpret_cast<double*>(A.out_full);
@@ -523,8 +530,19 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           for (int b = a + 1; b < NV; ++b) {
             const int p = pair_index(NV, a, b);
             out[(long long)p * A.ncell + lc] =
-                (double)eref * kref_off<D>(popc_small(a ^ b)) * A.hfac + (double)dl[p];
+                keep_prev ? A.prev_full[(long long)p * A.ncell + lc]
+                          : (double)eref * kref_off<D>(popc_small(a ^ b)) * A.hfac + (double)dl[p];
           }
+      } else if (keep_prev) {
+        // the previous record and class (exact mode: the FP64 surplus array
+        // already holds the previous level's entries)
+        uint8_t* rec = A.out_rec + (size_t)lc * Dim<D>::REC_MAX;
+        const int rb = pcls == 1 ? Dim<D>::REC1 : (pcls == 2 ? Dim<D>::REC2 : Dim<D>::REC3);
+        if (pcls)
+          for (int q = 0; q < rb; q += 4) *reinterpret_cast<uint32_t*>(rec + q) = *reinterpret_cast<const uint32_t*>(prec + q);
+        const long long row = lc / N;
+        const int x = (int)(lc - row * N);
+        A.out_cls[(row * A.nseg_x + (x >> 5)) * kSegCells + (x & 31)] = (uint8_t)pcls;
       } else {
         // storage class from the surplus size (the oracle's rule; in FP32 on
         // the FP32 assembly, in FP64 in exact mode).  The records hold the

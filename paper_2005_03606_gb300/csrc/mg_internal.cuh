@@ -252,6 +252,7 @@ struct AsmLaunch {
   uint8_t* final_flags;
   uint8_t* s_cell;
   double adapt_C;
+  int adapt_keep;        // 1: a cell that passes the test keeps its previous matrix
   // exact surplus of the mixed paths (eps64 != nullptr): FP64 arithmetic with
   // eps64 as the reference, the lossy records against the FP32 eps_c, and
   // the FP64 surplus written to out_x64 at the cell's list position xpos;
@@ -326,6 +327,8 @@ cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
                                  cudaStream_t st, int from_xpos = 0);
 // xpos[chunk * chunk_cells + list[chunk][i]] = i for every interface cell, -1 elsewhere
+// a = b - a over n entries (FP64 when vec64, else FP32)
+cudaError_t launch_sub_from(long long n, int vec64, void* a, const void* b, cudaStream_t st);
 cudaError_t launch_xpos(long long chunk_cells, int nchunk, const int* lists, const int* counts_host, int* xpos,
                         cudaStream_t st);
 

@@ -337,6 +337,10 @@ mg_status validate(const mg_problem_desc* d) {
     set_error("adapt_C must be a finite value >= 0");
     return MG_ERR_INVALID;
   }
+  if (d->adapt_keep != 0 && d->adapt_keep != 1) {
+    set_error("adapt_keep must be 0 or 1");
+    return MG_ERR_INVALID;
+  }
   if (validate_eps(d->eps) != MG_OK) return MG_ERR_INVALID;
   if (d->n_s < 1 || d->n_s > 8) {
     set_error("n_s must be 1..8");
@@ -398,7 +402,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
                                        (const double*)P->wlast[chunk].a64, nullptr, nullptr, (double*)cs.a64,
                                        P->ilist ? P->ilist + off : nullptr,
                                        P->ilist ? P->ilist_n[chunk] : P->chunk_cells, P->awork, P->anwork,
-                                       P->s_cell + off, s, adaptive_first(P, chunk), st));
+                                       P->s_cell + off, s, adaptive_first(P, chunk) && !P->desc.adapt_keep, st));
       int h = 0;
       MG_CHECK(cudaMemcpyAsync(&h, P->anwork, sizeof(int), cudaMemcpyDeviceToHost, st));
       MG_CHECK(cudaStreamSynchronize(st));
@@ -429,6 +433,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
         a.final_flags = P->final_flags + off;
         a.s_cell = P->s_cell + off;
         a.adapt_C = P->desc.adapt_C;
+        a.adapt_keep = P->desc.adapt_keep;
       } else if (P->ilist) {
         a.list = P->ilist + (size_t)chunk * P->chunk_cells;
         a.nlist = P->ilist_n[chunk];
@@ -479,7 +484,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
     MG_CHECK(launch_adaptive_prepare(D, P->N, P->nseg_x, P->chunk_cells, 0, P->final_flags + off, prev, nullptr,
                                      P->scratch, cs.cls, nullptr, P->ilist ? P->ilist + off : nullptr,
                                      P->ilist ? P->ilist_n[chunk] : P->chunk_cells, P->awork, P->anwork,
-                                     P->s_cell + off, s, adaptive_first(P, chunk), st));
+                                     P->s_cell + off, s, adaptive_first(P, chunk) && !P->desc.adapt_keep, st));
     int h = 0;
     MG_CHECK(cudaMemcpyAsync(&h, P->anwork, sizeof(int), cudaMemcpyDeviceToHost, st));
     MG_CHECK(cudaStreamSynchronize(st));
@@ -489,6 +494,7 @@ mg_status assemble_chunk(mg_problem* P, int s, int chunk, cudaStream_t st, Chunk
     a.final_flags = P->final_flags + off;
     a.s_cell = P->s_cell + off;
     a.adapt_C = P->desc.adapt_C;
+    a.adapt_keep = P->desc.adapt_keep;
   } else if (P->ilist) {   // only the interface cells can carry a surplus (the class bytes start at 0)
     a.list = P->ilist + (size_t)chunk * P->chunk_cells;
     a.nlist = P->ilist_n[chunk];
@@ -643,10 +649,13 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
 // for A e = lev[0].b from e = 0; returns the correction (lev[0].x0).  The fine
 // residual is restricted to every level; the coarsest is solved exactly and
 // every other level takes one damped Jacobi step from zero on its residual,
-// c_l = omega D_l^-1 r_l.  adaFAC-PI / adaFAC-Jac subtract from c_l the
-// prolongation of one damped Jacobi step on the next coarser level of the
-// auxiliary right-hand side I r_l (injection) / R (r_l - A_l c_l).  The
-// corrections are summed from the coarsest level up.  Levels are processed
+// c_l = omega D_l^-1 r_l.  adaFAC-PI subtracts from c_l the prolongation of
+// one damped Jacobi step s on the next coarser level of the auxiliary
+// right-hand side I r_l (injection); adaFAC-Jac takes s from R (r_l - A_l c_l)
+// (the transpose of the Jacobi-smoothed prolongation applied to r_l) and
+// removes it through the level's own smoother, c_l = S_l (r_l - A_l P s)
+// (the AFACx form: P~ = S_l A_l P).  The corrections are summed from the
+// coarsest level up.  Levels are processed
 // coarse to fine, so a level's b and x1 are free for the auxiliary step of
 // the level above it.
 void* additive_enqueue(mg_problem* P, mg_status* stt) {
@@ -678,17 +687,25 @@ void* additive_enqueue(mg_problem* P, mg_status* stt) {
     Level& lv = P->lev[l];
     Level& lc = P->lev[l + 1];
     jacobi0(lv, lv.b, lv.x0, om, lv.x1);
-    if (cyc == MG_CYCLE_ADAFAC_PI || cyc == MG_CYCLE_ADAFAC_JAC) {
-      if (cyc == MG_CYCLE_ADAFAC_PI) {
-        e = launch_inject(P->dim, lc.N, vec64, lv.b, lc.b, st);
-      } else {
-        e = launch_sweep(lv.op, SW_RESID, vec64, lv.x0, lv.b, lv.x1, om, nullptr, nullptr, st);
-        if (e == cudaSuccess) e = launch_restrict(P->dim, lc.N, vec64, lv.x1, lc.b, st);
-      }
+    if (cyc == MG_CYCLE_ADAFAC_PI) {
+      // c_l = S_l r_l - P S_(l-1) I r_l
+      e = launch_inject(P->dim, lc.N, vec64, lv.b, lc.b, st);
       if (e != cudaSuccess) *stt = oom_or_cuda(e, "auxiliary residual");
       jacobi0(lc, lc.b, lc.x1, -om, nullptr);   // minus the auxiliary step ...
       if ((e = launch_prolong_add(P->dim, lc.N, vec64, lc.x1, lv.x0, st)) != cudaSuccess)   // ... prolongated
         *stt = oom_or_cuda(e, "auxiliary prolongation");
+    } else if (cyc == MG_CYCLE_ADAFAC_JAC) {
+      // s = S_(l-1) R (r_l - A_l S_l r_l), then c_l = S_l (r_l - A_l P s):
+      // one Jacobi step from y = P s, minus y
+      e = launch_sweep(lv.op, SW_RESID, vec64, lv.x0, lv.b, lv.x1, om, nullptr, nullptr, st);
+      if (e == cudaSuccess) e = launch_restrict(P->dim, lc.N, vec64, lv.x1, lc.b, st);
+      if (e != cudaSuccess) *stt = oom_or_cuda(e, "auxiliary residual");
+      jacobi0(lc, lc.b, lc.x1, om, nullptr);
+      e = cudaMemsetAsync(lv.x0, 0, P->tv * lv.nvert, st);
+      if (e == cudaSuccess) e = launch_prolong_add(P->dim, lc.N, vec64, lc.x1, lv.x0, st);
+      if (e == cudaSuccess) e = launch_sweep(lv.op, SW_JACOBI, vec64, lv.x0, lv.b, lv.x1, om, nullptr, nullptr, st);
+      if (e == cudaSuccess) e = launch_sub_from(lv.nvert, vec64, lv.x0, lv.x1, st);   // x0 = x1 - x0
+      if (e != cudaSuccess) *stt = oom_or_cuda(e, "auxiliary correction");
     }
     if ((e = launch_prolong_add(P->dim, lc.N, vec64, lc.x0, lv.x0, st)) != cudaSuccess)
       *stt = oom_or_cuda(e, "prolong");

@@ -2290,6 +2290,21 @@ cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* co
   return launched();
 }
 
+template <typename T>
+__global__ void sub_from_kernel(long long n, T* __restrict__ a, const T* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] = b[i] - a[i];
+}
+
+cudaError_t launch_sub_from(long long n, int vec64, void* a, const void* b, cudaStream_t st) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  if (vec64) sub_from_kernel<double><<<(int)g, 256, 0, st>>>(n, (double*)a, (const double*)b);
+  else sub_from_kernel<float><<<(int)g, 256, 0, st>>>(n, (float*)a, (const float*)b);
+  return launched();
+}
+
 __global__ void xpos_kernel(long long chunk_cells, const int* __restrict__ list, int n, int* __restrict__ xpos) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) xpos[list[i]] = i;
 }

@@ -44,7 +44,7 @@ class mg_problem_desc(ctypes.Structure):
                 ("omega", ctypes.c_double), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("chunks", ctypes.c_int32),
                 ("u0", ctypes.POINTER(ctypes.c_double)), ("adapt_C", ctypes.c_double), ("cycle", ctypes.c_int32),
-                ("pad1", ctypes.c_int32), ("coarse_tau", ctypes.c_double)]
+                ("adapt_keep", ctypes.c_int32), ("coarse_tau", ctypes.c_double)]
 
 
 class mg_solve_info(ctypes.Structure):
@@ -172,7 +172,7 @@ def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_s
                  f_const: float = 1.0, outer: int = OUTER_FCG, tau: float = 1e-6, omega: float = 0.6,
                  nu_pre: int = 2, nu_post: int = 2, rtol: float = 1e-8, max_cycles: int = 500,
                  chunks: int = 0, u0: Optional[np.ndarray] = None, adapt_C: float = 0.0,
-                 cycle: int = 0, coarse_tau: float = 0.0) -> mg_problem_desc:
+                 cycle: int = 0, coarse_tau: float = 0.0, adapt_keep: int = 0) -> mg_problem_desc:
     d = mg_problem_desc()
     d.dim, d.n_cells = dim, n_cells
     d.eps = eps_desc(field)
@@ -187,6 +187,7 @@ def problem_desc(dim: int, n_cells: int, field, path: int = PATH_FP64_PLAIN, s_s
     d.adapt_C = adapt_C
     d.cycle = cycle
     d.coarse_tau = coarse_tau
+    d.adapt_keep = adapt_keep
     if u0 is not None:
         u0 = np.ascontiguousarray(u0, np.float64)
         d.u0 = u0.ctypes.data_as(_D)

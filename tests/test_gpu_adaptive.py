@@ -44,18 +44,22 @@ def _ratios(F, n, sched):
     return np.stack(r, axis=1), mats
 
 
-def _check(dim, n, fld, path, sched, chunks, run, C=C):
+def _check(dim, n, fld, path, sched, chunks, run, C=C, keep=0):
     F = oracle.Field(fld)
-    A_ref, s_ref = oracle.assemble_adaptive(F, n, sched, C)
+    A_ref, s_ref = oracle.assemble_adaptive(F, n, sched, C, keep_old=bool(keep))
     r, mats = _ratios(F, n, sched)
     mixed = path in (mg.PATH_MIXED_PLAIN, mg.PATH_MIXED_DELAYED)
     band, tol = (1e-4 * C / 1e-2, 1e-5) if mixed else (1e-10, 1e-12)
-    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=sched, chunks=chunks, adapt_C=C)) as P:
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=sched, chunks=chunks, adapt_C=C,
+                                    adapt_keep=keep)) as P:
         run(P)
         s_gpu = P.cell_accuracy()
         A = P.cell_matrices(np.arange(n ** dim, dtype=np.int64))
-    # the oracle's path for each cell: the judged levels up to its stop
+    # the oracle's path for each cell: the judged levels up to its stop (under
+    # keep-old the stored level is the one before the test that stopped it)
     k_stop = np.searchsorted(np.asarray(sched), s_ref)
+    if keep:
+        k_stop = np.minimum(k_stop + 1, len(sched) - 1)
     judged = np.arange(1, len(sched))[None, :] <= k_stop[:, None]
     near = (np.abs(r - C) <= band) & judged
     amb = near.any(axis=1)
@@ -103,6 +107,28 @@ CASES = [
 def test_adaptive_accuracy_matches_oracle(dim, n, fld, path, sched, chunks, how, c):
     run = _solve if how == "solve" else _assemble_all(sched)
     _check(dim, n, fld, path, sched, chunks, run, c)
+
+
+KEEP_CASES = [
+    (2, 81, inputs.disc_field(2), mg.PATH_FP64_PLAIN, (1, 2, 4, 8), 3, "assemble", C),
+    (2, 81, inputs.theta_field(2, 16.0), mg.PATH_FP64_DELAYED, (1, 2, 4, 8), 1, "solve", 1e-3),
+    (3, 27, inputs.fourier_field(3, 15, sigma=2.0, jump_x=0.37, jump_factor=1e4), mg.PATH_MIXED_PLAIN,
+     (1, 2, 3, 4, 6), 3, "assemble", C),
+    (3, 27, inputs.boxes_field(3, 14), mg.PATH_MIXED_DELAYED, (2, 4, 8), 0, "solve", C),
+]
+
+
+@pytest.mark.parametrize("dim,n,fld,path,sched,chunks,how,c", KEEP_CASES)
+def test_adaptive_keep_old_reading_matches_oracle(dim, n, fld, path, sched, chunks, how, c):
+    # adapt_keep = 1: a cell that passes the test keeps the matrix it was tested against
+    run = _solve if how == "solve" else _assemble_all(sched)
+    _check(dim, n, fld, path, sched, chunks, run, c, keep=1)
+
+
+def test_adaptive_keep_flag_rejected_outside_0_1():
+    with pytest.raises(mg.MGError) as ei:
+        mg.Problem(mg.problem_desc(2, 27, inputs.disc_field(2), s_schedule=(1, 2), adapt_C=0.01, adapt_keep=2))
+    assert ei.value.status == mg.MG_ERR_INVALID
 
 
 def test_adaptive_off_reports_chunk_accuracy():

@@ -143,3 +143,20 @@ def test_paper_format_end_to_end_from_oracle_matrices(dim, n, fld, s, delta):
     if diff.size:
         p_own, _ = oracle.paper_format(dim, A_gpu[diff], ec[diff], K, delta)
         assert np.array_equal(p3[diff].astype(np.int32), p_own)
+
+
+def test_memory_footprint_table_theta1_column_under_keep_old():
+    # Table "memory-footprint", theta = 1: one accuracy step n -> n + 1 per
+    # cycle with C = 1%; under the keep-old reading every cell keeps n = 1 and
+    # only its one-byte marker: max n 1, average 1.00, compression 128.00 in all
+    # ten cycles, as printed
+    # (the descriptor's schedule holds at most 8 levels; mg_assemble_level takes any s)
+    d = mg.problem_desc(2, 27, inputs.theta_field(2, 1.0), path=mg.PATH_FP64_PLAIN, s_schedule=tuple(range(1, 9)),
+                        adapt_C=0.01, adapt_keep=1)
+    with mg.Problem(d) as P:
+        for s in range(1, 11):
+            if s > 1:
+                P.assemble(s)
+            acc = P.cell_accuracy()
+            _, _, st = P.paper_format(1e-8)
+            assert acc.max() == 1 and st["compression"] == 128.0
