@@ -500,6 +500,25 @@ def run_probe(args, local_rank):
                                               ["disc2d"] + (["fourier3d"] if args.oracle_single_3d else []))}),
               flush=True)
         return
+    if args.probe == "peaks":   # arithmetic pipe rates of this GPU (FP32 / FP64 FMA, FP32 exp)
+        print(json.dumps({"probe": "peaks", "fp32_fma_per_s": mg.measure_peak(0),
+                          "fp64_fma_per_s": mg.measure_peak(1), "fp32_exp_per_s": mg.measure_peak(2)}), flush=True)
+        return
+    if args.probe == "assembly":   # the integration kernel alone: eps samples per second
+        w = inputs.workload(args.workload, args.n)
+        path = mg.PATH_FP64_PLAIN if args.probe_fp64 else mg.PATH_MIXED_PLAIN
+        d = mg.problem_desc(w.dim, w.n_cells, w.eps, path=path, s_schedule=(w.s_final,), rtol=1e-8)
+        with mg.Problem(d) as P:
+            ms = P.profile(4, args.probe_reps)
+        # the first chunk of the default chunking (9 slabs from 27 cells per axis);
+        # piecewise-constant fields integrate only its interface cells (count not reported)
+        pc = w.eps.kind in (inputs.KIND_BOXES, inputs.KIND_DISC, inputs.KIND_CONST)
+        ncell = w.n_cells ** w.dim // (9 if w.n_cells >= 27 else 1)
+        samples = ncell * w.s_final ** w.dim
+        print(json.dumps({"probe": "assembly", "workload": args.workload, "n_cells": w.n_cells, "fp64": args.probe_fp64,
+                          "s": w.s_final, "cells": None if pc else int(ncell), "ms_per_launch": ms,
+                          "samples_per_s": None if pc else samples / (ms * 1e-3)}), flush=True)
+        return
     if args.probe == "solve":   # whole mixed delayed solves, for launch lists
         w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED, n_cells=args.n)
         ms = []
@@ -671,7 +690,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--probe", choices=["oracle", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
+    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
                                         "adaptive", "starvation", "paths", "paper_format", "cycles", "coarse"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")

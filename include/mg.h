@@ -332,9 +332,26 @@ mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
  *   which = 1: finest-level FP64 matvec of the outer loop (with dot products)
  *   which = 2: finest-level FP64 residual f - A u
  *   which = 3: Galerkin product finest -> next coarser level
+ *   which = 4: the element-matrix integration kernel alone (Section
+ *              "Numerical computation of stencils") on the first chunk of
+ *              the finest level at the last accuracy of the schedule: its
+ *              interface cells on piecewise-constant fields, else every cell
+ *              of the chunk; outputs go to scratch buffers (the stored
+ *              operator is not changed)
  * The problem's iteration vectors are used as scratch (the next cycle
- * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_CUDA. */
+ * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_PENDING
+ * (which = 4 while delayed assembly jobs are in flight), MG_ERR_CUDA. */
 mg_status mg_profile_kernel(mg_problem* p, int which, int reps, double* ms_per_launch);
+
+/* Measures the throughput of one arithmetic pipe of the current device with
+ * kernels of independent dependency chains (a calibration for the pipe
+ * fractions this library reports; the paper has no counterpart):
+ *   kind = 0: FP32 fused multiply-add, kind = 1: FP64 fused multiply-add,
+ *   kind = 2: FP32 exponential (__expf, the special-function unit).
+ * *ops_per_s receives the operations per second (one FMA counts as one
+ * operation).  Allocates a small device buffer.  Errors: MG_ERR_INVALID,
+ * MG_ERR_CUDA. */
+mg_status mg_measure_peak(int kind, double* ops_per_s);
 
 /* Test hook for host-side failure injection (the paper has none; Section
  * "Asynchronous and anarchic stencil integration" runs assembly as

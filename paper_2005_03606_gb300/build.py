@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmg.so")
-SOURCES = ["assemble.cu", "sweep.cu", "galerkin.cu", "problem.cu", "server.cu", "noalloc.cu", "paper_format.cu"]
+SOURCES = ["assemble.cu", "sweep.cu", "galerkin.cu", "problem.cu", "server.cu", "noalloc.cu", "paper_format.cu",
+           "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

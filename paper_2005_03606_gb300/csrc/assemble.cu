@@ -36,7 +36,7 @@ constexpr int kAsmThreads = 256;
 constexpr int kMaxS = 64;
 
 template <typename T> __device__ __forceinline__ T t_exp(T x);
-template <> __device__ __forceinline__ float t_exp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ float t_exp<float>(float x) { return __expf(x); }
 template <> __device__ __forceinline__ double t_exp<double>(double x) { return exp(x); }
 template <typename T> __device__ __forceinline__ void t_sincospi(T x, T* s, T* c);
 template <> __device__ __forceinline__ void t_sincospi<float>(float x, float* s, float* c) { sincospif(x, s, c); }
@@ -159,17 +159,15 @@ struct Cplx {   // (cos, sin) pair
 };
 
 // MODES: compile-time bound of the Fourier mode loops (>= F.n_modes), so that
-// the per-row phases stay in registers
+// the per-row phases stay in registers; FP32 instances are held to two
+// resident blocks per SM
 template <int D, typename T, int KIND, int MODES>
-__global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, const SampleThresholds TH,
-                                                               const AsmLaunch A) {
+__global__ void __launch_bounds__(kAsmThreads, sizeof(T) == 4 ? 2 : 1)
+    assemble_kernel(const EpsDev F, const SampleThresholds TH, const AsmLaunch A) {
   constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
   constexpr int NW = D == 3 ? 27 : 6;
   const int N = A.N, s = A.s;
   __shared__ T s_t1[kMaxS], s_t2[kMaxS];
-  // Fourier fields: e^{i 2 pi k_x x} along a row of samples is the row's start
-  // phase times s_X[m][jx] = e^{i pi 2 k_x jx / (N s)}, the same for every cell
-  __shared__ Cplx<T> s_X[KIND == EPS_FOURIER ? MODES : 1][KIND == EPS_FOURIER ? kMaxS : 1];
   __shared__ XEntryT<T> s_x[kAsmThreads / 32][64];
   const FieldT<T> FT(F);
   const T vin = FT.v_in, vout = FT.v_out;
@@ -177,17 +175,6 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
     s_t1[j] = (T)(2 * j + 1) / (T)(2 * s);
     s_t2[j] = (T)(3 * j * j + 3 * j + 1) / (T)(3 * s * s);
   }
-  if (KIND == EPS_FOURIER) {
-    for (int idx = threadIdx.x; idx < F.n_modes * s; idx += blockDim.x) {
-      const int m = idx / s, j = idx - m * s;
-      T sn, cs;
-      t_sincospi<T>((T)(2.0 * F.k[m][0] * j / ((double)N * s)), &sn, &cs);
-      s_X[m][j].c = cs;
-      s_X[m][j].s = sn;
-    }
-  }
-  __syncthreads();
-
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int R = 1;
   for (int a = 1; a < D; ++a) R *= s;
@@ -195,6 +182,37 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
   while (G * 2 <= R && G < 32) G *= 2;
   const int CPW = 32 / G;
   const int grp = lane / G, lig = lane % G;
+  // Fourier fields (dynamic shared memory, sized at the launch): the phase
+  // e^{i pi (k.(2m + 1) / (N s) + phi)} of mode m at the global sample index m
+  // is the cell's start phase C (at the cell's first sample) times the
+  // per-axis rotations tX[jx] tY[jy] tZ[jz], tA[j] = e^{i pi 2 k_a j / (N s)}:
+  // one rotation table per axis for the block, C per cell (computed by the
+  // cell's lanes), so that a row costs two complex products per mode.  Modes
+  // beyond n_modes are zero.  tX is [jx][MODES]: every lane of a warp reads the
+  // same jx (a broadcast), at fixed offsets, two modes per 16-byte load in
+  // FP32; tY and tZ are [MODES][s]: the lanes of a cell read different rows j
+  // (consecutive j in consecutive banks).
+  extern __shared__ __align__(16) unsigned char asm_dyn[];
+  Cplx<T>* tX = reinterpret_cast<Cplx<T>*>(asm_dyn);
+  Cplx<T>* tY = tX + (KIND == EPS_FOURIER ? MODES * s : 0);
+  Cplx<T>* tZ = tY + (KIND == EPS_FOURIER ? MODES * s : 0);
+  Cplx<T>* tC = tZ + (KIND == EPS_FOURIER && D == 3 ? MODES * s : 0);
+  if (KIND == EPS_FOURIER) {
+    for (int idx = threadIdx.x; idx < MODES * s; idx += blockDim.x) {
+      const int j = idx / MODES, m = idx - j * MODES;
+      for (int a = 0; a < D; ++a) {
+        T sn = 0, cs = 0;
+        if (m < F.n_modes) t_sincospi<T>((T)(2.0 * F.k[m][a] * j / ((double)N * s)), &sn, &cs);
+        Cplx<T>* t = a == 0 ? tX + idx : (a == 1 ? tY : tZ) + m * s + j;
+        t->c = cs;
+        t->s = sn;
+      }
+    }
+  }
+  __syncthreads();
+  // this group's cell start phases (groups MODES + 1 apart: the groups of a
+  // warp read the same mode in different banks)
+  Cplx<T>* cellC = tC + (warp * CPW + grp) * (MODES + 1);
   XEntryT<T>* xt = &s_x[warp][0];
   const int xt_stride = s;  // entries per group (CPW * s <= 64 by construction)
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -239,6 +257,18 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
         e.th = theta_factor<T>(F, sample_x(N, s, ci[0], jx));
       }
       xt[grp * xt_stride + jx] = e;
+    }
+    if (KIND == EPS_FOURIER) {
+      const int twoNs = 2 * N * s;
+      for (int m = lig; m < MODES; m += G) {
+        T sn = 0, cs = 0;
+        if (m < F.n_modes) {
+          const int n = phase_num(F, m, D, m0, twoNs);
+          t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
+        }
+        cellC[m].c = cs;
+        cellC[m].s = sn;
+      }
     }
     __syncwarp();
     unsigned long long cand = 0;
@@ -380,19 +410,18 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           rowth = theta_factor<T>(F, sample_x(N, s, ci[1], jy));
           if (D == 3) rowth = rowth * theta_factor<T>(F, sample_x(N, s, ci[2], jz));
         } else if (KIND == EPS_FOURIER) {
-          int gm[3] = {m0[0], my, mz};
-          const int twoNs = 2 * N * s;
   #pragma unroll
-          for (int m = 0; m < MODES; ++m) {
-            P_re[m] = 0;
-            P_im[m] = 0;
-            if (m < F.n_modes) {
-              int n = phase_num(F, m, D, gm, twoNs);
-              T sn, cs;
-              t_sincospi<T>((T)n / (T)(N * s) + FieldT<T>::phi(F, m), &sn, &cs);
-              P_re[m] = cs;
-              P_im[m] = sn;
+          for (int m = 0; m < MODES; ++m) {   // (zero beyond n_modes)
+            const Cplx<T> c = cellC[m], y = tY[m * s + jy];
+            T ar = c.c * y.c - c.s * y.s, ai = c.c * y.s + c.s * y.c;
+            if (D == 3) {
+              const Cplx<T> z = tZ[m * s + jz];
+              const T br = ar * z.c - ai * z.s;
+              ai = ar * z.s + ai * z.c;
+              ar = br;
             }
+            P_re[m] = ar;
+            P_im[m] = ai;
           }
         }
         double dz2 = 0.0;
@@ -417,11 +446,27 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(const EpsDev F, c
           } else {
             // g = sum_m Re(P_m X_m[jx]) (modes beyond n_modes have P = 0)
             T g = 0;
+            const Cplx<T>* xr = tX + jx * MODES;
+            if (sizeof(T) == 4 && MODES % 2 == 0) {
+              // two modes per 16-byte load, four independent partial sums
+              const float4* x4 = reinterpret_cast<const float4*>(xr);
+              T g0 = 0, g1 = 0, g2 = 0, g3 = 0;
   #pragma unroll
-            for (int m = 0; m < MODES; ++m) {
-              const Cplx<T> x = s_X[m][jx];
-              g = fma(P_re[m], x.c, g);
-              g = fma(-P_im[m], x.s, g);
+              for (int m = 0; m < MODES; m += 2) {
+                const float4 x = x4[m / 2];
+                g0 = fma(P_re[m], (T)x.x, g0);
+                g1 = fma(P_im[m], (T)x.y, g1);
+                g2 = fma(P_re[m + 1], (T)x.z, g2);
+                g3 = fma(P_im[m + 1], (T)x.w, g3);
+              }
+              g = (g0 - g1) + (g2 - g3);
+            } else {
+  #pragma unroll
+              for (int m = 0; m < MODES; ++m) {
+                const Cplx<T> x = xr[m];
+                g = fma(P_re[m], x.c, g);
+                g = fma(-P_im[m], x.s, g);
+              }
             }
             e = vout * t_exp<T>(FT.amp * g);
           }
@@ -734,14 +779,29 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   const EpsDev& F = *a.eps_host;
   SampleThresholds TH;
   make_thresholds(F, a.N, a.s, &TH);
+  // Fourier tables: D rotation tables [n_modes][s] and the cell start phases
+  // [warps][cells per warp][MODES], as complex pairs
+  auto fourier_launch = [&](auto kern, int modes) -> cudaError_t {
+    const size_t bytes =
+        sizeof(Cplx<T>) * ((size_t)D * modes * a.s + (size_t)(kAsmThreads / 32) * (32 / G) * (modes + 1));
+    if (bytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<(int)blocks, kAsmThreads, bytes, st>>>(F, TH, a);
+    return cudaSuccess;
+  };
   switch (F.kind) {
     case EPS_CONST: assemble_kernel<D, T, EPS_CONST, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
     case EPS_DISC: assemble_kernel<D, T, EPS_DISC, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
-    case EPS_FOURIER:
-      if (F.n_modes <= 8) assemble_kernel<D, T, EPS_FOURIER, 8><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a);
-      else if (F.n_modes <= 16) assemble_kernel<D, T, EPS_FOURIER, 16><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a);
-      else assemble_kernel<D, T, EPS_FOURIER, kMaxModes><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a);
+    case EPS_FOURIER: {
+      cudaError_t e;
+      if (F.n_modes <= 8) e = fourier_launch(assemble_kernel<D, T, EPS_FOURIER, 8>, 8);
+      else if (F.n_modes <= 16) e = fourier_launch(assemble_kernel<D, T, EPS_FOURIER, 16>, 16);
+      else e = fourier_launch(assemble_kernel<D, T, EPS_FOURIER, kMaxModes>, kMaxModes);
+      if (e != cudaSuccess) return e;
       break;
+    }
     case EPS_BOXES: assemble_kernel<D, T, EPS_BOXES, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
     case EPS_THETA: assemble_kernel<D, T, EPS_THETA, 1><<<(int)blocks, kAsmThreads, 0, st>>>(F, TH, a); break;
     default: return cudaErrorInvalidValue;

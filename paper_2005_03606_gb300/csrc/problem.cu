@@ -2130,15 +2130,58 @@ mg_status mg_apply_level(mg_problem* P, int level, int op, int inner, const doub
 }
 
 mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_launch) {
-  if (!P || reps < 1 || which < 0 || which > 3 || !ms_per_launch) {
+  if (!P || reps < 1 || which < 0 || which > 4 || !ms_per_launch) {
     set_error("bad arguments");
     return MG_ERR_INVALID;
   }
   Level& l0 = P->lev[0];
+  const int vec64 = P->mixed ? 0 : 1;
+  // which = 4: the integration kernel alone on chunk 0 at the final accuracy
+  // (its interface cells, or every cell), into scratch outputs
+  AsmLaunch a{};
+  void* asm_out = nullptr;
+  uint8_t* asm_cls = nullptr;
+  if (which == 4) {
+    if (jobs_pending(P)) {
+      set_error("delayed assembly jobs are in flight");
+      return MG_ERR_PENDING;
+    }
+    const int NP = P->dim == 3 ? 28 : 6;
+    a.dim = P->dim;
+    a.N = P->N;
+    a.s = final_s(P);
+    a.kind = P->eps.kind;
+    a.prec64 = P->mixed ? 0 : 1;
+    a.cell0 = 0;
+    a.ncell = P->chunk_cells;
+    a.eps_host = &P->eps;
+    a.hfac = fine_op(P).hfac;
+    a.eps_c = P->eps_c;
+    a.nseg_x = P->nseg_x;
+    a.tau = P->desc.compress_tau;
+    if (P->ilist) {
+      a.list = P->ilist;
+      a.nlist = P->ilist_n[0];
+    }
+    cudaError_t e = P->mixed ? mg_malloc_async(&asm_cls, (size_t)P->chunk_nseg * kSegCells, P->st)
+                             : mg_malloc_async(&asm_out, sizeof(double) * NP * (size_t)P->chunk_cells, P->st);
+    if (e == cudaSuccess && P->exact && P->ilist_n[0] > 0)
+      e = mg_malloc_async(&a.out_x64, sizeof(double) * NP * (size_t)P->ilist_n[0], P->st);
+    if (e != cudaSuccess) return oom_or_cuda(e, "profile buffers");
+    if (P->mixed) {
+      a.out_rec = P->scratch;
+      a.out_cls = asm_cls;
+      if (P->exact) {
+        a.eps64 = P->eps64;
+        a.xpos = P->xpos;
+      }
+    } else {
+      a.out_full = asm_out;
+    }
+  }
   cudaEvent_t e0, e1;
   MG_CHECK(cudaEventCreate(&e0));
   MG_CHECK(cudaEventCreate(&e1));
-  const int vec64 = P->mixed ? 0 : 1;
   auto launch = [&](int i) -> cudaError_t {
     void* x = (i & 1) ? l0.x1 : l0.x0;
     void* y = (i & 1) ? l0.x0 : l0.x1;
@@ -2146,7 +2189,8 @@ mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_l
       case 0: return launch_sweep(l0.op, SW_JACOBI, vec64, x, l0.b, y, P->desc.omega, nullptr, nullptr, P->st);
       case 1: return launch_sweep(l0.op, SW_MATVEC, 1, P->p, P->r, P->q, 0.0, P->partials, nullptr, P->st);
       case 2: return launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->q, 0.0, nullptr, nullptr, P->st);
-      default: return launch_galerkin(l0.op, P->mixed ? 0 : 1, P->lev[1].full_store, P->st);
+      case 3: return launch_galerkin(l0.op, P->mixed ? 0 : 1, P->lev[1].full_store, P->st);
+      default: return launch_assemble(a, P->st);
     }
   };
   for (int i = 0; i < 3; ++i) MG_CHECK(launch(i));
@@ -2158,6 +2202,9 @@ mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_l
   MG_CHECK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (asm_out) cudaFreeAsync(asm_out, P->st);
+  if (asm_cls) cudaFreeAsync(asm_cls, P->st);
+  if (a.out_x64) cudaFreeAsync(a.out_x64, P->st);
   *ms_per_launch = ms / reps;
   P->need_restart = true;
   return MG_OK;

@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_profile_kernel": (st, [_VP, ctypes.c_int, ctypes.c_int, _D]),
             "mg_launch_count": (ctypes.c_uint64, []),
             "mg_inject_assembly_failure": (st, [_VP, ctypes.c_int]),
+            "mg_measure_peak": (st, [ctypes.c_int, _D]),
             "mg_assemble_surplus_noalloc": (st, [ctypes.POINTER(mg_eps_desc), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP,
                                                  _VP]),
@@ -345,6 +346,14 @@ class Problem:
         e = np.zeros_like(b)
         _check(load().mg_vcycle_apply(self.h, _p(b), _p(e)))
         return e
+
+
+def measure_peak(kind: int) -> float:
+    """Operations per second of one arithmetic pipe (0 FP32 FMA, 1 FP64 FMA,
+    2 FP32 exp); see mg_measure_peak in include/mg.h."""
+    v = np.zeros(1)
+    _check(load().mg_measure_peak(int(kind), _p(v)))
+    return float(v[0])
 
 
 def assemble_surplus_noalloc(field, dim: int, n_cells: int, s: int, cell0: int, ncell: int, eps_c_ptr: int,
