@@ -159,16 +159,19 @@ struct Cplx {   // (cos, sin) pair
 };
 
 // MODES: compile-time bound of the Fourier mode loops (>= F.n_modes), so that
-// the per-row phases stay in registers; FP32 instances are held to two
-// resident blocks per SM
+// the per-row phases stay in registers; FP32 instances and the
+// piecewise-constant FP64 ones are held to two resident blocks per SM
 template <int D, typename T, int KIND, int MODES>
-__global__ void __launch_bounds__(kAsmThreads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kAsmThreads, (sizeof(T) == 4 || KIND == EPS_BOXES || KIND == EPS_DISC) ? 2 : 1)
     assemble_kernel(const EpsDev F, const SampleThresholds TH, const AsmLaunch A) {
   constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
   constexpr int NW = D == 3 ? 27 : 6;
   const int N = A.N, s = A.s;
   __shared__ T s_t1[kMaxS], s_t2[kMaxS];
   __shared__ XEntryT<T> s_x[kAsmThreads / 32][64];
+  // FP64 exact mode: a group's reduced moment sums, staged for its lanes
+  // (at most 8 cell groups per warp in 3D, 16 in 2D)
+  __shared__ T s_W[sizeof(T) == 8 ? kAsmThreads / 32 : 1][sizeof(T) == 8 ? (D == 3 ? 8 : 16) * NW : 1];
   const FieldT<T> FT(F);
   const T vin = FT.v_in, vout = FT.v_out;
   for (int j = threadIdx.x; j < s; j += blockDim.x) {
@@ -307,16 +310,19 @@ __global__ void __launch_bounds__(kAsmThreads, sizeof(T) == 4 ? 2 : 1)
     // moment sums are integers: with D = 6 s^2, sum_x {1, t1, t2} over those
     // samples is {D n0, 3 s n1, 2 n2} / D (n1 = sum (2j + 1), n2 = sum
     // (3 j^2 + 3 j + 1)), and the J-type factors of the other axes are
-    // integers over D too.  Accumulated in 64-bit integers, scaled once.
+    // integers over D too.  Accumulated in integers, scaled once.
     constexpr bool kIntPath = (KIND == EPS_BOXES || KIND == EPS_DISC) && sizeof(T) == 8;
     const bool use_int = kIntPath && A.eps64 != nullptr && TH.mjump == INT_MAX;
     T wscale = (T)1;
-    if (kIntPath && use_int) {
-      long long WI[NW];
+    const int Dd = 6 * s * s;
+    const bool cin = eref == vin;   // the cell centre lies inside
+    // one lane's rows, summed in AccT: a row adds at most 48 s^5 in magnitude,
+    // so 32-bit sums hold a lane's rows for s <= 16; 64-bit ones beyond
+    auto int_rows = [&](auto acc0) {
+      using AccT = decltype(acc0);
+      AccT WI[NW];
 #pragma unroll
       for (int q = 0; q < NW; ++q) WI[q] = 0;
-      const int Dd = 6 * s * s;
-      const bool cin = eref == vin;   // the cell centre lies inside
       for (int r = lig; r < R && valid && !flat; r += G) {
         const int jy = r % s, jz = (D == 3) ? r / s : 0;
         const int my = m0[1] + jy, mz = m0[2] + jz;
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(kAsmThreads, sizeof(T) == 4 ? 2 : 1)
         if (D == 2) {
 #pragma unroll
           for (int t = 0; t < 3; ++t) {
-            WI[t] += (long long)n0 * Jy[t];
+            WI[t] += (AccT)n0 * Jy[t];
             WI[3 + t] += RJ[t];
           }
         } else {
@@ -369,19 +375,24 @@ __global__ void __launch_bounds__(kAsmThreads, sizeof(T) == 4 ? 2 : 1)
             const int p0 = n0 * Jy[a];
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-              WI[a * 3 + b] += (long long)p0 * Jz[b];
-              WI[9 + a * 3 + b] += (long long)RJ[a] * Jz[b];
-              WI[18 + a * 3 + b] += (long long)RJ[a] * Jy[b];
+              WI[a * 3 + b] += (AccT)p0 * Jz[b];
+              WI[9 + a * 3 + b] += (AccT)RJ[a] * Jz[b];
+              WI[18 + a * 3 + b] += (AccT)RJ[a] * Jy[b];
             }
           }
         }
       }
-      for (int off = G / 2; off >= 1; off >>= 1) {
-#pragma unroll
-        for (int q = 0; q < NW; ++q) WI[q] += __shfl_xor_sync(0xffffffffu, WI[q], off);
-      }
 #pragma unroll
       for (int q = 0; q < NW; ++q) W[q] = (T)WI[q];
+    };
+    if (kIntPath && use_int) {
+      if (s <= 16) int_rows(0);
+      else int_rows(0LL);
+      // the lanes' sums: integers below 2^53, exact in FP64
+      for (int off = G / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) W[q] += __shfl_xor_sync(0xffffffffu, W[q], off);
+      }
       const T dv = cin ? vout - vin : vin - vout;
       wscale = D == 3 ? dv / ((T)Dd * (T)Dd) : dv / (T)Dd;
     } else {
@@ -505,7 +516,96 @@ __global__ void __launch_bounds__(kAsmThreads, sizeof(T) == 4 ? 2 : 1)
         for (int q = 0; q < NW; ++q) W[q] += __shfl_xor_sync(0xffffffffu, W[q], off);
       }
     }
-    if (lig == 0 && valid) {
+    // FP64 exact mode without the adaptive test: the cell's epilogue is split
+    // over its group's lanes (FP64 runs at a small fraction of the FP32 rate
+    // here; one lane doing all of it left the FP64 pipe as the bound)
+    const bool par_epi = sizeof(T) == 8 && !A.prec64 && !A.final_flags;
+    if (par_epi) {
+      if (valid) {
+        const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+        T* Wg = &s_W[warp][grp * NW];
+#pragma unroll
+        for (int q = 0; q < NW; ++q)
+          if (q % G == lig) Wg[q] = W[q];
+        __syncwarp(gmask);
+        T scale = (T)A.hfac * wscale;
+        for (int a = 0; a < D; ++a) scale *= invs;
+        const T ge = eref * (T)A.hfac;
+        const T ge32 = (A.eps64 ? (T)reinterpret_cast<const float*>(A.eps_c)[c] : eref) * (T)A.hfac;
+        // surplus entry (a, b), a < b, from the staged sums (as in the serial epilogue)
+        auto dl_of = [&](int a, int b) -> T {
+          T v = 0;
+          for (int k = 0; k < D; ++k) {
+            const T sg = (((a >> k) & 1) == ((b >> k) & 1)) ? (T)1 : (T)-1;
+            int idx = 0;
+            for (int m = 0; m < D; ++m)
+              if (m != k) idx = idx * 3 + (((a >> m) & 1) + ((b >> m) & 1));
+            v += sg * Wg[k * (NW / D) + idx];
+          }
+          return v * scale;
+        };
+        auto pair_ab = [&](int p, int* a, int* b) {
+          int q = p, r = 0;
+          while (q >= NV - 1 - r) {
+            q -= NV - 1 - r;
+            ++r;
+          }
+          *a = r;
+          *b = r + 1 + q;
+        };
+        T Dm = 0, An = 0;
+        for (int p = lig; p < NP; p += G) {
+          int a, b;
+          pair_ab(p, &a, &b);
+          const T kv = (T)kref_off<D>(popc_small(a ^ b));
+          const T v = dl_of(a, b);
+          const T full = ge * kv + v;
+          Dm = fmax(Dm, fabs(full - ge32 * kv));
+          An = fmax(An, fabs(full));
+        }
+        for (int a = lig; a < NV; a += G) {   // diagonal entries: minus the row sums
+          T rs = 0;
+          for (int b = 0; b < NV; ++b)
+            if (b != a) rs += dl_of(a < b ? a : b, a < b ? b : a);
+          An = fmax(An, fabs(ge * (T)kref_diag<D>() - rs));
+        }
+        for (int off = G / 2; off >= 1; off >>= 1) {
+          Dm = fmax(Dm, __shfl_xor_sync(gmask, Dm, off));
+          An = fmax(An, __shfl_xor_sync(gmask, An, off));
+        }
+        const T Fm = (T)Dim<D>::F, tau = (T)A.tau;
+        int cls;
+        if (Fm * Dm <= tau * An) cls = 0;
+        else if (Fm * Dm * ((T)16 / (T)448) <= tau * An) cls = 1;
+        else if (Fm * Dm * ((T)16 / (T)65504) <= tau * An) cls = 2;
+        else cls = 3;
+        uint8_t* rec = A.out_rec + (size_t)lc * Dim<D>::REC_MAX;
+        const float sc = cls == 1 ? (float)(Dm / (T)448) : (float)(Dm / (T)65504);
+        if (lig == 0 && (cls == 1 || cls == 2)) *reinterpret_cast<float*>(rec) = sc;
+        double* xo = A.out_x64 ? A.out_x64 + (size_t)A.xpos[c] * NP : nullptr;
+        for (int p = lig; p < NP; p += G) {
+          int a, b;
+          pair_ab(p, &a, &b);
+          const T kv = (T)kref_off<D>(popc_small(a ^ b));
+          const T v = dl_of(a, b);
+          const T d = ge * kv + v - ge32 * kv;
+          if (xo) xo[p] = (double)v;
+          if (cls == 1) {
+            __nv_fp8_e4m3 q((float)(d / (T)sc));
+            rec[4 + p] = q.__x;
+          } else if (cls == 2) {
+            *reinterpret_cast<__half*>(rec + 4 + 2 * p) = __float2half_rn((float)(d / (T)sc));
+          } else if (cls == 3) {
+            *reinterpret_cast<float*>(rec + 4 * p) = (float)d;
+          }
+        }
+        if (lig == 0) {
+          const long long row = lc / N;
+          const int x = (int)(lc - row * N);
+          A.out_cls[(row * A.nseg_x + (x >> 5)) * kSegCells + (x & 31)] = (uint8_t)cls;
+        }
+      }
+    } else if (lig == 0 && valid) {
       T scale = (T)A.hfac * wscale;
       for (int a = 0; a < D; ++a) scale *= invs;
       T dl[NP];
@@ -784,10 +884,9 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   auto fourier_launch = [&](auto kern, int modes) -> cudaError_t {
     const size_t bytes =
         sizeof(Cplx<T>) * ((size_t)D * modes * a.s + (size_t)(kAsmThreads / 32) * (32 / G) * (modes + 1));
-    if (bytes > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      if (e != cudaSuccess) return e;
-    }
+    // static plus dynamic shared memory may pass the 48 KB default: opt in
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
     kern<<<(int)blocks, kAsmThreads, bytes, st>>>(F, TH, a);
     return cudaSuccess;
   };
