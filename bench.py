@@ -375,7 +375,8 @@ def run_ours(args, rank, world, local_rank):
                                     u0=u_host)) as P:
         P.assemble(w.s_final)
         rel_fp64_op = P.vcycle(0)
-    serving = serving_leg(mg, args.serving_requests) if args.serving_requests > 0 else None
+    serving = (serving_leg(mg, args.serving_requests, load_factors=(0.5, 0.7, 0.9))
+               if args.serving_requests > 0 else None)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores, _ = oracle_sample(args.workload, int(info0.cycles))
@@ -477,7 +478,7 @@ def serving_leg(mg, n_requests, seed=2004, load_factors=(0.7,), max_active=8):
            "eps": "lognormal, sigma ~ U[0.5, 2], 16 Fourier modes", "path": "mixed delayed, s = 1 -> 8, rtol 1e-8",
            "max_active": max_active,
            "closed_loop": {"solves_per_s": thr, "ok": ok_closed, "seconds": closed_s},
-           "open_loop": open_loops[0]}
+           "open_loop": next((o for o in open_loops if o["load_factor"] == 0.7), open_loops[0])}
     if len(open_loops) > 1:
         out["open_loop_by_load"] = open_loops
     return out

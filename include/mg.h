@@ -403,7 +403,9 @@ mg_status mg_assemble_surplus_noalloc(const mg_eps_desc* eps, int dim, int n_cel
 
 typedef struct {
   int32_t max_active;       /* concurrent solves on the GPU (0 => 8) */
-  int32_t use_graphs;       /* capture each problem's cycle in a CUDA graph */
+  int32_t use_graphs;       /* nonzero: each request replays its outer iteration as a
+                               captured CUDA graph (one graph per request and iteration
+                               kind); 0: kernel by kernel */
   double hbm_budget_bytes;  /* admission budget (0 => free HBM at creation minus 4 GiB) */
   int32_t inject_fail_every;/* tests: fail every k-th admission on the host (0 = off) */
   int32_t pad0;

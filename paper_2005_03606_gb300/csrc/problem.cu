@@ -1047,6 +1047,11 @@ int min_s(const mg_problem* P) {
 }  // namespace
 
 namespace mg {
+// whether a problem replays its outer iteration as a captured CUDA graph
+// (the serving loop's mg_server_desc.use_graphs)
+void problem_use_graphs(mg_problem* P, bool on) {
+  if (P) P->use_graphs = on;
+}
 // field descriptor of the C ABI to the device layout (used by other translation units)
 void eps_desc_to_dev(const mg_eps_desc& d, int dim, EpsDev* e) { fill_eps(d, dim, e); }
 // the descriptor checks of problem creation (MG_OK or MG_ERR_INVALID with the message set)

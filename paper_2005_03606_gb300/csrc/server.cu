@@ -17,6 +17,10 @@
 #include <thread>
 #include <vector>
 
+namespace mg {
+void problem_use_graphs(mg_problem* P, bool on);
+}
+
 using namespace mg;
 
 namespace {
@@ -94,6 +98,7 @@ void run_request(mg_server* S, Request* R) {
     st = MG_ERR_INJECTED;
   } else {
     st = mg_create_problem(&R->desc, nullptr, &P);
+    if (st == MG_OK) problem_use_graphs(P, S->desc.use_graphs != 0);
   }
   mg_solve_info info{};
   if (st == MG_OK) st = mg_solve(P, &info);

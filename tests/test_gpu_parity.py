@@ -455,7 +455,8 @@ def test_split_sweep_variants_match_oracle(monkeypatch, env):
     assert np.abs(jac - j_ref).max() <= 0.6 * (tol32 / dmin) * 4 + 1e-6 * np.abs(j_ref).max()
 
 
-def test_serving_results_alone_and_in_mix_agree():
+@pytest.mark.parametrize("graphs", [True, False])
+def test_serving_results_alone_and_in_mix_agree(graphs):
     reqs = [(3, 27, inputs.fourier_field(3, 101, sigma=0.7)), (2, 243, inputs.fourier_field(2, 102, sigma=1.5)),
             (3, 81, inputs.fourier_field(3, 103, sigma=1.0)), (2, 81, inputs.fourier_field(2, 104, sigma=2.0)),
             (3, 27, inputs.fourier_field(3, 105, sigma=2.0))]
@@ -466,7 +467,7 @@ def test_serving_results_alone_and_in_mix_agree():
         with mg.Problem(d) as P:
             P.solve()
             alone.append(P.solution())
-    S = mg.Server(max_active=4)
+    S = mg.Server(max_active=4, use_graphs=graphs)
     ts = [S.submit(d, want_solution=True) for d in descs for _ in range(2)]
     assert S.drain(120000) == mg.MG_OK
     for i, t in enumerate(ts):
