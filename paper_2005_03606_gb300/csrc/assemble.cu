@@ -23,6 +23,9 @@
 #include "mg_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 #include <cstdio>
 #include <climits>
@@ -865,6 +868,20 @@ int grid_for(long long work, int threads) {
   return (int)b;
 }
 
+// raises a kernel's dynamic shared-memory limit once per device and kernel
+cudaError_t opt_in_smem(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, kern})) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.insert({dev, kern});
+  return e;
+}
+
 template <int D, typename T>
 cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   int R = 1;
@@ -884,8 +901,11 @@ cudaError_t launch_assemble_t(const AsmLaunch& a, cudaStream_t st) {
   auto fourier_launch = [&](auto kern, int modes) -> cudaError_t {
     const size_t bytes =
         sizeof(Cplx<T>) * ((size_t)D * modes * a.s + (size_t)(kAsmThreads / 32) * (32 / G) * (modes + 1));
-    // static plus dynamic shared memory may pass the 48 KB default: opt in
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // static plus dynamic shared memory may pass the 48 KB default: opt in once
+    // per instance (assembly runs on several host threads), for its largest
+    // footprint (s = kMaxS, eight cell groups per warp)
+    cudaError_t e = opt_in_smem((const void*)kern,
+                                sizeof(Cplx<T>) * ((size_t)D * modes * kMaxS + (size_t)(kAsmThreads / 32) * 8 * (modes + 1)));
     if (e != cudaSuccess) return e;
     kern<<<(int)blocks, kAsmThreads, bytes, st>>>(F, TH, a);
     return cudaSuccess;

@@ -101,6 +101,7 @@ struct Job {
   cudaEvent_t ev = nullptr;
   ChunkStore store;
   int status = MG_OK;
+  std::string msg;   // the worker thread's error message when status != MG_OK
 };
 
 }  // namespace
@@ -901,7 +902,11 @@ void worker_main(mg_problem* P) {
       job.status = MG_ERR_INJECTED;
     } else {
       job.status = assemble_chunk(P, job.s, job.chunk, P->side, &job.store, 4);
-      if (job.status == MG_OK && cudaEventRecord(job.ev, P->side) != cudaSuccess) job.status = MG_ERR_CUDA;
+      if (job.status == MG_OK && cudaEventRecord(job.ev, P->side) != cudaSuccess) {
+        job.status = MG_ERR_CUDA;
+        set_error("event record failed");
+      }
+      if (job.status != MG_OK) job.msg = last_error();
     }
     {
       std::lock_guard<std::mutex> lk(P->mu);
@@ -967,7 +972,8 @@ mg_status publish_ready(mg_problem* P, bool wait, int* npub) {
     if (j.ev) cudaEventDestroy(j.ev);
     if (j.status != MG_OK) {
       bad = (mg_status)j.status;
-      set_error(j.status == MG_ERR_INJECTED ? "injected assembly failure" : "assembly job failed");
+      if (j.status == MG_ERR_INJECTED) set_error("injected assembly failure");
+      else set_error("assembly job (s = %d, chunk %d) failed: %s", j.s, j.chunk, j.msg.c_str());
       free_store(j.store, P->st);
       continue;
     }

@@ -9,6 +9,8 @@
 #include "mg.h"
 
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -107,6 +109,8 @@ void run_request(mg_server* S, Request* R) {
     for (int a = 0; a < R->desc.dim; ++a) nv *= R->desc.n_cells + 1;
     st = mg_get_solution(P, R->dst, (size_t)nv);
   }
+  if (st != MG_OK && getenv("MG_TRACE"))   // diagnostics: the worker thread's message
+    fprintf(stderr, "mg: request %llu failed (status %d): %s\n", (unsigned long long)R->id, (int)st, mg_last_error());
   if (P) mg_destroy_problem(P);
   R->t_done = Clock::now();
   R->res.status = st;
