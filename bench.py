@@ -520,6 +520,24 @@ def run_probe(args, local_rank):
                           "s": w.s_final, "cells": None if pc else int(ncell), "ms_per_launch": ms,
                           "samples_per_s": None if pc else samples / (ms * 1e-3)}), flush=True)
         return
+    if args.probe == "transfer":   # finest Jacobi sweep pair, residual + restriction, restriction alone
+        w = inputs.workload(args.workload, args.n)
+        rows = []
+        for fused in (True, False):
+            if fused:
+                os.environ["MG_FUSED_RESTRICT"] = "1"
+            else:
+                os.environ.pop("MG_FUSED_RESTRICT", None)
+            d = mg.problem_desc(w.dim, w.n_cells, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(w.s_final,), rtol=1e-8)
+            with mg.Problem(d) as P:
+                P.assemble(w.s_final)
+                rows.append({"fused": fused, "jacobi_ms": P.profile(0, args.probe_reps),
+                             "resid_restrict_ms": P.profile(5, args.probe_reps),
+                             "restrict_ms": P.profile(6, args.probe_reps)})
+        os.environ.pop("MG_FUSED_RESTRICT", None)
+        print(json.dumps({"probe": "transfer", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
+              flush=True)
+        return
     if args.probe == "solve":   # whole mixed delayed solves, for launch lists
         w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED, n_cells=args.n)
         ms = []
@@ -691,7 +709,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
+    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "transfer", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
                                         "adaptive", "starvation", "paths", "paper_format", "cycles", "coarse"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")

@@ -321,6 +321,20 @@ mg_status mg_get_cell_accuracy(const mg_problem* p, int32_t* s_out, size_t n);
 mg_status mg_apply_level(mg_problem* p, int level, int op, int inner, const double* x,
                          const double* b, double* y);
 
+/* Test hooks on the grid transfers of the V-cycle between `level` and
+ * level + 1 (Section "Stencil assembly variants": a sweep fused with the
+ * transfer that follows or precedes it), in the level's V-cycle arithmetic
+ * (inner as in mg_apply_level).  x, b: host (N_level+1)^d FP64 vectors;
+ * c: host (N_level+1+1)^d FP64 vector of level + 1:
+ *   op = 0: out (level + 1 size) = R (b - A x), R = P^T the transpose of the
+ *           d-linear 3:1 prolongation (c is not read)
+ *   op = 1: out (level size) = S(x + P c), S one damped Jacobi sweep with b
+ * The level's fused kernels run where it has them (op = 0 on a split
+ * compressed 3D finest level), the separate passes elsewhere.  Errors:
+ * MG_ERR_INVALID (no level below `level`, null vectors), MG_ERR_CUDA. */
+mg_status mg_apply_transfer(mg_problem* p, int level, int op, int inner, const double* x, const double* b,
+                            const double* c, double* out);
+
 /* Runs one V-cycle e = V(b) on the finest level from e = 0 with the
  * problem's operators; b and e are host (N+1)^d FP64 vectors. */
 mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
@@ -338,6 +352,9 @@ mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
  *              interface cells on piecewise-constant fields, else every cell
  *              of the chunk; outputs go to scratch buffers (the stored
  *              operator is not changed)
+ *   which = 5: finest-level residual and restriction b_c = R (b - A u) in the
+ *              V-cycle arithmetic (the fused kernels where the level has them)
+ *   which = 6: the restriction alone of a finest-level vector
  * The problem's iteration vectors are used as scratch (the next cycle
  * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_PENDING
  * (which = 4 while delayed assembly jobs are in flight), MG_ERR_CUDA. */

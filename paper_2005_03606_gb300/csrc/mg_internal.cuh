@@ -125,6 +125,9 @@ struct LevelOp {
   // operator is applied in difference form, sum_k c_k (u_k - u_v))
   float* tcoef;
   int tcap;
+  // bit v of tmask: vertex v is in the touched list (nullptr: no fused
+  // residual + restriction)
+  uint32_t* tmask;
   // split sweep: eps_c with rows padded to N+1 floats (zero pad), for float4 loads
   const float* eps_pad;
   // levels with full storage (and finest levels whose cells all carry a
@@ -307,10 +310,31 @@ cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const 
 // SW_JACOBI0: damped Jacobi from a zero iterate, y = omega D^-1 b (x is not
 // read); launch_sweep returns cudaErrorNotSupported (launching nothing) on the
 // paths without it, where the caller zeroes x and runs SW_JACOBI
-enum SweepMode { SW_JACOBI = 0, SW_RESID = 1, SW_MATVEC = 2, SW_JACOBI0 = 3 };
+// SW_RESID_RZ, SW_JACOBI_DOT: internal to launch_resid_restrict and
+// launch_jacobi_dot
+enum SweepMode { SW_JACOBI = 0, SW_RESID = 1, SW_MATVEC = 2, SW_JACOBI0 = 3, SW_RESID_RZ = 4, SW_JACOBI_DOT = 5 };
 cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, const void* b,
                          void* y, double omega, double* partials, int* nblocks, cudaStream_t st);
 cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
+// Fused residual + restriction (Section "Stencil assembly variants": the
+// residual sweep and R = P^T in one pass) on a split compressed finest level
+// (3D, FP32): the bulk pass restricts its residuals along z into zr (the
+// fine x-y grid at every coarse plane, (Nc + 1) (N + 1)^2 floats) leaving out
+// the touched vertices, the fix-up pass writes their residuals into rt (a fine
+// vector, other entries untouched), a third pass adds them to zr and an x-y
+// pass forms bc.  cudaErrorNotSupported (nothing launched) on levels without
+// that split or without zr.
+cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, const void* b, void* rt, void* zr,
+                                  void* bc, cudaStream_t st);
+// Damped Jacobi sweep y = x + omega D^-1 (b - A x) fused with the dot product
+// y . dq (the flexible-CG coefficient of the preconditioned residual y) on a
+// split compressed finest level (3D, FP32): partials receives one FP64 partial
+// per block, *nblocks of them.  cudaErrorNotSupported (nothing launched)
+// elsewhere.
+cudaError_t launch_jacobi_dot(const LevelOp& op, const float* x, const float* b, float* y, float omega,
+                              const float* dq, double* partials, int* nblocks, cudaStream_t st);
+// words of the touched-vertex bit mask of a split level
+size_t tmask_words(int N);
 cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void* ef, cudaStream_t st);
 cudaError_t launch_inject(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
@@ -337,9 +361,11 @@ cudaError_t launch_dot(const double* a, const double* b, long long n, double* pa
                        cudaStream_t st);
 cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double* partials, int* nblocks,
                            cudaStream_t st);
-cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out,
-                                 cudaStream_t st);
 enum ScalarOp { SC_SET_BETA = 0, SC_SET_ALPHA = 1 };
+// out[c] = sum over the nblocks partials of component c (ncomp interleaved
+// components); with sc, then the scalar update op on sc (one launch)
+cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out,
+                                 cudaStream_t st, DevScalars* sc = nullptr, int op = -1);
 cudaError_t launch_scalar_op(DevScalars* sc, int op, cudaStream_t st);
 cudaError_t launch_fcg_direction(long long n, int first, int z64, const void* z, double* p,
                                  const DevScalars* sc, cudaStream_t st);

@@ -160,8 +160,17 @@ struct mg_problem {
   uint32_t* tcounts = nullptr;
   float* tcoef = nullptr;
   float* eps_pad = nullptr;
+  // fused residual + restriction on that level: touched-vertex bit mask,
+  // z-restricted residual planes
+  uint32_t* tmask = nullptr;
+  float* zr = nullptr;
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+  // V-cycle enqueue: when set, the finest level's last post-smoothing sweep
+  // also forms z . vdot_q (its partials, vdot_nb of them, left in partials)
+  const float* vdot_q = nullptr;
+  bool vdot_done = false;
+  int vdot_nb = 0;
   int inner_its = 0;
   int last_inner_its = 0;
   bool have_correction = false;
@@ -632,15 +641,28 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
       *stt = oom_or_cuda(e, "pre-smooth");
     std::swap(cur, oth);
   }
-  if ((e = launch_sweep(lv.op, SW_RESID, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
-    *stt = oom_or_cuda(e, "residual");
   Level& lc = P->lev[l + 1];
-  if ((e = launch_restrict(P->dim, lc.N, vec64, oth, lc.b, st)) != cudaSuccess) *stt = oom_or_cuda(e, "restrict");
+  // b_c = R (b - A u): fused where the level supports it (oth then holds the
+  // touched vertices' residuals only), else a residual sweep and a restriction
+  e = l == 0 ? launch_resid_restrict(lv.op, vec64, cur, lv.b, oth, P->zr, lc.b, st) : cudaErrorNotSupported;
+  if (e == cudaErrorNotSupported) {
+    if ((e = launch_sweep(lv.op, SW_RESID, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
+      *stt = oom_or_cuda(e, "residual");
+    if ((e = launch_restrict(P->dim, lc.N, vec64, oth, lc.b, st)) != cudaSuccess) *stt = oom_or_cuda(e, "restrict");
+  } else if (e != cudaSuccess) {
+    *stt = oom_or_cuda(e, "residual and restriction");
+  }
   void* ec = vcycle_enqueue(P, l + 1, stt);
   if ((e = launch_prolong_add(P->dim, lc.N, vec64, ec, cur, st)) != cudaSuccess) *stt = oom_or_cuda(e, "prolong");
   for (int k = 0; k < P->desc.nu_post; ++k) {
-    if ((e = launch_sweep(lv.op, SW_JACOBI, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
-      *stt = oom_or_cuda(e, "post-smooth");
+    e = cudaErrorNotSupported;
+    if (l == 0 && k == P->desc.nu_post - 1 && P->vdot_q && !vec64) {   // with the Krylov dot product
+      e = launch_jacobi_dot(lv.op, (const float*)cur, (const float*)lv.b, (float*)oth, (float)om, P->vdot_q,
+                            P->partials, &P->vdot_nb, st);
+      P->vdot_done = e == cudaSuccess;
+    }
+    if (e == cudaErrorNotSupported) e = launch_sweep(lv.op, SW_JACOBI, vec64, cur, lv.b, oth, om, nullptr, nullptr, st);
+    if (e != cudaSuccess) *stt = oom_or_cuda(e, "post-smooth");
     std::swap(cur, oth);
   }
   return cur;
@@ -772,7 +794,12 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
   const long long n = l0.nvert;
   const int z64 = P->mixed ? 0 : 1;
   mg_status stt = MG_OK;
+  // the flexible-CG dot z . q of the mixed path, fused into the V-cycle's
+  // last sweep where the finest level supports it
+  P->vdot_q = (P->mixed && !first && P->desc.outer == MG_OUTER_FCG) ? P->q32 : nullptr;
+  P->vdot_done = false;
   void* z = cycle_enqueue(P, &stt);
+  P->vdot_q = nullptr;
   if (stt != MG_OK) return stt;
   int nb = 0;
   if (P->mixed) {
@@ -784,14 +811,13 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
     }
     // FP32 flexible CG on A e = r_in, preconditioned by the FP32 V-cycle
     if (!first) {
-      MG_CHECK(launch_dot_f32f32(zf, P->q32, n, P->partials, &nb, st));
-      MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st));
-      MG_CHECK(launch_scalar_op(P->sc, SC_SET_BETA, st));
+      if (P->vdot_done) nb = P->vdot_nb;
+      else MG_CHECK(launch_dot_f32f32(zf, P->q32, n, P->partials, &nb, st));
+      MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st, P->sc, SC_SET_BETA));
     }
     MG_CHECK(launch_fcg32_direction(n, first, zf, P->p32, P->sc, st));
     MG_CHECK(launch_sweep(l0.op, SW_MATVEC, 0, P->p32, rin, P->q32, 0.0, P->partials, &nb, st));
-    MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st));
-    MG_CHECK(launch_scalar_op(P->sc, SC_SET_ALPHA, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st, P->sc, SC_SET_ALPHA));
     MG_CHECK(launch_fcg32_update(n, P->e32, rin, P->p32, P->q32, P->sc, P->partials, &nb, st));
     MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr_in, st));
     return MG_OK;
@@ -807,13 +833,11 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
   if (!first) {
     if (z64) MG_CHECK(launch_dot((const double*)z, P->q, n, P->partials, &nb, st));
     else MG_CHECK(launch_dot_f32((const float*)z, P->q, n, P->partials, &nb, st));
-    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st));
-    MG_CHECK(launch_scalar_op(P->sc, SC_SET_BETA, st));
+    MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st, P->sc, SC_SET_BETA));
   }
   MG_CHECK(launch_fcg_direction(n, first, z64, z, P->p, P->sc, st));
   MG_CHECK(launch_sweep(l0.op, SW_MATVEC, 1, P->p, P->r, P->q, 0.0, P->partials, &nb, st));
-  MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st));
-  MG_CHECK(launch_scalar_op(P->sc, SC_SET_ALPHA, st));
+  MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st, P->sc, SC_SET_ALPHA));
   MG_CHECK(launch_fcg_update(n, P->u, P->r, P->p, P->q, P->sc, P->mixed ? 1 : 0, P->mixed ? l0.b : nullptr,
                              P->partials, &nb, st));
   MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
@@ -1243,6 +1267,18 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     if ((e = dalloc(P, &P->eps_pad, sizeof(float) * (size_t)P->N * P->N * (P->N + 1))) != cudaSuccess)
       return fail(oom_or_cuda(e, "padded eps"));
     l0.op.eps_pad = P->eps_pad;
+    if (!l0.stencil) {
+      // touched-vertex bits (the sweeps fused with a restriction or a dot product)
+      if ((e = dalloc(P, &P->tmask, sizeof(uint32_t) * tmask_words(P->N))) != cudaSuccess)
+        return fail(oom_or_cuda(e, "touched mask"));
+      l0.op.tmask = P->tmask;
+      const size_t nzr = (size_t)(P->N / 3 + 1) * (P->N + 1) * (P->N + 1);
+      // the fused residual + restriction (MG_FUSED_RESTRICT=1; measured slower
+      // than the residual sweep and the tiled restriction on this part: the
+      // bulk pass is latency-bound and gains nothing from the write it saves)
+      if (getenv("MG_FUSED_RESTRICT") && (e = dalloc(P, &P->zr, sizeof(float) * nzr)) != cudaSuccess)
+        return fail(oom_or_cuda(e, "fused restriction buffer"));
+    }
   }
   // outer vectors
   const size_t v8 = sizeof(double) * l0.nvert;
@@ -2140,8 +2176,69 @@ mg_status mg_apply_level(mg_problem* P, int level, int op, int inner, const doub
   return MG_OK;
 }
 
+mg_status mg_apply_transfer(mg_problem* P, int level, int op, int inner, const double* x, const double* b,
+                            const double* c, double* out) {
+  if (!P || level < 0 || level + 1 >= P->L || op < 0 || op > 1 || !x || !b || !out || (op == 1 && !c)) {
+    set_error("bad arguments");
+    return MG_ERR_INVALID;
+  }
+  Level& lv = P->lev[level];
+  Level& lc = P->lev[level + 1];
+  const int vec64 = (inner && P->mixed) ? 0 : 1;
+  const size_t n = lv.nvert, nc = lc.nvert;
+  const size_t eb = vec64 ? 8 : 4;
+  void *dx = nullptr, *db = nullptr, *dy = nullptr, *dc = nullptr;
+  double* tmp = nullptr;
+  cudaError_t e = mg_malloc_async(&dx, eb * n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&db, eb * n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&dy, eb * n, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&dc, eb * nc, P->st);
+  if (e == cudaSuccess) e = mg_malloc_async(&tmp, 8 * n, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "buffers");
+  // host FP64 -> device vector of the level's arithmetic
+  auto upload = [&](const double* h, void* d, size_t m) -> cudaError_t {
+    if (vec64) return cudaMemcpyAsync(d, h, 8 * m, cudaMemcpyHostToDevice, P->st);
+    cudaError_t r = cudaMemcpyAsync(tmp, h, 8 * m, cudaMemcpyHostToDevice, P->st);
+    if (r == cudaSuccess) r = launch_convert(m, 0, tmp, d, P->st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(P->st);   // tmp is reused
+    return r;
+  };
+  auto download = [&](const void* d, double* h, size_t m) -> cudaError_t {
+    if (vec64) return cudaMemcpyAsync(h, d, 8 * m, cudaMemcpyDeviceToHost, P->st);
+    cudaError_t r = launch_convert(m, 1, d, tmp, P->st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(h, tmp, 8 * m, cudaMemcpyDeviceToHost, P->st);
+    return r;
+  };
+  MG_CHECK(upload(x, dx, n));
+  MG_CHECK(upload(b, db, n));
+  MG_CHECK(cudaMemsetAsync(dc, 0, eb * nc, P->st));
+  MG_CHECK(cudaMemsetAsync(dy, 0, eb * n, P->st));
+  if (op == 0) {
+    e = level == 0 ? launch_resid_restrict(lv.op, vec64, dx, db, dy, P->zr, dc, P->st) : cudaErrorNotSupported;
+    if (e == cudaErrorNotSupported) {
+      MG_CHECK(launch_sweep(lv.op, SW_RESID, vec64, dx, db, dy, P->desc.omega, nullptr, nullptr, P->st));
+      e = launch_restrict(P->dim, lc.N, vec64, dy, dc, P->st);
+    }
+    MG_CHECK(e);
+    MG_CHECK(download(dc, out, nc));
+  } else {
+    MG_CHECK(upload(c, dc, nc));
+    MG_CHECK(launch_prolong_add(P->dim, lc.N, vec64, dc, dx, P->st));
+    MG_CHECK(launch_sweep(lv.op, SW_JACOBI, vec64, dx, db, dy, P->desc.omega, nullptr, nullptr, P->st));
+    MG_CHECK(download(dy, out, n));
+  }
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  cudaFreeAsync(dx, P->st);
+  cudaFreeAsync(db, P->st);
+  cudaFreeAsync(dy, P->st);
+  cudaFreeAsync(dc, P->st);
+  cudaFreeAsync(tmp, P->st);
+  MG_CHECK(cudaStreamSynchronize(P->st));
+  return MG_OK;
+}
+
 mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_launch) {
-  if (!P || reps < 1 || which < 0 || which > 4 || !ms_per_launch) {
+  if (!P || reps < 1 || which < 0 || which > 6 || !ms_per_launch || (which >= 5 && P->L < 2)) {
     set_error("bad arguments");
     return MG_ERR_INVALID;
   }
@@ -2201,6 +2298,13 @@ mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_l
       case 1: return launch_sweep(l0.op, SW_MATVEC, 1, P->p, P->r, P->q, 0.0, P->partials, nullptr, P->st);
       case 2: return launch_sweep(l0.op, SW_RESID, 1, P->u, P->f, P->q, 0.0, nullptr, nullptr, P->st);
       case 3: return launch_galerkin(l0.op, P->mixed ? 0 : 1, P->lev[1].full_store, P->st);
+      case 5: {   // b_c = R (b - A u) as in the V-cycle
+        cudaError_t r = launch_resid_restrict(l0.op, vec64, l0.x0, l0.b, l0.x1, P->zr, P->lev[1].b, P->st);
+        if (r != cudaErrorNotSupported) return r;
+        r = launch_sweep(l0.op, SW_RESID, vec64, l0.x0, l0.b, l0.x1, P->desc.omega, nullptr, nullptr, P->st);
+        return r == cudaSuccess ? launch_restrict(P->dim, P->lev[1].N, vec64, l0.x1, P->lev[1].b, P->st) : r;
+      }
+      case 6: return launch_restrict(P->dim, P->lev[1].N, vec64, l0.x1, P->lev[1].b, P->st);
       default: return launch_assemble(a, P->st);
     }
   };

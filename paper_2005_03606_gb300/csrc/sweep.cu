@@ -740,8 +740,10 @@ __device__ __forceinline__ bool next_geo_run(long long& w, long long w1, int nk,
   return true;
 }
 
-__device__ __forceinline__ void geo_share(int ntx, int nty, int N, long long& w0, long long& w1) {
-  const long long total = (long long)ntx * nty * (N - 1);
+// nk: work items per column (interior planes, or coarse planes for the fused
+// residual + restriction)
+__device__ __forceinline__ void geo_share(int ntx, int nty, int nk, long long& w0, long long& w1) {
+  const long long total = (long long)ntx * nty * nk;
   const long long per = (total + gridDim.x - 1) / gridDim.x;
   w0 = min(total, (long long)blockIdx.x * per);
   w1 = min(total, w0 + per);
@@ -821,8 +823,12 @@ struct GeoCtx {
   const float* b;
   float* y;
   const float* eps;
+  float* zr;              // fused residual + restriction: z-restricted residual planes
+  const float* dq;        // Jacobi sweep with a dot product: the other operand
+  const uint32_t* tmask;  // touched-vertex bits (their residuals are added later)
   int N, n1, q, j;
   int k1;                 // last plane of the current z run
+  int K0;                 // fused residual + restriction: first coarse plane of the run
   size_t plane, row0;
   bool hl, hr;
   bool first_row, last_row;   // edge rows of the block also prefetch the halo rows
@@ -857,7 +863,12 @@ template <int MODE, int NT>
 __device__ __forceinline__ void geo_step(const GeoCtx<NT>& c, int k, const Rows6& uc, Rows6& un,
                                          const float (&pyc)[2][5], float (&pyn)[2][5], const float (&gm)[2][5],
                                          float (&gc)[2][5], const float (&yTm)[5], float (&yTc)[5], float& d1,
-                                         float& d2) {
+                                         float& d2, float (&za)[4], float (&zb)[4]) {
+  const size_t v0 = (size_t)k * c.gplane() + c.row0 + c.q;
+  unsigned tw = 0;
+  if (MODE == SW_RESID_RZ || MODE == SW_JACOBI_DOT) tw = __ldg(c.tmask + (v0 >> 5));
+  float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (MODE == SW_JACOBI_DOT) q4 = __ldg(reinterpret_cast<const float4*>(c.dq + v0));
   load_rows6(c.x, (size_t)(k + 1) * c.gplane() + c.row0, c.gn1(), c.q, c.hl, c.hr, un);
   load_eps10(c.eps, c.gN(), k, c.j, c.q, c.hl, c.hr, gc);   // c.eps: padded rows
   geo_prefetch(c, k);
@@ -901,8 +912,8 @@ __device__ __forceinline__ void geo_step(const GeoCtx<NT>& c, int k, const Rows6
     const bool valid = i >= 1 && i <= c.gN() - 1;
     float r;
     // Jacobi: u + omega (b - h/12 w) / (h/3 G), with omega / (h/3) folded into c.omega
-    if (MODE == SW_JACOBI) r = fmaf(c.omega, __fdividef(fmaf(-c.h12, w, bb4[e]), G), uv);
-    else if (MODE == SW_RESID) r = fmaf(-c.h12, w, bb4[e]);
+    if (MODE == SW_JACOBI || MODE == SW_JACOBI_DOT) r = fmaf(c.omega, __fdividef(fmaf(-c.h12, w, bb4[e]), G), uv);
+    else if (MODE == SW_RESID || MODE == SW_RESID_RZ) r = fmaf(-c.h12, w, bb4[e]);
     else {
       const float acc = c.h12 * w;
       r = acc;
@@ -913,21 +924,65 @@ __device__ __forceinline__ void geo_step(const GeoCtx<NT>& c, int k, const Rows6
     }
     out[e] = valid ? r : 0.f;   // boundary vertices stay zero
   }
-  *reinterpret_cast<float4*>(c.y + (size_t)k * c.gplane() + c.row0 + c.q) =
-      make_float4(out[0], out[1], out[2], out[3]);
+  if (MODE == SW_JACOBI_DOT) {   // touched vertices: their term comes from the fix-up pass
+    const unsigned tb = (tw >> (unsigned)(v0 & 31)) & 0xFu;
+    d1 += ((tb & 1u) ? 0.f : out[0] * q4.x) + ((tb & 2u) ? 0.f : out[1] * q4.y) +
+          ((tb & 4u) ? 0.f : out[2] * q4.z) + ((tb & 8u) ? 0.f : out[3] * q4.w);
+  }
+  if (MODE == SW_RESID_RZ) {
+    // z restriction: plane k = 3 cz + m adds (1 - m/3) r to coarse plane cz and
+    // (m/3) r to cz + 1; cz is complete after m = 2.  Touched vertices add
+    // nothing here (zr_fix_kernel adds their fix-up residuals).
+    const unsigned tb = (tw >> (unsigned)(v0 & 31)) & 0xFu;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((tb >> e) & 1u) out[e] = 0.f;
+    const float wa = 1.f / 3.f, wb = 2.f / 3.f;
+    const int cz = k / 3, m = k - 3 * cz;
+    if (m == 0) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) za[e] += out[e];
+    } else if (m == 1) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        za[e] = fmaf(wb, out[e], za[e]);
+        zb[e] = fmaf(wa, out[e], zb[e]);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        za[e] = fmaf(wa, out[e], za[e]);
+        zb[e] = fmaf(wb, out[e], zb[e]);
+      }
+      if (cz >= c.K0)
+        *reinterpret_cast<float4*>(c.zr + (size_t)cz * c.gplane() + c.row0 + c.q) = make_float4(za[0], za[1], za[2], za[3]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        za[e] = zb[e];
+        zb[e] = 0.f;
+      }
+    }
+    return;
+  }
+  *reinterpret_cast<float4*>(c.y + v0) = make_float4(out[0], out[1], out[2], out[3]);
 }
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp op, const float* __restrict__ x,
                                                                   const float* __restrict__ b,
                                                                   float* __restrict__ y, float omega,
-                                                                  double* __restrict__ partials, int ntx, int nty) {
+                                                                  double* __restrict__ partials, int ntx, int nty,
+                                                                  float* __restrict__ zr) {
   __shared__ double sh[2][8];
   GeoCtx<NT> c;
   c.x = x;
   c.b = b;
   c.y = y;
   c.eps = op.eps_pad;
+  c.zr = zr;
+  c.dq = zr;   // SW_JACOBI_DOT: the dot operand comes in the last argument
+  c.tmask = op.tmask;
+  c.K0 = 0;
   c.N = NT ? NT : op.N;
   c.n1 = c.N + 1;
   c.plane = (size_t)c.n1 * c.n1;
@@ -938,12 +993,24 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
   // set the Krylov step lengths), summed over the block in FP64
   float d1 = 0.f, d2 = 0.f;
   long long w, w1;
-  geo_share(ntx, nty, c.gN(), w, w1);
+  // work items: (column, interior plane), or (column, interior coarse plane)
+  // for the fused residual + restriction, whose run over coarse planes
+  // K0 .. K1 marches the fine planes 3 K0 - 2 .. 3 K1 + 2
+  const int nk = MODE == SW_RESID_RZ ? c.gN() / 3 - 1 : c.gN() - 1;
+  geo_share(ntx, nty, nk, w, w1);
   GeoRun run;
-  while (next_geo_run(w, w1, c.gN() - 1, ntx, run)) {
+  float za[4] = {0.f, 0.f, 0.f, 0.f}, zb[4] = {0.f, 0.f, 0.f, 0.f};
+  while (next_geo_run(w, w1, nk, ntx, run)) {
     c.q = 4 * (run.tx * kGeoBX + threadIdx.x);   // vertices q .. q+3
     c.j = 1 + run.ty * kGeoBY + threadIdx.y;
-    const int k0 = run.k0, k1 = run.k1;
+    int k0 = run.k0, k1 = run.k1;
+    if (MODE == SW_RESID_RZ) {
+      c.K0 = k0;
+      k0 = 3 * k0 - 2;
+      k1 = 3 * k1 + 2;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) za[e] = zb[e] = 0.f;
+    }
     if (c.q >= c.gn1() || c.j >= c.gN()) continue;
     c.k1 = k1;
     c.hl = c.q > 0;
@@ -962,9 +1029,9 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
 #pragma unroll
     for (int i = 0; i < 5; ++i) ta[i] = ga[0][i] * (pb[0][i] + pa[0][i]) + ga[1][i] * (pb[1][i] + pa[1][i]);
     for (int k = k0; k <= k1; k += 2) {
-      geo_step<MODE, NT>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2);
+      geo_step<MODE, NT>(c, k, ua, ub, pa, pb, ga, gb, ta, tb, d1, d2, za, zb);
       if (k + 1 > k1) break;
-      geo_step<MODE, NT>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2);
+      geo_step<MODE, NT>(c, k + 1, ub, ua, pb, pa, gb, ga, tb, ta, d1, d2, za, zb);
     }
   }
   if (MODE == SW_MATVEC) {
@@ -974,6 +1041,9 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
       partials[2 * blockIdx.x] = s1;
       partials[2 * blockIdx.x + 1] = s2;
     }
+  } else if (MODE == SW_JACOBI_DOT) {
+    const double s1 = block_sum((double)d1, sh[0]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = s1;
   }
 }
 
@@ -981,11 +1051,13 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
 // full operator (geometric part and decoded surplus): from the precomputed
 // 27-point stencil for the first op.tcap of them, else from the cell records.
 // For SW_MATVEC the difference to the value the bulk pass wrote is added to
-// the dot products.
+// the dot products; for SW_JACOBI_DOT (dot operand dq, touched vertices left
+// out of the bulk pass's sum) the touched vertices' terms.
 template <int MODE>
 __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const float* __restrict__ x,
                                                     const float* __restrict__ b, float* __restrict__ y,
-                                                    float omega, double* __restrict__ partials) {
+                                                    float omega, double* __restrict__ partials,
+                                                    const float* __restrict__ dq) {
   __shared__ double sh[2][8];
   const int N = op.N, n1 = N + 1;
   const int nt = *op.ntouched;
@@ -1049,6 +1121,11 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
         const float r = uv + omega * (bv - Au) / dg;
         wait_bulk();
         y[v] = r;
+      } else if (MODE == SW_JACOBI_DOT) {
+        const float r = uv + omega * (bv - Au) / dg;
+        d1 += r * __ldg(dq + v);   // the bulk pass left the touched vertices out
+        wait_bulk();
+        y[v] = r;
       } else if (MODE == SW_RESID) {
         const float r = bv - Au;
         wait_bulk();
@@ -1066,6 +1143,9 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
       partials[2 * blockIdx.x] = s1;
       partials[2 * blockIdx.x + 1] = 0.0;
     }
+  } else if (MODE == SW_JACOBI_DOT) {
+    const double s1 = block_sum((double)d1, sh[0]);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s1;
   }
 }
 
@@ -1267,7 +1347,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, MINB) sweep3_geo2(const Level
   c.omega = omega;
   double d1 = 0.0, d2 = 0.0;
   long long w, w1;
-  geo_share(ntx, nty, c.N, w, w1);
+  geo_share(ntx, nty, c.N - 1, w, w1);
   GeoRun run;
   while (next_geo_run(w, w1, c.N - 1, ntx, run)) {
     c.q = 2 * (run.tx * kGeoBX + threadIdx.x);   // vertices q, q+1
@@ -1436,14 +1516,20 @@ __global__ void touched_mark_kernel(const LevelOp op, uint8_t* __restrict__ flag
   }
 }
 
-__global__ void touched_count_kernel(long long nv, const uint8_t* __restrict__ flags, uint32_t* __restrict__ counts) {
+// counts of the touched vertices per 32-vertex group; mask (optional) receives
+// the group's bits
+__global__ void touched_count_kernel(long long nv, const uint8_t* __restrict__ flags, uint32_t* __restrict__ counts,
+                                     uint32_t* __restrict__ mask) {
   const int lane = threadIdx.x & 31;
   const long long ng = (nv + 31) / 32;
   for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < ng;
        g += ((long long)gridDim.x * blockDim.x) >> 5) {
     const long long v = g * 32 + lane;
     const unsigned m = __ballot_sync(0xffffffffu, v < nv && flags[v]);
-    if (lane == 0) counts[g] = __popc(m);
+    if (lane == 0) {
+      counts[g] = __popc(m);
+      if (mask) mask[g] = m;
+    }
   }
 }
 
@@ -1528,7 +1614,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp 
   const size_t plane = (size_t)n1 * n1;
   const float c0 = omega / (4.f * -op.gk32);   // omega / (h / 3)
   long long w, w1;
-  geo_share(ntx, nty, N, w, w1);
+  geo_share(ntx, nty, N - 1, w, w1);
   GeoRun run;
   while (next_geo_run(w, w1, N - 1, ntx, run)) {
     const int q = 4 * (run.tx * kGeoBX + threadIdx.x);
@@ -1569,9 +1655,16 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp 
   }
 }
 
+// pdl = false: launched after its predecessor completes (the fix-up reads x
+// and b before its first wait, so it may only overlap a predecessor that
+// writes neither)
 template <int MODE>
 void launch_fixup(const LevelOp& op, const float* x, const float* b, float* y, float omega, double* pfix,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool pdl = true, const float* dq = nullptr) {
+  if (!pdl) {
+    sweep3_fixup<MODE><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix, dq);
+    return;
+  }
 #if MG_FIX_PDL
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(kFixBlocks);
@@ -1582,9 +1675,9 @@ void launch_fixup(const LevelOp& op, const float* x, const float* b, float* y, f
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, sweep3_fixup<MODE>, op, x, b, y, omega, pfix);
+  cudaLaunchKernelEx(&cfg, sweep3_fixup<MODE>, op, x, b, y, omega, pfix, dq);
 #else
-  sweep3_fixup<MODE><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix);
+  sweep3_fixup<MODE><<<kFixBlocks, 256, 0, st>>>(op, x, b, y, omega, pfix, dq);
 #endif
 }
 
@@ -1612,23 +1705,23 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
     launch_fixup<SW_JACOBI0>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_JACOBI) {
     if (op.N == 243)
-      sweep3_geo4<SW_JACOBI, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+      sweep3_geo4<SW_JACOBI, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
     else
-      sweep3_geo4<SW_JACOBI, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+      sweep3_geo4<SW_JACOBI, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
     count_launches(1);
     launch_fixup<SW_JACOBI>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_RESID) {
     if (op.N == 243)
-      sweep3_geo4<SW_RESID, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+      sweep3_geo4<SW_RESID, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
     else
-      sweep3_geo4<SW_RESID, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+      sweep3_geo4<SW_RESID, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
     count_launches(1);
     launch_fixup<SW_RESID>(op, x, b, y, omega, pfix, st);
   } else {
     if (op.N == 243)
-      sweep3_geo4<SW_MATVEC, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+      sweep3_geo4<SW_MATVEC, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
     else
-      sweep3_geo4<SW_MATVEC, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty);
+      sweep3_geo4<SW_MATVEC, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
     count_launches(1);
     launch_fixup<SW_MATVEC>(op, x, b, y, omega, pfix, st);
   }
@@ -1713,34 +1806,210 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
 }
 
 // ---------------------------------------------------------------- transfers
-// b_c(I) = sum_{|delta| <= 2} prod_a (1 - |delta_a| / 3) r_f(3 I + delta)   (R = P^T)
-template <int D, typename TV>
-__global__ void restrict_kernel(int Nc, const TV* __restrict__ rf, TV* __restrict__ bc) {
-  const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
-  long long ni = 1;
-  for (int a = 0; a < D; ++a) ni *= (Nc - 1);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ni;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int I = 1 + (int)(t % (Nc - 1));
-    const int J = 1 + (int)((t / (Nc - 1)) % (Nc - 1));
-    const int K = D == 3 ? 1 + (int)(t / ((long long)(Nc - 1) * (Nc - 1))) : 0;
-    // arithmetic in the vectors' own precision (FP32 V-cycles stay off the FP64 pipe)
-    TV acc = 0;
-    const TV w1[5] = {(TV)(1.0 / 3.0), (TV)(2.0 / 3.0), (TV)1, (TV)(2.0 / 3.0), (TV)(1.0 / 3.0)};
+// b_c(I) = sum_{|delta| <= 2} prod_a w(delta_a) r_f(3 I + delta),
+// w(d) = 1 - |d| / 3   (R = P^T).
+//
+// Tiled and separable: a block owns kRTX x kRTY coarse vertices (I, J).  Per
+// input plane it stages the tile's fine region (x from 3 I0 - 2 to 3 I1 + 2,
+// rows 3 J0 - 2 to 3 J1 + 2) in shared memory with asynchronous copies (the
+// next plane's copies fly while the current plane is restricted), restricts
+// it along x (one entry per fine row and coarse column), then along y (one
+// coarse vertex per thread).  In 3D a block marches over the fine planes
+// 3 K0 - 2 .. 3 K1 + 2 of its chunk of coarse planes K0 .. K1: fine plane
+// k = 3 c + m adds w(m) = 1 - m/3 of its x-y restriction to coarse plane c
+// and m/3 to plane c + 1, and plane c is complete after k = 3 c + 2.
+// Neighbouring chunks share two fine planes (the second read mostly hits L2).
+constexpr int kRTX = 32, kRTY = 8;
+constexpr int kRFX = 3 * kRTX + 2;   // fine columns of a tile
+constexpr int kRFY = 3 * kRTY + 2;   // fine rows of a tile
+constexpr int kRFP = 3 * kRTX + 4;   // padded row: 16-byte aligned rows, whole 4-element groups
+
+// S staged input planes: S - 1 planes of copies are in flight while one is
+// restricted (four for FP32 in 45 KB; two for FP64)
+template <typename TV, int S>
+struct __align__(16) RTile {
+  TV f[S][kRFY][kRFP];
+  TV rx[kRFY][kRTX];   // restricted along x
+};
+
+// asynchronous copy of B (4, 8 or 16) bytes global -> shared, both sides
+// B-aligned; zero fill when !valid (nothing is read)
+template <int B>
+__device__ __forceinline__ void cp_async_bytes(void* dst, const void* src, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned n = valid ? (unsigned)B : 0u;
+  if (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+  else if (B == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+}
+
+// issues (and commits as one group) the copies of the tile at (I0, J0) of the
+// input plane starting at src + zbase.  A row's window starts at the fine x
+// xs = (3 I0 - 2) rounded down to a multiple of 4 elements and holds kRFP
+// elements (the tile's columns sit at offset (3 I0 - 2) - xs); it is copied in
+// the widest pieces its global alignment allows (row starts are 16-byte
+// aligned only when (N + 1) is a multiple of the elements per 16 bytes).
+// Rows past the last interior row N - 1 and pieces starting past x = N are
+// zero filled; the other pieces may read the boundary vertex x = N and the
+// start of the next row (inside the array, since the row is at most N - 1):
+// only coarse vertices outside the grid use those entries.
+template <typename TV>
+__device__ __forceinline__ void rtile_stage(TV (&f)[kRFY][kRFP], const TV* __restrict__ src, int N, long long zbase,
+                                            int I0, int J0) {
+  const int nf1 = N + 1, xs = (3 * I0 - 2) & ~3, y0 = 3 * J0 - 2;
+  constexpr int E = 16 / sizeof(TV), NQ = kRFP / E;   // 16-byte pieces per row
+  if (nf1 % E == 0) {
+    // every row start is 16-byte aligned: the block's threads take the
+    // (row, piece) pairs of the tile in turn
+    const TV* g0 = src + zbase + (long long)y0 * nf1 + xs;
+    const int tid = threadIdx.y * kRTX + threadIdx.x;
 #pragma unroll
-    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz)
-#pragma unroll
-      for (int dy = -2; dy <= 2; ++dy) {
-        const int rowbase = D == 3 ? ((3 * K + dz) * nf1 + (3 * J + dy)) * nf1 : (3 * J + dy) * nf1;
-        const TV wyz = w1[dy + 2] * (D == 3 ? w1[dz + 2] : (TV)1);
-        TV racc = 0;
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) racc += w1[dx + 2] * __ldg(rf + rowbase + 3 * I + dx);
-        acc += wyz * racc;
-      }
-    const long long vc = D == 3 ? ((long long)K * nc1 + J) * nc1 + I : (long long)J * nc1 + I;
-    bc[vc] = (TV)acc;
+    for (int it = 0; it < (kRFY * NQ + kRTX * kRTY - 1) / (kRTX * kRTY); ++it) {
+      const int e = tid + it * kRTX * kRTY;
+      if (e >= kRFY * NQ) break;
+      const int r = e / NQ, q = e - r * NQ;
+      cp_async_bytes<16>(&f[r][E * q], g0 + r * nf1 + E * q, y0 + r <= N - 1 && xs + E * q <= N);
+    }
+    cp_async_commit();
+    return;
   }
+#pragma unroll
+  for (int rr = 0; rr < (kRFY + kRTY - 1) / kRTY; ++rr) {
+    const int r = threadIdx.y + rr * kRTY;   // warp-uniform
+    if (r >= kRFY) break;
+    const int y = y0 + r;
+    const TV* g = src + zbase + (long long)y * nf1 + xs;
+    const unsigned al = (unsigned)((uintptr_t)g & 15);
+    if (al == 0) {
+      constexpr int E = 16 / sizeof(TV);
+      for (int q = threadIdx.x; q < kRFP / E; q += kRTX)
+        cp_async_bytes<16>(&f[r][E * q], g + E * q, y <= N - 1 && xs + E * q <= N);
+    } else if ((al & 7) == 0) {
+      constexpr int E = 8 / sizeof(TV);
+      for (int q = threadIdx.x; q < kRFP / E; q += kRTX)
+        cp_async_bytes<8>(&f[r][E * q], g + E * q, y <= N - 1 && xs + E * q <= N);
+    } else {
+      for (int q = threadIdx.x; q < kRFP; q += kRTX)
+        cp_async_bytes<4>(&f[r][q], g + q, y <= N - 1 && xs + q <= N);
+    }
+  }
+  cp_async_commit();
+}
+
+// x-y restriction of a staged tile whose copies have landed and are visible
+// to the block; one barrier between the x and the y pass.  Returns the value
+// of coarse vertex (I0 + threadIdx.x, J0 + threadIdx.y).
+template <typename TV>
+__device__ __forceinline__ TV rtile_xy(const TV (&f)[kRFY][kRFP], TV (&rx)[kRFY][kRTX]) {
+  const TV wa = (TV)(1.0 / 3.0), wb = (TV)(2.0 / 3.0);
+  // x pass: a thread takes four consecutive coarse columns 4t .. 4t + 3 of one
+  // row, whose windows o + 3k .. o + 3k + 4 (o = (3 I0 - 2) mod 4, 1 for
+  // tiles of 32 columns) lie in the 16 staged values 12t .. 12t + 15 (read as
+  // 16-byte vectors)
+  const int tid = threadIdx.y * kRTX + threadIdx.x;
+  if (tid < kRFY * (kRTX / 4)) {
+    const int r = tid / (kRTX / 4), t = tid - r * (kRTX / 4);
+    TV v[16];
+    if constexpr (sizeof(TV) == 4) {
+      const float4* p = reinterpret_cast<const float4*>(&f[r][12 * t]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 a = p[q];
+        v[4 * q] = a.x;
+        v[4 * q + 1] = a.y;
+        v[4 * q + 2] = a.z;
+        v[4 * q + 3] = a.w;
+      }
+    } else {
+      const double2* p = reinterpret_cast<const double2*>(&f[r][12 * t]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double2 a = p[q];
+        v[2 * q] = a.x;
+        v[2 * q + 1] = a.y;
+      }
+    }
+    constexpr int o = (3 * 1 - 2) & 3;   // the same for every tile: 3 I0 - 2 = 1 + 3 kRTX m
+    static_assert((3 * kRTX) % 4 == 0, "tile origins must share the offset o");
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      rx[r][4 * t + k] = wa * v[o + 3 * k] + wb * v[o + 3 * k + 1] + v[o + 3 * k + 2] + wb * v[o + 3 * k + 3] +
+                         wa * v[o + 3 * k + 4];
+  }
+  __syncthreads();
+  const TV* q = &rx[3 * threadIdx.y][threadIdx.x];
+  return wa * q[0] + wb * q[kRTX] + q[2 * kRTX] + wb * q[3 * kRTX] + wa * q[4 * kRTX];
+}
+
+// TIN = false: the input is the fine vector; the fine planes 3 K0 - 2 ..
+// 3 K1 + 2 are marched and weighted along z.  TIN = true: the input is the
+// z-restricted residual planes of the fused residual + restriction, input
+// plane K is coarse plane K.
+template <typename TV, bool TIN>
+__global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int kchunk, const TV* __restrict__ src,
+                                                                     TV* __restrict__ bc) {
+  constexpr int S = sizeof(TV) == 4 ? 4 : 2;
+  __shared__ RTile<TV, S> s;
+  const int N = 3 * Nc, nf1 = N + 1, nc1 = Nc + 1;
+  const long long plane = (long long)nf1 * nf1;
+  const int I0 = 1 + blockIdx.x * kRTX, J0 = 1 + blockIdx.y * kRTY;
+  const int K0 = 1 + blockIdx.z * kchunk, K1 = min(Nc - 1, K0 + kchunk - 1);
+  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  const bool valid = I <= Nc - 1 && J <= Nc - 1;
+  const TV wa = (TV)(1.0 / 3.0), wb = (TV)(2.0 / 3.0);
+  const int p0 = TIN ? K0 : 3 * K0 - 2, p1 = TIN ? K1 : 3 * K1 + 2;
+  TV acc0 = 0, acc1 = 0;   // coarse planes c and c + 1
+  // one commit group per plane (empty past the last plane), so that waiting
+  // for all but the newest S - 1 groups waits for the current plane
+#pragma unroll
+  for (int q = 0; q < S - 1; ++q) {
+    if (p0 + q <= p1) rtile_stage<TV>(s.f[q], src, N, (long long)(p0 + q) * plane, I0, J0);
+    else cp_async_commit();
+  }
+  for (int p = p0; p <= p1; ++p) {
+    const int i = p - p0;
+    // buffer (i + S - 1) % S was last read by the x pass of plane p - 1,
+    // which every thread finished before that plane's second barrier
+    if (p + S - 1 <= p1) rtile_stage<TV>(s.f[(i + S - 1) % S], src, N, (long long)(p + S - 1) * plane, I0, J0);
+    else cp_async_commit();
+    cp_async_wait<S - 1>();
+    __syncthreads();
+    const TV v = rtile_xy(s.f[i % S], s.rx);
+    if (TIN) {
+      if (valid) bc[((long long)p * nc1 + J) * nc1 + I] = v;
+      continue;
+    }
+    const int c = p / 3, m = p - 3 * c;
+    if (m == 0) {
+      acc0 += v;
+    } else if (m == 1) {
+      acc0 += wb * v;
+      acc1 += wa * v;
+    } else {
+      acc0 += wa * v;
+      acc1 += wb * v;
+      if (c >= K0 && valid) bc[((long long)c * nc1 + J) * nc1 + I] = acc0;
+      acc0 = acc1;
+      acc1 = 0;
+    }
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kRTX * kRTY) restrict2_tile_kernel(int Nc, const TV* __restrict__ rf,
+                                                                     TV* __restrict__ bc) {
+  __shared__ RTile<TV, 1> s;
+  const int N = 3 * Nc, nc1 = Nc + 1;
+  const int I0 = 1 + blockIdx.x * kRTX, J0 = 1 + blockIdx.y * kRTY;
+  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  rtile_stage<TV>(s.f[0], rf, N, 0, I0, J0);
+  cp_async_wait<0>();
+  __syncthreads();
+  const TV v = rtile_xy(s.f[0], s.rx);
+  if (I <= Nc - 1 && J <= Nc - 1) bc[(long long)J * nc1 + I] = v;
 }
 
 // b_c = I r_f: interior coarse vertices take the fine value at the coinciding
@@ -2035,7 +2304,15 @@ __global__ void dot_kernel(const TA* __restrict__ a, const TB* __restrict__ b, l
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void reduce_finish_kernel(const double* __restrict__ partials, int nblocks, int ncomp, double* out) {
+__device__ __forceinline__ void scalar_op(DevScalars* sc, int op) {
+  if (op == SC_SET_BETA) sc->beta = sc->pq != 0.0 ? -sc->zq / sc->pq : 0.0;
+  else if (op == SC_SET_ALPHA) sc->alpha = sc->pq != 0.0 ? sc->pr / sc->pq : 0.0;
+}
+
+// out[c] = sum of the partials of component c; then (sc != nullptr) the
+// scalar update op that reads them
+__global__ void reduce_finish_kernel(const double* __restrict__ partials, int nblocks, int ncomp, double* out,
+                                     DevScalars* sc, int op) {
   __shared__ double sh[32];
   for (int c = 0; c < ncomp; ++c) {
     double acc = 0.0;
@@ -2044,12 +2321,10 @@ __global__ void reduce_finish_kernel(const double* __restrict__ partials, int nb
     if (threadIdx.x == 0) out[c] = s;
     __syncthreads();
   }
+  if (sc && threadIdx.x == 0) scalar_op(sc, op);
 }
 
-__global__ void scalar_kernel(DevScalars* sc, int op) {
-  if (op == SC_SET_BETA) sc->beta = sc->pq != 0.0 ? -sc->zq / sc->pq : 0.0;
-  else sc->alpha = sc->pq != 0.0 ? sc->pr / sc->pq : 0.0;
-}
+__global__ void scalar_kernel(DevScalars* sc, int op) { scalar_op(sc, op); }
 
 template <typename TZ>
 __global__ void fcg_direction_kernel(long long n, int first, const TZ* __restrict__ z, double* __restrict__ p,
@@ -2108,6 +2383,37 @@ __global__ void load_vector_kernel(int N, double val, double* f) {
 
 }  // namespace
 
+// y = x + omega D^-1 (b - A x) and partials[...] of y . dq on a split finest
+// level (bulk pass: one partial per block, then one per fix-up block);
+// cudaErrorNotSupported (nothing launched) elsewhere
+cudaError_t launch_jacobi_dot(const LevelOp& op, const float* x, const float* b, float* y, float omega,
+                              const float* dq, double* partials, int* nblocks, cudaStream_t st) {
+  if (op.dim != 3 || !op.compressed || op.stencil || !op.touched || !op.tmask || !op.eps_pad || op.N < 27 ||
+      (op.N + 1) % 4 != 0 || !dq || !partials)
+    return cudaErrorNotSupported;
+  const int nq = (op.N + 1) / 4;
+  const int ntx = (nq + kGeoBX - 1) / kGeoBX, nty = (op.N - 1 + kGeoBY - 1) / kGeoBY;
+  const long long ntiles = (long long)ntx * nty * (op.N - 1);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  const int nb_bulk = ntiles < 2 * nsm ? (int)ntiles : 2 * nsm;
+  const dim3 blk(kGeoBX, kGeoBY, 1);
+  float* dqf = const_cast<float*>(dq);   // read only (passed in the zr slot)
+  if (op.N == 243)
+    sweep3_geo4<SW_JACOBI_DOT, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, dqf);
+  else
+    sweep3_geo4<SW_JACOBI_DOT, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, dqf);
+  count_launches(1);
+  launch_fixup<SW_JACOBI_DOT>(op, x, b, y, omega, partials + nb_bulk, st, true, dq);
+  *nblocks = nb_bulk + kFixBlocks;
+  return launched();
+}
+
 bool vcycle_tail_supported(const LevelOp& op) {
   return op.N == kTailN && !op.compressed && !op.elem64 && op.stencil != nullptr;
 }
@@ -2161,17 +2467,117 @@ cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, 
 #undef MG_SW
 }
 
-cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st) {
-  long long ni = 1;
-  for (int a = 0; a < dim; ++a) ni *= (Nc - 1);
-  const int g = vgrid(ni);
-  if (dim == 2) {
-    if (vec64) restrict_kernel<2, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
-    else restrict_kernel<2, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
-  } else {
-    if (vec64) restrict_kernel<3, double><<<g, 256, 0, st>>>(Nc, (const double*)rf, (double*)bc);
-    else restrict_kernel<3, float><<<g, 256, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+// coarse planes per block of the 3D restriction: about four resident blocks
+// per SM (their shared-memory rings)
+static int restrict_chunk(int Nc) {
+  const long long ntx = (Nc - 1 + kRTX - 1) / kRTX, nty = (Nc - 1 + kRTY - 1) / kRTY;
+  const long long want = 152LL * 4;
+  const int k = (int)(((long long)(Nc - 1) * ntx * nty + want - 1) / want);
+  return k < 1 ? 1 : k;
+}
+
+size_t tmask_words(int N) {
+  const long long n1 = N + 1;
+  return (size_t)((n1 * n1 * n1 + 31) / 32);
+}
+
+// fused residual + restriction: adds the touched vertices' residuals (rt,
+// from the fix-up pass; zero in the bulk pass) to the z-restricted planes.
+// The sum over the touched vertices (i, j, 3K + dz), |dz| <= 2, of column
+// (i, j) and coarse plane K is formed, in the order of dz, by the one with the
+// smallest dz: one writer per entry, no atomics.
+__global__ void zr_fix_kernel(const LevelOp op, const float* __restrict__ rt, float* __restrict__ zr) {
+  const int N = op.N, n1 = N + 1, Nc = N / 3;
+  const long long plane = (long long)n1 * n1;
+  const int nt = *op.ntouched;
+  const float wz[5] = {1.f / 3.f, 2.f / 3.f, 1.f, 2.f / 3.f, 1.f / 3.f};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const long long v = op.touched[t];
+    const int k = (int)(v / plane);
+    const long long ij = v - (long long)k * plane;
+    // coarse planes K with |k - 3K| <= 2
+    const int Klo = max(1, k / 3), Khi = min(Nc - 1, (k + 2) / 3);
+    if (Klo > Khi) continue;
+    // touched bits of column (i, j) at the planes kb = 3 Klo - 2 .. 3 Khi + 2
+    // (at most eight), read together
+    const int kb = 3 * Klo - 2, ke = 3 * Khi + 2;
+    unsigned bits = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const long long vp = (long long)(kb + q) * plane + ij;
+      if (kb + q <= ke && ((__ldg(op.tmask + (vp >> 5)) >> (vp & 31)) & 1u)) bits |= 1u << q;
+    }
+    for (int K = Klo; K <= Khi; ++K) {
+      const int base = 3 * K - 2 - kb;   // bit of plane 3K - 2
+      // the sum's owner: no touched vertex of the column below k in the window
+      if ((bits >> base) & ((1u << (k - (3 * K - 2))) - 1u)) continue;
+      float add = 0.f;
+#pragma unroll
+      for (int dz = -2; dz <= 2; ++dz) {
+        const long long vp = (long long)(3 * K + dz) * plane + ij;
+        if ((bits >> (base + dz + 2)) & 1u) add = fmaf(wz[dz + 2], __ldg(rt + vp), add);
+      }
+      zr[(long long)K * plane + ij] += add;
+    }
   }
+}
+
+cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, const void* b, void* rt, void* zr,
+                                  void* bc, cudaStream_t st) {
+  if (vec64 || op.dim != 3 || !op.compressed || op.stencil || !zr || !op.tmask || !op.touched || !op.eps_pad ||
+      op.N < 27 || (op.N + 1) % 4 != 0)
+    return cudaErrorNotSupported;
+  const int N = op.N, Nc = N / 3;
+  const float* xf = (const float*)x;
+  const float* bf = (const float*)b;
+  // 1. bulk pass: residuals (zero at the touched vertices) restricted along z
+  const int nq = (N + 1) / 4;
+  const int ntx = (nq + kGeoBX - 1) / kGeoBX, nty = (N - 1 + kGeoBY - 1) / kGeoBY;
+  const long long nitems = (long long)ntx * nty * (Nc - 1);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  const int nb = nitems < 2 * nsm ? (int)nitems : 2 * nsm;
+  const dim3 blk(kGeoBX, kGeoBY, 1);
+  if (N == 243)
+    sweep3_geo4<SW_RESID_RZ, 243><<<nb, blk, 0, st>>>(op, xf, bf, nullptr, 0.f, nullptr, ntx, nty, (float*)zr);
+  else
+    sweep3_geo4<SW_RESID_RZ, 0><<<nb, blk, 0, st>>>(op, xf, bf, nullptr, 0.f, nullptr, ntx, nty, (float*)zr);
+  count_launches(1);
+  // 2. residuals of the touched vertices (full operator) into rt: independent
+  // of the bulk pass, launched as its programmatic dependent
+  launch_fixup<SW_RESID>(op, xf, bf, (float*)rt, 0.f, nullptr, st);
+  count_launches(1);
+  // 3. their z-weighted sums into the z-restricted planes
+  zr_fix_kernel<<<152 * 16, 256, 0, st>>>(op, (const float*)rt, (float*)zr);
+  count_launches(1);
+  // 4. x-y restriction of the z-restricted planes
+  const int kchunk = restrict_chunk(Nc);
+  const dim3 g((Nc - 1 + kRTX - 1) / kRTX, (Nc - 1 + kRTY - 1) / kRTY, (Nc - 1 + kchunk - 1) / kchunk);
+  restrict3_tile_kernel<float, true><<<g, dim3(kRTX, kRTY, 1), 0, st>>>(Nc, kchunk, (const float*)zr, (float*)bc);
+  return launched();
+}
+
+cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st) {
+  if (Nc < 2) return cudaSuccess;   // no interior coarse vertex
+  const int ntx = (Nc - 1 + kRTX - 1) / kRTX, nty = (Nc - 1 + kRTY - 1) / kRTY;
+  const dim3 blk(kRTX, kRTY, 1);
+  if (dim == 2) {
+    const dim3 g(ntx, nty, 1);
+    if (vec64) restrict2_tile_kernel<double><<<g, blk, 0, st>>>(Nc, (const double*)rf, (double*)bc);
+    else restrict2_tile_kernel<float><<<g, blk, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+    return launched();
+  }
+  const int kchunk = restrict_chunk(Nc);
+  const dim3 g(ntx, nty, (Nc - 1 + kchunk - 1) / kchunk);
+  if (vec64)
+    restrict3_tile_kernel<double, false><<<g, blk, 0, st>>>(Nc, kchunk, (const double*)rf, (double*)bc);
+  else
+    restrict3_tile_kernel<float, false><<<g, blk, 0, st>>>(Nc, kchunk, (const float*)rf, (float*)bc);
   return launched();
 }
 
@@ -2271,7 +2677,8 @@ cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* co
   if (e != cudaSuccess) return e;
   touched_mark_kernel<<<152 * 16, 256, 0, st>>>(op, flags, from_xpos);
   count_launches(1);
-  touched_count_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts);
+  uint32_t* tmask = from_xpos ? nullptr : op.tmask;
+  touched_count_kernel<<<152 * 16, 256, 0, st>>>(nv, flags, counts, tmask);
   count_launches(1);
   // exclusive scan of the group counts in 2048-entry tiles, then of the tile totals
   const long long ntiles = (ng + 2047) / 2048;
@@ -2345,8 +2752,9 @@ cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double*
   return launched();
 }
 
-cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st) {
-  reduce_finish_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncomp, out);
+cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st,
+                                 DevScalars* sc, int op) {
+  reduce_finish_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncomp, out, sc, op);
   return launched();
 }
 

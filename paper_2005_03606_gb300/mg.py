@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mg_get_cell_matrices": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t, _D]),
             "mg_apply_level": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
             "mg_vcycle_apply": (st, [_VP, _D, _D]),
+            "mg_apply_transfer": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
             "mg_server_create": (st, [ctypes.POINTER(mg_server_desc), ctypes.POINTER(_VP)]),
             "mg_submit": (st, [_VP, ctypes.POINTER(mg_problem_desc), _D, ctypes.POINTER(ctypes.c_uint64)]),
             "mg_poll": (st, [_VP, ctypes.c_uint64, ctypes.POINTER(mg_result)]),
@@ -335,6 +336,24 @@ class Problem:
         bp = _p(np.ascontiguousarray(b, np.float64)) if b is not None else None
         _check(load().mg_apply_level(self.h, level, op, 1 if inner else 0, _p(x), bp, _p(y)))
         return y
+
+    def restrict_residual(self, level: int, x: np.ndarray, b: np.ndarray, inner: bool = False) -> np.ndarray:
+        """R (b - A x) onto level + 1 (mg_apply_transfer, op 0)."""
+        x = np.ascontiguousarray(x, np.float64)
+        b = np.ascontiguousarray(b, np.float64)
+        nc = self.n // 3 ** (level + 1)
+        out = np.zeros((nc + 1) ** self.dim)
+        _check(load().mg_apply_transfer(self.h, level, 0, 1 if inner else 0, _p(x), _p(b), None, _p(out)))
+        return out
+
+    def prolong_smooth(self, level: int, x: np.ndarray, b: np.ndarray, c: np.ndarray, inner: bool = False) -> np.ndarray:
+        """S(x + P c) on the level (mg_apply_transfer, op 1)."""
+        x = np.ascontiguousarray(x, np.float64)
+        b = np.ascontiguousarray(b, np.float64)
+        c = np.ascontiguousarray(c, np.float64)
+        out = np.zeros_like(x)
+        _check(load().mg_apply_transfer(self.h, level, 1, 1 if inner else 0, _p(x), _p(b), _p(c), _p(out)))
+        return out
 
     def profile(self, which: int, reps: int = 20) -> float:
         ms = ctypes.c_double()

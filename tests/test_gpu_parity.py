@@ -220,7 +220,8 @@ def test_galerkin_levels_match_oracle(path, dim, n, fld, s):
 
 
 @pytest.mark.parametrize("path", [mg.PATH_FP64_PLAIN, mg.PATH_MIXED_PLAIN])
-@pytest.mark.parametrize("dim,n,fld", [(2, 81, inputs.disc_field(2)), (3, 27, inputs.fourier_field(3, 35, sigma=1.0))])
+@pytest.mark.parametrize("dim,n,fld", [(2, 81, inputs.disc_field(2)), (3, 27, inputs.fourier_field(3, 35, sigma=1.0)),
+                                       (3, 27, inputs.boxes_field(3, 31))])
 def test_vcycle_matches_oracle(path, dim, n, fld):
     A = _stored_operator(path, fld, n, 4)
     with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(4,))) as P:
@@ -686,3 +687,114 @@ def test_alternative_cycle_implementations_agree(switch, monkeypatch):
         u1 = P.solution()
     assert i1.status == mg.MG_OK and abs(i1.cycles - i0.cycles) <= 1
     assert np.abs(u1 - u0).max() <= 1e-6 * np.abs(u0).max()
+
+
+# ------------------------------------------------------------ transfers fused with sweeps
+TRANSFER_CASES = [
+    (2, 81, inputs.disc_field(2), mg.PATH_FP64_PLAIN, {}),
+    (2, 81, inputs.disc_field(2), mg.PATH_MIXED_PLAIN, {}),
+    (3, 27, inputs.boxes_field(3, 31), mg.PATH_FP64_PLAIN, {}),
+    (3, 27, inputs.boxes_field(3, 31), mg.PATH_MIXED_PLAIN, {}),
+    (3, 27, inputs.boxes_field(3, 31), mg.PATH_MIXED_PLAIN, {"MG_FUSED_RESTRICT": "1"}),   # fused (split level)
+    (3, 27, inputs.boxes_field(3, 31), mg.PATH_MIXED_PLAIN, {"MG_FUSED_RESTRICT": "1", "MG_STENCIL_CAP": "64"}),
+    (3, 81, inputs.disc_field(3, v_in=100.0), mg.PATH_MIXED_PLAIN, {}),
+]
+
+
+@pytest.mark.parametrize("dim,n,fld,path,env", TRANSFER_CASES)
+def test_restricted_residual_matches_oracle(monkeypatch, dim, n, fld, path, env):
+    # R (b - A x) onto the next coarser level in the V-cycle arithmetic: the
+    # fused residual + restriction on split 3D levels (its z-restricted bulk
+    # pass, the touched vertices' fix-up residuals and the x-y pass), the tiled
+    # restriction after a residual sweep elsewhere
+    for k in ("MG_FUSED_RESTRICT", "MG_STENCIL_CAP"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    s = 4
+    stored = _stored_operator(path, fld, n, s)
+    rng = np.random.default_rng(21)
+    m = dense.interior_mask(dim, n)
+    x = rng.standard_normal((n + 1) ** dim) * m
+    b = rng.standard_normal((n + 1) ** dim) * m
+    inner = path == mg.PATH_MIXED_PLAIN
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(s,))) as P:
+        P.assemble(s)
+        out = P.restrict_residual(0, x, b, inner=inner)
+        out2 = P.restrict_residual(0, x, b, inner=inner)
+    nc = n // 3
+    ref = oracle.restrict(dim, nc, oracle.residual(dim, n, stored, b, x))
+    mc = dense.interior_mask(dim, nc)
+    assert np.all(out[~mc] == 0.0)
+    # the restriction weights sum to 3^d per coarse vertex
+    rscale = (np.abs(stored).max() * np.abs(x).max() * (1 << dim) * 8 + np.abs(b).max()) * 3 ** dim
+    tol = (1e-11 if not inner else 2e-6) * rscale
+    assert np.abs(out - ref).max() <= tol
+    assert np.array_equal(out, out2)   # deterministic: no atomics in the sums
+
+
+@pytest.mark.parametrize("dim,n,fld,path,env", [c for c in TRANSFER_CASES if not c[4]])
+def test_prolonged_smoothing_matches_oracle(dim, n, fld, path, env):
+    # S(x + P c): prolongation of a coarse correction, then one damped Jacobi sweep
+    s = 4
+    stored = _stored_operator(path, fld, n, s)
+    rng = np.random.default_rng(22)
+    m = dense.interior_mask(dim, n)
+    nc = n // 3
+    x = rng.standard_normal((n + 1) ** dim) * m
+    b = rng.standard_normal((n + 1) ** dim) * m
+    c = rng.standard_normal((nc + 1) ** dim) * dense.interior_mask(dim, nc)
+    inner = path == mg.PATH_MIXED_PLAIN
+    with mg.Problem(mg.problem_desc(dim, n, fld, path=path, s_schedule=(s,))) as P:
+        P.assemble(s)
+        out = P.prolong_smooth(0, x, b, c, inner=inner)
+    xp = oracle.prolong_add(dim, nc, c, x)
+    ref = oracle.jacobi(dim, n, stored, b, xp, 0.6)
+    dmin = np.abs(oracle.diag(dim, n, stored)[m]).min()
+    scale = np.abs(stored).max() * np.abs(xp).max() * (1 << dim) * 8 + np.abs(b).max()
+    tol = (1e-11 if not inner else 2e-5) * (scale / dmin + np.abs(xp).max())
+    assert np.all(out[~m] == 0.0)
+    assert np.abs(out - ref).max() <= tol
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_full_size_fused_restriction_sampled(monkeypatch, fused):
+    # 243^3 boxes at s = 8, the launch configuration of the benchmark's
+    # V-cycle (the separate residual sweep and tiled restriction) and the fused
+    # residual + restriction: R (b - A x) at sampled coarse vertices (random
+    # ones and ones above a cell with a surplus record), each from the
+    # oracle's residual at its 5^3 fine vertices
+    if fused:
+        monkeypatch.setenv("MG_FUSED_RESTRICT", "1")
+    else:
+        monkeypatch.delenv("MG_FUSED_RESTRICT", raising=False)
+    w = inputs.workload("boxes3d")
+    n = w.n_cells
+    n1, nc = n + 1, n // 3
+    nc1 = nc + 1
+    line = np.zeros(n1, bool)
+    line[1:n] = True
+    mask = (line[:, None, None] & line[None, :, None] & line[None, None, :]).reshape(-1)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(n1 ** 3) * mask
+    b = rng.standard_normal(n1 ** 3) * mask
+    with mg.Problem(mg.problem_desc(3, n, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,))) as P:
+        P.assemble(8)
+        out = P.restrict_residual(0, x, b, inner=True)
+        cls_all, _ = P.cell_data()
+    nz = np.flatnonzero(cls_all)
+    cz = rng.choice(nz, 24, replace=False)
+    # the coarse vertex nearest to the cell's upper corner
+    near = [tuple(min(nc - 1, max(1, (int(v) + 1 + 1) // 3)) for v in (c % n, (c // n) % n, c // (n * n))) for c in cz]
+    rand = [tuple(int(t) for t in rng.integers(1, nc, 3)) for _ in range(24)]
+    w1 = np.array([1.0 / 3.0, 2.0 / 3.0, 1.0, 2.0 / 3.0, 1.0 / 3.0])
+    d = np.arange(-2, 3)
+    for (I, J, K) in near + rand:
+        fi, fj, fk = np.meshgrid(3 * I + d, 3 * J + d, 3 * K + d, indexing="ij")
+        verts = ((fk * n1 + fj) * n1 + fi).reshape(-1)
+        wts = (w1[:, None, None] * w1[None, :, None] * w1[None, None, :]).reshape(-1)
+        Ax, _, scale = _oracle_vertex_rows(w.eps, n, 8, verts, x)
+        ref = np.sum(wts * (b[verts] - Ax))
+        got = out[(K * nc1 + J) * nc1 + I]
+        tol = 2e-5 * np.sum(wts * (scale + np.abs(b[verts]))) + 1e-7 * np.abs(ref)
+        assert abs(got - ref) <= tol, (I, J, K, got, ref)
