@@ -533,7 +533,10 @@ def run_probe(args, local_rank):
                 P.assemble(w.s_final)
                 rows.append({"fused": fused, "jacobi_ms": P.profile(0, args.probe_reps),
                              "resid_restrict_ms": P.profile(5, args.probe_reps),
-                             "restrict_ms": P.profile(6, args.probe_reps)})
+                             "restrict_ms": P.profile(6, args.probe_reps),
+                             "vcycle_ms": P.profile(7, args.probe_reps),
+                             "vcycle_coarse_ms": P.profile(8, args.probe_reps),
+                             "vcycle_coarse2_ms": P.profile(9, args.probe_reps)})
         os.environ.pop("MG_FUSED_RESTRICT", None)
         print(json.dumps({"probe": "transfer", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
               flush=True)

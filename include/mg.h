@@ -355,6 +355,10 @@ mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
  *   which = 5: finest-level residual and restriction b_c = R (b - A u) in the
  *              V-cycle arithmetic (the fused kernels where the level has them)
  *   which = 6: the restriction alone of a finest-level vector
+ *   which = 7: one V-cycle of the solve from the finest level (right-hand side
+ *              and iterate buffers as they stand)
+ *   which = 8: the same from the next coarser level
+ *   which = 9: the same from the level below that
  * The problem's iteration vectors are used as scratch (the next cycle
  * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_PENDING
  * (which = 4 while delayed assembly jobs are in flight), MG_ERR_CUDA. */

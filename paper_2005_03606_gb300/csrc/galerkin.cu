@@ -236,6 +236,7 @@ __global__ void coarse_factor_kernel(const LevelOp op, double* L) {
 
 template <int D, typename TV>
 __global__ void coarse_solve_kernel(const double* __restrict__ L, const TV* __restrict__ b, TV* __restrict__ e) {
+  pdl_begin();
   constexpr int n = Dim<D>::NV;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double z[n];
@@ -443,11 +444,11 @@ cudaError_t launch_coarse_factor(const LevelOp& coarsest, double* L, cudaStream_
 
 cudaError_t launch_coarse_solve(int dim, const double* L, int vec64, const void* b, void* e, cudaStream_t st) {
   if (dim == 2) {
-    if (vec64) coarse_solve_kernel<2, double><<<1, 32, 0, st>>>(L, (const double*)b, (double*)e);
-    else coarse_solve_kernel<2, float><<<1, 32, 0, st>>>(L, (const float*)b, (float*)e);
+    if (vec64) launch_chain(coarse_solve_kernel<2, double>, 1, 32, 0, st, L, (const double*)b, (double*)e);
+    else launch_chain(coarse_solve_kernel<2, float>, 1, 32, 0, st, L, (const float*)b, (float*)e);
   } else {
-    if (vec64) coarse_solve_kernel<3, double><<<1, 32, 0, st>>>(L, (const double*)b, (double*)e);
-    else coarse_solve_kernel<3, float><<<1, 32, 0, st>>>(L, (const float*)b, (float*)e);
+    if (vec64) launch_chain(coarse_solve_kernel<3, double>, 1, 32, 0, st, L, (const double*)b, (double*)e);
+    else launch_chain(coarse_solve_kernel<3, float>, 1, 32, 0, st, L, (const float*)b, (float*)e);
   }
   return launched();
 }

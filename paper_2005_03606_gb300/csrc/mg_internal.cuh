@@ -148,6 +148,44 @@ struct LevelOp {
   const int* ntouched64;
 };
 
+// ------------------------------------------------------------ programmatic dependent launch
+// A kernel launched with programmatic stream serialization may start while
+// its predecessor in the stream still runs.  griddepcontrol.wait blocks the
+// calling thread until the predecessor grid completed and its memory is
+// visible (a no-op in a kernel launched without the attribute);
+// griddepcontrol.launch_dependents lets the next such kernel be scheduled
+// once every block of this grid executed it (or exited), so a grid never
+// waits on a dependent that took the slots its own unscheduled blocks need.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// kernels of the short latency-bound chains (coarse levels, transfers) begin with this
+__device__ __forceinline__ void pdl_begin() {
+  pdl_trigger();
+  pdl_wait();
+}
+
+// whether the coarse-level and transfer kernels are launched as programmatic
+// dependents of their predecessors (MG_NO_PDL=1 turns it off)
+bool pdl_enabled();
+
+// launches kern (which calls pdl_begin() before reading what a predecessor
+// writes) with programmatic stream serialization when enabled
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chain(void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st,
+                                Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------ helpers
 __device__ __forceinline__ long long cell_index(int D, int N, int i, int j, int k) {
   return D == 2 ? (long long)j * N + i : ((long long)k * N + j) * N + i;
@@ -374,10 +412,15 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
                               int* nblocks, cudaStream_t st);
 cudaError_t launch_richardson_update(long long n, double* u, int z64, const void* z, cudaStream_t st);
 // FP32 inner solve of the mixed path
-cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, const DevScalars* sc,
+// p = z + beta p (first = 1: p = z); first = 0 also applies the deferred
+// correction step e += alpha p of the previous iteration (alpha in sc)
+cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, float* e, const DevScalars* sc,
                                    cudaStream_t st);
-cudaError_t launch_fcg32_update(long long n, float* e, float* r, const float* p, const float* q,
-                                const DevScalars* sc, double* partials, int* nblocks, cudaStream_t st);
+// r -= alpha q and partials of r.r (the matching e += alpha p is deferred)
+cudaError_t launch_fcg32_update(long long n, float* r, const float* q, const DevScalars* sc, double* partials,
+                                int* nblocks, cudaStream_t st);
+// e += alpha p: applies the last deferred correction step
+cudaError_t launch_fcg32_flush(long long n, float* e, const float* p, const DevScalars* sc, cudaStream_t st);
 cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st);
 cudaError_t launch_apply_correction(long long n, double* u, const float* e, const DevScalars* sc, cudaStream_t st);
 cudaError_t launch_dot_f32f32(const float* a, const float* b, long long n, double* partials, int* nblocks,

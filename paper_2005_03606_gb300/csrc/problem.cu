@@ -174,6 +174,7 @@ struct mg_problem {
   int inner_its = 0;
   int last_inner_its = 0;
   bool have_correction = false;
+  bool e_pending = false;         // e32 still lacks the last step alpha p (FP32 flexible CG)
   bool trace = false;             // MG_TRACE: outer-loop trace on stderr
   double eta_min = 1e-2;          // smallest relative reduction asked of one FP32 inner solve
   double eta2 = 1e-10;            // inner tolerance (squared, relative to the unit-scaled residual)
@@ -759,6 +760,10 @@ mg_status outer_restart(mg_problem* P) {
   if (P->mixed) {
     MG_CHECK(launch_scale_residual(l0.nvert, P->r, (float*)l0.b, P->sc, st));
     MG_CHECK(cudaMemsetAsync(P->e32, 0, sizeof(float) * l0.nvert, st));
+    if (P->e_pending) {   // a discarded correction: its deferred step goes with it
+      MG_CHECK(cudaMemsetAsync(&P->sc->alpha, 0, sizeof(double), st));
+      P->e_pending = false;
+    }
     P->last_inner_its = P->inner_its;
     P->inner_its = 0;
     P->have_correction = false;
@@ -778,6 +783,13 @@ mg_status outer_restart(mg_problem* P) {
 // u += s e (mixed paths): the FP32 correction of the inner solve in FP64
 mg_status apply_inner_correction(mg_problem* P, bool reliable = false) {
   if (!P->mixed || !P->have_correction) return MG_OK;
+  if (P->e_pending) {
+    // the deferred step; alpha then reads zero, so that a next iteration that
+    // keeps the search direction adds nothing to the fresh correction
+    MG_CHECK(launch_fcg32_flush(P->lev[0].nvert, P->e32, P->p32, P->sc, P->st));
+    MG_CHECK(cudaMemsetAsync(&P->sc->alpha, 0, sizeof(double), P->st));
+    P->e_pending = false;
+  }
   MG_CHECK(launch_apply_correction(P->lev[0].nvert, P->u, P->e32, P->sc, P->st));
   P->have_correction = false;
   P->resid_fresh = false;
@@ -815,10 +827,10 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
       else MG_CHECK(launch_dot_f32f32(zf, P->q32, n, P->partials, &nb, st));
       MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->zq, st, P->sc, SC_SET_BETA));
     }
-    MG_CHECK(launch_fcg32_direction(n, first, zf, P->p32, P->sc, st));
+    MG_CHECK(launch_fcg32_direction(n, first, zf, P->p32, P->e32, P->sc, st));
     MG_CHECK(launch_sweep(l0.op, SW_MATVEC, 0, P->p32, rin, P->q32, 0.0, P->partials, &nb, st));
     MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st, P->sc, SC_SET_ALPHA));
-    MG_CHECK(launch_fcg32_update(n, P->e32, rin, P->p32, P->q32, P->sc, P->partials, &nb, st));
+    MG_CHECK(launch_fcg32_update(n, rin, P->q32, P->sc, P->partials, &nb, st));
     MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr_in, st));
     return MG_OK;
   }
@@ -900,6 +912,7 @@ void set_inner_tolerance(mg_problem* P) {
 mg_status mixed_after_iteration(mg_problem* P, bool* diverged) {
   P->inner_its++;
   P->have_correction = true;
+  if (P->desc.outer == MG_OUTER_FCG) P->e_pending = true;
   const double rin = P->h_sc->rr_in;
   *diverged = !std::isfinite(rin) || rin > 1e8;
   if (*diverged) return MG_OK;
@@ -2238,7 +2251,8 @@ mg_status mg_apply_transfer(mg_problem* P, int level, int op, int inner, const d
 }
 
 mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_launch) {
-  if (!P || reps < 1 || which < 0 || which > 6 || !ms_per_launch || (which >= 5 && P->L < 2)) {
+  if (!P || reps < 1 || which < 0 || which > 9 || !ms_per_launch || (which >= 5 && P->L < 2) ||
+      (which == 9 && P->L < 3)) {
     set_error("bad arguments");
     return MG_ERR_INVALID;
   }
@@ -2305,6 +2319,13 @@ mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_l
         return r == cudaSuccess ? launch_restrict(P->dim, P->lev[1].N, vec64, l0.x1, P->lev[1].b, P->st) : r;
       }
       case 6: return launch_restrict(P->dim, P->lev[1].N, vec64, l0.x1, P->lev[1].b, P->st);
+      case 7:
+      case 8:
+      case 9: {   // one V-cycle from the finest level, or from the next coarser ones
+        mg_status stt = MG_OK;
+        vcycle_enqueue(P, which - 7, &stt);
+        return stt == MG_OK ? cudaSuccess : cudaErrorUnknown;
+      }
       default: return launch_assemble(a, P->st);
     }
   };

@@ -326,6 +326,7 @@ template <int D, typename TV, typename TA, typename TS, int MODE>
 __global__ void __launch_bounds__(kBX * kBY) stencil_sweep_kernel(const LevelOp op, const TV* __restrict__ x,
                                                                   const TV* __restrict__ b, TV* __restrict__ y,
                                                                   TA omega, double* __restrict__ partials) {
+  pdl_begin();
   constexpr int C = D == 3 ? 13 : 4;   // centre of the 3^d stencil
   __shared__ double sh[2][kBX * kBY / 32];
   const int N = op.N, n1 = N + 1;
@@ -756,9 +757,6 @@ __device__ __forceinline__ void geo_share(int ntx, int nty, int nk, long long& w
 #ifndef MG_FIX_PDL
 #define MG_FIX_PDL 1
 #endif
-__device__ __forceinline__ void pdl_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
 
 // L2 prefetch of one address (no register, no scoreboard wait)
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -1741,19 +1739,19 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, ni);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
     if (mode == SW_JACOBI0)
-      stencil_sweep_kernel<3, float, float, float, SW_JACOBI0><<<grd, blk, 0, st>>>(op, (const float*)x,
+      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_JACOBI0>, grd, blk, 0, st, op, (const float*)x,
                                                                                   (const float*)b, (float*)y,
                                                                                   (float)omega, partials);
     else if (mode == SW_JACOBI)
-      stencil_sweep_kernel<3, float, float, float, SW_JACOBI><<<grd, blk, 0, st>>>(op, (const float*)x,
+      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_JACOBI>, grd, blk, 0, st, op, (const float*)x,
                                                                                  (const float*)b, (float*)y,
                                                                                  (float)omega, partials);
     else if (mode == SW_RESID)
-      stencil_sweep_kernel<3, float, float, float, SW_RESID><<<grd, blk, 0, st>>>(op, (const float*)x,
+      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_RESID>, grd, blk, 0, st, op, (const float*)x,
                                                                                 (const float*)b, (float*)y,
                                                                                 (float)omega, partials);
     else
-      stencil_sweep_kernel<3, float, float, float, SW_MATVEC><<<grd, blk, 0, st>>>(op, (const float*)x,
+      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_MATVEC>, grd, blk, 0, st, op, (const float*)x,
                                                                                  (const float*)b, (float*)y,
                                                                                  (float)omega, partials);
     return launched();
@@ -1767,13 +1765,13 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
     if (mode == SW_JACOBI0)
-      stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI0><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      launch_chain(stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI0>, grd, blk, 0, st, op, xv, bv, yv, (TA)omega, partials);
     else if (mode == SW_JACOBI)
-      stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      launch_chain(stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI>, grd, blk, 0, st, op, xv, bv, yv, (TA)omega, partials);
     else if (mode == SW_RESID)
-      stencil_sweep_kernel<D, TV, TA, TS, SW_RESID><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      launch_chain(stencil_sweep_kernel<D, TV, TA, TS, SW_RESID>, grd, blk, 0, st, op, xv, bv, yv, (TA)omega, partials);
     else
-      stencil_sweep_kernel<D, TV, TA, TS, SW_MATVEC><<<grd, blk, 0, st>>>(op, xv, bv, yv, (TA)omega, partials);
+      launch_chain(stencil_sweep_kernel<D, TV, TA, TS, SW_MATVEC>, grd, blk, 0, st, op, xv, bv, yv, (TA)omega, partials);
     return launched();
   }
   // the plane-streaming kernel needs enough (x, y, z-run) tiles to fill the GPU;
@@ -1951,6 +1949,7 @@ __device__ __forceinline__ TV rtile_xy(const TV (&f)[kRFY][kRFP], TV (&rx)[kRFY]
 template <typename TV, bool TIN>
 __global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int kchunk, const TV* __restrict__ src,
                                                                      TV* __restrict__ bc) {
+  pdl_begin();
   constexpr int S = sizeof(TV) == 4 ? 4 : 2;
   __shared__ RTile<TV, S> s;
   const int N = 3 * Nc, nf1 = N + 1, nc1 = Nc + 1;
@@ -2001,6 +2000,7 @@ __global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int
 template <typename TV>
 __global__ void __launch_bounds__(kRTX * kRTY) restrict2_tile_kernel(int Nc, const TV* __restrict__ rf,
                                                                      TV* __restrict__ bc) {
+  pdl_begin();
   __shared__ RTile<TV, 1> s;
   const int N = 3 * Nc, nc1 = Nc + 1;
   const int I0 = 1 + blockIdx.x * kRTX, J0 = 1 + blockIdx.y * kRTY;
@@ -2033,6 +2033,7 @@ __global__ void inject_kernel(int Nc, const TV* __restrict__ rf, TV* __restrict_
 // e_f += P e_c (d-linear interpolation on the 3:1 refined grid)
 template <int D, typename TV>
 __global__ void prolong_kernel(int Nc, const TV* __restrict__ ec, TV* __restrict__ ef) {
+  pdl_begin();
   // one thread per interior fine vertex: x from the block's x range, y from
   // blockIdx.y/threadIdx.y, z from blockIdx.z (3D)
   const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
@@ -2076,6 +2077,7 @@ __global__ void prolong_kernel(int Nc, const TV* __restrict__ ec, TV* __restrict
 // one float4 read-modify-write per thread.  Fine boundary vertices in x get
 // P e_c = 0 added (the coarse boundary values are zero).
 __global__ void prolong3_x4_kernel(int Nc, const float* __restrict__ ec, float* __restrict__ ef) {
+  pdl_begin();
   const int nc1 = Nc + 1, Nf = 3 * Nc, nf1 = Nf + 1;
   const int q = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int fy = 1 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -2142,6 +2144,7 @@ __global__ void __launch_bounds__(kTailThreads) vcycle_tail_kernel(const float* 
                                                                    float* __restrict__ xout,
                                                                    const double* __restrict__ Ainv, float omega,
                                                                    int nu_pre, int nu_post) {
+  pdl_begin();
   using T = TailDims<D>;
   constexpr int n1 = T::n1, nv = T::nv, NS = T::NS, C = D == 3 ? 13 : 4;   // C: centre of the 3^d block
   extern __shared__ float tail_smem[];
@@ -2383,6 +2386,11 @@ __global__ void load_vector_kernel(int N, double val, double* f) {
 
 }  // namespace
 
+bool pdl_enabled() {
+  static const bool on = !getenv("MG_NO_PDL");
+  return on;
+}
+
 // y = x + omega D^-1 (b - A x) and partials[...] of y . dq on a split finest
 // level (bulk pass: one partial per block, then one per fix-up block);
 // cudaErrorNotSupported (nothing launched) elsewhere
@@ -2426,10 +2434,10 @@ cudaError_t launch_vcycle_tail(const LevelOp& op, const double* Lc, const float*
     static const cudaError_t attr = cudaFuncSetAttribute(
         vcycle_tail_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tail_smem_bytes<3>());
     if (attr != cudaSuccess) return attr;
-    vcycle_tail_kernel<3><<<1, kTailThreads, tail_smem_bytes<3>(), st>>>((const float*)op.stencil, b, x, Lc + n * n,
+    launch_chain(vcycle_tail_kernel<3>, 1, kTailThreads, tail_smem_bytes<3>(), st, (const float*)op.stencil, b, x, Lc + n * n,
                                                                           omega, nu_pre, nu_post);
   } else {
-    vcycle_tail_kernel<2><<<1, kTailThreads, tail_smem_bytes<2>(), st>>>((const float*)op.stencil, b, x, Lc + n * n,
+    launch_chain(vcycle_tail_kernel<2>, 1, kTailThreads, tail_smem_bytes<2>(), st, (const float*)op.stencil, b, x, Lc + n * n,
                                                                           omega, nu_pre, nu_post);
   }
   return launched();
@@ -2558,7 +2566,7 @@ cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, c
   // 4. x-y restriction of the z-restricted planes
   const int kchunk = restrict_chunk(Nc);
   const dim3 g((Nc - 1 + kRTX - 1) / kRTX, (Nc - 1 + kRTY - 1) / kRTY, (Nc - 1 + kchunk - 1) / kchunk);
-  restrict3_tile_kernel<float, true><<<g, dim3(kRTX, kRTY, 1), 0, st>>>(Nc, kchunk, (const float*)zr, (float*)bc);
+  launch_chain(restrict3_tile_kernel<float, true>, g, dim3(kRTX, kRTY, 1), 0, st, Nc, kchunk, (const float*)zr, (float*)bc);
   return launched();
 }
 
@@ -2568,16 +2576,16 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
   const dim3 blk(kRTX, kRTY, 1);
   if (dim == 2) {
     const dim3 g(ntx, nty, 1);
-    if (vec64) restrict2_tile_kernel<double><<<g, blk, 0, st>>>(Nc, (const double*)rf, (double*)bc);
-    else restrict2_tile_kernel<float><<<g, blk, 0, st>>>(Nc, (const float*)rf, (float*)bc);
+    if (vec64) launch_chain(restrict2_tile_kernel<double>, g, blk, 0, st, Nc, (const double*)rf, (double*)bc);
+    else launch_chain(restrict2_tile_kernel<float>, g, blk, 0, st, Nc, (const float*)rf, (float*)bc);
     return launched();
   }
   const int kchunk = restrict_chunk(Nc);
   const dim3 g(ntx, nty, (Nc - 1 + kchunk - 1) / kchunk);
   if (vec64)
-    restrict3_tile_kernel<double, false><<<g, blk, 0, st>>>(Nc, kchunk, (const double*)rf, (double*)bc);
+    launch_chain(restrict3_tile_kernel<double, false>, g, blk, 0, st, Nc, kchunk, (const double*)rf, (double*)bc);
   else
-    restrict3_tile_kernel<float, false><<<g, blk, 0, st>>>(Nc, kchunk, (const float*)rf, (float*)bc);
+    launch_chain(restrict3_tile_kernel<float, false>, g, blk, 0, st, Nc, kchunk, (const float*)rf, (float*)bc);
   return launched();
 }
 
@@ -2600,18 +2608,18 @@ cudaError_t launch_prolong_add(int dim, int Nc, int vec64, const void* ec, void*
     const int nq = (3 * Nc + 1) / 4;
     const dim3 blk(32, 8, 1);
     const dim3 g((nq + 31) / 32, (3 * Nc - 1 + 7) / 8, 3 * Nc - 1);
-    prolong3_x4_kernel<<<g, blk, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+    launch_chain(prolong3_x4_kernel, g, blk, 0, st, Nc, (const float*)ec, (float*)ef);
     return launched();
   }
   const int nf = 3 * Nc - 1;
   const dim3 blk(32, 8, 1);
   const dim3 g((nf + 31) / 32, (nf + 7) / 8, dim == 3 ? nf : 1);
   if (dim == 2) {
-    if (vec64) prolong_kernel<2, double><<<g, blk, 0, st>>>(Nc, (const double*)ec, (double*)ef);
-    else prolong_kernel<2, float><<<g, blk, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+    if (vec64) launch_chain(prolong_kernel<2, double>, g, blk, 0, st, Nc, (const double*)ec, (double*)ef);
+    else launch_chain(prolong_kernel<2, float>, g, blk, 0, st, Nc, (const float*)ec, (float*)ef);
   } else {
-    if (vec64) prolong_kernel<3, double><<<g, blk, 0, st>>>(Nc, (const double*)ec, (double*)ef);
-    else prolong_kernel<3, float><<<g, blk, 0, st>>>(Nc, (const float*)ec, (float*)ef);
+    if (vec64) launch_chain(prolong_kernel<3, double>, g, blk, 0, st, Nc, (const double*)ec, (double*)ef);
+    else launch_chain(prolong_kernel<3, float>, g, blk, 0, st, Nc, (const float*)ec, (float*)ef);
   }
   return launched();
 }
@@ -2780,31 +2788,51 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
 }
 
 // ---- FP32 inner flexible CG of the mixed path (vectors FP32, dot products FP64)
+// p = z + beta p; first = 0 also applies the previous iteration's deferred
+// correction step e += alpha p (alpha still holds that iteration's step length)
+// before p is overwritten: one pass reads p for both.  first = 1: p = z.
 __global__ void fcg32_direction_kernel(long long n, int first, const float* __restrict__ z, float* __restrict__ p,
-                                       const DevScalars* __restrict__ sc) {
+                                       float* __restrict__ e, const DevScalars* __restrict__ sc) {
   const float beta = first ? 0.f : (float)sc->beta;
+  const float alpha = first ? 0.f : (float)sc->alpha;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n4 = 0;
-  if (aligned16(z) && aligned16(p)) {
+  if (aligned16(z) && aligned16(p) && aligned16(e)) {
     n4 = n / 4;
     const float4* z4 = reinterpret_cast<const float4*>(z);
     float4* p4 = reinterpret_cast<float4*>(p);
+    float4* e4 = reinterpret_cast<float4*>(e);
     for (long long t = t0; t < n4; t += stride) {
       const float4 a = __ldg(z4 + t);
       if (first) {
         p4[t] = a;
       } else {
         const float4 o = p4[t];
+        float4 ev = e4[t];
+        ev.x = fmaf(alpha, o.x, ev.x);
+        ev.y = fmaf(alpha, o.y, ev.y);
+        ev.z = fmaf(alpha, o.z, ev.z);
+        ev.w = fmaf(alpha, o.w, ev.w);
+        e4[t] = ev;
         p4[t] = make_float4(fmaf(beta, o.x, a.x), fmaf(beta, o.y, a.y), fmaf(beta, o.z, a.z), fmaf(beta, o.w, a.w));
       }
     }
   }
-  for (long long t = 4 * n4 + t0; t < n; t += stride) p[t] = first ? z[t] : z[t] + beta * p[t];
+  for (long long t = 4 * n4 + t0; t < n; t += stride) {
+    if (first) {
+      p[t] = z[t];
+    } else {
+      const float o = p[t];
+      e[t] = fmaf(alpha, o, e[t]);
+      p[t] = fmaf(beta, o, z[t]);
+    }
+  }
 }
 
-__global__ void fcg32_update_kernel(long long n, float* __restrict__ e, float* __restrict__ r,
-                                    const float* __restrict__ p, const float* __restrict__ q,
+// r -= alpha q and the partials of r.r (the correction e += alpha p is deferred
+// to the next direction update or fcg32_flush_kernel)
+__global__ void fcg32_update_kernel(long long n, float* __restrict__ r, const float* __restrict__ q,
                                     const DevScalars* __restrict__ sc, double* partials) {
   __shared__ double sh[8];
   const float alpha = (float)sc->alpha;
@@ -2812,36 +2840,36 @@ __global__ void fcg32_update_kernel(long long n, float* __restrict__ e, float* _
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n4 = 0;
-  if (aligned16(e) && aligned16(r) && aligned16(p) && aligned16(q)) {
+  if (aligned16(r) && aligned16(q)) {
     n4 = n / 4;
-    float4* e4 = reinterpret_cast<float4*>(e);
     float4* r4 = reinterpret_cast<float4*>(r);
-    const float4* p4 = reinterpret_cast<const float4*>(p);
     const float4* q4 = reinterpret_cast<const float4*>(q);
     for (long long t = t0; t < n4; t += stride) {
-      const float4 pv = __ldg(p4 + t), qv = __ldg(q4 + t);
-      float4 ev = e4[t], rv = r4[t];
-      ev.x = fmaf(alpha, pv.x, ev.x);
-      ev.y = fmaf(alpha, pv.y, ev.y);
-      ev.z = fmaf(alpha, pv.z, ev.z);
-      ev.w = fmaf(alpha, pv.w, ev.w);
+      const float4 qv = __ldg(q4 + t);
+      float4 rv = r4[t];
       rv.x = fmaf(-alpha, qv.x, rv.x);
       rv.y = fmaf(-alpha, qv.y, rv.y);
       rv.z = fmaf(-alpha, qv.z, rv.z);
       rv.w = fmaf(-alpha, qv.w, rv.w);
-      e4[t] = ev;
       r4[t] = rv;
       acc += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
     }
   }
   for (long long t = 4 * n4 + t0; t < n; t += stride) {
-    e[t] += alpha * p[t];
     const float rv = r[t] - alpha * q[t];
     r[t] = rv;
     acc += rv * rv;
   }
   const double s = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// e += alpha p: the last deferred correction step, before e is used
+__global__ void fcg32_flush_kernel(long long n, float* __restrict__ e, const float* __restrict__ p,
+                                   const DevScalars* __restrict__ sc) {
+  const float alpha = (float)sc->alpha;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    e[t] = fmaf(alpha, p[t], e[t]);
 }
 
 // r_in = r / s with s = sqrt(rr) (the residual scaled to unit norm, FP32)
@@ -2862,16 +2890,21 @@ __global__ void apply_correction_kernel(long long n, double* __restrict__ u, con
     u[t] += s * (double)e[t];
 }
 
-cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, const DevScalars* sc,
+cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, float* e, const DevScalars* sc,
                                    cudaStream_t st) {
-  fcg32_direction_kernel<<<vgrid((n + 3) / 4), 256, 0, st>>>(n, first, z, p, sc);
+  fcg32_direction_kernel<<<vgrid((n + 3) / 4), 256, 0, st>>>(n, first, z, p, e, sc);
   return launched();
 }
 
-cudaError_t launch_fcg32_update(long long n, float* e, float* r, const float* p, const float* q,
-                                const DevScalars* sc, double* partials, int* nblocks, cudaStream_t st) {
+cudaError_t launch_fcg32_update(long long n, float* r, const float* q, const DevScalars* sc, double* partials,
+                                int* nblocks, cudaStream_t st) {
   *nblocks = kRedBlocks;
-  fcg32_update_kernel<<<kRedBlocks, 256, 0, st>>>(n, e, r, p, q, sc, partials);
+  fcg32_update_kernel<<<kRedBlocks, 256, 0, st>>>(n, r, q, sc, partials);
+  return launched();
+}
+
+cudaError_t launch_fcg32_flush(long long n, float* e, const float* p, const DevScalars* sc, cudaStream_t st) {
+  fcg32_flush_kernel<<<vgrid(n), 256, 0, st>>>(n, e, p, sc);
   return launched();
 }
 
