@@ -541,6 +541,13 @@ def run_probe(args, local_rank):
         print(json.dumps({"probe": "transfer", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
               flush=True)
         return
+    if args.probe == "iteration":   # inner iteration with and without the host round trip
+        w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_PLAIN, n_cells=args.n)
+        with mg.Problem(d) as P:
+            P.solve()
+            rows = {"back_to_back_ms": P.profile(10, args.probe_reps), "with_host_read_ms": P.profile(11, args.probe_reps)}
+        print(json.dumps({"probe": "iteration", "workload": args.workload, "n_cells": w.n_cells, **rows}), flush=True)
+        return
     if args.probe == "solve":   # whole mixed delayed solves, for launch lists
         w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_DELAYED, n_cells=args.n)
         ms = []
@@ -712,7 +719,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "transfer", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
+    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "transfer", "iteration", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
                                         "adaptive", "starvation", "paths", "paper_format", "cycles", "coarse"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")

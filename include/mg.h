@@ -359,6 +359,10 @@ mg_status mg_vcycle_apply(mg_problem* p, const double* b, double* e);
  *              and iterate buffers as they stand)
  *   which = 8: the same from the next coarser level
  *   which = 9: the same from the level below that
+ *   which = 10: one inner iteration of the mixed paths (V-cycle and flexible-CG
+ *              step, replayed as the solve replays it), back to back
+ *   which = 11: the same, each followed by the host's read of the iteration's
+ *              scalars as in mg_solve (the difference is the host round trip)
  * The problem's iteration vectors are used as scratch (the next cycle
  * restarts the outer iteration).  Errors: MG_ERR_INVALID, MG_ERR_PENDING
  * (which = 4 while delayed assembly jobs are in flight), MG_ERR_CUDA. */

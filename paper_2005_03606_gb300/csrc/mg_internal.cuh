@@ -158,10 +158,14 @@ struct LevelOp {
 // waits on a dependent that took the slots its own unscheduled blocks need.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-// kernels of the short latency-bound chains (coarse levels, transfers) begin with this
+// kernels launched by launch_chain begin with this.  The wait comes first: a
+// dependent may then be scheduled only once this grid's predecessors have
+// completed, so a dependent that reads before its own wait (the fix-up pass,
+// which reads only inputs of the sweep before waiting) never sees data of a
+// kernel still running two steps back.
 __device__ __forceinline__ void pdl_begin() {
-  pdl_trigger();
   pdl_wait();
+  pdl_trigger();
 }
 
 // whether the coarse-level and transfer kernels are launched as programmatic

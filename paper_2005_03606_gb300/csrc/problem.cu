@@ -2251,8 +2251,8 @@ mg_status mg_apply_transfer(mg_problem* P, int level, int op, int inner, const d
 }
 
 mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_launch) {
-  if (!P || reps < 1 || which < 0 || which > 9 || !ms_per_launch || (which >= 5 && P->L < 2) ||
-      (which == 9 && P->L < 3)) {
+  if (!P || reps < 1 || which < 0 || which > 11 || !ms_per_launch || (which >= 5 && which <= 9 && P->L < 2) ||
+      (which == 9 && P->L < 3) || (which >= 10 && !P->mixed)) {
     set_error("bad arguments");
     return MG_ERR_INVALID;
   }
@@ -2329,6 +2329,36 @@ mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_l
       default: return launch_assemble(a, P->st);
     }
   };
+  if (which >= 10) {
+    // one inner iteration of the mixed path as the solve runs it (continuing
+    // the Krylov process of the last solve), back to back (10) or each
+    // followed by the host's read of the scalars, as the solve does (11)
+    mg_status s = apply_inner_correction(P);
+    if (s == MG_OK && P->need_restart) s = outer_restart(P);
+    if (s != MG_OK) return s;
+    P->first = false;
+    auto iter = [&]() -> mg_status {
+      mg_status r = outer_iteration(P);
+      if (r == MG_OK && which == 11) r = read_scalars(P);
+      return r;
+    };
+    for (int i = 0; i < 3; ++i)
+      if ((s = iter()) != MG_OK) return s;
+    MG_CHECK(cudaEventRecord(e0, P->st));
+    for (int i = 0; i < reps; ++i)
+      if ((s = iter()) != MG_OK) return s;
+    MG_CHECK(cudaEventRecord(e1, P->st));
+    MG_CHECK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MG_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = ms / reps;
+    P->have_correction = false;   // the extra iterations' correction is dropped
+    P->e_pending = false;
+    P->need_restart = true;
+    return MG_OK;
+  }
   for (int i = 0; i < 3; ++i) MG_CHECK(launch(i));
   MG_CHECK(cudaEventRecord(e0, P->st));
   for (int i = 0; i < reps; ++i) MG_CHECK(launch(i));

@@ -971,6 +971,7 @@ __global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geo4(const LevelOp 
                                                                   float* __restrict__ y, float omega,
                                                                   double* __restrict__ partials, int ntx, int nty,
                                                                   float* __restrict__ zr) {
+  pdl_begin();
   __shared__ double sh[2][8];
   GeoCtx<NT> c;
   c.x = x;
@@ -1056,6 +1057,10 @@ __global__ void __launch_bounds__(256) sweep3_fixup(const LevelOp op, const floa
                                                     const float* __restrict__ b, float* __restrict__ y,
                                                     float omega, double* __restrict__ partials,
                                                     const float* __restrict__ dq) {
+  // the next kernel may be scheduled now: it waits for this grid, which ends
+  // after the bulk pass (this grid was scheduled once the bulk pass's own wait
+  // had returned, so x and b are complete)
+  pdl_trigger();
   __shared__ double sh[2][8];
   const int N = op.N, n1 = N + 1;
   const int nt = *op.ntouched;
@@ -1608,6 +1613,7 @@ __global__ void touched_write_kernel(long long nv, const uint8_t* __restrict__ f
 __global__ void __launch_bounds__(kGeoBX * kGeoBY) sweep3_jacobi0(const LevelOp op, const float* __restrict__ b,
                                                                   float* __restrict__ y, float omega, int ntx,
                                                                   int nty) {
+  pdl_begin();
   const int N = op.N, n1 = N + 1;
   const size_t plane = (size_t)n1 * n1;
   const float c0 = omega / (4.f * -op.gk32);   // omega / (h / 3)
@@ -1698,28 +1704,28 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   if (mode == SW_JACOBI0) {
     // a streaming pass at 48 registers: five resident blocks per SM instead of the bulk pass's two
     const int nb0 = ntiles < MG_J0_BLOCKS_PER_SM * nsm ? (int)ntiles : MG_J0_BLOCKS_PER_SM * nsm;
-    sweep3_jacobi0<<<nb0, blk, 0, st>>>(op, b, y, omega, ntx, nty);
+    launch_chain(sweep3_jacobi0, nb0, blk, 0, st, op, b, y, omega, ntx, nty);
     count_launches(1);
     launch_fixup<SW_JACOBI0>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_JACOBI) {
     if (op.N == 243)
-      sweep3_geo4<SW_JACOBI, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
+      launch_chain(sweep3_geo4<SW_JACOBI, 243>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, nullptr);
     else
-      sweep3_geo4<SW_JACOBI, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
+      launch_chain(sweep3_geo4<SW_JACOBI, 0>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, nullptr);
     count_launches(1);
     launch_fixup<SW_JACOBI>(op, x, b, y, omega, pfix, st);
   } else if (mode == SW_RESID) {
     if (op.N == 243)
-      sweep3_geo4<SW_RESID, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
+      launch_chain(sweep3_geo4<SW_RESID, 243>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, nullptr);
     else
-      sweep3_geo4<SW_RESID, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
+      launch_chain(sweep3_geo4<SW_RESID, 0>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, nullptr);
     count_launches(1);
     launch_fixup<SW_RESID>(op, x, b, y, omega, pfix, st);
   } else {
     if (op.N == 243)
-      sweep3_geo4<SW_MATVEC, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
+      launch_chain(sweep3_geo4<SW_MATVEC, 243>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, nullptr);
     else
-      sweep3_geo4<SW_MATVEC, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, nullptr);
+      launch_chain(sweep3_geo4<SW_MATVEC, 0>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, nullptr);
     count_launches(1);
     launch_fixup<SW_MATVEC>(op, x, b, y, omega, pfix, st);
   }
@@ -2276,6 +2282,7 @@ __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p 
 // FP32 dot product: float4 body when both operands are 16-byte aligned, scalar tail
 __global__ void dot4_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
                             double* partials) {
+  pdl_begin();
   __shared__ double sh[8];
   float acc = 0.f;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -2316,6 +2323,7 @@ __device__ __forceinline__ void scalar_op(DevScalars* sc, int op) {
 // scalar update op that reads them
 __global__ void reduce_finish_kernel(const double* __restrict__ partials, int nblocks, int ncomp, double* out,
                                      DevScalars* sc, int op) {
+  pdl_begin();
   __shared__ double sh[32];
   for (int c = 0; c < ncomp; ++c) {
     double acc = 0.0;
@@ -2413,9 +2421,9 @@ cudaError_t launch_jacobi_dot(const LevelOp& op, const float* x, const float* b,
   const dim3 blk(kGeoBX, kGeoBY, 1);
   float* dqf = const_cast<float*>(dq);   // read only (passed in the zr slot)
   if (op.N == 243)
-    sweep3_geo4<SW_JACOBI_DOT, 243><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, dqf);
+    launch_chain(sweep3_geo4<SW_JACOBI_DOT, 243>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, dqf);
   else
-    sweep3_geo4<SW_JACOBI_DOT, 0><<<nb_bulk, blk, 0, st>>>(op, x, b, y, omega, partials, ntx, nty, dqf);
+    launch_chain(sweep3_geo4<SW_JACOBI_DOT, 0>, nb_bulk, blk, 0, st, op, x, b, y, omega, partials, ntx, nty, dqf);
   count_launches(1);
   launch_fixup<SW_JACOBI_DOT>(op, x, b, y, omega, partials + nb_bulk, st, true, dq);
   *nblocks = nb_bulk + kFixBlocks;
@@ -2495,6 +2503,7 @@ size_t tmask_words(int N) {
 // (i, j) and coarse plane K is formed, in the order of dz, by the one with the
 // smallest dz: one writer per entry, no atomics.
 __global__ void zr_fix_kernel(const LevelOp op, const float* __restrict__ rt, float* __restrict__ zr) {
+  pdl_begin();
   const int N = op.N, n1 = N + 1, Nc = N / 3;
   const long long plane = (long long)n1 * n1;
   const int nt = *op.ntouched;
@@ -2552,16 +2561,16 @@ cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, c
   const int nb = nitems < 2 * nsm ? (int)nitems : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
   if (N == 243)
-    sweep3_geo4<SW_RESID_RZ, 243><<<nb, blk, 0, st>>>(op, xf, bf, nullptr, 0.f, nullptr, ntx, nty, (float*)zr);
+    launch_chain(sweep3_geo4<SW_RESID_RZ, 243>, nb, blk, 0, st, op, xf, bf, nullptr, 0.f, nullptr, ntx, nty, (float*)zr);
   else
-    sweep3_geo4<SW_RESID_RZ, 0><<<nb, blk, 0, st>>>(op, xf, bf, nullptr, 0.f, nullptr, ntx, nty, (float*)zr);
+    launch_chain(sweep3_geo4<SW_RESID_RZ, 0>, nb, blk, 0, st, op, xf, bf, nullptr, 0.f, nullptr, ntx, nty, (float*)zr);
   count_launches(1);
   // 2. residuals of the touched vertices (full operator) into rt: independent
   // of the bulk pass, launched as its programmatic dependent
   launch_fixup<SW_RESID>(op, xf, bf, (float*)rt, 0.f, nullptr, st);
   count_launches(1);
   // 3. their z-weighted sums into the z-restricted planes
-  zr_fix_kernel<<<152 * 16, 256, 0, st>>>(op, (const float*)rt, (float*)zr);
+  launch_chain(zr_fix_kernel, 152 * 16, 256, 0, st, op, (const float*)rt, (float*)zr);
   count_launches(1);
   // 4. x-y restriction of the z-restricted planes
   const int kchunk = restrict_chunk(Nc);
@@ -2749,7 +2758,7 @@ cudaError_t launch_dot(const double* a, const double* b, long long n, double* pa
 cudaError_t launch_dot_f32f32(const float* a, const float* b, long long n, double* partials, int* nblocks,
                               cudaStream_t st) {
   *nblocks = kRedBlocks;
-  dot4_kernel<<<kRedBlocks, 256, 0, st>>>(a, b, n, partials);
+  launch_chain(dot4_kernel, kRedBlocks, 256, 0, st, a, b, n, partials);
   return launched();
 }
 
@@ -2762,7 +2771,7 @@ cudaError_t launch_dot_f32(const float* a, const double* b, long long n, double*
 
 cudaError_t launch_reduce_finish(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st,
                                  DevScalars* sc, int op) {
-  reduce_finish_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncomp, out, sc, op);
+  launch_chain(reduce_finish_kernel, 1, 1024, 0, st, partials, nblocks, ncomp, out, sc, op);
   return launched();
 }
 
@@ -2793,6 +2802,7 @@ cudaError_t launch_fcg_update(long long n, double* u, double* r, const double* p
 // before p is overwritten: one pass reads p for both.  first = 1: p = z.
 __global__ void fcg32_direction_kernel(long long n, int first, const float* __restrict__ z, float* __restrict__ p,
                                        float* __restrict__ e, const DevScalars* __restrict__ sc) {
+  pdl_begin();
   const float beta = first ? 0.f : (float)sc->beta;
   const float alpha = first ? 0.f : (float)sc->alpha;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -2834,6 +2844,7 @@ __global__ void fcg32_direction_kernel(long long n, int first, const float* __re
 // to the next direction update or fcg32_flush_kernel)
 __global__ void fcg32_update_kernel(long long n, float* __restrict__ r, const float* __restrict__ q,
                                     const DevScalars* __restrict__ sc, double* partials) {
+  pdl_begin();
   __shared__ double sh[8];
   const float alpha = (float)sc->alpha;
   float acc = 0.f;
@@ -2867,6 +2878,7 @@ __global__ void fcg32_update_kernel(long long n, float* __restrict__ r, const fl
 // e += alpha p: the last deferred correction step, before e is used
 __global__ void fcg32_flush_kernel(long long n, float* __restrict__ e, const float* __restrict__ p,
                                    const DevScalars* __restrict__ sc) {
+  pdl_begin();
   const float alpha = (float)sc->alpha;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     e[t] = fmaf(alpha, p[t], e[t]);
@@ -2875,6 +2887,7 @@ __global__ void fcg32_flush_kernel(long long n, float* __restrict__ e, const flo
 // r_in = r / s with s = sqrt(rr) (the residual scaled to unit norm, FP32)
 __global__ void scale_residual_kernel(long long n, const double* __restrict__ r, float* __restrict__ rin,
                                       DevScalars* __restrict__ sc) {
+  pdl_begin();
   const double s = sc->rr > 0.0 ? sqrt(sc->rr) : 1.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->s = s;
   const double inv = 1.0 / s;
@@ -2885,6 +2898,7 @@ __global__ void scale_residual_kernel(long long n, const double* __restrict__ r,
 // u += s e (the scaled FP32 correction applied in FP64)
 __global__ void apply_correction_kernel(long long n, double* __restrict__ u, const float* __restrict__ e,
                                         const DevScalars* __restrict__ sc) {
+  pdl_begin();
   const double s = sc->s;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     u[t] += s * (double)e[t];
@@ -2892,29 +2906,29 @@ __global__ void apply_correction_kernel(long long n, double* __restrict__ u, con
 
 cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, float* e, const DevScalars* sc,
                                    cudaStream_t st) {
-  fcg32_direction_kernel<<<vgrid((n + 3) / 4), 256, 0, st>>>(n, first, z, p, e, sc);
+  launch_chain(fcg32_direction_kernel, vgrid((n + 3) / 4), 256, 0, st, n, first, z, p, e, sc);
   return launched();
 }
 
 cudaError_t launch_fcg32_update(long long n, float* r, const float* q, const DevScalars* sc, double* partials,
                                 int* nblocks, cudaStream_t st) {
   *nblocks = kRedBlocks;
-  fcg32_update_kernel<<<kRedBlocks, 256, 0, st>>>(n, r, q, sc, partials);
+  launch_chain(fcg32_update_kernel, kRedBlocks, 256, 0, st, n, r, q, sc, partials);
   return launched();
 }
 
 cudaError_t launch_fcg32_flush(long long n, float* e, const float* p, const DevScalars* sc, cudaStream_t st) {
-  fcg32_flush_kernel<<<vgrid(n), 256, 0, st>>>(n, e, p, sc);
+  launch_chain(fcg32_flush_kernel, vgrid(n), 256, 0, st, n, e, p, sc);
   return launched();
 }
 
 cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st) {
-  scale_residual_kernel<<<vgrid(n), 256, 0, st>>>(n, r, rin, sc);
+  launch_chain(scale_residual_kernel, vgrid(n), 256, 0, st, n, r, rin, sc);
   return launched();
 }
 
 cudaError_t launch_apply_correction(long long n, double* u, const float* e, const DevScalars* sc, cudaStream_t st) {
-  apply_correction_kernel<<<vgrid(n), 256, 0, st>>>(n, u, e, sc);
+  launch_chain(apply_correction_kernel, vgrid(n), 256, 0, st, n, u, e, sc);
   return launched();
 }
 
