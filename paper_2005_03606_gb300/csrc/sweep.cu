@@ -2394,10 +2394,7 @@ __global__ void load_vector_kernel(int N, double val, double* f) {
 
 }  // namespace
 
-bool pdl_enabled() {
-  static const bool on = !getenv("MG_NO_PDL");
-  return on;
-}
+bool pdl_enabled() { return getenv("MG_NO_PDL") == nullptr; }
 
 // y = x + omega D^-1 (b - A x) and partials[...] of y . dq on a split finest
 // level (bulk pass: one partial per block, then one per fix-up block);
