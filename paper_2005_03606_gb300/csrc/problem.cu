@@ -129,6 +129,12 @@ struct mg_problem {
   long long npartials = 0;
   DevScalars* sc = nullptr;
   DevScalars* h_sc = nullptr;     // pinned
+  // mg_solve's iteration pipeline: pinned scalar slots and events of the
+  // iteration being tested and of one enqueued ahead of the test
+  DevScalars* h_slot[2] = {nullptr, nullptr};
+  cudaEvent_t slot_ev[2] = {nullptr, nullptr};
+  bool speculate = true;          // mixed flexible CG: enqueue the next iteration before testing this one
+  double rin_hist[2] = {-1.0, -1.0};  // inner residuals of the last two iterations since the last restart
   double* Lc = nullptr;           // coarse Cholesky factor, then the coarse inverse
   uint8_t* scratch = nullptr;     // assembly records of one chunk (mixed)
   // interface cells per chunk (fields with piecewise-constant eps): only these
@@ -766,6 +772,7 @@ mg_status outer_restart(mg_problem* P) {
     }
     P->last_inner_its = P->inner_its;
     P->inner_its = 0;
+    P->rin_hist[0] = P->rin_hist[1] = -1.0;
     P->have_correction = false;
   }
   // A restart after a reliable update (same operator, the FP32 correction
@@ -909,11 +916,12 @@ void set_inner_tolerance(mg_problem* P) {
 
 // After one inner iteration of the mixed path: apply the correction and ask
 // for a new outer residual once the inner residual met its tolerance.
-mg_status mixed_after_iteration(mg_problem* P, bool* diverged) {
+mg_status mixed_after_iteration(mg_problem* P, double rin, bool* diverged) {
   P->inner_its++;
   P->have_correction = true;
   if (P->desc.outer == MG_OUTER_FCG) P->e_pending = true;
-  const double rin = P->h_sc->rr_in;
+  P->rin_hist[1] = P->rin_hist[0];
+  P->rin_hist[0] = rin;
   *diverged = !std::isfinite(rin) || rin > 1e8;
   if (*diverged) return MG_OK;
   if (P->desc.outer == MG_OUTER_RICHARDSON || rin <= P->eta2 || P->inner_its >= kMaxInner)
@@ -1131,6 +1139,7 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
   fill_eps(d.eps, d.dim, &P->eps);
   if (cudaGetDevice(&P->device) != cudaSuccess) P->device = 0;
   if (const char* ng = getenv("MG_NO_GRAPHS")) P->use_graphs = ng[0] == '0';
+  if (getenv("MG_NO_SPECULATE")) P->speculate = false;
   P->trace = getenv("MG_TRACE") != nullptr;
   auto fail = [&](mg_status s) {
     mg_destroy_problem(P);
@@ -1329,6 +1338,10 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     return fail(oom_or_cuda(e, "scalars"));
   cudaMemsetAsync(P->sc, 0, sizeof(DevScalars), P->st);
   if (!cuda_ok(cudaMallocHost(&P->h_sc, sizeof(DevScalars)), "pinned") ||
+      !cuda_ok(cudaMallocHost(&P->h_slot[0], sizeof(DevScalars)), "pinned") ||
+      !cuda_ok(cudaMallocHost(&P->h_slot[1], sizeof(DevScalars)), "pinned") ||
+      !cuda_ok(cudaEventCreateWithFlags(&P->slot_ev[0], cudaEventDisableTiming), "event") ||
+      !cuda_ok(cudaEventCreateWithFlags(&P->slot_ev[1], cudaEventDisableTiming), "event") ||
       !cuda_ok(cudaMallocHost(&P->h_totals, sizeof(uint32_t) * 8), "pinned"))
     return fail(MG_ERR_CUDA);
   // load vector f_v = f_const h^d, initial guess
@@ -1442,6 +1455,10 @@ mg_status mg_destroy_problem(mg_problem* P) {
     cudaStreamSynchronize(st);
   }
   if (P->h_sc) cudaFreeHost(P->h_sc);
+  for (int i = 0; i < 2; ++i) {
+    if (P->h_slot[i]) cudaFreeHost(P->h_slot[i]);
+    if (P->slot_ev[i]) cudaEventDestroy(P->slot_ev[i]);
+  }
   if (P->h_totals) cudaFreeHost(P->h_totals);
   if (P->side) cudaStreamDestroy(P->side);
   if (P->own_stream && P->st) cudaStreamDestroy(P->st);
@@ -1507,7 +1524,7 @@ mg_status mg_vcycle(mg_problem* P, int n, double* rel_residual) {
     if (P->mixed) {
       s = read_scalars(P);
       bool diverged = false;
-      if (s == MG_OK) s = mixed_after_iteration(P, &diverged);
+      if (s == MG_OK) s = mixed_after_iteration(P, P->h_sc->rr_in, &diverged);
       if (s != MG_OK) return s;
     }
   }
@@ -1569,7 +1586,27 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
   int seg_cycles = 0;
   double op_rr = 0.0;   // mixed paths: true residual at the first restart on the current operator
   int op_cycles = 0;
-  while (P->cycles < d.max_cycles) {
+  bool pipe_next = false;   // an iteration enqueued ahead awaits its test (scalars in h_slot[pipe_slot])
+  int pipe_slot = 0;
+  int ahead_count = 0;
+  // trace entry of an iteration enqueued ahead whose step a correction folded
+  // in before its test (its scalars are read once it has completed)
+  auto trace_folded = [&](int slot) -> mg_status {
+    MG_CHECK(cudaEventSynchronize(P->slot_ev[slot]));
+    mg_trace_entry t{};
+    t.cycle = P->cycles;
+    {
+      std::lock_guard<std::mutex> lk(P->mu);
+      t.pending_jobs = P->in_flight + (int)P->held.size();
+    }
+    t.publishes = P->publishes;
+    const double ffn = P->ff > 0 ? P->ff : 1.0;
+    t.rel_residual_est = std::sqrt(P->rr / ffn) * std::sqrt(std::max(P->h_slot[slot]->rr_in, 0.0));
+    t.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    P->trace_log.push_back(t);
+    return MG_OK;
+  };
+  while (P->cycles < d.max_cycles || pipe_next) {
     int npub = 0;
     mg_status s = publish_ready(P, false, &npub);
     if (s != MG_OK) {
@@ -1580,6 +1617,10 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
     if (npub) {   // the correction computed so far belongs to the old operator: apply it
       s = apply_inner_correction(P);
       if (s != MG_OK) return s;
+      if (P->need_restart && pipe_next) {   // the iteration enqueued ahead is folded in
+        if ((s = trace_folded(pipe_slot)) != MG_OK) return s;
+        pipe_next = false;
+      }
     }
     if (P->need_restart) {
       s = outer_restart(P);
@@ -1593,8 +1634,9 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       if (P->ff <= 0) P->ff = P->rr > 0 ? P->rr : 1.0;
       if (P->mixed) set_inner_tolerance(P);
       if (P->trace)   // MG_TRACE=1: one line per outer restart on stderr
-        fprintf(stderr, "mg: restart at cycle %d  rel %.3e  inner its %d  eta %.1e  final %d\n", P->cycles,
-                std::sqrt(P->rr / (P->ff > 0 ? P->ff : 1.0)), P->last_inner_its, std::sqrt(P->eta2), all_final(P) ? 1 : 0);
+        fprintf(stderr, "mg: restart at cycle %d  rel %.3e  inner its %d  eta %.1e  final %d  ahead %d\n", P->cycles,
+                std::sqrt(P->rr / (P->ff > 0 ? P->ff : 1.0)), P->last_inner_its, std::sqrt(P->eta2),
+                all_final(P) ? 1 : 0, ahead_count);
       // divergence is judged against the residual of the current operator
       // at the last restart (a publication changes the operator)
       seg_rr = P->rr;
@@ -1638,15 +1680,43 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       result = MG_OK;
       break;
     }
-    s = outer_iteration(P);
-    if (s != MG_OK) return s;
-    s = read_scalars(P);
-    if (s != MG_OK) return s;
+    // Iteration pipeline.  Every iteration copies its scalars into a pinned
+    // slot and records an event; the host tests it after that event only.
+    // Mixed flexible CG: when the last two inner residuals predict that the
+    // iteration under test stays at least ten times above the inner
+    // tolerance, the next one is enqueued before the test, so the GPU works
+    // on it during the host's round trip.  A wrong guess adds one more
+    // flexible-CG step to the correction (folded in when it is applied).
+    auto enqueue_iter = [&](int slot) -> mg_status {
+      mg_status r = outer_iteration(P);
+      if (r != MG_OK) return r;
+      MG_CHECK(cudaMemcpyAsync(P->h_slot[slot], P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->st));
+      MG_CHECK(cudaEventRecord(P->slot_ev[slot], P->st));
+      return MG_OK;
+    };
+    int cur = pipe_slot;
+    if (!pipe_next) {
+      cur = 0;
+      if ((s = enqueue_iter(cur)) != MG_OK) return s;
+    }
+    bool ahead = false;
+    if (P->mixed && P->speculate && d.outer == MG_OUTER_FCG && P->cycles + 1 < d.max_cycles &&
+        P->inner_its + 2 < kMaxInner && P->rin_hist[0] > 0.0 && P->rin_hist[1] > 0.0) {
+      const double pred = P->rin_hist[0] * (P->rin_hist[0] / P->rin_hist[1]);
+      if (std::isfinite(pred) && pred > 10.0 * P->eta2) {
+        if ((s = enqueue_iter(cur ^ 1)) != MG_OK) return s;
+        ahead = true;
+      }
+    }
+    MG_CHECK(cudaEventSynchronize(P->slot_ev[cur]));
+    const DevScalars& hs = *P->h_slot[cur];
+    P->rr = hs.rr;
+    *P->h_sc = hs;
     ++seg_cycles;
     ++op_cycles;
     {
       mg_trace_entry t{};
-      t.cycle = P->cycles;
+      t.cycle = ahead ? P->cycles - 1 : P->cycles;
       {
         std::lock_guard<std::mutex> lk(P->mu);
         t.pending_jobs = P->in_flight + (int)P->held.size();
@@ -1654,23 +1724,31 @@ mg_status mg_solve(mg_problem* P, mg_solve_info* info) {
       t.publishes = P->publishes;
       t.restarted = restarted ? 1 : 0;
       const double ffn = P->ff > 0 ? P->ff : 1.0;
-      t.rel_residual_est = P->mixed ? std::sqrt(P->rr / ffn) * std::sqrt(std::max(P->h_sc->rr_in, 0.0))
+      t.rel_residual_est = P->mixed ? std::sqrt(P->rr / ffn) * std::sqrt(std::max(hs.rr_in, 0.0))
                                     : std::sqrt(P->rr / ffn);
       t.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       P->trace_log.push_back(t);
       restarted = false;
     }
+    bool stop = false;
     if (P->mixed) {
       bool diverged = false;
-      s = mixed_after_iteration(P, &diverged);
+      s = mixed_after_iteration(P, hs.rr_in, &diverged);
       if (s != MG_OK) return s;
       if (diverged) {
         result = MG_ERR_DIVERGED;
         set_error("inner residual diverged after %d cycles", P->cycles);
-        break;
+        stop = true;
       }
-      continue;
     }
+    // the iteration enqueued ahead is tested next, unless a correction applied
+    // now already folded it in
+    if (ahead) ++ahead_count;
+    if (ahead && !stop && P->need_restart && (s = trace_folded(cur ^ 1)) != MG_OK) return s;
+    pipe_next = ahead && !stop && !P->need_restart;
+    pipe_slot = cur ^ 1;
+    if (stop) break;
+    if (P->mixed) continue;
     if (!std::isfinite(P->rr) || (seg_cycles > 5 && P->rr > 1e4 * std::max(seg_rr, 1e-300))) {
       result = MG_ERR_DIVERGED;
       set_error("residual diverged: ||r||^2 = %.3e after %d cycles (%.3e at the last restart)", P->rr,

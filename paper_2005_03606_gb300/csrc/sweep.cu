@@ -322,14 +322,16 @@ __global__ void build_stencil_kernel(const LevelOp op, TS* __restrict__ out) {
   }
 }
 
-template <int D, typename TV, typename TA, typename TS, int MODE>
+// NT > 0: the grid size as a compile-time constant (strides fold into address
+// arithmetic of constants); NT = 0: from the LevelOp
+template <int D, typename TV, typename TA, typename TS, int MODE, int NT = 0>
 __global__ void __launch_bounds__(kBX * kBY) stencil_sweep_kernel(const LevelOp op, const TV* __restrict__ x,
                                                                   const TV* __restrict__ b, TV* __restrict__ y,
                                                                   TA omega, double* __restrict__ partials) {
   pdl_begin();
   constexpr int C = D == 3 ? 13 : 4;   // centre of the 3^d stencil
   __shared__ double sh[2][kBX * kBY / 32];
-  const int N = op.N, n1 = N + 1;
+  const int N = NT ? NT : op.N, n1 = N + 1;
   const int i = 1 + blockIdx.x * kBX + threadIdx.x;
   const int j = 1 + blockIdx.y * kBY + threadIdx.y;
   const int k = D == 3 ? 1 + blockIdx.z : 0;
@@ -1733,6 +1735,32 @@ cudaError_t launch_geo4(const LevelOp& op, int mode, const float* x, const float
   return launched();
 }
 
+// 3D FP32 stencil sweep, specialised for the grid sizes of the benchmark's levels
+template <int NT>
+void launch_stencil3f(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
+                      double* partials, dim3 grd, dim3 blk, cudaStream_t st) {
+  if (mode == SW_JACOBI0)
+    launch_chain(stencil_sweep_kernel<3, float, float, float, SW_JACOBI0, NT>, grd, blk, 0, st, op, x, b, y, omega,
+                 partials);
+  else if (mode == SW_JACOBI)
+    launch_chain(stencil_sweep_kernel<3, float, float, float, SW_JACOBI, NT>, grd, blk, 0, st, op, x, b, y, omega,
+                 partials);
+  else if (mode == SW_RESID)
+    launch_chain(stencil_sweep_kernel<3, float, float, float, SW_RESID, NT>, grd, blk, 0, st, op, x, b, y, omega,
+                 partials);
+  else
+    launch_chain(stencil_sweep_kernel<3, float, float, float, SW_MATVEC, NT>, grd, blk, 0, st, op, x, b, y, omega,
+                 partials);
+}
+
+void launch_stencil3f_any(const LevelOp& op, int mode, const float* x, const float* b, float* y, float omega,
+                          double* partials, dim3 grd, dim3 blk, cudaStream_t st) {
+  if (op.N == 27) launch_stencil3f<27>(op, mode, x, b, y, omega, partials, grd, blk, st);
+  else if (op.N == 81) launch_stencil3f<81>(op, mode, x, b, y, omega, partials, grd, blk, st);
+  else if (op.N == 243) launch_stencil3f<243>(op, mode, x, b, y, omega, partials, grd, blk, st);
+  else launch_stencil3f<0>(op, mode, x, b, y, omega, partials, grd, blk, st);
+}
+
 template <int D, typename TV, typename TA, typename TS, bool CMP>
 cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const void* b, void* y, double omega,
                            double* partials, int* nblocks, cudaStream_t st) {
@@ -1744,22 +1772,7 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     dim3 blk(kBX, kBY, 1);
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, ni);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
-    if (mode == SW_JACOBI0)
-      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_JACOBI0>, grd, blk, 0, st, op, (const float*)x,
-                                                                                  (const float*)b, (float*)y,
-                                                                                  (float)omega, partials);
-    else if (mode == SW_JACOBI)
-      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_JACOBI>, grd, blk, 0, st, op, (const float*)x,
-                                                                                 (const float*)b, (float*)y,
-                                                                                 (float)omega, partials);
-    else if (mode == SW_RESID)
-      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_RESID>, grd, blk, 0, st, op, (const float*)x,
-                                                                                (const float*)b, (float*)y,
-                                                                                (float)omega, partials);
-    else
-      launch_chain(stencil_sweep_kernel<3, float, float, float, SW_MATVEC>, grd, blk, 0, st, op, (const float*)x,
-                                                                                 (const float*)b, (float*)y,
-                                                                                 (float)omega, partials);
+    launch_stencil3f_any(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, grd, blk, st);
     return launched();
   }
   if (D == 3 && CMP && sizeof(TV) == 4 && op.N >= 27 && (op.N + 1) % 4 == 0 && op.touched && op.eps_pad)
@@ -1770,6 +1783,11 @@ cudaError_t sweep_dispatch(const LevelOp& op, int mode, const void* x, const voi
     dim3 blk(kBX, kBY, 1);
     dim3 grd((ni + kBX - 1) / kBX, (ni + kBY - 1) / kBY, D == 3 ? ni : 1);
     if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+    if (D == 3 && sizeof(TV) == 4 && sizeof(TA) == 4 && sizeof(TS) == 4) {
+      launch_stencil3f_any(op, mode, (const float*)x, (const float*)b, (float*)y, (float)omega, partials, grd, blk,
+                           st);
+      return launched();
+    }
     if (mode == SW_JACOBI0)
       launch_chain(stencil_sweep_kernel<D, TV, TA, TS, SW_JACOBI0>, grd, blk, 0, st, op, xv, bv, yv, (TA)omega, partials);
     else if (mode == SW_JACOBI)
