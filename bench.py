@@ -541,6 +541,28 @@ def run_probe(args, local_rank):
         print(json.dumps({"probe": "transfer", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
               flush=True)
         return
+    if args.probe == "precision":   # storage classes of the lossy surplus against the bound tau
+        # On piecewise-constant fields the FP64 outer residual applies the exact
+        # operator, so tau only sets how closely the FP32 V-cycle's operator
+        # follows it: larger bounds move cells to the FP8 / FP16 classes while
+        # the solution still meets 1e-8 under the exact operator.
+        w = inputs.workload(args.workload, args.n)
+        rows = []
+        for tau in (1e-6, 1e-4, 1e-3, 1e-2):
+            d = mg.problem_desc(w.dim, w.n_cells, w.eps, path=mg.PATH_MIXED_DELAYED, s_schedule=tuple(w.s_schedule),
+                                rtol=1e-8, max_cycles=3000, tau=tau)
+            ms, cyc = [], []
+            for _ in range(args.probe_reps):
+                with mg.Problem(d) as P:
+                    info = P.solve()
+                ms.append(info.time_ms)
+                cyc.append(info.cycles)
+            rows.append({"tau": tau, "ms": ms, "cycles": cyc, "rel_residual": info.rel_residual,
+                         "cells_by_class": [int(c) for c in info.cells_by_class],
+                         "payload_bytes": int(info.payload_bytes)})
+        print(json.dumps({"probe": "precision", "workload": args.workload, "n_cells": w.n_cells, "rows": rows}),
+              flush=True)
+        return
     if args.probe == "iteration":   # inner iteration with and without the host round trip
         w, d = workload_desc(mg, args.workload, mg.PATH_MIXED_PLAIN, n_cells=args.n)
         with mg.Problem(d) as P:
@@ -719,7 +741,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "transfer", "iteration", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
+    ap.add_argument("--probe", choices=["oracle", "peaks", "assembly", "transfer", "iteration", "precision", "sweep", "matvec", "residual", "galerkin", "solve", "serving",
                                         "adaptive", "starvation", "paths", "paper_format", "cycles", "coarse"],
                     help="profile one kernel on a small case instead of benchmarking")
     ap.add_argument("--probe-fp64", action="store_true", help="probe the FP64 plain path's kernel")
