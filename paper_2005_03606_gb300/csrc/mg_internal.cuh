@@ -420,12 +420,18 @@ cudaError_t launch_richardson_update(long long n, double* u, int z64, const void
 // correction step e += alpha p of the previous iteration (alpha in sc)
 cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float* p, float* e, const DevScalars* sc,
                                    cudaStream_t st);
-// r -= alpha q and partials of r.r (the matching e += alpha p is deferred)
+// r -= alpha q and partials of r.r (the matching e += alpha p is deferred);
+// with w = omega D^-1 of the finest level, also u1 = w r (the next V-cycle's
+// first smoothing step from the zero iterate)
 cudaError_t launch_fcg32_update(long long n, float* r, const float* q, const DevScalars* sc, double* partials,
-                                int* nblocks, cudaStream_t st);
+                                int* nblocks, cudaStream_t st, const float* w = nullptr, float* u1 = nullptr);
+// p[0 .. n) = v
+cudaError_t launch_fill(long long n, float v, float* p, cudaStream_t st);
 // e += alpha p: applies the last deferred correction step
 cudaError_t launch_fcg32_flush(long long n, float* e, const float* p, const DevScalars* sc, cudaStream_t st);
-cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st);
+// r_in = r / ||r|| in FP32 (||r||^2 from sc->rr); with w, also u1 = w r_in
+cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st,
+                                  const float* w = nullptr, float* u1 = nullptr);
 cudaError_t launch_apply_correction(long long n, double* u, const float* e, const DevScalars* sc, cudaStream_t st);
 cudaError_t launch_dot_f32f32(const float* a, const float* b, long long n, double* partials, int* nblocks,
                               cudaStream_t st);

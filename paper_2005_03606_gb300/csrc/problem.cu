@@ -172,6 +172,14 @@ struct mg_problem {
   float* zr = nullptr;
   // mixed paths: FP32 inner solve (iterative refinement)
   float *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+  // w32 = omega D^-1 of the finest level (rebuilt after every change of its
+  // operator, w_dirty): the restart's residual scaling and every flexible-CG
+  // update also write u1 = w32 r_in into lev[0].x1, the next V-cycle's first
+  // smoothing step from the zero iterate (u1_ready until a V-cycle uses it)
+  float* w32 = nullptr;
+  bool w_dirty = true;
+  bool w_ok = false;
+  bool u1_ready = false;
   // V-cycle enqueue: when set, the finest level's last post-smoothing sweep
   // also forms z . vdot_q (its partials, vdot_nb of them, left in partials)
   const float* vdot_q = nullptr;
@@ -592,6 +600,30 @@ mg_status upload_tables(mg_problem* P) {
     MG_CHECK(launch_build_touched(l0.op, P->tflags, P->tcounts, P->touched, P->ntouched, P->st));
   }
   if (l0.stencil) MG_CHECK(launch_build_stencil(l0.op, l0.stencil, P->st));
+  P->w_dirty = true;
+  return MG_OK;
+}
+
+// w32 = omega D^-1 of the finest level's FP32 operator: the zero-iterate
+// smoothing step applied to a vector of ones (the same kernels, so u1 = w32 b
+// is that step for any b up to one rounding)
+mg_status build_w(mg_problem* P) {
+  P->w_dirty = false;
+  P->w_ok = false;
+  if (!P->w32) return MG_OK;
+  Level& l0 = P->lev[0];
+  float* ones = nullptr;
+  cudaError_t e = mg_malloc_async(&ones, sizeof(float) * l0.nvert, P->st);
+  if (e != cudaSuccess) return oom_or_cuda(e, "scratch");
+  MG_CHECK(launch_fill(l0.nvert, 1.f, ones, P->st));
+  // boundary entries stay zero (some sweeps write interior vertices only), so
+  // u1 = w32 r is zero there
+  MG_CHECK(cudaMemsetAsync(P->w32, 0, sizeof(float) * l0.nvert, P->st));
+  e = launch_sweep(l0.op, SW_JACOBI0, 0, ones, ones, P->w32, P->desc.omega, nullptr, nullptr, P->st);
+  cudaFreeAsync(ones, P->st);
+  if (e == cudaErrorNotSupported) return MG_OK;   // no zero-iterate sweep on this level: no shortcut
+  MG_CHECK(e);
+  P->w_ok = true;
   return MG_OK;
 }
 
@@ -631,9 +663,16 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   void* cur = lv.x0;
   void* oth = lv.x1;
   // the V-cycle starts from a zero iterate: the first pre-smoothing step is
-  // omega D^-1 b where the sweep supports it (no zeroing, no read of x)
+  // omega D^-1 b where the sweep supports it (no zeroing, no read of x); on
+  // the finest level of the mixed flexible-CG iteration the kernel that wrote
+  // b also wrote that step into x1
   int k0 = 0;
-  if (P->desc.nu_pre > 0) {
+  const bool have_u1 = l == 0 && P->u1_ready && !vec64;
+  if (l == 0) P->u1_ready = false;
+  if (have_u1 && P->desc.nu_pre > 0) {
+    std::swap(cur, oth);
+    k0 = 1;
+  } else if (P->desc.nu_pre > 0) {
     e = launch_sweep(lv.op, SW_JACOBI0, vec64, cur, lv.b, oth, om, nullptr, nullptr, st);
     if (e == cudaSuccess) {
       std::swap(cur, oth);
@@ -764,7 +803,14 @@ mg_status outer_restart(mg_problem* P) {
     MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr, st));
   }
   if (P->mixed) {
-    MG_CHECK(launch_scale_residual(l0.nvert, P->r, (float*)l0.b, P->sc, st));
+    if (P->w_dirty) {
+      mg_status sw = build_w(P);
+      if (sw != MG_OK) return sw;
+    }
+    const bool u1 = P->w_ok && P->desc.cycle == MG_CYCLE_V;
+    MG_CHECK(launch_scale_residual(l0.nvert, P->r, (float*)l0.b, P->sc, st, u1 ? P->w32 : nullptr,
+                                   u1 ? (float*)l0.x1 : nullptr));
+    P->u1_ready = u1;
     MG_CHECK(cudaMemsetAsync(P->e32, 0, sizeof(float) * l0.nvert, st));
     if (P->e_pending) {   // a discarded correction: its deferred step goes with it
       MG_CHECK(cudaMemsetAsync(&P->sc->alpha, 0, sizeof(double), st));
@@ -837,7 +883,10 @@ mg_status outer_iteration_enqueue(mg_problem* P, int first) {
     MG_CHECK(launch_fcg32_direction(n, first, zf, P->p32, P->e32, P->sc, st));
     MG_CHECK(launch_sweep(l0.op, SW_MATVEC, 0, P->p32, rin, P->q32, 0.0, P->partials, &nb, st));
     MG_CHECK(launch_reduce_finish(P->partials, nb, 2, &P->sc->pq, st, P->sc, SC_SET_ALPHA));
-    MG_CHECK(launch_fcg32_update(n, rin, P->q32, P->sc, P->partials, &nb, st));
+    const bool u1 = P->w_ok && P->desc.cycle == MG_CYCLE_V;
+    MG_CHECK(launch_fcg32_update(n, rin, P->q32, P->sc, P->partials, &nb, st, u1 ? P->w32 : nullptr,
+                                 u1 ? (float*)l0.x1 : nullptr));
+    P->u1_ready = u1;
     MG_CHECK(launch_reduce_finish(P->partials, nb, 1, &P->sc->rr_in, st));
     return MG_OK;
   }
@@ -1322,6 +1371,8 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
     if ((e = dalloc(P, &P->p32, v4)) != cudaSuccess || (e = dalloc(P, &P->q32, v4)) != cudaSuccess ||
         (e = dalloc(P, &P->e32, v4)) != cudaSuccess)
       return fail(oom_or_cuda(e, "inner vectors"));
+    if (!getenv("MG_NO_U1") && (e = dalloc(P, &P->w32, v4)) != cudaSuccess)
+      return fail(oom_or_cuda(e, "inverse diagonal"));
     cudaMemsetAsync(P->p32, 0, v4, P->st);
     cudaMemsetAsync(P->q32, 0, v4, P->st);
     cudaMemsetAsync(P->e32, 0, v4, P->st);
@@ -2401,6 +2452,7 @@ mg_status mg_profile_kernel(mg_problem* P, int which, int reps, double* ms_per_l
       case 8:
       case 9: {   // one V-cycle from the finest level, or from the next coarser ones
         mg_status stt = MG_OK;
+        P->u1_ready = false;   // the whole cycle, its first smoothing step included
         vcycle_enqueue(P, which - 7, &stt);
         return stt == MG_OK ? cudaSuccess : cudaErrorUnknown;
       }
@@ -2467,6 +2519,7 @@ mg_status mg_vcycle_apply(mg_problem* P, const double* b, double* e_out) {
   cudaError_t e = mg_malloc_async(&tmp, 8 * n, P->st);
   if (e != cudaSuccess) return oom_or_cuda(e, "buffer");
   // the V-cycle reads lev[0].b (aliases r on FP64 paths): stage b there
+  P->u1_ready = false;
   if (P->mixed) {
     MG_CHECK(cudaMemcpyAsync(tmp, b, 8 * n, cudaMemcpyHostToDevice, P->st));
     MG_CHECK(launch_convert(n, 0, tmp, l0.b, P->st));

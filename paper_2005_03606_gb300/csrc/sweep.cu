@@ -2856,9 +2856,12 @@ __global__ void fcg32_direction_kernel(long long n, int first, const float* __re
 }
 
 // r -= alpha q and the partials of r.r (the correction e += alpha p is deferred
-// to the next direction update or fcg32_flush_kernel)
+// to the next direction update or fcg32_flush_kernel).  With w (= omega D^-1 of
+// the finest level), also u1 = w r: the next V-cycle's first smoothing step
+// from the zero iterate.
 __global__ void fcg32_update_kernel(long long n, float* __restrict__ r, const float* __restrict__ q,
-                                    const DevScalars* __restrict__ sc, double* partials) {
+                                    const DevScalars* __restrict__ sc, double* partials,
+                                    const float* __restrict__ w, float* __restrict__ u1) {
   pdl_begin();
   __shared__ double sh[8];
   const float alpha = (float)sc->alpha;
@@ -2866,7 +2869,8 @@ __global__ void fcg32_update_kernel(long long n, float* __restrict__ r, const fl
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n4 = 0;
-  if (aligned16(r) && aligned16(q)) {
+  const bool smooth = w != nullptr;
+  if (aligned16(r) && aligned16(q) && (!smooth || (aligned16(w) && aligned16(u1)))) {
     n4 = n / 4;
     float4* r4 = reinterpret_cast<float4*>(r);
     const float4* q4 = reinterpret_cast<const float4*>(q);
@@ -2878,12 +2882,17 @@ __global__ void fcg32_update_kernel(long long n, float* __restrict__ r, const fl
       rv.z = fmaf(-alpha, qv.z, rv.z);
       rv.w = fmaf(-alpha, qv.w, rv.w);
       r4[t] = rv;
+      if (smooth) {
+        const float4 wv = __ldg(reinterpret_cast<const float4*>(w) + t);
+        reinterpret_cast<float4*>(u1)[t] = make_float4(wv.x * rv.x, wv.y * rv.y, wv.z * rv.z, wv.w * rv.w);
+      }
       acc += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
     }
   }
   for (long long t = 4 * n4 + t0; t < n; t += stride) {
     const float rv = r[t] - alpha * q[t];
     r[t] = rv;
+    if (smooth) u1[t] = w[t] * rv;
     acc += rv * rv;
   }
   const double s = block_sum((double)acc, sh);
@@ -2900,14 +2909,20 @@ __global__ void fcg32_flush_kernel(long long n, float* __restrict__ e, const flo
 }
 
 // r_in = r / s with s = sqrt(rr) (the residual scaled to unit norm, FP32)
+// with w, also u1 = w r_in (as in fcg32_update_kernel)
 __global__ void scale_residual_kernel(long long n, const double* __restrict__ r, float* __restrict__ rin,
-                                      DevScalars* __restrict__ sc) {
+                                      DevScalars* __restrict__ sc, const float* __restrict__ w,
+                                      float* __restrict__ u1) {
   pdl_begin();
   const double s = sc->rr > 0.0 ? sqrt(sc->rr) : 1.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->s = s;
   const double inv = 1.0 / s;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    rin[t] = (float)(r[t] * inv);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float v = (float)(r[t] * inv);
+    rin[t] = v;
+    if (w) u1[t] = w[t] * v;
+  }
 }
 
 // u += s e (the scaled FP32 correction applied in FP64)
@@ -2926,9 +2941,19 @@ cudaError_t launch_fcg32_direction(long long n, int first, const float* z, float
 }
 
 cudaError_t launch_fcg32_update(long long n, float* r, const float* q, const DevScalars* sc, double* partials,
-                                int* nblocks, cudaStream_t st) {
+                                int* nblocks, cudaStream_t st, const float* w, float* u1) {
   *nblocks = kRedBlocks;
-  launch_chain(fcg32_update_kernel, kRedBlocks, 256, 0, st, n, r, q, sc, partials);
+  launch_chain(fcg32_update_kernel, kRedBlocks, 256, 0, st, n, r, q, sc, partials, w, u1);
+  return launched();
+}
+
+__global__ void fill_kernel(long long n, float v, float* __restrict__ p) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    p[t] = v;
+}
+
+cudaError_t launch_fill(long long n, float v, float* p, cudaStream_t st) {
+  fill_kernel<<<vgrid(n), 256, 0, st>>>(n, v, p);
   return launched();
 }
 
@@ -2937,8 +2962,9 @@ cudaError_t launch_fcg32_flush(long long n, float* e, const float* p, const DevS
   return launched();
 }
 
-cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st) {
-  launch_chain(scale_residual_kernel, vgrid(n), 256, 0, st, n, r, rin, sc);
+cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st,
+                                  const float* w, float* u1) {
+  launch_chain(scale_residual_kernel, vgrid(n), 256, 0, st, n, r, rin, sc, w, u1);
   return launched();
 }
 

@@ -672,13 +672,14 @@ def test_mixed_delayed_residual_under_the_fp64_operator(dim, n, fld, sched):
 
 
 @pytest.mark.parametrize("switch", ["MG_NO_VTAIL", "MG_NO_GRAPHS", "MG_NO_PDL", "MG_FUSED_RESTRICT",
-                                    "MG_NO_SPECULATE"])
+                                    "MG_NO_SPECULATE", "MG_NO_U1"])
 def test_alternative_cycle_implementations_agree(switch, monkeypatch):
     # the one-block tail of the V-cycle (levels 9 and 3), the CUDA-graph replay
     # of an iteration, the programmatic-dependent launches, the fused
-    # residual + restriction and the inner iterations enqueued ahead of the
-    # host's test are implementation choices: switching any of them must give
-    # the same solve (the last one may differ by the extra steps it takes)
+    # residual + restriction, the inner iterations enqueued ahead of the host's
+    # test and the first smoothing step formed by the kernel that writes the
+    # right-hand side are implementation choices: switching any of them must
+    # give the same solve (the speculation may differ by the extra steps it takes)
     w = inputs.workload("boxes3d", 27)
     d = mg.problem_desc(3, 27, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,), rtol=1e-8)
     with mg.Problem(d) as P:
