@@ -357,7 +357,10 @@ cudaError_t launch_pack_copy(int dim, int N, long long nrows, int nseg_x, const 
 enum SweepMode { SW_JACOBI = 0, SW_RESID = 1, SW_MATVEC = 2, SW_JACOBI0 = 3, SW_RESID_RZ = 4, SW_JACOBI_DOT = 5 };
 cudaError_t launch_sweep(const LevelOp& op, int mode, int vec64, const void* x, const void* b,
                          void* y, double omega, double* partials, int* nblocks, cudaStream_t st);
-cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st);
+// b_c = R r_f; with diag (the coarse level's stencil diagonals), also
+// u1 = omega b_c / diag, the coarse V-cycle's first smoothing step from zero
+cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st,
+                            const void* diag = nullptr, double omega = 0.0, void* u1 = nullptr);
 // Fused residual + restriction (Section "Stencil assembly variants": the
 // residual sweep and R = P^T in one pass) on a split compressed finest level
 // (3D, FP32): the bulk pass restricts its residuals along z into zr (the
@@ -367,7 +370,8 @@ cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc
 // pass forms bc.  cudaErrorNotSupported (nothing launched) on levels without
 // that split or without zr.
 cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, const void* b, void* rt, void* zr,
-                                  void* bc, cudaStream_t st);
+                                  void* bc, cudaStream_t st, const void* diag = nullptr, double omega = 0.0,
+                                  void* u1 = nullptr);
 // Damped Jacobi sweep y = x + omega D^-1 (b - A x) fused with the dot product
 // y . dq (the flexible-CG coefficient of the preconditioned residual y) on a
 // split compressed finest level (3D, FP32): partials receives one FP64 partial

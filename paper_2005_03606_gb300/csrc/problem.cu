@@ -94,6 +94,7 @@ struct Level {
   void* x1 = nullptr;
   float* eps_c = nullptr;         // coarse compression: eps at the cell centres (FP32)
   uint8_t* cls = nullptr;         // coarse compression: storage class per cell
+  bool u1_ready = false;          // x1 holds omega D^-1 b (written with b by the restriction)
 };
 
 struct Job {
@@ -653,7 +654,10 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   }
   const size_t vb = P->tv * lv.nvert;
   const double om = P->desc.omega;
-  if (l == P->L - 2 && !vec64 && vcycle_tail_supported(lv.op) && !getenv("MG_NO_VTAIL")) {
+  auto uses_tail = [&](int lev) {
+    return lev == P->L - 2 && !vec64 && vcycle_tail_supported(P->lev[lev].op) && !getenv("MG_NO_VTAIL");
+  };
+  if (uses_tail(l)) {
     // this level and the coarsest in one block
     e = launch_vcycle_tail(lv.op, P->Lc, (const float*)lv.b, (float*)lv.x0, (float)om, P->desc.nu_pre,
                            P->desc.nu_post, st);
@@ -667,8 +671,9 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   // the finest level of the mixed flexible-CG iteration the kernel that wrote
   // b also wrote that step into x1
   int k0 = 0;
-  const bool have_u1 = l == 0 && P->u1_ready && !vec64;
+  const bool have_u1 = l == 0 ? P->u1_ready && !vec64 : lv.u1_ready;
   if (l == 0) P->u1_ready = false;
+  lv.u1_ready = false;
   if (have_u1 && P->desc.nu_pre > 0) {
     std::swap(cur, oth);
     k0 = 1;
@@ -689,15 +694,24 @@ void* vcycle_enqueue(mg_problem* P, int l, mg_status* stt) {
   }
   Level& lc = P->lev[l + 1];
   // b_c = R (b - A u): fused where the level supports it (oth then holds the
-  // touched vertices' residuals only), else a residual sweep and a restriction
-  e = l == 0 ? launch_resid_restrict(lv.op, vec64, cur, lv.b, oth, P->zr, lc.b, st) : cudaErrorNotSupported;
+  // touched vertices' residuals only), else a residual sweep and a restriction.
+  // A coarse level that starts with the zero-iterate step of its stencil sweep
+  // receives that step, omega b_c / diag, from the restriction as well.
+  const bool pass_u1 = l + 1 < P->L - 1 && !uses_tail(l + 1) && lc.stencil && P->desc.nu_pre > 0 &&
+                       !getenv("MG_NO_U1");
+  const void* cdiag = pass_u1 ? lc.stencil : nullptr;
+  void* cu1 = pass_u1 ? lc.x1 : nullptr;
+  e = l == 0 ? launch_resid_restrict(lv.op, vec64, cur, lv.b, oth, P->zr, lc.b, st, cdiag, om, cu1)
+             : cudaErrorNotSupported;
   if (e == cudaErrorNotSupported) {
     if ((e = launch_sweep(lv.op, SW_RESID, vec64, cur, lv.b, oth, om, nullptr, nullptr, st)) != cudaSuccess)
       *stt = oom_or_cuda(e, "residual");
-    if ((e = launch_restrict(P->dim, lc.N, vec64, oth, lc.b, st)) != cudaSuccess) *stt = oom_or_cuda(e, "restrict");
+    if ((e = launch_restrict(P->dim, lc.N, vec64, oth, lc.b, st, cdiag, om, cu1)) != cudaSuccess)
+      *stt = oom_or_cuda(e, "restrict");
   } else if (e != cudaSuccess) {
     *stt = oom_or_cuda(e, "residual and restriction");
   }
+  lc.u1_ready = pass_u1 && e == cudaSuccess;
   void* ec = vcycle_enqueue(P, l + 1, stt);
   if ((e = launch_prolong_add(P->dim, lc.N, vec64, ec, cur, st)) != cudaSuccess) *stt = oom_or_cuda(e, "prolong");
   for (int k = 0; k < P->desc.nu_post; ++k) {

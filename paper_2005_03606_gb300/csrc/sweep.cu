@@ -1970,9 +1970,12 @@ __device__ __forceinline__ TV rtile_xy(const TV (&f)[kRFY][kRFP], TV (&rx)[kRFY]
 // 3 K1 + 2 are marched and weighted along z.  TIN = true: the input is the
 // z-restricted residual planes of the fused residual + restriction, input
 // plane K is coarse plane K.
+// With diag (the coarse level's stencil diagonals), also u1 = omega b_c / diag:
+// the coarse V-cycle's first smoothing step from the zero iterate.
 template <typename TV, bool TIN>
 __global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int kchunk, const TV* __restrict__ src,
-                                                                     TV* __restrict__ bc) {
+                                                                     TV* __restrict__ bc, const TV* __restrict__ diag,
+                                                                     TV omega, TV* __restrict__ u1) {
   pdl_begin();
   constexpr int S = sizeof(TV) == 4 ? 4 : 2;
   __shared__ RTile<TV, S> s;
@@ -2002,7 +2005,11 @@ __global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int
     __syncthreads();
     const TV v = rtile_xy(s.f[i % S], s.rx);
     if (TIN) {
-      if (valid) bc[((long long)p * nc1 + J) * nc1 + I] = v;
+      if (valid) {
+        const long long o = ((long long)p * nc1 + J) * nc1 + I;
+        bc[o] = v;
+        if (diag) u1[o] = omega * v / __ldg(diag + o);
+      }
       continue;
     }
     const int c = p / 3, m = p - 3 * c;
@@ -2014,7 +2021,11 @@ __global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int
     } else {
       acc0 += wa * v;
       acc1 += wb * v;
-      if (c >= K0 && valid) bc[((long long)c * nc1 + J) * nc1 + I] = acc0;
+      if (c >= K0 && valid) {
+        const long long o = ((long long)c * nc1 + J) * nc1 + I;
+        bc[o] = acc0;
+        if (diag) u1[o] = omega * acc0 / __ldg(diag + o);
+      }
       acc0 = acc1;
       acc1 = 0;
     }
@@ -2023,7 +2034,8 @@ __global__ void __launch_bounds__(kRTX * kRTY) restrict3_tile_kernel(int Nc, int
 
 template <typename TV>
 __global__ void __launch_bounds__(kRTX * kRTY) restrict2_tile_kernel(int Nc, const TV* __restrict__ rf,
-                                                                     TV* __restrict__ bc) {
+                                                                     TV* __restrict__ bc, const TV* __restrict__ diag,
+                                                                     TV omega, TV* __restrict__ u1) {
   pdl_begin();
   __shared__ RTile<TV, 1> s;
   const int N = 3 * Nc, nc1 = Nc + 1;
@@ -2033,7 +2045,11 @@ __global__ void __launch_bounds__(kRTX * kRTY) restrict2_tile_kernel(int Nc, con
   cp_async_wait<0>();
   __syncthreads();
   const TV v = rtile_xy(s.f[0], s.rx);
-  if (I <= Nc - 1 && J <= Nc - 1) bc[(long long)J * nc1 + I] = v;
+  if (I <= Nc - 1 && J <= Nc - 1) {
+    const long long o = (long long)J * nc1 + I;
+    bc[o] = v;
+    if (diag) u1[o] = omega * v / __ldg(diag + o);
+  }
 }
 
 // b_c = I r_f: interior coarse vertices take the fine value at the coinciding
@@ -2555,7 +2571,7 @@ __global__ void zr_fix_kernel(const LevelOp op, const float* __restrict__ rt, fl
 }
 
 cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, const void* b, void* rt, void* zr,
-                                  void* bc, cudaStream_t st) {
+                                  void* bc, cudaStream_t st, const void* diag, double omega, void* u1) {
   if (vec64 || op.dim != 3 || !op.compressed || op.stencil || !zr || !op.tmask || !op.touched || !op.eps_pad ||
       op.N < 27 || (op.N + 1) % 4 != 0)
     return cudaErrorNotSupported;
@@ -2590,26 +2606,34 @@ cudaError_t launch_resid_restrict(const LevelOp& op, int vec64, const void* x, c
   // 4. x-y restriction of the z-restricted planes
   const int kchunk = restrict_chunk(Nc);
   const dim3 g((Nc - 1 + kRTX - 1) / kRTX, (Nc - 1 + kRTY - 1) / kRTY, (Nc - 1 + kchunk - 1) / kchunk);
-  launch_chain(restrict3_tile_kernel<float, true>, g, dim3(kRTX, kRTY, 1), 0, st, Nc, kchunk, (const float*)zr, (float*)bc);
+  launch_chain(restrict3_tile_kernel<float, true>, g, dim3(kRTX, kRTY, 1), 0, st, Nc, kchunk, (const float*)zr,
+               (float*)bc, (const float*)diag, (float)omega, (float*)u1);
   return launched();
 }
 
-cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st) {
+cudaError_t launch_restrict(int dim, int Nc, int vec64, const void* rf, void* bc, cudaStream_t st, const void* diag,
+                            double omega, void* u1) {
   if (Nc < 2) return cudaSuccess;   // no interior coarse vertex
   const int ntx = (Nc - 1 + kRTX - 1) / kRTX, nty = (Nc - 1 + kRTY - 1) / kRTY;
   const dim3 blk(kRTX, kRTY, 1);
   if (dim == 2) {
     const dim3 g(ntx, nty, 1);
-    if (vec64) launch_chain(restrict2_tile_kernel<double>, g, blk, 0, st, Nc, (const double*)rf, (double*)bc);
-    else launch_chain(restrict2_tile_kernel<float>, g, blk, 0, st, Nc, (const float*)rf, (float*)bc);
+    if (vec64)
+      launch_chain(restrict2_tile_kernel<double>, g, blk, 0, st, Nc, (const double*)rf, (double*)bc,
+                   (const double*)diag, omega, (double*)u1);
+    else
+      launch_chain(restrict2_tile_kernel<float>, g, blk, 0, st, Nc, (const float*)rf, (float*)bc, (const float*)diag,
+                   (float)omega, (float*)u1);
     return launched();
   }
   const int kchunk = restrict_chunk(Nc);
   const dim3 g(ntx, nty, (Nc - 1 + kchunk - 1) / kchunk);
   if (vec64)
-    launch_chain(restrict3_tile_kernel<double, false>, g, blk, 0, st, Nc, kchunk, (const double*)rf, (double*)bc);
+    launch_chain(restrict3_tile_kernel<double, false>, g, blk, 0, st, Nc, kchunk, (const double*)rf, (double*)bc,
+                 (const double*)diag, omega, (double*)u1);
   else
-    launch_chain(restrict3_tile_kernel<float, false>, g, blk, 0, st, Nc, kchunk, (const float*)rf, (float*)bc);
+    launch_chain(restrict3_tile_kernel<float, false>, g, blk, 0, st, Nc, kchunk, (const float*)rf, (float*)bc,
+                 (const float*)diag, (float)omega, (float*)u1);
   return launched();
 }
 
