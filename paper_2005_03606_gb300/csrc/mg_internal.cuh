@@ -146,6 +146,14 @@ struct LevelOp {
   const int* xpos;
   const int* touched64;
   const int* ntouched64;
+  // FP64 bulk pass in vertex form (split finest level; nullptr: the cell
+  // form), built once from the cell-centre eps (eps64, else eps_c), h = 1/N:
+  // w64[0][v] = 5 h/12 G_v (G_v: eps summed over the 8 cells at v),
+  // w64[1..3][v] = h/12 W of the edges (v, v+x), (v, v+y), (v, v+z) (eps summed
+  // over the 4 cells at the edge), es64 = h/12 eps_c with rows padded to N+1
+  // cells (zero pad)
+  const double* w64[4];
+  const double* es64;
 };
 
 // ------------------------------------------------------------ programmatic dependent launch
@@ -394,6 +402,9 @@ cudaError_t launch_vcycle_tail(const LevelOp& op, const double* Lc, const float*
 cudaError_t launch_pad_eps(int N, const float* eps_c, float* eps_pad, cudaStream_t st);
 // from_xpos = 0: vertices next to a cell with a surplus record (and their
 // stencil table); 1: vertices next to an interface cell (op.xpos >= 0)
+// the vertex-form FP64 bulk weights of LevelOp::w64 / es64 (w: four arrays
+// of (N+1)^3, es: N * N * (N+1)) from eps64 if non-null, else from eps_c
+cudaError_t launch_geo_weights64(const LevelOp& op, double* const w[4], double* es, cudaStream_t st);
 cudaError_t launch_build_touched(const LevelOp& op, uint8_t* flags, uint32_t* counts, int* list, int* ntouched,
                                  cudaStream_t st, int from_xpos = 0);
 // xpos[chunk * chunk_cells + list[chunk][i]] = i for every interface cell, -1 elsewhere

@@ -1475,6 +1475,20 @@ mg_status mg_create_problem(const mg_problem_desc* desc, void* cuda_stream, mg_p
       l0.op.ntouched64 = P->ntouched64;
     }
   }
+  // FP64 bulk pass of the split finest level in vertex form (weights built
+  // once from the cell-centre eps; MG_CELL_FORM64=1 keeps the cell form)
+  if (P->touched && !getenv("MG_CELL_FORM64")) {
+    const size_t nv = (size_t)l0.nvert;
+    double* w[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* es = nullptr;
+    for (int m = 0; m < 4; ++m)
+      if ((e = dalloc(P, &w[m], sizeof(double) * nv)) != cudaSuccess) return fail(oom_or_cuda(e, "FP64 weights"));
+    if ((e = dalloc(P, &es, sizeof(double) * (size_t)P->N * P->N * (P->N + 1))) != cudaSuccess)
+      return fail(oom_or_cuda(e, "FP64 weights"));
+    if (!cuda_ok(launch_geo_weights64(l0.op, w, es, P->st), "FP64 weights")) return fail(MG_ERR_CUDA);
+    for (int m = 0; m < 4; ++m) l0.op.w64[m] = w[m];
+    l0.op.es64 = es;
+  }
   if (d.adapt_C > 0.0 && d.n_s >= 2) {
     P->adapt = true;
     P->wlast.resize(P->nchunk);

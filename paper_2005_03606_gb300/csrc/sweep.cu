@@ -1472,6 +1472,184 @@ __global__ void __launch_bounds__(256) sweep3_fixup64(const LevelOp op, const do
   }
 }
 
+// ---- FP64 bulk pass in vertex form.  With the weights built once per
+// problem, (A u)_v = gs_v u_v + sum over the 6 axis neighbours w of W_vw u_w
+// - sum over the 8 cells c at v of es_c T_c (gs = 5 h/12 G, W and es scaled by
+// h/12, T_c the sum of u over the vertices of c): the same terms as the cell
+// form above, but the eps sums per vertex and edge are loaded instead of
+// formed in every application, which cuts the FP64 operations per vertex
+// from about 38 to 25 (the pass is bound by the FP64 pipe).
+__global__ void geo_weights64_kernel(int N, const double* __restrict__ eps64, const float* __restrict__ eps32,
+                                     double h12, double* __restrict__ gs, double* __restrict__ wx,
+                                     double* __restrict__ wy, double* __restrict__ wz, double* __restrict__ es) {
+  const int n1 = N + 1;
+  const long long nv = (long long)n1 * n1 * n1;
+  auto E = [&](int cx, int cy, int cz) -> double {
+    if (cx < 0 || cx >= N || cy < 0 || cy >= N || cz < 0 || cz >= N) return 0.0;
+    const size_t c = ((size_t)cz * N + cy) * N + cx;
+    return eps64 ? eps64[c] : (double)eps32[c];
+  };
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(v % n1), j = (int)((v / n1) % n1), k = (int)(v / ((long long)n1 * n1));
+    double g = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+#pragma unroll
+    for (int a = -1; a <= 0; ++a)
+#pragma unroll
+      for (int b = -1; b <= 0; ++b) {
+        ex += E(i, j + a, k + b);   // cells at the edge (v, v+x): x index i
+        ey += E(i + a, j, k + b);
+        ez += E(i + a, j + b, k);
+#pragma unroll
+        for (int c = -1; c <= 0; ++c) g += E(i + a, j + b, k + c);
+      }
+    gs[v] = 5.0 * h12 * g;
+    wx[v] = h12 * ex;
+    wy[v] = h12 * ey;
+    wz[v] = h12 * ez;
+    // padded cell row: cell (i, j, k) for i < N, zero at i = N
+    if (j < N && k < N) es[((size_t)k * N + j) * n1 + i] = i < N ? h12 * E(i, j, k) : 0.0;
+  }
+}
+
+// three consecutive doubles e[-1], e[0], e[1] of a padded row (e[-1] = 0 when !has_left)
+__device__ __forceinline__ void load_es3(const double* __restrict__ e, bool has_left, double (&g)[3]) {
+  const double2 c = __ldg(reinterpret_cast<const double2*>(e));
+  g[0] = has_left ? __ldg(e - 1) : 0.0;
+  g[1] = c.x;
+  g[2] = c.y;
+}
+
+struct GeoW64Ctx {
+  const double* x;
+  const double* b;
+  double* y;
+  const double* w[4];
+  const double* es;
+  int N, n1, q, j;
+  size_t plane, row0;
+  bool hl, hr;
+};
+
+// one plane k of the vertex-form FP64 pass: 2 vertices (q, q+1) of row j
+template <int MODE>
+__device__ __forceinline__ void geow64_step(const GeoW64Ctx& c, int k, const Rows4<double>& uc, Rows4<double>& un,
+                                            const double (&pyc)[2][3], double (&pyn)[2][3],
+                                            const double (&yTm)[3], double (&yTc)[3], double (&wzm)[2],
+                                            double& d1, double& d2) {
+  const size_t v0 = (size_t)k * c.plane + c.row0 + c.q;
+  // row j of plane k-1: the centre row of the buffer refilled below
+  const double um1[2] = {un.v[1][1], un.v[1][2]};
+  load_rows4<double>(c.x + v0 + c.plane, c.n1, c.hl, c.hr, un);
+  double gc[2][3];
+  const size_t erow = ((size_t)k * c.N + (c.j - 1)) * c.n1 + c.q;   // cell row j-1 of layer k, cell q
+  load_es3(c.es + erow, c.hl, gc[0]);
+  load_es3(c.es + erow + c.n1, c.hl, gc[1]);
+  const double2 b2 = __ldg(reinterpret_cast<const double2*>(c.b + v0));
+  const double2 gs = __ldg(reinterpret_cast<const double2*>(c.w[0] + v0));
+  const double2 wx = __ldg(reinterpret_cast<const double2*>(c.w[1] + v0));
+  const double wxl = c.hl ? __ldg(c.w[1] + v0 - 1) : 0.0;
+  const double2 wy = __ldg(reinterpret_cast<const double2*>(c.w[2] + v0));
+  const double2 wym = __ldg(reinterpret_cast<const double2*>(c.w[2] + v0 - c.n1));
+  const double2 wz = __ldg(reinterpret_cast<const double2*>(c.w[3] + v0));
+  pair_sums4<double>(un, pyn);
+  double yZ[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    yTc[i] = gc[0][i] * (pyc[0][i] + pyn[0][i]) + gc[1][i] * (pyc[1][i] + pyn[1][i]);
+    yZ[i] = yTm[i] + yTc[i];
+  }
+  const double bb[2] = {b2.x, b2.y}, g5[2] = {gs.x, gs.y}, wxr[2] = {wx.x, wx.y}, wxm[2] = {wxl, wx.x};
+  const double wyp[2] = {wy.x, wy.y}, wyn[2] = {wym.x, wym.y}, wzp[2] = {wz.x, wz.y};
+  double out[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const double uv = uc.v[1][e + 1];
+    double w = fma(g5[e], uv, -(yZ[e] + yZ[e + 1]));
+    w = fma(wxr[e], uc.v[1][e + 2], w);   // x + 1
+    w = fma(wxm[e], uc.v[1][e], w);       // x - 1
+    w = fma(wyp[e], uc.v[2][e + 1], w);   // y + 1
+    w = fma(wyn[e], uc.v[0][e + 1], w);   // y - 1
+    w = fma(wzp[e], un.v[1][e + 1], w);   // z + 1
+    w = fma(wzm[e], um1[e], w);           // z - 1
+    const int i = c.q + e;
+    const bool valid = i >= 1 && i <= c.N - 1;
+    double r;
+    if (MODE == SW_RESID) {
+      r = bb[e] - w;
+    } else {
+      r = w;
+      if (valid) {
+        d1 += uv * w;
+        d2 += uv * bb[e];
+      }
+    }
+    out[e] = valid ? r : 0.0;
+  }
+  wzm[0] = wz.x;
+  wzm[1] = wz.y;
+  *reinterpret_cast<double2*>(c.y + v0) = make_double2(out[0], out[1]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kGeoBX * kGeoBY, 2) sweep3_geow64(const LevelOp op, const double* __restrict__ x,
+                                                                    const double* __restrict__ b,
+                                                                    double* __restrict__ y,
+                                                                    double* __restrict__ partials, int ntx, int nty) {
+  __shared__ double sh[2][8];
+  GeoW64Ctx c;
+  c.x = x;
+  c.b = b;
+  c.y = y;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) c.w[m] = op.w64[m];
+  c.es = op.es64;
+  c.N = op.N;
+  c.n1 = op.N + 1;
+  c.plane = (size_t)c.n1 * c.n1;
+  double d1 = 0.0, d2 = 0.0;
+  long long w, w1;
+  geo_share(ntx, nty, c.N - 1, w, w1);
+  GeoRun run;
+  while (next_geo_run(w, w1, c.N - 1, ntx, run)) {
+    c.q = 2 * (run.tx * kGeoBX + threadIdx.x);   // vertices q, q+1
+    c.j = 1 + run.ty * kGeoBY + threadIdx.y;
+    const int k0 = run.k0, k1 = run.k1;
+    if (c.q >= c.n1 || c.j >= c.N) continue;
+    c.hl = c.q > 0;
+    c.hr = c.q + 2 <= c.N;
+    c.row0 = (size_t)c.j * c.n1;
+    Rows4<double> ua, ub;
+    double pa[2][3], pb[2][3], ta[3], tb[3], ga[2][3], wzm[2];
+    const size_t v0 = (size_t)k0 * c.plane + c.row0 + c.q;
+    load_rows4<double>(x + v0 - c.plane, c.n1, c.hl, c.hr, ub);
+    load_rows4<double>(x + v0, c.n1, c.hl, c.hr, ua);
+    const size_t erow = ((size_t)(k0 - 1) * c.N + (c.j - 1)) * c.n1 + c.q;   // layer k0-1
+    load_es3(c.es + erow, c.hl, ga[0]);
+    load_es3(c.es + erow + c.n1, c.hl, ga[1]);
+    const double2 wz0 = __ldg(reinterpret_cast<const double2*>(c.w[3] + v0 - c.plane));
+    wzm[0] = wz0.x;
+    wzm[1] = wz0.y;
+    pair_sums4<double>(ub, pb);
+    pair_sums4<double>(ua, pa);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ta[i] = ga[0][i] * (pb[0][i] + pa[0][i]) + ga[1][i] * (pb[1][i] + pa[1][i]);
+    for (int k = k0; k <= k1; k += 2) {
+      geow64_step<MODE>(c, k, ua, ub, pa, pb, ta, tb, wzm, d1, d2);
+      if (k + 1 > k1) break;
+      geow64_step<MODE>(c, k + 1, ub, ua, pb, pa, tb, ta, wzm, d1, d2);
+    }
+  }
+  if (MODE == SW_MATVEC) {
+    const double s1 = block_sum(d1, sh[0]);
+    const double s2 = block_sum(d2, sh[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      partials[2 * blockIdx.x] = s1;
+      partials[2 * blockIdx.x + 1] = s2;
+    }
+  }
+}
+
 cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const double* b, double* y,
                          double* partials, int* nblocks, cudaStream_t st) {
   const int np = (op.N + 1) / 2;
@@ -1487,12 +1665,15 @@ cudaError_t launch_geo64(const LevelOp& op, int mode, const double* x, const dou
   const int nb = ntiles < 2 * nsm ? (int)ntiles : 2 * nsm;
   const dim3 blk(kGeoBX, kGeoBY, 1);
   double* pfix = partials ? partials + 2 * (size_t)nb : nullptr;
+  const bool vform = op.w64[0] != nullptr;
   if (mode == SW_RESID) {
-    sweep3_geo2<double, SW_RESID, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty);
+    if (vform) sweep3_geow64<SW_RESID><<<nb, blk, 0, st>>>(op, x, b, y, partials, ntx, nty);
+    else sweep3_geo2<double, SW_RESID, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup64<SW_RESID><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
   } else {
-    sweep3_geo2<double, SW_MATVEC, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty);
+    if (vform) sweep3_geow64<SW_MATVEC><<<nb, blk, 0, st>>>(op, x, b, y, partials, ntx, nty);
+    else sweep3_geo2<double, SW_MATVEC, 2><<<nb, blk, 0, st>>>(op, x, b, y, 0.0, partials, ntx, nty);
     count_launches(1);
     sweep3_fixup64<SW_MATVEC><<<kFixBlocks, 256, 0, st>>>(op, x, y, pfix);
   }
@@ -2429,6 +2610,12 @@ __global__ void load_vector_kernel(int N, double val, double* f) {
 }  // namespace
 
 bool pdl_enabled() { return getenv("MG_NO_PDL") == nullptr; }
+
+cudaError_t launch_geo_weights64(const LevelOp& op, double* const w[4], double* es, cudaStream_t st) {
+  geo_weights64_kernel<<<152 * 8, 256, 0, st>>>(op.N, op.eps64, op.eps_c, -op.gk64, w[0], w[1], w[2], w[3], es);
+  count_launches(1);
+  return launched();
+}
 
 // y = x + omega D^-1 (b - A x) and partials[...] of y . dq on a split finest
 // level (bulk pass: one partial per block, then one per fix-up block);

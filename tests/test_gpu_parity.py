@@ -672,13 +672,14 @@ def test_mixed_delayed_residual_under_the_fp64_operator(dim, n, fld, sched):
 
 
 @pytest.mark.parametrize("switch", ["MG_NO_VTAIL", "MG_NO_GRAPHS", "MG_NO_PDL", "MG_FUSED_RESTRICT",
-                                    "MG_NO_SPECULATE", "MG_NO_U1"])
+                                    "MG_NO_SPECULATE", "MG_NO_U1", "MG_CELL_FORM64"])
 def test_alternative_cycle_implementations_agree(switch, monkeypatch):
     # the one-block tail of the V-cycle (levels 9 and 3), the CUDA-graph replay
     # of an iteration, the programmatic-dependent launches, the fused
     # residual + restriction, the inner iterations enqueued ahead of the host's
     # test and the first smoothing step formed by the kernel that writes the
-    # right-hand side are implementation choices: switching any of them must
+    # right-hand side and the cell form of the FP64 bulk pass (instead of its
+    # vertex form) are implementation choices: switching any of them must
     # give the same solve (the speculation may differ by the extra steps it takes)
     w = inputs.workload("boxes3d", 27)
     d = mg.problem_desc(3, 27, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,), rtol=1e-8)
@@ -759,6 +760,42 @@ def test_prolonged_smoothing_matches_oracle(dim, n, fld, path, env):
     tol = (1e-11 if not inner else 2e-5) * (scale / dmin + np.abs(xp).max())
     assert np.all(out[~m] == 0.0)
     assert np.abs(out - ref).max() <= tol
+
+
+@pytest.mark.parametrize("cell_form", [False, True])
+def test_full_size_fp64_residual_sampled(monkeypatch, cell_form):
+    # 243^3 boxes at s = 8: the outer FP64 residual b - A x of the mixed path
+    # (the exact FP64 operator) in the launch configuration of the benchmark,
+    # at sampled vertices (random ones and ones next to a cell with a surplus
+    # record) against the oracle's FP64 A(8) rows.  The vertex form (eps sums
+    # per vertex and per edge built once) is the default; MG_CELL_FORM64=1
+    # forms them in every application.
+    if cell_form:
+        monkeypatch.setenv("MG_CELL_FORM64", "1")
+    else:
+        monkeypatch.delenv("MG_CELL_FORM64", raising=False)
+    w = inputs.workload("boxes3d")
+    n = w.n_cells
+    n1 = n + 1
+    line = np.zeros(n1, bool)
+    line[1:n] = True
+    mask = (line[:, None, None] & line[None, :, None] & line[None, None, :]).reshape(-1)
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(n1 ** 3) * mask
+    b = rng.standard_normal(n1 ** 3) * mask
+    with mg.Problem(mg.problem_desc(3, n, w.eps, path=mg.PATH_MIXED_PLAIN, s_schedule=(8,))) as P:
+        P.assemble(8)
+        r = P.apply(0, 2, x, b)
+        cls_all, _ = P.cell_data()
+    nz = rng.choice(np.flatnonzero(cls_all), 32, replace=False)
+    # the upper corner vertex of each cell (interior, so that the row is a full one)
+    near = [(min(n - 1, c % n + 1), min(n - 1, (c // n) % n + 1), min(n - 1, c // (n * n) + 1)) for c in nz]
+    rand = [tuple(int(t) for t in rng.integers(1, n, 3)) for _ in range(32)]
+    verts = np.array([(k * n1 + j) * n1 + i for (i, j, k) in near + rand])
+    Ax, _, scale = _oracle_vertex_rows(w.eps, n, 8, verts, x, lossy=False)
+    ref = b[verts] - Ax
+    assert np.all(np.abs(r[verts] - ref) <= 1e-12 * (scale + np.abs(b[verts])))
+    assert np.all(r.reshape(n1, n1, n1)[0] == 0) and np.all(r.reshape(n1, n1, n1)[:, :, n] == 0)
 
 
 @pytest.mark.parametrize("fused", [False, True])
