@@ -16,6 +16,7 @@
 #include "mg_internal.cuh"
 
 #include <mutex>
+#include <type_traits>
 
 namespace mg {
 
@@ -23,6 +24,10 @@ namespace {
 
 __constant__ double c_G2[9][6];
 __constant__ double c_G3[27][28];
+// the same tables rounded to FP32, for the FP32 products (no FP64 -> FP32
+// conversion per coarse entry in the kernel)
+__constant__ float c_G2f[9][6];
+__constant__ float c_G3f[27][28];
 bool g_tables_ready = false;
 
 template <int D>
@@ -71,11 +76,23 @@ cudaError_t ensure_tables() {
   double g2[9 * 6], g3[27 * 28];
   host_G<2>(g2);
   host_G<3>(g3);
+  float g2f[9 * 6], g3f[27 * 28];
+  for (int i = 0; i < 9 * 6; ++i) g2f[i] = (float)g2[i];
+  for (int i = 0; i < 27 * 28; ++i) g3f[i] = (float)g3[i];
   cudaError_t e = cudaMemcpyToSymbol(c_G2, g2, sizeof(g2));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_G2f, g2f, sizeof(g2f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_G3f, g3f, sizeof(g3f));
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_G3, g3, sizeof(g3));
   if (e == cudaSuccess) g_tables_ready = true;
   return e;
+}
+
+// entry p of the table G of child ch in the arithmetic type
+template <int D, typename TA>
+__device__ __forceinline__ TA gtab(int ch, int p) {
+  if constexpr (std::is_same<TA, float>::value) return D == 3 ? c_G3f[ch][p] : c_G2f[ch][p];
+  else return D == 3 ? c_G3[ch][p] : c_G2[ch][p];
 }
 
 // off-diagonals of the fine cell (i,j,k) (full storage) into A[NP]
@@ -117,7 +134,7 @@ __global__ void galerkin_kernel(const LevelOp fine, int last0, int last1, TC* __
         const long long c = D == 2 ? (long long)fj * fine.N + fi : ((long long)fk * fine.N + fj) * fine.N + fi;
         const TA ge = (TA)fine.eps_c[c] * (TA)fine.hfac;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) acc[p] += ge * (TA)(D == 3 ? c_G3[ch][p] : c_G2[ch][p]);
+        for (int p = 0; p < NP; ++p) acc[p] += ge * gtab<D, TA>(ch, p);
         int chn = (D == 2 ? fj : fk) / fine.layers;
         if (chn >= fine.nchunk) chn = fine.nchunk - 1;
         const long long lc = c - (long long)chn * fine.chunk_cells;
