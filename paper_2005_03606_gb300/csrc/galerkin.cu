@@ -189,25 +189,30 @@ __global__ void galerkin_kernel(const LevelOp fine, int last0, int last1, TC* __
 template <int D, typename TS>
 __global__ void coarse_factor_kernel(const LevelOp op, double* L) {
   constexpr int NV = Dim<D>::NV, NP = Dim<D>::NP;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  constexpr int NC = D == 3 ? 27 : 9;   // cells of the coarsest level (3 per axis)
+  // thread c < NC writes cell c's contribution to the dense interior system;
+  // the contributions are then summed in cell order (as one thread would)
+  __shared__ double S[NC][NV * NV];
+  __shared__ double Ms[NV * NV];
   const int n = NV;  // 2^d interior vertices (1..2 per axis)
-  double M[NV][NV];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) M[i][j] = 0.0;
   const TS* a = reinterpret_cast<const TS*>(op.full[0].a);
   const long long ncell = op.chunk_cells;
-  const int ncell_i = D == 3 ? 27 : 9;
-  for (int c = 0; c < ncell_i; ++c) {
+  const int c = threadIdx.x;
+  if (c < NC) {
     const int ci = c % 3, cj = (c / 3) % 3, ck = c / 9;
     int gidx[NV];
+#pragma unroll
     for (int b = 0; b < NV; ++b) {
       const int vx = ci + (b & 1), vy = cj + ((b >> 1) & 1), vz = D == 3 ? ck + ((b >> 2) & 1) : 1;
       const bool in = vx >= 1 && vx <= 2 && vy >= 1 && vy <= 2 && vz >= 1 && vz <= 2;
       gidx[b] = in ? (vx - 1) + 2 * (vy - 1) + (D == 3 ? 4 * (vz - 1) : 0) : -1;
     }
     double A[NV][NV];
+#pragma unroll
     for (int x = 0; x < NV; ++x) A[x][x] = 0.0;
+#pragma unroll
     for (int x = 0; x < NV; ++x)
+#pragma unroll
       for (int y = x + 1; y < NV; ++y) {
         const double v = (double)a[(long long)pair_index(NV, x, y) * ncell + c];
         A[x][y] = v;
@@ -215,10 +220,24 @@ __global__ void coarse_factor_kernel(const LevelOp op, double* L) {
         A[x][x] -= v;
         A[y][y] -= v;
       }
+    for (int e = 0; e < NV * NV; ++e) S[c][e] = 0.0;
+#pragma unroll
     for (int x = 0; x < NV; ++x)
+#pragma unroll
       for (int y = 0; y < NV; ++y)
-        if (gidx[x] >= 0 && gidx[y] >= 0) M[gidx[x]][gidx[y]] += A[x][y];
+        if (gidx[x] >= 0 && gidx[y] >= 0) S[c][gidx[x] * NV + gidx[y]] = A[x][y];
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV * NV; e += blockDim.x) {
+    double sum = 0.0;
+    for (int k = 0; k < NC; ++k) sum += S[k][e];
+    Ms[e] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double M[NV][NV];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) M[i][j] = Ms[i * NV + j];
   (void)NP;
   for (int j = 0; j < n; ++j) {
     double s = M[j][j];

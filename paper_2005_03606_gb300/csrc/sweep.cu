@@ -3127,12 +3127,25 @@ __global__ void scale_residual_kernel(long long n, const double* __restrict__ r,
   pdl_begin();
   const double s = sc->rr > 0.0 ? sqrt(sc->rr) : 1.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->s = s;
-  const double inv = 1.0 / s;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+  // the scaling in FP32 after the conversion (one FP64-pipe operation per
+  // entry instead of two; the entry is rounded to FP32 either way)
+  const float inv = (float)(1.0 / s);
+  const long long n2 = n / 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t <= n2;
        t += (long long)gridDim.x * blockDim.x) {
-    const float v = (float)(r[t] * inv);
-    rin[t] = v;
-    if (w) u1[t] = w[t] * v;
+    if (t < n2) {
+      const double2 r2 = reinterpret_cast<const double2*>(r)[t];
+      const float2 v = make_float2((float)r2.x * inv, (float)r2.y * inv);
+      reinterpret_cast<float2*>(rin)[t] = v;
+      if (w) {
+        const float2 w2 = reinterpret_cast<const float2*>(w)[t];
+        reinterpret_cast<float2*>(u1)[t] = make_float2(w2.x * v.x, w2.y * v.y);
+      }
+    } else if (2 * t < n) {   // odd n: the last entry
+      const float v = (float)r[2 * t] * inv;
+      rin[2 * t] = v;
+      if (w) u1[2 * t] = w[2 * t] * v;
+    }
   }
 }
 
@@ -3175,7 +3188,7 @@ cudaError_t launch_fcg32_flush(long long n, float* e, const float* p, const DevS
 
 cudaError_t launch_scale_residual(long long n, const double* r, float* rin, DevScalars* sc, cudaStream_t st,
                                   const float* w, float* u1) {
-  launch_chain(scale_residual_kernel, vgrid(n), 256, 0, st, n, r, rin, sc, w, u1);
+  launch_chain(scale_residual_kernel, vgrid(n / 2 + 1), 256, 0, st, n, r, rin, sc, w, u1);
   return launched();
 }
 
