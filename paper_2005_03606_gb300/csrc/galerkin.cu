@@ -185,6 +185,156 @@ __global__ void galerkin_kernel(const LevelOp fine, int last0, int last1, TC* __
   }
 }
 
+// 3D FP32 Galerkin product of a compressed fine level, one thread per coarse
+// cell, in two phases.  (1) The 27 children's eps and classes are loaded
+// together (one memory latency instead of 27 dependent ones), their
+// geometric part eps_c G_ch is summed, and the children with a surplus are
+// marked.  (2) The marked (cell, child) pairs of a warp go through a queue in
+// shared memory and their pair products run 32 at a time, one per lane
+// (one thread per coarse cell would run them child position by child
+// position, mostly with one or two lanes active); each coarse cell then adds
+// the contributions of its own children in child order.
+constexpr int kGalWarps = 4;
+
+// P[a][I] = wx[a0][I0] wy[a1][I1] wz[a2][I2]: the d-linear interpolation
+// weight of coarse vertex I at vertex a of child (ox, oy, oz)
+__device__ __forceinline__ void child_weights1d(int o, float (&w)[2][2]) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const float t = (float)(o + a) / 3.f;
+    w[a][0] = 1.f - t;
+    w[a][1] = t;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kGalWarps) galerkin3q_kernel(const LevelOp fine, int last0, int last1,
+                                                                     float* __restrict__ out) {
+  constexpr int NV = 8, NP = 28;
+  __shared__ unsigned short q_s[kGalWarps][64];
+  __shared__ float c_s[kGalWarps][32][NP + 1];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned short* q = q_s[wid];
+  float(*cs)[NP + 1] = c_s[wid];
+  const int N = fine.N, Nc = N / 3;
+  const long long per_layer = (long long)Nc * Nc;
+  const long long ncc_total = per_layer * Nc;
+  const long long c_begin = (long long)last0 * per_layer, c_end = (long long)last1 * per_layer;
+  const long long wstride = (long long)gridDim.x * kGalWarps * 32;
+  const float hfac = (float)fine.hfac;
+  for (long long base = c_begin + ((long long)blockIdx.x * kGalWarps + wid) * 32; base < c_end; base += wstride) {
+    const long long C = base + lane;
+    const bool valid = C < c_end;
+    const long long Cv = valid ? C : c_end - 1;
+    const int I0 = (int)(Cv % Nc), J0 = (int)((Cv / Nc) % Nc), K0 = (int)(Cv / per_layer);
+    float acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = 0.f;
+    // (1) geometric part and the surplus children
+    float ge[27];
+    uint8_t cls[27];
+#pragma unroll
+    for (int ch = 0; ch < 27; ++ch) {
+      const int fi = 3 * I0 + ch % 3, fj = 3 * J0 + (ch / 3) % 3, fk = 3 * K0 + ch / 9;
+      const long long c = ((long long)fk * N + fj) * N + fi;
+      int chn = fk / fine.layers;
+      if (chn >= fine.nchunk) chn = fine.nchunk - 1;
+      ge[ch] = __ldg(fine.eps_c + c);
+      // the cell's row within its chunk, without dividing the cell index
+      const long long row = (long long)(fk - chn * fine.layers) * N + fj;
+      cls[ch] = fine.cmp[chn].cls[(row * fine.nseg_x + (fi >> 5)) * kSegCells + (fi & 31)];
+    }
+    unsigned mine = 0;
+#pragma unroll
+    for (int ch = 0; ch < 27; ++ch) {
+      const float g = ge[ch] * hfac;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) acc[p] = fmaf(g, c_G3f[ch][p], acc[p]);
+      if (cls[ch] && valid) mine |= 1u << ch;
+    }
+    // (2) the surplus children, in rounds (each lane's next child) through the queue
+    int qn = 0;
+    bool more = __any_sync(0xffffffffu, mine != 0u);
+    while (more || qn > 0) {
+      if (more) {
+        const unsigned m = __ballot_sync(0xffffffffu, mine != 0u);
+        if (mine) {
+          const int ch = __ffs(mine) - 1;
+          mine &= mine - 1;
+          q[qn + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(lane | (ch << 5));
+        }
+        qn += __popc(m);
+        more = __any_sync(0xffffffffu, mine != 0u);
+      }
+      if (qn < 32 && more) continue;
+      // one batch: the first min(qn, 32) queued pairs, one per lane
+      __syncwarp();
+      const int nb = qn < 32 ? qn : 32;
+      if (lane < nb) {
+        const int e = q[lane], o = e & 31, ch = e >> 5;
+        const long long Co = base + o;
+        const int oI = (int)(Co % Nc), oJ = (int)((Co / Nc) % Nc), oK = (int)(Co / per_layer);
+        const int ox = ch % 3, oy = (ch / 3) % 3, oz = ch / 9;
+        const int fi = 3 * oI + ox, fj = 3 * oJ + oy, fk = 3 * oK + oz;
+        const long long c = ((long long)fk * N + fj) * N + fi;
+        int chn = fk / fine.layers;
+        if (chn >= fine.nchunk) chn = fine.nchunk - 1;
+        const CmpChunk& ck = fine.cmp[chn];
+        const long long lc = c - (long long)chn * fine.chunk_cells;
+        const int cl = cell_class(ck, N, fine.nseg_x, lc);
+        const uint8_t* rec = cell_record<3>(ck, N, fine.nseg_x, lc, cl);
+        float A[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) A[p] = decode_entry<3>(rec, cl, p);
+        float wx[2][2], wy[2][2], wz[2][2];
+        child_weights1d(ox, wx);
+        child_weights1d(oy, wy);
+        child_weights1d(oz, wz);
+        float con[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) con[p] = 0.f;
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+          for (int b = a + 1; b < NV; ++b) {
+            const float v = A[pair_index(NV, a, b)];
+            float d[NV], vd[NV];
+#pragma unroll
+            for (int I = 0; I < NV; ++I) {
+              const float pa = wx[a & 1][I & 1] * wy[(a >> 1) & 1][(I >> 1) & 1] * wz[a >> 2][I >> 2];
+              const float pb = wx[b & 1][I & 1] * wy[(b >> 1) & 1][(I >> 1) & 1] * wz[b >> 2][I >> 2];
+              d[I] = pa - pb;
+              vd[I] = -v * d[I];
+            }
+#pragma unroll
+            for (int I = 0; I < NV; ++I)
+#pragma unroll
+              for (int J = I + 1; J < NV; ++J) con[pair_index(NV, I, J)] = fmaf(vd[I], d[J], con[pair_index(NV, I, J)]);
+          }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) cs[lane][p] = con[p];
+      }
+      __syncwarp();
+      for (int t = 0; t < nb; ++t)
+        if ((q[t] & 31) == lane) {
+#pragma unroll
+          for (int p = 0; p < NP; ++p) acc[p] += cs[t][p];
+        }
+      __syncwarp();
+      // keep the pairs beyond the batch
+      const int rest = qn - nb;
+      const unsigned short keep = lane < rest ? q[nb + lane] : 0;
+      __syncwarp();
+      if (lane < rest) q[lane] = keep;
+      __syncwarp();
+      qn = rest;
+    }
+    if (valid) {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) out[(long long)p * ncc_total + C] = acc[p];
+    }
+  }
+}
+
 // dense interior system of the coarsest level (N = 3) and its Cholesky factor
 template <int D, typename TS>
 __global__ void coarse_factor_kernel(const LevelOp op, double* L) {
@@ -437,8 +587,16 @@ cudaError_t launch_galerkin_range(const LevelOp& fine, int out64, void* coarse_f
     }
   } else {
     if (fine.compressed) {
-      if (out64) MG_GAL(3, double, float, double, true);
-      else MG_GAL(3, float, float, float, true);
+      if (out64) {
+        MG_GAL(3, double, float, double, true);
+      } else if (!getenv("MG_GALERKIN_THREAD")) {   // queued surplus products (see galerkin3q_kernel)
+        const long long nwarps = (n + 31) / 32;
+        long long nblk = (nwarps + kGalWarps - 1) / kGalWarps;
+        nblk = nblk < 152LL * 16 ? nblk : 152LL * 16;
+        galerkin3q_kernel<<<(int)nblk, 32 * kGalWarps, 0, st>>>(fine, last0, last1, (float*)coarse_full);
+      } else {
+        MG_GAL(3, float, float, float, true);
+      }
     } else if (fine.elem64) {
       if (out64) MG_GAL(3, double, double, double, false);
       else MG_GAL(3, double, double, float, false);
