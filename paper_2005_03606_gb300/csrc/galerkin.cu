@@ -385,37 +385,53 @@ __global__ void coarse_factor_kernel(const LevelOp op, double* L) {
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  // factor and inverse of the 2^d x 2^d system, loops unrolled so that the
+  // matrix stays in registers
   double M[NV][NV];
+#pragma unroll
   for (int i = 0; i < n; ++i)
+#pragma unroll
     for (int j = 0; j < n; ++j) M[i][j] = Ms[i * NV + j];
   (void)NP;
+#pragma unroll
   for (int j = 0; j < n; ++j) {
     double s = M[j][j];
+#pragma unroll
     for (int k = 0; k < j; ++k) s -= M[j][k] * M[j][k];
     M[j][j] = sqrt(s);
+#pragma unroll
     for (int i = j + 1; i < n; ++i) {
       double t = M[i][j];
+#pragma unroll
       for (int k = 0; k < j; ++k) t -= M[i][k] * M[j][k];
       M[i][j] = t / M[j][j];
     }
   }
+#pragma unroll
   for (int i = 0; i < n; ++i)
+#pragma unroll
     for (int j = 0; j < n; ++j) L[i * n + j] = j <= i ? M[i][j] : 0.0;
   // the inverse, column by column from the factor (L[n*n ..]: row-major, used
   // by the single-block tail of the FP32 V-cycle)
   double* Ainv = L + n * n;
+#pragma unroll
   for (int c = 0; c < n; ++c) {
     double z[NV];
+#pragma unroll
     for (int i = 0; i < n; ++i) {
       double t = i == c ? 1.0 : 0.0;
+#pragma unroll
       for (int k = 0; k < i; ++k) t -= M[i][k] * z[k];
       z[i] = t / M[i][i];
     }
+#pragma unroll
     for (int i = n - 1; i >= 0; --i) {
       double t = z[i];
+#pragma unroll
       for (int k = i + 1; k < n; ++k) t -= M[k][i] * z[k];
       z[i] = t / M[i][i];
     }
+#pragma unroll
     for (int i = 0; i < n; ++i) Ainv[i * n + c] = z[i];
   }
 }

@@ -1492,23 +1492,31 @@ __global__ void geo_weights64_kernel(int N, const double* __restrict__ eps64, co
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
        v += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(v % n1), j = (int)((v / n1) % n1), k = (int)(v / ((long long)n1 * n1));
+    // e[c][b][a]: eps of the cell (i - 1 + a, j - 1 + b, k - 1 + c) at v (0 outside)
+    double e[2][2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) e[c][b][a] = E(i - 1 + a, j - 1 + b, k - 1 + c);
     double g = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
 #pragma unroll
-    for (int a = -1; a <= 0; ++a)
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int b = -1; b <= 0; ++b) {
-        ex += E(i, j + a, k + b);   // cells at the edge (v, v+x): x index i
-        ey += E(i + a, j, k + b);
-        ez += E(i + a, j + b, k);
+      for (int b = 0; b < 2; ++b) {
+        ex += e[c][b][1];   // cells at the edge (v, v+x): x index i
+        ey += e[c][1][b];
+        ez += e[1][c][b];
 #pragma unroll
-        for (int c = -1; c <= 0; ++c) g += E(i + a, j + b, k + c);
+        for (int a = 0; a < 2; ++a) g += e[c][b][a];
       }
     gs[v] = 5.0 * h12 * g;
     wx[v] = h12 * ex;
     wy[v] = h12 * ey;
     wz[v] = h12 * ez;
     // padded cell row: cell (i, j, k) for i < N, zero at i = N
-    if (j < N && k < N) es[((size_t)k * N + j) * n1 + i] = i < N ? h12 * E(i, j, k) : 0.0;
+    if (j < N && k < N) es[((size_t)k * N + j) * n1 + i] = h12 * e[1][1][1];   // zero at i = N
   }
 }
 
