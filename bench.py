@@ -360,14 +360,18 @@ def run_ours(args, rank, world, local_rank):
     nvert = (n + 1) ** dim
     # the result lands in pinned host memory (the copy runs at the host link's speed)
     u_host = torch.empty(nvert, dtype=torch.float64, pin_memory=True).numpy()
-    for _ in range(max(1, args.e2e_steps)):
+    # one untimed step first, as the device loop has its warm-up steps: the
+    # first creation of a problem of this footprint grows the device memory
+    # pool (about 30 ms once per process; 3 ms per creation afterwards)
+    for step in range(1 + max(1, args.e2e_steps)):
         barrier()
         t0 = time.perf_counter()
         with mg.Problem(workload_desc(mg, args.workload, mixed_path)[1]) as P:
             P.solve()
             P.solution(out=u_host)
         barrier()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if step > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = rep.aggregate(len(e2e_ms), max_over_ranks(sum(e2e_ms)))
     # the mixed path's solution under the FP64 operator of the final accuracy:
     # how far the lossy FP32 surplus storage moves the answer
@@ -734,7 +738,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="boxes3d", choices=["boxes3d", "fourier3d", "jump3d", "disc2d"])
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-cycles", type=int, default=140,
                     help="cycle count used to scale the oracle sample in --impl reference: the FP64 "
                          "assemble-then-solve iteration the oracle runs needs 140 cycles on boxes3d 243^3")
