@@ -60,6 +60,10 @@ size_t estimate_bytes(const mg_problem_desc& d) {
   const double ns = D == 3 ? 14.0 : 5.0;                                 // vertex stencils (symmetric)
   bytes += (mixed ? 0.0 : nv * ns * 8) + nv / (D == 3 ? 27.0 : 9.0) * ns * (mixed ? 4 : 8) * 1.05;
   if (mixed && D == 3) bytes += nv * 5 + (nv / 4) * 27 * 4;   // touched list, flags, stencil table
+  if (mixed && D == 3) {
+    bytes += nv * 4 * 8 + nc * 8 * 1.01;   // FP64 bulk pass in vertex form: vertex and edge weights, scaled eps
+    bytes += nc * 12 + nv * 4;             // exact FP64 operator: eps64, list positions, touched vertices
+  }
   bytes += 64ull << 20;                             // partials, tables, pool slack
   return (size_t)bytes;
 }
