@@ -284,6 +284,59 @@ def test_jacobi_matches_dense_formula():
     np.testing.assert_allclose(oracle.apply(dim, n, A, u)[m], Mi @ u[m], atol=1e-13)
 
 
+def test_geometric_operator_in_factored_and_vertex_form():
+    # The geometric part eps_c K_ref h of every cell (s = 1, Section "Numerical
+    # computation of stencils") applied in the factored form the bulk passes
+    # use: with 12 K_ref = 5 I + E - J (E: adjacency along cell edges, J: all
+    # ones), (A u)_v = h/12 [5 G_v u_v + sum_{6 axis neighbours w} W_vw u_w
+    # - sum_{8 cells c at v} eps_c T_c], G_v the eps summed over the cells at v,
+    # W_vw over the 4 cells at the edge vw, T_c the sum of u over c's vertices.
+    # The FP64 vertex form loads 5h/12 G_v and h/12 W of the edges leaving v.
+    n = 9
+    h = 1.0 / n
+    f = oracle.Field(inputs.boxes_field(3, 8, n_boxes=12, side=(0.15, 0.4)))
+    A = oracle.assemble(f, n, 1)
+    eps = np.zeros((n + 2, n + 2, n + 2))   # [cz + 1][cy + 1][cx + 1], zero outside the grid
+    for cz in range(n):
+        for cy in range(n):
+            for cx in range(n):
+                eps[cz + 1, cy + 1, cx + 1] = oracle.eps_at(f, [(cx + 0.5) * h, (cy + 0.5) * h, (cz + 0.5) * h])
+    assert len(np.unique(eps[1:-1, 1:-1, 1:-1])) == 2   # both the boxes and the background
+    # 12 K_ref = 5 I + E - J on the unit cell (the cell's matrix is eps_c K_ref h)
+    K = kref_closed(3)
+    E = np.array([[1.0 if bin(a ^ b).count("1") == 1 else 0.0 for b in range(8)] for a in range(8)])
+    np.testing.assert_allclose(12 * K, 5 * np.eye(8) + E - np.ones((8, 8)), atol=1e-14)
+    rng = np.random.default_rng(21)
+    n1 = n + 1
+    u = rng.standard_normal((n1, n1, n1))
+    u[0, :, :] = u[-1, :, :] = u[:, 0, :] = u[:, -1, :] = u[:, :, 0] = u[:, :, -1] = 0.0
+    ref = oracle.apply(3, n, A, u.reshape(-1)).reshape(n1, n1, n1)
+
+    def e(k, j, i):   # eps of cell (i, j, k), zero outside
+        return eps[k + 1, j + 1, i + 1]
+
+    got = np.zeros_like(ref)
+    for k in range(1, n):
+        for j in range(1, n):
+            for i in range(1, n):
+                cells = [(i - 1 + a, j - 1 + b, k - 1 + c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+                G = sum(e(cz, cy, cx) for cx, cy, cz in cells)
+                wx = [sum(e(k - 1 + c, j - 1 + b, i - 1 + a) for c in (0, 1) for b in (0, 1)) for a in (0, 1)]
+                wy = [sum(e(k - 1 + c, j - 1 + b, i - 1 + a) for c in (0, 1) for a in (0, 1)) for b in (0, 1)]
+                wz = [sum(e(k - 1 + c, j - 1 + b, i - 1 + a) for b in (0, 1) for a in (0, 1)) for c in (0, 1)]
+                axis = (wx[0] * u[k, j, i - 1] + wx[1] * u[k, j, i + 1] + wy[0] * u[k, j - 1, i]
+                        + wy[1] * u[k, j + 1, i] + wz[0] * u[k - 1, j, i] + wz[1] * u[k + 1, j, i])
+                cellsum = 0.0
+                for cx, cy, cz in cells:
+                    T = u[cz:cz + 2, cy:cy + 2, cx:cx + 2].sum()
+                    cellsum += e(cz, cy, cx) * T
+                got[k, j, i] = h / 12 * (5 * G * u[k, j, i] + axis - cellsum)
+    m = np.zeros((n1, n1, n1), bool)
+    m[1:n, 1:n, 1:n] = True
+    scale = np.abs(ref[m]).max()
+    np.testing.assert_allclose(got[m], ref[m], rtol=0, atol=1e-12 * scale)
+
+
 @pytest.mark.parametrize("dim,n,fld", [(2, 9, inputs.disc_field(2)), (2, 27, inputs.boxes_field(2, 5)),
                                        (3, 9, inputs.fourier_field(3, 6, sigma=1.0)),
                                        (2, 3, inputs.disc_field(2))])
